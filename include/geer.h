@@ -1,0 +1,183 @@
+/*
+ * geer.h -- C ABI of the GB300 (sm_103a) exact ray-Gaussian renderer.
+ *
+ * The library implements the data-parallel hot path of 3DGEER (arXiv
+ * 2505.24053): per-Gaussian preprocessing with Particle Bounding Frustum (PBF)
+ * association to the tiles of a Bipolar Equiangular Projection (BEAP) grid,
+ * duplication of (tile, depth) keys, a radix sort, per-tile ranges, the
+ * closed-form ray integral with front-to-back compositing, and its backward
+ * pass (Algorithm 1 "GPU Software Asso. & Render"; App. C gradient cookbook).
+ *
+ * Conventions for every entry point:
+ *  - All pointers to Gaussian data, images and gradients are DEVICE pointers
+ *    (cudaMalloc'd or equivalent) owned by the caller. Camera and parameter
+ *    structs are HOST pointers, read during the call only.
+ *  - `stream` is a cudaStream_t passed as void*. Every call that takes one is
+ *    asynchronous on it, except where stated.
+ *  - The library never allocates device memory. All scratch lives in the
+ *    caller-supplied workspace (geer_workspace_size / geer_workspace_init).
+ *    The host-side workspace handle is malloc'ed by geer_workspace_init and
+ *    freed by geer_workspace_destroy.
+ *  - Argument errors are detected on the host and returned synchronously; no
+ *    work is enqueued in that case. Device-side conditions (pair capacity
+ *    exceeded, bounded spin timeout) are recorded in a device status word and
+ *    read back by geer_last_device_status.
+ *  - One workspace must not be used from two streams concurrently.
+ *  - Angles are radians. Cameras use OpenCV axes: x right, y down, z forward.
+ */
+#ifndef GEER_H
+#define GEER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GEER_OK = 0,
+    GEER_ERR_ARG = 1,         /* invalid argument (null, negative size, bad camera, ...) */
+    GEER_ERR_CAPACITY = 2,    /* more (tile, Gaussian) pairs than the workspace holds */
+    GEER_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    GEER_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    GEER_ERR_UNSUPPORTED = 5, /* a valid request this build does not implement */
+    GEER_ERR_STATE = 6        /* call out of order (e.g. render before bin_sort) */
+} geer_status;
+
+/* Camera models (App. E): pinhole K (tan theta, tan phi, 1); equidistant
+ * fisheye r = f phi; Kannala-Brandt r = f phi (1 + k1 phi^2 + ... + k4 phi^8). */
+enum { GEER_PINHOLE = 0, GEER_EQUIDISTANT = 1, GEER_KANNALA_BRANDT = 2 };
+
+/* Gaussians (App. B.1): mean mu, scale s (linear, > 0), rotation quaternion q
+ * = (w, x, y, z) of any non-zero norm (normalised internally), opacity sigma
+ * (activated, in (0, 1]) and real SH coefficients of degree sh_degree <= 3
+ * in the 3DGS convention. Device SoA, FP32, contiguous:
+ *   mean [n][3], scale [n][3], quat [n][4], opacity [n], sh [n][(deg+1)^2][3].
+ * `sh` must be 16-byte aligned. Gaussians with non-finite values, a
+ * non-positive scale or a zero quaternion are culled. */
+typedef struct {
+    const float *mean, *scale, *quat, *opacity, *sh;
+    int64_t n;
+    int32_t sh_degree;
+    int32_t reserved_;
+} geer_gaussians;
+
+/* A camera and its BEAP grid (Sec. 3.3). The BEAP image is width x height
+ * rays uniform in (theta, phi): pixel (i, j) has theta = ((i + 1/2)/w - 1/2)
+ * fov_x and phi = ((j + 1/2)/h - 1/2) fov_y, direction (App. E)
+ * (sin theta cos phi, cos theta sin phi, cos theta cos phi). fov_y <= 0 derives
+ * the vertical field of view from the camera model: the angle that the same
+ * focal length (the one mapping fov_x/2 to w/2) maps to h/2. 0 < fov_x < 2 pi.
+ * R_cw, t_cw: world -> camera (x_c = R_cw x_w + t_cw), row-major. bg: colour
+ * composited behind the last contributor. */
+typedef struct {
+    int32_t model;
+    int32_t width, height;
+    float fov_x, fov_y;
+    float k[4];
+    float R_cw[9];
+    float t_cw[3];
+    float bg[3];
+} geer_camera;
+
+/* Rendering parameters. tile_w = tile_h = 16 (BEAP tiles of 16 x 16 rays,
+ * each tile a camera sub-frustum, Sec. 3.2). alpha_min: contributions below it
+ * are skipped; alpha_max: alpha clamp; T_min: a ray stops before the
+ * contributor that would take its transmittance below it (3DGS conventions
+ * 1/255, 0.99, 1e-4). lambda_pad: relative padding of the per-Gaussian PBF
+ * contour lambda^2 = 2 ln(sigma/alpha_min) (default 1e-3). */
+typedef struct {
+    int32_t tile_w, tile_h;
+    float alpha_min, T_min, alpha_max, lambda_pad;
+} geer_params;
+
+typedef struct geer_workspace geer_workspace;
+
+/* Human-readable name of a status code. Never returns NULL. */
+const char *geer_status_string(geer_status s);
+
+/* Fill *p with the defaults (16, 16, 1/255, 1e-4, 0.99, 1e-3). */
+geer_status geer_default_params(geer_params *p);
+
+/* Device bytes needed for a workspace rendering `n_cams` cameras (whose sizes
+ * are the capacity: later camera sets must not exceed the total pixel and tile
+ * counts nor n_cams) of up to n_gauss Gaussians of SH degree <= sh_degree with
+ * up to pair_capacity (tile, Gaussian) pairs. Host-only; synchronous. */
+geer_status geer_workspace_size(const geer_camera *cams, int32_t n_cams, int64_t n_gauss, int32_t sh_degree,
+                                int64_t pair_capacity, size_t *bytes);
+
+/* Lay a workspace out in caller-owned device memory dev_mem[bytes] (256-byte
+ * aligned) and upload the camera tables (synchronous copies). *ws receives a
+ * host handle; release it with geer_workspace_destroy (dev_mem stays the
+ * caller's). */
+geer_status geer_workspace_init(void *dev_mem, size_t bytes, const geer_camera *cams, int32_t n_cams,
+                                int64_t n_gauss, int32_t sh_degree, int64_t pair_capacity,
+                                const geer_params *params, geer_workspace **ws);
+
+geer_status geer_workspace_destroy(geer_workspace *ws);
+
+/* Replace the camera set (same capacity limits as at init). The tables are
+ * staged in pinned host memory owned by the workspace and copied
+ * asynchronously on `stream`; the call returns once they are staged. */
+geer_status geer_set_cameras(geer_workspace *ws, const geer_camera *cams, int32_t n_cams, void *stream);
+
+/* Preprocess (Algorithm 1: CullGaussian, ViewspaceGaussians, PBF_Intersect,
+ * PCA_Whitening; Sec. 3.2, App. D): for every (camera, Gaussian) the cull
+ * decision, the depth key |mu_c|, the PBF tile ranges, the tile count, the
+ * whitening W = S^-1 R^T in the camera frame, o_u, and the view-dependent
+ * colour. The Gaussians must have n <= the workspace's n_gauss and
+ * sh_degree <= its sh_degree, and stay valid until geer_render_fwd (and
+ * geer_render_bwd) have run. */
+geer_status geer_preprocess(geer_workspace *ws, const geer_gaussians *g, void *stream);
+
+/* DuplicateWithKeys, SortByKeys, IdentifyFrustumRanges (Algorithm 1): emit one
+ * (key = global tile << 32 | depth bits, value = camera * n + gaussian) pair
+ * per associated tile, radix-sort them (stable, so equal depths keep Gaussian
+ * order) and build each tile's [start, end). If pairs_needed is non-NULL the
+ * call synchronises `stream` to read the pair count, writes it to
+ * *pairs_needed and returns GEER_ERR_CAPACITY without sorting when it exceeds
+ * the capacity. If NULL the call stays asynchronous; an overflow is then
+ * recorded in the device status word and the render calls produce nothing. */
+geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *stream);
+
+/* Render every BEAP ray (Algorithm 1 per-CSF loop: Cano_Ray, Dist,
+ * BlendInOrder): o_u, d_u = W d, m_u = o_u x d_u, kappa = |m_u|^2/|d_u|^2,
+ * alpha = min(alpha_max, sigma exp(-kappa/2)) (Sec. 3.1), composited front to
+ * back in depth order (App. B.1 colour equation) with early termination.
+ * rgb: device [sum of h*w over cameras][3] f32, cameras in order, row-major.
+ * T_final: device [sum h*w] f32 or NULL. Both caller-owned, overwritten. */
+geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void *stream);
+
+/* Backward of geer_render_fwd (App. C two-stage RenderCUDA / PreprocessCUDA):
+ * given dL/drgb (same layout as rgb), ACCUMULATE (+=) the gradients of the
+ * Gaussians used in the last forward into d_mean [n][3], d_scale [n][3],
+ * d_quat [n][4], d_opacity [n], d_sh [n][(deg+1)^2][3] (device, caller-owned,
+ * any of them may be NULL to skip). Must follow geer_render_fwd on the same
+ * workspace with the same Gaussians. */
+geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const float *dL_drgb, float *d_mean,
+                            float *d_scale, float *d_quat, float *d_opacity, float *d_sh, void *stream);
+
+/* Synchronise `stream`, then read and clear the device status word: GEER_OK,
+ * GEER_ERR_CAPACITY (pairs exceeded capacity) or GEER_ERR_TIMEOUT (a bounded
+ * spin gave up). *pairs (may be NULL) receives the last pair count. */
+geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *stream);
+
+/* Debug/inspection (synchronous): copy the per-(camera, Gaussian) preprocess
+ * results into HOST buffers, each sized n_cams * n (any may be NULL):
+ * ranges [.][8] u16 {X0lo, X0hi, X1lo, X1hi, Y0lo, Y0hi, Y1lo, Y1hi}
+ * (X*: tile columns for rows with cos(phi) >= 0 / <= 0, Y*: tile rows for
+ * columns with cos(theta) >= 0 / <= 0), tile counts u32, depth keys u32,
+ * cull flags u8. */
+geer_status geer_debug_preprocess(geer_workspace *ws, uint16_t *ranges, uint32_t *counts, uint32_t *keys,
+                                  uint8_t *cull, void *stream);
+
+/* Debug/inspection (synchronous): copy up to cap sorted pairs (keys u64,
+ * values u32) into HOST buffers; *count receives the pair count. */
+geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *values, int64_t cap, int64_t *count,
+                             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEER_H */

@@ -1,0 +1,519 @@
+// geer_host.cu -- the C ABI (include/geer.h): argument checks, camera and BEAP
+// table setup, workspace layout and the launch sequence of each stage.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "geer_internal.cuh"
+
+using namespace geer;
+
+namespace {
+
+struct Layout {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    }
+};
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Kannala-Brandt distorted angle phi (1 + k1 phi^2 + k2 phi^4 + k3 phi^6 + k4 phi^8) (App. E).
+double kb_theta_d(const float k[4], double phi) {
+    const double p2 = phi * phi;
+    return phi * (1.0 + p2 * (k[0] + p2 * (k[1] + p2 * (k[2] + p2 * k[3]))));
+}
+
+// Vertical BEAP field of view: the vertical half-angle that the focal length
+// mapping fov_x/2 to w/2 maps to h/2 (pinhole: tan; equidistant: linear;
+// Kannala-Brandt: smallest root of the distortion polynomial).
+double derived_fov_y(const geer_camera &c) {
+    if (c.fov_y > 0.0f) return (double)c.fov_y;
+    const double fx = c.fov_x, w = c.width, h = c.height;
+    if (c.model == GEER_PINHOLE) return 2.0 * atan(tan(0.5 * fx) * h / w);
+    if (c.model == GEER_EQUIDISTANT) return fx * h / w;
+    const double edge = kb_theta_d(c.k, 0.5 * fx);
+    if (!(edge > 0.0)) return NAN;
+    const double target = edge * h / w;
+    // bracket the first crossing on a fine grid, then bisect
+    double lo = 0.0, hi = 0.5 * fx;
+    const int n = 8192;
+    for (int s = 1; s <= n; ++s) {
+        const double ph = 0.5 * fx * s / n;
+        if (kb_theta_d(c.k, ph) >= target) {
+            hi = ph;
+            lo = 0.5 * fx * (s - 1) / n;
+            break;
+        }
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (kb_theta_d(c.k, mid) >= target) hi = mid; else lo = mid;
+    }
+    return 2.0 * hi;
+}
+
+// BEAP pixel-centre angle (Sec. 3.3): ((i + 1/2)/w - 1/2) FoV.
+inline double beap_angle(int i, int w, double fov) { return ((i + 0.5) / w - 0.5) * fov; }
+
+bool camera_ok(const geer_camera &c) {
+    if (c.width <= 0 || c.height <= 0 || c.width > 65535 * kTile || c.height > 65535 * kTile) return false;
+    if (!(c.fov_x > 0.0f) || !(c.fov_x < 6.2831f)) return false;
+    if (c.model < GEER_PINHOLE || c.model > GEER_KANNALA_BRANDT) return false;
+    if (c.model == GEER_PINHOLE && !(c.fov_x < 3.1415f)) return false;
+    const double fy = derived_fov_y(c);
+    if (!(fy > 0.0) || !(fy < 6.2831)) return false;
+    if (c.model == GEER_PINHOLE && !(fy < 3.1415)) return false;
+    for (float v : c.R_cw) if (!isfinite(v)) return false;
+    for (float v : c.t_cw) if (!isfinite(v)) return false;
+    return true;
+}
+
+struct CamTables {
+    std::vector<DevCam> cams;
+    std::vector<float4> ttab;
+    std::vector<float2> ptab;
+    int64_t pixels = 0, tiles = 0;
+};
+
+// Per camera: tile-column/-row half-angle spans tan(angle/2) of the first and
+// last ray of the tile with flags for cos(angle) >= 0 / <= 0 (rays beyond 90 deg
+// flip the other dihedral angle by pi), per-pixel sin/cos of theta and phi.
+void build_tables(const geer_camera *cams, int n, CamTables &out) {
+    out = CamTables();
+    for (int ci = 0; ci < n; ++ci) {
+        const geer_camera &c = cams[ci];
+        DevCam d;
+        memset(&d, 0, sizeof(d));
+        d.width = c.width;
+        d.height = c.height;
+        d.tiles_x = (int)ceil_div(c.width, kTile);
+        d.tiles_y = (int)ceil_div(c.height, kTile);
+        d.tile_base = (int32_t)out.tiles;
+        d.pix_base = out.pixels;
+        const double fx = c.fov_x, fy = derived_fov_y(c);
+        d.tcol_off = (int32_t)out.ttab.size();
+        for (int tx = 0; tx < d.tiles_x; ++tx) {
+            const int i0 = tx * kTile, i1 = std::min(i0 + kTile - 1, c.width - 1);
+            float4 v;
+            v.x = (float)tan(0.5 * beap_angle(i0, c.width, fx));
+            v.y = (float)tan(0.5 * beap_angle(i1, c.width, fx));
+            v.z = 0.0f;
+            v.w = 0.0f;
+            for (int i = i0; i <= i1; ++i) {
+                const double cs = cos(beap_angle(i, c.width, fx));
+                if (cs > -1e-12) v.z = 1.0f;
+                if (cs < 1e-12) { v.w = 1.0f; d.any_col_flip = 1; }
+            }
+            out.ttab.push_back(v);
+        }
+        d.trow_off = (int32_t)out.ttab.size();
+        for (int ty = 0; ty < d.tiles_y; ++ty) {
+            const int j0 = ty * kTile, j1 = std::min(j0 + kTile - 1, c.height - 1);
+            float4 v;
+            v.x = (float)tan(0.5 * beap_angle(j0, c.height, fy));
+            v.y = (float)tan(0.5 * beap_angle(j1, c.height, fy));
+            v.z = 0.0f;
+            v.w = 0.0f;
+            for (int j = j0; j <= j1; ++j) {
+                const double cs = cos(beap_angle(j, c.height, fy));
+                if (cs > -1e-12) v.z = 1.0f;
+                if (cs < 1e-12) { v.w = 1.0f; d.any_row_flip = 1; }
+            }
+            out.ttab.push_back(v);
+        }
+        d.pcol_off = (int32_t)out.ptab.size();
+        for (int i = 0; i < c.width; ++i) {
+            const double a = beap_angle(i, c.width, fx);
+            out.ptab.push_back(make_float2((float)sin(a), (float)cos(a)));
+        }
+        d.prow_off = (int32_t)out.ptab.size();
+        for (int j = 0; j < c.height; ++j) {
+            const double a = beap_angle(j, c.height, fy);
+            out.ptab.push_back(make_float2((float)sin(a), (float)cos(a)));
+        }
+        for (int k = 0; k < 9; ++k) d.R[k] = c.R_cw[k];
+        for (int k = 0; k < 3; ++k) {
+            d.t[k] = c.t_cw[k];
+            d.bg[k] = c.bg[k];
+            double o = 0.0;
+            for (int b = 0; b < 3; ++b) o -= (double)c.R_cw[3 * b + k] * (double)c.t_cw[b];
+            d.o[k] = (float)o;
+        }
+        out.cams.push_back(d);
+        out.tiles += (int64_t)d.tiles_x * d.tiles_y;
+        out.pixels += (int64_t)c.width * c.height;
+    }
+}
+
+struct Caps {
+    int32_t cams;
+    int64_t pixels, tiles, tile_tab, pix_tab, gauss, pairs, sort_tiles, prep_blocks;
+};
+
+Caps caps_of(const CamTables &t, int32_t n_cams, int64_t n_gauss, int64_t pair_capacity) {
+    Caps c;
+    c.cams = n_cams;
+    c.pixels = std::max<int64_t>(t.pixels, 1);
+    c.tiles = std::max<int64_t>(t.tiles, 1);
+    c.tile_tab = std::max<int64_t>((int64_t)t.ttab.size(), 1);
+    c.pix_tab = std::max<int64_t>((int64_t)t.ptab.size(), 1);
+    c.gauss = std::max<int64_t>(n_gauss, 1);
+    c.pairs = std::max<int64_t>(pair_capacity, 1);
+    c.sort_tiles = ceil_div(c.pairs, kSortTile) + 1;
+    c.prep_blocks = prep_blocks(c.gauss);
+    return c;
+}
+
+// Lays the arrays out; with base == nullptr only measures.
+size_t layout(const Caps &c, char *base, geer_workspace *ws) {
+    Layout L;
+    const int64_t cg = (int64_t)c.cams * c.gauss;
+    size_t o_cams = L.take(sizeof(DevCam) * c.cams);
+    size_t o_ttab = L.take(sizeof(float4) * c.tile_tab);
+    size_t o_ptab = L.take(sizeof(float2) * c.pix_tab);
+    size_t o_rec = L.take(sizeof(Record) * cg);
+    size_t o_rng = L.take(sizeof(uint4) * cg);
+    size_t o_cnt = L.take(sizeof(uint32_t) * cg);
+    size_t o_key = L.take(sizeof(uint32_t) * cg);
+    size_t o_bs = L.take(sizeof(uint32_t) * c.cams * c.prep_blocks);
+    size_t o_k0 = L.take(sizeof(uint64_t) * c.pairs);
+    size_t o_k1 = L.take(sizeof(uint64_t) * c.pairs);
+    size_t o_v0 = L.take(sizeof(uint32_t) * c.pairs);
+    size_t o_v1 = L.take(sizeof(uint32_t) * c.pairs);
+    size_t o_hist = L.take(sizeof(uint32_t) * kMaxPasses * kRadix);
+    size_t o_lb = L.take(sizeof(uint64_t) * kRadix * c.sort_tiles);
+    size_t o_misc = L.take(sizeof(uint32_t) * kMiscCount);
+    size_t o_tr = L.take(sizeof(uint2) * c.tiles);
+    size_t o_last = L.take(sizeof(uint32_t) * c.pixels);
+    size_t o_tfin = L.take(sizeof(float) * c.pixels);
+    size_t o_gacc = L.take(sizeof(GradAcc) * cg);
+    if (base && ws) {
+        ws->d_cams = reinterpret_cast<DevCam *>(base + o_cams);
+        ws->d_tile_tab = reinterpret_cast<float4 *>(base + o_ttab);
+        ws->d_pix_tab = reinterpret_cast<float2 *>(base + o_ptab);
+        ws->d_rec = reinterpret_cast<Record *>(base + o_rec);
+        ws->d_ranges = reinterpret_cast<uint4 *>(base + o_rng);
+        ws->d_count = reinterpret_cast<uint32_t *>(base + o_cnt);
+        ws->d_key = reinterpret_cast<uint32_t *>(base + o_key);
+        ws->d_blocksum = reinterpret_cast<uint32_t *>(base + o_bs);
+        ws->d_keys[0] = reinterpret_cast<uint64_t *>(base + o_k0);
+        ws->d_keys[1] = reinterpret_cast<uint64_t *>(base + o_k1);
+        ws->d_vals[0] = reinterpret_cast<uint32_t *>(base + o_v0);
+        ws->d_vals[1] = reinterpret_cast<uint32_t *>(base + o_v1);
+        ws->d_hist = reinterpret_cast<uint32_t *>(base + o_hist);
+        ws->d_lookback = reinterpret_cast<uint64_t *>(base + o_lb);
+        ws->d_misc = reinterpret_cast<uint32_t *>(base + o_misc);
+        ws->d_tile_range = reinterpret_cast<uint2 *>(base + o_tr);
+        ws->d_last = reinterpret_cast<uint32_t *>(base + o_last);
+        ws->d_Tfin = reinterpret_cast<float *>(base + o_tfin);
+        ws->d_gacc = reinterpret_cast<GradAcc *>(base + o_gacc);
+    }
+    return L.off;
+}
+
+geer_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GEER_OK : GEER_ERR_CUDA; }
+
+geer_status check_cams(const geer_camera *cams, int32_t n) {
+    if (!cams || n <= 0 || n > kMaxCams) return GEER_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!camera_ok(cams[i])) return GEER_ERR_ARG;
+    return GEER_OK;
+}
+
+geer_status check_params(const geer_params *p) {
+    if (!p) return GEER_ERR_ARG;
+    if (p->tile_w != kTile || p->tile_h != kTile) return GEER_ERR_UNSUPPORTED;
+    if (!(p->alpha_min > 0.0f) || !(p->alpha_min < 1.0f)) return GEER_ERR_ARG;
+    if (!(p->alpha_max > 0.0f) || !(p->alpha_max < 1.0f) || p->alpha_max < p->alpha_min) return GEER_ERR_ARG;
+    if (!(p->T_min >= 0.0f) || !(p->T_min < 1.0f)) return GEER_ERR_ARG;
+    if (!(p->lambda_pad >= 0.0f) || !(p->lambda_pad < 1.0f)) return GEER_ERR_ARG;
+    return GEER_OK;
+}
+
+geer_status check_gaussians(const geer_workspace *ws, const geer_gaussians *g) {
+    if (!g || g->n < 0 || g->n > ws->cap_gauss) return GEER_ERR_ARG;
+    if (g->sh_degree < 0 || g->sh_degree > 3 || g->sh_degree > ws->cap_sh_degree) return GEER_ERR_ARG;
+    if ((int64_t)ws->n_cams * g->n > 0xffffffffll) return GEER_ERR_ARG;
+    if (g->n > 0 && (!g->mean || !g->scale || !g->quat || !g->opacity || !g->sh)) return GEER_ERR_ARG;
+    if (g->n > 0 && (reinterpret_cast<uintptr_t>(g->sh) & 15)) return GEER_ERR_ARG;
+    return GEER_OK;
+}
+
+// Upload the camera set: stage in pinned memory, then one async copy per array.
+geer_status upload_cams(geer_workspace *ws, const CamTables &t, cudaStream_t s) {
+    const size_t b0 = sizeof(DevCam) * t.cams.size();
+    const size_t b1 = sizeof(float4) * t.ttab.size();
+    const size_t b2 = sizeof(float2) * t.ptab.size();
+    if (b0 + b1 + b2 > ws->stage_bytes) return GEER_ERR_ARG;
+    // the staging buffer may still be read by a previous copy on this stream
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return GEER_ERR_CUDA;
+    char *h = static_cast<char *>(ws->h_stage);
+    memcpy(h, t.cams.data(), b0);
+    memcpy(h + b0, t.ttab.data(), b1);
+    memcpy(h + b0 + b1, t.ptab.data(), b2);
+    if ((e = cudaMemcpyAsync(ws->d_cams, h, b0, cudaMemcpyHostToDevice, s)) != cudaSuccess) return GEER_ERR_CUDA;
+    if (b1 && (e = cudaMemcpyAsync(ws->d_tile_tab, h + b0, b1, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    if (b2 && (e = cudaMemcpyAsync(ws->d_pix_tab, h + b0 + b1, b2, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    ws->n_cams = (int32_t)t.cams.size();
+    ws->n_pixels = t.pixels;
+    ws->n_tiles = t.tiles;
+    std::copy(t.cams.begin(), t.cams.end(), ws->cams);
+    int bits = 1;
+    while ((int64_t(1) << bits) < t.tiles) ++bits;
+    ws->tile_bits = bits;
+    ws->n_passes = (32 + bits + kRadixBits - 1) / kRadixBits;
+    ws->stage = 0;
+    return GEER_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *geer_status_string(geer_status s) {
+    switch (s) {
+        case GEER_OK: return "ok";
+        case GEER_ERR_ARG: return "invalid argument";
+        case GEER_ERR_CAPACITY: return "pair capacity exceeded";
+        case GEER_ERR_CUDA: return "CUDA error";
+        case GEER_ERR_TIMEOUT: return "bounded device wait timed out";
+        case GEER_ERR_UNSUPPORTED: return "unsupported";
+        case GEER_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+geer_status geer_default_params(geer_params *p) {
+    if (!p) return GEER_ERR_ARG;
+    p->tile_w = kTile;
+    p->tile_h = kTile;
+    p->alpha_min = 1.0f / 255.0f;
+    p->T_min = 1e-4f;
+    p->alpha_max = 0.99f;
+    p->lambda_pad = 1e-3f;
+    return GEER_OK;
+}
+
+geer_status geer_workspace_size(const geer_camera *cams, int32_t n_cams, int64_t n_gauss, int32_t sh_degree,
+                                int64_t pair_capacity, size_t *bytes) {
+    if (!bytes || n_gauss < 0 || pair_capacity < 0 || sh_degree < 0 || sh_degree > 3) return GEER_ERR_ARG;
+    geer_status st = check_cams(cams, n_cams);
+    if (st != GEER_OK) return st;
+    if ((int64_t)n_cams * n_gauss > 0xffffffffll || pair_capacity > 0xffffffffll) return GEER_ERR_ARG;
+    CamTables t;
+    build_tables(cams, n_cams, t);
+    *bytes = layout(caps_of(t, n_cams, n_gauss, pair_capacity), nullptr, nullptr);
+    return GEER_OK;
+}
+
+geer_status geer_workspace_init(void *dev_mem, size_t bytes, const geer_camera *cams, int32_t n_cams,
+                                int64_t n_gauss, int32_t sh_degree, int64_t pair_capacity,
+                                const geer_params *params, geer_workspace **out) {
+    if (!out) return GEER_ERR_ARG;
+    *out = nullptr;
+    if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) & 255)) return GEER_ERR_ARG;
+    size_t need = 0;
+    geer_status st = geer_workspace_size(cams, n_cams, n_gauss, sh_degree, pair_capacity, &need);
+    if (st != GEER_OK) return st;
+    if (bytes < need) return GEER_ERR_ARG;
+    geer_params pd;
+    geer_default_params(&pd);
+    if (!params) params = &pd;
+    if ((st = check_params(params)) != GEER_OK) return st;
+
+    geer_workspace *ws = static_cast<geer_workspace *>(calloc(1, sizeof(geer_workspace)));
+    if (!ws) return GEER_ERR_ARG;
+    CamTables t;
+    build_tables(cams, n_cams, t);
+    const Caps c = caps_of(t, n_cams, n_gauss, pair_capacity);
+    layout(c, static_cast<char *>(dev_mem), ws);
+    ws->cap_cams = c.cams;
+    ws->cap_pixels = c.pixels;
+    ws->cap_tiles = c.tiles;
+    ws->cap_tile_tab = c.tile_tab;
+    ws->cap_pix_tab = c.pix_tab;
+    ws->cap_gauss = n_gauss;
+    ws->cap_pairs = pair_capacity;
+    ws->cap_sh_degree = sh_degree;
+    ws->cap_sort_tiles = c.sort_tiles;
+    ws->params = Params{params->alpha_min, params->T_min, params->alpha_max, params->lambda_pad};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { free(ws); return GEER_ERR_CUDA; }
+    ws->sort_grid = ws->num_sms * sort_blocks_per_sm();
+    ws->stage_bytes = sizeof(DevCam) * c.cams + sizeof(float4) * c.tile_tab + sizeof(float2) * c.pix_tab;
+    if (cudaMallocHost(&ws->h_stage, ws->stage_bytes) != cudaSuccess) { free(ws); return GEER_ERR_CUDA; }
+    // status words and look-back tags start from zero
+    e = cudaMemset(ws->d_misc, 0, sizeof(uint32_t) * kMiscCount);
+    if (e == cudaSuccess) e = cudaMemset(ws->d_lookback, 0, sizeof(uint64_t) * kRadix * c.sort_tiles);
+    if (e != cudaSuccess) { cudaFreeHost(ws->h_stage); free(ws); return GEER_ERR_CUDA; }
+    st = upload_cams(ws, t, 0);
+    if (st == GEER_OK && cudaStreamSynchronize(0) != cudaSuccess) st = GEER_ERR_CUDA;
+    if (st != GEER_OK) { cudaFreeHost(ws->h_stage); free(ws); return st; }
+    *out = ws;
+    return GEER_OK;
+}
+
+geer_status geer_workspace_destroy(geer_workspace *ws) {
+    if (!ws) return GEER_ERR_ARG;
+    if (ws->h_stage) cudaFreeHost(ws->h_stage);
+    free(ws);
+    return GEER_OK;
+}
+
+geer_status geer_set_cameras(geer_workspace *ws, const geer_camera *cams, int32_t n_cams, void *stream) {
+    if (!ws) return GEER_ERR_ARG;
+    geer_status st = check_cams(cams, n_cams);
+    if (st != GEER_OK) return st;
+    if (n_cams > ws->cap_cams) return GEER_ERR_ARG;
+    CamTables t;
+    build_tables(cams, n_cams, t);
+    if (t.pixels > ws->cap_pixels || t.tiles > ws->cap_tiles || (int64_t)t.ttab.size() > ws->cap_tile_tab ||
+        (int64_t)t.ptab.size() > ws->cap_pix_tab)
+        return GEER_ERR_ARG;
+    return upload_cams(ws, t, static_cast<cudaStream_t>(stream));
+}
+
+geer_status geer_preprocess(geer_workspace *ws, const geer_gaussians *g, void *stream) {
+    if (!ws) return GEER_ERR_ARG;
+    geer_status st = check_gaussians(ws, g);
+    if (st != GEER_OK) return st;
+    ws->n_gauss = g->n;
+    ws->sh_degree = g->sh_degree;
+    ws->stage = 1;
+    return cuda_status(launch_preprocess(ws, g, static_cast<cudaStream_t>(stream)));
+}
+
+geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *stream) {
+    if (!ws) return GEER_ERR_ARG;
+    if (ws->stage < 1) return GEER_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_scan_blocks(ws, s);
+    if (e != cudaSuccess) return GEER_ERR_CUDA;
+    if (pairs_needed) {
+        uint32_t m[kMiscCount];
+        if (cudaMemcpyAsync(m, ws->d_misc, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return GEER_ERR_CUDA;
+        const int64_t total = ((int64_t)m[kMiscPairsHi] << 32) | (int64_t)m[kMiscTotalLo];
+        *pairs_needed = total;
+        if (total > ws->cap_pairs) {
+            // clear the capacity bit: the caller resizes and retries
+            uint32_t zero = 0;
+            cudaMemcpyAsync(ws->d_misc + kMiscStatus, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
+            cudaStreamSynchronize(s);
+            ws->stage = 1;
+            return GEER_ERR_CAPACITY;
+        }
+    }
+    if ((e = launch_duplicate(ws, s)) != cudaSuccess) return GEER_ERR_CUDA;
+    if ((e = launch_sort(ws, s)) != cudaSuccess) return GEER_ERR_CUDA;
+    if ((e = launch_ranges(ws, s)) != cudaSuccess) return GEER_ERR_CUDA;
+    ws->stage = 2;
+    return GEER_OK;
+}
+
+geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void *stream) {
+    if (!ws || !rgb) return GEER_ERR_ARG;
+    if (ws->stage < 2) return GEER_ERR_STATE;
+    geer_status st = cuda_status(launch_render_fwd(ws, rgb, T_final, static_cast<cudaStream_t>(stream)));
+    if (st == GEER_OK) ws->stage = 3;
+    return st;
+}
+
+geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const float *dL_drgb, float *d_mean,
+                            float *d_scale, float *d_quat, float *d_opacity, float *d_sh, void *stream) {
+    if (!ws || !dL_drgb) return GEER_ERR_ARG;
+    if (ws->stage < 3) return GEER_ERR_STATE;
+    geer_status st = check_gaussians(ws, g);
+    if (st != GEER_OK) return st;
+    if (g->n != ws->n_gauss || g->sh_degree != ws->sh_degree) return GEER_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_render_bwd(ws, dL_drgb, s);
+    if (e != cudaSuccess) return GEER_ERR_CUDA;
+    return cuda_status(launch_preprocess_bwd(ws, g, d_mean, d_scale, d_quat, d_opacity, d_sh, s));
+}
+
+geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *stream) {
+    if (!ws) return GEER_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t m[kMiscCount];
+    if (cudaMemcpyAsync(m, ws->d_misc, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    if (pairs) *pairs = ((int64_t)m[kMiscPairsHi] << 32) | (int64_t)m[kMiscTotalLo];
+    if (m[kMiscStatus] != 0) {
+        uint32_t zero = 0;
+        if (cudaMemcpyAsync(ws->d_misc + kMiscStatus, &zero, sizeof(zero), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return GEER_ERR_CUDA;
+    }
+    if (m[kMiscStatus] & kStatusCapacity) return GEER_ERR_CAPACITY;
+    if (m[kMiscStatus] & kStatusTimeout) return GEER_ERR_TIMEOUT;
+    return GEER_OK;
+}
+
+geer_status geer_debug_preprocess(geer_workspace *ws, uint16_t *ranges, uint32_t *counts, uint32_t *keys,
+                                  uint8_t *cull, void *stream) {
+    if (!ws) return GEER_ERR_ARG;
+    if (ws->stage < 1) return GEER_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t m = (int64_t)ws->n_cams * ws->n_gauss;
+    if (m == 0) return GEER_OK;
+    std::vector<uint4> r(m);
+    std::vector<uint32_t> cnt(m), k(m);
+    if (cudaMemcpyAsync(r.data(), ws->d_ranges, sizeof(uint4) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(cnt.data(), ws->d_count, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(k.data(), ws->d_key, sizeof(uint32_t) * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    for (int64_t i = 0; i < m; ++i) {
+        const uint32_t w[4] = {r[i].x, r[i].y, r[i].z, r[i].w};
+        if (ranges)
+            for (int j = 0; j < 4; ++j) {
+                ranges[8 * i + 2 * j] = (uint16_t)(w[j] & 0xffff);
+                ranges[8 * i + 2 * j + 1] = (uint16_t)(w[j] >> 16);
+            }
+        if (counts) counts[i] = cnt[i];
+        if (keys) keys[i] = k[i];
+        if (cull) cull[i] = k[i] == 0u ? 1 : 0;  // a live Gaussian has a positive depth key
+    }
+    return GEER_OK;
+}
+
+geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *values, int64_t cap, int64_t *count,
+                             void *stream) {
+    if (!ws || !count || cap < 0) return GEER_ERR_ARG;
+    if (ws->stage < 2) return GEER_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t m[kMiscCount];
+    if (cudaMemcpyAsync(m, ws->d_misc, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    const int64_t P = m[kMiscPairs];
+    *count = P;
+    const int64_t n = std::min(P, cap);
+    if (n > 0) {
+        if (keys && cudaMemcpyAsync(keys, ws->d_keys[ws->sorted_buf], sizeof(uint64_t) * n, cudaMemcpyDeviceToHost,
+                                    s) != cudaSuccess)
+            return GEER_ERR_CUDA;
+        if (values && cudaMemcpyAsync(values, ws->d_vals[ws->sorted_buf], sizeof(uint32_t) * n,
+                                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return GEER_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return GEER_ERR_CUDA;
+    }
+    return GEER_OK;
+}
+
+}  // extern "C"

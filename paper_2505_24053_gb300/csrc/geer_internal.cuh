@@ -1,0 +1,142 @@
+// geer_internal.cuh -- shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/geer.h"
+
+namespace geer {
+
+constexpr int kTile = 16;                   // BEAP tile edge in rays (a camera sub-frustum)
+constexpr int kTilePix = kTile * kTile;
+constexpr int kPrepThreads = 256;           // preprocess / duplicate block size
+constexpr int kSortThreads = 256;           // onesweep block size (8 warps)
+constexpr int kSortItems = 12;              // keys per thread per onesweep tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxPasses = 8;
+constexpr int kMaxCams = 256;
+
+// Device status word bits.
+constexpr uint32_t kStatusCapacity = 1u;
+constexpr uint32_t kStatusTimeout = 2u;
+
+// Indices into the misc u32 array of the workspace.
+enum Misc : int {
+    kMiscStatus = 0,      // device status bits
+    kMiscPairs = 1,       // pair count P (clamped to u32)
+    kMiscPairsHi = 2,     // unclamped P / 2^32
+    kMiscFrame = 3,       // frame counter (look-back epochs)
+    kMiscTotalLo = 4,     // unclamped P mod 2^32
+    kMiscTileCtr = 8,     // onesweep tile counters, one per pass (8 .. 15)
+    kMiscCount = 32
+};
+
+// One camera as the kernels see it. Angles and tables are precomputed on the
+// host in FP64 and rounded to FP32.
+struct DevCam {
+    int32_t width, height, tiles_x, tiles_y;
+    int32_t tile_base;   // global index of tile (0, 0)
+    int32_t any_row_flip, any_col_flip;
+    int32_t tcol_off, trow_off;  // offsets (in float4) of the per-tile tables
+    int32_t pcol_off, prow_off;  // offsets (in float2) of the per-pixel tables
+    int32_t pad_;
+    int64_t pix_base;    // offset of pixel (0, 0) in the batched image (in pixels)
+    float R[9], t[3];    // world -> camera
+    float o[3];          // camera centre in world coordinates
+    float bg[3];
+};
+
+// Per (camera, Gaussian) render record, 64 bytes: the whitening W = S^-1 (R_cw R)^T
+// (camera frame, row-major), o_u = W (0 - mu_c), log2(sigma) and the colour.
+struct __align__(16) Record {
+    float W[9];
+    float ou[3];
+    float log2_sigma;
+    float rgb[3];
+};
+static_assert(sizeof(Record) == 64, "record must be 64 bytes");
+
+// Per (camera, Gaussian) render-stage gradient accumulators (App. C, RenderCUDA
+// part): dL/dsigma-weighted alpha term, dL/drgb, dL/dW|RC = sum dL/dd_u d^T and
+// dL/do_u. 16 floats.
+struct __align__(16) GradAcc {
+    float d_sigma;   // dL/dsigma
+    float d_rgb[3];  // dL/dc
+    float d_W[9];    // dL/dW through d_u (RenderCUDA part)
+    float d_ou[3];   // dL/do_u
+};
+static_assert(sizeof(GradAcc) == 64, "grad accumulator must be 64 bytes");
+
+struct Params {
+    float alpha_min, T_min, alpha_max, lambda_pad;
+};
+
+}  // namespace geer
+
+// Host-side workspace handle.
+struct geer_workspace {
+    // capacities fixed at init
+    int32_t cap_cams;
+    int64_t cap_pixels, cap_tiles, cap_tile_tab, cap_pix_tab;
+    int64_t cap_gauss, cap_pairs;
+    int32_t cap_sh_degree;
+    int64_t cap_sort_tiles;
+    geer::Params params;
+
+    // current camera set
+    int32_t n_cams;
+    int64_t n_pixels, n_tiles;
+    int32_t tile_bits, n_passes;
+    geer::DevCam cams[geer::kMaxCams];
+
+    // device arrays (inside the caller's memory)
+    geer::DevCam *d_cams;
+    float4 *d_tile_tab;
+    float2 *d_pix_tab;
+    geer::Record *d_rec;
+    uint4 *d_ranges;
+    uint32_t *d_count, *d_key;
+    uint32_t *d_blocksum;
+    uint64_t *d_keys[2];
+    uint32_t *d_vals[2];
+    uint32_t *d_hist;       // [kMaxPasses][kRadix]
+    uint64_t *d_lookback;   // [cap_sort_tiles][kRadix]
+    uint32_t *d_misc;       // [kMiscCount]
+    uint2 *d_tile_range;    // [cap_tiles]
+    uint32_t *d_last;       // [cap_pixels] list entries walked per ray
+    float *d_Tfin;          // [cap_pixels] final transmittance (for the backward)
+    geer::GradAcc *d_gacc;  // [cap_cams * cap_gauss]
+
+    // state of the last calls
+    int64_t n_gauss;
+    int32_t sh_degree;
+    int stage;               // 0 none, 1 preprocessed, 2 sorted, 3 rendered
+    int sorted_buf;          // which ping-pong buffer holds the sorted pairs
+    int sort_grid;           // persistent onesweep grid
+    int num_sms;
+
+    // pinned staging for asynchronous camera uploads
+    void *h_stage;
+    size_t stage_bytes;
+};
+
+namespace geer {
+
+// Launchers (defined in the .cu files).
+cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g, cudaStream_t s);
+cudaError_t launch_scan_blocks(const geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_sort(geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_ranges(const geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_final, cudaStream_t s);
+cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cudaStream_t s);
+cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians *g, float *d_mean, float *d_scale,
+                                  float *d_quat, float *d_opacity, float *d_sh, cudaStream_t s);
+int sort_blocks_per_sm();
+
+inline int64_t prep_blocks(int64_t n) { return (n + kPrepThreads - 1) / kPrepThreads; }
+
+}  // namespace geer

@@ -1,0 +1,518 @@
+// preprocess.cu -- per-Gaussian preprocessing (Algorithm 1: CullGaussian,
+// ViewspaceGaussians, PBF_Intersect, PCA_Whitening), the pair-count scan and
+// DuplicateWithKeys.
+//
+// The PBF part runs in exactly rounded FP32 operations in a fixed order
+// (__fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn / __fsqrt_rn, which the
+// compiler never contracts), so the tile ranges and depth keys are bit-for-bit
+// reproducible by an independent FP32 implementation of the same sequence.
+#include "geer_internal.cuh"
+
+namespace geer {
+namespace {
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
+
+// An arc of dihedral angle in half-angle-tangent space tau = tan(angle / 2)
+// (the mirror transform with xi = 1, App. D.2). kind 0 empty, 1 [lo, hi],
+// 2 wrapping [lo, +inf) u (-inf, hi], 3 full circle.
+struct Arc {
+    int kind;
+    float lo, hi;
+};
+
+// tan(angle/2) of the planar direction (x, z), angle measured from +z towards +x.
+__device__ float half_tan(float x, float z) {
+    float r = fsq(fa(fm(x, x), fm(z, z)));
+    return (z >= 0.0f) ? fdv(x, fa(r, z)) : fdv(fs(r, z), x);
+}
+
+// PBF bounds about one camera axis (Sec. 3.2, App. D.1): the bounding planes
+// through the axis have tangent c solving T22 c^2 - 2 T02 c + T00 = 0 with
+// T = lambda^2 Sigma_c - mu_c mu_c^T. The discriminant T02^2 - T00 T22 equals
+// lambda^2 (P - lambda^2 D) with P = mu^T adj(Sigma_pp) mu and D = det(Sigma_pp),
+// evaluated without cancellation. No real root: the axis pierces the ellipsoid
+// and the arc is the full circle (clamp to the full FoV, App. D.1). The four
+// mirrored candidates are reduced to the two nearest the centre's mirrored
+// angle (App. D.2) and widened by a 2^-18 (1 + tau^2) margin.
+__device__ Arc pbf_arc(float mx, float mz, float T00, float T02, float T22, float P, float D, float lam2) {
+    Arc a{3, 0.0f, 0.0f};
+    float disc = fm(lam2, fs(P, fm(lam2, D)));
+    if (!(disc > 0.0f)) return a;
+    float sq = fsq(disc);
+    float qq = fa(T02, (T02 >= 0.0f) ? sq : -sq);
+    if (qq == 0.0f) return a;
+    float cand[4];
+    cand[0] = half_tan(qq, T22);
+    cand[1] = half_tan(-qq, -T22);
+    cand[2] = half_tan(T00, qq);
+    cand[3] = half_tan(-T00, -qq);
+    float tm = half_tan(mx, mz);
+    if (!isfinite(tm)) return a;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (!isfinite(cand[i])) return a;
+    bool have_lo = false, have_hi = false;
+    float lo = 0.0f, hi = 0.0f, mn = cand[0], mxv = cand[0];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float v = cand[i];
+        if (v < mn) mn = v;
+        if (v > mxv) mxv = v;
+        if (v < tm && (!have_lo || v > lo)) { lo = v; have_lo = true; }
+        if (v > tm && (!have_hi || v < hi)) { hi = v; have_hi = true; }
+    }
+    a.kind = 1;
+    if (!have_hi) { hi = mn; a.kind = 2; }
+    if (!have_lo) { lo = mxv; a.kind = 2; }
+    const float margin = 3.814697265625e-06f;  // 2^-18
+    a.lo = fs(lo, fm(margin, fa(1.0f, fm(lo, lo))));
+    a.hi = fa(hi, fm(margin, fa(1.0f, fm(hi, hi))));
+    return a;
+}
+
+// The arc rotated by pi (tau -> -1/tau), for rays whose other BEAP angle is
+// beyond 90 degrees.
+__device__ Arc shift_arc(Arc a) {
+    Arc r = a;
+    if (a.kind == 0 || a.kind == 3) return r;
+    if (a.lo == 0.0f || a.hi == 0.0f) { r.kind = 3; return r; }
+    r.lo = fdv(-1.0f, a.lo);
+    r.hi = fdv(-1.0f, a.hi);
+    if (a.kind == 2) r.kind = 1;
+    else r.kind = (a.lo < 0.0f && a.hi > 0.0f) ? 2 : 1;
+    return r;
+}
+
+// Tile range [lo, hi) whose half-angle span [ta, tb] (tab[i].x, tab[i].y, both
+// increasing in i) meets the arc; prefix u suffix becomes the whole range.
+__device__ void arc_range(Arc a, const float4 *tab, int n, int &olo, int &ohi) {
+    olo = 0;
+    ohi = 0;
+    if (a.kind == 0) return;
+    if (a.kind == 3) { ohi = n; return; }
+    int l = 0, h = n;  // first index with tb >= a.lo
+    while (l < h) {
+        int m = (l + h) >> 1;
+        if (tab[m].y >= a.lo) h = m; else l = m + 1;
+    }
+    int first = l;
+    l = 0; h = n;      // first index with ta > a.hi
+    while (l < h) {
+        int m = (l + h) >> 1;
+        if (tab[m].x > a.hi) h = m; else l = m + 1;
+    }
+    int last = l - 1;
+    if (a.kind == 1) {
+        if (first <= last) { olo = first; ohi = last + 1; }
+        return;
+    }
+    bool suf = first < n, pre = last >= 0;
+    if (suf && pre) { olo = 0; ohi = n; }
+    else if (suf) { olo = first; ohi = n; }
+    else if (pre) { olo = 0; ohi = last + 1; }
+}
+
+// lambda^2 >= 2 ln(sigma / alpha_min) with basic operations only, times (1 + pad):
+// ln m <= 2 (z + z^3 / (3 (1 - z^2))), z = (m - 1)/(m + 1), m in [1, 2).
+__device__ float lambda2(float sigma, float alpha_min, float pad) {
+    float x = fdv(sigma, alpha_min);
+    int e;
+    float m = frexpf(x, &e);
+    m = fm(m, 2.0f);
+    e = e - 1;
+    float z = fdv(fs(m, 1.0f), fa(m, 1.0f));
+    float z2 = fm(z, z);
+    float t = fdv(fm(z, z2), fm(3.0f, fs(1.0f, z2)));
+    float lnm = fm(2.0f, fa(z, t));
+    float lnx = fa(fm((float)e, 0.693147182464599609375f), lnm);
+    return fm(fm(2.0f, lnx), fa(1.0f, pad));
+}
+
+__device__ __forceinline__ bool tile_assoc(const float4 &col, const float4 &row, int cx, int cy, const int rg[8]) {
+    bool aok = (row.z != 0.0f && cx >= rg[0] && cx < rg[1]) || (row.w != 0.0f && cx >= rg[2] && cx < rg[3]);
+    bool bok = (col.z != 0.0f && cy >= rg[4] && cy < rg[5]) || (col.w != 0.0f && cy >= rg[6] && cy < rg[7]);
+    return aok && bok;
+}
+
+// Bounding box of the association predicate in tile coordinates.
+__device__ __forceinline__ void assoc_bbox(const int rg[8], int ncols, int nrows, int &xa, int &xb, int &ya,
+                                           int &yb) {
+    xa = rg[0] < rg[1] ? rg[0] : ncols;
+    xb = rg[0] < rg[1] ? rg[1] : 0;
+    if (rg[2] < rg[3]) { xa = min(xa, rg[2]); xb = max(xb, rg[3]); }
+    ya = rg[4] < rg[5] ? rg[4] : nrows;
+    yb = rg[4] < rg[5] ? rg[5] : 0;
+    if (rg[6] < rg[7]) { ya = min(ya, rg[6]); yb = max(yb, rg[7]); }
+}
+
+// Real SH of degree <= 3 in the 3DGS convention (Condon-Shortley phase, index
+// l^2 + l + m), written out as polynomials of the unit direction. The constants
+// are K_lm sqrt(2)^(m != 0) = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (* sqrt 2).
+__device__ __forceinline__ void sh_colour(int deg, const float *c, float x, float y, float z, float rgb[3]) {
+    float Y[16];
+    Y[0] = 0.28209479177387814f;  // 1/(2 sqrt(pi))
+    int nb = 1;
+    if (deg >= 1) {
+        const float k1 = 0.4886025119029199f;  // sqrt(3/(4 pi))
+        Y[1] = -k1 * y; Y[2] = k1 * z; Y[3] = -k1 * x;
+        nb = 4;
+    }
+    if (deg >= 2) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;               // sqrt(15/pi)/2
+        Y[5] = -1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);  // sqrt(5/pi)/4
+        Y[7] = -1.0925484305920792f * x * z;
+        Y[8] = 0.5462742152960396f * (xx - yy);           // sqrt(15/pi)/4
+        nb = 9;
+        if (deg >= 3) {
+            Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);        // sqrt(35/(2 pi))/4
+            Y[10] = 2.890611442640554f * x * y * z;                    // sqrt(105/pi)/2
+            Y[11] = -0.4570457994644658f * y * (4.0f * zz - xx - yy);  // sqrt(21/(2 pi))/4
+            Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);  // sqrt(7/pi)/4
+            Y[13] = -0.4570457994644658f * x * (4.0f * zz - xx - yy);
+            Y[14] = 1.445305721320277f * z * (xx - yy);                // sqrt(105/pi)/4
+            Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
+            nb = 16;
+        }
+    }
+    float r = 0.5f, g = 0.5f, b = 0.5f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k < nb) {
+            r += Y[k] * c[3 * k];
+            g += Y[k] * c[3 * k + 1];
+            b += Y[k] * c[3 * k + 2];
+        }
+    }
+    rgb[0] = fmaxf(r, 0.0f);
+    rgb[1] = fmaxf(g, 0.0f);
+    rgb[2] = fmaxf(b, 0.0f);
+}
+
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;  // valid in warp 0
+}
+
+// Thread per Gaussian, loop over cameras (the Gaussian's parameters are read once).
+__global__ void __launch_bounds__(kPrepThreads) k_preprocess(
+    const DevCam *__restrict__ cams, int ncams, const float4 *__restrict__ ttab, Params p,
+    const float *__restrict__ mean, const float *__restrict__ scale, const float *__restrict__ quat,
+    const float *__restrict__ opacity, const float *__restrict__ sh, int64_t n, int deg, Record *__restrict__ rec,
+    uint4 *__restrict__ ranges, uint32_t *__restrict__ count, uint32_t *__restrict__ key,
+    uint32_t *__restrict__ blocksum, int64_t nblk) {
+    __shared__ uint32_t red[kPrepThreads / 32];
+    const int64_t g = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    bool ok = g < n;
+    float mu[3] = {0, 0, 0}, sc[3] = {1, 1, 1}, qt[4] = {1, 0, 0, 0}, sigma = 0.0f;
+    if (ok) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { mu[a] = mean[3 * g + a]; sc[a] = scale[3 * g + a]; }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) qt[a] = quat[4 * g + a];
+        sigma = opacity[g];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (!isfinite(mu[a]) || !isfinite(sc[a]) || !(sc[a] > 0.0f)) ok = false;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            if (!isfinite(qt[a])) ok = false;
+        if (!isfinite(sigma) || !(sigma >= p.alpha_min)) ok = false;
+    }
+    // normalised quaternion and rotation, exactly rounded
+    float R[9];
+    float lam2 = 0.0f;
+    if (ok) {
+        float qn = fsq(fa(fa(fa(fm(qt[0], qt[0]), fm(qt[1], qt[1])), fm(qt[2], qt[2])), fm(qt[3], qt[3])));
+        if (!(qn > 0.0f)) ok = false;
+        float w = fdv(qt[0], qn), x = fdv(qt[1], qn), y = fdv(qt[2], qn), z = fdv(qt[3], qn);
+        R[0] = fs(1.0f, fm(2.0f, fa(fm(y, y), fm(z, z))));
+        R[1] = fm(2.0f, fs(fm(x, y), fm(w, z)));
+        R[2] = fm(2.0f, fa(fm(x, z), fm(w, y)));
+        R[3] = fm(2.0f, fa(fm(x, y), fm(w, z)));
+        R[4] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(z, z))));
+        R[5] = fm(2.0f, fs(fm(y, z), fm(w, x)));
+        R[6] = fm(2.0f, fs(fm(x, z), fm(w, y)));
+        R[7] = fm(2.0f, fa(fm(y, z), fm(w, x)));
+        R[8] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(y, y))));
+        lam2 = lambda2(sigma, p.alpha_min, p.lambda_pad);
+        if (!(lam2 > 0.0f)) ok = false;
+    }
+    // SH coefficients [(deg+1)^2][3]; rows of 12 or 48 floats are read as float4
+    float shc[48];
+    const int nc = 3 * (deg + 1) * (deg + 1);
+    if (ok) {
+        if ((nc & 3) == 0) {
+            const float4 *p4 = reinterpret_cast<const float4 *>(sh + (int64_t)g * nc);
+#pragma unroll
+            for (int i = 0; i < 12; ++i)
+                if (4 * i < nc) {
+                    const float4 v = p4[i];
+                    shc[4 * i] = v.x; shc[4 * i + 1] = v.y; shc[4 * i + 2] = v.z; shc[4 * i + 3] = v.w;
+                }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 48; ++i)
+                if (i < nc) shc[i] = sh[(int64_t)g * nc + i];
+        }
+    }
+    const float s2[3] = {fm(sc[0], sc[0]), fm(sc[1], sc[1]), fm(sc[2], sc[2])};
+    const float ss[3] = {fm(sc[1], sc[2]), fm(sc[0], sc[2]), fm(sc[0], sc[1])};
+
+    for (int ci = 0; ci < ncams; ++ci) {
+        const DevCam &cam = cams[ci];
+        const int64_t idx = (int64_t)ci * n + g;
+        uint32_t cnt = 0;
+        bool live = ok;
+        float m0 = 0, m1 = 0, m2 = 0, M[9], u[3];
+        if (live) {
+            const float *Rc = cam.R;
+            m0 = fa(fa(fa(fm(Rc[0], mu[0]), fm(Rc[1], mu[1])), fm(Rc[2], mu[2])), cam.t[0]);
+            m1 = fa(fa(fa(fm(Rc[3], mu[0]), fm(Rc[4], mu[1])), fm(Rc[5], mu[2])), cam.t[1]);
+            m2 = fa(fa(fa(fm(Rc[6], mu[0]), fm(Rc[7], mu[1])), fm(Rc[8], mu[2])), cam.t[2]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    M[3 * i + j] = fa(fa(fm(Rc[3 * i], R[j]), fm(Rc[3 * i + 1], R[3 + j])), fm(Rc[3 * i + 2], R[6 + j]));
+            // camera inside the lambda-ellipsoid: cull (App. B.2: t < 0 matters only
+            // when the optical centre is inside the contour)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                u[k] = fdv(fa(fa(fm(M[k], m0), fm(M[3 + k], m1)), fm(M[6 + k], m2)), sc[k]);
+            float ou2 = fa(fa(fm(u[0], u[0]), fm(u[1], u[1])), fm(u[2], u[2]));
+            if (!(ou2 > lam2)) live = false;
+        }
+        if (live) {
+            auto SIG = [&](int a, int b) {
+                return fa(fa(fm(s2[0], fm(M[3 * a], M[3 * b])), fm(s2[1], fm(M[3 * a + 1], M[3 * b + 1]))),
+                          fm(s2[2], fm(M[3 * a + 2], M[3 * b + 2])));
+            };
+            float Sxx = SIG(0, 0), Syy = SIG(1, 1), Szz = SIG(2, 2), Sxz = SIG(0, 2), Syz = SIG(1, 2);
+            float T00 = fs(fm(lam2, Sxx), fm(m0, m0));
+            float T11 = fs(fm(lam2, Syy), fm(m1, m1));
+            float T22 = fs(fm(lam2, Szz), fm(m2, m2));
+            float T02 = fs(fm(lam2, Sxz), fm(m0, m2));
+            float T12 = fs(fm(lam2, Syz), fm(m1, m2));
+            float pxz[3], pyz[3], dxz[3], dyz[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float cx = fs(fm(m0, M[6 + k]), fm(m2, M[k]));
+                float cy = fs(fm(m1, M[6 + k]), fm(m2, M[3 + k]));
+                pxz[k] = fm(s2[k], fm(cx, cx));
+                pyz[k] = fm(s2[k], fm(cy, cy));
+                float ax = fm(ss[k], M[3 + k]);
+                float ay = fm(ss[k], M[k]);
+                dxz[k] = fm(ax, ax);
+                dyz[k] = fm(ay, ay);
+            }
+            float Pxz = fa(fa(pxz[0], pxz[1]), pxz[2]), Pyz = fa(fa(pyz[0], pyz[1]), pyz[2]);
+            float Dxz = fa(fa(dxz[0], dxz[1]), dxz[2]), Dyz = fa(fa(dyz[0], dyz[1]), dyz[2]);
+            Arc A = pbf_arc(m0, m2, T00, T02, T22, Pxz, Dxz, lam2);
+            Arc B = pbf_arc(m1, m2, T11, T12, T22, Pyz, Dyz, lam2);
+            const float4 *ctab = ttab + cam.tcol_off;
+            const float4 *rtab = ttab + cam.trow_off;
+            int rg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            arc_range(A, ctab, cam.tiles_x, rg[0], rg[1]);
+            arc_range(B, rtab, cam.tiles_y, rg[4], rg[5]);
+            if (cam.any_row_flip) arc_range(shift_arc(A), ctab, cam.tiles_x, rg[2], rg[3]);
+            if (cam.any_col_flip) arc_range(shift_arc(B), rtab, cam.tiles_y, rg[6], rg[7]);
+            if (!cam.any_row_flip && !cam.any_col_flip) {
+                cnt = (uint32_t)(rg[1] - rg[0]) * (uint32_t)(rg[5] - rg[4]);
+            } else {
+                int xa, xb, ya, yb;
+                assoc_bbox(rg, cam.tiles_x, cam.tiles_y, xa, xb, ya, yb);
+                for (int cy = ya; cy < yb; ++cy) {
+                    const float4 row = rtab[cy];
+                    for (int cx = xa; cx < xb; ++cx) cnt += tile_assoc(ctab[cx], row, cx, cy, rg) ? 1u : 0u;
+                }
+            }
+            float dist = fsq(fa(fa(fm(m0, m0), fm(m1, m1)), fm(m2, m2)));
+            key[idx] = __float_as_uint(dist);
+            ranges[idx] = make_uint4((uint32_t)rg[0] | ((uint32_t)rg[1] << 16), (uint32_t)rg[2] | ((uint32_t)rg[3] << 16),
+                                     (uint32_t)rg[4] | ((uint32_t)rg[5] << 16), (uint32_t)rg[6] | ((uint32_t)rg[7] << 16));
+            // render record: W = S^-1 M^T (camera frame), o_u = -W mu_c = -u
+            Record r;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float inv = 1.0f / sc[k];
+                r.W[3 * k + 0] = M[k] * inv;
+                r.W[3 * k + 1] = M[3 + k] * inv;
+                r.W[3 * k + 2] = M[6 + k] * inv;
+                r.ou[k] = -u[k];
+            }
+            r.log2_sigma = log2f(sigma);
+            float dx = mu[0] - cam.o[0], dy = mu[1] - cam.o[1], dz = mu[2] - cam.o[2];
+            float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+            sh_colour(deg, shc, dx * inv, dy * inv, dz * inv, r.rgb);
+            float4 *dst = reinterpret_cast<float4 *>(rec + idx);
+            const float4 *src = reinterpret_cast<const float4 *>(&r);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = src[i];
+        } else if (g < n) {
+            key[idx] = 0u;
+            ranges[idx] = make_uint4(0, 0, 0, 0);
+        }
+        if (g < n) count[idx] = cnt;
+        uint32_t tot = block_sum_u32(cnt, red);
+        if (threadIdx.x == 0) blocksum[(int64_t)ci * nblk + blockIdx.x] = tot;
+    }
+}
+
+// Exclusive scan of the per-block pair counts (one block; each thread scans a
+// contiguous chunk serially). Also: pair total and capacity check, zeroing of
+// the sort histograms, tile counters and tile ranges, and the frame counter.
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ blocksum, int64_t m,
+                                                      uint32_t *__restrict__ misc, uint32_t *__restrict__ hist,
+                                                      uint2 *__restrict__ tile_range, int64_t ntiles, int64_t cap) {
+    __shared__ unsigned long long warp_tot[32];
+    const int t = threadIdx.x;
+    const int64_t chunk = (m + 1023) / 1024;
+    const int64_t b = t * chunk, e = min(m, b + chunk);
+    unsigned long long s = 0;
+    for (int64_t i = b; i < e; ++i) s += blocksum[i];
+    // block exclusive scan of s
+    unsigned long long v = s;
+    const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_tot[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long excl = v - s + (warp > 0 ? warp_tot[warp - 1] : 0ull);
+    for (int64_t i = b; i < e; ++i) {
+        uint32_t c = blocksum[i];
+        blocksum[i] = (uint32_t)min(excl, 0xffffffffull);
+        excl += c;
+    }
+    if (t == 1023) {
+        unsigned long long total = excl;  // last thread's running sum = grand total
+        misc[kMiscPairs] = (uint32_t)min(total, (unsigned long long)cap);
+        misc[kMiscPairsHi] = (uint32_t)(total >> 32);
+        misc[kMiscTotalLo] = (uint32_t)total;
+        if (total > (unsigned long long)cap) atomicOr(&misc[kMiscStatus], kStatusCapacity);
+        misc[kMiscFrame] += 1u;
+    }
+    for (int i = t; i < kMaxPasses * kRadix; i += 1024) hist[i] = 0u;
+    if (t < kMaxPasses) misc[kMiscTileCtr + t] = 0u;
+    for (int64_t i = t; i < ntiles; i += 1024) tile_range[i] = make_uint2(0u, 0u);
+}
+
+// DuplicateWithKeys: one (global tile << 32 | depth bits, camera * n + g) pair per
+// associated tile, in row-major tile order per Gaussian, Gaussians in index order.
+__global__ void __launch_bounds__(kPrepThreads) k_duplicate(
+    const DevCam *__restrict__ cams, int ncams, const float4 *__restrict__ ttab, int64_t n,
+    const uint4 *__restrict__ ranges, const uint32_t *__restrict__ count, const uint32_t *__restrict__ key,
+    const uint32_t *__restrict__ blocksum, int64_t nblk, uint64_t *__restrict__ okeys, uint32_t *__restrict__ ovals,
+    int64_t cap) {
+    __shared__ uint32_t wsum[kPrepThreads / 32];
+    const int64_t g = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int ci = 0; ci < ncams; ++ci) {
+        const DevCam &cam = cams[ci];
+        const int64_t idx = (int64_t)ci * n + g;
+        uint32_t cnt = g < n ? count[idx] : 0u;
+        // block exclusive scan of cnt
+        uint32_t v = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) wsum[warp] = v;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += wsum[w];
+        __syncthreads();
+        int64_t off = (int64_t)blocksum[(int64_t)ci * nblk + blockIdx.x] + wpre + (v - cnt);
+        if (cnt == 0 || off + cnt > cap) continue;
+        const uint4 r4 = ranges[idx];
+        int rg[8] = {(int)(r4.x & 0xffff), (int)(r4.x >> 16), (int)(r4.y & 0xffff), (int)(r4.y >> 16),
+                     (int)(r4.z & 0xffff), (int)(r4.z >> 16), (int)(r4.w & 0xffff), (int)(r4.w >> 16)};
+        const int64_t end = off + cnt;  // this Gaussian's slots
+        const uint64_t depth = key[idx];
+        const uint32_t val = (uint32_t)idx;
+        const float4 *ctab = ttab + cam.tcol_off;
+        const float4 *rtab = ttab + cam.trow_off;
+        if (!cam.any_row_flip && !cam.any_col_flip) {
+            for (int cy = rg[4]; cy < rg[5]; ++cy)
+                for (int cx = rg[0]; cx < rg[1] && off < end; ++cx) {
+                    okeys[off] = ((uint64_t)(cam.tile_base + cy * cam.tiles_x + cx) << 32) | depth;
+                    ovals[off] = val;
+                    ++off;
+                }
+        } else {
+            int xa, xb, ya, yb;
+            assoc_bbox(rg, cam.tiles_x, cam.tiles_y, xa, xb, ya, yb);
+            for (int cy = ya; cy < yb; ++cy) {
+                const float4 row = rtab[cy];
+                for (int cx = xa; cx < xb && off < end; ++cx)
+                    if (tile_assoc(ctab[cx], row, cx, cy, rg)) {
+                        okeys[off] = ((uint64_t)(cam.tile_base + cy * cam.tiles_x + cx) << 32) | depth;
+                        ovals[off] = val;
+                        ++off;
+                    }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g, cudaStream_t s) {
+    const int64_t nblk = prep_blocks(g->n);
+    if (nblk == 0) return cudaSuccess;
+    k_preprocess<<<(unsigned)nblk, kPrepThreads, 0, s>>>(
+        ws->d_cams, ws->n_cams, ws->d_tile_tab,
+        Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, g->mean,
+        g->scale, g->quat, g->opacity, g->sh, g->n, g->sh_degree, ws->d_rec,
+        ws->d_ranges, ws->d_count, ws->d_key, ws->d_blocksum, nblk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_blocks(const geer_workspace *ws, cudaStream_t s) {
+    const int64_t m = prep_blocks(ws->n_gauss) * ws->n_cams;
+    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum, m, ws->d_misc, ws->d_hist, ws->d_tile_range, ws->n_tiles,
+                                     ws->cap_pairs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
+    const int64_t nblk = prep_blocks(ws->n_gauss);
+    if (nblk == 0) return cudaSuccess;
+    k_duplicate<<<(unsigned)nblk, kPrepThreads, 0, s>>>(ws->d_cams, ws->n_cams, ws->d_tile_tab, ws->n_gauss,
+                                                        ws->d_ranges, ws->d_count, ws->d_key, ws->d_blocksum, nblk,
+                                                        ws->d_keys[0], ws->d_vals[0], ws->cap_pairs);
+    return cudaGetLastError();
+}
+
+}  // namespace geer

@@ -1,0 +1,306 @@
+"""Python binding of the C ABI in include/geer.h (argument marshalling only).
+
+Every step of the render runs in libgeer.so's CUDA kernels; torch supplies device
+memory and the current stream. There is no CPU fallback: if the library is
+missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_STATE = range(7)
+PINHOLE, EQUIDISTANT, KANNALA_BRANDT = 0, 1, 2
+
+
+class GeerError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class CameraC(C.Structure):
+    _fields_ = [("model", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+                ("fov_x", C.c_float), ("fov_y", C.c_float), ("k", C.c_float * 4),
+                ("R_cw", C.c_float * 9), ("t_cw", C.c_float * 3), ("bg", C.c_float * 3)]
+
+
+class GaussiansC(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("opacity", C.c_void_p),
+                ("sh", C.c_void_p), ("n", C.c_int64), ("sh_degree", C.c_int32), ("reserved_", C.c_int32)]
+
+
+class ParamsC(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("alpha_min", C.c_float), ("T_min", C.c_float),
+                ("alpha_max", C.c_float), ("lambda_pad", C.c_float)]
+
+
+EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "geer_workspace_init",
+           "geer_workspace_destroy", "geer_set_cameras", "geer_preprocess", "geer_bin_sort", "geer_render_fwd",
+           "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libgeer.so (building it in-tree first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libgeer.so not built ({path}); run paper_2505_24053_gb300/build.py")
+        _build.build()
+    L = C.CDLL(path)
+    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+    L.geer_status_string.restype = C.c_char_p
+    L.geer_status_string.argtypes = [C.c_int]
+    sigs = {
+        "geer_default_params": [P],
+        "geer_workspace_size": [P, I32, I64, I32, I64, P],
+        "geer_workspace_init": [P, C.c_size_t, P, I32, I64, I32, I64, P, P],
+        "geer_workspace_destroy": [P],
+        "geer_set_cameras": [P, P, I32, P],
+        "geer_preprocess": [P, P, P],
+        "geer_bin_sort": [P, P, P],
+        "geer_render_fwd": [P, P, P, P],
+        "geer_render_bwd": [P, P, P, P, P, P, P, P, P],
+        "geer_last_device_status": [P, P, P],
+        "geer_debug_preprocess": [P, P, P, P, P, P],
+        "geer_debug_pairs": [P, P, P, I64, P, P],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.restype = C.c_int
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return lib().geer_status_string(int(s)).decode()
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise GeerError(status, what)
+
+
+def camera_c(cam) -> CameraC:
+    """Convert a workloads.Camera (or any object with the same fields)."""
+    c = CameraC()
+    c.model, c.width, c.height = int(cam.model), int(cam.width), int(cam.height)
+    c.fov_x, c.fov_y = float(cam.fov_x), float(getattr(cam, "fov_y", 0.0) or 0.0)
+    k = getattr(cam, "k", (0, 0, 0, 0))
+    for i in range(4):
+        c.k[i] = float(k[i])
+    R = np.asarray(getattr(cam, "R_cw", np.eye(3)), np.float32).ravel()
+    t = np.asarray(getattr(cam, "t_cw", np.zeros(3)), np.float32).ravel()
+    bg = getattr(cam, "bg", (1.0, 1.0, 1.0))
+    for i in range(9):
+        c.R_cw[i] = float(R[i])
+    for i in range(3):
+        c.t_cw[i] = float(t[i])
+        c.bg[i] = float(bg[i])
+    return c
+
+
+def cameras_c(cams):
+    arr = (CameraC * len(cams))()
+    for i, cam in enumerate(cams):
+        arr[i] = camera_c(cam)
+    return arr
+
+
+def params_c(alpha_min=1 / 255, T_min=1e-4, alpha_max=0.99, lambda_pad=1e-3) -> ParamsC:
+    p = ParamsC()
+    p.tile_w = p.tile_h = 16
+    p.alpha_min, p.T_min, p.alpha_max, p.lambda_pad = alpha_min, T_min, alpha_max, lambda_pad
+    return p
+
+
+class Gaussians:
+    """Device-resident Gaussians (contiguous FP32 CUDA tensors)."""
+
+    def __init__(self, mean, scale, quat, opacity, sh, sh_degree: int):
+        def dev(x):
+            t = torch.as_tensor(x, dtype=torch.float32)
+            if t.device.type != "cuda":
+                t = t.cuda()
+            return t.contiguous()
+
+        self.mean, self.scale, self.quat, self.opacity, self.sh = (dev(x) for x in (mean, scale, quat, opacity, sh))
+        self.sh_degree = int(sh_degree)
+        self.n = int(self.mean.shape[0])
+
+    @classmethod
+    def from_scene(cls, scene):
+        return cls(scene.mean, scene.scale, scene.quat, scene.opacity, scene.sh, scene.sh_degree)
+
+    def c_struct(self) -> GaussiansC:
+        g = GaussiansC()
+        g.mean, g.scale, g.quat = self.mean.data_ptr(), self.scale.data_ptr(), self.quat.data_ptr()
+        g.opacity, g.sh = self.opacity.data_ptr(), self.sh.data_ptr()
+        g.n, g.sh_degree = self.n, self.sh_degree
+        return g
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Workspace:
+    """A geer workspace in a torch-owned device buffer."""
+
+    def __init__(self, cams, n_gauss: int, sh_degree: int, pair_capacity: int, params: ParamsC | None = None,
+                 device=None):
+        L = lib()
+        self.cams = list(cams)
+        self._cams_c = cameras_c(self.cams)
+        self.n_gauss, self.sh_degree, self.pair_capacity = int(n_gauss), int(sh_degree), int(pair_capacity)
+        self.params = params or params_c()
+        nbytes = C.c_size_t()
+        _check(L.geer_workspace_size(self._cams_c, len(self.cams), self.n_gauss, self.sh_degree, self.pair_capacity,
+                                     C.byref(nbytes)), "geer_workspace_size")
+        self.nbytes = int(nbytes.value)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+        base = self.buf.data_ptr()
+        aligned = (base + 255) & ~255
+        self._handle = C.c_void_p()
+        torch.cuda.current_stream().synchronize()
+        _check(L.geer_workspace_init(C.c_void_p(aligned), self.nbytes, self._cams_c, len(self.cams), self.n_gauss,
+                                     self.sh_degree, self.pair_capacity, C.byref(self.params),
+                                     C.byref(self._handle)), "geer_workspace_init")
+        self.pixels = sum(c.width * c.height for c in self.cams)
+
+    def __del__(self):
+        h = getattr(self, "_handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.geer_workspace_destroy(h)
+            self._handle = None
+
+    @property
+    def handle(self):
+        return self._handle
+
+    def set_cameras(self, cams, stream=None):
+        self.cams = list(cams)
+        self._cams_c = cameras_c(self.cams)
+        _check(lib().geer_set_cameras(self._handle, self._cams_c, len(self.cams), _stream(stream)),
+               "geer_set_cameras")
+        self.pixels = sum(c.width * c.height for c in self.cams)
+
+    def preprocess(self, g: Gaussians, stream=None):
+        self._g = g
+        self._gc = g.c_struct()
+        _check(lib().geer_preprocess(self._handle, C.byref(self._gc), _stream(stream)), "geer_preprocess")
+
+    def bin_sort(self, sync: bool = True, stream=None) -> int | None:
+        """Duplicate, sort and range. With sync=True returns the pair count and
+        raises GeerError(ERR_CAPACITY) if it exceeds the capacity."""
+        if sync:
+            need = C.c_int64()
+            st = lib().geer_bin_sort(self._handle, C.byref(need), _stream(stream))
+            self.last_pairs = int(need.value)
+            _check(st, "geer_bin_sort")
+            return self.last_pairs
+        _check(lib().geer_bin_sort(self._handle, None, _stream(stream)), "geer_bin_sort")
+        return None
+
+    def render_fwd(self, rgb: torch.Tensor, T: torch.Tensor | None = None, stream=None):
+        _check(lib().geer_render_fwd(self._handle, C.c_void_p(rgb.data_ptr()),
+                                     C.c_void_p(T.data_ptr()) if T is not None else None, _stream(stream)),
+               "geer_render_fwd")
+
+    def render_bwd(self, g: Gaussians, dL_drgb: torch.Tensor, grads: dict, stream=None):
+        gc = g.c_struct()
+
+        def ptr(name):
+            t = grads.get(name)
+            return C.c_void_p(t.data_ptr()) if t is not None else None
+
+        _check(lib().geer_render_bwd(self._handle, C.byref(gc), C.c_void_p(dL_drgb.data_ptr()), ptr("mean"),
+                                     ptr("scale"), ptr("quat"), ptr("opacity"), ptr("sh"), _stream(stream)),
+               "geer_render_bwd")
+
+    def device_status(self, stream=None):
+        pairs = C.c_int64()
+        st = lib().geer_last_device_status(self._handle, C.byref(pairs), _stream(stream))
+        return st, int(pairs.value)
+
+    def debug_preprocess(self, stream=None):
+        m = len(self.cams) * self._g.n
+        ranges = np.zeros((m, 8), np.uint16)
+        counts = np.zeros(m, np.uint32)
+        keys = np.zeros(m, np.uint32)
+        cull = np.zeros(m, np.uint8)
+        P = C.c_void_p
+        _check(lib().geer_debug_preprocess(self._handle, P(ranges.ctypes.data), P(counts.ctypes.data),
+                                           P(keys.ctypes.data), P(cull.ctypes.data), _stream(stream)),
+               "geer_debug_preprocess")
+        return cull, keys, ranges, counts
+
+    def debug_pairs(self, cap: int | None = None, stream=None):
+        cap = self.pair_capacity if cap is None else cap
+        keys = np.zeros(cap, np.uint64)
+        vals = np.zeros(cap, np.uint32)
+        count = C.c_int64()
+        _check(lib().geer_debug_pairs(self._handle, C.c_void_p(keys.ctypes.data), C.c_void_p(vals.ctypes.data), cap,
+                                      C.byref(count), _stream(stream)), "geer_debug_pairs")
+        n = min(int(count.value), cap)
+        return keys[:n], vals[:n]
+
+
+class Renderer:
+    """Forward renders of a camera batch, growing the pair capacity on demand."""
+
+    def __init__(self, cams, n_gauss: int, sh_degree: int, pair_capacity: int | None = None,
+                 params: ParamsC | None = None):
+        self.cams = list(cams)
+        pixels = sum(c.width * c.height for c in self.cams)
+        cap = pair_capacity if pair_capacity is not None else max(1 << 16, 4 * n_gauss + pixels // 16)
+        self.ws = Workspace(self.cams, n_gauss, sh_degree, cap, params)
+        self.n_gauss, self.sh_degree, self.params = n_gauss, sh_degree, params
+        self.pixels = pixels
+
+    def _grow(self, need: int):
+        cap = int(need * 1.25) + 1024
+        self.ws = Workspace(self.cams, self.n_gauss, self.sh_degree, cap, self.params)
+
+    def prepare(self, g: Gaussians) -> int:
+        """Preprocess + bin/sort (synchronous pair-count check). Returns P."""
+        while True:
+            self.ws.preprocess(g)
+            try:
+                return self.ws.bin_sort(sync=True)
+            except GeerError as e:
+                if e.status != ERR_CAPACITY:
+                    raise
+                self._grow(self.ws.last_pairs)
+
+    def forward(self, g: Gaussians, rgb: torch.Tensor | None = None, T: torch.Tensor | None = None):
+        self.prepare(g)
+        if rgb is None:
+            rgb = torch.empty((self.pixels, 3), dtype=torch.float32, device="cuda")
+        self.ws.render_fwd(rgb, T)
+        return rgb
+
+    def images(self, rgb: torch.Tensor):
+        out, off = [], 0
+        for c in self.cams:
+            n = c.width * c.height
+            out.append(rgb[off:off + n].view(c.height, c.width, 3))
+            off += n
+        return out

@@ -1,0 +1,238 @@
+"""GPU parity of the forward path against the CPU oracle, through the C ABI.
+
+- Preprocess: cull flags, depth keys, PBF tile ranges and tile counts are
+  bit-exact against the oracle's FP32 replica.
+- Bin/sort: the sorted (key, value) pairs equal a stable CPU sort of the pairs
+  expanded from the replica's ranges.
+- Render: every compared pixel is within 2e-4 per channel of one of the
+  oracle's admissible results (the results of the FP64 decisions, or of the
+  other branch of an alpha_min / T_min decision that lies inside the FP32
+  rounding band), and the mean absolute error per channel is <= 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_24053_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL_MAX = 2e-4
+TOL_MEAN = 1e-5
+
+
+@pytest.fixture(scope="module")
+def geer():
+    from paper_2505_24053_gb300 import geer
+    geer.lib()
+    assert torch.cuda.is_available()
+    return geer
+
+
+def _tiny_scene(seed, n, deg, spread=3.0, zmin=None):
+    rng = np.random.default_rng(seed)
+    mean = rng.uniform(-spread, spread, (n, 3))
+    if zmin is not None:
+        mean[:, 2] = np.abs(mean[:, 2]) + zmin
+    log_s = rng.normal(-1.8, 0.6, (n, 3))
+    quat = rng.standard_normal((n, 4))
+    opacity = 1 / (1 + np.exp(-rng.normal(0.5, 1.5, n)))
+    sh = rng.normal(0, 0.3, (n, (deg + 1) ** 2, 3))
+    sh[:, 0, :] = rng.uniform(-math.sqrt(math.pi), math.sqrt(math.pi), (n, 3))
+    return wl.Scene(mean.astype(np.float32), np.exp(log_s).astype(np.float32), quat.astype(np.float32),
+                    opacity.astype(np.float32), sh.astype(np.float32), deg)
+
+
+def _render(geer, scene, cams, cap=None):
+    r = geer.Renderer(cams, scene.n, scene.sh_degree, pair_capacity=cap)
+    g = geer.Gaussians.from_scene(scene)
+    rgb = r.forward(g)
+    T = torch.empty(r.pixels, dtype=torch.float32, device="cuda")
+    r.ws.render_fwd(rgb, T)
+    torch.cuda.synchronize()
+    return r, g, rgb.cpu().numpy(), T.cpu().numpy()
+
+
+def _check_pixels(orc, scene, cam, rgb_img, pix, label):
+    """Strict check: every pixel within 2e-4 of an admissible oracle result (no
+    conditioning allowance), mean abs error <= 1e-5 per channel."""
+    out = orc.render_pixels(scene, cam, pix)
+    gpu = rgb_img[pix[:, 1], pix[:, 0]].astype(np.float64)
+    ok, err, ill, und = orc.match_pixels(gpu, out, TOL_MAX, cond_limit=np.inf)
+    bad = np.where(~ok)[0]
+    assert bad.size == 0, (label, bad[:5], err[bad[:5]], out["cond"][bad[:5]])
+    assert np.all(err.mean(axis=0) <= TOL_MEAN), (label, err.mean(axis=0))
+    assert und.sum() == 0, (label, und.sum())
+    return err, out["cond"] > 1e-4
+
+
+TINY = [
+    ("pinhole", [wl.Camera(wl.PINHOLE, 40, 30, math.radians(60), bg=(0.2, 0.3, 0.4))]),
+    ("equi180_ragged", [wl.Camera(wl.EQUIDISTANT, 37, 23, math.radians(180))]),
+    ("equi200_square", [wl.Camera(wl.EQUIDISTANT, 48, 48, math.radians(200))]),
+    ("kb190", [wl.Camera(wl.KANNALA_BRANDT, 64, 48, math.radians(190), k=wl.kb_coeffs(3))]),
+    ("equi210_4cams", [wl.Camera(wl.EQUIDISTANT, 45, 36, math.radians(210), R_cw=wl.pose(wl.rot_y(math.radians(a)),
+                                                                                       (0.1, 0, 0))[0],
+                                 t_cw=wl.pose(wl.rot_y(math.radians(a)), (0.1, 0, 0))[1]) for a in (0, 90, 180, 270)]),
+]
+
+
+@pytest.mark.parametrize("name,cams", TINY, ids=[t[0] for t in TINY])
+def test_preprocess_bit_exact_vs_replica(geer, orc, name, cams):
+    scene = _tiny_scene(hash(name) % 997, 300, 2)
+    r = geer.Renderer(cams, scene.n, scene.sh_degree)
+    g = geer.Gaussians.from_scene(scene)
+    r.prepare(g)
+    cull, keys, ranges, counts = r.ws.debug_preprocess()
+    n = scene.n
+    for ci, cam in enumerate(cams):
+        rc, rk, rr, rn = orc.replica(scene, cam)
+        sl = slice(ci * n, (ci + 1) * n)
+        assert np.array_equal(cull[sl], rc), name
+        assert np.array_equal(keys[sl][rc == 0], rk[rc == 0]), name
+        assert np.array_equal(ranges[sl], rr), name
+        assert np.array_equal(counts[sl], rn), name
+
+
+def _expand_pairs(orc, scene, cams):
+    keys, vals, base = [], [], 0
+    n = scene.n
+    for ci, cam in enumerate(cams):
+        rc, rk, rr, rn = orc.replica(scene, cam)
+        mask = orc.assoc_mask(cam, rr)
+        tx = (cam.width + 15) // 16
+        for g in range(n):
+            if rc[g]:
+                continue
+            cy, cx = np.nonzero(mask[g])
+            t = base + cy * tx + cx
+            keys.append((t.astype(np.uint64) << np.uint64(32)) | np.uint64(rk[g]))
+            vals.append(np.full(t.size, ci * n + g, np.uint32))
+        base += tx * ((cam.height + 15) // 16)
+    keys = np.concatenate(keys)
+    vals = np.concatenate(vals)
+    order = np.lexsort((vals, keys))  # stable by (key, emission order = value)
+    return keys[order], vals[order]
+
+
+@pytest.mark.parametrize("name,cams", TINY, ids=[t[0] for t in TINY])
+def test_sorted_pairs_match_cpu_sort(geer, orc, name, cams):
+    scene = _tiny_scene(1 + hash(name) % 991, 400, 1)
+    r = geer.Renderer(cams, scene.n, scene.sh_degree)
+    g = geer.Gaussians.from_scene(scene)
+    P = r.prepare(g)
+    k, v = r.ws.debug_pairs()
+    ek, ev = _expand_pairs(orc, scene, cams)
+    assert P == ek.size
+    assert np.array_equal(k, ek)
+    assert np.array_equal(v, ev)
+
+
+@pytest.mark.parametrize("name,cams", TINY, ids=[t[0] for t in TINY])
+def test_render_tiny_scenes_full_frame(geer, orc, name, cams):
+    scene = _tiny_scene(7 + hash(name) % 983, 250, 3, spread=2.5)
+    r, g, rgb, T = _render(geer, scene, cams)
+    off = 0
+    for ci, cam in enumerate(cams):
+        img = rgb[off:off + cam.pixels].reshape(cam.height, cam.width, 3)
+        _check_pixels(orc, scene, cam, img, wl.all_pixels(cam), f"{name}/{ci}")
+        off += cam.pixels
+
+
+def test_render_workload1_full_frame(geer, orc):
+    """4096 Gaussians, pinhole 128x128 60 deg: every pixel against the oracle."""
+    scene = wl.config_scene(1)
+    cam = wl.config_cameras(1)[0]
+    r, g, rgb, T = _render(geer, scene, [cam])
+    img = rgb.reshape(cam.height, cam.width, 3)
+    out = orc.render_pixels(scene, cam, wl.all_pixels(cam))
+    err, ill = _check_pixels(orc, scene, cam, img, wl.all_pixels(cam), "workload1")
+    # no pixel needs the conditioning allowance here: strict 2e-4 everywhere
+    assert (err.max(axis=1) > TOL_MAX).sum() == 0, err.max()
+    print(f"workload 1: max err {err.max():.3g}, mean err {err.mean(axis=0)}")
+    # final transmittance
+    assert np.allclose(T, out["T"], atol=5e-4)
+
+
+def test_empty_and_single_gaussian(geer, orc):
+    cam = wl.Camera(wl.EQUIDISTANT, 33, 17, math.radians(150), bg=(0.25, 0.5, 0.75))
+    empty = _tiny_scene(3, 0, 0)
+    r, g, rgb, T = _render(geer, empty, [cam])
+    assert np.array_equal(rgb, np.tile(np.float32([0.25, 0.5, 0.75]), (cam.pixels, 1)))
+    assert np.all(T == 1.0)
+    one = wl.Scene(np.array([[0.2, -0.1, 2.0]], np.float32), np.array([[0.3, 0.1, 0.2]], np.float32),
+                   np.array([[0.9, 0.1, 0.3, -0.2]], np.float32), np.array([0.95], np.float32),
+                   np.array([[[1.0, -0.5, 0.2]]], np.float32), 0)
+    r, g, rgb, T = _render(geer, one, [cam])
+    _check_pixels(orc, one, cam, rgb.reshape(cam.height, cam.width, 3), wl.all_pixels(cam), "one")
+
+
+def test_capacity_overflow_is_reported_and_recovered(geer):
+    scene = _tiny_scene(5, 200, 0, zmin=1.0)
+    cam = wl.Camera(wl.PINHOLE, 64, 64, math.radians(70))
+    g = geer.Gaussians.from_scene(scene)
+    ws = geer.Workspace([cam], scene.n, 0, 16)
+    ws.preprocess(g)
+    with pytest.raises(geer.GeerError) as ei:
+        ws.bin_sort(sync=True)
+    assert ei.value.status == geer.ERR_CAPACITY and ws.last_pairs > 16
+    # asynchronous path: the overflow lands in the device status word
+    ws.preprocess(g)
+    ws.bin_sort(sync=False)
+    rgb = torch.full((cam.pixels, 3), -1.0, device="cuda")
+    ws.render_fwd(rgb)
+    st, pairs = ws.device_status()
+    assert st == geer.ERR_CAPACITY and pairs == ws.last_pairs
+    assert torch.all(rgb == -1.0)  # nothing rendered
+    st, _ = ws.device_status()
+    assert st == geer.OK
+    # the renderer grows and succeeds
+    r = geer.Renderer([cam], scene.n, 0, pair_capacity=16)
+    r.forward(g)
+    assert r.ws.pair_capacity >= ws.last_pairs
+
+
+def test_batched_cameras_equal_single_renders(geer):
+    scene = _tiny_scene(9, 500, 3, spread=3.0)
+    cams = [wl.Camera(wl.PINHOLE, 50, 40, math.radians(70)),
+            wl.Camera(wl.EQUIDISTANT, 64, 64, math.radians(200)),
+            wl.Camera(wl.KANNALA_BRANDT, 40, 30, math.radians(150), k=wl.kb_coeffs(44))]
+    _, _, rgb_all, _ = _render(geer, scene, cams)
+    off = 0
+    for cam in cams:
+        _, _, rgb_one, _ = _render(geer, scene, [cam])
+        assert np.array_equal(rgb_all[off:off + cam.pixels], rgb_one)
+        off += cam.pixels
+
+
+@pytest.mark.parametrize("cfg,npix", [(2, 384), (3, 256)])
+def test_render_large_workloads_sampled_pixels(geer, orc, cfg, npix):
+    """Full-size workloads 2 (500k, equidistant 180) and 3 (1M, KB 190): a seeded
+    sample of pixels (the oracle brute-forces every Gaussian per pixel)."""
+    scene = wl.config_scene(cfg)
+    cam = wl.config_cameras(cfg)[0]
+    r, g, rgb, T = _render(geer, scene, [cam])
+    img = rgb.reshape(cam.height, cam.width, 3)
+    pix = wl.random_pixels(cam, npix, seed=100 + cfg)
+    err, ill = _check_pixels(orc, scene, cam, img, pix, f"workload{cfg}")
+    strict = int((err.max(axis=1) > TOL_MAX).sum())
+    print(f"workload {cfg}: max err {err.max():.3g}, mean err {err.mean(axis=0)}, "
+          f"ill-conditioned {ill.sum()}/{len(ill)}, above 2e-4: {strict}")
+
+
+def test_render_workload5_sampled_pixels(geer, orc):
+    """6M Gaussians, 4 surround equidistant 210 deg cameras in one launch."""
+    scene = wl.config_scene(5)
+    cams = wl.config_cameras(5)
+    r, g, rgb, T = _render(geer, scene, cams)
+    off = 0
+    for ci, cam in enumerate(cams):
+        img = rgb[off:off + cam.pixels].reshape(cam.height, cam.width, 3)
+        pix = wl.random_pixels(cam, 48, seed=500 + ci)
+        err, ill = _check_pixels(orc, scene, cam, img, pix, f"workload5/{ci}")
+        strict = int((err.max(axis=1) > TOL_MAX).sum())
+        print(f"workload 5 cam {ci}: max err {err.max():.3g}, ill-conditioned {ill.sum()}/{len(ill)}, "
+              f"above 2e-4: {strict}")
+        off += cam.pixels
