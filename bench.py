@@ -1,0 +1,328 @@
+"""Benchmark of the exact ray-Gaussian render hot path on GB300.
+
+Workload (the headline configuration): 1M Gaussians (means uniform in a 4 m cube
+3-7 m ahead, log-scales N(-2.5, 0.5), SH degree 3), Kannala-Brandt fisheye
+1280x960, 190 deg FoV, k_i ~ U[-0.05, 0.05], BEAP 16x16 tiles, seeded synthetic
+data. One step = preprocess (PBF association) + duplicate + radix sort + ranges +
+render of the whole frame, plus the backward when available.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun), every rank renders its
+own replica of the workload (the path has no cross-GPU exchange) and the time
+is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s fwd and fwd+bwd at 1M Gaussians, 180° fisheye; serving p50/p99 ms"
+WORKLOAD = "1M Gaussians (cube 4 m, 3-7 m ahead, SH3), Kannala-Brandt 1280x960 190deg, BEAP 16x16 tiles"
+FLOPS_TEST = 43    # per ray-Gaussian evaluation: W d, cross product, two norms, divide, exp arg, exp, t* dot
+FLOPS_BLEND = 10   # per applied contributor: clamp, transmittance update, weight, 3 colour FMAs
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.strip()]
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 8]
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _oracle_sample(scene, cam, seconds: float, seed: int = 7):
+    """Time the CPU oracle on a seeded pixel sample sized to ~seconds of work."""
+    from oracle import oracle as orc
+    from paper_2505_24053_gb300 import workloads as wl
+    t0 = time.perf_counter()
+    rep = orc.replica(scene, cam)
+    t_rep = time.perf_counter() - t0
+    probe = wl.random_pixels(cam, 32, seed)
+    t0 = time.perf_counter()
+    orc.render_pixels(scene, cam, probe, rep=rep)
+    per_px = (time.perf_counter() - t0) / probe.shape[0]
+    n = int(max(32, min(8192, (seconds - t_rep) / max(per_px, 1e-9))))
+    pix = wl.random_pixels(cam, n, seed + 1)
+    t0 = time.perf_counter()
+    rep = orc.replica(scene, cam)
+    orc.render_pixels(scene, cam, pix, rep=rep)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n / dt / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} seeded pixels of the {cam.width}x{cam.height} frame against all {scene.n} Gaussians "
+                      f"(brute force, FP64, incl. the FP32 replica pass), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_2505_24053_gb300 import workloads as wl
+    orc.build()
+    scene = wl.config_scene(3)
+    cam = wl.config_cameras(3)[0]
+    per_step = args.ref_pixels
+    rep = orc.replica(scene, cam)
+    for w in range(args.warmup):
+        orc.render_pixels(scene, cam, wl.random_pixels(cam, per_step, 1000 + w), rep=rep)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        rep = orc.replica(scene, cam)
+        orc.render_pixels(scene, cam, wl.random_pixels(cam, per_step, 2000 + k), rep=rep)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pass": "fwd", "sample_pixels_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} seeded pixels per step against all {scene.n} Gaussians"},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_24053_gb300 import geer
+    from paper_2505_24053_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    scene = wl.config_scene(args.workload)
+    cam = wl.config_cameras(args.workload)[0]
+    g = geer.Gaussians.from_scene(scene)
+    r = geer.Renderer([cam], scene.n, scene.sh_degree)
+    P = r.prepare(g)  # sizes the pair capacity (synchronous count), then everything stays asynchronous
+    ws = r.ws
+    pixels = cam.pixels * 1
+    rgb = torch.empty((pixels, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+    have_bwd = False
+    grads = None
+    try:
+        grads = {k: torch.zeros_like(v) for k, v in (("mean", g.mean), ("scale", g.scale), ("quat", g.quat),
+                                                     ("opacity", g.opacity), ("sh", g.sh))}
+        ws.render_fwd(rgb)
+        ws.render_bwd(g, torch.ones_like(rgb), grads)
+        torch.cuda.synchronize()
+        have_bwd = True
+    except geer.GeerError:
+        have_bwd = False
+    dL = torch.full_like(rgb, 1.0 / (3 * pixels))
+
+    def step(ev):
+        ev[0].record(stream)
+        ws.preprocess(g)
+        ev[1].record(stream)
+        ws.bin_sort(sync=False)
+        ev[2].record(stream)
+        ws.render_fwd(rgb)
+        ev[3].record(stream)
+        if have_bwd:
+            ws.render_bwd(g, dL, grads)
+        ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step([torch.cuda.Event(enable_timing=True) for _ in range(5)])
+    torch.cuda.synchronize()
+    st, pairs = ws.device_status()
+    if st != geer.OK:
+        raise RuntimeError(f"device status after warm-up: {geer.status_string(st)}")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()  # between timed steps, outside the step's events
+            step(evs[k])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    st, pairs = ws.device_status()
+    if st != geer.OK:
+        raise RuntimeError(f"device status after timed steps: {geer.status_string(st)}")
+    step_ms = [e[0].elapsed_time(e[4]) for e in evs]
+    prep_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    sort_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    rend_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    bwd_ms = [e[3].elapsed_time(e[4]) for e in evs]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * pixels * args.steps / (total_ms / 1e3) / 1e6
+
+    # end to end through the C ABI with host buffers: H2D of the Gaussians from
+    # pinned memory, the step, D2H of the image
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+            (scene.mean, scene.scale, scene.quat, scene.opacity, scene.sh)]
+    dst = [g.mean, g.scale, g.quat, g.opacity, g.sh]
+    out_host = torch.empty((pixels, 3), dtype=torch.float32).pin_memory()
+    h2d = sum(h.numel() * 4 for h in host)
+    d2h = out_host.numel() * 4
+    e_evs = []
+    for k in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        for h, d in zip(host, dst):
+            d.copy_(h, non_blocking=True)
+        ws.preprocess(g)
+        ws.bin_sort(sync=False)
+        ws.render_fwd(rgb)
+        if have_bwd:
+            ws.render_bwd(g, dL, grads)
+        out_host.copy_(rgb, non_blocking=True)
+        e1.record(stream)
+        if k >= args.warmup:
+            e_evs.append((e0, e1))
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e_evs)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = world * pixels * args.steps / (e2e_ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel (the render: FP32 pipe / issue bound)
+    evals, applied = ws.render_counts()
+    peaks, peak_src = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    r_ms = statistics.mean(rend_ms)
+    flops = FLOPS_TEST * evals + FLOPS_BLEND * applied
+    achieved = flops / (r_ms / 1e3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "render_fwd_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+    tiles = math.ceil(cam.width / 16) * math.ceil(cam.height / 16)
+    n_passes = math.ceil((32 + max(1, math.ceil(math.log2(tiles)))) / 8)
+    launches_per_step = 6 + n_passes + (2 if have_bwd else 0)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == 3 else f"workload {args.workload}",
+                   "pass": "fwd+bwd" if have_bwd else "fwd", "gaussians": scene.n,
+                   "pixels_per_gpu": pixels, "pairs": int(pairs), "parallelism": f"replicas x{world}",
+                   "l2": "512 MB buffer written between timed steps (outside step events); inputs 236 MB > L2"},
+        "stages_ms": {"preprocess": statistics.mean(prep_ms), "bin_sort": statistics.mean(sort_ms),
+                      "render_fwd": r_ms, "backward": statistics.mean(bwd_ms) if have_bwd else None},
+        "roofline": {"bound": "alu", "kernel": "k_render_fwd", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                     "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
+                                    f"(max SM clock, {peak_src})",
+                     "work": {"evaluations": evals, "applied": applied, "flops_per_eval": FLOPS_TEST,
+                              "flops_per_applied": FLOPS_BLEND}},
+        "e2e": {"value": e2e, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _oracle_sample(scene, cam, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="geer", choices=["geer", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-pixels", type=int, default=24)
+    ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3],
+                    help="3 = the headline configuration; 1, 2 = smaller cases for profiling")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -177,6 +177,11 @@ geer_status geer_debug_preprocess(geer_workspace *ws, uint16_t *ranges, uint32_t
 geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *values, int64_t cap, int64_t *count,
                              void *stream);
 
+/* Measurement (synchronous): totals over all rays of the last geer_render_fwd
+ * of the ray-Gaussian evaluations executed (list entries walked up to early
+ * termination) and of the contributors composited. */
+geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t *applied, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -193,6 +193,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_tr = L.take(sizeof(uint2) * c.tiles);
     size_t o_last = L.take(sizeof(uint32_t) * c.pixels);
     size_t o_tfin = L.take(sizeof(float) * c.pixels);
+    size_t o_ev = L.take(sizeof(uint2) * c.pixels);
     size_t o_gacc = L.take(sizeof(GradAcc) * cg);
     if (base && ws) {
         ws->d_cams = reinterpret_cast<DevCam *>(base + o_cams);
@@ -213,6 +214,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_tile_range = reinterpret_cast<uint2 *>(base + o_tr);
         ws->d_last = reinterpret_cast<uint32_t *>(base + o_last);
         ws->d_Tfin = reinterpret_cast<float *>(base + o_tfin);
+        ws->d_evals = reinterpret_cast<uint2 *>(base + o_ev);
         ws->d_gacc = reinterpret_cast<GradAcc *>(base + o_gacc);
     }
     return L.off;
@@ -513,6 +515,25 @@ geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *value
             return GEER_ERR_CUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return GEER_ERR_CUDA;
     }
+    return GEER_OK;
+}
+
+geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t *applied, void *stream) {
+    if (!ws || !evaluated || !applied) return GEER_ERR_ARG;
+    if (ws->stage < 3) return GEER_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<uint2> v(ws->n_pixels);
+    if (cudaMemcpyAsync(v.data(), ws->d_evals, sizeof(uint2) * ws->n_pixels, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    uint64_t e = 0, a = 0;
+    for (const uint2 &x : v) {
+        e += x.x;
+        a += x.y;
+    }
+    *evaluated = e;
+    *applied = a;
     return GEER_OK;
 }
 

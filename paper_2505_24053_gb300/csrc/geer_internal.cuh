@@ -108,6 +108,7 @@ struct geer_workspace {
     uint2 *d_tile_range;    // [cap_tiles]
     uint32_t *d_last;       // [cap_pixels] list entries walked per ray
     float *d_Tfin;          // [cap_pixels] final transmittance (for the backward)
+    uint2 *d_evals;         // [cap_pixels] ray-Gaussian evaluations executed / contributors applied
     geer::GradAcc *d_gacc;  // [cap_cams * cap_gauss]
 
     // state of the last calls

@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
                                                         const Record *__restrict__ rec,
                                                         const uint32_t *__restrict__ misc, Params p,
                                                         float *__restrict__ rgb, float *__restrict__ Tout,
-                                                        float *__restrict__ Tfin, uint32_t *__restrict__ last_out) {
+                                                        float *__restrict__ Tfin, uint32_t *__restrict__ last_out,
+                                                        uint2 *__restrict__ evals) {
     __shared__ float4 s_rec[kBatch * 4];
     __shared__ int s_cam;
     if (misc[kMiscStatus] & kStatusCapacity) return;
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
     const uint2 range = tile_range[t];
     const float log2_amin = log2f(p.alpha_min);
     float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-    uint32_t last = 0;
+    uint32_t last = 0, n_eval = 0, n_applied = 0;
     bool done = !inside;
 
     for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
         const int cnt = (int)min((uint32_t)kBatch, range.y - b0);
         if (!done) {
             for (int j = 0; j < cnt; ++j) {
+                ++n_eval;
                 const float4 a = s_rec[j * 4 + 0];  // W00 W01 W02 W10
                 const float4 b = s_rec[j * 4 + 1];  // W11 W12 W20 W21
                 const float4 c = s_rec[j * 4 + 2];  // W22 ou0 ou1 ou2
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
                 cg = fmaf(wgt, e.z, cg);
                 cb = fmaf(wgt, e.w, cb);
                 T = Tn;
+                ++n_applied;
                 last = b0 - range.x + (uint32_t)j + 1u;
             }
         }
@@ -113,6 +116,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
         if (Tout) Tout[pix] = T;
         Tfin[pix] = T;
         last_out[pix] = last;
+        evals[pix] = make_uint2(n_eval, n_applied);
     }
 }
 
@@ -123,7 +127,7 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
     k_render_fwd<<<(unsigned)ws->n_tiles, kTilePix, 0, s>>>(
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_range, ws->d_vals[ws->sorted_buf], ws->d_rec, ws->d_misc,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, rgb, T_final,
-        ws->d_Tfin, ws->d_last);
+        ws->d_Tfin, ws->d_last, ws->d_evals);
     return cudaGetLastError();
 }
 

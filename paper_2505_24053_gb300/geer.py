@@ -43,7 +43,8 @@ class ParamsC(C.Structure):
 
 EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "geer_workspace_init",
            "geer_workspace_destroy", "geer_set_cameras", "geer_preprocess", "geer_bin_sort", "geer_render_fwd",
-           "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs"]
+           "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
+           "geer_render_counts"]
 
 _lib = None
 
@@ -79,6 +80,7 @@ def lib(build_if_missing: bool = True):
         "geer_last_device_status": [P, P, P],
         "geer_debug_preprocess": [P, P, P, P, P, P],
         "geer_debug_pairs": [P, P, P, I64, P, P],
+        "geer_render_counts": [P, P, P, P],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -251,6 +253,13 @@ class Workspace:
                                            P(keys.ctypes.data), P(cull.ctypes.data), _stream(stream)),
                "geer_debug_preprocess")
         return cull, keys, ranges, counts
+
+    def render_counts(self, stream=None):
+        """(evaluations executed, contributors applied) of the last forward render."""
+        e, a = C.c_uint64(), C.c_uint64()
+        _check(lib().geer_render_counts(self._handle, C.byref(e), C.byref(a), _stream(stream)),
+               "geer_render_counts")
+        return int(e.value), int(a.value)
 
     def debug_pairs(self, cap: int | None = None, stream=None):
         cap = self.pair_capacity if cap is None else cap
