@@ -272,8 +272,10 @@ def run(args):
         with open(prof) as f:
             traffic = json.load(f).get("bytes_per_launch")
     tiles = math.ceil(cam.width / 16) * math.ceil(cam.height / 16)
-    n_passes = math.ceil((32 + max(1, math.ceil(math.log2(tiles)))) / 8)
-    launches_per_step = 6 + n_passes + (2 if have_bwd else 0)
+    tile_passes = math.ceil(max(1, math.ceil(math.log2(tiles))) / 8)
+    # preprocess, scan, compact, 4 depth passes x 3, gather, scan, duplicate, tile offsets,
+    # tile passes x 3, render
+    launches_per_step = 20 + 3 * tile_passes + (2 if have_bwd else 0)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,

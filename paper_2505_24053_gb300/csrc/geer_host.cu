@@ -138,6 +138,17 @@ void build_tables(const geer_camera *cams, int n, CamTables &out) {
             const double a = beap_angle(j, c.height, fy);
             out.ptab.push_back(make_float2((float)sin(a), (float)cos(a)));
         }
+        // tiles whose rays all have cos >= 0 (a contiguous middle range)
+        d.c0lo = d.tiles_x; d.c0hi = 0;
+        for (int tx = 0; tx < d.tiles_x; ++tx) {
+            const float4 v = out.ttab[d.tcol_off + tx];
+            if (v.z != 0.0f && v.w == 0.0f) { d.c0lo = std::min(d.c0lo, tx); d.c0hi = tx + 1; }
+        }
+        d.r0lo = d.tiles_y; d.r0hi = 0;
+        for (int ty = 0; ty < d.tiles_y; ++ty) {
+            const float4 v = out.ttab[d.trow_off + ty];
+            if (v.z != 0.0f && v.w == 0.0f) { d.r0lo = std::min(d.r0lo, ty); d.r0hi = ty + 1; }
+        }
         for (int k = 0; k < 9; ++k) d.R[k] = c.R_cw[k];
         for (int k = 0; k < 3; ++k) {
             d.t[k] = c.t_cw[k];
@@ -166,7 +177,7 @@ Caps caps_of(const CamTables &t, int32_t n_cams, int64_t n_gauss, int64_t pair_c
     c.pix_tab = std::max<int64_t>((int64_t)t.ptab.size(), 1);
     c.gauss = std::max<int64_t>(n_gauss, 1);
     c.pairs = std::max<int64_t>(pair_capacity, 1);
-    c.sort_tiles = ceil_div(c.pairs, kSortTile) + 1;
+    c.sort_tiles = ceil_div(std::max<int64_t>(c.pairs, (int64_t)n_cams * c.gauss), kSortTile) + 1;
     c.prep_blocks = prep_blocks(c.gauss);
     return c;
 }
@@ -183,14 +194,22 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_cnt = L.take(sizeof(uint32_t) * cg);
     size_t o_key = L.take(sizeof(uint32_t) * cg);
     size_t o_bs = L.take(sizeof(uint32_t) * c.cams * c.prep_blocks);
-    size_t o_k0 = L.take(sizeof(uint64_t) * c.pairs);
-    size_t o_k1 = L.take(sizeof(uint64_t) * c.pairs);
+    size_t o_bs2 = L.take(sizeof(uint32_t) * prep_blocks(cg));
+    size_t o_ik0 = L.take(sizeof(uint32_t) * cg);
+    size_t o_ik1 = L.take(sizeof(uint32_t) * cg);
+    size_t o_ii0 = L.take(sizeof(uint32_t) * cg);
+    size_t o_ii1 = L.take(sizeof(uint32_t) * cg);
+    size_t o_k0 = L.take(sizeof(uint32_t) * c.pairs);
+    size_t o_k1 = L.take(sizeof(uint32_t) * c.pairs);
     size_t o_v0 = L.take(sizeof(uint32_t) * c.pairs);
     size_t o_v1 = L.take(sizeof(uint32_t) * c.pairs);
-    size_t o_hist = L.take(sizeof(uint32_t) * kMaxPasses * kRadix);
-    size_t o_lb = L.take(sizeof(uint64_t) * kRadix * c.sort_tiles);
+    const int64_t groups = ceil_div(c.sort_tiles, kGroupTiles) + 1;
+    size_t o_th = L.take(sizeof(uint32_t) * kRadix * c.sort_tiles);
+    size_t o_gs = L.take(sizeof(uint32_t) * kRadix * groups);
+    size_t o_ge = L.take(sizeof(uint32_t) * kRadix * groups);
+    size_t o_db = L.take(sizeof(uint32_t) * kRadix);
     size_t o_misc = L.take(sizeof(uint32_t) * kMiscCount);
-    size_t o_tr = L.take(sizeof(uint2) * c.tiles);
+    size_t o_tr = L.take((sizeof(uint2) + sizeof(uint32_t)) * c.tiles);
     size_t o_last = L.take(sizeof(uint32_t) * c.pixels);
     size_t o_tfin = L.take(sizeof(float) * c.pixels);
     size_t o_ev = L.take(sizeof(uint2) * c.pixels);
@@ -204,12 +223,19 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_count = reinterpret_cast<uint32_t *>(base + o_cnt);
         ws->d_key = reinterpret_cast<uint32_t *>(base + o_key);
         ws->d_blocksum = reinterpret_cast<uint32_t *>(base + o_bs);
-        ws->d_keys[0] = reinterpret_cast<uint64_t *>(base + o_k0);
-        ws->d_keys[1] = reinterpret_cast<uint64_t *>(base + o_k1);
+        ws->d_blocksum2 = reinterpret_cast<uint32_t *>(base + o_bs2);
+        ws->d_ikey[0] = reinterpret_cast<uint32_t *>(base + o_ik0);
+        ws->d_ikey[1] = reinterpret_cast<uint32_t *>(base + o_ik1);
+        ws->d_iid[0] = reinterpret_cast<uint32_t *>(base + o_ii0);
+        ws->d_iid[1] = reinterpret_cast<uint32_t *>(base + o_ii1);
+        ws->d_keys[0] = reinterpret_cast<uint32_t *>(base + o_k0);
+        ws->d_keys[1] = reinterpret_cast<uint32_t *>(base + o_k1);
         ws->d_vals[0] = reinterpret_cast<uint32_t *>(base + o_v0);
         ws->d_vals[1] = reinterpret_cast<uint32_t *>(base + o_v1);
-        ws->d_hist = reinterpret_cast<uint32_t *>(base + o_hist);
-        ws->d_lookback = reinterpret_cast<uint64_t *>(base + o_lb);
+        ws->d_tile_hist = reinterpret_cast<uint32_t *>(base + o_th);
+        ws->d_group_sum = reinterpret_cast<uint32_t *>(base + o_gs);
+        ws->d_group_excl = reinterpret_cast<uint32_t *>(base + o_ge);
+        ws->d_digit_base = reinterpret_cast<uint32_t *>(base + o_db);
         ws->d_misc = reinterpret_cast<uint32_t *>(base + o_misc);
         ws->d_tile_range = reinterpret_cast<uint2 *>(base + o_tr);
         ws->d_last = reinterpret_cast<uint32_t *>(base + o_last);
@@ -273,7 +299,7 @@ geer_status upload_cams(geer_workspace *ws, const CamTables &t, cudaStream_t s) 
     int bits = 1;
     while ((int64_t(1) << bits) < t.tiles) ++bits;
     ws->tile_bits = bits;
-    ws->n_passes = (32 + bits + kRadixBits - 1) / kRadixBits;
+    ws->n_tile_passes = (bits + kRadixBits - 1) / kRadixBits;
     ws->stage = 0;
     return GEER_OK;
 }
@@ -356,9 +382,10 @@ geer_status geer_workspace_init(void *dev_mem, size_t bytes, const geer_camera *
     ws->sort_grid = ws->num_sms * sort_blocks_per_sm();
     ws->stage_bytes = sizeof(DevCam) * c.cams + sizeof(float4) * c.tile_tab + sizeof(float2) * c.pix_tab;
     if (cudaMallocHost(&ws->h_stage, ws->stage_bytes) != cudaSuccess) { free(ws); return GEER_ERR_CUDA; }
-    // status words and look-back tags start from zero
+    // status words and radix group sums start from zero
     e = cudaMemset(ws->d_misc, 0, sizeof(uint32_t) * kMiscCount);
-    if (e == cudaSuccess) e = cudaMemset(ws->d_lookback, 0, sizeof(uint64_t) * kRadix * c.sort_tiles);
+    if (e == cudaSuccess)
+        e = cudaMemset(ws->d_group_sum, 0, sizeof(uint32_t) * kRadix * (ceil_div(c.sort_tiles, kGroupTiles) + 1));
     if (e != cudaSuccess) { cudaFreeHost(ws->h_stage); free(ws); return GEER_ERR_CUDA; }
     st = upload_cams(ws, t, 0);
     if (st == GEER_OK && cudaStreamSynchronize(0) != cudaSuccess) st = GEER_ERR_CUDA;
@@ -401,8 +428,10 @@ geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *strea
     if (!ws) return GEER_ERR_ARG;
     if (ws->stage < 1) return GEER_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_scan_blocks(ws, s);
-    if (e != cudaSuccess) return GEER_ERR_CUDA;
+    // live items in index order -> stable depth sort -> pair counts in depth order
+    if (launch_bin_front(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    if (launch_depth_sort(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    if (launch_count_pairs(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
     if (pairs_needed) {
         uint32_t m[kMiscCount];
         if (cudaMemcpyAsync(m, ws->d_misc, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -419,9 +448,9 @@ geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *strea
             return GEER_ERR_CAPACITY;
         }
     }
-    if ((e = launch_duplicate(ws, s)) != cudaSuccess) return GEER_ERR_CUDA;
-    if ((e = launch_sort(ws, s)) != cudaSuccess) return GEER_ERR_CUDA;
-    if ((e = launch_ranges(ws, s)) != cudaSuccess) return GEER_ERR_CUDA;
+    // emit (tile, item) pairs in depth order, stable sort by tile, ranges
+    if (launch_duplicate(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    if (launch_tile_sort(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
     ws->stage = 2;
     return GEER_OK;
 }
@@ -462,7 +491,6 @@ geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *st
             return GEER_ERR_CUDA;
     }
     if (m[kMiscStatus] & kStatusCapacity) return GEER_ERR_CAPACITY;
-    if (m[kMiscStatus] & kStatusTimeout) return GEER_ERR_TIMEOUT;
     return GEER_OK;
 }
 
@@ -507,13 +535,20 @@ geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *value
     *count = P;
     const int64_t n = std::min(P, cap);
     if (n > 0) {
-        if (keys && cudaMemcpyAsync(keys, ws->d_keys[ws->sorted_buf], sizeof(uint64_t) * n, cudaMemcpyDeviceToHost,
-                                    s) != cudaSuccess)
+        const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
+        std::vector<uint32_t> t(n), v(n), depth(items);
+        if (cudaMemcpyAsync(t.data(), ws->d_keys[ws->sorted_buf], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(v.data(), ws->d_vals[ws->sorted_buf], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(depth.data(), ws->d_key, sizeof(uint32_t) * items, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
             return GEER_ERR_CUDA;
-        if (values && cudaMemcpyAsync(values, ws->d_vals[ws->sorted_buf], sizeof(uint32_t) * n,
-                                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
-            return GEER_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return GEER_ERR_CUDA;
+        for (int64_t i = 0; i < n; ++i) {
+            if (keys) keys[i] = ((uint64_t)t[i] << 32) | (v[i] < items ? depth[v[i]] : 0u);
+            if (values) values[i] = v[i];
+        }
     }
     return GEER_OK;
 }

@@ -16,21 +16,20 @@ constexpr int kSortItems = 12;              // keys per thread per onesweep tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
-constexpr int kMaxPasses = 8;
 constexpr int kMaxCams = 256;
+constexpr int kGroupTiles = 32;            // sort tiles per group (radix offsets are scanned per group)
+constexpr int kSmemTiles = 12288;          // per-block tile histogram in shared memory up to this many tiles
 
 // Device status word bits.
 constexpr uint32_t kStatusCapacity = 1u;
-constexpr uint32_t kStatusTimeout = 2u;
 
 // Indices into the misc u32 array of the workspace.
 enum Misc : int {
     kMiscStatus = 0,      // device status bits
     kMiscPairs = 1,       // pair count P (clamped to u32)
     kMiscPairsHi = 2,     // unclamped P / 2^32
-    kMiscFrame = 3,       // frame counter (look-back epochs)
     kMiscTotalLo = 4,     // unclamped P mod 2^32
-    kMiscTileCtr = 8,     // onesweep tile counters, one per pass (8 .. 15)
+    kMiscLive = 5,        // live (camera, Gaussian) items (tile count > 0)
     kMiscCount = 32
 };
 
@@ -42,7 +41,8 @@ struct DevCam {
     int32_t any_row_flip, any_col_flip;
     int32_t tcol_off, trow_off;  // offsets (in float4) of the per-tile tables
     int32_t pcol_off, prow_off;  // offsets (in float2) of the per-pixel tables
-    int32_t pad_;
+    int32_t c0lo, c0hi, r0lo, r0hi;  // tile columns / rows whose rays all have cos >= 0
+    int32_t pad_[3];
     int64_t pix_base;    // offset of pixel (0, 0) in the batched image (in pixels)
     float R[9], t[3];    // world -> camera
     float o[3];          // camera centre in world coordinates
@@ -89,7 +89,7 @@ struct geer_workspace {
     // current camera set
     int32_t n_cams;
     int64_t n_pixels, n_tiles;
-    int32_t tile_bits, n_passes;
+    int32_t tile_bits, n_tile_passes;
     geer::DevCam cams[geer::kMaxCams];
 
     // device arrays (inside the caller's memory)
@@ -99,13 +99,18 @@ struct geer_workspace {
     geer::Record *d_rec;
     uint4 *d_ranges;
     uint32_t *d_count, *d_key;
-    uint32_t *d_blocksum;
-    uint64_t *d_keys[2];
-    uint32_t *d_vals[2];
-    uint32_t *d_hist;       // [kMaxPasses][kRadix]
-    uint64_t *d_lookback;   // [cap_sort_tiles][kRadix]
+    uint32_t *d_blocksum;   // live items per preprocess block
+    uint32_t *d_blocksum2;  // pairs per block of depth-sorted items
+    uint32_t *d_ikey[2];    // depth keys of the live items (ping-pong)
+    uint32_t *d_iid[2];     // item ids (camera * n + gaussian) of the live items
+    uint32_t *d_keys[2];    // pair tile ids (ping-pong)
+    uint32_t *d_vals[2];    // pair item ids
+    uint32_t *d_tile_hist;  // [cap_sort_tiles][kRadix] digit histogram per sort tile
+    uint32_t *d_group_sum;  // [cap_sort_groups][kRadix] (zero between passes)
+    uint32_t *d_group_excl; // [cap_sort_groups][kRadix]
+    uint32_t *d_digit_base; // [kRadix]
     uint32_t *d_misc;       // [kMiscCount]
-    uint2 *d_tile_range;    // [cap_tiles]
+    uint2 *d_tile_range;    // [cap_tiles] tile [start, end), followed by [cap_tiles] u32 pair counts
     uint32_t *d_last;       // [cap_pixels] list entries walked per ray
     float *d_Tfin;          // [cap_pixels] final transmittance (for the backward)
     uint2 *d_evals;         // [cap_pixels] ray-Gaussian evaluations executed / contributors applied
@@ -115,8 +120,9 @@ struct geer_workspace {
     int64_t n_gauss;
     int32_t sh_degree;
     int stage;               // 0 none, 1 preprocessed, 2 sorted, 3 rendered
-    int sorted_buf;          // which ping-pong buffer holds the sorted pairs
-    int sort_grid;           // persistent onesweep grid
+    int sorted_buf;          // which ping-pong buffer holds the tile-sorted pairs
+    int depth_buf;           // which ping-pong buffer holds the depth-sorted items
+    int sort_grid;           // grid of the radix kernels (grid-stride over sort tiles)
     int num_sms;
 
     // pinned staging for asynchronous camera uploads
@@ -128,10 +134,11 @@ namespace geer {
 
 // Launchers (defined in the .cu files).
 cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g, cudaStream_t s);
-cudaError_t launch_scan_blocks(const geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_bin_front(const geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_depth_sort(geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_count_pairs(const geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s);
-cudaError_t launch_sort(geer_workspace *ws, cudaStream_t s);
-cudaError_t launch_ranges(const geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_tile_sort(geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_final, cudaStream_t s);
 cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians *g, float *d_mean, float *d_scale,

@@ -195,6 +195,43 @@ __device__ __forceinline__ void sh_colour(int deg, const float *c, float x, floa
     rgb[2] = fmaxf(b, 0.0f);
 }
 
+// True when the association predicate reduces to the rectangle X0 x Y0: no
+// flipped-angle ranges and X0, Y0 inside the tiles whose rays all have
+// cos(theta) >= 0 (columns) and cos(phi) >= 0 (rows).
+__device__ __forceinline__ bool is_rect(const DevCam &cam, const int rg[8]) {
+    if (rg[2] < rg[3] || rg[6] < rg[7]) return false;
+    if (rg[0] >= rg[1] || rg[4] >= rg[5]) return true;  // empty
+    return rg[0] >= cam.c0lo && rg[1] <= cam.c0hi && rg[4] >= cam.r0lo && rg[5] <= cam.r0hi;
+}
+
+__device__ __forceinline__ void unpack_ranges(const uint4 r4, int rg[8]) {
+    rg[0] = (int)(r4.x & 0xffff); rg[1] = (int)(r4.x >> 16); rg[2] = (int)(r4.y & 0xffff); rg[3] = (int)(r4.y >> 16);
+    rg[4] = (int)(r4.z & 0xffff); rg[5] = (int)(r4.z >> 16); rg[6] = (int)(r4.w & 0xffff); rg[7] = (int)(r4.w >> 16);
+}
+
+// Block-wide exclusive scan (256 threads); returns the exclusive prefix and the block total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *wsum, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kPrepThreads / 32; ++w) {
+        const uint32_t t = wsum[w];
+        pre += w < warp ? t : 0u;
+        tot += t;
+    }
+    __syncthreads();
+    total = tot;
+    return pre + v - x;
+}
+
 __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -334,7 +371,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_preprocess(
             arc_range(B, rtab, cam.tiles_y, rg[4], rg[5]);
             if (cam.any_row_flip) arc_range(shift_arc(A), ctab, cam.tiles_x, rg[2], rg[3]);
             if (cam.any_col_flip) arc_range(shift_arc(B), rtab, cam.tiles_y, rg[6], rg[7]);
-            if (!cam.any_row_flip && !cam.any_col_flip) {
+            if (is_rect(cam, rg)) {
                 cnt = (uint32_t)(rg[1] - rg[0]) * (uint32_t)(rg[5] - rg[4]);
             } else {
                 int xa, xb, ya, yb;
@@ -371,24 +408,24 @@ __global__ void __launch_bounds__(kPrepThreads) k_preprocess(
             ranges[idx] = make_uint4(0, 0, 0, 0);
         }
         if (g < n) count[idx] = cnt;
-        uint32_t tot = block_sum_u32(cnt, red);
+        uint32_t tot = block_sum_u32(cnt > 0 ? 1u : 0u, red);
         if (threadIdx.x == 0) blocksum[(int64_t)ci * nblk + blockIdx.x] = tot;
     }
 }
 
-// Exclusive scan of the per-block pair counts (one block; each thread scans a
-// contiguous chunk serially). Also: pair total and capacity check, zeroing of
-// the sort histograms, tile counters and tile ranges, and the frame counter.
+// Exclusive scan of per-block counts (one block; each thread scans a contiguous
+// chunk serially). mode 0 (live items): total -> misc[kMiscLive]; also clears the
+// tile ranges and per-tile pair counts.
+// mode 1 (pairs): total -> misc[kMiscPairs] (clamped to cap) with the capacity check.
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ blocksum, int64_t m,
-                                                      uint32_t *__restrict__ misc, uint32_t *__restrict__ hist,
-                                                      uint2 *__restrict__ tile_range, int64_t ntiles, int64_t cap) {
+                                                      uint32_t *__restrict__ misc, uint2 *__restrict__ tile_range,
+                                                      int64_t ntiles, int64_t cap, int mode) {
     __shared__ unsigned long long warp_tot[32];
     const int t = threadIdx.x;
     const int64_t chunk = (m + 1023) / 1024;
     const int64_t b = t * chunk, e = min(m, b + chunk);
     unsigned long long s = 0;
     for (int64_t i = b; i < e; ++i) s += blocksum[i];
-    // block exclusive scan of s
     unsigned long long v = s;
     const int lane = t & 31, warp = t >> 5;
 #pragma unroll
@@ -415,74 +452,191 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ blo
         excl += c;
     }
     if (t == 1023) {
-        unsigned long long total = excl;  // last thread's running sum = grand total
-        misc[kMiscPairs] = (uint32_t)min(total, (unsigned long long)cap);
-        misc[kMiscPairsHi] = (uint32_t)(total >> 32);
-        misc[kMiscTotalLo] = (uint32_t)total;
-        if (total > (unsigned long long)cap) atomicOr(&misc[kMiscStatus], kStatusCapacity);
-        misc[kMiscFrame] += 1u;
+        const unsigned long long total = excl;
+        if (mode == 0) {
+            misc[kMiscLive] = (uint32_t)total;
+        } else {
+            misc[kMiscPairs] = (uint32_t)min(total, (unsigned long long)cap);
+            misc[kMiscPairsHi] = (uint32_t)(total >> 32);
+            misc[kMiscTotalLo] = (uint32_t)total;
+            if (total > (unsigned long long)cap) atomicOr(&misc[kMiscStatus], kStatusCapacity);
+        }
     }
-    for (int i = t; i < kMaxPasses * kRadix; i += 1024) hist[i] = 0u;
-    if (t < kMaxPasses) misc[kMiscTileCtr + t] = 0u;
-    for (int64_t i = t; i < ntiles; i += 1024) tile_range[i] = make_uint2(0u, 0u);
+    if (mode == 0) {
+        uint32_t *tile_count = reinterpret_cast<uint32_t *>(tile_range + ntiles);
+        for (int64_t i = t; i < ntiles; i += 1024) {
+            tile_range[i] = make_uint2(0u, 0u);
+            tile_count[i] = 0u;
+        }
+    }
 }
 
-// DuplicateWithKeys: one (global tile << 32 | depth bits, camera * n + g) pair per
-// associated tile, in row-major tile order per Gaussian, Gaussians in index order.
-__global__ void __launch_bounds__(kPrepThreads) k_duplicate(
-    const DevCam *__restrict__ cams, int ncams, const float4 *__restrict__ ttab, int64_t n,
-    const uint4 *__restrict__ ranges, const uint32_t *__restrict__ count, const uint32_t *__restrict__ key,
-    const uint32_t *__restrict__ blocksum, int64_t nblk, uint64_t *__restrict__ okeys, uint32_t *__restrict__ ovals,
-    int64_t cap) {
+// Compaction of the live (camera, Gaussian) items, in index order, into
+// (depth key, item) arrays.
+__global__ void __launch_bounds__(kPrepThreads) k_compact(int ncams, int64_t n, const uint32_t *__restrict__ count,
+                                                          const uint32_t *__restrict__ key,
+                                                          const uint32_t *__restrict__ blocksum, int64_t nblk,
+                                                          uint32_t *__restrict__ okey, uint32_t *__restrict__ oid) {
     __shared__ uint32_t wsum[kPrepThreads / 32];
     const int64_t g = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int ci = 0; ci < ncams; ++ci) {
-        const DevCam &cam = cams[ci];
         const int64_t idx = (int64_t)ci * n + g;
-        uint32_t cnt = g < n ? count[idx] : 0u;
-        // block exclusive scan of cnt
-        uint32_t v = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
+        const bool live = g < n && count[idx] > 0;
+        uint32_t tot;
+        const uint32_t pre = block_excl_scan(live ? 1u : 0u, wsum, tot);
+        if (live) {
+            const uint32_t k = key[idx];
+            const uint32_t pos = blocksum[(int64_t)ci * nblk + blockIdx.x] + pre;
+            okey[pos] = k;
+            oid[pos] = (uint32_t)idx;
         }
-        if (lane == 31) wsum[warp] = v;
-        __syncthreads();
-        uint32_t wpre = 0;
-        for (int w = 0; w < warp; ++w) wpre += wsum[w];
-        __syncthreads();
-        int64_t off = (int64_t)blocksum[(int64_t)ci * nblk + blockIdx.x] + wpre + (v - cnt);
-        if (cnt == 0 || off + cnt > cap) continue;
-        const uint4 r4 = ranges[idx];
-        int rg[8] = {(int)(r4.x & 0xffff), (int)(r4.x >> 16), (int)(r4.y & 0xffff), (int)(r4.y >> 16),
-                     (int)(r4.z & 0xffff), (int)(r4.z >> 16), (int)(r4.w & 0xffff), (int)(r4.w >> 16)};
-        const int64_t end = off + cnt;  // this Gaussian's slots
-        const uint64_t depth = key[idx];
-        const uint32_t val = (uint32_t)idx;
+    }
+}
+
+// Tile counts of the depth-sorted items, summed per block.
+__global__ void __launch_bounds__(kPrepThreads) k_gather_counts(const uint32_t *__restrict__ sorted_id,
+                                                                const uint32_t *__restrict__ count,
+                                                                const uint32_t *__restrict__ misc,
+                                                                uint32_t *__restrict__ blocksum) {
+    __shared__ uint32_t red[kPrepThreads / 32];
+    const uint32_t L = misc[kMiscLive];
+    const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    const uint32_t c = i < L ? count[sorted_id[i]] : 0u;
+    const uint32_t tot = block_sum_u32(c, red);
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+}
+
+// DuplicateWithKeys in depth order: item i of the depth-sorted list emits one
+// (global tile, item) pair per associated tile, tiles in row-major order. Items
+// whose association is a rectangle are emitted by the whole warp together
+// (lane j writes output j: coalesced); others loop per thread. Accumulates the
+// digit histograms of the tile ids for the tile sort.
+__global__ void __launch_bounds__(kPrepThreads) k_duplicate(
+    const DevCam *__restrict__ cams, const float4 *__restrict__ ttab, int64_t n, const uint32_t *__restrict__ sorted_id,
+    const uint4 *__restrict__ ranges, const uint32_t *__restrict__ count, const uint32_t *__restrict__ misc,
+    const uint32_t *__restrict__ blocksum, uint32_t *__restrict__ okeys, uint32_t *__restrict__ ovals,
+    uint32_t *__restrict__ tile_count, int ntiles, int64_t cap) {
+    __shared__ uint32_t wsum[kPrepThreads / 32];
+    extern __shared__ uint32_t sh[];  // per-tile pair counts when they fit (ntiles <= kSmemTiles)
+    const bool smem = ntiles <= kSmemTiles;
+    if (smem)
+        for (int k = threadIdx.x; k < ntiles; k += kPrepThreads) sh[k] = 0u;
+    const uint32_t L = misc[kMiscLive];
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    uint32_t item = 0, cnt = 0;
+    int rg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int ci = 0;
+    bool rect = true;
+    if (i < L) {
+        item = sorted_id[i];
+        cnt = count[item];
+        ci = (int)(item / (uint32_t)n);
+        unpack_ranges(ranges[item], rg);
+        rect = is_rect(cams[ci], rg);
+    }
+    uint32_t tot;
+    const uint32_t pre = block_excl_scan(cnt, wsum, tot);
+    const int64_t off = (int64_t)blocksum[blockIdx.x] + pre;
+    const bool fits = off + cnt <= cap;
+    const DevCam &cam = cams[ci];
+    // cooperative emission of the rectangle items of this warp
+    const uint32_t rc = (rect && fits) ? cnt : 0u;
+    uint32_t incl = rc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+    const int rw = rg[1] - rg[0];
+    const uint32_t tb = (uint32_t)(cam.tile_base + rg[4] * cam.tiles_x + rg[0]);
+    for (uint32_t j0 = 0; j0 < wtot; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        // owner: first lane whose inclusive count exceeds j
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+            if (v <= j) lo += step;
+        }
+        const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, lo);
+        const uint32_t o_cnt = __shfl_sync(0xffffffffu, rc, lo);
+        const int o_rw = __shfl_sync(0xffffffffu, rw, lo);
+        const uint32_t o_tb = __shfl_sync(0xffffffffu, tb, lo);
+        const int o_tx = __shfl_sync(0xffffffffu, cam.tiles_x, lo);
+        const uint32_t o_item = __shfl_sync(0xffffffffu, item, lo);
+        const int64_t o_off = __shfl_sync(0xffffffffu, off, lo);
+        if (j < wtot) {
+            const uint32_t k = j - (o_incl - o_cnt);
+            const uint32_t ky = k / (uint32_t)o_rw, kx = k - ky * (uint32_t)o_rw;
+            const uint32_t t = o_tb + ky * (uint32_t)o_tx + kx;
+            okeys[o_off + k] = t;
+            ovals[o_off + k] = o_item;
+            atomicAdd(smem ? &sh[t] : &tile_count[t], 1u);
+        }
+    }
+    // per-thread emission of the other items (flipped angular ranges)
+    if (!rect && fits && cnt > 0) {
         const float4 *ctab = ttab + cam.tcol_off;
         const float4 *rtab = ttab + cam.trow_off;
-        if (!cam.any_row_flip && !cam.any_col_flip) {
-            for (int cy = rg[4]; cy < rg[5]; ++cy)
-                for (int cx = rg[0]; cx < rg[1] && off < end; ++cx) {
-                    okeys[off] = ((uint64_t)(cam.tile_base + cy * cam.tiles_x + cx) << 32) | depth;
-                    ovals[off] = val;
-                    ++off;
+        int64_t o = off;
+        const int64_t end = off + cnt;
+        int xa, xb, ya, yb;
+        assoc_bbox(rg, cam.tiles_x, cam.tiles_y, xa, xb, ya, yb);
+        for (int cy = ya; cy < yb; ++cy) {
+            const float4 row = rtab[cy];
+            for (int cx = xa; cx < xb && o < end; ++cx)
+                if (tile_assoc(ctab[cx], row, cx, cy, rg)) {
+                    const uint32_t t = (uint32_t)(cam.tile_base + cy * cam.tiles_x + cx);
+                    okeys[o] = t;
+                    ovals[o] = item;
+                    atomicAdd(smem ? &sh[t] : &tile_count[t], 1u);
+                    ++o;
                 }
-        } else {
-            int xa, xb, ya, yb;
-            assoc_bbox(rg, cam.tiles_x, cam.tiles_y, xa, xb, ya, yb);
-            for (int cy = ya; cy < yb; ++cy) {
-                const float4 row = rtab[cy];
-                for (int cx = xa; cx < xb && off < end; ++cx)
-                    if (tile_assoc(ctab[cx], row, cx, cy, rg)) {
-                        okeys[off] = ((uint64_t)(cam.tile_base + cy * cam.tiles_x + cx) << 32) | depth;
-                        ovals[off] = val;
-                        ++off;
-                    }
-            }
         }
+    }
+    __syncthreads();
+    if (smem)
+        for (int k = threadIdx.x; k < ntiles; k += kPrepThreads)
+            if (sh[k]) atomicAdd(&tile_count[k], sh[k]);
+}
+
+// IdentifyFrustumRanges from the per-tile pair counts (one block): the
+// exclusive scan over tiles gives each tile's [start, end) in the tile-sorted
+// pairs.
+__global__ void __launch_bounds__(1024) k_tile_offsets(const uint32_t *__restrict__ tile_count, int ntiles,
+                                                       const uint32_t *__restrict__ misc, uint2 *__restrict__ tile_range) {
+    __shared__ uint32_t warp_tot[32];
+    if (misc[kMiscStatus] & kStatusCapacity) return;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int chunk = (ntiles + 1023) / 1024;
+    const int b = t * chunk, e = min(ntiles, b + chunk);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += tile_count[i];
+    uint32_t v = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_tot[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = v - s + (warp > 0 ? warp_tot[warp - 1] : 0u);
+    for (int i = b; i < e; ++i) {
+        const uint32_t c = tile_count[i];
+        tile_range[i] = make_uint2(run, run + c);
+        run += c;
     }
 }
 
@@ -494,24 +648,49 @@ cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g,
     k_preprocess<<<(unsigned)nblk, kPrepThreads, 0, s>>>(
         ws->d_cams, ws->n_cams, ws->d_tile_tab,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, g->mean,
-        g->scale, g->quat, g->opacity, g->sh, g->n, g->sh_degree, ws->d_rec,
-        ws->d_ranges, ws->d_count, ws->d_key, ws->d_blocksum, nblk);
+        g->scale, g->quat, g->opacity, g->sh, g->n, g->sh_degree, ws->d_rec, ws->d_ranges, ws->d_count, ws->d_key,
+        ws->d_blocksum, nblk);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_blocks(const geer_workspace *ws, cudaStream_t s) {
-    const int64_t m = prep_blocks(ws->n_gauss) * ws->n_cams;
-    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum, m, ws->d_misc, ws->d_hist, ws->d_tile_range, ws->n_tiles,
-                                     ws->cap_pairs);
+cudaError_t launch_bin_front(const geer_workspace *ws, cudaStream_t s) {
+    const int64_t nblk = prep_blocks(ws->n_gauss);
+    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum, nblk * ws->n_cams, ws->d_misc, ws->d_tile_range, ws->n_tiles,
+                                     ws->cap_pairs, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || nblk == 0) return e;
+    k_compact<<<(unsigned)nblk, kPrepThreads, 0, s>>>(ws->n_cams, ws->n_gauss, ws->d_count, ws->d_key,
+                                                      ws->d_blocksum, nblk, ws->d_ikey[0], ws->d_iid[0]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_pairs(const geer_workspace *ws, cudaStream_t s) {
+    const int64_t m = prep_blocks((int64_t)ws->n_cams * ws->n_gauss);
+    if (m == 0) {
+        k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum2, 0, ws->d_misc, ws->d_tile_range, 0, ws->cap_pairs, 1);
+        return cudaGetLastError();
+    }
+    k_gather_counts<<<(unsigned)m, kPrepThreads, 0, s>>>(ws->d_iid[ws->depth_buf], ws->d_count, ws->d_misc,
+                                                         ws->d_blocksum2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum2, m, ws->d_misc, ws->d_tile_range, 0, ws->cap_pairs, 1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
-    const int64_t nblk = prep_blocks(ws->n_gauss);
-    if (nblk == 0) return cudaSuccess;
-    k_duplicate<<<(unsigned)nblk, kPrepThreads, 0, s>>>(ws->d_cams, ws->n_cams, ws->d_tile_tab, ws->n_gauss,
-                                                        ws->d_ranges, ws->d_count, ws->d_key, ws->d_blocksum, nblk,
-                                                        ws->d_keys[0], ws->d_vals[0], ws->cap_pairs);
+    const int64_t m = prep_blocks((int64_t)ws->n_cams * ws->n_gauss);
+    uint32_t *tile_count = reinterpret_cast<uint32_t *>(ws->d_tile_range + ws->n_tiles);
+    if (m > 0) {
+        const size_t smem = ws->n_tiles <= kSmemTiles ? sizeof(uint32_t) * ws->n_tiles : 0;
+        k_duplicate<<<(unsigned)m, kPrepThreads, smem, s>>>(ws->d_cams, ws->d_tile_tab, ws->n_gauss,
+                                                            ws->d_iid[ws->depth_buf], ws->d_ranges, ws->d_count,
+                                                            ws->d_misc, ws->d_blocksum2, ws->d_keys[0], ws->d_vals[0],
+                                                            tile_count, (int)ws->n_tiles, ws->cap_pairs);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_tile_offsets<<<1, 1024, 0, s>>>(tile_count, (int)ws->n_tiles, ws->d_misc, ws->d_tile_range);
     return cudaGetLastError();
 }
 
