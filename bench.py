@@ -3,8 +3,9 @@
 Workload (the headline configuration): 1M Gaussians (means uniform in a 4 m cube
 3-7 m ahead, log-scales N(-2.5, 0.5), SH degree 3), Kannala-Brandt fisheye
 1280x960, 190 deg FoV, k_i ~ U[-0.05, 0.05], BEAP 16x16 tiles, seeded synthetic
-data. One step = preprocess (PBF association) + duplicate + radix sort + ranges +
-render of the whole frame, plus the backward when available.
+data. One step = preprocess (PBF association) + depth sort + duplicate + tile
+sort + render of the whole frame + L1 loss gradient against a seeded target +
+backward (render and preprocess stages) to all Gaussian parameters.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -164,18 +165,12 @@ def run(args):
     rgb = torch.empty((pixels, 3), dtype=torch.float32, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > 129 MB L2
     stream = torch.cuda.current_stream()
-    have_bwd = False
-    grads = None
-    try:
-        grads = {k: torch.zeros_like(v) for k, v in (("mean", g.mean), ("scale", g.scale), ("quat", g.quat),
-                                                     ("opacity", g.opacity), ("sh", g.sh))}
-        ws.render_fwd(rgb)
-        ws.render_bwd(g, torch.ones_like(rgb), grads)
-        torch.cuda.synchronize()
-        have_bwd = True
-    except geer.GeerError:
-        have_bwd = False
-    dL = torch.full_like(rgb, 1.0 / (3 * pixels))
+    grads = {k: torch.zeros_like(v) for k, v in (("mean", g.mean), ("scale", g.scale), ("quat", g.quat),
+                                                 ("opacity", g.opacity), ("sh", g.sh))}
+    have_bwd = not args.fwd_only
+    target = torch.as_tensor(wl.l1_target(cam, seed=3), device=dev).reshape(pixels, 3)
+    dL = torch.empty_like(rgb)
+    loss = torch.empty(1, device=dev)
 
     def step(ev):
         ev[0].record(stream)
@@ -186,6 +181,8 @@ def run(args):
         ws.render_fwd(rgb)
         ev[3].record(stream)
         if have_bwd:
+            # training-style step: L1 loss gradient, then the backward (gradients accumulate)
+            geer.l1_loss_grad(rgb, target, dL)
             ws.render_bwd(g, dL, grads)
         ev[4].record(stream)
 
@@ -224,6 +221,8 @@ def run(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * pixels * args.steps / (total_ms / 1e3) / 1e6
+    fwd_ms = [a + b + c for a, b, c in zip(prep_ms, sort_ms, rend_ms)]
+    fwd_value = pixels / (statistics.mean(fwd_ms) / 1e3) / 1e6
 
     # end to end through the C ABI with host buffers: H2D of the Gaussians from
     # pinned memory, the step, D2H of the image
@@ -244,6 +243,7 @@ def run(args):
         ws.bin_sort(sync=False)
         ws.render_fwd(rgb)
         if have_bwd:
+            geer.l1_loss_grad(rgb, target, dL)
             ws.render_bwd(g, dL, grads)
         out_host.copy_(rgb, non_blocking=True)
         e1.record(stream)
@@ -275,7 +275,7 @@ def run(args):
     tile_passes = math.ceil(max(1, math.ceil(math.log2(tiles))) / 8)
     # preprocess, scan, compact, 4 depth passes x 3, gather, scan, duplicate, tile offsets,
     # tile passes x 3, render
-    launches_per_step = 20 + 3 * tile_passes + (2 if have_bwd else 0)
+    launches_per_step = 20 + 3 * tile_passes + (3 if have_bwd else 0)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
@@ -285,6 +285,7 @@ def run(args):
                    "pass": "fwd+bwd" if have_bwd else "fwd", "gaussians": scene.n,
                    "pixels_per_gpu": pixels, "pairs": int(pairs), "parallelism": f"replicas x{world}",
                    "l2": "512 MB buffer written between timed steps (outside step events); inputs 236 MB > L2"},
+        "fwd_only": {"value": fwd_value, "unit": "Mpix/s", "ms": statistics.mean(fwd_ms)},
         "stages_ms": {"preprocess": statistics.mean(prep_ms), "bin_sort": statistics.mean(sort_ms),
                       "render_fwd": r_ms, "backward": statistics.mean(bwd_ms) if have_bwd else None},
         "roofline": {"bound": "alu", "kernel": "k_render_fwd", "achieved": achieved, "peak": fp32_peak,
@@ -314,6 +315,7 @@ def main():
     ap.add_argument("--impl", default="geer", choices=["geer", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fwd-only", action="store_true", help="time the forward render only")
     ap.add_argument("--ref-pixels", type=int, default=24)
     ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3],
                     help="3 = the headline configuration; 1, 2 = smaller cases for profiling")

@@ -40,7 +40,7 @@ typedef enum {
     GEER_ERR_ARG = 1,         /* invalid argument (null, negative size, bad camera, ...) */
     GEER_ERR_CAPACITY = 2,    /* more (tile, Gaussian) pairs than the workspace holds */
     GEER_ERR_CUDA = 3,        /* a CUDA runtime call failed */
-    GEER_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    GEER_ERR_TIMEOUT = 4,     /* reserved: this build has no device-side waits */
     GEER_ERR_UNSUPPORTED = 5, /* a valid request this build does not implement */
     GEER_ERR_STATE = 6        /* call out of order (e.g. render before bin_sort) */
 } geer_status;
@@ -158,9 +158,9 @@ geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void
 geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const float *dL_drgb, float *d_mean,
                             float *d_scale, float *d_quat, float *d_opacity, float *d_sh, void *stream);
 
-/* Synchronise `stream`, then read and clear the device status word: GEER_OK,
- * GEER_ERR_CAPACITY (pairs exceeded capacity) or GEER_ERR_TIMEOUT (a bounded
- * spin gave up). *pairs (may be NULL) receives the last pair count. */
+/* Synchronise `stream`, then read and clear the device status word: GEER_OK or
+ * GEER_ERR_CAPACITY (pairs exceeded capacity). *pairs (may be NULL) receives
+ * the last pair count. */
 geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *stream);
 
 /* Debug/inspection (synchronous): copy the per-(camera, Gaussian) preprocess
@@ -176,6 +176,13 @@ geer_status geer_debug_preprocess(geer_workspace *ws, uint16_t *ranges, uint32_t
  * values u32) into HOST buffers; *count receives the pair count. */
 geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *values, int64_t cap, int64_t *count,
                              void *stream);
+
+/* L1 photometric loss of a render against a target image (the training loss of
+ * Algorithm 2 instantiated as mean |C - target|): writes dL/drgb =
+ * sign(rgb - target) / n_values and, if loss is non-NULL, the loss (device
+ * float). rgb, target, dL_drgb: device [n_values] f32. */
+geer_status geer_l1_loss_grad(const float *rgb, const float *target, int64_t n_values, float *dL_drgb, float *loss,
+                              void *stream);
 
 /* Measurement (synchronous): totals over all rays of the last geer_render_fwd
  * of the ray-Gaussian evaluations executed (list entries walked up to early

@@ -553,6 +553,16 @@ geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *value
     return GEER_OK;
 }
 
+geer_status geer_l1_loss_grad(const float *rgb, const float *target, int64_t n_values, float *dL_drgb, float *loss,
+                              void *stream) {
+    if (n_values < 0 || (n_values > 0 && (!rgb || !target || !dL_drgb))) return GEER_ERR_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    return cuda_status(launch_l1_grad(rgb, target, n_values, dL_drgb, loss, sms, static_cast<cudaStream_t>(stream)));
+}
+
 geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t *applied, void *stream) {
     if (!ws || !evaluated || !applied) return GEER_ERR_ARG;
     if (ws->stage < 3) return GEER_ERR_STATE;

@@ -44,7 +44,7 @@ class ParamsC(C.Structure):
 EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "geer_workspace_init",
            "geer_workspace_destroy", "geer_set_cameras", "geer_preprocess", "geer_bin_sort", "geer_render_fwd",
            "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
-           "geer_render_counts"]
+           "geer_render_counts", "geer_l1_loss_grad"]
 
 _lib = None
 
@@ -81,6 +81,7 @@ def lib(build_if_missing: bool = True):
         "geer_debug_preprocess": [P, P, P, P, P, P],
         "geer_debug_pairs": [P, P, P, I64, P, P],
         "geer_render_counts": [P, P, P, P],
+        "geer_l1_loss_grad": [P, P, I64, P, P, P],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -272,6 +273,18 @@ class Workspace:
         return keys[:n], vals[:n]
 
 
+def l1_loss_grad(rgb: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None, stream=None):
+    """L1 loss mean|rgb - target| and its gradient, computed by the library kernel.
+    Returns (loss tensor [1] on the device, dL/drgb)."""
+    if grad is None:
+        grad = torch.empty_like(rgb)
+    loss = torch.empty(1, dtype=torch.float32, device=rgb.device)
+    _check(lib().geer_l1_loss_grad(C.c_void_p(rgb.data_ptr()), C.c_void_p(target.data_ptr()), rgb.numel(),
+                                   C.c_void_p(grad.data_ptr()), C.c_void_p(loss.data_ptr()), _stream(stream)),
+           "geer_l1_loss_grad")
+    return loss, grad
+
+
 class Renderer:
     """Forward renders of a camera batch, growing the pair capacity on demand."""
 
@@ -306,6 +319,14 @@ class Renderer:
         self.ws.render_fwd(rgb, T)
         return rgb
 
+    def backward(self, g: Gaussians, dL_drgb: torch.Tensor, grads: dict | None = None) -> dict:
+        """Gradients of the last forward (accumulated into grads if given)."""
+        if grads is None:
+            grads = {k: torch.zeros_like(v) for k, v in (("mean", g.mean), ("scale", g.scale), ("quat", g.quat),
+                                                         ("opacity", g.opacity), ("sh", g.sh))}
+        self.ws.render_bwd(g, dL_drgb.contiguous(), grads)
+        return grads
+
     def images(self, rgb: torch.Tensor):
         out, off = [], 0
         for c in self.cams:
@@ -313,3 +334,26 @@ class Renderer:
             out.append(rgb[off:off + n].view(c.height, c.width, 3))
             off += n
         return out
+
+
+class _RenderFn(torch.autograd.Function):
+    """rgb = render(mean, scale, quat, opacity, sh); backward through geer_render_bwd."""
+
+    @staticmethod
+    def forward(ctx, renderer, sh_degree, mean, scale, quat, opacity, sh):
+        g = Gaussians(mean.detach(), scale.detach(), quat.detach(), opacity.detach(), sh.detach(), sh_degree)
+        rgb = renderer.forward(g)
+        ctx.renderer, ctx.g = renderer, g
+        return rgb
+
+    @staticmethod
+    def backward(ctx, dL_drgb):
+        grads = ctx.renderer.backward(ctx.g, dL_drgb)
+        return None, None, grads["mean"], grads["scale"], grads["quat"], grads["opacity"], grads["sh"]
+
+
+def render(renderer: Renderer, mean, scale, quat, opacity, sh, sh_degree: int) -> torch.Tensor:
+    """Differentiable render of all cameras of `renderer`: [sum h*w, 3] f32.
+
+    Gradients flow to mean, scale, quat, opacity (activated) and sh."""
+    return _RenderFn.apply(renderer, int(sh_degree), mean, scale, quat, opacity, sh)
