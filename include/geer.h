@@ -153,8 +153,8 @@ geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void
  * given dL/drgb (same layout as rgb), ACCUMULATE (+=) the gradients of the
  * Gaussians used in the last forward into d_mean [n][3], d_scale [n][3],
  * d_quat [n][4], d_opacity [n], d_sh [n][(deg+1)^2][3] (device, caller-owned,
- * any of them may be NULL to skip). Must follow geer_render_fwd on the same
- * workspace with the same Gaussians. */
+ * any of them may be NULL to skip; d_sh 16-byte aligned). Must follow
+ * geer_render_fwd on the same workspace with the same Gaussians. */
 geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const float *dL_drgb, float *d_mean,
                             float *d_scale, float *d_quat, float *d_opacity, float *d_sh, void *stream);
 

@@ -86,10 +86,14 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(
     R[3] = 2.0f * (x * y + w * z);        R[4] = 1.0f - 2.0f * (x * x + z * z); R[5] = 2.0f * (y * z - w * x);
     R[6] = 2.0f * (x * z - w * y);        R[7] = 2.0f * (y * z + w * x);        R[8] = 1.0f - 2.0f * (x * x + y * y);
     float dmu[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, dsig = 0.0f;
-    float dsh[48];
+    float dsh[48], shc[48];
+    const int nc = 3 * nb;
+    const float *shg = sh + (int64_t)g * nc;
 #pragma unroll
-    for (int k = 0; k < 48; ++k) dsh[k] = 0.0f;
-    const float *shg = sh + (int64_t)g * 3 * nb;
+    for (int k = 0; k < 48; ++k) {
+        dsh[k] = 0.0f;
+        shc[k] = k < nc ? shg[k] : 0.0f;
+    }
 
     for (int ci = 0; ci < ncams; ++ci) {
         const int64_t idx = (int64_t)ci * n + g;
@@ -148,20 +152,25 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             float raw = 0.5f;
-            for (int k = 0; k < nb; ++k) raw += Y[k] * shg[3 * k + ch];
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < nb) raw += Y[k] * shc[3 * k + ch];
             dLdc[ch] = raw > 0.0f ? acc[1 + ch] : 0.0f;
         }
         float ddir[3] = {0, 0, 0};
-        for (int k = 0; k < nb; ++k) {
-            float wk = 0.0f;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                dsh[3 * k + ch] += dLdc[ch] * Y[k];
-                wk += dLdc[ch] * shg[3 * k + ch];
+        for (int k = 0; k < 16; ++k) {
+            if (k < nb) {
+                float wk = 0.0f;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    dsh[3 * k + ch] += dLdc[ch] * Y[k];
+                    wk += dLdc[ch] * shc[3 * k + ch];
+                }
+                ddir[0] += wk * dY[k][0];
+                ddir[1] += wk * dY[k][1];
+                ddir[2] += wk * dY[k][2];
             }
-            ddir[0] += wk * dY[k][0];
-            ddir[1] += wk * dY[k][1];
-            ddir[2] += wk * dY[k][2];
         }
         const float dp = ddir[0] * ux + ddir[1] * uy + ddir[2] * uz;
         dmu[0] += (ddir[0] - ux * dp) / vn;
@@ -190,8 +199,23 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(
 #pragma unroll
         for (int a = 0; a < 3; ++a) d_scale[3 * g + a] += ds[a];
     if (d_opacity) d_opacity[g] += dsig;
-    if (d_sh)
-        for (int k = 0; k < 3 * nb; ++k) d_sh[(int64_t)g * 3 * nb + k] += dsh[k];
+    if (d_sh) {
+        float *dst = d_sh + (int64_t)g * nc;
+        if ((nc & 3) == 0) {
+            float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+            for (int i = 0; i < 12; ++i)
+                if (4 * i < nc) {
+                    float4 v = d4[i];
+                    v.x += dsh[4 * i]; v.y += dsh[4 * i + 1]; v.z += dsh[4 * i + 2]; v.w += dsh[4 * i + 3];
+                    d4[i] = v;
+                }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 48; ++k)
+                if (k < nc) dst[k] += dsh[k];
+        }
+    }
 }
 
 // L1 loss mean |C - target| over all values and its gradient sign(C - target)/m.

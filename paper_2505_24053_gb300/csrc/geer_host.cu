@@ -470,6 +470,7 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
     geer_status st = check_gaussians(ws, g);
     if (st != GEER_OK) return st;
     if (g->n != ws->n_gauss || g->sh_degree != ws->sh_degree) return GEER_ERR_ARG;
+    if (d_sh && (reinterpret_cast<uintptr_t>(d_sh) & 15)) return GEER_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_render_bwd(ws, dL_drgb, s);
     if (e != cudaSuccess) return GEER_ERR_CUDA;
