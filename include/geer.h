@@ -189,6 +189,32 @@ geer_status geer_l1_loss_grad(const float *rgb, const float *target, int64_t n_v
  * termination) and of the contributors composited. */
 geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t *applied, void *stream);
 
+/* Render one small camera without allocating anything.
+ *
+ * For callers that cannot call cudaMalloc or any other allocator at render
+ * time: code running while a CUDA stream is being captured, plugins whose host
+ * application owns all device memory, and latency-critical loops that must not
+ * synchronise with an allocator. This entry point takes no workspace: every
+ * piece of device scratch it needs lives in one fixed array inside the library
+ * (28 MiB per GPU that loads the library, held until the process exits), and
+ * its host-side state is static too. No paper counterpart: it is a packaging
+ * of geer_preprocess + geer_bin_sort + geer_render_fwd for one camera.
+ *
+ * Limits: n <= 32768 Gaussians, width * height <= 262144 rays,
+ * ceil(w/16) * ceil(h/16) <= 2048 tiles, w + h <= 8192, at most 2^20 (tile,
+ * Gaussian) pairs. Larger requests return GEER_ERR_CAPACITY and render nothing.
+ * Inputs and outputs as for geer_preprocess / geer_render_fwd (rgb [h*w][3],
+ * T_final [h*w] or NULL, device, caller-owned). params may be NULL (defaults).
+ *
+ * The first call on a device sets that device up (it looks up the address of the
+ * scratch array with that device current); make that first call before any
+ * stream capture. Each call synchronises `stream` once, to check the pair count.
+ * All calls on a device share the one scratch array, which keeps the last
+ * call's contents: calls that overlap on the GPU (different streams, or host
+ * threads) race and corrupt each other's results; serialise them. */
+geer_status geer_render_noalloc(const geer_gaussians *g, const geer_camera *cam, const geer_params *params,
+                                float *rgb, float *T_final, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -584,3 +584,198 @@ geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free render of one small camera (geer_render_noalloc).
+//
+// All device scratch lives in the file-scope array g_noalloc_scratch below;
+// every GPU that loads the library holds it until the process exits. Host code
+// sees only a host-side stand-in for the symbol, so the device address is
+// taken once per device with cudaGetSymbolAddress (with that device current)
+// and handed to the kernels. Host-side state is static as well: no heap,
+// no cudaMalloc/cudaMallocHost/cudaFree.
+namespace {
+
+constexpr int64_t kNoAllocMaxGauss = 32768;
+constexpr int64_t kNoAllocMaxPixels = 512 * 512;
+constexpr int64_t kNoAllocMaxPairs = int64_t(1) << 20;
+constexpr int64_t kNoAllocMaxTileTab = 2 * 1024;   // tile columns + rows
+constexpr int64_t kNoAllocMaxPixTab = 8 * 1024;    // pixel columns + rows
+constexpr int64_t kNoAllocMaxTiles = 2 * 1024;
+constexpr size_t kNoAllocBytes = size_t(28) << 20;  // 28 MiB, checked against the layout at set-up
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocState {
+    bool ready;
+    char *base;  // device address of g_noalloc_scratch on this device
+    int num_sms;
+    geer_workspace ws;
+    DevCam cam;
+    float4 ttab[kNoAllocMaxTileTab];
+    float2 ptab[kNoAllocMaxPixTab];
+};
+NoAllocState g_noalloc[kNoAllocMaxDevices];
+
+// The per-camera tables of build_tables, for one camera, into fixed arrays.
+bool noalloc_tables(const geer_camera &c, NoAllocState &st, int64_t &ntt, int64_t &npt) {
+    DevCam &d = st.cam;
+    memset(&d, 0, sizeof(d));
+    d.width = c.width;
+    d.height = c.height;
+    d.tiles_x = (int)ceil_div(c.width, kTile);
+    d.tiles_y = (int)ceil_div(c.height, kTile);
+    ntt = (int64_t)d.tiles_x + d.tiles_y;
+    npt = (int64_t)c.width + c.height;
+    if (ntt > kNoAllocMaxTileTab || npt > kNoAllocMaxPixTab || (int64_t)d.tiles_x * d.tiles_y > kNoAllocMaxTiles)
+        return false;
+    const double fx = c.fov_x, fy = derived_fov_y(c);
+    d.tcol_off = 0;
+    for (int tx = 0; tx < d.tiles_x; ++tx) {
+        const int i0 = tx * kTile, i1 = std::min(i0 + kTile - 1, c.width - 1);
+        float4 v = make_float4((float)tan(0.5 * beap_angle(i0, c.width, fx)),
+                               (float)tan(0.5 * beap_angle(i1, c.width, fx)), 0.0f, 0.0f);
+        for (int i = i0; i <= i1; ++i) {
+            const double cs = cos(beap_angle(i, c.width, fx));
+            if (cs > -1e-12) v.z = 1.0f;
+            if (cs < 1e-12) { v.w = 1.0f; d.any_col_flip = 1; }
+        }
+        st.ttab[tx] = v;
+    }
+    d.trow_off = d.tiles_x;
+    for (int ty = 0; ty < d.tiles_y; ++ty) {
+        const int j0 = ty * kTile, j1 = std::min(j0 + kTile - 1, c.height - 1);
+        float4 v = make_float4((float)tan(0.5 * beap_angle(j0, c.height, fy)),
+                               (float)tan(0.5 * beap_angle(j1, c.height, fy)), 0.0f, 0.0f);
+        for (int j = j0; j <= j1; ++j) {
+            const double cs = cos(beap_angle(j, c.height, fy));
+            if (cs > -1e-12) v.z = 1.0f;
+            if (cs < 1e-12) { v.w = 1.0f; d.any_row_flip = 1; }
+        }
+        st.ttab[d.tiles_x + ty] = v;
+    }
+    d.pcol_off = 0;
+    for (int i = 0; i < c.width; ++i) {
+        const double a = beap_angle(i, c.width, fx);
+        st.ptab[i] = make_float2((float)sin(a), (float)cos(a));
+    }
+    d.prow_off = c.width;
+    for (int j = 0; j < c.height; ++j) {
+        const double a = beap_angle(j, c.height, fy);
+        st.ptab[c.width + j] = make_float2((float)sin(a), (float)cos(a));
+    }
+    d.c0lo = d.tiles_x; d.c0hi = 0;
+    for (int tx = 0; tx < d.tiles_x; ++tx) {
+        const float4 v = st.ttab[tx];
+        if (v.z != 0.0f && v.w == 0.0f) { d.c0lo = std::min(d.c0lo, tx); d.c0hi = tx + 1; }
+    }
+    d.r0lo = d.tiles_y; d.r0hi = 0;
+    for (int ty = 0; ty < d.tiles_y; ++ty) {
+        const float4 v = st.ttab[d.tiles_x + ty];
+        if (v.z != 0.0f && v.w == 0.0f) { d.r0lo = std::min(d.r0lo, ty); d.r0hi = ty + 1; }
+    }
+    for (int k = 0; k < 9; ++k) d.R[k] = c.R_cw[k];
+    for (int k = 0; k < 3; ++k) {
+        d.t[k] = c.t_cw[k];
+        d.bg[k] = c.bg[k];
+        double o = 0.0;
+        for (int b = 0; b < 3; ++b) o -= (double)c.R_cw[3 * b + k] * (double)c.t_cw[b];
+        d.o[k] = (float)o;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" geer_status geer_render_noalloc(const geer_gaussians *g, const geer_camera *cam, const geer_params *params,
+                                           float *rgb, float *T_final, void *stream) {
+    if (!g || !cam || !rgb) return GEER_ERR_ARG;
+    geer_params pd;
+    geer_default_params(&pd);
+    if (!params) params = &pd;
+    geer_status st = check_params(params);
+    if (st != GEER_OK) return st;
+    if (!camera_ok(*cam)) return GEER_ERR_ARG;
+    if (g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3) return GEER_ERR_ARG;
+    if (g->n > 0 && (!g->mean || !g->scale || !g->quat || !g->opacity || !g->sh)) return GEER_ERR_ARG;
+    if (g->n > 0 && (reinterpret_cast<uintptr_t>(g->sh) & 15)) return GEER_ERR_ARG;
+    if (g->n > kNoAllocMaxGauss || (int64_t)cam->width * cam->height > kNoAllocMaxPixels) return GEER_ERR_CAPACITY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GEER_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return GEER_ERR_UNSUPPORTED;
+    NoAllocState &S = g_noalloc[dev];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!S.ready) {
+        // once per device, with the device current: the device address of the scratch array
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return GEER_ERR_CUDA;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GEER_ERR_CUDA;
+        S.base = static_cast<char *>(ptr);
+        S.num_sms = sms;
+        S.ready = true;
+    }
+    int64_t ntt = 0, npt = 0;
+    if (!noalloc_tables(*cam, S, ntt, npt)) return GEER_ERR_CAPACITY;
+    // lay the workspace out in the scratch array for the fixed maxima
+    Caps c;
+    c.cams = 1;
+    c.pixels = kNoAllocMaxPixels;
+    c.tiles = kNoAllocMaxTiles;
+    c.tile_tab = kNoAllocMaxTileTab;
+    c.pix_tab = kNoAllocMaxPixTab;
+    c.gauss = kNoAllocMaxGauss;
+    c.pairs = kNoAllocMaxPairs;
+    c.sort_tiles = ceil_div(std::max<int64_t>(c.pairs, c.gauss), kSortTile) + 1;
+    c.prep_blocks = prep_blocks(c.gauss);
+    if (layout(c, nullptr, nullptr) > kNoAllocBytes) return GEER_ERR_UNSUPPORTED;
+    geer_workspace &ws = S.ws;
+    memset(&ws, 0, sizeof(ws));
+    layout(c, S.base, &ws);
+    ws.cap_cams = 1;
+    ws.cap_pixels = c.pixels;
+    ws.cap_tiles = c.tiles;
+    ws.cap_tile_tab = c.tile_tab;
+    ws.cap_pix_tab = c.pix_tab;
+    ws.cap_gauss = kNoAllocMaxGauss;
+    ws.cap_pairs = kNoAllocMaxPairs;
+    ws.cap_sh_degree = 3;
+    ws.cap_sort_tiles = c.sort_tiles;
+    ws.params = Params{params->alpha_min, params->T_min, params->alpha_max, params->lambda_pad};
+    ws.num_sms = S.num_sms;
+    ws.sort_grid = S.num_sms * sort_blocks_per_sm();
+    ws.n_cams = 1;
+    ws.n_pixels = (int64_t)cam->width * cam->height;
+    ws.n_tiles = (int64_t)S.cam.tiles_x * S.cam.tiles_y;
+    ws.cams[0] = S.cam;
+    int bits = 1;
+    while ((int64_t(1) << bits) < ws.n_tiles) ++bits;
+    ws.tile_bits = bits;
+    ws.n_tile_passes = (bits + kRadixBits - 1) / kRadixBits;
+    ws.n_gauss = g->n;
+    ws.sh_degree = g->sh_degree;
+    // the array keeps the previous call's contents: clear what must start at zero
+    // and upload this camera's tables (from static host buffers)
+    if (cudaMemsetAsync(ws.d_misc, 0, sizeof(uint32_t) * kMiscCount, s) != cudaSuccess ||
+        cudaMemsetAsync(ws.d_group_sum, 0, sizeof(uint32_t) * kRadix * (ceil_div(c.sort_tiles, kGroupTiles) + 1),
+                        s) != cudaSuccess ||
+        cudaMemcpyAsync(ws.d_cams, &S.cam, sizeof(DevCam), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws.d_tile_tab, S.ttab, sizeof(float4) * ntt, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws.d_pix_tab, S.ptab, sizeof(float2) * npt, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    if (launch_preprocess(&ws, g, s) != cudaSuccess || launch_bin_front(&ws, s) != cudaSuccess ||
+        launch_depth_sort(&ws, s) != cudaSuccess || launch_count_pairs(&ws, s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    static uint32_t h_misc[kNoAllocMaxDevices][kMiscCount];
+    if (cudaMemcpyAsync(h_misc[dev], ws.d_misc, sizeof(uint32_t) * kMiscCount, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    if (h_misc[dev][kMiscPairsHi] != 0 || (int64_t)h_misc[dev][kMiscTotalLo] > kNoAllocMaxPairs)
+        return GEER_ERR_CAPACITY;
+    if (launch_duplicate(&ws, s) != cudaSuccess || launch_tile_sort(&ws, s) != cudaSuccess ||
+        launch_render_fwd(&ws, rgb, T_final, s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    return GEER_OK;
+}

@@ -44,7 +44,7 @@ class ParamsC(C.Structure):
 EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "geer_workspace_init",
            "geer_workspace_destroy", "geer_set_cameras", "geer_preprocess", "geer_bin_sort", "geer_render_fwd",
            "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
-           "geer_render_counts", "geer_l1_loss_grad"]
+           "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc"]
 
 _lib = None
 
@@ -82,6 +82,7 @@ def lib(build_if_missing: bool = True):
         "geer_debug_pairs": [P, P, P, I64, P, P],
         "geer_render_counts": [P, P, P, P],
         "geer_l1_loss_grad": [P, P, I64, P, P, P],
+        "geer_render_noalloc": [P, P, P, P, P, P],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
