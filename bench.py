@@ -140,6 +140,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, dev):
+    """Workload 4: 2M-Gaussian resident scene, Poisson request stream (pinhole
+    1920x1080 70 deg / equidistant 1280x1280 200 deg / Kannala-Brandt 640x480
+    150 deg, random poses within 1 m), served with continuous batching (camera
+    slots, two buffers, captured CUDA graphs) and, on the same trace, one request
+    at a time (FIFO, one slot, one buffer)."""
+    import torch
+
+    from paper_2505_24053_gb300 import geer, serve
+    from paper_2505_24053_gb300 import workloads as wl
+
+    scene = wl.config_scene(4)
+    g = geer.Gaussians.from_scene(scene)
+    n_req = int(round(args.serving_rate * args.serving_seconds))
+    trace = wl.serving_requests(n_req, seed=4, rate_hz=args.serving_rate)
+    models = [k[0] for k in wl.SERVING_KINDS]
+
+    def requests():
+        return [serve.Request(i, t, c, kind=models.index(c.model)) for i, (t, c) in enumerate(trace)]
+
+    warm = args.serving_warmup
+    out = {"trace": f"Poisson {args.serving_rate:g} req/s, {n_req} requests over {args.serving_seconds:g} s "
+                    f"(first {warm:g} s excluded), equal mix of pinhole 1920x1080 70deg, equidistant 1280x1280 "
+                    f"200deg, Kannala-Brandt 640x480 150deg; 2M Gaussians resident"}
+    for name, slots, bufs, cap in (("batched", 4, 2, 700_000_000), ("one_at_a_time", 1, 1, 400_000_000)):
+        eng = serve.Engine(g, n_slots=slots, n_buffers=bufs, pair_capacity=cap)
+        eng.calibrate(requests()[:24])
+        eng.prepare()
+        reqs = requests()
+        done = eng.run(reqs)
+        keep = [r for r in done if r.arrival >= warm]
+        st = serve.summarize(keep, max(1e-9, args.serving_seconds - warm))
+        st.update({"slots": slots, "buffers": bufs, "graphs": True, "failed": len(eng.failed)})
+        out[name] = st
+        del eng
+        torch.cuda.empty_cache()
+    return out
+
+
 def run(args):
     import torch
     import torch.distributed as dist
@@ -299,6 +338,8 @@ def run(args):
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,
     }
+    if args.serving_seconds > 0 and world == 1:
+        line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _oracle_sample(scene, cam, args.cpu_seconds)
     if rank == 0:
@@ -310,12 +351,15 @@ def run(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="geer", choices=["geer", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fwd-only", action="store_true", help="time the forward render only")
+    ap.add_argument("--serving-seconds", type=float, default=8.0, help="serving trace length (0: skip)")
+    ap.add_argument("--serving-warmup", type=float, default=1.0)
+    ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--ref-pixels", type=int, default=24)
     ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3],
                     help="3 = the headline configuration; 1, 2 = smaller cases for profiling")

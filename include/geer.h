@@ -122,6 +122,17 @@ geer_status geer_workspace_destroy(geer_workspace *ws);
  * asynchronously on `stream`; the call returns once they are staged. */
 geer_status geer_set_cameras(geer_workspace *ws, const geer_camera *cams, int32_t n_cams, void *stream);
 
+/* Like geer_set_cameras, but camera i is placed at a fixed slot: its tiles start
+ * at global tile i * slot_tiles and its pixels at i * slot_pixels of the batched
+ * image (rgb and T_final then hold n_slots * slot_pixels rows; rows beyond a
+ * camera's w*h are left untouched). active[i] == 0 (active may be NULL = all
+ * active) leaves slot i empty: no tiles, no pairs, nothing rendered. With a
+ * fixed slot layout every launch of a step has the same configuration, so a
+ * step can be captured once in a CUDA graph and replayed with new cameras.
+ * Each active camera must fit its slot (tiles and pixels). */
+geer_status geer_set_camera_slots(geer_workspace *ws, const geer_camera *cams, int32_t n_slots, const uint8_t *active,
+                                  int64_t slot_tiles, int64_t slot_pixels, void *stream);
+
 /* Preprocess (Algorithm 1: CullGaussian, ViewspaceGaussians, PBF_Intersect,
  * PCA_Whitening; Sec. 3.2, App. D): for every (camera, Gaussian) the cull
  * decision, the depth key |mu_c|, the PBF tile ranges, the tile count, the

@@ -85,12 +85,29 @@ struct CamTables {
 // Per camera: tile-column/-row half-angle spans tan(angle/2) of the first and
 // last ray of the tile with flags for cos(angle) >= 0 / <= 0 (rays beyond 90 deg
 // flip the other dihedral angle by pi), per-pixel sin/cos of theta and phi.
-void build_tables(const geer_camera *cams, int n, CamTables &out) {
+void build_tables(const geer_camera *cams, int n, CamTables &out, const uint8_t *active = nullptr,
+                  int64_t slot_tiles = 0, int64_t slot_pixels = 0) {
     out = CamTables();
     for (int ci = 0; ci < n; ++ci) {
         const geer_camera &c = cams[ci];
         DevCam d;
         memset(&d, 0, sizeof(d));
+        if (slot_tiles > 0) {
+            // fixed slot placement: camera ci owns tiles [ci * slot_tiles, ...) and
+            // pixels [ci * slot_pixels, ...); an inactive slot has no tiles at all
+            out.tiles = (int64_t)ci * slot_tiles;
+            out.pixels = (int64_t)ci * slot_pixels;
+            if (active && !active[ci]) {
+                d.tile_base = (int32_t)out.tiles;
+                d.pix_base = out.pixels;
+                d.tcol_off = d.trow_off = (int32_t)out.ttab.size();
+                d.pcol_off = d.prow_off = (int32_t)out.ptab.size();
+                out.cams.push_back(d);
+                out.tiles = (int64_t)(ci + 1) * slot_tiles;
+                out.pixels = (int64_t)(ci + 1) * slot_pixels;
+                continue;
+            }
+        }
         d.width = c.width;
         d.height = c.height;
         d.tiles_x = (int)ceil_div(c.width, kTile);
@@ -160,6 +177,10 @@ void build_tables(const geer_camera *cams, int n, CamTables &out) {
         out.cams.push_back(d);
         out.tiles += (int64_t)d.tiles_x * d.tiles_y;
         out.pixels += (int64_t)c.width * c.height;
+        if (slot_tiles > 0) {
+            out.tiles = (int64_t)(ci + 1) * slot_tiles;
+            out.pixels = (int64_t)(ci + 1) * slot_pixels;
+        }
     }
 }
 
@@ -408,6 +429,24 @@ geer_status geer_set_cameras(geer_workspace *ws, const geer_camera *cams, int32_
     if (n_cams > ws->cap_cams) return GEER_ERR_ARG;
     CamTables t;
     build_tables(cams, n_cams, t);
+    if (t.pixels > ws->cap_pixels || t.tiles > ws->cap_tiles || (int64_t)t.ttab.size() > ws->cap_tile_tab ||
+        (int64_t)t.ptab.size() > ws->cap_pix_tab)
+        return GEER_ERR_ARG;
+    return upload_cams(ws, t, static_cast<cudaStream_t>(stream));
+}
+
+geer_status geer_set_camera_slots(geer_workspace *ws, const geer_camera *cams, int32_t n_slots, const uint8_t *active,
+                                  int64_t slot_tiles, int64_t slot_pixels, void *stream) {
+    if (!ws || !cams || n_slots <= 0 || n_slots > ws->cap_cams || slot_tiles <= 0 || slot_pixels <= 0)
+        return GEER_ERR_ARG;
+    for (int i = 0; i < n_slots; ++i) {
+        if (active && !active[i]) continue;
+        if (!camera_ok(cams[i])) return GEER_ERR_ARG;
+        const int64_t tiles = ceil_div(cams[i].width, kTile) * ceil_div(cams[i].height, kTile);
+        if (tiles > slot_tiles || (int64_t)cams[i].width * cams[i].height > slot_pixels) return GEER_ERR_ARG;
+    }
+    CamTables t;
+    build_tables(cams, n_slots, t, active, slot_tiles, slot_pixels);
     if (t.pixels > ws->cap_pixels || t.tiles > ws->cap_tiles || (int64_t)t.ttab.size() > ws->cap_tile_tab ||
         (int64_t)t.ptab.size() > ws->cap_pix_tab)
         return GEER_ERR_ARG;

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
     __syncthreads();
     const DevCam &cam = cams[s_cam];
     const int lt = t - cam.tile_base;
+    if (lt >= cam.tiles_x * cam.tiles_y) return;  // padding tile of a camera slot
     const int cx = lt % cam.tiles_x, cy = lt / cam.tiles_x;
     const int x = cx * kTile + (tid & (kTile - 1));
     const int y = cy * kTile + (tid / kTile);
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_bwd(const DevCam *__restric
     __syncthreads();
     const DevCam &cam = cams[s_cam];
     const int lt = t - cam.tile_base;
+    if (lt >= cam.tiles_x * cam.tiles_y) return;  // padding tile of a camera slot
     const int cx = lt % cam.tiles_x, cy = lt / cam.tiles_x;
     const int x = cx * kTile + (tid & (kTile - 1));
     const int y = cy * kTile + (tid / kTile);

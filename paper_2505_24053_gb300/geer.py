@@ -44,7 +44,7 @@ class ParamsC(C.Structure):
 EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "geer_workspace_init",
            "geer_workspace_destroy", "geer_set_cameras", "geer_preprocess", "geer_bin_sort", "geer_render_fwd",
            "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
-           "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc"]
+           "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc", "geer_set_camera_slots"]
 
 _lib = None
 
@@ -83,6 +83,7 @@ def lib(build_if_missing: bool = True):
         "geer_render_counts": [P, P, P, P],
         "geer_l1_loss_grad": [P, P, I64, P, P, P],
         "geer_render_noalloc": [P, P, P, P, P, P],
+        "geer_set_camera_slots": [P, P, I32, P, I64, I64, P],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -205,6 +206,15 @@ class Workspace:
         _check(lib().geer_set_cameras(self._handle, self._cams_c, len(self.cams), _stream(stream)),
                "geer_set_cameras")
         self.pixels = sum(c.width * c.height for c in self.cams)
+
+    def set_camera_slots(self, cams, active, slot_tiles: int, slot_pixels: int, stream=None):
+        """Place camera i at fixed slot i (see geer_set_camera_slots); active: list of bools."""
+        arr = cameras_c(cams)
+        act = (C.c_uint8 * len(cams))(*[1 if a else 0 for a in active])
+        _check(lib().geer_set_camera_slots(self._handle, arr, len(cams), act, int(slot_tiles), int(slot_pixels),
+                                           _stream(stream)), "geer_set_camera_slots")
+        self.cams = list(cams)
+        self._slots = (list(active), int(slot_tiles), int(slot_pixels))
 
     def preprocess(self, g: Gaussians, stream=None):
         self._g = g

@@ -1,0 +1,269 @@
+"""Continuous-batching render server over the geer C ABI.
+
+A scene stays resident on the device. Requests (a camera each: pinhole, equidistant
+or Kannala-Brandt, any pose) arrive over time. Each GPU buffer is a workspace with
+a fixed slot layout (geer_set_camera_slots): every launch of a step depends only
+on the number of occupied slots k, so the step (preprocess -> bin/sort ->
+render) is captured once per k in a CUDA graph per buffer and replayed with the
+cameras of the admitted requests. With two or more buffers on their own streams, requests that arrive
+while a batch is on the GPU are admitted into the next free buffer and their
+work overlaps on the device.
+
+Admission is by slots and by memory: each request kind carries an estimate of
+its (tile, Gaussian) pairs (calibrated by rendering it alone), and a batch takes
+requests first come, first served while the estimates fit the buffer's pair
+capacity. A batch that overflows anyway (the device status says so) is split and
+its requests go back to the head of the queue.
+
+Latency = request arrival -> completion event of its batch, measured with CUDA
+events against a start event recorded when the trace starts.
+"""
+from __future__ import annotations
+
+import math
+import statistics
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import geer
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the trace start
+    camera: object          # workloads.Camera
+    kind: int = 0
+    done_ms: float | None = None   # completion time, ms after the trace start
+    batch: int = -1
+    image: object = None
+    error: str | None = None
+
+    @property
+    def latency_ms(self) -> float | None:
+        return None if self.done_ms is None else self.done_ms - 1e3 * self.arrival
+
+
+@dataclass
+class Scheduler:
+    """First come, first served admission by free slots and estimated pair memory."""
+
+    n_slots: int
+    pair_budget: int
+    estimates: dict = field(default_factory=dict)   # kind -> estimated pairs
+    default_estimate: int = 1
+
+    def estimate(self, req: Request) -> int:
+        return int(self.estimates.get(req.kind, self.default_estimate))
+
+    def admit(self, queue: deque) -> list:
+        batch, used = [], 0
+        while queue and len(batch) < self.n_slots:
+            e = self.estimate(queue[0])
+            if batch and used + e > self.pair_budget:
+                break
+            batch.append(queue.popleft())
+            used += e
+        return batch
+
+    def observe(self, req: Request, pairs: int):
+        """Raise the estimate of a kind when a request needed more pairs."""
+        self.estimates[req.kind] = max(self.estimate(req), int(pairs * 1.25))
+
+
+class _Buffer:
+    def __init__(self, idx, engine):
+        import torch
+        self.idx = idx
+        self.engine = engine
+        self.stream = torch.cuda.Stream()
+        cap_cam = engine.capacity_camera
+        self.ws = geer.Workspace([cap_cam] * engine.n_slots, engine.g.n, engine.g.sh_degree, engine.pair_capacity)
+        self.rgb = torch.zeros((engine.n_slots * engine.slot_pixels, 3), dtype=torch.float32, device="cuda")
+        self.graph = False
+        self.graphs = {}
+        self.done = None
+        self.batch = []
+        self.batch_id = -1
+
+    def load(self, reqs):
+        """Cameras of a batch into slots 0..len(reqs)-1 (the step's shape is the batch size)."""
+        cams = [r.camera for r in reqs] if reqs else [self.engine.capacity_camera]
+        self.ws.set_camera_slots(cams, [True] * len(cams), self.engine.slot_tiles, self.engine.slot_pixels,
+                                 stream=self.stream)
+
+    def step_body(self):
+        self.ws.preprocess(self.engine.g, stream=self.stream)
+        self.ws.bin_sort(sync=False, stream=self.stream)
+        self.ws.render_fwd(self.rgb, None, stream=self.stream)
+
+    def capture(self):
+        """One graph per batch size k = 1..n_slots: every launch configuration of a
+        step depends only on k, so each is captured once and replayed."""
+        import torch
+        self.graphs = {}
+        from . import workloads as wl
+        small = wl.Camera(wl.PINHOLE, 64, 64, math.radians(60))  # launch shapes do not depend on it
+        for k in range(1, self.engine.n_slots + 1):
+            dummy = [Request(-1, 0.0, small)] * k
+            self.load(dummy)
+            self.step_body()  # warm the path outside capture
+            self.stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=self.stream):
+                self.step_body()
+            self.graphs[k] = g
+        self.graph = True
+
+    def launch(self, reqs, batch_id):
+        import torch
+        self.load(reqs)
+        with torch.cuda.stream(self.stream):
+            if self.graph:
+                self.graphs[len(reqs)].replay()
+            else:
+                self.step_body()
+            self.done = torch.cuda.Event(enable_timing=True)
+            self.done.record(self.stream)
+        self.batch = list(reqs)
+        self.batch_id = batch_id
+
+    def busy(self) -> bool:
+        return self.done is not None and not self.done.query()
+
+
+class Engine:
+    """Serving engine: n_buffers workspaces x n_slots camera slots each."""
+
+    def __init__(self, gaussians: geer.Gaussians, n_slots: int = 4, n_buffers: int = 2,
+                 pair_capacity: int = 200_000_000, max_width: int = 1920, max_height: int = 1280,
+                 use_graphs: bool = True):
+        from . import workloads as wl
+        self.g = gaussians
+        self.n_slots, self.n_buffers = n_slots, n_buffers
+        self.pair_capacity = pair_capacity
+        self.capacity_camera = wl.Camera(wl.PINHOLE, max_width, max_height, math.radians(60))
+        self.slot_tiles = math.ceil(max_width / 16) * math.ceil(max_height / 16)
+        self.slot_pixels = max_width * max_height
+        self.scheduler = Scheduler(n_slots, int(pair_capacity * 0.9))
+        self.buffers = [_Buffer(i, self) for i in range(n_buffers)]
+        self.use_graphs = use_graphs
+        self.failed: list = []
+
+    def calibrate(self, sample_requests, margin: float = 1.25):
+        """Pairs per request kind, from rendering each sample alone (synchronous)."""
+        buf = self.buffers[0]
+        for r in sample_requests:
+            buf.load([r])
+            buf.ws.preprocess(self.g, stream=buf.stream)
+            try:
+                need = buf.ws.bin_sort(sync=True, stream=buf.stream)
+            except geer.GeerError as e:
+                if e.status != geer.ERR_CAPACITY:
+                    raise
+                need = buf.ws.last_pairs
+            self.scheduler.observe(r, int(need * margin / 1.25))
+        buf.stream.synchronize()
+
+    def prepare(self):
+        for b in self.buffers:
+            b.load([])
+            if self.use_graphs:
+                b.capture()
+            else:
+                b.step_body()
+            b.stream.synchronize()
+            # the warm-up steps may have overflowed the pair capacity: read and clear
+            # the device status so the first real batch does not inherit it
+            b.ws.device_status(stream=b.stream)
+
+    def _slot_view(self, buf, k, cam):
+        n = cam.width * cam.height
+        off = k * self.slot_pixels
+        return buf.rgb[off:off + n].view(cam.height, cam.width, 3)
+
+    def _complete(self, buf, t0, keep_images, out_done):
+        import torch
+        st, pairs = buf.ws.device_status(stream=buf.stream)
+        t_ms = t0.elapsed_time(buf.done)
+        if st == geer.ERR_CAPACITY and len(buf.batch) == 1:
+            # a single request beyond the pair capacity can never be served here
+            buf.batch[0].error = "pair capacity exceeded"
+            self.failed.append(buf.batch[0])
+            requeue = []
+        elif st == geer.ERR_CAPACITY:
+            # split and retry the batch: back to the head of the queue, estimates raised
+            for r in buf.batch:
+                self.scheduler.observe(r, max(pairs // max(1, len(buf.batch)), self.scheduler.estimate(r)))
+            requeue = list(buf.batch)
+        else:
+            if st != geer.OK:
+                raise geer.GeerError(st, "serving batch")
+            requeue = []
+            for k, r in enumerate(buf.batch):
+                r.done_ms = t_ms
+                r.batch = buf.batch_id
+                if keep_images:
+                    r.image = self._slot_view(buf, k, r.camera).clone()
+                out_done.append(r)
+        buf.batch = []
+        buf.done = None
+        return requeue
+
+    def run(self, requests, keep_images: bool = False, realtime: bool = True):
+        """Serve the trace. Requests are admitted once their arrival time has passed
+        (wall clock since the start, or immediately if realtime=False)."""
+        import torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue: deque = deque()
+        done: list = []
+        t0 = torch.cuda.Event(enable_timing=True)
+        t0.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        i = 0
+        batch_id = 0
+        while i < len(pending) or queue or any(b.batch for b in self.buffers):
+            now = time.perf_counter() - wall0 if realtime else float("inf")
+            while i < len(pending) and pending[i].arrival <= now:
+                queue.append(pending[i])
+                i += 1
+            progressed = False
+            for b in self.buffers:
+                if b.batch and not b.busy():
+                    requeue = self._complete(b, t0, keep_images, done)
+                    for r in reversed(requeue):
+                        queue.appendleft(r)
+                    progressed = True
+            for b in self.buffers:
+                if not b.batch and queue:
+                    reqs = self.scheduler.admit(queue)
+                    if reqs:
+                        b.launch(reqs, batch_id)
+                        batch_id += 1
+                        progressed = True
+            if not progressed:
+                if realtime and not queue and i < len(pending):
+                    wait = pending[i].arrival - (time.perf_counter() - wall0)
+                    if wait > 2e-4:
+                        time.sleep(min(wait, 1e-3))
+                else:
+                    time.sleep(2e-5)
+        torch.cuda.synchronize()
+        return done
+
+
+def summarize(done, duration_s: float) -> dict:
+    lat = sorted(r.latency_ms for r in done)
+    pix = sum(r.camera.width * r.camera.height for r in done)
+
+    def pct(p):
+        k = min(len(lat) - 1, max(0, int(math.ceil(p / 100.0 * len(lat))) - 1))
+        return lat[k]
+
+    return {"requests": len(done), "p50_ms": pct(50), "p99_ms": pct(99), "mean_ms": statistics.mean(lat),
+            "max_ms": lat[-1], "req_per_s": len(done) / duration_s, "mpix_per_s": pix / duration_s / 1e6,
+            "batches": len({r.batch for r in done})}
