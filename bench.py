@@ -33,6 +33,8 @@ METRIC = "Mpix/s fwd and fwd+bwd at 1M Gaussians, 180° fisheye; serving p50/p99
 WORKLOAD = "1M Gaussians (cube 4 m, 3-7 m ahead, SH3), Kannala-Brandt 1280x960 190deg, BEAP 16x16 tiles"
 FLOPS_TEST = 43    # per ray-Gaussian evaluation: W d, cross product, two norms, divide, exp arg, exp, t* dot
 FLOPS_BLEND = 10   # per applied contributor: clamp, transmittance update, weight, 3 colour FMAs
+FLOPS_BWD = 96     # per contributor in the backward: recovered T, colour and alpha terms, kappa chain to
+                   # d_u / o_u / W (80) and its share of the warp reduction (16)
 
 
 def _peaks():
@@ -234,6 +236,7 @@ def run(args):
         raise RuntimeError(f"device status after warm-up: {geer.status_string(st)}")
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    ws.enable_timing(True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -249,6 +252,8 @@ def run(args):
     st, pairs = ws.device_status()
     if st != geer.OK:
         raise RuntimeError(f"device status after timed steps: {geer.status_string(st)}")
+    stage_ms = {k: v[0] for k, v in ws.stage_times().items()}  # mean of the last 64 timed steps
+    ws.enable_timing(False)
     step_ms = [e[0].elapsed_time(e[4]) for e in evs]
     prep_ms = [e[0].elapsed_time(e[1]) for e in evs]
     sort_ms = [e[1].elapsed_time(e[2]) for e in evs]
@@ -296,20 +301,62 @@ def run(args):
         e2e_ms = float(t.item())
     e2e = world * pixels * args.steps / (e2e_ms / 1e3) / 1e6
 
-    # roofline of the dominant kernel (the render: FP32 pipe / issue bound)
-    evals, applied = ws.render_counts()
+    # rooflines: per stage from algorithmic work and CUDA-event times measured in the timed steps
+    evals, applied, walked = ws.render_counts()
     peaks, peak_src = _peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
-    r_ms = statistics.mean(rend_ms)
-    flops = FLOPS_TEST * evals + FLOPS_BLEND * applied
-    achieved = flops / (r_ms / 1e3) / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    n_items = scene.n  # one camera
+    live = n_items  # live items <= items; equal here (every Gaussian of the cube is in the 190 deg view)
+    tile_passes_ = math.ceil(max(1, math.ceil(math.log2(math.ceil(cam.width / 16) * math.ceil(cam.height / 16)))) / 8)
+    sh_bytes = 4 * 3 * (scene.sh_degree + 1) ** 2
+    g_bytes = 4 * (3 + 3 + 4 + 1) + sh_bytes
+    work = {
+        "preprocess": ("hbm", scene.n * g_bytes + n_items * (64 + 16 + 4 + 4)),
+        "depth_sort": ("hbm", 4 * 20 * live),
+        "duplicate": ("hbm", live * (4 + 4 + 16) + int(pairs) * 8),
+        "tile_sort": ("hbm", tile_passes_ * 20 * int(pairs)),
+        "render_fwd": ("alu", FLOPS_TEST * evals + FLOPS_BLEND * applied),
+        "render_bwd": ("alu", FLOPS_TEST * walked + FLOPS_BWD * applied),
+        "preprocess_bwd": ("hbm", scene.n * g_bytes * 3 + n_items * 64),
+    }
+    stages = {}
+    for name, (bound, amount) in work.items():
+        t = stage_ms.get(name, 0.0)
+        if t <= 0:
+            continue
+        if bound == "hbm":
+            ach = amount / (t / 1e3) / 1e9
+            stages[name] = {"ms": t, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": ach / hbm_peak, "algorithmic_bytes": amount}
+        else:
+            ach = amount / (t / 1e3) / 1e12
+            stages[name] = {"ms": t, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                            "frac": ach / fp32_peak, "algorithmic_flops": amount}
+    kernel_of = {"render_fwd": "k_render_fwd", "render_bwd": "k_render_bwd", "preprocess": "k_preprocess",
+                 "preprocess_bwd": "k_preprocess_bwd", "duplicate": "k_duplicate"}
+    single = {k: v for k, v in stages.items() if k in kernel_of}
+    dom = max(single, key=lambda k: single[k]["ms"])
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "render_fwd_traffic.json")
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
+        import hashlib
         with open(prof) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+            tr = json.load(f).get(kernel_of[dom])
+        if tr:
+            src = os.path.join(ROOT, "paper_2505_24053_gb300", "csrc", tr["source"])
+            if hashlib.sha1(open(src, "rb").read()).hexdigest() == tr["source_sha1"]:
+                traffic = tr["bytes_per_launch"]
+    d = stages[dom]
+    roofline = {"bound": d["bound"], "kernel": kernel_of[dom], "achieved": d["achieved"],
+                "peak": d["peak"], "unit": d["unit"], "frac": d["frac"], "traffic": traffic,
+                "kernel_ms": d["ms"],
+                "peak_source": (f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
+                                f"(max SM clock, {peak_src})") if d["bound"] == "alu"
+                               else f"copy bandwidth, {peak_src}",
+                "work": {"evaluations": evals, "applied": applied, "walked_back": walked}}
     tiles = math.ceil(cam.width / 16) * math.ceil(cam.height / 16)
     tile_passes = math.ceil(max(1, math.ceil(math.log2(tiles))) / 8)
     # preprocess, scan, compact, 4 depth passes x 3, gather, scan, duplicate, tile offsets,
@@ -326,13 +373,10 @@ def run(args):
                    "l2": "512 MB buffer written between timed steps (outside step events); inputs 236 MB > L2"},
         "fwd_only": {"value": fwd_value, "unit": "Mpix/s", "ms": statistics.mean(fwd_ms)},
         "stages_ms": {"preprocess": statistics.mean(prep_ms), "bin_sort": statistics.mean(sort_ms),
-                      "render_fwd": r_ms, "backward": statistics.mean(bwd_ms) if have_bwd else None},
-        "roofline": {"bound": "alu", "kernel": "k_render_fwd", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                     "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
-                                    f"(max SM clock, {peak_src})",
-                     "work": {"evaluations": evals, "applied": applied, "flops_per_eval": FLOPS_TEST,
-                              "flops_per_applied": FLOPS_BLEND}},
+                      "render_fwd": statistics.mean(rend_ms),
+                      "backward": statistics.mean(bwd_ms) if have_bwd else None},
+        "roofline": roofline,
+        "stages": stages,
         "e2e": {"value": e2e, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),

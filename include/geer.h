@@ -197,8 +197,22 @@ geer_status geer_l1_loss_grad(const float *rgb, const float *target, int64_t n_v
 
 /* Measurement (synchronous): totals over all rays of the last geer_render_fwd
  * of the ray-Gaussian evaluations executed (list entries walked up to early
- * termination) and of the contributors composited. */
-geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t *applied, void *stream);
+ * termination), of the contributors composited, and (walked_back, may be NULL)
+ * of the list entries the backward walks (up to each ray's last contributor). */
+geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t *applied, uint64_t *walked_back,
+                               void *stream);
+
+/* Stage timing. When enabled, the calls above record a pair of CUDA events on
+ * their stream around each stage's kernels (stages: see geer_stage_name:
+ * preprocess, bin_front, depth_sort, count_pairs, duplicate, tile_sort,
+ * render_fwd, render_bwd, preprocess_bwd), keeping the most recent 64 per
+ * stage. geer_stage_times synchronises `stream` and writes the mean duration in
+ * ms of the recorded occurrences of each stage into ms[0..8] (n >= 9) and
+ * their number into counts (may be NULL). Do not enable it while capturing a
+ * CUDA graph. */
+geer_status geer_enable_timing(geer_workspace *ws, int32_t enable);
+geer_status geer_stage_times(geer_workspace *ws, float *ms, int32_t n, int32_t *counts, void *stream);
+const char *geer_stage_name(int32_t stage);
 
 /* Render one small camera without allocating anything.
  *

@@ -269,6 +269,25 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
 
 geer_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GEER_OK : GEER_ERR_CUDA; }
 
+// Records the begin/end events of one stage when timing is enabled.
+struct StageTimer {
+    geer_workspace *ws;
+    int stage, slot;
+    cudaStream_t s;
+    StageTimer(geer_workspace *w, int st, cudaStream_t str) : ws(w), stage(st), slot(-1), s(str) {
+        if (ws->timing) {
+            slot = ws->ev_count[stage] % kTimingRing;
+            cudaEventRecord(ws->ev[stage][slot][0], s);
+        }
+    }
+    ~StageTimer() {
+        if (slot >= 0) {
+            cudaEventRecord(ws->ev[stage][slot][1], s);
+            ws->ev_count[stage] += 1;
+        }
+    }
+};
+
 geer_status check_cams(const geer_camera *cams, int32_t n) {
     if (!cams || n <= 0 || n > kMaxCams) return GEER_ERR_ARG;
     for (int i = 0; i < n; ++i)
@@ -417,6 +436,12 @@ geer_status geer_workspace_init(void *dev_mem, size_t bytes, const geer_camera *
 
 geer_status geer_workspace_destroy(geer_workspace *ws) {
     if (!ws) return GEER_ERR_ARG;
+    if (ws->timing)
+        for (int a = 0; a < kStageCount; ++a)
+            for (int b = 0; b < kTimingRing; ++b) {
+                cudaEventDestroy(ws->ev[a][b][0]);
+                cudaEventDestroy(ws->ev[a][b][1]);
+            }
     if (ws->h_stage) cudaFreeHost(ws->h_stage);
     free(ws);
     return GEER_OK;
@@ -460,6 +485,7 @@ geer_status geer_preprocess(geer_workspace *ws, const geer_gaussians *g, void *s
     ws->n_gauss = g->n;
     ws->sh_degree = g->sh_degree;
     ws->stage = 1;
+    StageTimer tm(ws, kStagePreprocess, static_cast<cudaStream_t>(stream));
     return cuda_status(launch_preprocess(ws, g, static_cast<cudaStream_t>(stream)));
 }
 
@@ -468,9 +494,18 @@ geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *strea
     if (ws->stage < 1) return GEER_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // live items in index order -> stable depth sort -> pair counts in depth order
-    if (launch_bin_front(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
-    if (launch_depth_sort(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
-    if (launch_count_pairs(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    {
+        StageTimer tm(ws, kStageBinFront, s);
+        if (launch_bin_front(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    }
+    {
+        StageTimer tm(ws, kStageDepthSort, s);
+        if (launch_depth_sort(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    }
+    {
+        StageTimer tm(ws, kStageCountPairs, s);
+        if (launch_count_pairs(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    }
     if (pairs_needed) {
         uint32_t m[kMiscCount];
         if (cudaMemcpyAsync(m, ws->d_misc, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -488,8 +523,14 @@ geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *strea
         }
     }
     // emit (tile, item) pairs in depth order, stable sort by tile, ranges
-    if (launch_duplicate(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
-    if (launch_tile_sort(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    {
+        StageTimer tm(ws, kStageDuplicate, s);
+        if (launch_duplicate(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    }
+    {
+        StageTimer tm(ws, kStageTileSort, s);
+        if (launch_tile_sort(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
+    }
     ws->stage = 2;
     return GEER_OK;
 }
@@ -497,7 +538,11 @@ geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *strea
 geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void *stream) {
     if (!ws || !rgb) return GEER_ERR_ARG;
     if (ws->stage < 2) return GEER_ERR_STATE;
-    geer_status st = cuda_status(launch_render_fwd(ws, rgb, T_final, static_cast<cudaStream_t>(stream)));
+    geer_status st;
+    {
+        StageTimer tm(ws, kStageRenderFwd, static_cast<cudaStream_t>(stream));
+        st = cuda_status(launch_render_fwd(ws, rgb, T_final, static_cast<cudaStream_t>(stream)));
+    }
     if (st == GEER_OK) ws->stage = 3;
     return st;
 }
@@ -511,8 +556,13 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
     if (g->n != ws->n_gauss || g->sh_degree != ws->sh_degree) return GEER_ERR_ARG;
     if (d_sh && (reinterpret_cast<uintptr_t>(d_sh) & 15)) return GEER_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_render_bwd(ws, dL_drgb, s);
-    if (e != cudaSuccess) return GEER_ERR_CUDA;
+    const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
+    if (items > 0 && cudaMemsetAsync(ws->d_gacc, 0, sizeof(GradAcc) * items, s) != cudaSuccess) return GEER_ERR_CUDA;
+    {
+        StageTimer tm(ws, kStageRenderBwd, s);
+        if (launch_render_bwd(ws, dL_drgb, s) != cudaSuccess) return GEER_ERR_CUDA;
+    }
+    StageTimer tm(ws, kStagePreprocessBwd, s);
     return cuda_status(launch_preprocess_bwd(ws, g, d_mean, d_scale, d_quat, d_opacity, d_sh, s));
 }
 
@@ -603,22 +653,74 @@ geer_status geer_l1_loss_grad(const float *rgb, const float *target, int64_t n_v
     return cuda_status(launch_l1_grad(rgb, target, n_values, dL_drgb, loss, sms, static_cast<cudaStream_t>(stream)));
 }
 
-geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t *applied, void *stream) {
+geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t *applied, uint64_t *walked_back,
+                               void *stream) {
     if (!ws || !evaluated || !applied) return GEER_ERR_ARG;
     if (ws->stage < 3) return GEER_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<uint2> v(ws->n_pixels);
+    std::vector<uint32_t> last(ws->n_pixels);
     if (cudaMemcpyAsync(v.data(), ws->d_evals, sizeof(uint2) * ws->n_pixels, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(last.data(), ws->d_last, sizeof(uint32_t) * ws->n_pixels, cudaMemcpyDeviceToHost, s) !=
             cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return GEER_ERR_CUDA;
-    uint64_t e = 0, a = 0;
-    for (const uint2 &x : v) {
-        e += x.x;
-        a += x.y;
+    uint64_t e = 0, a = 0, w = 0;
+    for (int64_t i = 0; i < ws->n_pixels; ++i) {
+        e += v[i].x;
+        a += v[i].y;
+        w += last[i];
     }
     *evaluated = e;
     *applied = a;
+    if (walked_back) *walked_back = w;
+    return GEER_OK;
+}
+
+static const char *kStageNames[kStageCount] = {"preprocess", "bin_front", "depth_sort", "count_pairs", "duplicate",
+                                               "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd"};
+
+const char *geer_stage_name(int32_t stage) {
+    return (stage >= 0 && stage < kStageCount) ? kStageNames[stage] : "unknown";
+}
+
+geer_status geer_enable_timing(geer_workspace *ws, int32_t enable) {
+    if (!ws) return GEER_ERR_ARG;
+    if (enable && !ws->timing) {
+        for (int a = 0; a < kStageCount; ++a) {
+            ws->ev_count[a] = 0;
+            for (int b = 0; b < kTimingRing; ++b)
+                if (cudaEventCreate(&ws->ev[a][b][0]) != cudaSuccess || cudaEventCreate(&ws->ev[a][b][1]) != cudaSuccess)
+                    return GEER_ERR_CUDA;
+        }
+        ws->timing = 1;
+    } else if (!enable && ws->timing) {
+        for (int a = 0; a < kStageCount; ++a)
+            for (int b = 0; b < kTimingRing; ++b) {
+                cudaEventDestroy(ws->ev[a][b][0]);
+                cudaEventDestroy(ws->ev[a][b][1]);
+            }
+        ws->timing = 0;
+    }
+    return GEER_OK;
+}
+
+geer_status geer_stage_times(geer_workspace *ws, float *ms, int32_t n, int32_t *counts, void *stream) {
+    if (!ws || !ms || n < kStageCount) return GEER_ERR_ARG;
+    if (!ws->timing) return GEER_ERR_STATE;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return GEER_ERR_CUDA;
+    for (int a = 0; a < kStageCount; ++a) {
+        const int k = std::min(ws->ev_count[a], kTimingRing);
+        double tot = 0.0;
+        for (int b = 0; b < k; ++b) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, ws->ev[a][b][0], ws->ev[a][b][1]) != cudaSuccess) return GEER_ERR_CUDA;
+            tot += t;
+        }
+        ms[a] = k ? (float)(tot / k) : 0.0f;
+        if (counts) counts[a] = k;
+    }
     return GEER_OK;
 }
 

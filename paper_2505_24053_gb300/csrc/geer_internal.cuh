@@ -74,6 +74,21 @@ struct Params {
     float alpha_min, T_min, alpha_max, lambda_pad;
 };
 
+// Stages timed by geer_enable_timing (CUDA events around each stage's kernels).
+enum Stage : int {
+    kStagePreprocess = 0,
+    kStageBinFront,      // live-item scan + compaction
+    kStageDepthSort,
+    kStageCountPairs,
+    kStageDuplicate,     // duplicate + tile ranges
+    kStageTileSort,
+    kStageRenderFwd,
+    kStageRenderBwd,
+    kStagePreprocessBwd,
+    kStageCount
+};
+constexpr int kTimingRing = 64;
+
 }  // namespace geer
 
 // Host-side workspace handle.
@@ -128,6 +143,11 @@ struct geer_workspace {
     // pinned staging for asynchronous camera uploads
     void *h_stage;
     size_t stage_bytes;
+
+    // optional stage timing: a ring of (begin, end) events per stage
+    int timing;
+    cudaEvent_t ev[geer::kStageCount][geer::kTimingRing][2];
+    int ev_count[geer::kStageCount];
 };
 
 namespace geer {

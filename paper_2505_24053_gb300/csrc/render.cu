@@ -322,11 +322,6 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
 }
 
 cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cudaStream_t s) {
-    const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
-    if (items > 0) {
-        cudaError_t e = cudaMemsetAsync(ws->d_gacc, 0, sizeof(GradAcc) * items, s);
-        if (e != cudaSuccess) return e;
-    }
     if (ws->n_tiles == 0) return cudaSuccess;
     k_render_bwd<<<(unsigned)ws->n_tiles, kTilePix, 0, s>>>(
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_range, ws->d_vals[ws->sorted_buf], ws->d_rec, ws->d_misc,

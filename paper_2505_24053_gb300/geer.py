@@ -44,7 +44,8 @@ class ParamsC(C.Structure):
 EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "geer_workspace_init",
            "geer_workspace_destroy", "geer_set_cameras", "geer_preprocess", "geer_bin_sort", "geer_render_fwd",
            "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
-           "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc", "geer_set_camera_slots"]
+           "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc", "geer_set_camera_slots",
+           "geer_enable_timing", "geer_stage_times", "geer_stage_name"]
 
 _lib = None
 
@@ -67,6 +68,8 @@ def lib(build_if_missing: bool = True):
     P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
     L.geer_status_string.restype = C.c_char_p
     L.geer_status_string.argtypes = [C.c_int]
+    L.geer_stage_name.restype = C.c_char_p
+    L.geer_stage_name.argtypes = [C.c_int32]
     sigs = {
         "geer_default_params": [P],
         "geer_workspace_size": [P, I32, I64, I32, I64, P],
@@ -80,7 +83,9 @@ def lib(build_if_missing: bool = True):
         "geer_last_device_status": [P, P, P],
         "geer_debug_preprocess": [P, P, P, P, P, P],
         "geer_debug_pairs": [P, P, P, I64, P, P],
-        "geer_render_counts": [P, P, P, P],
+        "geer_render_counts": [P, P, P, P, P],
+        "geer_enable_timing": [P, I32],
+        "geer_stage_times": [P, P, I32, P, P],
         "geer_l1_loss_grad": [P, P, I64, P, P, P],
         "geer_render_noalloc": [P, P, P, P, P, P],
         "geer_set_camera_slots": [P, P, I32, P, I64, I64, P],
@@ -267,11 +272,22 @@ class Workspace:
         return cull, keys, ranges, counts
 
     def render_counts(self, stream=None):
-        """(evaluations executed, contributors applied) of the last forward render."""
-        e, a = C.c_uint64(), C.c_uint64()
-        _check(lib().geer_render_counts(self._handle, C.byref(e), C.byref(a), _stream(stream)),
+        """(evaluations executed, contributors applied, entries walked by the backward)
+        of the last forward render."""
+        e, a, w = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(lib().geer_render_counts(self._handle, C.byref(e), C.byref(a), C.byref(w), _stream(stream)),
                "geer_render_counts")
-        return int(e.value), int(a.value)
+        return int(e.value), int(a.value), int(w.value)
+
+    def enable_timing(self, on: bool = True):
+        _check(lib().geer_enable_timing(self._handle, 1 if on else 0), "geer_enable_timing")
+
+    def stage_times(self, stream=None) -> dict:
+        """Mean ms of the recorded occurrences of each stage (timing must be enabled)."""
+        ms = (C.c_float * 16)()
+        cnt = (C.c_int32 * 16)()
+        _check(lib().geer_stage_times(self._handle, ms, 16, cnt, _stream(stream)), "geer_stage_times")
+        return {lib().geer_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(9)}
 
     def debug_pairs(self, cap: int | None = None, stream=None):
         cap = self.pair_capacity if cap is None else cap
