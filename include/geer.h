@@ -214,6 +214,17 @@ geer_status geer_enable_timing(geer_workspace *ws, int32_t enable);
 geer_status geer_stage_times(geer_workspace *ws, float *ms, int32_t n, int32_t *counts, void *stream);
 const char *geer_stage_name(int32_t stage);
 
+/* Resample a BEAP image of camera `cam` (beap_rgb: device [h][w][3] f32, the
+ * camera's rows of a geer_render_fwd output) into the camera's native image
+ * (native_rgb: device [h][w][3] f32) by bilinear inverse interpolation (App. E).
+ * Native intrinsics: square pixels, principal point at the image centre, focal
+ * length mapping fov_x/2 to w/2; pinhole x = f tan(theta), equidistant r = f phi,
+ * Kannala-Brandt r = f phi_d(phi). Native pixels whose ray falls outside the BEAP
+ * grid, or where the distortion cannot be inverted, get fill_rgb (host [3],
+ * NULL = black). Asynchronous on `stream`. */
+geer_status geer_remap_to_native(const float *beap_rgb, const geer_camera *cam, const float *fill_rgb,
+                                 float *native_rgb, void *stream);
+
 /* Render one small camera without allocating anything.
  *
  * For callers that cannot call cudaMalloc or any other allocator at render

@@ -957,3 +957,125 @@ void orc_render_grad(const orc_gaussians *g, const orc_camera *c, const orc_para
     }
     free(buf);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Part 4: resampling a BEAP image into the native camera image (App. E)       */
+/* ------------------------------------------------------------------------- */
+
+/* Native intrinsics (the reading that also fixes FoV_y): square pixels, principal
+ * point at the image centre, focal length mapping FoV_x/2 to w/2. */
+double orc_native_focal(const orc_camera *c)
+{
+    double half = 0.5 * (double)c->fov_x;
+    if (c->model == 0) return 0.5 * c->width / tan(half);
+    double k[4] = {0, 0, 0, 0};
+    if (c->model == 2) for (int i = 0; i < 4; ++i) k[i] = c->k[i];
+    return 0.5 * c->width / kb_distort(k, half);
+}
+
+/* Forward projection of App. E for a camera-frame direction in front of the
+ * camera: pinhole (x_p, y_p) = f (tan theta, tan phi) + c; fisheye
+ * r = sqrt(tan^2 theta + tan^2 phi), varphi = atan r, varphi_d = KB polynomial,
+ * (x_p, y_p) = f varphi_d / r (tan theta, tan phi) + c. */
+void orc_project(const orc_camera *c, const double d[3], double *xp, double *yp)
+{
+    double f = orc_native_focal(c);
+    double tt = d[0] / d[2], tp = d[1] / d[2];
+    double cx = 0.5 * c->width, cy = 0.5 * c->height;
+    if (c->model == 0) { *xp = f * tt + cx; *yp = f * tp + cy; return; }
+    double k[4] = {0, 0, 0, 0};
+    if (c->model == 2) for (int i = 0; i < 4; ++i) k[i] = c->k[i];
+    double r = sqrt(tt * tt + tp * tp);
+    if (r == 0.0) { *xp = cx; *yp = cy; return; }
+    double vd = kb_distort(k, atan(r));
+    *xp = f * vd / r * tt + cx;
+    *yp = f * vd / r * tp + cy;
+}
+
+/* End of the increasing branch of the distortion phi_d below pi (pi if none). */
+static double kb_branch_end(const double k[4])
+{
+    double prev = 0.0;
+    for (int s = 1; s <= 4096; ++s) {
+        double ph = M_PI * s / 4096, val = kb_distort(k, ph);
+        if (!(val > prev)) return M_PI * (s - 1) / 4096;
+        prev = val;
+    }
+    return M_PI;
+}
+
+static int native_ray_k(const orc_camera *c, double f, const double k[4], double pmax, int i, int j,
+                        double d[3])
+{
+    double u = (i + 0.5 - 0.5 * c->width) / f, v = (j + 0.5 - 0.5 * c->height) / f;
+    if (c->model == 0) {
+        double n = sqrt(u * u + v * v + 1.0);
+        d[0] = u / n; d[1] = v / n; d[2] = 1.0 / n;
+        return 1;
+    }
+    double rd = sqrt(u * u + v * v);
+    if (rd > kb_distort(k, pmax)) return 0;
+    double lo = 0.0, hi = pmax;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (kb_distort(k, mid) < rd) lo = mid; else hi = mid;
+    }
+    double p = 0.5 * (lo + hi);
+    if (rd > 0) { d[0] = sin(p) * u / rd; d[1] = sin(p) * v / rd; } else { d[0] = 0; d[1] = 0; }
+    d[2] = cos(p);
+    return 1;
+}
+
+static void native_model(const orc_camera *c, double k[4], double *pmax)
+{
+    for (int a = 0; a < 4; ++a) k[a] = c->model == 2 ? c->k[a] : 0.0;
+    *pmax = c->model == 0 ? 0.0 : kb_branch_end(k);
+}
+
+/* Ray of native pixel (i, j) (centre at i + 1/2, j + 1/2): the inverse of the
+ * projection. Fisheye: the incidence angle solves varphi_d(varphi) = r_d, found by
+ * bisection on the increasing branch starting at 0. Returns 0 when no ray. */
+int orc_native_ray(const orc_camera *c, int i, int j, double d[3])
+{
+    double k[4], pmax;
+    native_model(c, k, &pmax);
+    return native_ray_k(c, orc_native_focal(c), k, pmax, i, j, d);
+}
+
+/* Native image from a BEAP image of the same camera: bilinear interpolation at
+ * u = theta/FoV_x w + w/2 - 1/2, v = phi/FoV_y h + h/2 - 1/2 with theta =
+ * atan2(x, z), phi = atan(y / z); outside the grid (beyond half a pixel) or
+ * without a ray: fill. out: [h][w][3] doubles; coords (may be NULL): [h][w][2], the
+ * BEAP coordinate (u, v) of each native pixel, NaN where it has no ray. */
+void orc_remap_to_native(const orc_camera *c, const float *beap, const float *fill, double *out,
+                         double *coords)
+{
+    int w = c->width, h = c->height;
+    double fy = orc_fov_y(c), f = orc_native_focal(c), k[4], pmax;
+    native_model(c, k, &pmax);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < h; ++j)
+        for (int i = 0; i < w; ++i) {
+            double d[3], o[3] = {fill[0], fill[1], fill[2]};
+            if (coords) coords[2 * (j * w + i)] = coords[2 * (j * w + i) + 1] = NAN;
+            if (native_ray_k(c, f, k, pmax, i, j, d) && d[2] != 0.0) {
+                double th = atan2(d[0], d[2]), ph = atan(d[1] / d[2]);
+                double ub = th / c->fov_x * w + 0.5 * w - 0.5, vb = ph / fy * h + 0.5 * h - 0.5;
+                if (coords) { coords[2 * (j * w + i)] = ub; coords[2 * (j * w + i) + 1] = vb; }
+                if (ub >= -0.5 && ub <= w - 0.5 && vb >= -0.5 && vb <= h - 0.5) {
+                    double uc = fmin(fmax(ub, 0.0), w - 1.0), vc = fmin(fmax(vb, 0.0), h - 1.0);
+                    int x0 = (int)floor(uc), y0 = (int)floor(vc);
+                    if (x0 > w - 2) x0 = w - 2 < 0 ? 0 : w - 2;
+                    if (y0 > h - 2) y0 = h - 2 < 0 ? 0 : h - 2;
+                    int x1 = x0 + 1 < w ? x0 + 1 : w - 1, y1 = y0 + 1 < h ? y0 + 1 : h - 1;
+                    double ax = uc - x0, ay = vc - y0;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        double p00 = beap[3 * (y0 * w + x0) + ch], p01 = beap[3 * (y0 * w + x1) + ch];
+                        double p10 = beap[3 * (y1 * w + x0) + ch], p11 = beap[3 * (y1 * w + x1) + ch];
+                        o[ch] = (1 - ay) * ((1 - ax) * p00 + ax * p01) + ay * ((1 - ax) * p10 + ax * p11);
+                    }
+                }
+            }
+            for (int ch = 0; ch < 3; ++ch) out[3 * (j * w + i) + ch] = o[ch];
+        }
+}

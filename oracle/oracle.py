@@ -70,6 +70,12 @@ def lib():
         _lib.orc_pixel_contributors.restype = C.c_int64
         _lib.orc_pixel_contributors.argtypes = [P, P, P, P, C.c_int32, C.c_int32, P, C.c_int64]
         _lib.orc_render_grad.argtypes = [P, P, P, P, P, C.c_int64, P, P, P, P, P, P, P]
+        _lib.orc_native_focal.restype = C.c_double
+        _lib.orc_native_focal.argtypes = [P]
+        _lib.orc_project.argtypes = [P, P, P, P]
+        _lib.orc_native_ray.restype = C.c_int
+        _lib.orc_native_ray.argtypes = [P, C.c_int, C.c_int, P]
+        _lib.orc_remap_to_native.argtypes = [P, P, P, P, P]
     return _lib
 
 
@@ -257,3 +263,35 @@ def match_pixels(gpu_rgb: np.ndarray, orc: dict, tol: float = 2e-4, cond_limit: 
     undecidable = orc["flags"] != 0
     ok = (err.max(axis=1) <= lim) | undecidable
     return ok, err, ill, undecidable
+
+
+def native_focal(cam) -> float:
+    c = camera_c(cam)
+    return lib().orc_native_focal(C.byref(c))
+
+
+def project(cam, d):
+    """App. E forward projection of a camera-frame direction to native pixel coordinates."""
+    c = camera_c(cam)
+    d = np.ascontiguousarray(d, np.float64)
+    xp, yp = C.c_double(), C.c_double()
+    lib().orc_project(C.byref(c), _ptr(d), C.byref(xp), C.byref(yp))
+    return xp.value, yp.value
+
+
+def native_ray(cam, i: int, j: int):
+    c = camera_c(cam)
+    d = np.zeros(3)
+    ok = lib().orc_native_ray(C.byref(c), i, j, _ptr(d))
+    return (d if ok else None)
+
+
+def remap_to_native(cam, beap: np.ndarray, fill=(0.0, 0.0, 0.0), coords: bool = False):
+    """Native image [h,w,3] (and, with coords=True, each native pixel's BEAP (u, v), NaN without a ray)."""
+    c = camera_c(cam)
+    beap = np.ascontiguousarray(beap, np.float32)
+    f = np.ascontiguousarray(fill, np.float32)
+    out = np.zeros((cam.height, cam.width, 3))
+    uv = np.zeros((cam.height, cam.width, 2)) if coords else None
+    lib().orc_remap_to_native(C.byref(c), _ptr(beap), _ptr(f), _ptr(out), _ptr(uv) if coords else None)
+    return (out, uv) if coords else out

@@ -678,6 +678,34 @@ geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t
     return GEER_OK;
 }
 
+geer_status geer_remap_to_native(const float *beap_rgb, const geer_camera *cam, const float *fill_rgb,
+                                 float *native_rgb, void *stream) {
+    if (!beap_rgb || !cam || !native_rgb || !camera_ok(*cam)) return GEER_ERR_ARG;
+    const double fy = derived_fov_y(*cam);
+    const double half = 0.5 * (double)cam->fov_x;
+    double focal, phi_max;
+    if (cam->model == GEER_PINHOLE) {
+        focal = 0.5 * cam->width / tan(half);
+        phi_max = 0.0;
+    } else {
+        float k0[4] = {0, 0, 0, 0};
+        const float *k = cam->model == GEER_KANNALA_BRANDT ? cam->k : k0;
+        focal = 0.5 * cam->width / kb_theta_d(k, half);
+        // the distortion must stay invertible (increasing) up to phi_max: the first
+        // turning point of phi_d(phi) below pi, or pi
+        phi_max = M_PI;
+        const int steps = 4096;
+        double prev = 0.0;
+        for (int s2 = 1; s2 <= steps; ++s2) {
+            const double ph = M_PI * s2 / steps, val = kb_theta_d(k, ph);
+            if (!(val > prev)) { phi_max = M_PI * (s2 - 1) / steps; break; }
+            prev = val;
+        }
+    }
+    return cuda_status(
+        launch_remap_to_native(beap_rgb, cam, fy, focal, phi_max, fill_rgb, native_rgb, static_cast<cudaStream_t>(stream)));
+}
+
 static const char *kStageNames[kStageCount] = {"preprocess", "bin_front", "depth_sort", "count_pairs", "duplicate",
                                                "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd"};
 

@@ -165,6 +165,8 @@ cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians
                                   float *d_quat, float *d_opacity, float *d_sh, cudaStream_t s);
 cudaError_t launch_l1_grad(const float *pred, const float *target, int64_t m, float *grad, float *loss, int num_sms,
                            cudaStream_t s);
+cudaError_t launch_remap_to_native(const float *beap, const geer_camera *cam, double fov_y, double focal,
+                                   double phi_max, const float *fill, float *out, cudaStream_t s);
 int sort_blocks_per_sm();
 
 inline int64_t prep_blocks(int64_t n) { return (n + kPrepThreads - 1) / kPrepThreads; }

@@ -1,0 +1,118 @@
+// remap.cu -- resampling a BEAP render into the camera's native image (App. E,
+// inverse interpolation, read in reverse: native pixel -> ray -> BEAP angles).
+//
+// Native intrinsics: square pixels, principal point at the image centre, and the
+// focal length that maps the horizontal half field of view to w/2 (the same
+// reading that fixes the BEAP grid's vertical field of view):
+//   pinhole       x_p = f tan(theta) + c_x                (App. E)
+//   fisheye (KB)  x_p = f phi_d / r tan(theta) + c_x,
+//                 r = sqrt(tan^2 theta + tan^2 phi), phi = atan r,
+//                 phi_d = phi (1 + k1 phi^2 + k2 phi^4 + k3 phi^6 + k4 phi^8)
+//                 (equidistant: k = 0).
+// A native pixel's ray inverts these (Newton on phi_d(phi) = r_d); its BEAP
+// angles are theta = atan2(x, z), phi = atan(y / z), its BEAP coordinate
+// u = theta / FoV_x w + w/2 - 1/2 (likewise v), and its colour the bilinear
+// interpolation of the BEAP image there. Rays outside the BEAP grid (beyond half
+// a pixel) or where the distortion cannot be inverted get the fill colour.
+#include "geer_internal.cuh"
+
+namespace geer {
+namespace {
+
+struct RemapCam {
+    int32_t model, width, height, pad_;
+    float f, fov_x, fov_y, phi_max;
+    float k[4];
+    float fill[3];
+};
+
+__device__ __forceinline__ float kb_poly(const float k[4], float p, float &dp) {
+    const float p2 = p * p;
+    const float s = 1.0f + p2 * (k[0] + p2 * (k[1] + p2 * (k[2] + p2 * k[3])));
+    // d/dp of p s(p^2) = s + p * 2p s'(p^2)
+    const float ds = k[0] + p2 * (2.0f * k[1] + p2 * (3.0f * k[2] + p2 * 4.0f * k[3]));
+    dp = s + 2.0f * p2 * ds;
+    return p * s;
+}
+
+__global__ void __launch_bounds__(256) k_remap_to_native(const float *__restrict__ beap, RemapCam c,
+                                                         float *__restrict__ out) {
+    const int64_t n = (int64_t)c.width * c.height;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int i = (int)(idx % c.width), j = (int)(idx / c.width);
+    const float u = ((float)i + 0.5f - 0.5f * (float)c.width) / c.f;
+    const float v = ((float)j + 0.5f - 0.5f * (float)c.height) / c.f;
+    float dx, dy, dz;
+    bool ok = true;
+    if (c.model == GEER_PINHOLE) {
+        dx = u; dy = v; dz = 1.0f;
+    } else {
+        const float rd = sqrtf(u * u + v * v);
+        float p = rd;  // Newton on phi_d(phi) = rd from phi = rd
+        for (int it = 0; it < 12; ++it) {
+            float dp;
+            const float val = kb_poly(c.k, p, dp);
+            if (!(dp > 0.0f)) { ok = false; break; }
+            p = fminf(fmaxf(p - (val - rd) / dp, 0.0f), c.phi_max);
+        }
+        float dp;
+        if (ok && fabsf(kb_poly(c.k, p, dp) - rd) > 1e-5f * (1.0f + rd)) ok = false;
+        const float sp = sinf(p), cp = cosf(p);
+        if (rd > 0.0f) { dx = sp * u / rd; dy = sp * v / rd; } else { dx = 0.0f; dy = 0.0f; }
+        dz = cp;
+    }
+    float r = c.fill[0], g = c.fill[1], b = c.fill[2];
+    if (ok && dz != 0.0f) {
+        const float th = atan2f(dx, dz);
+        const float ph = atanf(dy / dz);
+        const float ub = th / c.fov_x * (float)c.width + 0.5f * (float)c.width - 0.5f;
+        const float vb = ph / c.fov_y * (float)c.height + 0.5f * (float)c.height - 0.5f;
+        if (ub >= -0.5f && ub <= (float)c.width - 0.5f && vb >= -0.5f && vb <= (float)c.height - 0.5f) {
+            const float uc = fminf(fmaxf(ub, 0.0f), (float)(c.width - 1));
+            const float vc = fminf(fmaxf(vb, 0.0f), (float)(c.height - 1));
+            const int x0 = min((int)uc, c.width - 2 < 0 ? 0 : c.width - 2);
+            const int y0 = min((int)vc, c.height - 2 < 0 ? 0 : c.height - 2);
+            const int x1 = min(x0 + 1, c.width - 1), y1 = min(y0 + 1, c.height - 1);
+            const float ax = uc - (float)x0, ay = vc - (float)y0;
+            const float *p00 = beap + 3 * ((int64_t)y0 * c.width + x0);
+            const float *p01 = beap + 3 * ((int64_t)y0 * c.width + x1);
+            const float *p10 = beap + 3 * ((int64_t)y1 * c.width + x0);
+            const float *p11 = beap + 3 * ((int64_t)y1 * c.width + x1);
+            float o[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float top = p00[ch] + ax * (p01[ch] - p00[ch]);
+                const float bot = p10[ch] + ax * (p11[ch] - p10[ch]);
+                o[ch] = top + ay * (bot - top);
+            }
+            r = o[0]; g = o[1]; b = o[2];
+        }
+    }
+    out[3 * idx + 0] = r;
+    out[3 * idx + 1] = g;
+    out[3 * idx + 2] = b;
+}
+
+}  // namespace
+
+cudaError_t launch_remap_to_native(const float *beap, const geer_camera *cam, double fov_y, double focal,
+                                   double phi_max, const float *fill, float *out, cudaStream_t s) {
+    RemapCam c;
+    c.model = cam->model;
+    c.width = cam->width;
+    c.height = cam->height;
+    c.pad_ = 0;
+    c.f = (float)focal;
+    c.fov_x = cam->fov_x;
+    c.fov_y = (float)fov_y;
+    c.phi_max = (float)phi_max;
+    for (int i = 0; i < 4; ++i) c.k[i] = cam->model == GEER_KANNALA_BRANDT ? cam->k[i] : 0.0f;
+    for (int i = 0; i < 3; ++i) c.fill[i] = fill ? fill[i] : 0.0f;
+    const int64_t n = (int64_t)cam->width * cam->height;
+    if (n == 0) return cudaSuccess;
+    k_remap_to_native<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(beap, c, out);
+    return cudaGetLastError();
+}
+
+}  // namespace geer

@@ -45,7 +45,7 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_workspace_destroy", "geer_set_cameras", "geer_preprocess", "geer_bin_sort", "geer_render_fwd",
            "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
            "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc", "geer_set_camera_slots",
-           "geer_enable_timing", "geer_stage_times", "geer_stage_name"]
+           "geer_enable_timing", "geer_stage_times", "geer_stage_name", "geer_remap_to_native"]
 
 _lib = None
 
@@ -86,6 +86,7 @@ def lib(build_if_missing: bool = True):
         "geer_render_counts": [P, P, P, P, P],
         "geer_enable_timing": [P, I32],
         "geer_stage_times": [P, P, I32, P, P],
+        "geer_remap_to_native": [P, P, P, P, P],
         "geer_l1_loss_grad": [P, P, I64, P, P, P],
         "geer_render_noalloc": [P, P, P, P, P, P],
         "geer_set_camera_slots": [P, P, I32, P, I64, I64, P],
@@ -310,6 +311,18 @@ def l1_loss_grad(rgb: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | N
                                    C.c_void_p(grad.data_ptr()), C.c_void_p(loss.data_ptr()), _stream(stream)),
            "geer_l1_loss_grad")
     return loss, grad
+
+
+def remap_to_native(beap_img: torch.Tensor, cam, fill=(0.0, 0.0, 0.0), out: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """Native camera image [h, w, 3] from the camera's BEAP render [h, w, 3]."""
+    if out is None:
+        out = torch.empty_like(beap_img)
+    cc = camera_c(cam)
+    f = (C.c_float * 3)(*[float(x) for x in fill])
+    _check(lib().geer_remap_to_native(C.c_void_p(beap_img.data_ptr()), C.byref(cc), f, C.c_void_p(out.data_ptr()),
+                                      _stream(stream)), "geer_remap_to_native")
+    return out
 
 
 class Renderer:

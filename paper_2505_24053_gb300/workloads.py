@@ -240,3 +240,16 @@ def random_pixels(cam: Camera, count: int, seed: int) -> np.ndarray:
 def all_pixels(cam: Camera) -> np.ndarray:
     j, i = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
     return np.stack([i.ravel(), j.ravel()], 1).astype(np.int32)
+
+
+def beap_image(cam: Camera, seed: int) -> np.ndarray:
+    """Seeded synthetic BEAP image [h, w, 3] f32 in [0, 1]: smooth low-frequency
+    waves plus a small per-pixel noise, the input of a BEAP -> native resampling."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    j, i = np.meshgrid(np.arange(cam.height) / cam.height, np.arange(cam.width) / cam.width, indexing="ij")
+    ph = rng.uniform(0, 2 * math.pi, (3, 2))
+    fr = rng.uniform(1.0, 4.0, (3, 2))
+    img = np.stack([0.5 + 0.25 * np.sin(2 * math.pi * fr[c, 0] * i + ph[c, 0])
+                    + 0.2 * np.cos(2 * math.pi * fr[c, 1] * j + ph[c, 1]) for c in range(3)], -1)
+    img += rng.uniform(-0.05, 0.05, img.shape)
+    return np.clip(img, 0.0, 1.0).astype(np.float32)

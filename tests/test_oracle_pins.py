@@ -449,3 +449,52 @@ def test_transmittance_monotone_along_contributors(orc):
         assert np.all((T <= prev + 1e-15) | stopped)
         prev = T
     assert np.allclose(prev, base["T"])
+
+
+REMAP_CAMS = [
+    wl.Camera(wl.PINHOLE, 48, 36, math.radians(70)),
+    wl.Camera(wl.EQUIDISTANT, 40, 40, math.radians(180)),
+    wl.Camera(wl.KANNALA_BRANDT, 64, 48, math.radians(190), k=wl.kb_coeffs(3)),
+    wl.Camera(wl.KANNALA_BRANDT, 40, 30, math.radians(150), k=wl.kb_coeffs(44)),
+]
+
+
+@pytest.mark.parametrize("cam", REMAP_CAMS, ids=["pinhole", "equi180", "kb190", "kb150"])
+def test_native_rays_invert_the_app_e_projection(orc, cam):
+    """App. E projects a ray to (f tan theta, f tan phi) + c (pinhole) or
+    (f phi_d / r)(tan theta, tan phi) + c (fisheye): the oracle's native pixel rays
+    must project back onto their pixel centres."""
+    checked = 0
+    for j in range(cam.height):
+        for i in range(cam.width):
+            d = orc.native_ray(cam, i, j)
+            if d is None or d[2] < math.cos(math.radians(85)):
+                continue
+            assert np.linalg.norm(d) == pytest.approx(1.0, abs=1e-12)
+            xp, yp = orc.project(cam, d)
+            assert xp == pytest.approx(i + 0.5, abs=1e-8) and yp == pytest.approx(j + 0.5, abs=1e-8)
+            checked += 1
+    assert checked > 0.5 * cam.pixels or cam.model != wl.PINHOLE
+
+
+def test_remap_of_a_linear_beap_image_is_exact(orc):
+    """Bilinear interpolation reproduces a BEAP image linear in (column, row): the
+    native image then equals that linear function at each native ray's BEAP
+    coordinate, computed here from atan2 / the BEAP equation directly."""
+    cam = wl.Camera(wl.EQUIDISTANT, 40, 32, math.radians(180))
+    fy = orc.fov_y(cam)
+    fx = float(np.float32(cam.fov_x))
+    jj, ii = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
+    beap = np.stack([0.01 * ii + 0.02 * jj, 0.5 - 0.01 * jj, 0.003 * ii], -1).astype(np.float64)
+    out = orc.remap_to_native(cam, beap.astype(np.float32), fill=(9, 9, 9))
+    for j in range(cam.height):
+        for i in range(cam.width):
+            d = orc.native_ray(cam, i, j)
+            if d is None or d[2] <= 0:
+                continue
+            u = math.atan2(d[0], d[2]) / fx * cam.width + cam.width / 2 - 0.5
+            v = math.atan(d[1] / d[2]) / fy * cam.height + cam.height / 2 - 0.5
+            if not (0 <= u <= cam.width - 1 and 0 <= v <= cam.height - 1):
+                continue
+            exp = [0.01 * u + 0.02 * v, 0.5 - 0.01 * v, 0.003 * u]
+            assert np.allclose(out[j, i], exp, atol=1e-6), (i, j)
