@@ -33,7 +33,7 @@ METRIC = "Mpix/s fwd and fwd+bwd at 1M Gaussians, 180° fisheye; serving p50/p99
 WORKLOAD = "1M Gaussians (cube 4 m, 3-7 m ahead, SH3), Kannala-Brandt 1280x960 190deg, BEAP 16x16 tiles"
 FLOPS_TEST = 43    # per ray-Gaussian evaluation: W d, cross product, two norms, divide, exp arg, exp, t* dot
 FLOPS_BLEND = 10   # per applied contributor: clamp, transmittance update, weight, 3 colour FMAs
-FLOPS_BWD = 96     # per contributor in the backward: recovered T, colour and alpha terms, kappa chain to
+FLOPS_BWD = 96  # per backward contributor: alpha, transmittance and colour terms, dL/dkappa, the d_u and o_u gradients, 16 accumulations
                    # d_u / o_u / W (80) and its share of the warp reduction (16)
 
 

@@ -63,104 +63,124 @@ __device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z
     }
 }
 
-__global__ void __launch_bounds__(128) k_preprocess_bwd(
-    const DevCam *__restrict__ cams, int ncams, const float *__restrict__ mean, const float *__restrict__ scale,
-    const float *__restrict__ quat, const float *__restrict__ opacity, const float *__restrict__ sh, int64_t n, int deg,
-    const uint32_t *__restrict__ count, const GradAcc *__restrict__ gacc, float *__restrict__ d_mean,
-    float *__restrict__ d_scale, float *__restrict__ d_quat, float *__restrict__ d_opacity, float *__restrict__ d_sh) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    const int nb = (deg + 1) * (deg + 1);
-    bool any = false;
-    for (int ci = 0; ci < ncams; ++ci) any |= count[(int64_t)ci * n + g] > 0;
-    if (!any) return;  // not associated with any tile: no gradient
-    float mu[3], s[3], q[4];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) { mu[a] = mean[3 * g + a]; s[a] = scale[3 * g + a]; }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) q[a] = quat[4 * g + a];
-    const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const float w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
-    float R[9];
-    R[0] = 1.0f - 2.0f * (y * y + z * z); R[1] = 2.0f * (x * y - w * z);        R[2] = 2.0f * (x * z + w * y);
-    R[3] = 2.0f * (x * y + w * z);        R[4] = 1.0f - 2.0f * (x * x + z * z); R[5] = 2.0f * (y * z - w * x);
-    R[6] = 2.0f * (x * z - w * y);        R[7] = 2.0f * (y * z + w * x);        R[8] = 1.0f - 2.0f * (x * x + y * y);
-    float dmu[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, dsig = 0.0f;
-    float dsh[48], shc[48];
-    const int nc = 3 * nb;
-    const float *shg = sh + (int64_t)g * nc;
-#pragma unroll
-    for (int k = 0; k < 48; ++k) {
-        dsh[k] = 0.0f;
-        shc[k] = k < nc ? shg[k] : 0.0f;
-    }
+// One block per 64 Gaussians. The block's SH coefficients and its slice of
+// dL/dsh are staged through shared memory with coalesced loads (row stride made
+// odd so that per-thread rows do not share banks); each thread then runs the
+// chain for its Gaussian over the cameras, adds its SH gradient in shared
+// memory, and the block writes dL/dsh back coalesced.
+constexpr int kPBThreads = 64;
 
-    for (int ci = 0; ci < ncams; ++ci) {
-        const int64_t idx = (int64_t)ci * n + g;
-        if (count[idx] == 0) continue;
-        const DevCam &cam = cams[ci];
-        const float4 *ap = reinterpret_cast<const float4 *>(gacc + idx);
-        const float4 a0 = ap[0], a1 = ap[1], a2 = ap[2], a3 = ap[3];
-        const float acc[16] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
-                               a2.x, a2.y, a2.z, a2.w, a3.x, a3.y, a3.z, a3.w};
-        dsig += acc[0];
-        const float *Rc = cam.R;
-        // camera-frame mean and Gaussian axes M = R_cw R
-        float mc[3], M[9];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            mc[i] = Rc[3 * i] * mu[0] + Rc[3 * i + 1] * mu[1] + Rc[3 * i + 2] * mu[2] + cam.t[i];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) M[3 * i + j] = Rc[3 * i] * R[j] + Rc[3 * i + 1] * R[3 + j] + Rc[3 * i + 2] * R[6 + j];
+template <int DEG>
+__global__ void __launch_bounds__(kPBThreads) k_preprocess_bwd(
+    const DevCam *__restrict__ cams, int ncams, const float *__restrict__ mean, const float *__restrict__ scale,
+    const float *__restrict__ quat, const float *__restrict__ sh, int64_t n, const uint32_t *__restrict__ count,
+    const GradAcc *__restrict__ gacc, float *__restrict__ d_mean, float *__restrict__ d_scale,
+    float *__restrict__ d_quat, float *__restrict__ d_opacity, float *__restrict__ d_sh) {
+    constexpr int NB = (DEG + 1) * (DEG + 1), NC = 3 * NB, ST = NC | 1;
+    __shared__ float s_sh[kPBThreads * ST];
+    __shared__ float s_dsh[kPBThreads * ST];
+    const int tid = threadIdx.x;
+    const int64_t g0 = (int64_t)blockIdx.x * kPBThreads;
+    const int nloc = (int)min((int64_t)kPBThreads, n - g0);
+    {
+        const float *src = sh + g0 * NC;
+        const float *dsrc = d_sh ? d_sh + g0 * NC : nullptr;
+        for (int i = tid; i < nloc * NC; i += kPBThreads) {
+            const int gl = i / NC, k = i - gl * NC;
+            s_sh[gl * ST + k] = src[i];
+            if (dsrc) s_dsh[gl * ST + k] = dsrc[i];
         }
-        // W_ki = M_ik / s_k; dL/dW = dW|RC + dL/do_u (-mu_c)^T
-        float dW[9];
+    }
+    __syncthreads();
+    const int64_t g = g0 + tid;
+    bool any = false;
+    if (tid < nloc)
+        for (int ci = 0; ci < ncams; ++ci) any |= count[(int64_t)ci * n + g] > 0;
+    if (any) {  // a Gaussian not associated with any tile has no gradient
+        const float *shc = s_sh + tid * ST;
+        float *dsh = s_dsh + tid * ST;
+        float mu[3], s[3], is[3], q[4];
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a) {
+            mu[a] = mean[3 * g + a];
+            s[a] = scale[3 * g + a];
+            is[a] = 1.0f / s[a];
+        }
 #pragma unroll
-            for (int i = 0; i < 3; ++i) dW[3 * k + i] = acc[4 + 3 * k + i] - acc[13 + k] * mc[i];
-        // dL/dmu_c = -W^T dL/do_u, dL/dmu += R_cw^T dL/dmu_c
-        float dmc[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-            dmc[i] = -(M[3 * i] / s[0] * acc[13] + M[3 * i + 1] / s[1] * acc[14] + M[3 * i + 2] / s[2] * acc[15]);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) dmu[j] += Rc[j] * dmc[0] + Rc[3 + j] * dmc[1] + Rc[6 + j] * dmc[2];
-        // scales and the rotation
-        float dM[9];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float acc_s = 0.0f;
+        for (int a = 0; a < 4; ++a) q[a] = quat[4 * g + a];
+        const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const float w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+        float R[9];
+        R[0] = 1.0f - 2.0f * (y * y + z * z); R[1] = 2.0f * (x * y - w * z);        R[2] = 2.0f * (x * z + w * y);
+        R[3] = 2.0f * (x * y + w * z);        R[4] = 1.0f - 2.0f * (x * x + z * z); R[5] = 2.0f * (y * z - w * x);
+        R[6] = 2.0f * (x * z - w * y);        R[7] = 2.0f * (y * z + w * x);        R[8] = 1.0f - 2.0f * (x * x + y * y);
+        float dmu[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, dsig = 0.0f;
+
+        for (int ci = 0; ci < ncams; ++ci) {
+            const int64_t idx = (int64_t)ci * n + g;
+            if (count[idx] == 0) continue;
+            const DevCam &cam = cams[ci];
+            const float4 *ap = reinterpret_cast<const float4 *>(gacc + idx);
+            const float4 a0 = ap[0], a1 = ap[1], a2 = ap[2], a3 = ap[3];
+            dsig += a0.x;
+            const float *Rc = cam.R;
+            // camera-frame mean and Gaussian axes M = R_cw R (W = S^-1 M^T)
+            float mc[3], M[9];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                acc_s += dW[3 * k + i] * M[3 * i + k];
-                dM[3 * i + k] = dW[3 * k + i] / s[k];
+                mc[i] = Rc[3 * i] * mu[0] + Rc[3 * i + 1] * mu[1] + Rc[3 * i + 2] * mu[2] + cam.t[i];
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    M[3 * i + j] = Rc[3 * i] * R[j] + Rc[3 * i + 1] * R[3 + j] + Rc[3 * i + 2] * R[6 + j];
             }
-            ds[k] -= acc_s / (s[k] * s[k]);
-        }
+            const float dou[3] = {a3.y, a3.z, a3.w};
+            const float dWr[9] = {a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3.x};
+            // o_u = -W mu_c: dL/dW = dW|RC - dL/do_u mu_c^T, dL/dmu_c = -W^T dL/do_u, dL/dmu += R_cw^T dL/dmu_c
+            float dW[9], dmc[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) dR[3 * j + k] += Rc[j] * dM[k] + Rc[3 + j] * dM[3 + k] + Rc[6 + j] * dM[6 + k];
-        // colour: SH at the world direction from the camera centre
-        const float vx = mu[0] - cam.o[0], vy = mu[1] - cam.o[1], vz = mu[2] - cam.o[2];
-        const float vn = sqrtf(vx * vx + vy * vy + vz * vz);
-        const float ux = vx / vn, uy = vy / vn, uz = vz / vn;
-        float Y[16], dY[16][3];
-        sh_basis_grad(deg, ux, uy, uz, Y, dY);
-        float dLdc[3];
+                for (int i = 0; i < 3; ++i) dW[3 * k + i] = dWr[3 * k + i] - dou[k] * mc[i];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float raw = 0.5f;
+            for (int i = 0; i < 3; ++i)
+                dmc[i] = -(M[3 * i] * is[0] * dou[0] + M[3 * i + 1] * is[1] * dou[1] + M[3 * i + 2] * is[2] * dou[2]);
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < nb) raw += Y[k] * shc[3 * k + ch];
-            dLdc[ch] = raw > 0.0f ? acc[1 + ch] : 0.0f;
-        }
-        float ddir[3] = {0, 0, 0};
+            for (int j = 0; j < 3; ++j) dmu[j] += Rc[j] * dmc[0] + Rc[3 + j] * dmc[1] + Rc[6 + j] * dmc[2];
+            // W_ki = M_ik / s_k: scales and the rotation
+            float dM[9];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            if (k < nb) {
+            for (int k = 0; k < 3; ++k) {
+                float acc_s = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    acc_s += dW[3 * k + i] * M[3 * i + k];
+                    dM[3 * i + k] = dW[3 * k + i] * is[k];
+                }
+                ds[k] -= acc_s * is[k] * is[k];
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    dR[3 * j + k] += Rc[j] * dM[k] + Rc[3 + j] * dM[3 + k] + Rc[6 + j] * dM[6 + k];
+            // colour: SH at the world direction from the camera centre
+            const float vx = mu[0] - cam.o[0], vy = mu[1] - cam.o[1], vz = mu[2] - cam.o[2];
+            const float vn = sqrtf(vx * vx + vy * vy + vz * vz);
+            const float ux = vx / vn, uy = vy / vn, uz = vz / vn;
+            float Y[16], dY[16][3];
+            sh_basis_grad(DEG, ux, uy, uz, Y, dY);
+            const float drgb[3] = {a0.y, a0.z, a0.w};
+            float dLdc[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float raw = 0.5f;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) raw += Y[k] * shc[3 * k + ch];
+                dLdc[ch] = raw > 0.0f ? drgb[ch] : 0.0f;
+            }
+            float ddir[3] = {0, 0, 0};
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
                 float wk = 0.0f;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
@@ -171,49 +191,40 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(
                 ddir[1] += wk * dY[k][1];
                 ddir[2] += wk * dY[k][2];
             }
+            const float dp = ddir[0] * ux + ddir[1] * uy + ddir[2] * uz;
+            dmu[0] += (ddir[0] - ux * dp) / vn;
+            dmu[1] += (ddir[1] - uy * dp) / vn;
+            dmu[2] += (ddir[2] - uz * dp) / vn;
         }
-        const float dp = ddir[0] * ux + ddir[1] * uy + ddir[2] * uz;
-        dmu[0] += (ddir[0] - ux * dp) / vn;
-        dmu[1] += (ddir[1] - uy * dp) / vn;
-        dmu[2] += (ddir[2] - uz * dp) / vn;
-    }
-    // unit-quaternion polynomial R(w, x, y, z) (App. C.4) then the normalisation
-    const float gw = 2.0f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    const float gx = 2.0f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.0f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
-                             2.0f * x * dR[8]);
-    const float gy = 2.0f * (-2.0f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
-                             2.0f * y * dR[8]);
-    const float gz = 2.0f * (-2.0f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.0f * z * dR[4] + y * dR[5] +
-                             x * dR[6] + y * dR[7]);
-    const float proj = gw * w + gx * x + gy * y + gz * z;
-    if (d_quat) {
-        d_quat[4 * g + 0] += (gw - w * proj) / qn;
-        d_quat[4 * g + 1] += (gx - x * proj) / qn;
-        d_quat[4 * g + 2] += (gy - y * proj) / qn;
-        d_quat[4 * g + 3] += (gz - z * proj) / qn;
-    }
-    if (d_mean)
+        // unit-quaternion polynomial R(w, x, y, z) (App. C.4) then the normalisation
+        const float gw = 2.0f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+        const float gx = 2.0f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.0f * x * dR[4] - w * dR[5] + z * dR[6] +
+                                 w * dR[7] - 2.0f * x * dR[8]);
+        const float gy = 2.0f * (-2.0f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
+                                 z * dR[7] - 2.0f * y * dR[8]);
+        const float gz = 2.0f * (-2.0f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.0f * z * dR[4] +
+                                 y * dR[5] + x * dR[6] + y * dR[7]);
+        const float proj = gw * w + gx * x + gy * y + gz * z;
+        if (d_quat) {
+            d_quat[4 * g + 0] += (gw - w * proj) / qn;
+            d_quat[4 * g + 1] += (gx - x * proj) / qn;
+            d_quat[4 * g + 2] += (gy - y * proj) / qn;
+            d_quat[4 * g + 3] += (gz - z * proj) / qn;
+        }
+        if (d_mean)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) d_mean[3 * g + a] += dmu[a];
-    if (d_scale)
+            for (int a = 0; a < 3; ++a) d_mean[3 * g + a] += dmu[a];
+        if (d_scale)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) d_scale[3 * g + a] += ds[a];
-    if (d_opacity) d_opacity[g] += dsig;
+            for (int a = 0; a < 3; ++a) d_scale[3 * g + a] += ds[a];
+        if (d_opacity) d_opacity[g] += dsig;
+    }
+    __syncthreads();
     if (d_sh) {
-        float *dst = d_sh + (int64_t)g * nc;
-        if ((nc & 3) == 0) {
-            float4 *d4 = reinterpret_cast<float4 *>(dst);
-#pragma unroll
-            for (int i = 0; i < 12; ++i)
-                if (4 * i < nc) {
-                    float4 v = d4[i];
-                    v.x += dsh[4 * i]; v.y += dsh[4 * i + 1]; v.z += dsh[4 * i + 2]; v.w += dsh[4 * i + 3];
-                    d4[i] = v;
-                }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 48; ++k)
-                if (k < nc) dst[k] += dsh[k];
+        float *dst = d_sh + g0 * NC;
+        for (int i = tid; i < nloc * NC; i += kPBThreads) {
+            const int gl = i / NC, k = i - gl * NC;
+            dst[i] = s_dsh[gl * ST + k];
         }
     }
 }
@@ -247,11 +258,18 @@ __global__ void __launch_bounds__(256) k_l1_grad(const float *__restrict__ pred,
 cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians *g, float *d_mean, float *d_scale,
                                   float *d_quat, float *d_opacity, float *d_sh, cudaStream_t s) {
     if (g->n == 0) return cudaSuccess;
-    const int threads = 128;
-    const int64_t blocks = (g->n + threads - 1) / threads;
-    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, s>>>(ws->d_cams, ws->n_cams, g->mean, g->scale, g->quat,
-                                                          g->opacity, g->sh, g->n, g->sh_degree, ws->d_count,
-                                                          ws->d_gacc, d_mean, d_scale, d_quat, d_opacity, d_sh);
+    const unsigned blocks = (unsigned)((g->n + kPBThreads - 1) / kPBThreads);
+#define GEER_PB_LAUNCH(D)                                                                                      \
+    k_preprocess_bwd<D><<<blocks, kPBThreads, 0, s>>>(ws->d_cams, ws->n_cams, g->mean, g->scale, g->quat, g->sh, \
+                                                      g->n, ws->d_count, ws->d_gacc, d_mean, d_scale, d_quat,   \
+                                                      d_opacity, d_sh)
+    switch (g->sh_degree) {
+        case 0: GEER_PB_LAUNCH(0); break;
+        case 1: GEER_PB_LAUNCH(1); break;
+        case 2: GEER_PB_LAUNCH(2); break;
+        default: GEER_PB_LAUNCH(3); break;
+    }
+#undef GEER_PB_LAUNCH
     return cudaGetLastError();
 }
 

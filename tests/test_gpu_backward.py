@@ -129,12 +129,19 @@ def test_autograd_and_accumulation(geer):
     r2 = geer.Renderer([cam], scene.n, scene.sh_degree)
     r2.forward(g)
     direct = r2.backward(g, w)
+
+    def close(a, b, k):
+        # the float atomics sum in a run-dependent order: equal up to rounding
+        # relative to the block's scale (an entry may itself be a cancelling sum)
+        scale = float(b.abs().max())
+        assert float((a - b).abs().max()) <= 1e-5 * scale + 1e-9, (k, float((a - b).abs().max()), scale)
+
     for p, k in zip(params, BLOCKS):
-        assert torch.allclose(p.grad, direct[k], rtol=1e-4, atol=1e-7), k
+        close(p.grad, direct[k], k)
     # geer_render_bwd accumulates
     r2.backward(g, w, direct)
     for p, k in zip(params, BLOCKS):
-        assert torch.allclose(direct[k], 2 * p.grad, rtol=1e-4, atol=1e-7), k
+        close(direct[k], 2 * p.grad, k)
 
 
 def _sparse_dl(cams, per_cam, seed):
