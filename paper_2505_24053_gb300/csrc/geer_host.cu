@@ -231,6 +231,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_db = L.take(sizeof(uint32_t) * kRadix);
     size_t o_misc = L.take(sizeof(uint32_t) * kMiscCount);
     size_t o_tr = L.take((sizeof(uint2) + sizeof(uint32_t)) * c.tiles);
+    size_t o_to = L.take(sizeof(uint32_t) * c.tiles);
     size_t o_last = L.take(sizeof(uint32_t) * c.pixels);
     size_t o_tfin = L.take(sizeof(float) * c.pixels);
     size_t o_ev = L.take(sizeof(uint2) * c.pixels);
@@ -259,6 +260,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_digit_base = reinterpret_cast<uint32_t *>(base + o_db);
         ws->d_misc = reinterpret_cast<uint32_t *>(base + o_misc);
         ws->d_tile_range = reinterpret_cast<uint2 *>(base + o_tr);
+        ws->d_tile_order = reinterpret_cast<uint32_t *>(base + o_to);
         ws->d_last = reinterpret_cast<uint32_t *>(base + o_last);
         ws->d_Tfin = reinterpret_cast<float *>(base + o_tfin);
         ws->d_evals = reinterpret_cast<uint2 *>(base + o_ev);

@@ -128,6 +128,7 @@ struct geer_workspace {
     uint32_t *d_digit_base; // [kRadix]
     uint32_t *d_misc;       // [kMiscCount]
     uint2 *d_tile_range;    // [cap_tiles] tile [start, end), followed by [cap_tiles] u32 pair counts
+    uint32_t *d_tile_order; // [cap_tiles] tiles by descending pair count: the render blocks' schedule
     uint32_t *d_last;       // [cap_pixels] list entries walked per ray
     float *d_Tfin;          // [cap_pixels] final transmittance (for the backward)
     uint2 *d_evals;         // [cap_pixels] ray-Gaussian evaluations executed / contributors applied

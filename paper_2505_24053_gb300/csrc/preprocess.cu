@@ -605,15 +605,37 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
 // IdentifyFrustumRanges from the per-tile pair counts (one block): the
 // exclusive scan over tiles gives each tile's [start, end) in the tile-sorted
 // pairs.
+// Render schedule bucket of a tile with c pairs: larger counts first, four
+// buckets per octave, empty tiles last.
+constexpr int kOrderBuckets = 129;
+__device__ __forceinline__ int order_bucket(uint32_t c) {
+    if (c == 0) return kOrderBuckets - 1;
+    const int lg = 31 - __clz(c);
+    const int sub = (int)((c >> (lg >= 2 ? lg - 2 : 0)) & 3u);
+    return 127 - (lg * 4 + (lg >= 2 ? sub : 0));
+}
+
+// One block: tile ranges from the per-tile pair counts (exclusive scan), and the
+// order in which the render blocks take the tiles: by descending pair count
+// (bucketed), so that the costliest tiles start first and the grid does not end
+// on a tail of heavy tiles. The order within a bucket is arbitrary.
 __global__ void __launch_bounds__(1024) k_tile_offsets(const uint32_t *__restrict__ tile_count, int ntiles,
-                                                       const uint32_t *__restrict__ misc, uint2 *__restrict__ tile_range) {
+                                                       const uint32_t *__restrict__ misc, uint2 *__restrict__ tile_range,
+                                                       uint32_t *__restrict__ tile_order) {
     __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t hist[kOrderBuckets];
     if (misc[kMiscStatus] & kStatusCapacity) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int i = t; i < kOrderBuckets; i += 1024) hist[i] = 0u;
+    __syncthreads();
     const int chunk = (ntiles + 1023) / 1024;
     const int b = t * chunk, e = min(ntiles, b + chunk);
     uint32_t s = 0;
-    for (int i = b; i < e; ++i) s += tile_count[i];
+    for (int i = b; i < e; ++i) {
+        const uint32_t c = tile_count[i];
+        s += c;
+        atomicAdd(&hist[order_bucket(c)], 1u);
+    }
     uint32_t v = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -631,12 +653,21 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const uint32_t *__restric
         }
         warp_tot[lane] = w;
     }
+    if (t == 32) {  // exclusive scan of the bucket sizes (129 entries, one thread)
+        uint32_t run = 0;
+        for (int i = 0; i < kOrderBuckets; ++i) {
+            const uint32_t h = hist[i];
+            hist[i] = run;
+            run += h;
+        }
+    }
     __syncthreads();
     uint32_t run = v - s + (warp > 0 ? warp_tot[warp - 1] : 0u);
     for (int i = b; i < e; ++i) {
         const uint32_t c = tile_count[i];
         tile_range[i] = make_uint2(run, run + c);
         run += c;
+        tile_order[atomicAdd(&hist[order_bucket(c)], 1u)] = (uint32_t)i;
     }
 }
 
@@ -690,7 +721,7 @@ cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    k_tile_offsets<<<1, 1024, 0, s>>>(tile_count, (int)ws->n_tiles, ws->d_misc, ws->d_tile_range);
+    k_tile_offsets<<<1, 1024, 0, s>>>(tile_count, (int)ws->n_tiles, ws->d_misc, ws->d_tile_range, ws->d_tile_order);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,11 @@
 // render.cu -- the per-ray render (Algorithm 1 per-CSF loop: Cano_Ray, Dist,
 // BlendInOrder) and its backward (App. C, RenderCUDA stage).
 //
-// One block per BEAP tile (a camera sub-frustum) of 16 x 16 rays, one thread per
-// ray. The tile's depth-sorted Gaussian records are staged through shared
-// memory in batches of 256 and every ray walks them front to back with the
-// closed-form ray integral (Sec. 3.1):
+// A BEAP tile (a camera sub-frustum) of 16 x 16 rays is processed by 16 / ROWS
+// blocks of ROWS x 16 threads, one thread per ray, tiles taken in the order of
+// descending pair count (the costliest first); each block stages the tile's
+// depth-sorted Gaussian records through shared memory in batches of BATCH and
+// every ray walks them front to back with the closed-form ray integral (Sec. 3.1):
 //   d_u = W d, m_u = o_u x d_u, kappa = |m_u|^2 / |d_u|^2,
 //   alpha = min(alpha_max, sigma exp(-kappa / 2)),
 // skipping alpha < alpha_min and Gaussians whose closest approach lies behind
@@ -15,11 +16,21 @@
 namespace geer {
 namespace {
 
-constexpr int kBatch = kTilePix;
-// Rays per thread in the backward. Measured on workload 3 (1M Gaussians, KB
-// 1280x960): 1 -> 0.773 ms, 2 -> 0.777 ms, 4 -> 1.07 ms (fewer resident warps and a
-// wider warp footprint outweigh the shared record loads and reductions).
-constexpr int kBwdRaysPerThread = 1;
+#ifndef GEER_FWD_ROWS
+#define GEER_FWD_ROWS 16
+#endif
+#ifndef GEER_FWD_BATCH
+#define GEER_FWD_BATCH 256
+#endif
+#ifndef GEER_BWD_ROWS
+#define GEER_BWD_ROWS 8
+#endif
+#ifndef GEER_BWD_BATCH
+#define GEER_BWD_BATCH 128
+#endif
+#ifndef GEER_BWD_MINB
+#define GEER_BWD_MINB 8
+#endif
 constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -log2(e) / 2
 
 __device__ __forceinline__ int find_cam(const DevCam *cams, int ncams, int t) {
@@ -56,19 +67,22 @@ __device__ __forceinline__ Eval evaluate(const float4 &a, const float4 &b, const
     return v;
 }
 
-__global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
-                                                        const float2 *__restrict__ ptab,
-                                                        const uint2 *__restrict__ tile_range,
-                                                        const uint32_t *__restrict__ vals,
-                                                        const Record *__restrict__ rec,
-                                                        const uint32_t *__restrict__ misc, Params p,
-                                                        float *__restrict__ rgb, float *__restrict__ Tout,
-                                                        float *__restrict__ Tfin, uint32_t *__restrict__ last_out,
-                                                        uint2 *__restrict__ evals) {
-    __shared__ float4 s_rec[kBatch * 4];
+template <int ROWS, int BATCH>
+__global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
+                                                            const float2 *__restrict__ ptab,
+                                                            const uint2 *__restrict__ tile_range,
+                                                            const uint32_t *__restrict__ tile_order,
+                                                            const uint32_t *__restrict__ vals,
+                                                            const Record *__restrict__ rec,
+                                                            const uint32_t *__restrict__ misc, Params p,
+                                                            float *__restrict__ rgb, float *__restrict__ Tout,
+                                                            float *__restrict__ Tfin, uint32_t *__restrict__ last_out,
+                                                            uint2 *__restrict__ evals) {
+    constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
+    __shared__ float4 s_rec[BATCH * 4];
     __shared__ int s_cam;
     if (misc[kMiscStatus] & kStatusCapacity) return;
-    const int t = blockIdx.x;
+    const int t = (int)tile_order[blockIdx.x / kParts], part = blockIdx.x % kParts;
     const int tid = threadIdx.x;
     if (tid == 0) s_cam = find_cam(cams, ncams, t);
     __syncthreads();
@@ -77,7 +91,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
     if (lt >= cam.tiles_x * cam.tiles_y) return;  // padding tile of a camera slot
     const int cx = lt % cam.tiles_x, cy = lt / cam.tiles_x;
     const int x = cx * kTile + (tid & (kTile - 1));
-    const int y = cy * kTile + (tid / kTile);
+    const int y = cy * kTile + part * ROWS + (tid / kTile);
     const bool inside = x < cam.width && y < cam.height;
 
     float dx = 0.0f, dy = 0.0f, dz = 1.0f;
@@ -94,16 +108,15 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
     uint32_t last = 0, n_eval = 0, n_applied = 0;
     bool done = !inside;
 
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += kBatch) {
-        if (__syncthreads_count(done) == kTilePix) break;
-        const uint32_t i = b0 + tid;
-        if (i < range.y) {
-            const float4 *src = reinterpret_cast<const float4 *>(rec + vals[i]);
+    for (uint32_t b0 = range.x; b0 < range.y; b0 += BATCH) {
+        if (__syncthreads_count(done) == kThreads) break;
+        const int cnt = (int)min((uint32_t)BATCH, range.y - b0);
+        for (int r = tid; r < cnt; r += kThreads) {
+            const float4 *src = reinterpret_cast<const float4 *>(rec + vals[b0 + r]);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) s_rec[tid * 4 + k] = src[k];
+            for (int k = 0; k < 4; ++k) s_rec[r * 4 + k] = src[k];
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)kBatch, range.y - b0);
         if (!done) {
             for (int j = 0; j < cnt; ++j) {
                 ++n_eval;
@@ -113,8 +126,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
                 const float4 e = s_rec[j * 4 + 3];  // log2 sigma, r, g, b
                 const Eval v = evaluate(a, b, c, e, dx, dy, dz, log2_amin);
                 if (!v.hit) continue;
-                const float arg = v.arg;
-                const float alpha = fminf(exp2f(arg), p.alpha_max);
+                const float alpha = fminf(exp2f(v.arg), p.alpha_max);
                 const float Tn = T * (1.0f - alpha);
                 if (Tn < p.T_min) {
                     done = true;
@@ -149,12 +161,10 @@ __global__ void __launch_bounds__(kTilePix) k_render_fwd(const DevCam *__restric
 // dL/dsigma, dL/dc, dL/dW through d_u (outer product with the ray direction)
 // and dL/do_u (the PreprocessCUDA part chains o_u = -W mu_c).
 //
-// Each thread owns PPT vertically adjacent rays of the tile, so a warp covers a
-// 16 x 2*PPT block of rays: one record load and one reduction serve PPT rays.
-// The 16 values are summed over the thread's rays in registers, over the warp by
-// a shuffle reduce-scatter, over the block in shared memory, then added to
-// global memory with one set of float4 atomics per (tile, Gaussian). A warp
-// skips list entries beyond the last contributor of all its rays.
+// The 16 values are reduced over the warp (reduce-scatter by shuffles), over the
+// block in shared memory, then added to global memory with one set of float4
+// atomics per (block, Gaussian). A warp skips list entries beyond the last
+// contributor of its rays.
 struct BwdRay {
     float dx, dy, dz, g0, g1, g2, T, S0, S1, S2;
     uint32_t last;
@@ -202,24 +212,25 @@ __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const f
     }
 }
 
-template <int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT) k_render_bwd(const DevCam *__restrict__ cams, int ncams,
-                                                              const float2 *__restrict__ ptab,
-                                                              const uint2 *__restrict__ tile_range,
-                                                              const uint32_t *__restrict__ vals,
-                                                              const Record *__restrict__ rec,
-                                                              const uint32_t *__restrict__ misc, Params p,
-                                                              const float *__restrict__ dL_drgb,
-                                                              const float *__restrict__ Tfin,
-                                                              const uint32_t *__restrict__ last_in,
-                                                              GradAcc *__restrict__ gacc) {
-    constexpr int kThreads = kTilePix / PPT;
-    __shared__ float4 s_rec[kBatch * 4];
-    __shared__ float s_acc[kBatch][17];
+template <int ROWS, int BATCH>
+__global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(const DevCam *__restrict__ cams, int ncams,
+                                                            const float2 *__restrict__ ptab,
+                                                            const uint2 *__restrict__ tile_range,
+                                                            const uint32_t *__restrict__ tile_order,
+                                                            const uint32_t *__restrict__ vals,
+                                                            const Record *__restrict__ rec,
+                                                            const uint32_t *__restrict__ misc, Params p,
+                                                            const float *__restrict__ dL_drgb,
+                                                            const float *__restrict__ Tfin,
+                                                            const uint32_t *__restrict__ last_in,
+                                                            GradAcc *__restrict__ gacc) {
+    constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
+    __shared__ float4 s_rec[BATCH * 4];
+    __shared__ float s_acc[BATCH][17];
     __shared__ uint32_t s_last;
     __shared__ int s_cam;
     if (misc[kMiscStatus] & kStatusCapacity) return;
-    const int t = blockIdx.x;
+    const int t = (int)tile_order[blockIdx.x / kParts], part = blockIdx.x % kParts;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
         s_cam = find_cam(cams, ncams, t);
@@ -231,45 +242,38 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_render_bwd(const DevCam *__r
     if (lt >= cam.tiles_x * cam.tiles_y) return;  // padding tile of a camera slot
     const int cx = lt % cam.tiles_x, cy = lt / cam.tiles_x;
     const int x = cx * kTile + (tid & (kTile - 1));
-    const int y0 = cy * kTile + (tid / kTile) * PPT;
-    BwdRay ray[PPT];
-    uint32_t my_last = 0;
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        BwdRay &r = ray[q];
-        const int y = y0 + q;
-        r.dx = 0.0f; r.dy = 0.0f; r.dz = 1.0f;
-        r.g0 = r.g1 = r.g2 = 0.0f;
-        r.T = 1.0f;
-        r.last = 0;
-        if (x < cam.width && y < cam.height) {
-            const float2 th = ptab[cam.pcol_off + x];
-            const float2 ph = ptab[cam.prow_off + y];
-            r.dx = th.x * ph.y;
-            r.dy = th.y * ph.x;
-            r.dz = th.y * ph.y;
-            const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
-            r.g0 = dL_drgb[3 * pix + 0];
-            r.g1 = dL_drgb[3 * pix + 1];
-            r.g2 = dL_drgb[3 * pix + 2];
-            r.T = Tfin[pix];
-            r.last = last_in[pix];
-        }
-        // colour composited behind the current contributor (starts with the background)
-        r.S0 = r.T * cam.bg[0];
-        r.S1 = r.T * cam.bg[1];
-        r.S2 = r.T * cam.bg[2];
-        my_last = max(my_last, r.last);
+    const int y = cy * kTile + part * ROWS + (tid / kTile);
+    BwdRay ray;
+    ray.dx = 0.0f; ray.dy = 0.0f; ray.dz = 1.0f;
+    ray.g0 = ray.g1 = ray.g2 = 0.0f;
+    ray.T = 1.0f;
+    ray.last = 0;
+    if (x < cam.width && y < cam.height) {
+        const float2 th = ptab[cam.pcol_off + x];
+        const float2 ph = ptab[cam.prow_off + y];
+        ray.dx = th.x * ph.y;
+        ray.dy = th.y * ph.x;
+        ray.dz = th.y * ph.y;
+        const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
+        ray.g0 = dL_drgb[3 * pix + 0];
+        ray.g1 = dL_drgb[3 * pix + 1];
+        ray.g2 = dL_drgb[3 * pix + 2];
+        ray.T = Tfin[pix];
+        ray.last = last_in[pix];
     }
-    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, my_last);
+    // colour composited behind the current contributor (starts with the background)
+    ray.S0 = ray.T * cam.bg[0];
+    ray.S1 = ray.T * cam.bg[1];
+    ray.S2 = ray.T * cam.bg[2];
+    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, ray.last);
     if (lane == 0) atomicMax(&s_last, warp_last);
     const uint2 range = tile_range[t];
     const float log2_amin = log2f(p.alpha_min);
     __syncthreads();
     const uint32_t block_last = s_last;
 
-    for (int32_t b_end = (int32_t)block_last; b_end > 0; b_end -= kBatch) {
-        const int32_t b_start = max(0, b_end - kBatch);
+    for (int32_t b_end = (int32_t)block_last; b_end > 0; b_end -= BATCH) {
+        const int32_t b_start = max(0, b_end - BATCH);
         const int cnt = b_end - b_start;
         for (int r = tid; r < cnt; r += kThreads) {
             const float4 *src = reinterpret_cast<const float4 *>(rec + vals[range.x + b_start + r]);
@@ -281,17 +285,17 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_render_bwd(const DevCam *__r
         const int jj_top = min(cnt, (int)warp_last - b_start) - 1;  // warp-uniform
         for (int jj = jj_top; jj >= 0; --jj) {
             const uint32_t j = (uint32_t)(b_start + jj);
-            const float4 a = s_rec[jj * 4 + 0];
-            const float4 b = s_rec[jj * 4 + 1];
-            const float4 c = s_rec[jj * 4 + 2];
-            const float4 e = s_rec[jj * 4 + 3];
             float gv[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) gv[k] = 0.0f;
             bool contrib = false;
-#pragma unroll
-            for (int q = 0; q < PPT; ++q)
-                if (j < ray[q].last) ray_gradient(ray[q], a, b, c, e, log2_amin, p.alpha_max, gv, contrib);
+            if (j < ray.last) {
+                const float4 a = s_rec[jj * 4 + 0];
+                const float4 b = s_rec[jj * 4 + 1];
+                const float4 c = s_rec[jj * 4 + 2];
+                const float4 e = s_rec[jj * 4 + 3];
+                ray_gradient(ray, a, b, c, e, log2_amin, p.alpha_max, gv, contrib);
+            }
             if (__any_sync(0xffffffffu, contrib)) {
                 // warp reduce-scatter of the 16 values: lane l ends with the sum of value (l >> 1)
 #pragma unroll
@@ -348,8 +352,9 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_render_bwd(const DevCam *__r
 
 cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_final, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
-    k_render_fwd<<<(unsigned)ws->n_tiles, kTilePix, 0, s>>>(
-        ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_range, ws->d_vals[ws->sorted_buf], ws->d_rec, ws->d_misc,
+    constexpr int R = GEER_FWD_ROWS, B = GEER_FWD_BATCH;
+    k_render_fwd<R, B><<<(unsigned)(ws->n_tiles * (kTile / R)), R * kTile, 0, s>>>(
+        ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_range, ws->d_tile_order, ws->d_vals[ws->sorted_buf], ws->d_rec, ws->d_misc,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, rgb, T_final,
         ws->d_Tfin, ws->d_last, ws->d_evals);
     return cudaGetLastError();
@@ -357,9 +362,9 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
 
 cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
-    constexpr int kPPT = kBwdRaysPerThread;
-    k_render_bwd<kPPT><<<(unsigned)ws->n_tiles, kTilePix / kPPT, 0, s>>>(
-        ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_range, ws->d_vals[ws->sorted_buf], ws->d_rec, ws->d_misc,
+    constexpr int R = GEER_BWD_ROWS, B = GEER_BWD_BATCH;
+    k_render_bwd<R, B><<<(unsigned)(ws->n_tiles * (kTile / R)), R * kTile, 0, s>>>(
+        ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_range, ws->d_tile_order, ws->d_vals[ws->sorted_buf], ws->d_rec, ws->d_misc,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, dL_drgb,
         ws->d_Tfin, ws->d_last, ws->d_gacc);
     return cudaGetLastError();
