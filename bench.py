@@ -261,9 +261,10 @@ def run(args):
         t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
-    st, pairs = ws.device_status()
+    st, _ = ws.device_status()
     if st != geer.OK:
         raise RuntimeError(f"device status after timed steps: {geer.status_string(st)}")
+    pairs, super_pairs = ws.pair_counts()
     stage_ms = {k: v[0] for k, v in ws.stage_times().items()}  # mean of the last 64 timed steps
     ws.enable_timing(False)
     step_ms = [e[0].elapsed_time(e[4]) for e in evs]
@@ -328,14 +329,15 @@ def run(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     n_items = scene.n  # one camera
     live = n_items  # live items <= items; equal here (every Gaussian of the cube is in the 190 deg view)
-    tile_passes_ = math.ceil(max(1, math.ceil(math.log2(math.ceil(cam.width / 16) * math.ceil(cam.height / 16)))) / 8)
+    sort_passes = ws.sort_passes()
     sh_bytes = 4 * 3 * (scene.sh_degree + 1) ** 2
     g_bytes = 4 * (3 + 3 + 4 + 1) + sh_bytes
     work = {
         "preprocess": ("hbm", scene.n * g_bytes + n_items * (64 + 16 + 4 + 4)),
         "depth_sort": ("hbm", 4 * 20 * live),
-        "duplicate": ("hbm", live * (4 + 4 + 16) + int(pairs) * 8),
-        "tile_sort": ("hbm", tile_passes_ * 20 * int(pairs)),
+        # per live item: id, tile count and ranges read; 8 B per (super-tile, item) pair written
+        "duplicate": ("hbm", live * (4 + 4 + 16) + int(super_pairs) * 8),
+        "tile_sort": ("hbm", sort_passes * 20 * int(super_pairs)),
         "render_fwd": ("alu", FLOPS_TEST * evals + FLOPS_BLEND * applied),
         "render_bwd": ("alu", FLOPS_TEST * walked + FLOPS_BWD * applied),
         "preprocess_bwd": ("hbm", scene.n * g_bytes * 3 + n_items * 64),
@@ -380,10 +382,10 @@ def run(args):
                                else f"copy bandwidth, {peak_src}",
                 "work": {"evaluations": evals, "applied": applied, "walked_back": walked}}
     tiles = math.ceil(cam.width / 16) * math.ceil(cam.height / 16)
-    tile_passes = math.ceil(max(1, math.ceil(math.log2(tiles))) / 8)
-    # preprocess, scan, compact, 4 depth passes x 3, gather, scan, duplicate, tile offsets,
-    # tile passes x 3, render
-    launches_per_step = 20 + 3 * tile_passes + (3 if have_bwd else 0)
+    # preprocess, live scan, compact, 4 depth passes x 3, gather, 2 scans, emit, offsets,
+    # super-tile sort passes x 3, sorted ranges, render fwd (+ L1 gradient, backward order, render bwd,
+    # preprocess bwd)
+    launches_per_step = 22 + 3 * sort_passes + (4 if have_bwd else 0)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
@@ -391,7 +393,8 @@ def run(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.workload == 3 else f"workload {args.workload}",
                    "pass": "fwd+bwd" if have_bwd else "fwd", "gaussians": scene.n,
-                   "pixels_per_gpu": pixels, "pairs": int(pairs), "parallelism": f"replicas x{world}",
+                   "pixels_per_gpu": pixels, "pairs": int(pairs), "super_pairs": int(super_pairs),
+                   "parallelism": f"replicas x{world}",
                    "l2": "512 MB buffer written between timed steps (outside step events); inputs 236 MB > L2"},
         "fwd_only": {"value": fwd_value, "unit": "Mpix/s", "ms": statistics.mean(fwd_ms)},
         "stages_ms": {"preprocess": statistics.mean(prep_ms), "bin_sort": statistics.mean(sort_ms),

@@ -142,11 +142,16 @@ geer_status geer_set_camera_slots(geer_workspace *ws, const geer_camera *cams, i
  * geer_render_bwd) have run. */
 geer_status geer_preprocess(geer_workspace *ws, const geer_gaussians *g, void *stream);
 
-/* DuplicateWithKeys, SortByKeys, IdentifyFrustumRanges (Algorithm 1): emit one
- * (key = global tile << 32 | depth bits, value = camera * n + gaussian) pair
- * per associated tile, radix-sort them (stable, so equal depths keep Gaussian
- * order) and build each tile's [start, end). If pairs_needed is non-NULL the
- * call synchronises `stream` to read the pair count, writes it to
+/* DuplicateWithKeys, SortByKeys, IdentifyFrustumRanges (Algorithm 1), with the
+ * Gaussians ordered by depth first: the live (camera, Gaussian) items are
+ * sorted by depth (ties by item index), then each item emits one (super-tile,
+ * item) pair per super-tile (S x S tiles, S in 4..8) holding an associated tile,
+ * in depth order, and a stable radix sort by super-tile id yields every
+ * super-tile's depth-ordered list. Each tile's list (its super-tile's list
+ * filtered by the association test, i.e. its (tile, Gaussian) pairs in depth
+ * order) is read by the render kernels as far as their rays walk it. The pair
+ * capacity bounds the number of (super-tile, Gaussian) pairs. If pairs_needed is
+ * non-NULL the call synchronises `stream` to read that count, writes it to
  * *pairs_needed and returns GEER_ERR_CAPACITY without sorting when it exceeds
  * the capacity. If NULL the call stays asynchronous; an overflow is then
  * recorded in the device status word and the render calls produce nothing. */
@@ -183,8 +188,13 @@ geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *st
 geer_status geer_debug_preprocess(geer_workspace *ws, uint16_t *ranges, uint32_t *counts, uint32_t *keys,
                                   uint8_t *cull, void *stream);
 
-/* Debug/inspection (synchronous): copy up to cap sorted pairs (keys u64,
- * values u32) into HOST buffers; *count receives the pair count. */
+/* Debug/inspection (synchronous): build every tile's full list and copy up to
+ * cap of the (tile, Gaussian) pairs, ordered by tile then depth (keys u64 =
+ * tile << 32 | depth bits, values u32 = camera * n + gaussian), into HOST
+ * buffers; *count receives the number P of (tile, Gaussian) associations.
+ * Returns GEER_ERR_CUDA if the lists do not hold exactly P pairs and
+ * GEER_ERR_CAPACITY if P exceeds the workspace's pair capacity. Leaves the
+ * render state intact. */
 geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *values, int64_t cap, int64_t *count,
                              void *stream);
 
@@ -194,6 +204,12 @@ geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *value
  * float). rgb, target, dL_drgb: device [n_values] f32. */
 geer_status geer_l1_loss_grad(const float *rgb, const float *target, int64_t n_values, float *dL_drgb, float *loss,
                               void *stream);
+
+/* Measurement (synchronous): after geer_bin_sort, the number of (tile,
+ * Gaussian) associations P, of (super-tile, Gaussian) pairs sorted, and the
+ * radix passes of that sort (any pointer may be NULL). */
+geer_status geer_pair_counts(geer_workspace *ws, int64_t *tile_pairs, int64_t *super_pairs, int32_t *sort_passes,
+                             void *stream);
 
 /* Measurement (synchronous): totals over all rays of the last geer_render_fwd
  * of the ray-Gaussian evaluations executed (list entries walked up to early
@@ -237,8 +253,9 @@ geer_status geer_remap_to_native(const float *beap_rgb, const geer_camera *cam, 
  * of geer_preprocess + geer_bin_sort + geer_render_fwd for one camera.
  *
  * Limits: n <= 32768 Gaussians, width * height <= 262144 rays,
- * ceil(w/16) * ceil(h/16) <= 2048 tiles, w + h <= 8192, at most 2^20 (tile,
- * Gaussian) pairs. Larger requests return GEER_ERR_CAPACITY and render nothing.
+ * ceil(w/16) * ceil(h/16) <= 2048 tiles, w + h <= 8192, at most 2^19
+ * (super-tile, Gaussian) pairs (geer_bin_sort). Larger requests return
+ * GEER_ERR_CAPACITY and render nothing.
  * Inputs and outputs as for geer_preprocess / geer_render_fwd (rgb [h*w][3],
  * T_final [h*w] or NULL, device, caller-owned). params may be NULL (defaults).
  *

@@ -80,7 +80,50 @@ struct CamTables {
     std::vector<float4> ttab;
     std::vector<float2> ptab;
     int64_t pixels = 0, tiles = 0;
+    int32_t super_size = 4;
+    int64_t stiles = 0;
 };
+
+// Super-tile grid of each camera (binning is by super-tiles of S x S tiles; the
+// render filters a super-tile's list down to its tile). Free layouts take the
+// smallest S in 4..8 that keeps every super-tile id below 256 (one radix pass),
+// else 4. Slot layouts take S = 4 and the slot's own tile ids, so that every
+// launch shape depends on the slot count only.
+void assign_super(DevCam *cams, int n, int64_t slot_tiles, int32_t &S, int64_t &n_stiles) {
+    if (slot_tiles > 0) {
+        S = 4;
+        for (int ci = 0; ci < n; ++ci) {
+            DevCam &d = cams[ci];
+            d.stiles_x = (int32_t)ceil_div(d.tiles_x, S);
+            d.stile_base = (int32_t)(ci * slot_tiles);
+        }
+        n_stiles = n * slot_tiles;
+        return;
+    }
+    S = 4;
+    for (int e = 4; e <= 8; ++e) {
+        int64_t tot = 0;
+        for (int ci = 0; ci < n; ++ci) tot += ceil_div(cams[ci].tiles_x, e) * ceil_div(cams[ci].tiles_y, e);
+        if (tot <= kRadix) {
+            S = e;
+            break;
+        }
+    }
+    int64_t sb = 0;
+    for (int ci = 0; ci < n; ++ci) {
+        DevCam &d = cams[ci];
+        d.stiles_x = (int32_t)ceil_div(d.tiles_x, S);
+        d.stile_base = (int32_t)sb;
+        sb += (int64_t)d.stiles_x * ceil_div(d.tiles_y, S);
+    }
+    n_stiles = sb;
+}
+
+int32_t sort_passes(int64_t ids) {
+    int bits = 1;
+    while ((int64_t(1) << bits) < ids) ++bits;
+    return (bits + kRadixBits - 1) / kRadixBits;
+}
 
 // Per camera: tile-column/-row half-angle spans tan(angle/2) of the first and
 // last ray of the tile with flags for cos(angle) >= 0 / <= 0 (rays beyond 90 deg
@@ -182,6 +225,7 @@ void build_tables(const geer_camera *cams, int n, CamTables &out, const uint8_t 
             out.pixels = (int64_t)(ci + 1) * slot_pixels;
         }
     }
+    assign_super(out.cams.data(), (int)out.cams.size(), slot_tiles, out.super_size, out.stiles);
 }
 
 struct Caps {
@@ -216,6 +260,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_key = L.take(sizeof(uint32_t) * cg);
     size_t o_bs = L.take(sizeof(uint32_t) * c.cams * c.prep_blocks);
     size_t o_bs2 = L.take(sizeof(uint32_t) * prep_blocks(cg));
+    size_t o_bs3 = L.take(sizeof(uint32_t) * prep_blocks(cg));
     size_t o_ik0 = L.take(sizeof(uint32_t) * cg);
     size_t o_ik1 = L.take(sizeof(uint32_t) * cg);
     size_t o_ii0 = L.take(sizeof(uint32_t) * cg);
@@ -224,6 +269,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_k1 = L.take(sizeof(uint32_t) * c.pairs);
     size_t o_v0 = L.take(sizeof(uint32_t) * c.pairs);
     size_t o_v1 = L.take(sizeof(uint32_t) * c.pairs);
+    size_t o_srg = L.take(sizeof(uint4) * c.pairs);
     const int64_t groups = ceil_div(c.sort_tiles, kGroupTiles) + 1;
     size_t o_th = L.take(sizeof(uint32_t) * kRadix * c.sort_tiles);
     size_t o_gs = L.take(sizeof(uint32_t) * kRadix * groups);
@@ -232,6 +278,8 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_misc = L.take(sizeof(uint32_t) * kMiscCount);
     size_t o_tr = L.take((sizeof(uint2) + sizeof(uint32_t)) * c.tiles);
     size_t o_to = L.take(sizeof(uint32_t) * c.tiles);
+    size_t o_bo = L.take(sizeof(uint32_t) * c.tiles);
+    size_t o_sr = L.take((sizeof(uint2) + sizeof(uint32_t)) * c.tiles);
     size_t o_last = L.take(sizeof(uint32_t) * c.pixels);
     size_t o_tfin = L.take(sizeof(float) * c.pixels);
     size_t o_ev = L.take(sizeof(uint2) * c.pixels);
@@ -246,6 +294,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_key = reinterpret_cast<uint32_t *>(base + o_key);
         ws->d_blocksum = reinterpret_cast<uint32_t *>(base + o_bs);
         ws->d_blocksum2 = reinterpret_cast<uint32_t *>(base + o_bs2);
+        ws->d_blocksum3 = reinterpret_cast<uint32_t *>(base + o_bs3);
         ws->d_ikey[0] = reinterpret_cast<uint32_t *>(base + o_ik0);
         ws->d_ikey[1] = reinterpret_cast<uint32_t *>(base + o_ik1);
         ws->d_iid[0] = reinterpret_cast<uint32_t *>(base + o_ii0);
@@ -254,13 +303,16 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_keys[1] = reinterpret_cast<uint32_t *>(base + o_k1);
         ws->d_vals[0] = reinterpret_cast<uint32_t *>(base + o_v0);
         ws->d_vals[1] = reinterpret_cast<uint32_t *>(base + o_v1);
+        ws->d_sranges = reinterpret_cast<uint4 *>(base + o_srg);
         ws->d_tile_hist = reinterpret_cast<uint32_t *>(base + o_th);
         ws->d_group_sum = reinterpret_cast<uint32_t *>(base + o_gs);
         ws->d_group_excl = reinterpret_cast<uint32_t *>(base + o_ge);
         ws->d_digit_base = reinterpret_cast<uint32_t *>(base + o_db);
         ws->d_misc = reinterpret_cast<uint32_t *>(base + o_misc);
-        ws->d_tile_range = reinterpret_cast<uint2 *>(base + o_tr);
+        ws->d_tile_walk = reinterpret_cast<uint2 *>(base + o_tr);
         ws->d_tile_order = reinterpret_cast<uint32_t *>(base + o_to);
+        ws->d_bwd_order = reinterpret_cast<uint32_t *>(base + o_bo);
+        ws->d_srange = reinterpret_cast<uint2 *>(base + o_sr);
         ws->d_last = reinterpret_cast<uint32_t *>(base + o_last);
         ws->d_Tfin = reinterpret_cast<float *>(base + o_tfin);
         ws->d_evals = reinterpret_cast<uint2 *>(base + o_ev);
@@ -322,6 +374,7 @@ geer_status upload_cams(geer_workspace *ws, const CamTables &t, cudaStream_t s) 
     const size_t b1 = sizeof(float4) * t.ttab.size();
     const size_t b2 = sizeof(float2) * t.ptab.size();
     if (b0 + b1 + b2 > ws->stage_bytes) return GEER_ERR_ARG;
+    if (t.stiles > ws->cap_tiles) return GEER_ERR_ARG;
     // the staging buffer may still be read by a previous copy on this stream
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return GEER_ERR_CUDA;
@@ -338,10 +391,9 @@ geer_status upload_cams(geer_workspace *ws, const CamTables &t, cudaStream_t s) 
     ws->n_pixels = t.pixels;
     ws->n_tiles = t.tiles;
     std::copy(t.cams.begin(), t.cams.end(), ws->cams);
-    int bits = 1;
-    while ((int64_t(1) << bits) < t.tiles) ++bits;
-    ws->tile_bits = bits;
-    ws->n_tile_passes = (bits + kRadixBits - 1) / kRadixBits;
+    ws->super_size = t.super_size;
+    ws->n_stiles = t.stiles;
+    ws->n_sort_passes = sort_passes(t.stiles);
     ws->stage = 0;
     return GEER_OK;
 }
@@ -562,7 +614,8 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
     if (items > 0 && cudaMemsetAsync(ws->d_gacc, 0, sizeof(GradAcc) * items, s) != cudaSuccess) return GEER_ERR_CUDA;
     {
         StageTimer tm(ws, kStageRenderBwd, s);
-        if (launch_render_bwd(ws, dL_drgb, s) != cudaSuccess) return GEER_ERR_CUDA;
+        if (launch_bwd_order(ws, s) != cudaSuccess || launch_render_bwd(ws, dL_drgb, s) != cudaSuccess)
+            return GEER_ERR_CUDA;
     }
     StageTimer tm(ws, kStagePreprocessBwd, s);
     return cuda_status(launch_preprocess_bwd(ws, g, d_mean, d_scale, d_quat, d_opacity, d_sh, s));
@@ -623,25 +676,58 @@ geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *value
     if (cudaMemcpyAsync(m, ws->d_misc, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return GEER_ERR_CUDA;
-    const int64_t P = m[kMiscPairs];
+    if (m[kMiscStatus] & kStatusCapacity) return GEER_ERR_CAPACITY;
+    const int64_t P = ((int64_t)m[kMiscTileHi] << 32) | (int64_t)m[kMiscTileLo];
     *count = P;
     const int64_t n = std::min(P, cap);
-    if (n > 0) {
-        const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
-        std::vector<uint32_t> t(n), v(n), depth(items);
-        if (cudaMemcpyAsync(t.data(), ws->d_keys[ws->sorted_buf], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(v.data(), ws->d_vals[ws->sorted_buf], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(depth.data(), ws->d_key, sizeof(uint32_t) * items, cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return GEER_ERR_CUDA;
-        for (int64_t i = 0; i < n; ++i) {
-            if (keys) keys[i] = ((uint64_t)t[i] << 32) | (v[i] < items ? depth[v[i]] : 0u);
+    if (n == 0) return GEER_OK;
+    // every tile's full list, filtered from its super-tile's list as the renders
+    // do: count, offsets on the host, then the lists (into the free sort buffer)
+    if (P > ws->cap_pairs) return GEER_ERR_CAPACITY;
+    uint32_t *scratch = reinterpret_cast<uint32_t *>(ws->d_tile_walk + ws->n_tiles);
+    uint32_t *lists = ws->d_keys[ws->sorted_buf ^ 1];
+    std::vector<uint32_t> cnt(ws->n_tiles), off(ws->n_tiles);
+    if (launch_expand_tiles(ws, scratch, nullptr, s) != cudaSuccess ||
+        cudaMemcpyAsync(cnt.data(), scratch, sizeof(uint32_t) * ws->n_tiles, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    int64_t run = 0;
+    for (int64_t t = 0; t < ws->n_tiles; ++t) {
+        off[t] = (uint32_t)run;
+        run += cnt[t];
+    }
+    if (run != P) return GEER_ERR_CUDA;  // the filtered lists must hold exactly the counted associations
+    const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
+    std::vector<uint32_t> v(P), depth(items);
+    if (cudaMemcpyAsync(scratch, off.data(), sizeof(uint32_t) * ws->n_tiles, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        launch_expand_tiles(ws, scratch, lists, s) != cudaSuccess ||
+        cudaMemcpyAsync(v.data(), lists, sizeof(uint32_t) * P, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(depth.data(), ws->d_key, sizeof(uint32_t) * items, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    for (int64_t t = 0; t < ws->n_tiles; ++t)
+        for (int64_t i = off[t]; i < (int64_t)off[t] + cnt[t] && i < n; ++i) {
+            if (keys) keys[i] = ((uint64_t)t << 32) | (v[i] < items ? depth[v[i]] : 0u);
             if (values) values[i] = v[i];
         }
-    }
+    return GEER_OK;
+}
+
+geer_status geer_pair_counts(geer_workspace *ws, int64_t *tile_pairs, int64_t *super_pairs, int32_t *sort_passes,
+                             void *stream) {
+    if (!ws) return GEER_ERR_ARG;
+    if (ws->stage < 2) return GEER_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t m[kMiscCount];
+    if (cudaMemcpyAsync(m, ws->d_misc, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    if (tile_pairs) *tile_pairs = ((int64_t)m[kMiscTileHi] << 32) | (int64_t)m[kMiscTileLo];
+    if (super_pairs) *super_pairs = ((int64_t)m[kMiscPairsHi] << 32) | (int64_t)m[kMiscTotalLo];
+    if (sort_passes) *sort_passes = ws->n_sort_passes;
     return GEER_OK;
 }
 
@@ -769,7 +855,7 @@ namespace {
 
 constexpr int64_t kNoAllocMaxGauss = 32768;
 constexpr int64_t kNoAllocMaxPixels = 512 * 512;
-constexpr int64_t kNoAllocMaxPairs = int64_t(1) << 20;
+constexpr int64_t kNoAllocMaxPairs = int64_t(1) << 19;  // (super-tile, Gaussian) pairs
 constexpr int64_t kNoAllocMaxTileTab = 2 * 1024;   // tile columns + rows
 constexpr int64_t kNoAllocMaxPixTab = 8 * 1024;    // pixel columns + rows
 constexpr int64_t kNoAllocMaxTiles = 2 * 1024;
@@ -919,11 +1005,9 @@ extern "C" geer_status geer_render_noalloc(const geer_gaussians *g, const geer_c
     ws.n_cams = 1;
     ws.n_pixels = (int64_t)cam->width * cam->height;
     ws.n_tiles = (int64_t)S.cam.tiles_x * S.cam.tiles_y;
+    assign_super(&S.cam, 1, 0, ws.super_size, ws.n_stiles);
+    ws.n_sort_passes = sort_passes(ws.n_stiles);
     ws.cams[0] = S.cam;
-    int bits = 1;
-    while ((int64_t(1) << bits) < ws.n_tiles) ++bits;
-    ws.tile_bits = bits;
-    ws.n_tile_passes = (bits + kRadixBits - 1) / kRadixBits;
     ws.n_gauss = g->n;
     ws.sh_degree = g->sh_degree;
     // the array keeps the previous call's contents: clear what must start at zero

@@ -22,14 +22,17 @@ constexpr int kSmemTiles = 12288;          // per-block tile histogram in shared
 
 // Device status word bits.
 constexpr uint32_t kStatusCapacity = 1u;
+constexpr uint32_t kStatusListOverflow = 2u;  // inspection: a tile list differs from its counted length
 
 // Indices into the misc u32 array of the workspace.
 enum Misc : int {
     kMiscStatus = 0,      // device status bits
-    kMiscPairs = 1,       // pair count P (clamped to u32)
-    kMiscPairsHi = 2,     // unclamped P / 2^32
-    kMiscTotalLo = 4,     // unclamped P mod 2^32
+    kMiscPairs = 1,       // (super-tile, item) pairs to sort (clamped to the capacity)
+    kMiscPairsHi = 2,     // unclamped pair count / 2^32
+    kMiscTotalLo = 4,     // unclamped pair count mod 2^32
     kMiscLive = 5,        // live (camera, Gaussian) items (tile count > 0)
+    kMiscTileLo = 6,      // (tile, item) associations P mod 2^32
+    kMiscTileHi = 7,      // P / 2^32
     kMiscCount = 32
 };
 
@@ -42,7 +45,9 @@ struct DevCam {
     int32_t tcol_off, trow_off;  // offsets (in float4) of the per-tile tables
     int32_t pcol_off, prow_off;  // offsets (in float2) of the per-pixel tables
     int32_t c0lo, c0hi, r0lo, r0hi;  // tile columns / rows whose rays all have cos >= 0
-    int32_t pad_[3];
+    int32_t stiles_x;    // super-tiles per row (ceil(tiles_x / super-tile size))
+    int32_t stile_base;  // global index of super-tile (0, 0)
+    int32_t pad_;
     int64_t pix_base;    // offset of pixel (0, 0) in the batched image (in pixels)
     float R[9], t[3];    // world -> camera
     float o[3];          // camera centre in world coordinates
@@ -76,14 +81,32 @@ struct Params {
     float alpha_min, T_min, alpha_max, lambda_pad;
 };
 
+// PBF association ranges of a (camera, Gaussian) item, packed as u16 pairs:
+// [0,1) columns and [4,5) rows of the direct arcs, [2,3) and [6,7) of the arcs
+// shifted by pi (rays beyond 90 degrees).
+__device__ __forceinline__ void unpack_ranges(const uint4 r4, int rg[8]) {
+    rg[0] = (int)(r4.x & 0xffff); rg[1] = (int)(r4.x >> 16); rg[2] = (int)(r4.y & 0xffff); rg[3] = (int)(r4.y >> 16);
+    rg[4] = (int)(r4.z & 0xffff); rg[5] = (int)(r4.z >> 16); rg[6] = (int)(r4.w & 0xffff); rg[7] = (int)(r4.w >> 16);
+}
+
+// Association of tile (cx, cy) with an item: the column test takes the arc kind
+// of the tile's rows (cos(phi) >= 0: direct, < 0: shifted) and the row test that
+// of its columns; col / row are the tile's table entries (z, w: the tile has rays
+// with cos >= 0 / cos <= 0).
+__device__ __forceinline__ bool tile_assoc(const float4 &col, const float4 &row, int cx, int cy, const int rg[8]) {
+    bool aok = (row.z != 0.0f && cx >= rg[0] && cx < rg[1]) || (row.w != 0.0f && cx >= rg[2] && cx < rg[3]);
+    bool bok = (col.z != 0.0f && cy >= rg[4] && cy < rg[5]) || (col.w != 0.0f && cy >= rg[6] && cy < rg[7]);
+    return aok && bok;
+}
+
 // Stages timed by geer_enable_timing (CUDA events around each stage's kernels).
 enum Stage : int {
     kStagePreprocess = 0,
     kStageBinFront,      // live-item scan + compaction
     kStageDepthSort,
     kStageCountPairs,
-    kStageDuplicate,     // duplicate + tile ranges
-    kStageTileSort,
+    kStageDuplicate,     // super-tile pairs, super-tile ranges, render order
+    kStageTileSort,      // sort of the super-tile pairs
     kStageRenderFwd,
     kStageRenderBwd,
     kStagePreprocessBwd,
@@ -106,7 +129,9 @@ struct geer_workspace {
     // current camera set
     int32_t n_cams;
     int64_t n_pixels, n_tiles;
-    int32_t tile_bits, n_tile_passes;
+    int32_t super_size;      // super-tile edge in tiles
+    int64_t n_stiles;        // super-tile id range
+    int32_t n_sort_passes;   // radix passes over the super-tile ids
     geer::DevCam cams[geer::kMaxCams];
 
     // device arrays (inside the caller's memory)
@@ -117,18 +142,23 @@ struct geer_workspace {
     uint4 *d_ranges;
     uint32_t *d_count, *d_key;
     uint32_t *d_blocksum;   // live items per preprocess block
-    uint32_t *d_blocksum2;  // pairs per block of depth-sorted items
+    uint32_t *d_blocksum2;  // super-tile pairs per block of depth-sorted items (scanned: emission offsets)
+    uint32_t *d_blocksum3;  // (tile, item) associations per block of depth-sorted items
     uint32_t *d_ikey[2];    // depth keys of the live items (ping-pong)
     uint32_t *d_iid[2];     // item ids (camera * n + gaussian) of the live items
-    uint32_t *d_keys[2];    // pair tile ids (ping-pong)
-    uint32_t *d_vals[2];    // pair item ids
+    uint32_t *d_keys[2];    // super-tile ids of the (super-tile, item) pairs (ping-pong)
+    uint32_t *d_vals[2];    // item ids of the pairs
     uint32_t *d_tile_hist;  // [cap_sort_tiles][kRadix] digit histogram per sort tile
     uint32_t *d_group_sum;  // [cap_sort_groups][kRadix] (zero between passes)
     uint32_t *d_group_excl; // [cap_sort_groups][kRadix]
     uint32_t *d_digit_base; // [kRadix]
     uint32_t *d_misc;       // [kMiscCount]
-    uint2 *d_tile_range;    // [cap_tiles] tile [start, end), followed by [cap_tiles] u32 pair counts
-    uint32_t *d_tile_order; // [cap_tiles] tiles by descending pair count: the render blocks' schedule
+    uint2 *d_tile_walk;     // [cap_tiles] per tile, where the forward's scan of its super-tile list ended:
+                            // (position, tile-list entries found before it); followed by [cap_tiles] u32 scratch
+    uint32_t *d_tile_order; // [cap_tiles] tiles by descending super-tile list length: the forward's schedule
+    uint32_t *d_bwd_order;  // [cap_tiles] tiles by descending walked list length: the backward's schedule
+    uint4 *d_sranges;       // [cap_pairs] association ranges of the sorted pairs' items (in list order)
+    uint2 *d_srange;        // [cap_tiles] super-tile [start, end) in the sorted pairs, followed by [cap_tiles] u32 counts
     uint32_t *d_last;       // [cap_pixels] list entries walked per ray
     float *d_Tfin;          // [cap_pixels] final transmittance (for the backward)
     uint2 *d_evals;         // [cap_pixels] ray-Gaussian evaluations executed / contributors applied
@@ -138,7 +168,7 @@ struct geer_workspace {
     int64_t n_gauss;
     int32_t sh_degree;
     int stage;               // 0 none, 1 preprocessed, 2 sorted, 3 rendered
-    int sorted_buf;          // which ping-pong buffer holds the tile-sorted pairs
+    int sorted_buf;          // which ping-pong buffer holds the sorted super-tile pairs
     int depth_buf;           // which ping-pong buffer holds the depth-sorted items
     int sort_grid;           // grid of the radix kernels (grid-stride over sort tiles)
     int num_sms;
@@ -161,6 +191,9 @@ cudaError_t launch_bin_front(const geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_depth_sort(geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_count_pairs(const geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_sorted_ranges(const geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_bwd_order(const geer_workspace *ws, cudaStream_t s);
+cudaError_t launch_expand_tiles(const geer_workspace *ws, uint32_t *counts_or_offsets, uint32_t *lists, cudaStream_t s);
 cudaError_t launch_tile_sort(geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_final, cudaStream_t s);
 cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cudaStream_t s);

@@ -6,6 +6,8 @@
 // (__fmul_rn / __fadd_rn / __fsub_rn / __fdiv_rn / __fsqrt_rn, which the
 // compiler never contracts), so the tile ranges and depth keys are bit-for-bit
 // reproducible by an independent FP32 implementation of the same sequence.
+#include <algorithm>
+
 #include "geer_internal.cuh"
 
 namespace geer {
@@ -133,11 +135,6 @@ __device__ float lambda2(float sigma, float alpha_min, float pad) {
     return fm(fm(2.0f, lnx), fa(1.0f, pad));
 }
 
-__device__ __forceinline__ bool tile_assoc(const float4 &col, const float4 &row, int cx, int cy, const int rg[8]) {
-    bool aok = (row.z != 0.0f && cx >= rg[0] && cx < rg[1]) || (row.w != 0.0f && cx >= rg[2] && cx < rg[3]);
-    bool bok = (col.z != 0.0f && cy >= rg[4] && cy < rg[5]) || (col.w != 0.0f && cy >= rg[6] && cy < rg[7]);
-    return aok && bok;
-}
 
 // Bounding box of the association predicate in tile coordinates.
 __device__ __forceinline__ void assoc_bbox(const int rg[8], int ncols, int nrows, int &xa, int &xb, int &ya,
@@ -204,10 +201,6 @@ __device__ __forceinline__ bool is_rect(const DevCam &cam, const int rg[8]) {
     return rg[0] >= cam.c0lo && rg[1] <= cam.c0hi && rg[4] >= cam.r0lo && rg[5] <= cam.r0hi;
 }
 
-__device__ __forceinline__ void unpack_ranges(const uint4 r4, int rg[8]) {
-    rg[0] = (int)(r4.x & 0xffff); rg[1] = (int)(r4.x >> 16); rg[2] = (int)(r4.y & 0xffff); rg[3] = (int)(r4.y >> 16);
-    rg[4] = (int)(r4.z & 0xffff); rg[5] = (int)(r4.z >> 16); rg[6] = (int)(r4.w & 0xffff); rg[7] = (int)(r4.w >> 16);
-}
 
 // Block-wide exclusive scan (256 threads); returns the exclusive prefix and the block total.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *wsum, uint32_t &total) {
@@ -415,11 +408,12 @@ __global__ void __launch_bounds__(kPrepThreads) k_preprocess(
 
 // Exclusive scan of per-block counts (one block; each thread scans a contiguous
 // chunk serially). mode 0 (live items): total -> misc[kMiscLive]; also clears the
-// tile ranges and per-tile pair counts.
-// mode 1 (pairs): total -> misc[kMiscPairs] (clamped to cap) with the capacity check.
+// per-super-tile pair counts. mode 1 ((super-tile, item) pairs): total ->
+// misc[kMiscPairs] (clamped to cap) with the capacity check. mode 2 ((tile, item)
+// associations P): total -> misc[kMiscTileLo / Hi].
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ blocksum, int64_t m,
-                                                      uint32_t *__restrict__ misc, uint2 *__restrict__ tile_range,
-                                                      int64_t ntiles, int64_t cap, int mode) {
+                                                      uint32_t *__restrict__ misc, uint2 *__restrict__ srange,
+                                                      int64_t nst, int64_t cap, int mode) {
     __shared__ unsigned long long warp_tot[32];
     const int t = threadIdx.x;
     const int64_t chunk = (m + 1023) / 1024;
@@ -455,6 +449,9 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ blo
         const unsigned long long total = excl;
         if (mode == 0) {
             misc[kMiscLive] = (uint32_t)total;
+        } else if (mode == 2) {
+            misc[kMiscTileLo] = (uint32_t)total;
+            misc[kMiscTileHi] = (uint32_t)(total >> 32);
         } else {
             misc[kMiscPairs] = (uint32_t)min(total, (unsigned long long)cap);
             misc[kMiscPairsHi] = (uint32_t)(total >> 32);
@@ -463,11 +460,8 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ blo
         }
     }
     if (mode == 0) {
-        uint32_t *tile_count = reinterpret_cast<uint32_t *>(tile_range + ntiles);
-        for (int64_t i = t; i < ntiles; i += 1024) {
-            tile_range[i] = make_uint2(0u, 0u);
-            tile_count[i] = 0u;
-        }
+        uint32_t *scount = reinterpret_cast<uint32_t *>(srange + nst);
+        for (int64_t i = t; i < nst; i += 1024) scount[i] = 0u;
     }
 }
 
@@ -493,34 +487,87 @@ __global__ void __launch_bounds__(kPrepThreads) k_compact(int ncams, int64_t n, 
     }
 }
 
-// Tile counts of the depth-sorted items, summed per block.
-__global__ void __launch_bounds__(kPrepThreads) k_gather_counts(const uint32_t *__restrict__ sorted_id,
+// The super-tiles (S x S tiles, camera-local coordinates) holding at least one
+// tile associated with an item whose association is not a rectangle, in
+// row-major order.
+template <typename F>
+__device__ __forceinline__ void for_each_super_general(const DevCam &cam, const float4 *ctab, const float4 *rtab,
+                                                       int S, const int rg[8], F f) {
+    int xa, xb, ya, yb;
+    assoc_bbox(rg, cam.tiles_x, cam.tiles_y, xa, xb, ya, yb);
+    if (xa >= xb || ya >= yb) return;
+    for (int sy = ya / S; sy <= (yb - 1) / S; ++sy)
+        for (int sx = xa / S; sx <= (xb - 1) / S; ++sx) {
+            bool any = false;
+            for (int cy = max(ya, sy * S); cy < min(yb, sy * S + S) && !any; ++cy) {
+                const float4 row = rtab[cy];
+                for (int cx = max(xa, sx * S); cx < min(xb, sx * S + S); ++cx)
+                    if (tile_assoc(ctab[cx], row, cx, cy, rg)) {
+                        any = true;
+                        break;
+                    }
+            }
+            if (any) f(sx, sy);
+        }
+}
+
+// Number of (super-tile, item) pairs of an item with c associated tiles.
+__device__ __forceinline__ uint32_t super_count(const DevCam &cam, const float4 *ttab, int S, const int rg[8],
+                                                uint32_t c, bool rect) {
+    if (c == 0) return 0u;
+    if (rect) {
+        const int sx0 = rg[0] / S, sx1 = (rg[1] - 1) / S + 1, sy0 = rg[4] / S, sy1 = (rg[5] - 1) / S + 1;
+        return (uint32_t)((sx1 - sx0) * (sy1 - sy0));
+    }
+    uint32_t k = 0;
+    for_each_super_general(cam, ttab + cam.tcol_off, ttab + cam.trow_off, S, rg, [&](int, int) { ++k; });
+    return k;
+}
+
+// Per block of depth-sorted live items: their super-tile pairs (emission
+// offsets) and their tile pairs (the total, for the capacity check).
+__global__ void __launch_bounds__(kPrepThreads) k_gather_counts(const DevCam *__restrict__ cams,
+                                                                const float4 *__restrict__ ttab, int64_t n, int S,
+                                                                const uint32_t *__restrict__ sorted_id,
                                                                 const uint32_t *__restrict__ count,
+                                                                const uint4 *__restrict__ ranges,
                                                                 const uint32_t *__restrict__ misc,
-                                                                uint32_t *__restrict__ blocksum) {
+                                                                uint32_t *__restrict__ bs_super,
+                                                                uint32_t *__restrict__ bs_tile) {
     __shared__ uint32_t red[kPrepThreads / 32];
     const uint32_t L = misc[kMiscLive];
     const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
-    const uint32_t c = i < L ? count[sorted_id[i]] : 0u;
+    uint32_t c = 0, sc = 0;
+    if (i < L) {
+        const uint32_t item = sorted_id[i];
+        c = count[item];
+        int rg[8];
+        unpack_ranges(ranges[item], rg);
+        const DevCam &cam = cams[item / (uint32_t)n];
+        sc = super_count(cam, ttab, S, rg, c, is_rect(cam, rg));
+    }
     const uint32_t tot = block_sum_u32(c, red);
-    if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+    if (threadIdx.x == 0) bs_tile[blockIdx.x] = tot;
+    __syncthreads();
+    const uint32_t stot = block_sum_u32(sc, red);
+    if (threadIdx.x == 0) bs_super[blockIdx.x] = stot;
 }
 
-// DuplicateWithKeys in depth order: item i of the depth-sorted list emits one
-// (global tile, item) pair per associated tile, tiles in row-major order. Items
-// whose association is a rectangle are emitted by the whole warp together
-// (lane j writes output j: coalesced); others loop per thread. Accumulates the
-// digit histograms of the tile ids for the tile sort.
+// DuplicateWithKeys in depth order, at super-tile granularity: item i of the
+// depth-sorted list emits one (global super-tile, item) pair per super-tile
+// holding an associated tile, in row-major order, and counts the pairs per
+// super-tile. Items whose association is a rectangle are emitted by the whole
+// warp together (lane j writes output j: coalesced); others loop per thread.
 __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
-    const DevCam *__restrict__ cams, const float4 *__restrict__ ttab, int64_t n, const uint32_t *__restrict__ sorted_id,
-    const uint4 *__restrict__ ranges, const uint32_t *__restrict__ count, const uint32_t *__restrict__ misc,
-    const uint32_t *__restrict__ blocksum, uint32_t *__restrict__ okeys, uint32_t *__restrict__ ovals,
-    uint32_t *__restrict__ tile_count, int ntiles, int64_t cap) {
+    const DevCam *__restrict__ cams, const float4 *__restrict__ ttab, int64_t n, int S,
+    const uint32_t *__restrict__ sorted_id, const uint4 *__restrict__ ranges, const uint32_t *__restrict__ count,
+    const uint32_t *__restrict__ misc, const uint32_t *__restrict__ blocksum, uint32_t *__restrict__ okeys,
+    uint32_t *__restrict__ ovals, uint32_t *__restrict__ scount, int nst, int64_t cap) {
     __shared__ uint32_t wsum[kPrepThreads / 32];
-    extern __shared__ uint32_t sh[];  // per-tile pair counts when they fit (ntiles <= kSmemTiles)
-    const bool smem = ntiles <= kSmemTiles;
+    extern __shared__ uint32_t sh[];  // per-super-tile pair counts when they fit (nst <= kSmemTiles)
+    const bool smem = nst <= kSmemTiles;
     if (smem)
-        for (int k = threadIdx.x; k < ntiles; k += kPrepThreads) sh[k] = 0u;
+        for (int k = threadIdx.x; k < nst; k += kPrepThreads) sh[k] = 0u;
     const uint32_t L = misc[kMiscLive];
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
@@ -530,16 +577,23 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
     bool rect = true;
     if (i < L) {
         item = sorted_id[i];
-        cnt = count[item];
         ci = (int)(item / (uint32_t)n);
         unpack_ranges(ranges[item], rg);
         rect = is_rect(cams[ci], rg);
+        cnt = super_count(cams[ci], ttab, S, rg, count[item], rect);
     }
     uint32_t tot;
     const uint32_t pre = block_excl_scan(cnt, wsum, tot);
     const int64_t off = (int64_t)blocksum[blockIdx.x] + pre;
     const bool fits = off + cnt <= cap;
     const DevCam &cam = cams[ci];
+    __syncthreads();  // the per-super-tile counters are cleared
+    int sx0 = 0, sy0 = 0, rw = 1;
+    if (rect && fits && cnt > 0) {
+        sx0 = rg[0] / S;
+        sy0 = rg[4] / S;
+        rw = (rg[1] - 1) / S + 1 - sx0;
+    }
     // cooperative emission of the rectangle items of this warp
     const uint32_t rc = (rect && fits) ? cnt : 0u;
     uint32_t incl = rc;
@@ -549,8 +603,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
         if (lane >= o) incl += y;
     }
     const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-    const int rw = rg[1] - rg[0];
-    const uint32_t tb = (uint32_t)(cam.tile_base + rg[4] * cam.tiles_x + rg[0]);
+    const uint32_t sb = (uint32_t)(cam.stile_base + sy0 * cam.stiles_x + sx0);
     for (uint32_t j0 = 0; j0 < wtot; j0 += 32) {
         const uint32_t j = j0 + lane;
         // owner: first lane whose inclusive count exceeds j
@@ -563,17 +616,17 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
         const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, lo);
         const uint32_t o_cnt = __shfl_sync(0xffffffffu, rc, lo);
         const int o_rw = __shfl_sync(0xffffffffu, rw, lo);
-        const uint32_t o_tb = __shfl_sync(0xffffffffu, tb, lo);
-        const int o_tx = __shfl_sync(0xffffffffu, cam.tiles_x, lo);
+        const uint32_t o_sb = __shfl_sync(0xffffffffu, sb, lo);
+        const int o_sx = __shfl_sync(0xffffffffu, cam.stiles_x, lo);
         const uint32_t o_item = __shfl_sync(0xffffffffu, item, lo);
         const int64_t o_off = __shfl_sync(0xffffffffu, off, lo);
         if (j < wtot) {
             const uint32_t k = j - (o_incl - o_cnt);
             const uint32_t ky = k / (uint32_t)o_rw, kx = k - ky * (uint32_t)o_rw;
-            const uint32_t t = o_tb + ky * (uint32_t)o_tx + kx;
-            okeys[o_off + k] = t;
+            const uint32_t st = o_sb + ky * (uint32_t)o_sx + kx;
+            okeys[o_off + k] = st;
             ovals[o_off + k] = o_item;
-            atomicAdd(smem ? &sh[t] : &tile_count[t], 1u);
+            atomicAdd(smem ? &sh[st] : &scount[st], 1u);
         }
     }
     // per-thread emission of the other items (flipped angular ranges)
@@ -582,29 +635,22 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
         const float4 *rtab = ttab + cam.trow_off;
         int64_t o = off;
         const int64_t end = off + cnt;
-        int xa, xb, ya, yb;
-        assoc_bbox(rg, cam.tiles_x, cam.tiles_y, xa, xb, ya, yb);
-        for (int cy = ya; cy < yb; ++cy) {
-            const float4 row = rtab[cy];
-            for (int cx = xa; cx < xb && o < end; ++cx)
-                if (tile_assoc(ctab[cx], row, cx, cy, rg)) {
-                    const uint32_t t = (uint32_t)(cam.tile_base + cy * cam.tiles_x + cx);
-                    okeys[o] = t;
-                    ovals[o] = item;
-                    atomicAdd(smem ? &sh[t] : &tile_count[t], 1u);
-                    ++o;
-                }
-        }
+        for_each_super_general(cam, ctab, rtab, S, rg, [&](int sx, int sy) {
+            if (o < end) {
+                const uint32_t st = (uint32_t)(cam.stile_base + sy * cam.stiles_x + sx);
+                okeys[o] = st;
+                ovals[o] = item;
+                atomicAdd(smem ? &sh[st] : &scount[st], 1u);
+                ++o;
+            }
+        });
     }
     __syncthreads();
     if (smem)
-        for (int k = threadIdx.x; k < ntiles; k += kPrepThreads)
-            if (sh[k]) atomicAdd(&tile_count[k], sh[k]);
+        for (int k = threadIdx.x; k < nst; k += kPrepThreads)
+            if (sh[k]) atomicAdd(&scount[k], sh[k]);
 }
 
-// IdentifyFrustumRanges from the per-tile pair counts (one block): the
-// exclusive scan over tiles gives each tile's [start, end) in the tile-sorted
-// pairs.
 // Render schedule bucket of a tile with c pairs: larger counts first, four
 // buckets per octave, empty tiles last.
 constexpr int kOrderBuckets = 129;
@@ -615,27 +661,10 @@ __device__ __forceinline__ int order_bucket(uint32_t c) {
     return 127 - (lg * 4 + (lg >= 2 ? sub : 0));
 }
 
-// One block: tile ranges from the per-tile pair counts (exclusive scan), and the
-// order in which the render blocks take the tiles: by descending pair count
-// (bucketed), so that the costliest tiles start first and the grid does not end
-// on a tail of heavy tiles. The order within a bucket is arbitrary.
-__global__ void __launch_bounds__(1024) k_tile_offsets(const uint32_t *__restrict__ tile_count, int ntiles,
-                                                       const uint32_t *__restrict__ misc, uint2 *__restrict__ tile_range,
-                                                       uint32_t *__restrict__ tile_order) {
-    __shared__ uint32_t warp_tot[32];
-    __shared__ uint32_t hist[kOrderBuckets];
-    if (misc[kMiscStatus] & kStatusCapacity) return;
+// Exclusive scan over [0, m) of counts held as contiguous per-thread chunks by a
+// 1024-thread block: returns the prefix of the thread's chunk (s = the chunk's sum).
+__device__ __forceinline__ uint32_t block_chunk_prefix(uint32_t s, uint32_t *warp_tot) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int i = t; i < kOrderBuckets; i += 1024) hist[i] = 0u;
-    __syncthreads();
-    const int chunk = (ntiles + 1023) / 1024;
-    const int b = t * chunk, e = min(ntiles, b + chunk);
-    uint32_t s = 0;
-    for (int i = b; i < e; ++i) {
-        const uint32_t c = tile_count[i];
-        s += c;
-        atomicAdd(&hist[order_bucket(c)], 1u);
-    }
     uint32_t v = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -653,7 +682,101 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const uint32_t *__restric
         }
         warp_tot[lane] = w;
     }
-    if (t == 32) {  // exclusive scan of the bucket sizes (129 entries, one thread)
+    __syncthreads();
+    const uint32_t pre = v - s + (warp > 0 ? warp_tot[warp - 1] : 0u);
+    __syncthreads();
+    return pre;
+}
+
+// One block, IdentifyFrustumRanges at super-tile granularity: each super-tile's
+// [start, end) in the sorted super-tile pairs (exclusive scan of its pair
+// count), and the order in which the render blocks take the tiles: by
+// descending length of their super-tile's list (bucketed), so that the costliest
+// tiles start first and the grid does not end on a tail of heavy tiles.
+__global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict__ cams, int ncams, int S,
+                                                       int ntiles, uint2 *__restrict__ srange, int nst,
+                                                       const uint32_t *__restrict__ misc,
+                                                       uint32_t *__restrict__ tile_order) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t hist[kOrderBuckets];
+    if (misc[kMiscStatus] & kStatusCapacity) return;
+    const int t = threadIdx.x;
+    for (int i = t; i < kOrderBuckets; i += 1024) hist[i] = 0u;
+    // super-tile ranges
+    const uint32_t *scount = reinterpret_cast<const uint32_t *>(srange + nst);
+    const int schunk = (nst + 1023) / 1024;
+    const int sb = t * schunk, se = min(nst, sb + schunk);
+    uint32_t ss = 0;
+    for (int i = sb; i < se; ++i) ss += scount[i];
+    uint32_t srun = block_chunk_prefix(ss, warp_tot);
+    for (int i = sb; i < se; ++i) {
+        const uint32_t cnt = scount[i];
+        srange[i] = make_uint2(srun, srun + cnt);
+        srun += cnt;
+    }
+    __syncthreads();
+    // each tile's cost estimate: its super-tile's list length (0 for padding tiles)
+    const int chunk = (ntiles + 1023) / 1024;
+    const int b = t * chunk, e = min(ntiles, b + chunk);
+    int c = 0;
+    for (int k = 1; k < ncams; ++k)
+        if (cams[k].tile_base <= b) c = k;
+    for (int pass = 0; pass < 2; ++pass) {
+        int cc = c;
+        for (int i = b; i < e; ++i) {
+            while (cc + 1 < ncams && cams[cc + 1].tile_base <= i) ++cc;
+            const DevCam &cm = cams[cc];
+            const int lt = i - cm.tile_base;
+            uint32_t len = 0;
+            if (lt >= 0 && lt < cm.tiles_x * cm.tiles_y) {
+                const int cy = lt / cm.tiles_x, cx = lt - cy * cm.tiles_x;
+                const uint2 r = srange[cm.stile_base + (cy / S) * cm.stiles_x + cx / S];
+                len = r.y - r.x;
+            }
+            if (pass == 0)
+                atomicAdd(&hist[order_bucket(len)], 1u);
+            else
+                tile_order[atomicAdd(&hist[order_bucket(len)], 1u)] = (uint32_t)i;
+        }
+        __syncthreads();
+        if (pass == 0 && t == 0) {  // exclusive scan of the bucket sizes (129 entries, one thread)
+            uint32_t run = 0;
+            for (int i = 0; i < kOrderBuckets; ++i) {
+                const uint32_t h = hist[i];
+                hist[i] = run;
+                run += h;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The association ranges of the sorted pairs' items, in list order, so that the
+// render kernels' list filters read them coalesced.
+__global__ void __launch_bounds__(256) k_sorted_ranges(const uint32_t *__restrict__ svals,
+                                                       const uint4 *__restrict__ ranges,
+                                                       const uint32_t *__restrict__ misc,
+                                                       uint4 *__restrict__ sranges) {
+    if (misc[kMiscStatus] & kStatusCapacity) return;
+    const uint32_t P = misc[kMiscPairs];
+    for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < P; i += gridDim.x * 256u) sranges[i] = ranges[svals[i]];
+}
+
+// One block: the backward's schedule, tiles by descending length of the list
+// prefix the forward walked (bucketed as for the forward's schedule).
+__global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ tile_walk, int ntiles,
+                                                    const uint32_t *__restrict__ misc,
+                                                    uint32_t *__restrict__ order) {
+    __shared__ uint32_t hist[kOrderBuckets];
+    if (misc[kMiscStatus] & kStatusCapacity) return;
+    const int t = threadIdx.x;
+    for (int i = t; i < kOrderBuckets; i += 1024) hist[i] = 0u;
+    __syncthreads();
+    const int chunk = (ntiles + 1023) / 1024;
+    const int b = t * chunk, e = min(ntiles, b + chunk);
+    for (int i = b; i < e; ++i) atomicAdd(&hist[order_bucket(tile_walk[i].y)], 1u);
+    __syncthreads();
+    if (t == 0) {
         uint32_t run = 0;
         for (int i = 0; i < kOrderBuckets; ++i) {
             const uint32_t h = hist[i];
@@ -662,13 +785,7 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const uint32_t *__restric
         }
     }
     __syncthreads();
-    uint32_t run = v - s + (warp > 0 ? warp_tot[warp - 1] : 0u);
-    for (int i = b; i < e; ++i) {
-        const uint32_t c = tile_count[i];
-        tile_range[i] = make_uint2(run, run + c);
-        run += c;
-        tile_order[atomicAdd(&hist[order_bucket(c)], 1u)] = (uint32_t)i;
-    }
+    for (int i = b; i < e; ++i) order[atomicAdd(&hist[order_bucket(tile_walk[i].y)], 1u)] = (uint32_t)i;
 }
 
 }  // namespace
@@ -686,7 +803,7 @@ cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g,
 
 cudaError_t launch_bin_front(const geer_workspace *ws, cudaStream_t s) {
     const int64_t nblk = prep_blocks(ws->n_gauss);
-    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum, nblk * ws->n_cams, ws->d_misc, ws->d_tile_range, ws->n_tiles,
+    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum, nblk * ws->n_cams, ws->d_misc, ws->d_srange, ws->n_stiles,
                                      ws->cap_pairs, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || nblk == 0) return e;
@@ -697,31 +814,49 @@ cudaError_t launch_bin_front(const geer_workspace *ws, cudaStream_t s) {
 
 cudaError_t launch_count_pairs(const geer_workspace *ws, cudaStream_t s) {
     const int64_t m = prep_blocks((int64_t)ws->n_cams * ws->n_gauss);
-    if (m == 0) {
-        k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum2, 0, ws->d_misc, ws->d_tile_range, 0, ws->cap_pairs, 1);
-        return cudaGetLastError();
+    if (m > 0) {
+        k_gather_counts<<<(unsigned)m, kPrepThreads, 0, s>>>(ws->d_cams, ws->d_tile_tab, ws->n_gauss,
+                                                             ws->super_size, ws->d_iid[ws->depth_buf], ws->d_count,
+                                                             ws->d_ranges, ws->d_misc, ws->d_blocksum2,
+                                                             ws->d_blocksum3);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    k_gather_counts<<<(unsigned)m, kPrepThreads, 0, s>>>(ws->d_iid[ws->depth_buf], ws->d_count, ws->d_misc,
-                                                         ws->d_blocksum2);
+    // super-tile pairs: emission offsets and the capacity check; tile associations: the count P
+    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum2, m, ws->d_misc, nullptr, 0, ws->cap_pairs, 1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum2, m, ws->d_misc, ws->d_tile_range, 0, ws->cap_pairs, 1);
+    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum3, m, ws->d_misc, nullptr, 0, ws->cap_pairs, 2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
     const int64_t m = prep_blocks((int64_t)ws->n_cams * ws->n_gauss);
-    uint32_t *tile_count = reinterpret_cast<uint32_t *>(ws->d_tile_range + ws->n_tiles);
+    uint32_t *scount = reinterpret_cast<uint32_t *>(ws->d_srange + ws->n_stiles);
     if (m > 0) {
-        const size_t smem = ws->n_tiles <= kSmemTiles ? sizeof(uint32_t) * ws->n_tiles : 0;
-        k_duplicate<<<(unsigned)m, kPrepThreads, smem, s>>>(ws->d_cams, ws->d_tile_tab, ws->n_gauss,
-                                                            ws->d_iid[ws->depth_buf], ws->d_ranges, ws->d_count,
-                                                            ws->d_misc, ws->d_blocksum2, ws->d_keys[0], ws->d_vals[0],
-                                                            tile_count, (int)ws->n_tiles, ws->cap_pairs);
+        const size_t smem = ws->n_stiles <= kSmemTiles ? sizeof(uint32_t) * ws->n_stiles : 0;
+        k_duplicate<<<(unsigned)m, kPrepThreads, smem, s>>>(
+            ws->d_cams, ws->d_tile_tab, ws->n_gauss, ws->super_size, ws->d_iid[ws->depth_buf], ws->d_ranges,
+            ws->d_count, ws->d_misc, ws->d_blocksum2, ws->d_keys[0], ws->d_vals[0], scount, (int)ws->n_stiles,
+            ws->cap_pairs);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    k_tile_offsets<<<1, 1024, 0, s>>>(tile_count, (int)ws->n_tiles, ws->d_misc, ws->d_tile_range, ws->d_tile_order);
+    k_tile_offsets<<<1, 1024, 0, s>>>(ws->d_cams, ws->n_cams, ws->super_size, (int)ws->n_tiles, ws->d_srange,
+                                      (int)ws->n_stiles, ws->d_misc, ws->d_tile_order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sorted_ranges(const geer_workspace *ws, cudaStream_t s) {
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((ws->cap_pairs + 255) / 256, (int64_t)ws->num_sms * 8));
+    k_sorted_ranges<<<(unsigned)grid, 256, 0, s>>>(ws->d_vals[ws->sorted_buf], ws->d_ranges, ws->d_misc,
+                                                   ws->d_sranges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_order(const geer_workspace *ws, cudaStream_t s) {
+    if (ws->n_tiles == 0) return cudaSuccess;
+    k_bwd_order<<<1, 1024, 0, s>>>(ws->d_tile_walk, (int)ws->n_tiles, ws->d_misc, ws->d_bwd_order);
     return cudaGetLastError();
 }
 

@@ -3,9 +3,10 @@
 //
 // A BEAP tile (a camera sub-frustum) of 16 x 16 rays is processed by 16 / ROWS
 // blocks of ROWS x 16 threads, one thread per ray, tiles taken in the order of
-// descending pair count (the costliest first); each block stages the tile's
-// depth-sorted Gaussian records through shared memory in batches of BATCH and
-// every ray walks them front to back with the closed-form ray integral (Sec. 3.1):
+// descending pair count (the costliest first). The forward builds the tile's
+// depth-ordered list on the fly from its super-tile's list (association test per
+// entry), stages the records through shared memory in batches of BATCH and every
+// ray walks them front to back with the closed-form ray integral (Sec. 3.1):
 //   d_u = W d, m_u = o_u x d_u, kappa = |m_u|^2 / |d_u|^2,
 //   alpha = min(alpha_max, sigma exp(-kappa / 2)),
 // skipping alpha < alpha_min and Gaussians whose closest approach lies behind
@@ -23,13 +24,13 @@ namespace {
 #define GEER_FWD_BATCH 256
 #endif
 #ifndef GEER_BWD_ROWS
-#define GEER_BWD_ROWS 8
+#define GEER_BWD_ROWS 16
 #endif
 #ifndef GEER_BWD_BATCH
-#define GEER_BWD_BATCH 128
+#define GEER_BWD_BATCH 256
 #endif
 #ifndef GEER_BWD_MINB
-#define GEER_BWD_MINB 8
+#define GEER_BWD_MINB 4
 #endif
 constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -log2(e) / 2
 
@@ -67,19 +68,128 @@ __device__ __forceinline__ Eval evaluate(const float4 &a, const float4 &b, const
     return v;
 }
 
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Tile (cx, cy)'s list is its super-tile's depth-ordered list filtered by the
+// association test (sranges: the association ranges of the sorted pairs, in
+// list order): appends the entries of [pos, end) that pass, kThreads per step,
+// until s_id holds at least `want` entries or the list ends. Block-uniform (pos,
+// end, s_cnt, want are the same in every thread); s_id is visible on return.
+template <int kThreads>
+__device__ __forceinline__ void fill_list(const uint32_t *__restrict__ svals, const uint4 *__restrict__ sranges,
+                                          const float4 &col, const float4 &row, int cx, int cy, uint32_t &pos,
+                                          uint32_t end, int want, uint32_t *s_id, uint32_t *s_pos, int &s_cnt,
+                                          uint32_t *s_wcnt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    while (s_cnt < want && pos < end) {
+        const uint32_t i = pos + threadIdx.x;
+        bool ok = false;
+        uint32_t id = 0;
+        if (i < end) {
+            int rg[8];
+            unpack_ranges(sranges[i], rg);
+            ok = tile_assoc(col, row, cx, cy, rg);
+            if (ok) id = svals[i];
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t base = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const uint32_t c = s_wcnt[w];
+            base += w < warp ? c : 0u;
+            tot += c;
+        }
+        if (ok) {
+            const int k = s_cnt + (int)(base + __popc(bal & lanemask_lt()));
+            s_id[k] = id;
+            if (s_pos) s_pos[k] = i;
+        }
+        __syncthreads();
+        s_cnt += (int)tot;
+        pos += kThreads;
+    }
+}
+
+// Moves the s_cnt - cnt entries not yet consumed (fewer than kThreads) to the front.
+template <int kThreads>
+__device__ __forceinline__ void shift_list(uint32_t *s_id, uint32_t *s_pos, int cnt, int &s_cnt) {
+    const int rem = s_cnt - cnt;
+    uint32_t keep = 0, keep_pos = 0;
+    if ((int)threadIdx.x < rem) {
+        keep = s_id[cnt + threadIdx.x];
+        if (s_pos) keep_pos = s_pos[cnt + threadIdx.x];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < rem) {
+        s_id[threadIdx.x] = keep;
+        if (s_pos) s_pos[threadIdx.x] = keep_pos;
+    }
+    s_cnt = rem;
+}
+
+// The same filter walking the super-tile list backwards: appends the passing
+// entries of [beg, pos) in descending position order (the tile list read back to
+// front) until s_id holds at least BATCH entries or pos reaches beg.
+template <int kThreads, int BATCH>
+__device__ __forceinline__ void fill_list_rev(const uint32_t *__restrict__ svals, const uint4 *__restrict__ sranges,
+                                              const float4 &col, const float4 &row, int cx, int cy, uint32_t &pos,
+                                              uint32_t beg, uint32_t *s_id, int &s_cnt, uint32_t *s_wcnt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    while (s_cnt < BATCH && pos > beg) {
+        bool ok = false;
+        uint32_t id = 0;
+        if (pos - beg > threadIdx.x) {
+            const uint32_t i = pos - 1 - threadIdx.x;
+            int rg[8];
+            unpack_ranges(sranges[i], rg);
+            ok = tile_assoc(col, row, cx, cy, rg);
+            if (ok) id = svals[i];
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t base = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const uint32_t c = s_wcnt[w];
+            base += w < warp ? c : 0u;
+            tot += c;
+        }
+        if (ok) s_id[s_cnt + base + __popc(bal & lanemask_lt())] = id;
+        __syncthreads();
+        s_cnt += (int)tot;
+        pos = pos - beg > (uint32_t)kThreads ? pos - kThreads : beg;
+    }
+}
+
 template <int ROWS, int BATCH>
 __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
                                                             const float2 *__restrict__ ptab,
-                                                            const uint2 *__restrict__ tile_range,
+                                                            const float4 *__restrict__ ttab, int S,
+                                                            uint2 *__restrict__ tile_walk,
                                                             const uint32_t *__restrict__ tile_order,
-                                                            const uint32_t *__restrict__ vals,
+                                                            const uint2 *__restrict__ srange,
+                                                            const uint32_t *__restrict__ svals,
+                                                            const uint4 *__restrict__ sranges,
                                                             const Record *__restrict__ rec,
                                                             const uint32_t *__restrict__ misc, Params p,
-                                                            float *__restrict__ rgb, float *__restrict__ Tout,
-                                                            float *__restrict__ Tfin, uint32_t *__restrict__ last_out,
+                                                            float *__restrict__ rgb,
+                                                            float *__restrict__ Tout, float *__restrict__ Tfin,
+                                                            uint32_t *__restrict__ last_out,
                                                             uint2 *__restrict__ evals) {
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
+    static_assert(kParts == 1, "one block per tile: the block records the tile's walk");
     __shared__ float4 s_rec[BATCH * 4];
+    __shared__ uint32_t s_id[BATCH + kThreads];
+    __shared__ uint32_t s_pos[BATCH + kThreads];
+    __shared__ uint32_t s_wcnt[kThreads / 32];
+    __shared__ uint32_t s_maxlast, s_walkpos;
     __shared__ int s_cam;
     if (misc[kMiscStatus] & kStatusCapacity) return;
     const int t = (int)tile_order[blockIdx.x / kParts], part = blockIdx.x % kParts;
@@ -88,7 +198,10 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
     __syncthreads();
     const DevCam &cam = cams[s_cam];
     const int lt = t - cam.tile_base;
-    if (lt >= cam.tiles_x * cam.tiles_y) return;  // padding tile of a camera slot
+    if (lt >= cam.tiles_x * cam.tiles_y) {  // padding tile of a camera slot
+        if (tid == 0) tile_walk[t] = make_uint2(0u, 0u);
+        return;
+    }
     const int cx = lt % cam.tiles_x, cy = lt / cam.tiles_x;
     const int x = cx * kTile + (tid & (kTile - 1));
     const int y = cy * kTile + part * ROWS + (tid / kTile);
@@ -102,17 +215,28 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         dy = th.y * ph.x;
         dz = th.y * ph.y;
     }
-    const uint2 range = tile_range[t];
+    const float4 col = ttab[cam.tcol_off + cx], row = ttab[cam.trow_off + cy];
+    const uint2 sr = srange[cam.stile_base + (cy / S) * cam.stiles_x + cx / S];
+    if (tid == 0) {
+        s_maxlast = 0u;
+        s_walkpos = sr.x;
+    }
     const float log2_amin = log2f(p.alpha_min);
     float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
     uint32_t last = 0, n_eval = 0, n_applied = 0;
     bool done = !inside;
+    uint32_t pos = sr.x, n_list = 0;
+    int s_cnt = 0, want = BATCH < 64 ? BATCH : 64;
 
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += BATCH) {
+    while (true) {
         if (__syncthreads_count(done) == kThreads) break;
-        const int cnt = (int)min((uint32_t)BATCH, range.y - b0);
+        // batches grow 64, 128, ... BATCH: most rays of a dense scene stop early
+        fill_list<kThreads>(svals, sranges, col, row, cx, cy, pos, sr.y, want, s_id, s_pos, s_cnt, s_wcnt);
+        want = min(2 * want, BATCH);
+        const int cnt = min(s_cnt, BATCH);
+        if (cnt == 0) break;
         for (int r = tid; r < cnt; r += kThreads) {
-            const float4 *src = reinterpret_cast<const float4 *>(rec + vals[b0 + r]);
+            const float4 *src = reinterpret_cast<const float4 *>(rec + s_id[r]);
 #pragma unroll
             for (int k = 0; k < 4; ++k) s_rec[r * 4 + k] = src[k];
         }
@@ -138,11 +262,20 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                 cb = fmaf(wgt, e.w, cb);
                 T = Tn;
                 ++n_applied;
-                last = b0 - range.x + (uint32_t)j + 1u;
+                last = n_list + (uint32_t)j + 1u;
             }
         }
+        // the tile's last contributor so far and where it lies in the super-tile list
+        const uint32_t wl = __reduce_max_sync(0xffffffffu, last);
+        if ((tid & 31) == 0) atomicMax(&s_maxlast, wl);
         __syncthreads();
+        if (tid == 0 && s_maxlast > n_list) s_walkpos = s_pos[s_maxlast - 1u - n_list] + 1u;
+        shift_list<kThreads>(s_id, s_pos, cnt, s_cnt);
+        n_list += (uint32_t)cnt;
     }
+    // [sr.x, walkpos) of the super-tile list holds tile-list entries 0 .. maxlast - 1:
+    // the backward reads them back from there
+    if (tid == 0) tile_walk[t] = make_uint2(s_walkpos, s_maxlast);
     if (inside) {
         const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
         rgb[3 * pix + 0] = fmaf(T, cam.bg[0], cr);
@@ -153,6 +286,50 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         last_out[pix] = last;
         evals[pix] = make_uint2(n_eval, n_applied);
     }
+}
+
+// Every tile's full list (no early termination), filtered from its super-tile's
+// list exactly as the renders do. With lists == NULL: count[t] = the list's
+// length; else lists[off[t] + k] = entry k (off in the same array). For inspection.
+__global__ void __launch_bounds__(kTilePix) k_expand_tiles(const DevCam *__restrict__ cams, int ncams,
+                                                          const float4 *__restrict__ ttab, int S,
+                                                          const uint2 *__restrict__ srange,
+                                                          const uint32_t *__restrict__ svals,
+                                                          const uint4 *__restrict__ sranges,
+                                                          const uint32_t *__restrict__ misc,
+                                                          uint32_t *__restrict__ count_or_off,
+                                                          uint32_t *__restrict__ lists, int64_t cap) {
+    __shared__ uint32_t s_id[2 * kTilePix];
+    __shared__ uint32_t s_wcnt[kTilePix / 32];
+    __shared__ int s_cam;
+    if (misc[kMiscStatus] & kStatusCapacity) return;
+    const int t = blockIdx.x, tid = threadIdx.x;
+    if (tid == 0) s_cam = find_cam(cams, ncams, t);
+    __syncthreads();
+    const DevCam &cam = cams[s_cam];
+    const int lt = t - cam.tile_base;
+    if (lt >= cam.tiles_x * cam.tiles_y) {
+        if (!lists && tid == 0) count_or_off[t] = 0u;
+        return;
+    }
+    const int cx = lt % cam.tiles_x, cy = lt / cam.tiles_x;
+    const float4 col = ttab[cam.tcol_off + cx], row = ttab[cam.trow_off + cy];
+    const uint2 sr = srange[cam.stile_base + (cy / S) * cam.stiles_x + cx / S];
+    const int64_t off = lists ? (int64_t)count_or_off[t] : 0;
+    uint32_t pos = sr.x, n_list = 0;
+    int s_cnt = 0;
+    while (true) {
+        fill_list<kTilePix>(svals, sranges, col, row, cx, cy, pos, sr.y, kTilePix, s_id, nullptr, s_cnt, s_wcnt);
+        const int cnt = min(s_cnt, kTilePix);
+        if (cnt == 0) break;
+        if (lists)
+            for (int r = tid; r < cnt; r += kTilePix)
+                if (off + n_list + r < cap) lists[off + n_list + r] = s_id[r];
+        __syncthreads();
+        shift_list<kTilePix>(s_id, nullptr, cnt, s_cnt);
+        n_list += (uint32_t)cnt;
+    }
+    if (!lists && tid == 0) count_or_off[t] = n_list;
 }
 
 // RenderCUDA backward (App. C): reverse traversal of each ray's contributors
@@ -215,9 +392,12 @@ __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const f
 template <int ROWS, int BATCH>
 __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(const DevCam *__restrict__ cams, int ncams,
                                                             const float2 *__restrict__ ptab,
-                                                            const uint2 *__restrict__ tile_range,
+                                                            const float4 *__restrict__ ttab, int S,
+                                                            const uint2 *__restrict__ tile_walk,
                                                             const uint32_t *__restrict__ tile_order,
-                                                            const uint32_t *__restrict__ vals,
+                                                            const uint2 *__restrict__ srange,
+                                                            const uint32_t *__restrict__ svals,
+                                                            const uint4 *__restrict__ sranges,
                                                             const Record *__restrict__ rec,
                                                             const uint32_t *__restrict__ misc, Params p,
                                                             const float *__restrict__ dL_drgb,
@@ -227,6 +407,8 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     __shared__ float4 s_rec[BATCH * 4];
     __shared__ float s_acc[BATCH][17];
+    __shared__ uint32_t s_id[BATCH + kThreads];
+    __shared__ uint32_t s_wcnt[kThreads / 32];
     __shared__ uint32_t s_last;
     __shared__ int s_cam;
     if (misc[kMiscStatus] & kStatusCapacity) return;
@@ -267,24 +449,35 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
     ray.S2 = ray.T * cam.bg[2];
     const uint32_t warp_last = __reduce_max_sync(0xffffffffu, ray.last);
     if (lane == 0) atomicMax(&s_last, warp_last);
-    const uint2 range = tile_range[t];
+    const float4 col = ttab[cam.tcol_off + cx], row = ttab[cam.trow_off + cy];
+    const uint2 sr = srange[cam.stile_base + (cy / S) * cam.stiles_x + cx / S];
+    const uint2 walk = tile_walk[t];
     const float log2_amin = log2f(p.alpha_min);
     __syncthreads();
     const uint32_t block_last = s_last;
-
-    for (int32_t b_end = (int32_t)block_last; b_end > 0; b_end -= BATCH) {
-        const int32_t b_start = max(0, b_end - BATCH);
-        const int cnt = b_end - b_start;
-        for (int r = tid; r < cnt; r += kThreads) {
-            const float4 *src = reinterpret_cast<const float4 *>(rec + vals[range.x + b_start + r]);
+    if (block_last == 0) return;
+    // the tile's list read back to front from just past the tile's last
+    // contributor (recorded by the forward): entry r of a batch has list index top - 1 - r
+    uint32_t pos = walk.x, top = walk.y;
+    int s_cnt = 0;
+    while (top > 0) {
+        fill_list_rev<kThreads, BATCH>(svals, sranges, col, row, cx, cy, pos, sr.x, s_id, s_cnt, s_wcnt);
+        const int cnt = min(s_cnt, BATCH);
+        if (cnt == 0) break;
+        // entries at or beyond the block's last contributor are not walked
+        const int skip = top > block_last ? (int)min((uint32_t)cnt, top - block_last) : 0;
+        for (int r = skip + tid; r < cnt; r += kThreads) {
+            const float4 *src = reinterpret_cast<const float4 *>(rec + s_id[r]);
 #pragma unroll
             for (int k = 0; k < 4; ++k) s_rec[r * 4 + k] = src[k];
         }
-        for (int i = tid; i < cnt * 17; i += kThreads) (&s_acc[0][0])[i] = 0.0f;
+        for (int i = skip * 17 + tid; i < cnt * 17; i += kThreads) (&s_acc[0][0])[i] = 0.0f;
         __syncthreads();
-        const int jj_top = min(cnt, (int)warp_last - b_start) - 1;  // warp-uniform
-        for (int jj = jj_top; jj >= 0; --jj) {
-            const uint32_t j = (uint32_t)(b_start + jj);
+        // this warp's first entry below its rays' last contributor (warp-uniform)
+        const int r0 = max(skip, top > warp_last ? (int)min((uint32_t)cnt, top - warp_last) : 0);
+        for (int r = r0; r < cnt; ++r) {
+            const int jj = r;
+            const uint32_t j = top - 1u - (uint32_t)r;
             float gv[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) gv[k] = 0.0f;
@@ -331,20 +524,21 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
         }
         __syncthreads();
         // flush: one Gaussian of the batch per thread, four float4 atomics
-        for (int r = tid; r < cnt; r += kThreads) {
+        for (int r = skip + tid; r < cnt; r += kThreads) {
             const float *v = s_acc[r];
             bool any = false;
 #pragma unroll
             for (int k = 0; k < 16; ++k) any |= v[k] != 0.0f;
             if (any) {
-                float4 *dst = reinterpret_cast<float4 *>(gacc + vals[range.x + b_start + r]);
+                float4 *dst = reinterpret_cast<float4 *>(gacc + s_id[r]);
                 atomicAdd(dst + 0, make_float4(v[0], v[1], v[2], v[3]));
                 atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
                 atomicAdd(dst + 2, make_float4(v[8], v[9], v[10], v[11]));
                 atomicAdd(dst + 3, make_float4(v[12], v[13], v[14], v[15]));
             }
         }
-        __syncthreads();
+        shift_list<kThreads>(s_id, nullptr, cnt, s_cnt);
+        top -= (uint32_t)cnt;
     }
 }
 
@@ -354,9 +548,18 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
     if (ws->n_tiles == 0) return cudaSuccess;
     constexpr int R = GEER_FWD_ROWS, B = GEER_FWD_BATCH;
     k_render_fwd<R, B><<<(unsigned)(ws->n_tiles * (kTile / R)), R * kTile, 0, s>>>(
-        ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_range, ws->d_tile_order, ws->d_vals[ws->sorted_buf], ws->d_rec, ws->d_misc,
+        ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_tile_order,
+        ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, rgb, T_final,
         ws->d_Tfin, ws->d_last, ws->d_evals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_tiles(const geer_workspace *ws, uint32_t *count_or_off, uint32_t *lists, cudaStream_t s) {
+    if (ws->n_tiles == 0) return cudaSuccess;
+    k_expand_tiles<<<(unsigned)ws->n_tiles, kTilePix, 0, s>>>(ws->d_cams, ws->n_cams, ws->d_tile_tab, ws->super_size,
+                                                             ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges,
+                                                             ws->d_misc, count_or_off, lists, ws->cap_pairs);
     return cudaGetLastError();
 }
 
@@ -364,7 +567,8 @@ cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cu
     if (ws->n_tiles == 0) return cudaSuccess;
     constexpr int R = GEER_BWD_ROWS, B = GEER_BWD_BATCH;
     k_render_bwd<R, B><<<(unsigned)(ws->n_tiles * (kTile / R)), R * kTile, 0, s>>>(
-        ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_range, ws->d_tile_order, ws->d_vals[ws->sorted_buf], ws->d_rec, ws->d_misc,
+        ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_bwd_order,
+        ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, dL_drgb,
         ws->d_Tfin, ws->d_last, ws->d_gacc);
     return cudaGetLastError();

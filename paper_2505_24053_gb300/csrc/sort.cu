@@ -278,16 +278,17 @@ cudaError_t launch_depth_sort(geer_workspace *ws, cudaStream_t s) {
     return cudaSuccess;
 }
 
-// Stable sort of the pairs by tile id (ceil(tile_bits / 8) digits).
+// Stable sort of the (super-tile, item) pairs by super-tile id (one or two
+// 8-bit digits).
 cudaError_t launch_tile_sort(geer_workspace *ws, cudaStream_t s) {
     int cur = 0;
-    for (int p = 0; p < ws->n_tile_passes; ++p) {
+    for (int p = 0; p < ws->n_sort_passes; ++p) {
         cudaError_t e = radix_pass(ws, ws->d_keys, ws->d_vals, cur, kMiscPairs, 1, p, ws->cap_pairs, s);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
     ws->sorted_buf = cur;
-    return cudaSuccess;
+    return launch_sorted_ranges(ws, s);
 }
 
 }  // namespace geer

@@ -45,7 +45,8 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_workspace_destroy", "geer_set_cameras", "geer_preprocess", "geer_bin_sort", "geer_render_fwd",
            "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
            "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc", "geer_set_camera_slots",
-           "geer_enable_timing", "geer_stage_times", "geer_stage_name", "geer_remap_to_native"]
+           "geer_enable_timing", "geer_stage_times", "geer_stage_name", "geer_remap_to_native",
+           "geer_pair_counts"]
 
 _lib = None
 
@@ -87,6 +88,7 @@ def lib(build_if_missing: bool = True):
         "geer_enable_timing": [P, I32],
         "geer_stage_times": [P, P, I32, P, P],
         "geer_remap_to_native": [P, P, P, P, P],
+        "geer_pair_counts": [P, P, P, P, P],
         "geer_l1_loss_grad": [P, P, I64, P, P, P],
         "geer_render_noalloc": [P, P, P, P, P, P],
         "geer_set_camera_slots": [P, P, I32, P, I64, I64, P],
@@ -279,6 +281,19 @@ class Workspace:
         _check(lib().geer_render_counts(self._handle, C.byref(e), C.byref(a), C.byref(w), _stream(stream)),
                "geer_render_counts")
         return int(e.value), int(a.value), int(w.value)
+
+    def pair_counts(self, stream=None):
+        """(tile-Gaussian associations P, super-tile pairs sorted) of the last bin_sort."""
+        t, u = C.c_int64(), C.c_int64()
+        _check(lib().geer_pair_counts(self._handle, C.byref(t), C.byref(u), None, _stream(stream)),
+               "geer_pair_counts")
+        return int(t.value), int(u.value)
+
+    def sort_passes(self, stream=None) -> int:
+        """Radix passes of the super-tile sort for the current cameras."""
+        p = C.c_int32()
+        _check(lib().geer_pair_counts(self._handle, None, None, C.byref(p), _stream(stream)), "geer_pair_counts")
+        return int(p.value)
 
     def enable_timing(self, on: bool = True):
         _check(lib().geer_enable_timing(self._handle, 1 if on else 0), "geer_enable_timing")
