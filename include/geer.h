@@ -205,6 +205,15 @@ geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *value
 geer_status geer_l1_loss_grad(const float *rgb, const float *target, int64_t n_values, float *dL_drgb, float *loss,
                               void *stream);
 
+/* Debug/inspection (synchronous), after geer_render_fwd: per ray (HOST buffers
+ * of n_pixels, any may be NULL) the ray-Gaussian evaluations executed and the
+ * contributors composited (evals [.][2] u32) and the list entries its backward
+ * walks (last u32); per tile (n_tiles) the forward's walk record (walk [.][2]
+ * u32: super-tile list position just past the tile's last contributor, and the
+ * number of tile-list entries before it). */
+geer_status geer_debug_render_state(geer_workspace *ws, uint32_t *evals, uint32_t *last, uint32_t *walk,
+                                    void *stream);
+
 /* Measurement (synchronous): after geer_bin_sort, the number of (tile,
  * Gaussian) associations P, of (super-tile, Gaussian) pairs sorted, and the
  * radix passes of that sort (any pointer may be NULL). */

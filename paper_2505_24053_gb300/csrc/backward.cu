@@ -85,10 +85,38 @@ __global__ void __launch_bounds__(kPBThreads) k_preprocess_bwd(
     {
         const float *src = sh + g0 * NC;
         const float *dsrc = d_sh ? d_sh + g0 * NC : nullptr;
-        for (int i = tid; i < nloc * NC; i += kPBThreads) {
-            const int gl = i / NC, k = i - gl * NC;
-            s_sh[gl * ST + k] = src[i];
-            if (dsrc) s_dsh[gl * ST + k] = dsrc[i];
+        if (nloc == kPBThreads) {
+            // a full block's rows are kPBThreads * NC * 4 bytes (a multiple of 16) from a
+            // 16-byte aligned base: all its 16-byte loads are issued before any is used
+            constexpr int kF = kPBThreads * NC / 4;                // float4 in the block's rows
+            constexpr int kV = (kF + kPBThreads - 1) / kPBThreads;  // per thread
+            float4 a[kV], b[kV];
+#pragma unroll
+            for (int u = 0; u < kV; ++u) {
+                if (u * kPBThreads + tid < kF) {
+                    a[u] = reinterpret_cast<const float4 *>(src)[u * kPBThreads + tid];
+                    if (dsrc) b[u] = reinterpret_cast<const float4 *>(dsrc)[u * kPBThreads + tid];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kV; ++u) {
+                if (u * kPBThreads + tid >= kF) continue;
+                const int i = 4 * (u * kPBThreads + tid);
+                const float va[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
+                const float vb[4] = {b[u].x, b[u].y, b[u].z, b[u].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int gl = (i + q) / NC, k = i + q - gl * NC;
+                    s_sh[gl * ST + k] = va[q];
+                    if (dsrc) s_dsh[gl * ST + k] = vb[q];
+                }
+            }
+        } else {
+            for (int i = tid; i < nloc * NC; i += kPBThreads) {
+                const int gl = i / NC, k = i - gl * NC;
+                s_sh[gl * ST + k] = src[i];
+                if (dsrc) s_dsh[gl * ST + k] = dsrc[i];
+            }
         }
     }
     __syncthreads();

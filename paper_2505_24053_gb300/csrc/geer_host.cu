@@ -716,6 +716,22 @@ geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *value
     return GEER_OK;
 }
 
+geer_status geer_debug_render_state(geer_workspace *ws, uint32_t *evals, uint32_t *last, uint32_t *walk,
+                                    void *stream) {
+    if (!ws) return GEER_ERR_ARG;
+    if (ws->stage < 3) return GEER_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((evals && cudaMemcpyAsync(evals, ws->d_evals, sizeof(uint2) * ws->n_pixels, cudaMemcpyDeviceToHost, s) !=
+                      cudaSuccess) ||
+        (last && cudaMemcpyAsync(last, ws->d_last, sizeof(uint32_t) * ws->n_pixels, cudaMemcpyDeviceToHost, s) !=
+                     cudaSuccess) ||
+        (walk && cudaMemcpyAsync(walk, ws->d_tile_walk, sizeof(uint2) * ws->n_tiles, cudaMemcpyDeviceToHost, s) !=
+                     cudaSuccess) ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    return GEER_OK;
+}
+
 geer_status geer_pair_counts(geer_workspace *ws, int64_t *tile_pairs, int64_t *super_pairs, int32_t *sort_passes,
                              void *stream) {
     if (!ws) return GEER_ERR_ARG;

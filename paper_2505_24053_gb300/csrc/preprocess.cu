@@ -692,7 +692,9 @@ __device__ __forceinline__ uint32_t block_chunk_prefix(uint32_t s, uint32_t *war
 // [start, end) in the sorted super-tile pairs (exclusive scan of its pair
 // count), and the order in which the render blocks take the tiles: by
 // descending length of their super-tile's list (bucketed), so that the costliest
-// tiles start first and the grid does not end on a tail of heavy tiles.
+// tiles start first and the grid does not end on a tail of heavy tiles. (Measured
+// on the 1M-Gaussian fisheye workload: 0.344 ms forward against 0.358 - 0.409 ms
+// with the length capped at 16K - 1K entries and 0.424 ms in tile order.)
 __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict__ cams, int ncams, int S,
                                                        int ntiles, uint2 *__restrict__ srange, int nst,
                                                        const uint32_t *__restrict__ misc,

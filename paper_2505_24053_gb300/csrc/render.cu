@@ -23,6 +23,10 @@ namespace {
 #ifndef GEER_FWD_BATCH
 #define GEER_FWD_BATCH 256
 #endif
+#ifndef GEER_FWD_UNROLL
+#define GEER_FWD_UNROLL 4
+#endif
+constexpr int kFwdUnroll = GEER_FWD_UNROLL;
 #ifndef GEER_BWD_ROWS
 #define GEER_BWD_ROWS 16
 #endif
@@ -242,12 +246,45 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         }
         __syncthreads();
         if (!done) {
-            for (int j = 0; j < cnt; ++j) {
+            // kFwdUnroll entries are evaluated together (independent work for the
+            // scheduler on long walks), then composited strictly in list order
+            int j = 0;
+            for (; j + kFwdUnroll <= cnt && !done; j += kFwdUnroll) {
+                Eval v[kFwdUnroll];
+                float4 e[kFwdUnroll];
+#pragma unroll
+                for (int u = 0; u < kFwdUnroll; ++u) {
+                    const float4 a = s_rec[(j + u) * 4 + 0];  // W00 W01 W02 W10
+                    const float4 b = s_rec[(j + u) * 4 + 1];  // W11 W12 W20 W21
+                    const float4 c = s_rec[(j + u) * 4 + 2];  // W22 ou0 ou1 ou2
+                    e[u] = s_rec[(j + u) * 4 + 3];            // log2 sigma, r, g, b
+                    v[u] = evaluate(a, b, c, e[u], dx, dy, dz, log2_amin);
+                }
+#pragma unroll
+                for (int u = 0; u < kFwdUnroll; ++u) {
+                    ++n_eval;
+                    if (!v[u].hit) continue;
+                    const float alpha = fminf(exp2f(v[u].arg), p.alpha_max);
+                    const float Tn = T * (1.0f - alpha);
+                    if (Tn < p.T_min) {
+                        done = true;
+                        break;
+                    }
+                    const float wgt = alpha * T;
+                    cr = fmaf(wgt, e[u].y, cr);
+                    cg = fmaf(wgt, e[u].z, cg);
+                    cb = fmaf(wgt, e[u].w, cb);
+                    T = Tn;
+                    ++n_applied;
+                    last = n_list + (uint32_t)(j + u) + 1u;
+                }
+            }
+            for (; j < cnt && !done; ++j) {
                 ++n_eval;
-                const float4 a = s_rec[j * 4 + 0];  // W00 W01 W02 W10
-                const float4 b = s_rec[j * 4 + 1];  // W11 W12 W20 W21
-                const float4 c = s_rec[j * 4 + 2];  // W22 ou0 ou1 ou2
-                const float4 e = s_rec[j * 4 + 3];  // log2 sigma, r, g, b
+                const float4 a = s_rec[j * 4 + 0];
+                const float4 b = s_rec[j * 4 + 1];
+                const float4 c = s_rec[j * 4 + 2];
+                const float4 e = s_rec[j * 4 + 3];
                 const Eval v = evaluate(a, b, c, e, dx, dy, dz, log2_amin);
                 if (!v.hit) continue;
                 const float alpha = fminf(exp2f(v.arg), p.alpha_max);

@@ -46,7 +46,7 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
            "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc", "geer_set_camera_slots",
            "geer_enable_timing", "geer_stage_times", "geer_stage_name", "geer_remap_to_native",
-           "geer_pair_counts"]
+           "geer_pair_counts", "geer_debug_render_state"]
 
 _lib = None
 
@@ -89,6 +89,7 @@ def lib(build_if_missing: bool = True):
         "geer_stage_times": [P, P, I32, P, P],
         "geer_remap_to_native": [P, P, P, P, P],
         "geer_pair_counts": [P, P, P, P, P],
+        "geer_debug_render_state": [P, P, P, P, P],
         "geer_l1_loss_grad": [P, P, I64, P, P, P],
         "geer_render_noalloc": [P, P, P, P, P, P],
         "geer_set_camera_slots": [P, P, I32, P, I64, I64, P],
@@ -294,6 +295,19 @@ class Workspace:
         p = C.c_int32()
         _check(lib().geer_pair_counts(self._handle, None, None, C.byref(p), _stream(stream)), "geer_pair_counts")
         return int(p.value)
+
+    def debug_render_state(self, stream=None):
+        """Per ray (evaluations, contributors) [n_pixels, 2] and last [n_pixels]; per tile
+        the forward's walk record [n_tiles, 2] (super-list position, entries)."""
+        npix = sum(c.width * c.height for c in self.cams)
+        ntiles = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in self.cams)
+        ev = np.zeros((npix, 2), np.uint32)
+        last = np.zeros(npix, np.uint32)
+        walk = np.zeros((ntiles, 2), np.uint32)
+        _check(lib().geer_debug_render_state(self._handle, C.c_void_p(ev.ctypes.data), C.c_void_p(last.ctypes.data),
+                                             C.c_void_p(walk.ctypes.data), _stream(stream)),
+               "geer_debug_render_state")
+        return ev, last, walk
 
     def enable_timing(self, on: bool = True):
         _check(lib().geer_enable_timing(self._handle, 1 if on else 0), "geer_enable_timing")
