@@ -394,7 +394,9 @@ __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const f
     contrib = true;
     const float ae = exp2f(v.arg);
     const float alpha = fminf(ae, alpha_max);
-    const float inv_om = __frcp_rn(1.0f - alpha);
+    // approximate reciprocal (within 2 ulp): the correctly rounded one costs more
+    // than the rest of this step's transmittance update
+    const float inv_om = __fdividef(1.0f, 1.0f - alpha);
     const float Ti = r.T * inv_om;  // transmittance in front of this Gaussian
     const float wgt = Ti * alpha;
     gv[1] = fmaf(r.g0, wgt, gv[1]);
