@@ -382,10 +382,10 @@ def run(args):
                                else f"copy bandwidth, {peak_src}",
                 "work": {"evaluations": evals, "applied": applied, "walked_back": walked}}
     tiles = math.ceil(cam.width / 16) * math.ceil(cam.height / 16)
-    # preprocess, live scan, compact, 4 depth passes x 3, gather, 2 scans, emit, offsets,
-    # super-tile sort passes x 3, sorted ranges, render fwd (+ L1 gradient, backward order, render bwd,
+    # preprocess, live scan, compact, 4 depth passes x 2, gather, 2 scans, emit, offsets,
+    # super-tile sort passes x 2, sorted ranges, render fwd (+ L1 gradient, backward order, render bwd,
     # preprocess bwd)
-    launches_per_step = 22 + 3 * sort_passes + (4 if have_bwd else 0)
+    launches_per_step = 18 + 2 * sort_passes + (4 if have_bwd else 0)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,

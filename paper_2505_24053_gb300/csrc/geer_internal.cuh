@@ -12,7 +12,7 @@ constexpr int kTile = 16;                   // BEAP tile edge in rays (a camera 
 constexpr int kTilePix = kTile * kTile;
 constexpr int kPrepThreads = 256;           // preprocess / duplicate block size
 constexpr int kSortThreads = 256;           // onesweep block size (8 warps)
-constexpr int kSortItems = 12;              // keys per thread per onesweep tile
+constexpr int kSortItems = 12;              // keys per thread per sort tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
@@ -33,6 +33,7 @@ enum Misc : int {
     kMiscLive = 5,        // live (camera, Gaussian) items (tile count > 0)
     kMiscTileLo = 6,      // (tile, item) associations P mod 2^32
     kMiscTileHi = 7,      // P / 2^32
+    kMiscSortDone = 8,    // radix histogram blocks finished in the current pass
     kMiscCount = 32
 };
 
