@@ -49,17 +49,35 @@ class Request:
 
 @dataclass
 class Scheduler:
-    """First come, first served admission by free slots and estimated pair memory."""
+    """First come, first served admission by free slots and estimated pair memory.
+
+    With same_kind, a batch takes the queue head and then only queued requests of
+    the head's kind (in arrival order): a batch completes with its costliest
+    request, so mixing a small request into a batch of large ones delays it."""
 
     n_slots: int
     pair_budget: int
     estimates: dict = field(default_factory=dict)   # kind -> estimated pairs
     default_estimate: int = 1
+    same_kind: bool = False
 
     def estimate(self, req: Request) -> int:
         return int(self.estimates.get(req.kind, self.default_estimate))
 
     def admit(self, queue: deque) -> list:
+        if self.same_kind and queue:
+            kind = queue[0].kind
+            batch, used, rest = [], 0, deque()
+            while queue and len(batch) < self.n_slots:
+                r = queue.popleft()
+                e = self.estimate(r)
+                if r.kind != kind or (batch and used + e > self.pair_budget):
+                    rest.append(r)
+                    continue
+                batch.append(r)
+                used += e
+            queue.extendleft(reversed(rest))
+            return batch
         batch, used = [], 0
         while queue and len(batch) < self.n_slots:
             e = self.estimate(queue[0])
@@ -140,7 +158,7 @@ class Engine:
 
     def __init__(self, gaussians: geer.Gaussians, n_slots: int = 4, n_buffers: int = 2,
                  pair_capacity: int = 200_000_000, max_width: int = 1920, max_height: int = 1280,
-                 use_graphs: bool = True):
+                 use_graphs: bool = True, same_kind: bool = False):
         from . import workloads as wl
         self.g = gaussians
         self.n_slots, self.n_buffers = n_slots, n_buffers
@@ -148,7 +166,7 @@ class Engine:
         self.capacity_camera = wl.Camera(wl.PINHOLE, max_width, max_height, math.radians(60))
         self.slot_tiles = math.ceil(max_width / 16) * math.ceil(max_height / 16)
         self.slot_pixels = max_width * max_height
-        self.scheduler = Scheduler(n_slots, int(pair_capacity * 0.9))
+        self.scheduler = Scheduler(n_slots, int(pair_capacity * 0.9), same_kind=same_kind)
         self.buffers = [_Buffer(i, self) for i in range(n_buffers)]
         self.use_graphs = use_graphs
         self.failed: list = []

@@ -46,3 +46,13 @@ def test_summary_percentiles():
     s = summarize(done, 2.0)
     assert s["p50_ms"] == 50.0 and s["p99_ms"] == 99.0 and s["requests"] == 100
     assert s["req_per_s"] == 50.0 and s["batches"] == 25
+
+
+def test_same_kind_batches_keep_arrival_order():
+    s = Scheduler(n_slots=3, pair_budget=10**9, estimates={0: 10, 1: 10}, same_kind=True)
+    q = _reqs([0, 1, 0, 1, 0, 0])
+    assert [r.rid for r in s.admit(q)] == [0, 2, 4]   # the head's kind, in arrival order
+    assert [r.rid for r in q] == [1, 3, 5]             # the others keep their order
+    assert [r.rid for r in s.admit(q)] == [1, 3]
+    assert [r.rid for r in s.admit(q)] == [5]
+    assert not q
