@@ -16,6 +16,7 @@ is the maximum over ranks.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import math
 import os
@@ -228,7 +229,19 @@ def run(args):
     dL = torch.empty_like(rgb)
     loss = torch.empty(1, device=dev)
 
-    def step(ev):
+    def train_step(ev):
+        ev[0].record(stream)
+        ws.preprocess(g)
+        ev[1].record(stream)
+        ws.bin_sort(sync=False)
+        ev[2].record(stream)
+        # training step: forward, L1 loss gradient, backward (gradients accumulate)
+        ws.render_fwd(rgb)
+        geer.l1_loss_grad(rgb, target, dL)
+        ws.render_bwd(g, dL, grads)
+        ev[3].record(stream)
+
+    def fwd_step(ev):
         ev[0].record(stream)
         ws.preprocess(g)
         ev[1].record(stream)
@@ -236,48 +249,52 @@ def run(args):
         ev[2].record(stream)
         ws.render_fwd(rgb)
         ev[3].record(stream)
-        if have_bwd:
-            # training-style step: L1 loss gradient, then the backward (gradients accumulate)
-            geer.l1_loss_grad(rgb, target, dL)
-            ws.render_bwd(g, dL, grads)
-        ev[4].record(stream)
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step([torch.cuda.Event(enable_timing=True) for _ in range(5)])
-    torch.cuda.synchronize()
-    st, pairs = ws.device_status()
-    if st != geer.OK:
-        raise RuntimeError(f"device status after warm-up: {geer.status_string(st)}")
-
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    ws.enable_timing(True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        t_wall = time.perf_counter()
-        for k in range(args.steps):
-            flush.zero_()  # between timed steps, outside the step's events
-            step(evs[k])
+    def timed(step, clk_sample):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
         torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall
-    if world > 1:
-        dist.barrier()
-    st, _ = ws.device_status()
-    if st != geer.OK:
-        raise RuntimeError(f"device status after timed steps: {geer.status_string(st)}")
+        st, _ = ws.device_status()
+        if st != geer.OK:
+            raise RuntimeError(f"device status after warm-up: {geer.status_string(st)}")
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) if clk_sample else contextlib.nullcontext() as clk:
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                flush.zero_()  # between timed steps, outside the step's events
+                step(evs[k])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        if world > 1:
+            dist.barrier()
+        st, _ = ws.device_status()
+        if st != geer.OK:
+            raise RuntimeError(f"device status after timed steps: {geer.status_string(st)}")
+        return evs, wall, clk
+
+    ws.enable_timing(True)
+    train_evs = None
+    if have_bwd:
+        train_evs, t_wall, clk = timed(train_step, True)
+    fwd_evs, fwd_wall, fclk = timed(fwd_step, not have_bwd)
+    if not have_bwd:
+        t_wall, clk = fwd_wall, fclk
     pairs, super_pairs = ws.pair_counts()
-    stage_ms = {k: v[0] for k, v in ws.stage_times().items()}  # mean of the last 64 timed steps
+    stage_ms = {k: v[0] for k, v in ws.stage_times().items()}  # mean of the last 64 recorded occurrences
     ws.enable_timing(False)
-    step_ms = [e[0].elapsed_time(e[4]) for e in evs]
-    prep_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    sort_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    rend_ms = [e[2].elapsed_time(e[3]) for e in evs]
-    bwd_ms = [e[3].elapsed_time(e[4]) for e in evs]
+    main_evs = train_evs if have_bwd else fwd_evs
+    step_ms = [e[0].elapsed_time(e[3]) for e in main_evs]
+    prep_ms = [e[0].elapsed_time(e[1]) for e in main_evs]
+    sort_ms = [e[1].elapsed_time(e[2]) for e in main_evs]
+    rend_ms = [e[2].elapsed_time(e[3]) for e in main_evs]
     value, total_ms = aggregate(float(sum(step_ms)), pixels, args.steps, world, dist, dev)
-    fwd_ms = [a + b + c for a, b, c in zip(prep_ms, sort_ms, rend_ms)]
+    fwd_ms = [e[0].elapsed_time(e[3]) for e in fwd_evs]
     fwd_value = pixels / (statistics.mean(fwd_ms) / 1e3) / 1e6
+    fwd_render_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in fwd_evs)
 
     # end to end through the C ABI with host buffers: H2D of the Gaussians from
     # pinned memory, the step, D2H of the image
@@ -386,8 +403,8 @@ def run(args):
                 "work": {"evaluations": evals, "applied": applied, "walked_back": walked}}
     tiles = math.ceil(cam.width / 16) * math.ceil(cam.height / 16)
     # preprocess, live scan, compact, 4 depth passes x 2, gather, 2 scans, emit, offsets,
-    # super-tile sort passes x 2, sorted ranges, render fwd (+ L1 gradient, backward order, render bwd,
-    # preprocess bwd)
+    # super-tile sort passes x 2, sorted ranges, render forward (+ L1 gradient, backward order,
+    # render backward, preprocess backward)
     launches_per_step = 18 + 2 * sort_passes + (4 if have_bwd else 0)
 
     line = {
@@ -395,14 +412,14 @@ def run(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.workload == 3 else f"workload {args.workload}",
-                   "pass": "fwd+bwd" if have_bwd else "fwd", "gaussians": scene.n,
+                   "pass": "fwd+L1+bwd" if have_bwd else "fwd", "gaussians": scene.n,
                    "pixels_per_gpu": pixels, "pairs": int(pairs), "super_pairs": int(super_pairs),
                    "parallelism": f"replicas x{world}",
                    "l2": "512 MB buffer written between timed steps (outside step events); inputs 236 MB > L2"},
         "fwd_only": {"value": fwd_value, "unit": "Mpix/s", "ms": statistics.mean(fwd_ms)},
         "stages_ms": {"preprocess": statistics.mean(prep_ms), "bin_sort": statistics.mean(sort_ms),
-                      "render_fwd": statistics.mean(rend_ms),
-                      "backward": statistics.mean(bwd_ms) if have_bwd else None},
+                      "render_fwd": fwd_render_ms,
+                      "render_fwd_l1_bwd": statistics.mean(rend_ms) if have_bwd else None},
         "roofline": roofline,
         "stages": stages,
         "remap": remap,

@@ -172,6 +172,161 @@ __device__ __forceinline__ void fill_list_rev(const uint32_t *__restrict__ svals
     }
 }
 
+// Shared-memory working set of one block's walk over its tile's list.
+template <int kThreads, int BATCH>
+struct WalkSmem {
+    float4 rec[BATCH * 4];           // records of the current batch
+    uint32_t id[BATCH + kThreads];   // tile-list entries found by the filter (item ids)
+    uint32_t pos[BATCH + kThreads];  // their positions in the super-tile list (forward)
+    uint32_t wcnt[kThreads / 32];
+    uint32_t maxlast, walkpos;       // the tile's last contributor and its super-list position + 1
+    int cam;
+};
+
+// Per-ray forward state.
+struct FwdRay {
+    float T, cr, cg, cb;
+    uint32_t last, n_eval, n_applied;
+    bool done;
+};
+
+// The tile's forward walk (the per-CSF loop of Algorithm 1): its list is the
+// super-tile list [sr.x, sr.y) filtered by the association test; batches of
+// records are staged in shared memory and each ray composites them front to
+// back until it terminates. On return sm.maxlast / sm.walkpos hold the tile's
+// walk record: [sr.x, walkpos) of the super-tile list holds tile-list entries
+// 0 .. maxlast - 1.
+template <int kThreads, int BATCH>
+__device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, const uint32_t *__restrict__ svals,
+                                             const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
+                                             const Params &p, const float4 &col, const float4 &row, int cx, int cy,
+                                             uint2 sr, float dx, float dy, float dz, FwdRay &f) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        sm.maxlast = 0u;
+        sm.walkpos = sr.x;
+    }
+    const float log2_amin = log2f(p.alpha_min);
+    uint32_t pos = sr.x, n_list = 0;
+    int s_cnt = 0, want = BATCH < 64 ? BATCH : 64;
+    while (true) {
+        if (__syncthreads_count(f.done) == kThreads) break;
+        // batches grow 64, 128, ... BATCH: most rays of a dense scene stop early
+        fill_list<kThreads>(svals, sranges, col, row, cx, cy, pos, sr.y, want, sm.id, sm.pos, s_cnt, sm.wcnt);
+        want = min(2 * want, BATCH);
+        const int cnt = min(s_cnt, BATCH);
+        if (cnt == 0) break;
+        for (int r = tid; r < cnt; r += kThreads) {
+            const float4 *src = reinterpret_cast<const float4 *>(rec + sm.id[r]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sm.rec[r * 4 + k] = src[k];
+        }
+        __syncthreads();
+        if (!f.done) {
+            // kFwdUnroll entries are evaluated together (independent work for the
+            // scheduler on long walks), then composited strictly in list order
+            int j = 0;
+            for (; j + kFwdUnroll <= cnt && !f.done; j += kFwdUnroll) {
+                Eval v[kFwdUnroll];
+                float4 e[kFwdUnroll];
+#pragma unroll
+                for (int u = 0; u < kFwdUnroll; ++u) {
+                    const float4 a = sm.rec[(j + u) * 4 + 0];  // W00 W01 W02 W10
+                    const float4 b = sm.rec[(j + u) * 4 + 1];  // W11 W12 W20 W21
+                    const float4 c = sm.rec[(j + u) * 4 + 2];  // W22 ou0 ou1 ou2
+                    e[u] = sm.rec[(j + u) * 4 + 3];            // log2 sigma, r, g, b
+                    v[u] = evaluate(a, b, c, e[u], dx, dy, dz, log2_amin);
+                }
+#pragma unroll
+                for (int u = 0; u < kFwdUnroll; ++u) {
+                    ++f.n_eval;
+                    if (!v[u].hit) continue;
+                    const float alpha = fminf(exp2f(v[u].arg), p.alpha_max);
+                    const float Tn = f.T * (1.0f - alpha);
+                    if (Tn < p.T_min) {
+                        f.done = true;
+                        break;
+                    }
+                    const float wgt = alpha * f.T;
+                    f.cr = fmaf(wgt, e[u].y, f.cr);
+                    f.cg = fmaf(wgt, e[u].z, f.cg);
+                    f.cb = fmaf(wgt, e[u].w, f.cb);
+                    f.T = Tn;
+                    ++f.n_applied;
+                    f.last = n_list + (uint32_t)(j + u) + 1u;
+                }
+            }
+            for (; j < cnt && !f.done; ++j) {
+                ++f.n_eval;
+                const float4 a = sm.rec[j * 4 + 0];
+                const float4 b = sm.rec[j * 4 + 1];
+                const float4 c = sm.rec[j * 4 + 2];
+                const float4 e = sm.rec[j * 4 + 3];
+                const Eval v = evaluate(a, b, c, e, dx, dy, dz, log2_amin);
+                if (!v.hit) continue;
+                const float alpha = fminf(exp2f(v.arg), p.alpha_max);
+                const float Tn = f.T * (1.0f - alpha);
+                if (Tn < p.T_min) {
+                    f.done = true;
+                    break;
+                }
+                const float wgt = alpha * f.T;
+                f.cr = fmaf(wgt, e.y, f.cr);
+                f.cg = fmaf(wgt, e.z, f.cg);
+                f.cb = fmaf(wgt, e.w, f.cb);
+                f.T = Tn;
+                ++f.n_applied;
+                f.last = n_list + (uint32_t)j + 1u;
+            }
+        }
+        // the tile's last contributor so far and where it lies in the super-tile list
+        const uint32_t wl = __reduce_max_sync(0xffffffffu, f.last);
+        if ((tid & 31) == 0) atomicMax(&sm.maxlast, wl);
+        __syncthreads();
+        if (tid == 0 && sm.maxlast > n_list) sm.walkpos = sm.pos[sm.maxlast - 1u - n_list] + 1u;
+        shift_list<kThreads>(sm.id, sm.pos, cnt, s_cnt);
+        n_list += (uint32_t)cnt;
+    }
+    __syncthreads();
+}
+
+// The block's rays and tile: camera, tile coordinates, ray direction (from the
+// per-pixel (sin, cos) tables of the BEAP angles), the tile's association
+// table entries and super-tile list. Returns false for a padding tile.
+struct TileRay {
+    int cx, cy, x, y;
+    bool inside;
+    float dx, dy, dz;
+    float4 col, row;
+    uint2 sr;
+};
+
+__device__ __forceinline__ bool tile_ray(const DevCam &cam, int t, int row0, const float2 *__restrict__ ptab,
+                                         const float4 *__restrict__ ttab, const uint2 *__restrict__ srange, int S,
+                                         TileRay &r) {
+    const int lt = t - cam.tile_base;
+    if (lt >= cam.tiles_x * cam.tiles_y) return false;  // padding tile of a camera slot
+    r.cx = lt % cam.tiles_x;
+    r.cy = lt / cam.tiles_x;
+    r.x = r.cx * kTile + ((int)threadIdx.x & (kTile - 1));
+    r.y = r.cy * kTile + row0 + ((int)threadIdx.x / kTile);
+    r.inside = r.x < cam.width && r.y < cam.height;
+    r.dx = 0.0f;
+    r.dy = 0.0f;
+    r.dz = 1.0f;
+    if (r.inside) {
+        const float2 th = ptab[cam.pcol_off + r.x];  // (sin theta, cos theta)
+        const float2 ph = ptab[cam.prow_off + r.y];  // (sin phi, cos phi)
+        r.dx = th.x * ph.y;
+        r.dy = th.y * ph.x;
+        r.dz = th.y * ph.y;
+    }
+    r.col = ttab[cam.tcol_off + r.cx];
+    r.row = ttab[cam.trow_off + r.cy];
+    r.sr = srange[cam.stile_base + (r.cy / S) * cam.stiles_x + r.cx / S];
+    return true;
+}
+
 template <int ROWS, int BATCH>
 __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
                                                             const float2 *__restrict__ ptab,
@@ -189,139 +344,30 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                                             uint2 *__restrict__ evals) {
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     static_assert(kParts == 1, "one block per tile: the block records the tile's walk");
-    __shared__ float4 s_rec[BATCH * 4];
-    __shared__ uint32_t s_id[BATCH + kThreads];
-    __shared__ uint32_t s_pos[BATCH + kThreads];
-    __shared__ uint32_t s_wcnt[kThreads / 32];
-    __shared__ uint32_t s_maxlast, s_walkpos;
-    __shared__ int s_cam;
+    __shared__ WalkSmem<kThreads, BATCH> sm;
     if (misc[kMiscStatus] & kStatusCapacity) return;
-    const int t = (int)tile_order[blockIdx.x / kParts], part = blockIdx.x % kParts;
-    const int tid = threadIdx.x;
-    if (tid == 0) s_cam = find_cam(cams, ncams, t);
+    const int t = (int)tile_order[blockIdx.x];
+    if (threadIdx.x == 0) sm.cam = find_cam(cams, ncams, t);
     __syncthreads();
-    const DevCam &cam = cams[s_cam];
-    const int lt = t - cam.tile_base;
-    if (lt >= cam.tiles_x * cam.tiles_y) {  // padding tile of a camera slot
-        if (tid == 0) tile_walk[t] = make_uint2(0u, 0u);
+    const DevCam &cam = cams[sm.cam];
+    TileRay tr;
+    if (!tile_ray(cam, t, 0, ptab, ttab, srange, S, tr)) {
+        if (threadIdx.x == 0) tile_walk[t] = make_uint2(0u, 0u);
         return;
     }
-    const int cx = lt % cam.tiles_x, cy = lt / cam.tiles_x;
-    const int x = cx * kTile + (tid & (kTile - 1));
-    const int y = cy * kTile + part * ROWS + (tid / kTile);
-    const bool inside = x < cam.width && y < cam.height;
-
-    float dx = 0.0f, dy = 0.0f, dz = 1.0f;
-    if (inside) {
-        const float2 th = ptab[cam.pcol_off + x];  // (sin theta, cos theta)
-        const float2 ph = ptab[cam.prow_off + y];  // (sin phi, cos phi)
-        dx = th.x * ph.y;
-        dy = th.y * ph.x;
-        dz = th.y * ph.y;
-    }
-    const float4 col = ttab[cam.tcol_off + cx], row = ttab[cam.trow_off + cy];
-    const uint2 sr = srange[cam.stile_base + (cy / S) * cam.stiles_x + cx / S];
-    if (tid == 0) {
-        s_maxlast = 0u;
-        s_walkpos = sr.x;
-    }
-    const float log2_amin = log2f(p.alpha_min);
-    float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-    uint32_t last = 0, n_eval = 0, n_applied = 0;
-    bool done = !inside;
-    uint32_t pos = sr.x, n_list = 0;
-    int s_cnt = 0, want = BATCH < 64 ? BATCH : 64;
-
-    while (true) {
-        if (__syncthreads_count(done) == kThreads) break;
-        // batches grow 64, 128, ... BATCH: most rays of a dense scene stop early
-        fill_list<kThreads>(svals, sranges, col, row, cx, cy, pos, sr.y, want, s_id, s_pos, s_cnt, s_wcnt);
-        want = min(2 * want, BATCH);
-        const int cnt = min(s_cnt, BATCH);
-        if (cnt == 0) break;
-        for (int r = tid; r < cnt; r += kThreads) {
-            const float4 *src = reinterpret_cast<const float4 *>(rec + s_id[r]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) s_rec[r * 4 + k] = src[k];
-        }
-        __syncthreads();
-        if (!done) {
-            // kFwdUnroll entries are evaluated together (independent work for the
-            // scheduler on long walks), then composited strictly in list order
-            int j = 0;
-            for (; j + kFwdUnroll <= cnt && !done; j += kFwdUnroll) {
-                Eval v[kFwdUnroll];
-                float4 e[kFwdUnroll];
-#pragma unroll
-                for (int u = 0; u < kFwdUnroll; ++u) {
-                    const float4 a = s_rec[(j + u) * 4 + 0];  // W00 W01 W02 W10
-                    const float4 b = s_rec[(j + u) * 4 + 1];  // W11 W12 W20 W21
-                    const float4 c = s_rec[(j + u) * 4 + 2];  // W22 ou0 ou1 ou2
-                    e[u] = s_rec[(j + u) * 4 + 3];            // log2 sigma, r, g, b
-                    v[u] = evaluate(a, b, c, e[u], dx, dy, dz, log2_amin);
-                }
-#pragma unroll
-                for (int u = 0; u < kFwdUnroll; ++u) {
-                    ++n_eval;
-                    if (!v[u].hit) continue;
-                    const float alpha = fminf(exp2f(v[u].arg), p.alpha_max);
-                    const float Tn = T * (1.0f - alpha);
-                    if (Tn < p.T_min) {
-                        done = true;
-                        break;
-                    }
-                    const float wgt = alpha * T;
-                    cr = fmaf(wgt, e[u].y, cr);
-                    cg = fmaf(wgt, e[u].z, cg);
-                    cb = fmaf(wgt, e[u].w, cb);
-                    T = Tn;
-                    ++n_applied;
-                    last = n_list + (uint32_t)(j + u) + 1u;
-                }
-            }
-            for (; j < cnt && !done; ++j) {
-                ++n_eval;
-                const float4 a = s_rec[j * 4 + 0];
-                const float4 b = s_rec[j * 4 + 1];
-                const float4 c = s_rec[j * 4 + 2];
-                const float4 e = s_rec[j * 4 + 3];
-                const Eval v = evaluate(a, b, c, e, dx, dy, dz, log2_amin);
-                if (!v.hit) continue;
-                const float alpha = fminf(exp2f(v.arg), p.alpha_max);
-                const float Tn = T * (1.0f - alpha);
-                if (Tn < p.T_min) {
-                    done = true;
-                    break;
-                }
-                const float wgt = alpha * T;
-                cr = fmaf(wgt, e.y, cr);
-                cg = fmaf(wgt, e.z, cg);
-                cb = fmaf(wgt, e.w, cb);
-                T = Tn;
-                ++n_applied;
-                last = n_list + (uint32_t)j + 1u;
-            }
-        }
-        // the tile's last contributor so far and where it lies in the super-tile list
-        const uint32_t wl = __reduce_max_sync(0xffffffffu, last);
-        if ((tid & 31) == 0) atomicMax(&s_maxlast, wl);
-        __syncthreads();
-        if (tid == 0 && s_maxlast > n_list) s_walkpos = s_pos[s_maxlast - 1u - n_list] + 1u;
-        shift_list<kThreads>(s_id, s_pos, cnt, s_cnt);
-        n_list += (uint32_t)cnt;
-    }
-    // [sr.x, walkpos) of the super-tile list holds tile-list entries 0 .. maxlast - 1:
-    // the backward reads them back from there
-    if (tid == 0) tile_walk[t] = make_uint2(s_walkpos, s_maxlast);
-    if (inside) {
-        const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
-        rgb[3 * pix + 0] = fmaf(T, cam.bg[0], cr);
-        rgb[3 * pix + 1] = fmaf(T, cam.bg[1], cg);
-        rgb[3 * pix + 2] = fmaf(T, cam.bg[2], cb);
-        if (Tout) Tout[pix] = T;
-        Tfin[pix] = T;
-        last_out[pix] = last;
-        evals[pix] = make_uint2(n_eval, n_applied);
+    FwdRay f{1.0f, 0.0f, 0.0f, 0.0f, 0u, 0u, 0u, !tr.inside};
+    forward_walk<kThreads, BATCH>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy, tr.dz,
+                                  f);
+    if (threadIdx.x == 0) tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
+    if (tr.inside) {
+        const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
+        rgb[3 * pix + 0] = fmaf(f.T, cam.bg[0], f.cr);
+        rgb[3 * pix + 1] = fmaf(f.T, cam.bg[1], f.cg);
+        rgb[3 * pix + 2] = fmaf(f.T, cam.bg[2], f.cb);
+        if (Tout) Tout[pix] = f.T;
+        Tfin[pix] = f.T;
+        last_out[pix] = f.last;
+        evals[pix] = make_uint2(f.n_eval, f.n_applied);
     }
 }
 
@@ -428,104 +474,47 @@ __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const f
     }
 }
 
-template <int ROWS, int BATCH>
-__global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(const DevCam *__restrict__ cams, int ncams,
-                                                            const float2 *__restrict__ ptab,
-                                                            const float4 *__restrict__ ttab, int S,
-                                                            const uint2 *__restrict__ tile_walk,
-                                                            const uint32_t *__restrict__ tile_order,
-                                                            const uint2 *__restrict__ srange,
-                                                            const uint32_t *__restrict__ svals,
-                                                            const uint4 *__restrict__ sranges,
-                                                            const Record *__restrict__ rec,
-                                                            const uint32_t *__restrict__ misc, Params p,
-                                                            const float *__restrict__ dL_drgb,
-                                                            const float *__restrict__ Tfin,
-                                                            const uint32_t *__restrict__ last_in,
-                                                            GradAcc *__restrict__ gacc) {
-    constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
-    __shared__ float4 s_rec[BATCH * 4];
-    __shared__ float s_acc[BATCH][17];
-    __shared__ uint32_t s_id[BATCH + kThreads];
-    __shared__ uint32_t s_wcnt[kThreads / 32];
-    __shared__ uint32_t s_last;
-    __shared__ int s_cam;
-    if (misc[kMiscStatus] & kStatusCapacity) return;
-    const int t = (int)tile_order[blockIdx.x / kParts], part = blockIdx.x % kParts;
+// The tile's backward walk: its list read back to front from the walk record
+// (walk.x: super-list position just past the tile's last contributor, walk.y:
+// that contributor's list index + 1), filtered as in the forward.
+template <int kThreads, int BATCH>
+__device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, float (*s_acc)[17],
+                                              const uint32_t *__restrict__ svals,
+                                              const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
+                                              const Params &p, const float4 &col, const float4 &row, int cx, int cy,
+                                              uint2 sr, uint2 walk, uint32_t warp_last, uint32_t block_last,
+                                              BwdRay &ray, GradAcc *__restrict__ gacc) {
     const int tid = threadIdx.x, lane = tid & 31;
-    if (tid == 0) {
-        s_cam = find_cam(cams, ncams, t);
-        s_last = 0u;
-    }
-    __syncthreads();
-    const DevCam &cam = cams[s_cam];
-    const int lt = t - cam.tile_base;
-    if (lt >= cam.tiles_x * cam.tiles_y) return;  // padding tile of a camera slot
-    const int cx = lt % cam.tiles_x, cy = lt / cam.tiles_x;
-    const int x = cx * kTile + (tid & (kTile - 1));
-    const int y = cy * kTile + part * ROWS + (tid / kTile);
-    BwdRay ray;
-    ray.dx = 0.0f; ray.dy = 0.0f; ray.dz = 1.0f;
-    ray.g0 = ray.g1 = ray.g2 = 0.0f;
-    ray.T = 1.0f;
-    ray.last = 0;
-    if (x < cam.width && y < cam.height) {
-        const float2 th = ptab[cam.pcol_off + x];
-        const float2 ph = ptab[cam.prow_off + y];
-        ray.dx = th.x * ph.y;
-        ray.dy = th.y * ph.x;
-        ray.dz = th.y * ph.y;
-        const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
-        ray.g0 = dL_drgb[3 * pix + 0];
-        ray.g1 = dL_drgb[3 * pix + 1];
-        ray.g2 = dL_drgb[3 * pix + 2];
-        ray.T = Tfin[pix];
-        ray.last = last_in[pix];
-    }
-    // colour composited behind the current contributor (starts with the background)
-    ray.S0 = ray.T * cam.bg[0];
-    ray.S1 = ray.T * cam.bg[1];
-    ray.S2 = ray.T * cam.bg[2];
-    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, ray.last);
-    if (lane == 0) atomicMax(&s_last, warp_last);
-    const float4 col = ttab[cam.tcol_off + cx], row = ttab[cam.trow_off + cy];
-    const uint2 sr = srange[cam.stile_base + (cy / S) * cam.stiles_x + cx / S];
-    const uint2 walk = tile_walk[t];
     const float log2_amin = log2f(p.alpha_min);
-    __syncthreads();
-    const uint32_t block_last = s_last;
-    if (block_last == 0) return;
-    // the tile's list read back to front from just past the tile's last
-    // contributor (recorded by the forward): entry r of a batch has list index top - 1 - r
+    // entry r of a batch has list index top - 1 - r
     uint32_t pos = walk.x, top = walk.y;
     int s_cnt = 0;
     while (top > 0) {
-        fill_list_rev<kThreads, BATCH>(svals, sranges, col, row, cx, cy, pos, sr.x, s_id, s_cnt, s_wcnt);
+        fill_list_rev<kThreads, BATCH>(svals, sranges, col, row, cx, cy, pos, sr.x, sm.id, s_cnt, sm.wcnt);
         const int cnt = min(s_cnt, BATCH);
         if (cnt == 0) break;
         // entries at or beyond the block's last contributor are not walked
         const int skip = top > block_last ? (int)min((uint32_t)cnt, top - block_last) : 0;
         for (int r = skip + tid; r < cnt; r += kThreads) {
-            const float4 *src = reinterpret_cast<const float4 *>(rec + s_id[r]);
+            const float4 *src = reinterpret_cast<const float4 *>(rec + sm.id[r]);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) s_rec[r * 4 + k] = src[k];
+            for (int k = 0; k < 4; ++k) sm.rec[r * 4 + k] = src[k];
         }
         for (int i = skip * 17 + tid; i < cnt * 17; i += kThreads) (&s_acc[0][0])[i] = 0.0f;
         __syncthreads();
         // this warp's first entry below its rays' last contributor (warp-uniform)
         const int r0 = max(skip, top > warp_last ? (int)min((uint32_t)cnt, top - warp_last) : 0);
         for (int r = r0; r < cnt; ++r) {
-            const int jj = r;
             const uint32_t j = top - 1u - (uint32_t)r;
             float gv[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) gv[k] = 0.0f;
             bool contrib = false;
             if (j < ray.last) {
-                const float4 a = s_rec[jj * 4 + 0];
-                const float4 b = s_rec[jj * 4 + 1];
-                const float4 c = s_rec[jj * 4 + 2];
-                const float4 e = s_rec[jj * 4 + 3];
+                const float4 a = sm.rec[r * 4 + 0];
+                const float4 b = sm.rec[r * 4 + 1];
+                const float4 c = sm.rec[r * 4 + 2];
+                const float4 e = sm.rec[r * 4 + 3];
                 ray_gradient(ray, a, b, c, e, log2_amin, p.alpha_max, gv, contrib);
             }
             if (__any_sync(0xffffffffu, contrib)) {
@@ -558,7 +547,7 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
                     gv[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
                 }
                 gv[0] += __shfl_xor_sync(0xffffffffu, gv[0], 1);
-                if ((lane & 1) == 0) atomicAdd(&s_acc[jj][lane >> 1], gv[0]);
+                if ((lane & 1) == 0) atomicAdd(&s_acc[r][lane >> 1], gv[0]);
             }
         }
         __syncthreads();
@@ -569,16 +558,83 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
 #pragma unroll
             for (int k = 0; k < 16; ++k) any |= v[k] != 0.0f;
             if (any) {
-                float4 *dst = reinterpret_cast<float4 *>(gacc + s_id[r]);
+                float4 *dst = reinterpret_cast<float4 *>(gacc + sm.id[r]);
                 atomicAdd(dst + 0, make_float4(v[0], v[1], v[2], v[3]));
                 atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
                 atomicAdd(dst + 2, make_float4(v[8], v[9], v[10], v[11]));
                 atomicAdd(dst + 3, make_float4(v[12], v[13], v[14], v[15]));
             }
         }
-        shift_list<kThreads>(s_id, nullptr, cnt, s_cnt);
+        shift_list<kThreads>(sm.id, nullptr, cnt, s_cnt);
         top -= (uint32_t)cnt;
     }
+}
+
+// Backward ray state at the end of the forward: direction, dL/dC, final
+// transmittance and last contributor; the colour behind starts with the background.
+__device__ __forceinline__ BwdRay bwd_ray(const TileRay &tr, const DevCam &cam, float g0, float g1, float g2, float T,
+                                          uint32_t last) {
+    BwdRay r;
+    r.dx = tr.dx;
+    r.dy = tr.dy;
+    r.dz = tr.dz;
+    r.g0 = g0;
+    r.g1 = g1;
+    r.g2 = g2;
+    r.T = T;
+    r.last = last;
+    r.S0 = T * cam.bg[0];
+    r.S1 = T * cam.bg[1];
+    r.S2 = T * cam.bg[2];
+    return r;
+}
+
+template <int ROWS, int BATCH>
+__global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(const DevCam *__restrict__ cams, int ncams,
+                                                                           const float2 *__restrict__ ptab,
+                                                                           const float4 *__restrict__ ttab, int S,
+                                                                           const uint2 *__restrict__ tile_walk,
+                                                                           const uint32_t *__restrict__ tile_order,
+                                                                           const uint2 *__restrict__ srange,
+                                                                           const uint32_t *__restrict__ svals,
+                                                                           const uint4 *__restrict__ sranges,
+                                                                           const Record *__restrict__ rec,
+                                                                           const uint32_t *__restrict__ misc, Params p,
+                                                                           const float *__restrict__ dL_drgb,
+                                                                           const float *__restrict__ Tfin,
+                                                                           const uint32_t *__restrict__ last_in,
+                                                                           GradAcc *__restrict__ gacc) {
+    constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
+    __shared__ WalkSmem<kThreads, BATCH> sm;
+    __shared__ float s_acc[BATCH][17];
+    if (misc[kMiscStatus] & kStatusCapacity) return;
+    const int t = (int)tile_order[blockIdx.x / kParts], part = blockIdx.x % kParts;
+    if (threadIdx.x == 0) {
+        sm.cam = find_cam(cams, ncams, t);
+        sm.maxlast = 0u;
+    }
+    __syncthreads();
+    const DevCam &cam = cams[sm.cam];
+    TileRay tr;
+    if (!tile_ray(cam, t, part * ROWS, ptab, ttab, srange, S, tr)) return;
+    float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, T = 1.0f;
+    uint32_t last = 0;
+    if (tr.inside) {
+        const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
+        g0 = dL_drgb[3 * pix + 0];
+        g1 = dL_drgb[3 * pix + 1];
+        g2 = dL_drgb[3 * pix + 2];
+        T = Tfin[pix];
+        last = last_in[pix];
+    }
+    BwdRay ray = bwd_ray(tr, cam, g0, g1, g2, T, last);
+    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
+    if ((threadIdx.x & 31) == 0) atomicMax(&sm.maxlast, warp_last);
+    __syncthreads();
+    const uint32_t block_last = sm.maxlast;
+    if (block_last == 0) return;
+    backward_walk<kThreads, BATCH>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr,
+                                   tile_walk[t], warp_last, block_last, ray, gacc);
 }
 
 }  // namespace

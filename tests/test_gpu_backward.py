@@ -175,3 +175,4 @@ def test_backward_full_size_sampled_pixels(geer, orc, cfg, per_cam):
         ref = gi if ref is None else {k: ref[k] + gi[k] for k in ref}
         off += cam.pixels
     _compare(g, ref, f"workload{cfg}")
+
