@@ -212,20 +212,22 @@ def run(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
 
-    scene = wl.config_scene(args.workload)
-    cam = wl.config_cameras(args.workload)[0]
+    scene = wl.config_scene(args.workload, n=args.gaussians)
+    cams = wl.config_cameras(args.workload)
+    cam = cams[0]
     g = geer.Gaussians.from_scene(scene)
-    r = geer.Renderer([cam], scene.n, scene.sh_degree)
+    r = geer.Renderer(cams, scene.n, scene.sh_degree)
     P = r.prepare(g)  # sizes the pair capacity (synchronous count), then everything stays asynchronous
     ws = r.ws
-    pixels = cam.pixels * 1
+    pixels = sum(c.pixels for c in cams)
     rgb = torch.empty((pixels, 3), dtype=torch.float32, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > 129 MB L2
     stream = torch.cuda.current_stream()
     grads = {k: torch.zeros_like(v) for k, v in (("mean", g.mean), ("scale", g.scale), ("quat", g.quat),
                                                  ("opacity", g.opacity), ("sh", g.sh))}
     have_bwd = not args.fwd_only
-    target = torch.as_tensor(wl.l1_target(cam, seed=3), device=dev).reshape(pixels, 3)
+    target = torch.as_tensor(np.concatenate([wl.l1_target(c, seed=3 + i).reshape(-1, 3) for i, c in enumerate(cams)]),
+                             device=dev)
     dL = torch.empty_like(rgb)
     loss = torch.empty(1, device=dev)
 
@@ -327,13 +329,13 @@ def run(args):
     # remap of the BEAP render to the native camera image: an optional output
     # stage, timed on its own (not part of the step or of Mpix/s)
     native = torch.empty_like(rgb)
-    beap_img = rgb.view(cam.height, cam.width, 3)
+    beap_img = rgb[:cam.pixels].view(cam.height, cam.width, 3)
     r_evs = []
     for k in range(3 + 20):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        geer.remap_to_native(beap_img, cam, out=native.view(cam.height, cam.width, 3))
+        geer.remap_to_native(beap_img, cam, out=native[:cam.pixels].view(cam.height, cam.width, 3))
         e1.record(stream)
         if k >= 3:
             r_evs.append((e0, e1))
@@ -347,8 +349,8 @@ def run(args):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    n_items = scene.n  # one camera
-    live = n_items  # live items <= items; equal here (every Gaussian of the cube is in the 190 deg view)
+    n_items = scene.n * len(cams)  # (camera, Gaussian) items
+    live = ws.live_items()
     sort_passes = ws.sort_passes()
     sh_bytes = 4 * 3 * (scene.sh_degree + 1) ** 2
     g_bytes = 4 * (3 + 3 + 4 + 1) + sh_bytes
@@ -389,9 +391,9 @@ def run(args):
             src = os.path.join(ROOT, "paper_2505_24053_gb300", "csrc", tr["source"])
             if hashlib.sha1(open(src, "rb").read()).hexdigest() == tr["source_sha1"]:
                 traffic = tr["bytes_per_launch"]
-    remap_gbs = 24 * pixels / (remap_ms / 1e3) / 1e9  # 12 B read + 12 B written per native pixel
+    remap_gbs = 24 * cam.pixels / (remap_ms / 1e3) / 1e9  # 12 B read + 12 B written per native pixel
     remap = {"ms": remap_ms, "bound": "hbm", "achieved": remap_gbs, "peak": hbm_peak, "unit": "GB/s",
-             "frac": remap_gbs / hbm_peak, "algorithmic_bytes": 24 * pixels,
+             "frac": remap_gbs / hbm_peak, "algorithmic_bytes": 24 * cam.pixels,
              "note": "BEAP -> native Kannala-Brandt resampling, timed separately, not in value"}
     d = stages[dom]
     roofline = {"bound": d["bound"], "kernel": kernel_of[dom], "achieved": d["achieved"],
@@ -451,7 +453,9 @@ def main():
     ap.add_argument("--serving-warmup", type=float, default=1.0)
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--ref-pixels", type=int, default=24)
-    ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3],
+    ap.add_argument("--gaussians", type=int, default=None,
+                    help="scene size override (the workload's distribution with fewer Gaussians; profiling)")
+    ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3, 5],
                     help="3 = the headline configuration; 1, 2 = smaller cases for profiling")
     args = ap.parse_args()
     if args.warmup < 3:

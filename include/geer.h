@@ -215,10 +215,11 @@ geer_status geer_debug_render_state(geer_workspace *ws, uint32_t *evals, uint32_
                                     void *stream);
 
 /* Measurement (synchronous): after geer_bin_sort, the number of (tile,
- * Gaussian) associations P, of (super-tile, Gaussian) pairs sorted, and the
- * radix passes of that sort (any pointer may be NULL). */
+ * Gaussian) associations P, of (super-tile, Gaussian) pairs sorted, the radix
+ * passes of that sort and the live (camera, Gaussian) items (associated with at
+ * least one tile); any pointer may be NULL. */
 geer_status geer_pair_counts(geer_workspace *ws, int64_t *tile_pairs, int64_t *super_pairs, int32_t *sort_passes,
-                             void *stream);
+                             int64_t *live_items, void *stream);
 
 /* Measurement (synchronous): totals over all rays of the last geer_render_fwd
  * of the ray-Gaussian evaluations executed (list entries walked up to early

@@ -82,7 +82,32 @@ struct CamTables {
     int64_t pixels = 0, tiles = 0;
     int32_t super_size = 4;
     int64_t stiles = 0;
+    bool ok = true;  // every camera's flag sets have the interval shape the kernels assume
 };
+
+// The tile columns (or rows) of a camera whose rays have cos >= 0 form one
+// interval, those with cos <= 0 a leading and a trailing run (the BEAP angles
+// grow monotonically): records them for the association counts and checks the
+// shape.
+bool flag_intervals(const float4 *tab, int n, int32_t z[2], int32_t w[2]) {
+    z[0] = n;
+    z[1] = 0;
+    for (int i = 0; i < n; ++i)
+        if (tab[i].z != 0.0f) {
+            z[0] = std::min(z[0], i);
+            z[1] = i + 1;
+        }
+    int a = 0, b = n;
+    while (a < n && tab[a].w != 0.0f) ++a;
+    while (b > a && tab[b - 1].w != 0.0f) --b;
+    w[0] = a;
+    w[1] = b;
+    for (int i = 0; i < n; ++i) {
+        if ((tab[i].z != 0.0f) != (i >= z[0] && i < z[1])) return false;
+        if ((tab[i].w != 0.0f) != (i < a || i >= b)) return false;
+    }
+    return true;
+}
 
 // Super-tile grid of each camera (binning is by super-tiles of S x S tiles; the
 // render filters a super-tile's list down to its tile). Free layouts take the
@@ -198,6 +223,8 @@ void build_tables(const geer_camera *cams, int n, CamTables &out, const uint8_t 
             const double a = beap_angle(j, c.height, fy);
             out.ptab.push_back(make_float2((float)sin(a), (float)cos(a)));
         }
+        out.ok &= flag_intervals(out.ttab.data() + d.tcol_off, d.tiles_x, d.zc, d.wc);
+        out.ok &= flag_intervals(out.ttab.data() + d.trow_off, d.tiles_y, d.zr, d.wr);
         // tiles whose rays all have cos >= 0 (a contiguous middle range)
         d.c0lo = d.tiles_x; d.c0hi = 0;
         for (int tx = 0; tx < d.tiles_x; ++tx) {
@@ -434,6 +461,7 @@ geer_status geer_workspace_size(const geer_camera *cams, int32_t n_cams, int64_t
     if ((int64_t)n_cams * n_gauss > 0xffffffffll || pair_capacity > 0xffffffffll) return GEER_ERR_ARG;
     CamTables t;
     build_tables(cams, n_cams, t);
+    if (!t.ok) return GEER_ERR_UNSUPPORTED;
     *bytes = layout(caps_of(t, n_cams, n_gauss, pair_capacity), nullptr, nullptr);
     return GEER_OK;
 }
@@ -508,6 +536,7 @@ geer_status geer_set_cameras(geer_workspace *ws, const geer_camera *cams, int32_
     if (n_cams > ws->cap_cams) return GEER_ERR_ARG;
     CamTables t;
     build_tables(cams, n_cams, t);
+    if (!t.ok) return GEER_ERR_UNSUPPORTED;
     if (t.pixels > ws->cap_pixels || t.tiles > ws->cap_tiles || (int64_t)t.ttab.size() > ws->cap_tile_tab ||
         (int64_t)t.ptab.size() > ws->cap_pix_tab)
         return GEER_ERR_ARG;
@@ -526,6 +555,7 @@ geer_status geer_set_camera_slots(geer_workspace *ws, const geer_camera *cams, i
     }
     CamTables t;
     build_tables(cams, n_slots, t, active, slot_tiles, slot_pixels);
+    if (!t.ok) return GEER_ERR_UNSUPPORTED;
     if (t.pixels > ws->cap_pixels || t.tiles > ws->cap_tiles || (int64_t)t.ttab.size() > ws->cap_tile_tab ||
         (int64_t)t.ptab.size() > ws->cap_pix_tab)
         return GEER_ERR_ARG;
@@ -733,7 +763,7 @@ geer_status geer_debug_render_state(geer_workspace *ws, uint32_t *evals, uint32_
 }
 
 geer_status geer_pair_counts(geer_workspace *ws, int64_t *tile_pairs, int64_t *super_pairs, int32_t *sort_passes,
-                             void *stream) {
+                             int64_t *live_items, void *stream) {
     if (!ws) return GEER_ERR_ARG;
     if (ws->stage < 2) return GEER_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -744,6 +774,7 @@ geer_status geer_pair_counts(geer_workspace *ws, int64_t *tile_pairs, int64_t *s
     if (tile_pairs) *tile_pairs = ((int64_t)m[kMiscTileHi] << 32) | (int64_t)m[kMiscTileLo];
     if (super_pairs) *super_pairs = ((int64_t)m[kMiscPairsHi] << 32) | (int64_t)m[kMiscTotalLo];
     if (sort_passes) *sort_passes = ws->n_sort_passes;
+    if (live_items) *live_items = m[kMiscLive];
     return GEER_OK;
 }
 
@@ -938,6 +969,8 @@ bool noalloc_tables(const geer_camera &c, NoAllocState &st, int64_t &ntt, int64_
         const double a = beap_angle(j, c.height, fy);
         st.ptab[c.width + j] = make_float2((float)sin(a), (float)cos(a));
     }
+    if (!flag_intervals(st.ttab, d.tiles_x, d.zc, d.wc) || !flag_intervals(st.ttab + d.tiles_x, d.tiles_y, d.zr, d.wr))
+        return false;
     d.c0lo = d.tiles_x; d.c0hi = 0;
     for (int tx = 0; tx < d.tiles_x; ++tx) {
         const float4 v = st.ttab[tx];

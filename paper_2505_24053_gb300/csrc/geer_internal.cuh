@@ -48,6 +48,9 @@ struct DevCam {
     int32_t c0lo, c0hi, r0lo, r0hi;  // tile columns / rows whose rays all have cos >= 0
     int32_t stiles_x;    // super-tiles per row (ceil(tiles_x / super-tile size))
     int32_t stile_base;  // global index of super-tile (0, 0)
+    // tile columns / rows holding rays with cos >= 0 (the z flag): one interval [lo, hi);
+    // with cos <= 0 (the w flag): the runs [0, a) and [b, n)
+    int32_t zc[2], wc[2], zr[2], wr[2];
     int32_t pad_;
     int64_t pix_base;    // offset of pixel (0, 0) in the batched image (in pixels)
     float R[9], t[3];    // world -> camera

@@ -136,17 +136,6 @@ __device__ float lambda2(float sigma, float alpha_min, float pad) {
 }
 
 
-// Bounding box of the association predicate in tile coordinates.
-__device__ __forceinline__ void assoc_bbox(const int rg[8], int ncols, int nrows, int &xa, int &xb, int &ya,
-                                           int &yb) {
-    xa = rg[0] < rg[1] ? rg[0] : ncols;
-    xb = rg[0] < rg[1] ? rg[1] : 0;
-    if (rg[2] < rg[3]) { xa = min(xa, rg[2]); xb = max(xb, rg[3]); }
-    ya = rg[4] < rg[5] ? rg[4] : nrows;
-    yb = rg[4] < rg[5] ? rg[5] : 0;
-    if (rg[6] < rg[7]) { ya = min(ya, rg[6]); yb = max(yb, rg[7]); }
-}
-
 // Real SH of degree <= 3 in the 3DGS convention (Condon-Shortley phase, index
 // l^2 + l + m), written out as polynomials of the unit direction. The constants
 // are K_lm sqrt(2)^(m != 0) = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (* sqrt 2).
@@ -202,6 +191,98 @@ __device__ __forceinline__ bool is_rect(const DevCam &cam, const int rg[8]) {
 }
 
 
+// The association predicate tile_assoc(x, y) = (z_row(y) & x in X0 | w_row(y) & x in X1)
+// & (z_col(x) & y in Y0 | w_col(x) & y in Y1), with the z / w flag sets of the
+// camera's rows and columns (one interval / two runs, DevCam), is a union of
+// products of row and column sets. Its count over a region follows in constant
+// time by inclusion-exclusion, and the set itself is the union of at most nine
+// rectangles.
+__device__ __forceinline__ int ilen(int lo, int hi) { return hi > lo ? hi - lo : 0; }
+
+// Members of [lo, hi) in a flag set: kind 0 the z interval, 1 the w runs, 2 both.
+__device__ __forceinline__ int flag_count(int lo, int hi, const int32_t z[2], const int32_t w[2], int kind) {
+    if (kind == 0) return ilen(max(lo, z[0]), min(hi, z[1]));
+    int alo = lo, ahi = min(hi, w[0]), blo = max(lo, w[1]), bhi = hi;
+    if (kind == 2) {
+        alo = max(alo, z[0]);
+        ahi = min(ahi, z[1]);
+        blo = max(blo, z[0]);
+        bhi = min(bhi, z[1]);
+    }
+    return ilen(alo, ahi) + ilen(blo, bhi);
+}
+
+// Associated tiles of the item with ranges rg in [x0, x1) x [y0, y1).
+__device__ __forceinline__ uint32_t assoc_count(const DevCam &cam, const int rg[8], int x0, int x1, int y0, int y1) {
+    // column sets of the terms a0 (X0), a1 (X1), a0 a1; row sets of b0 (Y0), b1 (Y1), b0 b1
+    const int alo[3] = {rg[0], rg[2], max(rg[0], rg[2])}, ahi[3] = {rg[1], rg[3], min(rg[1], rg[3])};
+    const int blo[3] = {rg[4], rg[6], max(rg[4], rg[6])}, bhi[3] = {rg[5], rg[7], min(rg[5], rg[7])};
+    int64_t total = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            // rows with the flag of term i inside Y_j, columns with the flag of term j inside X_i
+            const int rows = flag_count(max(y0, blo[j]), min(y1, bhi[j]), cam.zr, cam.wr, i);
+            if (rows == 0) continue;
+            const int cols = flag_count(max(x0, alo[i]), min(x1, ahi[i]), cam.zc, cam.wc, j);
+            const int sg = (i == 2) != (j == 2) ? -1 : 1;
+            total += (int64_t)sg * rows * cols;
+        }
+    }
+    return (uint32_t)total;
+}
+
+// The associated set as rectangles {x0, x1, y0, y1} (at most nine, overlapping
+// only on rows / columns that carry both flags); returns their number.
+__device__ __forceinline__ int assoc_rects(const DevCam &cam, const int rg[8], int4 rc[9]) {
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {      // rows of the z interval (i = 0) or the w runs (i = 1) ...
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {  // ... crossed with columns of the z interval or the w runs
+            const int xlo = rg[2 * i], xhi = rg[2 * i + 1];      // X_i
+            const int ylo = rg[4 + 2 * j], yhi = rg[5 + 2 * j];  // Y_j
+            if (xlo >= xhi || ylo >= yhi) continue;
+#pragma unroll
+            for (int ri = 0; ri < 2; ++ri) {
+                if (i == 0 && ri == 1) break;
+                const int r0 = i == 0 ? cam.zr[0] : (ri == 0 ? 0 : cam.wr[1]);
+                const int r1 = i == 0 ? cam.zr[1] : (ri == 0 ? cam.wr[0] : cam.tiles_y);
+                const int y0 = max(ylo, r0), y1 = min(yhi, r1);
+                if (y0 >= y1) continue;
+#pragma unroll
+                for (int ci = 0; ci < 2; ++ci) {
+                    if (j == 0 && ci == 1) break;
+                    const int c0 = j == 0 ? cam.zc[0] : (ci == 0 ? 0 : cam.wc[1]);
+                    const int c1 = j == 0 ? cam.zc[1] : (ci == 0 ? cam.wc[0] : cam.tiles_x);
+                    const int x0 = max(xlo, c0), x1 = min(xhi, c1);
+                    if (x0 < x1) rc[n++] = make_int4(x0, x1, y0, y1);
+                }
+            }
+        }
+    }
+    return n;
+}
+
+// The super-tiles (S x S tiles) holding an associated tile: the union of the
+// rectangles' super-tile boxes, each super-tile visited once.
+template <typename F>
+__device__ __forceinline__ void for_each_super_general(const DevCam &cam, int S, const int rg[8], F f) {
+    int4 rc[9];
+    const int n = assoc_rects(cam, rg, rc);
+    for (int k = 0; k < n; ++k) {
+        const int sx0 = rc[k].x / S, sx1 = (rc[k].y - 1) / S + 1, sy0 = rc[k].z / S, sy1 = (rc[k].w - 1) / S + 1;
+        for (int sy = sy0; sy < sy1; ++sy)
+            for (int sx = sx0; sx < sx1; ++sx) {
+                bool seen = false;
+                for (int q = 0; q < k && !seen; ++q)
+                    seen = sx >= rc[q].x / S && sx <= (rc[q].y - 1) / S && sy >= rc[q].z / S && sy <= (rc[q].w - 1) / S;
+                if (!seen) f(sx, sy);
+            }
+    }
+}
+
 // Block-wide exclusive scan (256 threads); returns the exclusive prefix and the block total.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *wsum, uint32_t &total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -242,7 +323,9 @@ __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sm) {
 }
 
 // Thread per Gaussian, loop over cameras (the Gaussian's parameters are read once).
-__global__ void __launch_bounds__(kPrepThreads) k_preprocess(
+// Two blocks per SM (128 registers): measured faster than one block without
+// spills and than three with more.
+__global__ void __launch_bounds__(kPrepThreads, 2) k_preprocess(
     const DevCam *__restrict__ cams, int ncams, const float4 *__restrict__ ttab, Params p,
     const float *__restrict__ mean, const float *__restrict__ scale, const float *__restrict__ quat,
     const float *__restrict__ opacity, const float *__restrict__ sh, int64_t n, int deg, Record *__restrict__ rec,
@@ -364,16 +447,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_preprocess(
             arc_range(B, rtab, cam.tiles_y, rg[4], rg[5]);
             if (cam.any_row_flip) arc_range(shift_arc(A), ctab, cam.tiles_x, rg[2], rg[3]);
             if (cam.any_col_flip) arc_range(shift_arc(B), rtab, cam.tiles_y, rg[6], rg[7]);
-            if (is_rect(cam, rg)) {
+            if (is_rect(cam, rg))
                 cnt = (uint32_t)(rg[1] - rg[0]) * (uint32_t)(rg[5] - rg[4]);
-            } else {
-                int xa, xb, ya, yb;
-                assoc_bbox(rg, cam.tiles_x, cam.tiles_y, xa, xb, ya, yb);
-                for (int cy = ya; cy < yb; ++cy) {
-                    const float4 row = rtab[cy];
-                    for (int cx = xa; cx < xb; ++cx) cnt += tile_assoc(ctab[cx], row, cx, cy, rg) ? 1u : 0u;
-                }
-            }
+            else
+                cnt = assoc_count(cam, rg, 0, cam.tiles_x, 0, cam.tiles_y);
             float dist = fsq(fa(fa(fm(m0, m0), fm(m1, m1)), fm(m2, m2)));
             key[idx] = __float_as_uint(dist);
             ranges[idx] = make_uint4((uint32_t)rg[0] | ((uint32_t)rg[1] << 16), (uint32_t)rg[2] | ((uint32_t)rg[3] << 16),
@@ -487,40 +564,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_compact(int ncams, int64_t n, 
     }
 }
 
-// The super-tiles (S x S tiles, camera-local coordinates) holding at least one
-// tile associated with an item whose association is not a rectangle, in
-// row-major order.
-template <typename F>
-__device__ __forceinline__ void for_each_super_general(const DevCam &cam, const float4 *ctab, const float4 *rtab,
-                                                       int S, const int rg[8], F f) {
-    int xa, xb, ya, yb;
-    assoc_bbox(rg, cam.tiles_x, cam.tiles_y, xa, xb, ya, yb);
-    if (xa >= xb || ya >= yb) return;
-    for (int sy = ya / S; sy <= (yb - 1) / S; ++sy)
-        for (int sx = xa / S; sx <= (xb - 1) / S; ++sx) {
-            bool any = false;
-            for (int cy = max(ya, sy * S); cy < min(yb, sy * S + S) && !any; ++cy) {
-                const float4 row = rtab[cy];
-                for (int cx = max(xa, sx * S); cx < min(xb, sx * S + S); ++cx)
-                    if (tile_assoc(ctab[cx], row, cx, cy, rg)) {
-                        any = true;
-                        break;
-                    }
-            }
-            if (any) f(sx, sy);
-        }
-}
-
 // Number of (super-tile, item) pairs of an item with c associated tiles.
-__device__ __forceinline__ uint32_t super_count(const DevCam &cam, const float4 *ttab, int S, const int rg[8],
-                                                uint32_t c, bool rect) {
+__device__ __forceinline__ uint32_t super_count(const DevCam &cam, int S, const int rg[8], uint32_t c, bool rect) {
     if (c == 0) return 0u;
     if (rect) {
         const int sx0 = rg[0] / S, sx1 = (rg[1] - 1) / S + 1, sy0 = rg[4] / S, sy1 = (rg[5] - 1) / S + 1;
         return (uint32_t)((sx1 - sx0) * (sy1 - sy0));
     }
     uint32_t k = 0;
-    for_each_super_general(cam, ttab + cam.tcol_off, ttab + cam.trow_off, S, rg, [&](int, int) { ++k; });
+    for_each_super_general(cam, S, rg, [&](int, int) { ++k; });
     return k;
 }
 
@@ -544,7 +596,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_gather_counts(const DevCam *__
         int rg[8];
         unpack_ranges(ranges[item], rg);
         const DevCam &cam = cams[item / (uint32_t)n];
-        sc = super_count(cam, ttab, S, rg, c, is_rect(cam, rg));
+        sc = super_count(cam, S, rg, c, is_rect(cam, rg));
     }
     const uint32_t tot = block_sum_u32(c, red);
     if (threadIdx.x == 0) bs_tile[blockIdx.x] = tot;
@@ -580,7 +632,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
         ci = (int)(item / (uint32_t)n);
         unpack_ranges(ranges[item], rg);
         rect = is_rect(cams[ci], rg);
-        cnt = super_count(cams[ci], ttab, S, rg, count[item], rect);
+        cnt = super_count(cams[ci], S, rg, count[item], rect);
     }
     uint32_t tot;
     const uint32_t pre = block_excl_scan(cnt, wsum, tot);
@@ -631,11 +683,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
     }
     // per-thread emission of the other items (flipped angular ranges)
     if (!rect && fits && cnt > 0) {
-        const float4 *ctab = ttab + cam.tcol_off;
-        const float4 *rtab = ttab + cam.trow_off;
         int64_t o = off;
         const int64_t end = off + cnt;
-        for_each_super_general(cam, ctab, rtab, S, rg, [&](int sx, int sy) {
+        for_each_super_general(cam, S, rg, [&](int sx, int sy) {
             if (o < end) {
                 const uint32_t st = (uint32_t)(cam.stile_base + sy * cam.stiles_x + sx);
                 okeys[o] = st;

@@ -88,7 +88,7 @@ def lib(build_if_missing: bool = True):
         "geer_enable_timing": [P, I32],
         "geer_stage_times": [P, P, I32, P, P],
         "geer_remap_to_native": [P, P, P, P, P],
-        "geer_pair_counts": [P, P, P, P, P],
+        "geer_pair_counts": [P, P, P, P, P, P],
         "geer_debug_render_state": [P, P, P, P, P],
         "geer_l1_loss_grad": [P, P, I64, P, P, P],
         "geer_render_noalloc": [P, P, P, P, P, P],
@@ -286,14 +286,20 @@ class Workspace:
     def pair_counts(self, stream=None):
         """(tile-Gaussian associations P, super-tile pairs sorted) of the last bin_sort."""
         t, u = C.c_int64(), C.c_int64()
-        _check(lib().geer_pair_counts(self._handle, C.byref(t), C.byref(u), None, _stream(stream)),
+        _check(lib().geer_pair_counts(self._handle, C.byref(t), C.byref(u), None, None, _stream(stream)),
                "geer_pair_counts")
         return int(t.value), int(u.value)
+
+    def live_items(self, stream=None) -> int:
+        """Live (camera, Gaussian) items of the last bin_sort."""
+        n = C.c_int64()
+        _check(lib().geer_pair_counts(self._handle, None, None, None, C.byref(n), _stream(stream)), "geer_pair_counts")
+        return int(n.value)
 
     def sort_passes(self, stream=None) -> int:
         """Radix passes of the super-tile sort for the current cameras."""
         p = C.c_int32()
-        _check(lib().geer_pair_counts(self._handle, None, None, C.byref(p), _stream(stream)), "geer_pair_counts")
+        _check(lib().geer_pair_counts(self._handle, None, None, C.byref(p), None, _stream(stream)), "geer_pair_counts")
         return int(p.value)
 
     def debug_render_state(self, stream=None):
