@@ -359,7 +359,8 @@ def run(args):
         "depth_sort": ("hbm", 4 * 20 * live),
         # per live item: id, tile count and ranges read; 8 B per (super-tile, item) pair written
         "duplicate": ("hbm", live * (4 + 4 + 16) + int(super_pairs) * 8),
-        "tile_sort": ("hbm", sort_passes * 20 * int(super_pairs)),
+        # passes x (read key 4 B + key/value 8 B, write 8 B), and 16 B of ranges gathered + written
+        "tile_sort": ("hbm", sort_passes * 20 * int(super_pairs) + 32 * int(super_pairs)),
         "render_fwd": ("alu", FLOPS_TEST * evals + FLOPS_BLEND * applied),
         "render_bwd": ("alu", FLOPS_TEST * walked + FLOPS_BWD * applied),
         "preprocess_bwd": ("hbm", scene.n * g_bytes * 3 + n_items * 64),
@@ -405,9 +406,9 @@ def run(args):
                 "work": {"evaluations": evals, "applied": applied, "walked_back": walked}}
     tiles = math.ceil(cam.width / 16) * math.ceil(cam.height / 16)
     # preprocess, live scan, compact, 4 depth passes x 2, gather, 2 scans, emit, offsets,
-    # super-tile sort passes x 2, sorted ranges, render forward (+ L1 gradient, backward order,
-    # render backward, preprocess backward)
-    launches_per_step = 18 + 2 * sort_passes + (4 if have_bwd else 0)
+    # super-tile sort passes x 2, render forward (+ L1 gradient, backward order, render backward,
+    # preprocess backward)
+    launches_per_step = 17 + 2 * sort_passes + (4 if have_bwd else 0)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,

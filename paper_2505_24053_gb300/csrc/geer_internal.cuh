@@ -34,6 +34,7 @@ enum Misc : int {
     kMiscTileLo = 6,      // (tile, item) associations P mod 2^32
     kMiscTileHi = 7,      // P / 2^32
     kMiscSortDone = 8,    // radix histogram blocks finished in the current pass
+    kMiscSortSame = 9,    // the current pass's digit is the same for every key (an identity pass)
     kMiscCount = 32
 };
 
@@ -195,7 +196,6 @@ cudaError_t launch_bin_front(const geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_depth_sort(geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_count_pairs(const geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s);
-cudaError_t launch_sorted_ranges(const geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_bwd_order(const geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_expand_tiles(const geer_workspace *ws, uint32_t *counts_or_offsets, uint32_t *lists, cudaStream_t s);
 cudaError_t launch_tile_sort(geer_workspace *ws, cudaStream_t s);

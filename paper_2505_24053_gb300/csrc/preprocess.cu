@@ -803,17 +803,6 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
     }
 }
 
-// The association ranges of the sorted pairs' items, in list order, so that the
-// render kernels' list filters read them coalesced.
-__global__ void __launch_bounds__(256) k_sorted_ranges(const uint32_t *__restrict__ svals,
-                                                       const uint4 *__restrict__ ranges,
-                                                       const uint32_t *__restrict__ misc,
-                                                       uint4 *__restrict__ sranges) {
-    if (misc[kMiscStatus] & kStatusCapacity) return;
-    const uint32_t P = misc[kMiscPairs];
-    for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < P; i += gridDim.x * 256u) sranges[i] = ranges[svals[i]];
-}
-
 // One block: the backward's schedule, tiles by descending length of the list
 // prefix the forward walked (bucketed as for the forward's schedule).
 __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ tile_walk, int ntiles,
@@ -896,13 +885,6 @@ cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
     }
     k_tile_offsets<<<1, 1024, 0, s>>>(ws->d_cams, ws->n_cams, ws->super_size, (int)ws->n_tiles, ws->d_srange,
                                       (int)ws->n_stiles, ws->d_misc, ws->d_tile_order);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sorted_ranges(const geer_workspace *ws, cudaStream_t s) {
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((ws->cap_pairs + 255) / 256, (int64_t)ws->num_sms * 8));
-    k_sorted_ranges<<<(unsigned)grid, 256, 0, s>>>(ws->d_vals[ws->sorted_buf], ws->d_ranges, ws->d_misc,
-                                                   ws->d_sranges);
     return cudaGetLastError();
 }
 

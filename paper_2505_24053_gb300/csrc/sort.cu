@@ -105,15 +105,22 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
 #pragma unroll
     for (int w = 0; w < W; ++w) pre += w < warp ? s_wsum[w] : 0u;
     digit_base[d] = pre + v - run;
-    if (tid == 0) misc[kMiscSortDone] = 0u;
+    // one digit holds every key: the pass keeps the order and the scatter only copies
+    const bool all = __syncthreads_or(run == n);
+    if (tid == 0) {
+        misc[kMiscSortSame] = all ? 1u : 0u;
+        misc[kMiscSortDone] = 0u;
+    }
 }
 
+// With rout: also rout[pos] = ranges[value] for every key written (the last pass
+// of the super-tile sort gathers the association ranges into list order).
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ misc, int count_slot, int check_capacity, int shift,
     const uint32_t *__restrict__ tile_hist, const uint32_t *__restrict__ group_excl,
-    const uint32_t *__restrict__ digit_base) {
+    const uint32_t *__restrict__ digit_base, const uint4 *__restrict__ ranges, uint4 *__restrict__ rout) {
     constexpr int W = kSortThreads / 32, TILE = kSortThreads * ITEMS, GROUP = kGroupTiles;
     __shared__ uint32_t s_whist[W][kRadix];
     __shared__ uint32_t s_match[W][kRadix];  // lane masks per digit, zero between ranking steps
@@ -126,6 +133,17 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t n = key_count(misc, count_slot, check_capacity);
     const uint32_t tile = blockIdx.x;
     if ((uint64_t)tile * TILE >= n) return;
+    if (misc[kMiscSortSame]) {  // identity pass: coalesced copy of the tile
+        const uint32_t nt = (uint32_t)min((uint64_t)TILE, (uint64_t)n - (uint64_t)tile * TILE);
+        const uint64_t t0 = (uint64_t)tile * TILE;
+        for (uint32_t i = tid; i < nt; i += kSortThreads) {
+            const uint32_t v = vin[t0 + i];
+            kout[t0 + i] = kin[t0 + i];
+            vout[t0 + i] = v;
+            if (rout) rout[t0 + i] = ranges[v];
+        }
+        return;
+    }
     const uint32_t base_d = digit_base[tid];
     for (int i = tid; i < W * kRadix; i += kSortThreads) (&s_match[0][0])[i] = 0u;
     for (int i = tid; i < W * kRadix; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
@@ -216,8 +234,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             const uint32_t d = (kk >> shift) & 0xffu;
             const uint32_t pos = s_out[d] + (lp - s_lbase[d]);
             if (pos < n) {
+                const uint32_t v = s_val[lp];
                 kout[pos] = kk;
-                vout[pos] = s_val[lp];
+                vout[pos] = v;
+                if (rout) rout[pos] = ranges[v];
             }
         }
     }
@@ -235,7 +255,7 @@ int sort_blocks_per_sm() {
 
 template <int ITEMS>
 static cudaError_t radix_pass_t(geer_workspace *ws, uint32_t *const kbuf[2], uint32_t *const vbuf[2], int cur,
-                                int slot, int check, int shift, int64_t cap_keys, cudaStream_t s) {
+                                int slot, int check, int shift, int64_t cap_keys, uint4 *rout, cudaStream_t s) {
     constexpr int TILE = kSortThreads * ITEMS;
     const unsigned tiles = (unsigned)std::max<int64_t>(1, (cap_keys + TILE - 1) / TILE);
     k_radix_hist<ITEMS><<<tiles, kSortThreads, 0, s>>>(kbuf[cur], ws->d_misc, slot, check, shift, ws->d_tile_hist,
@@ -244,7 +264,7 @@ static cudaError_t radix_pass_t(geer_workspace *ws, uint32_t *const kbuf[2], uin
     if (e != cudaSuccess) return e;
     k_radix_scatter<ITEMS><<<tiles, kSortThreads, 0, s>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1],
                                                           ws->d_misc, slot, check, shift, ws->d_tile_hist,
-                                                          ws->d_group_excl, ws->d_digit_base);
+                                                          ws->d_group_excl, ws->d_digit_base, ws->d_ranges, rout);
     return cudaGetLastError();
 }
 
@@ -252,8 +272,8 @@ static cudaError_t radix_pass_t(geer_workspace *ws, uint32_t *const kbuf[2], uin
 // (Tiles of 1024 keys for small sorts were measured slower: 0.106 against 0.079 ms
 // for the four passes over 1M depth keys.)
 static cudaError_t radix_pass(geer_workspace *ws, uint32_t *const kbuf[2], uint32_t *const vbuf[2], int cur, int slot,
-                              int check, int pass, int64_t cap_keys, cudaStream_t s) {
-    return radix_pass_t<kSortItems>(ws, kbuf, vbuf, cur, slot, check, kRadixBits * pass, cap_keys, s);
+                              int check, int pass, int64_t cap_keys, cudaStream_t s, uint4 *rout = nullptr) {
+    return radix_pass_t<kSortItems>(ws, kbuf, vbuf, cur, slot, check, kRadixBits * pass, cap_keys, rout, s);
 }
 
 // Stable sort of the live items by depth key (4 digits of the FP32 bits).
@@ -272,16 +292,18 @@ cudaError_t launch_depth_sort(geer_workspace *ws, cudaStream_t s) {
 }
 
 // Stable sort of the (super-tile, item) pairs by super-tile id (one or two
-// 8-bit digits).
+// 8-bit digits); the last pass also writes the items' association ranges in
+// list order (the render kernels' filters read them coalesced).
 cudaError_t launch_tile_sort(geer_workspace *ws, cudaStream_t s) {
     int cur = 0;
     for (int p = 0; p < ws->n_sort_passes; ++p) {
-        cudaError_t e = radix_pass(ws, ws->d_keys, ws->d_vals, cur, kMiscPairs, 1, p, ws->cap_pairs, s);
+        cudaError_t e = radix_pass(ws, ws->d_keys, ws->d_vals, cur, kMiscPairs, 1, p, ws->cap_pairs, s,
+                                   p + 1 == ws->n_sort_passes ? ws->d_sranges : nullptr);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
     ws->sorted_buf = cur;
-    return launch_sorted_ranges(ws, s);
+    return cudaSuccess;
 }
 
 }  // namespace geer
