@@ -18,124 +18,141 @@
 namespace geer {
 namespace {
 
-// Real SH basis (3DGS convention, as in the forward) and its gradient with
-// respect to the (unit) direction components.
-__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float Y[16], float dY[16][3]) {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        Y[k] = 0.0f;
-        dY[k][0] = dY[k][1] = dY[k][2] = 0.0f;
-    }
-    Y[0] = 0.28209479177387814f;
-    if (deg >= 1) {
-        const float k1 = 0.4886025119029199f;
-        Y[1] = -k1 * y; dY[1][1] = -k1;
-        Y[2] = k1 * z;  dY[2][2] = k1;
-        Y[3] = -k1 * x; dY[3][0] = -k1;
-    }
-    if (deg >= 2) {
-        const float a = 1.0925484305920792f, b = 0.31539156525252005f, c = 0.5462742152960396f;
-        const float xx = x * x, yy = y * y, zz = z * z;
-        Y[4] = a * x * y;                  dY[4][0] = a * y;  dY[4][1] = a * x;
-        Y[5] = -a * y * z;                 dY[5][1] = -a * z; dY[5][2] = -a * y;
-        Y[6] = b * (2.0f * zz - xx - yy);  dY[6][0] = -2.0f * b * x; dY[6][1] = -2.0f * b * y; dY[6][2] = 4.0f * b * z;
-        Y[7] = -a * x * z;                 dY[7][0] = -a * z; dY[7][2] = -a * x;
-        Y[8] = c * (xx - yy);              dY[8][0] = 2.0f * c * x; dY[8][1] = -2.0f * c * y;
-        if (deg >= 3) {
-            const float e = 0.5900435899266435f, f = 2.890611442640554f, h = 0.4570457994644658f;
-            const float pp = 0.3731763325901154f, r = 1.445305721320277f;
-            Y[9] = -e * y * (3.0f * xx - yy);
-            dY[9][0] = -6.0f * e * x * y; dY[9][1] = -e * (3.0f * xx - 3.0f * yy);
-            Y[10] = f * x * y * z;
-            dY[10][0] = f * y * z; dY[10][1] = f * x * z; dY[10][2] = f * x * y;
-            Y[11] = -h * y * (4.0f * zz - xx - yy);
-            dY[11][0] = 2.0f * h * x * y; dY[11][1] = -h * (4.0f * zz - xx - 3.0f * yy); dY[11][2] = -8.0f * h * y * z;
-            Y[12] = pp * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
-            dY[12][0] = -6.0f * pp * x * z; dY[12][1] = -6.0f * pp * y * z;
-            dY[12][2] = pp * (6.0f * zz - 3.0f * xx - 3.0f * yy);
-            Y[13] = -h * x * (4.0f * zz - xx - yy);
-            dY[13][0] = -h * (4.0f * zz - 3.0f * xx - yy); dY[13][1] = 2.0f * h * x * y; dY[13][2] = -8.0f * h * x * z;
-            Y[14] = r * z * (xx - yy);
-            dY[14][0] = 2.0f * r * x * z; dY[14][1] = -2.0f * r * y * z; dY[14][2] = r * (xx - yy);
-            Y[15] = -e * x * (xx - 3.0f * yy);
-            dY[15][0] = -e * (3.0f * xx - 3.0f * yy); dY[15][1] = 6.0f * e * x * y;
-        }
+// Real SH basis (3DGS convention, as in the forward): term k and its gradient
+// with respect to the (unit) direction components. Called with k a compile-time
+// constant inside unrolled loops, so each call folds to its own polynomial and no
+// table of all terms is held in registers.
+struct ShDir {
+    float x, y, z, xx, yy, zz;
+};
+
+__device__ __forceinline__ float sh_value(int k, const ShDir &d) {
+    const float k1 = 0.4886025119029199f;
+    const float a = 1.0925484305920792f, b = 0.31539156525252005f, c = 0.5462742152960396f;
+    const float e = 0.5900435899266435f, f = 2.890611442640554f, h = 0.4570457994644658f;
+    const float pp = 0.3731763325901154f, r = 1.445305721320277f;
+    const float x = d.x, y = d.y, z = d.z, xx = d.xx, yy = d.yy, zz = d.zz;
+    switch (k) {
+        case 0: return 0.28209479177387814f;
+        case 1: return -k1 * y;
+        case 2: return k1 * z;
+        case 3: return -k1 * x;
+        case 4: return a * x * y;
+        case 5: return -a * y * z;
+        case 6: return b * (2.0f * zz - xx - yy);
+        case 7: return -a * x * z;
+        case 8: return c * (xx - yy);
+        case 9: return -e * y * (3.0f * xx - yy);
+        case 10: return f * x * y * z;
+        case 11: return -h * y * (4.0f * zz - xx - yy);
+        case 12: return pp * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+        case 13: return -h * x * (4.0f * zz - xx - yy);
+        case 14: return r * z * (xx - yy);
+        default: return -e * x * (xx - 3.0f * yy);
     }
 }
 
-// One block per 64 Gaussians. The block's SH coefficients and its slice of
-// dL/dsh are staged through shared memory with coalesced loads (row stride made
-// odd so that per-thread rows do not share banks); each thread then runs the
-// chain for its Gaussian over the cameras, adds its SH gradient in shared
-// memory, and the block writes dL/dsh back coalesced.
-constexpr int kPBThreads = 64;
+__device__ __forceinline__ void sh_grad(int k, const ShDir &d, float g[3]) {
+    const float k1 = 0.4886025119029199f;
+    const float a = 1.0925484305920792f, b = 0.31539156525252005f, c = 0.5462742152960396f;
+    const float e = 0.5900435899266435f, f = 2.890611442640554f, h = 0.4570457994644658f;
+    const float pp = 0.3731763325901154f, r = 1.445305721320277f;
+    const float x = d.x, y = d.y, z = d.z, xx = d.xx, yy = d.yy, zz = d.zz;
+    g[0] = g[1] = g[2] = 0.0f;
+    switch (k) {
+        case 0: break;
+        case 1: g[1] = -k1; break;
+        case 2: g[2] = k1; break;
+        case 3: g[0] = -k1; break;
+        case 4: g[0] = a * y; g[1] = a * x; break;
+        case 5: g[1] = -a * z; g[2] = -a * y; break;
+        case 6: g[0] = -2.0f * b * x; g[1] = -2.0f * b * y; g[2] = 4.0f * b * z; break;
+        case 7: g[0] = -a * z; g[2] = -a * x; break;
+        case 8: g[0] = 2.0f * c * x; g[1] = -2.0f * c * y; break;
+        case 9: g[0] = -6.0f * e * x * y; g[1] = -e * (3.0f * xx - 3.0f * yy); break;
+        case 10: g[0] = f * y * z; g[1] = f * x * z; g[2] = f * x * y; break;
+        case 11: g[0] = 2.0f * h * x * y; g[1] = -h * (4.0f * zz - xx - 3.0f * yy); g[2] = -8.0f * h * y * z; break;
+        case 12: g[0] = -6.0f * pp * x * z; g[1] = -6.0f * pp * y * z; g[2] = pp * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+            break;
+        case 13: g[0] = -h * (4.0f * zz - 3.0f * xx - yy); g[1] = 2.0f * h * x * y; g[2] = -8.0f * h * x * z; break;
+        case 14: g[0] = 2.0f * r * x * z; g[1] = -2.0f * r * y * z; g[2] = r * (xx - yy); break;
+        default: g[0] = -e * (3.0f * xx - 3.0f * yy); g[1] = 6.0f * e * x * y; break;
+    }
+}
 
-template <int DEG>
-__global__ void __launch_bounds__(kPBThreads) k_preprocess_bwd(
+// One block per 64 Gaussians. The block's SH coefficients are staged into shared
+// memory with coalesced asynchronous copies (row stride made odd so that
+// per-thread rows do not share banks) while each thread loads its own
+// parameters; each thread then runs the chain for its Gaussian over the cameras
+// and collects its dL/dsh in shared memory, and the block adds that to dL/dsh in
+// global memory coalesced. With one camera the SH row itself is overwritten by
+// its gradient term by term (each coefficient is read before its slot is
+// written), which halves the block's shared memory; with several cameras the
+// gradient has a row of its own.
+constexpr int kPBThreads = 64;
+#ifndef GEER_PB_MINB
+#define GEER_PB_MINB 14  // resident blocks of the one-camera variant: caps registers at 72
+#endif
+
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+
+template <int DEG, bool ONE_CAM>
+__global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_preprocess_bwd(
     const DevCam *__restrict__ cams, int ncams, const float *__restrict__ mean, const float *__restrict__ scale,
     const float *__restrict__ quat, const float *__restrict__ sh, int64_t n, const uint32_t *__restrict__ count,
     const GradAcc *__restrict__ gacc, float *__restrict__ d_mean, float *__restrict__ d_scale,
     float *__restrict__ d_quat, float *__restrict__ d_opacity, float *__restrict__ d_sh) {
     constexpr int NB = (DEG + 1) * (DEG + 1), NC = 3 * NB, ST = NC | 1;
     __shared__ float s_sh[kPBThreads * ST];
-    __shared__ float s_dsh[kPBThreads * ST];
+    __shared__ float s_dsh[ONE_CAM ? 1 : kPBThreads * ST];
+    __shared__ uint8_t s_live[kPBThreads];
     const int tid = threadIdx.x;
     const int64_t g0 = (int64_t)blockIdx.x * kPBThreads;
     const int nloc = (int)min((int64_t)kPBThreads, n - g0);
     {
+        // asynchronous 4-byte copies into the padded rows: no registers held while
+        // the block's rows are in flight
         const float *src = sh + g0 * NC;
-        const float *dsrc = d_sh ? d_sh + g0 * NC : nullptr;
-        if (nloc == kPBThreads) {
-            // a full block's rows are kPBThreads * NC * 4 bytes (a multiple of 16) from a
-            // 16-byte aligned base: all its 16-byte loads are issued before any is used
-            constexpr int kF = kPBThreads * NC / 4;                // float4 in the block's rows
-            constexpr int kV = (kF + kPBThreads - 1) / kPBThreads;  // per thread
-            float4 a[kV], b[kV];
-#pragma unroll
-            for (int u = 0; u < kV; ++u) {
-                if (u * kPBThreads + tid < kF) {
-                    a[u] = reinterpret_cast<const float4 *>(src)[u * kPBThreads + tid];
-                    if (dsrc) b[u] = reinterpret_cast<const float4 *>(dsrc)[u * kPBThreads + tid];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kV; ++u) {
-                if (u * kPBThreads + tid >= kF) continue;
-                const int i = 4 * (u * kPBThreads + tid);
-                const float va[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
-                const float vb[4] = {b[u].x, b[u].y, b[u].z, b[u].w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int gl = (i + q) / NC, k = i + q - gl * NC;
-                    s_sh[gl * ST + k] = va[q];
-                    if (dsrc) s_dsh[gl * ST + k] = vb[q];
-                }
-            }
-        } else {
-            for (int i = tid; i < nloc * NC; i += kPBThreads) {
-                const int gl = i / NC, k = i - gl * NC;
-                s_sh[gl * ST + k] = src[i];
-                if (dsrc) s_dsh[gl * ST + k] = dsrc[i];
-            }
+        for (int i = tid; i < nloc * NC; i += kPBThreads) {
+            const int gl = i / NC, k = i - gl * NC;
+            cp_async4(&s_sh[gl * ST + k], src + i);
         }
+        if (!ONE_CAM)
+            for (int i = tid; i < kPBThreads * ST; i += kPBThreads) s_dsh[i] = 0.0f;
     }
-    __syncthreads();
     const int64_t g = g0 + tid;
     bool any = false;
     if (tid < nloc)
         for (int ci = 0; ci < ncams; ++ci) any |= count[(int64_t)ci * n + g] > 0;
+    float mu[3], s[3], q[4];
+    float4 pa[4];  // the one camera's accumulators, loaded with the parameters
     if (any) {  // a Gaussian not associated with any tile has no gradient
-        const float *shc = s_sh + tid * ST;
-        float *dsh = s_dsh + tid * ST;
-        float mu[3], s[3], is[3], q[4];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             mu[a] = mean[3 * g + a];
             s[a] = scale[3 * g + a];
-            is[a] = 1.0f / s[a];
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a) q[a] = quat[4 * g + a];
+        if (ONE_CAM) {
+            const float4 *ap = reinterpret_cast<const float4 *>(gacc + g);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pa[k] = ap[k];
+        }
+    }
+    s_live[tid] = any ? 1 : 0;
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    const bool block_any = __syncthreads_or(any);
+    if (!block_any) return;
+    if (any) {
+        float *shc = s_sh + tid * ST;
+        float *dsh = ONE_CAM ? shc : s_dsh + tid * ST;
+        float is[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) is[a] = 1.0f / s[a];
         const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
         const float w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
         float R[9];
@@ -144,12 +161,17 @@ __global__ void __launch_bounds__(kPBThreads) k_preprocess_bwd(
         R[6] = 2.0f * (x * z - w * y);        R[7] = 2.0f * (y * z + w * x);        R[8] = 1.0f - 2.0f * (x * x + y * y);
         float dmu[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, dsig = 0.0f;
 
-        for (int ci = 0; ci < ncams; ++ci) {
+        for (int ci = 0; ci < (ONE_CAM ? 1 : ncams); ++ci) {
             const int64_t idx = (int64_t)ci * n + g;
-            if (count[idx] == 0) continue;
+            if (!ONE_CAM && count[idx] == 0) continue;
             const DevCam &cam = cams[ci];
-            const float4 *ap = reinterpret_cast<const float4 *>(gacc + idx);
-            const float4 a0 = ap[0], a1 = ap[1], a2 = ap[2], a3 = ap[3];
+            float4 a0, a1, a2, a3;
+            if (ONE_CAM) {
+                a0 = pa[0]; a1 = pa[1]; a2 = pa[2]; a3 = pa[3];
+            } else {
+                const float4 *ap = reinterpret_cast<const float4 *>(gacc + idx);
+                a0 = ap[0]; a1 = ap[1]; a2 = ap[2]; a3 = ap[3];
+            }
             dsig += a0.x;
             const float *Rc = cam.R;
             // camera-frame mean and Gaussian axes M = R_cw R (W = S^-1 M^T)
@@ -194,35 +216,41 @@ __global__ void __launch_bounds__(kPBThreads) k_preprocess_bwd(
             // colour: SH at the world direction from the camera centre
             const float vx = mu[0] - cam.o[0], vy = mu[1] - cam.o[1], vz = mu[2] - cam.o[2];
             const float vn = sqrtf(vx * vx + vy * vy + vz * vz);
-            const float ux = vx / vn, uy = vy / vn, uz = vz / vn;
-            float Y[16], dY[16][3];
-            sh_basis_grad(DEG, ux, uy, uz, Y, dY);
+            ShDir u;
+            u.x = vx / vn; u.y = vy / vn; u.z = vz / vn;
+            u.xx = u.x * u.x; u.yy = u.y * u.y; u.zz = u.z * u.z;
             const float drgb[3] = {a0.y, a0.z, a0.w};
+            float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const float Yk = sh_value(k, u);
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) raw[ch] += Yk * shc[3 * k + ch];
+            }
             float dLdc[3];
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float raw = 0.5f;
-#pragma unroll
-                for (int k = 0; k < NB; ++k) raw += Y[k] * shc[3 * k + ch];
-                dLdc[ch] = raw > 0.0f ? drgb[ch] : 0.0f;
-            }
+            for (int ch = 0; ch < 3; ++ch) dLdc[ch] = raw[ch] > 0.0f ? drgb[ch] : 0.0f;
             float ddir[3] = {0, 0, 0};
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
+                const float Yk = sh_value(k, u);
+                float gk[3];
+                sh_grad(k, u, gk);
                 float wk = 0.0f;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    dsh[3 * k + ch] += dLdc[ch] * Y[k];
                     wk += dLdc[ch] * shc[3 * k + ch];
+                    if (ONE_CAM) dsh[3 * k + ch] = dLdc[ch] * Yk;  // slot read just above
+                    else dsh[3 * k + ch] += dLdc[ch] * Yk;
                 }
-                ddir[0] += wk * dY[k][0];
-                ddir[1] += wk * dY[k][1];
-                ddir[2] += wk * dY[k][2];
+                ddir[0] += wk * gk[0];
+                ddir[1] += wk * gk[1];
+                ddir[2] += wk * gk[2];
             }
-            const float dp = ddir[0] * ux + ddir[1] * uy + ddir[2] * uz;
-            dmu[0] += (ddir[0] - ux * dp) / vn;
-            dmu[1] += (ddir[1] - uy * dp) / vn;
-            dmu[2] += (ddir[2] - uz * dp) / vn;
+            const float dp = ddir[0] * u.x + ddir[1] * u.y + ddir[2] * u.z;
+            dmu[0] += (ddir[0] - u.x * dp) / vn;
+            dmu[1] += (ddir[1] - u.y * dp) / vn;
+            dmu[2] += (ddir[2] - u.z * dp) / vn;
         }
         // unit-quaternion polynomial R(w, x, y, z) (App. C.4) then the normalisation
         const float gw = 2.0f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
@@ -233,26 +261,54 @@ __global__ void __launch_bounds__(kPBThreads) k_preprocess_bwd(
         const float gz = 2.0f * (-2.0f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.0f * z * dR[4] +
                                  y * dR[5] + x * dR[6] + y * dR[7]);
         const float proj = gw * w + gx * x + gy * y + gz * z;
+        // the accumulated gradients are all read before any is written, so that
+        // their loads are in flight together
+        float om[3] = {0, 0, 0}, os[3] = {0, 0, 0}, oq[4] = {0, 0, 0, 0}, oo = 0.0f;
+        if (d_mean)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) om[a] = d_mean[3 * g + a];
+        if (d_scale)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) os[a] = d_scale[3 * g + a];
+        if (d_quat)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) oq[a] = d_quat[4 * g + a];
+        if (d_opacity) oo = d_opacity[g];
         if (d_quat) {
-            d_quat[4 * g + 0] += (gw - w * proj) / qn;
-            d_quat[4 * g + 1] += (gx - x * proj) / qn;
-            d_quat[4 * g + 2] += (gy - y * proj) / qn;
-            d_quat[4 * g + 3] += (gz - z * proj) / qn;
+            d_quat[4 * g + 0] = oq[0] + (gw - w * proj) / qn;
+            d_quat[4 * g + 1] = oq[1] + (gx - x * proj) / qn;
+            d_quat[4 * g + 2] = oq[2] + (gy - y * proj) / qn;
+            d_quat[4 * g + 3] = oq[3] + (gz - z * proj) / qn;
         }
         if (d_mean)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) d_mean[3 * g + a] += dmu[a];
+            for (int a = 0; a < 3; ++a) d_mean[3 * g + a] = om[a] + dmu[a];
         if (d_scale)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) d_scale[3 * g + a] += ds[a];
-        if (d_opacity) d_opacity[g] += dsig;
+            for (int a = 0; a < 3; ++a) d_scale[3 * g + a] = os[a] + ds[a];
+        if (d_opacity) d_opacity[g] = oo + dsig;
     }
     __syncthreads();
     if (d_sh) {
+        // rows of Gaussians without a gradient are left untouched
+        const float *acc = ONE_CAM ? s_sh : s_dsh;
         float *dst = d_sh + g0 * NC;
-        for (int i = tid; i < nloc * NC; i += kPBThreads) {
-            const int gl = i / NC, k = i - gl * NC;
-            dst[i] = s_dsh[gl * ST + k];
+#ifndef GEER_PB_BATCH
+#define GEER_PB_BATCH 24
+#endif
+        constexpr int kBatch = GEER_PB_BATCH;  // values in flight per thread
+        for (int i0 = tid; i0 < nloc * NC; i0 += kBatch * kPBThreads) {
+            float v[kBatch];
+#pragma unroll
+            for (int b = 0; b < kBatch; ++b) {
+                const int i = i0 + b * kPBThreads, gl = i / NC;
+                v[b] = (i < nloc * NC && s_live[gl]) ? dst[i] : 0.0f;
+            }
+#pragma unroll
+            for (int b = 0; b < kBatch; ++b) {
+                const int i = i0 + b * kPBThreads, gl = i / NC;
+                if (i < nloc * NC && s_live[gl]) dst[i] = v[b] + acc[gl * ST + (i - gl * NC)];
+            }
         }
     }
 }
@@ -288,9 +344,14 @@ cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians
     if (g->n == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((g->n + kPBThreads - 1) / kPBThreads);
 #define GEER_PB_LAUNCH(D)                                                                                      \
-    k_preprocess_bwd<D><<<blocks, kPBThreads, 0, s>>>(ws->d_cams, ws->n_cams, g->mean, g->scale, g->quat, g->sh, \
-                                                      g->n, ws->d_count, ws->d_gacc, d_mean, d_scale, d_quat,   \
-                                                      d_opacity, d_sh)
+    if (ws->n_cams == 1)                                                                                       \
+        k_preprocess_bwd<D, true><<<blocks, kPBThreads, 0, s>>>(                                               \
+            ws->d_cams, 1, g->mean, g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean, d_scale,   \
+            d_quat, d_opacity, d_sh);                                                                          \
+    else                                                                                                       \
+        k_preprocess_bwd<D, false><<<blocks, kPBThreads, 0, s>>>(                                              \
+            ws->d_cams, ws->n_cams, g->mean, g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean,  \
+            d_scale, d_quat, d_opacity, d_sh)
     switch (g->sh_degree) {
         case 0: GEER_PB_LAUNCH(0); break;
         case 1: GEER_PB_LAUNCH(1); break;

@@ -93,6 +93,19 @@ def test_backward_matches_oracle_tiny(geer, orc, name, cams):
     _compare(g, ref, name)
 
 
+@pytest.mark.parametrize("deg", [0, 1, 3])
+@pytest.mark.parametrize("name,cams", CAMS[1:], ids=[c[0] for c in CAMS[1:]])
+def test_backward_sh_degrees(geer, orc, name, cams, deg):
+    """Every SH degree through the one-camera and the several-camera variants of
+    the per-Gaussian backward."""
+    scene = _scene(31 + deg, 48, deg)
+    pixels = sum(c.pixels for c in cams)
+    dLdC = np.random.default_rng(6 + deg).normal(0, 1, (pixels, 3)).astype(np.float32)
+    rgb, dL, g = _gpu_grads(geer, scene, cams, dLdC=dLdC)
+    ref = _oracle_grads(orc, scene, cams, dL)
+    _compare(g, ref, f"{name}-deg{deg}")
+
+
 def test_backward_workload3_subset_l1(geer, orc):
     """The workload-3 gradient check: 2048 Gaussians of the 1M scene, 64x64
     Kannala-Brandt 190 deg camera, L1 loss against the seeded target."""
