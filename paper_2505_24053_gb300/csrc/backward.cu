@@ -94,11 +94,6 @@ constexpr int kPBThreads = 64;
 #define GEER_PB_MINB 14  // resident blocks of the one-camera variant: caps registers at 72
 #endif
 
-__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
-}
-
 template <int DEG, bool ONE_CAM>
 __global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_preprocess_bwd(
     const DevCam *__restrict__ cams, int ncams, const float *__restrict__ mean, const float *__restrict__ scale,

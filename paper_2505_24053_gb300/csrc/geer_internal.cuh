@@ -89,6 +89,12 @@ struct Params {
 // PBF association ranges of a (camera, Gaussian) item, packed as u16 pairs:
 // [0,1) columns and [4,5) rows of the direct arcs, [2,3) and [6,7) of the arcs
 // shifted by pi (rays beyond 90 degrees).
+// Asynchronous 4-byte global -> shared copy (completed by cp.async.wait_all).
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+
 __device__ __forceinline__ void unpack_ranges(const uint4 r4, int rg[8]) {
     rg[0] = (int)(r4.x & 0xffff); rg[1] = (int)(r4.x >> 16); rg[2] = (int)(r4.y & 0xffff); rg[3] = (int)(r4.y >> 16);
     rg[4] = (int)(r4.z & 0xffff); rg[5] = (int)(r4.z >> 16); rg[6] = (int)(r4.w & 0xffff); rg[7] = (int)(r4.w >> 16);

@@ -325,14 +325,38 @@ __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sm) {
 // Thread per Gaussian, loop over cameras (the Gaussian's parameters are read once).
 // Two blocks per SM (128 registers): measured faster than one block without
 // spills and than three with more.
-__global__ void __launch_bounds__(kPrepThreads, 2) k_preprocess(
+// SH rows of the block staged in shared memory: row stride NC | 1 floats (odd, so
+// that the threads' rows do not share banks).
+template <int DEG>
+struct PrepSh {
+    static constexpr int kStride = (3 * (DEG + 1) * (DEG + 1)) | 1;
+};
+
+#ifndef GEER_PREP_MINB
+#define GEER_PREP_MINB 3  // resident blocks per SM: caps registers at 80
+#endif
+template <int DEG>
+__global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
     const DevCam *__restrict__ cams, int ncams, const float4 *__restrict__ ttab, Params p,
     const float *__restrict__ mean, const float *__restrict__ scale, const float *__restrict__ quat,
-    const float *__restrict__ opacity, const float *__restrict__ sh, int64_t n, int deg, Record *__restrict__ rec,
+    const float *__restrict__ opacity, const float *__restrict__ sh, int64_t n, Record *__restrict__ rec,
     uint4 *__restrict__ ranges, uint32_t *__restrict__ count, uint32_t *__restrict__ key,
     uint32_t *__restrict__ blocksum, int64_t nblk) {
+    constexpr int NC = 3 * (DEG + 1) * (DEG + 1), ST = PrepSh<DEG>::kStride;
+    extern __shared__ float s_sh[];  // [kPrepThreads][ST]
     __shared__ uint32_t red[kPrepThreads / 32];
-    const int64_t g = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    const int64_t g0 = (int64_t)blockIdx.x * kPrepThreads;
+    const int64_t g = g0 + threadIdx.x;
+    {
+        // the block's SH coefficients, copied asynchronously while the bounds are
+        // computed; read only for the colour
+        const int nloc = (int)min((int64_t)kPrepThreads, n - g0);
+        const float *src = sh + g0 * NC;
+        for (int i = threadIdx.x; i < nloc * NC; i += kPrepThreads) {
+            const int gl = i / NC;
+            cp_async4(&s_sh[gl * ST + (i - gl * NC)], src + i);
+        }
+    }
     bool ok = g < n;
     float mu[3] = {0, 0, 0}, sc[3] = {1, 1, 1}, qt[4] = {1, 0, 0, 0}, sigma = 0.0f;
     if (ok) {
@@ -368,24 +392,6 @@ __global__ void __launch_bounds__(kPrepThreads, 2) k_preprocess(
         lam2 = lambda2(sigma, p.alpha_min, p.lambda_pad);
         if (!(lam2 > 0.0f)) ok = false;
     }
-    // SH coefficients [(deg+1)^2][3]; rows of 12 or 48 floats are read as float4
-    float shc[48];
-    const int nc = 3 * (deg + 1) * (deg + 1);
-    if (ok) {
-        if ((nc & 3) == 0) {
-            const float4 *p4 = reinterpret_cast<const float4 *>(sh + (int64_t)g * nc);
-#pragma unroll
-            for (int i = 0; i < 12; ++i)
-                if (4 * i < nc) {
-                    const float4 v = p4[i];
-                    shc[4 * i] = v.x; shc[4 * i + 1] = v.y; shc[4 * i + 2] = v.z; shc[4 * i + 3] = v.w;
-                }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 48; ++i)
-                if (i < nc) shc[i] = sh[(int64_t)g * nc + i];
-        }
-    }
     const float s2[3] = {fm(sc[0], sc[0]), fm(sc[1], sc[1]), fm(sc[2], sc[2])};
     const float ss[3] = {fm(sc[1], sc[2]), fm(sc[0], sc[2]), fm(sc[0], sc[1])};
 
@@ -395,6 +401,7 @@ __global__ void __launch_bounds__(kPrepThreads, 2) k_preprocess(
         uint32_t cnt = 0;
         bool live = ok;
         float m0 = 0, m1 = 0, m2 = 0, M[9], u[3];
+        Record r;
         if (live) {
             const float *Rc = cam.R;
             m0 = fa(fa(fa(fm(Rc[0], mu[0]), fm(Rc[1], mu[1])), fm(Rc[2], mu[2])), cam.t[0]);
@@ -456,7 +463,6 @@ __global__ void __launch_bounds__(kPrepThreads, 2) k_preprocess(
             ranges[idx] = make_uint4((uint32_t)rg[0] | ((uint32_t)rg[1] << 16), (uint32_t)rg[2] | ((uint32_t)rg[3] << 16),
                                      (uint32_t)rg[4] | ((uint32_t)rg[5] << 16), (uint32_t)rg[6] | ((uint32_t)rg[7] << 16));
             // render record: W = S^-1 M^T (camera frame), o_u = -W mu_c = -u
-            Record r;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 float inv = 1.0f / sc[k];
@@ -466,16 +472,22 @@ __global__ void __launch_bounds__(kPrepThreads, 2) k_preprocess(
                 r.ou[k] = -u[k];
             }
             r.log2_sigma = log2f(sigma);
+        } else if (g < n) {
+            key[idx] = 0u;
+            ranges[idx] = make_uint4(0, 0, 0, 0);
+        }
+        if (ci == 0) {  // the SH rows have arrived (block-uniform)
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            __syncthreads();
+        }
+        if (live) {
             float dx = mu[0] - cam.o[0], dy = mu[1] - cam.o[1], dz = mu[2] - cam.o[2];
             float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-            sh_colour(deg, shc, dx * inv, dy * inv, dz * inv, r.rgb);
+            sh_colour(DEG, s_sh + threadIdx.x * ST, dx * inv, dy * inv, dz * inv, r.rgb);
             float4 *dst = reinterpret_cast<float4 *>(rec + idx);
             const float4 *src = reinterpret_cast<const float4 *>(&r);
 #pragma unroll
             for (int i = 0; i < 4; ++i) dst[i] = src[i];
-        } else if (g < n) {
-            key[idx] = 0u;
-            ranges[idx] = make_uint4(0, 0, 0, 0);
         }
         if (g < n) count[idx] = cnt;
         uint32_t tot = block_sum_u32(cnt > 0 ? 1u : 0u, red);
@@ -834,11 +846,26 @@ __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ ti
 cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g, cudaStream_t s) {
     const int64_t nblk = prep_blocks(g->n);
     if (nblk == 0) return cudaSuccess;
-    k_preprocess<<<(unsigned)nblk, kPrepThreads, 0, s>>>(
-        ws->d_cams, ws->n_cams, ws->d_tile_tab,
-        Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, g->mean,
-        g->scale, g->quat, g->opacity, g->sh, g->n, g->sh_degree, ws->d_rec, ws->d_ranges, ws->d_count, ws->d_key,
-        ws->d_blocksum, nblk);
+    const Params prm{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad};
+#define GEER_PREP_LAUNCH(D)                                                                                      \
+    {                                                                                                            \
+        const int smem = kPrepThreads * PrepSh<D>::kStride * (int)sizeof(float);                               \
+        if (smem > 48 * 1024) {                                                                                  \
+            const cudaError_t e = cudaFuncSetAttribute(k_preprocess<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                       smem);                                                    \
+            if (e != cudaSuccess) return e;                                                                      \
+        }                                                                                                        \
+        k_preprocess<D><<<(unsigned)nblk, kPrepThreads, smem, s>>>(                                              \
+            ws->d_cams, ws->n_cams, ws->d_tile_tab, prm, g->mean, g->scale, g->quat, g->opacity, g->sh, g->n,    \
+            ws->d_rec, ws->d_ranges, ws->d_count, ws->d_key, ws->d_blocksum, nblk);                             \
+    }
+    switch (g->sh_degree) {
+        case 0: GEER_PREP_LAUNCH(0); break;
+        case 1: GEER_PREP_LAUNCH(1); break;
+        case 2: GEER_PREP_LAUNCH(2); break;
+        default: GEER_PREP_LAUNCH(3); break;
+    }
+#undef GEER_PREP_LAUNCH
     return cudaGetLastError();
 }
 

@@ -149,6 +149,15 @@ def test_render_tiny_scenes_full_frame(geer, orc, name, cams):
         off += cam.pixels
 
 
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_render_sh_degrees_full_frame(geer, orc, deg):
+    """The colour of every SH degree (the preprocess is specialised per degree)."""
+    cam = TINY[3][1][0]
+    scene = _tiny_scene(40 + deg, 333, deg, spread=2.5)
+    r, g, rgb, T = _render(geer, scene, [cam])
+    _check_pixels(orc, scene, cam, rgb.reshape(cam.height, cam.width, 3), wl.all_pixels(cam), f"deg{deg}")
+
+
 def test_render_workload1_full_frame(geer, orc):
     """4096 Gaussians, pinhole 128x128 60 deg: every pixel against the oracle."""
     scene = wl.config_scene(1)
