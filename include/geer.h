@@ -103,7 +103,11 @@ geer_status geer_default_params(geer_params *p);
 /* Device bytes needed for a workspace rendering `n_cams` cameras (whose sizes
  * are the capacity: later camera sets must not exceed the total pixel and tile
  * counts nor n_cams) of up to n_gauss Gaussians of SH degree <= sh_degree with
- * up to pair_capacity (tile, Gaussian) pairs. Host-only; synchronous. */
+ * up to pair_capacity (super-tile, Gaussian) pairs (see geer_bin_sort). Besides
+ * the per-pair, per-Gaussian and per-pixel arrays it holds 16 KB per tile: the
+ * forward's record of which warps' rays hit each of the tile's first 2048 list
+ * entries, from which the backward skips entries a warp never hit.
+ * Host-only; synchronous. */
 geer_status geer_workspace_size(const geer_camera *cams, int32_t n_cams, int64_t n_gauss, int32_t sh_degree,
                                 int64_t pair_capacity, size_t *bytes);
 

@@ -258,6 +258,7 @@ void build_tables(const geer_camera *cams, int n, CamTables &out, const uint8_t 
 struct Caps {
     int32_t cams;
     int64_t pixels, tiles, tile_tab, pix_tab, gauss, pairs, sort_tiles, prep_blocks;
+    int64_t hit_entries;  // per tile: the forward's hit record for the backward (0: none)
 };
 
 Caps caps_of(const CamTables &t, int32_t n_cams, int64_t n_gauss, int64_t pair_capacity) {
@@ -271,6 +272,7 @@ Caps caps_of(const CamTables &t, int32_t n_cams, int64_t n_gauss, int64_t pair_c
     c.pairs = std::max<int64_t>(pair_capacity, 1);
     c.sort_tiles = ceil_div(std::max<int64_t>(c.pairs, (int64_t)n_cams * c.gauss), kSortTile) + 1;
     c.prep_blocks = prep_blocks(c.gauss);
+    c.hit_entries = kHitEntries;
     return c;
 }
 
@@ -311,6 +313,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_tfin = L.take(sizeof(float) * c.pixels);
     size_t o_ev = L.take(sizeof(uint2) * c.pixels);
     size_t o_gacc = L.take(sizeof(GradAcc) * cg);
+    size_t o_hit = L.take(sizeof(uint2) * c.tiles * c.hit_entries);
     if (base && ws) {
         ws->d_cams = reinterpret_cast<DevCam *>(base + o_cams);
         ws->d_tile_tab = reinterpret_cast<float4 *>(base + o_ttab);
@@ -344,6 +347,8 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_Tfin = reinterpret_cast<float *>(base + o_tfin);
         ws->d_evals = reinterpret_cast<uint2 *>(base + o_ev);
         ws->d_gacc = reinterpret_cast<GradAcc *>(base + o_gacc);
+        ws->d_hit = c.hit_entries > 0 ? reinterpret_cast<uint2 *>(base + o_hit) : nullptr;
+        ws->hit_entries = c.hit_entries;
     }
     return L.off;
 }
@@ -1035,6 +1040,7 @@ extern "C" geer_status geer_render_noalloc(const geer_gaussians *g, const geer_c
     c.pairs = kNoAllocMaxPairs;
     c.sort_tiles = ceil_div(std::max<int64_t>(c.pairs, c.gauss), kSortTile) + 1;
     c.prep_blocks = prep_blocks(c.gauss);
+    c.hit_entries = 0;  // forward only: no hit record
     if (layout(c, nullptr, nullptr) > kNoAllocBytes) return GEER_ERR_UNSUPPORTED;
     geer_workspace &ws = S.ws;
     memset(&ws, 0, sizeof(ws));

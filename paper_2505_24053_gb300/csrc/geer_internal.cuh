@@ -10,6 +10,8 @@ namespace geer {
 
 constexpr int kTile = 16;                   // BEAP tile edge in rays (a camera sub-frustum)
 constexpr int kTilePix = kTile * kTile;
+constexpr int kTileWarps = kTilePix / 32;    // warps of a tile's rays (one byte each in the hit record)
+constexpr int64_t kHitEntries = 2048;      // tile-list entries per tile whose hit bytes are recorded
 constexpr int kPrepThreads = 256;           // preprocess / duplicate block size
 constexpr int kSortThreads = 256;           // onesweep block size (8 warps)
 constexpr int kSortItems = 12;              // keys per thread per sort tile
@@ -174,6 +176,9 @@ struct geer_workspace {
     float *d_Tfin;          // [cap_pixels] final transmittance (for the backward)
     uint2 *d_evals;         // [cap_pixels] ray-Gaussian evaluations executed / contributors applied
     geer::GradAcc *d_gacc;  // [cap_cams * cap_gauss]
+    uint2 *d_hit;           // [cap_tiles][hit_entries] per tile-list entry, one byte per warp of the tile:
+                            // nonzero when one of the warp's rays hit the entry in the forward (or null)
+    int64_t hit_entries;    // list entries recorded per tile (0: none)
 
     // state of the last calls
     int64_t n_gauss;

@@ -178,6 +178,7 @@ struct WalkSmem {
     float4 rec[BATCH * 4];           // records of the current batch
     uint32_t id[BATCH + kThreads];   // tile-list entries found by the filter (item ids)
     uint32_t pos[BATCH + kThreads];  // their positions in the super-tile list (forward)
+    uint2 hit[BATCH];                // per entry: one byte per warp of the tile, nonzero if a ray hit it
     uint32_t wcnt[kThreads / 32];
     uint32_t maxlast, walkpos;       // the tile's last contributor and its super-list position + 1
     int cam;
@@ -200,8 +201,10 @@ template <int kThreads, int BATCH>
 __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, const uint32_t *__restrict__ svals,
                                              const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
                                              const Params &p, const float4 &col, const float4 &row, int cx, int cy,
-                                             uint2 sr, float dx, float dy, float dz, FwdRay &f) {
+                                             uint2 sr, float dx, float dy, float dz, uint2 *__restrict__ hit_rec,
+                                             int64_t hit_entries, FwdRay &f) {
     const int tid = threadIdx.x;
+    uint8_t *const hit_b = reinterpret_cast<uint8_t *>(sm.hit) + (tid >> 5);  // this warp's byte of entry 0
     if (tid == 0) {
         sm.maxlast = 0u;
         sm.walkpos = sr.x;
@@ -220,6 +223,7 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
             const float4 *src = reinterpret_cast<const float4 *>(rec + sm.id[r]);
 #pragma unroll
             for (int k = 0; k < 4; ++k) sm.rec[r * 4 + k] = src[k];
+            sm.hit[r] = make_uint2(0u, 0u);
         }
         __syncthreads();
         if (!f.done) {
@@ -237,6 +241,11 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                     e[u] = sm.rec[(j + u) * 4 + 3];            // log2 sigma, r, g, b
                     v[u] = evaluate(a, b, c, e[u], dx, dy, dz, log2_amin);
                 }
+                // after the group's record loads (a byte store may alias them); the
+                // same value from every lane of the warp: no race
+#pragma unroll
+                for (int u = 0; u < kFwdUnroll; ++u)
+                    if (v[u].hit) hit_b[(j + u) * 8] = 1;
 #pragma unroll
                 for (int u = 0; u < kFwdUnroll; ++u) {
                     ++f.n_eval;
@@ -264,6 +273,7 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                 const float4 e = sm.rec[j * 4 + 3];
                 const Eval v = evaluate(a, b, c, e, dx, dy, dz, log2_amin);
                 if (!v.hit) continue;
+                hit_b[j * 8] = 1;
                 const float alpha = fminf(exp2f(v.arg), p.alpha_max);
                 const float Tn = f.T * (1.0f - alpha);
                 if (Tn < p.T_min) {
@@ -284,6 +294,9 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
         if ((tid & 31) == 0) atomicMax(&sm.maxlast, wl);
         __syncthreads();
         if (tid == 0 && sm.maxlast > n_list) sm.walkpos = sm.pos[sm.maxlast - 1u - n_list] + 1u;
+        // the batch's hit bytes, for the backward's skip of entries its warp never hit
+        if (hit_rec)
+            for (int r = tid; r < cnt && (int64_t)n_list + r < hit_entries; r += kThreads) hit_rec[n_list + r] = sm.hit[r];
         shift_list<kThreads>(sm.id, sm.pos, cnt, s_cnt);
         n_list += (uint32_t)cnt;
     }
@@ -341,7 +354,8 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                                             float *__restrict__ rgb,
                                                             float *__restrict__ Tout, float *__restrict__ Tfin,
                                                             uint32_t *__restrict__ last_out,
-                                                            uint2 *__restrict__ evals) {
+                                                            uint2 *__restrict__ evals, uint2 *__restrict__ hit,
+                                                            int64_t hit_entries) {
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     static_assert(kParts == 1, "one block per tile: the block records the tile's walk");
     __shared__ WalkSmem<kThreads, BATCH> sm;
@@ -357,7 +371,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
     }
     FwdRay f{1.0f, 0.0f, 0.0f, 0.0f, 0u, 0u, 0u, !tr.inside};
     forward_walk<kThreads, BATCH>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy, tr.dz,
-                                  f);
+                                  hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, f);
     if (threadIdx.x == 0) tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
     if (tr.inside) {
         const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
@@ -424,7 +438,8 @@ __global__ void __launch_bounds__(kTilePix) k_expand_tiles(const DevCam *__restr
 // The 16 values are reduced over the warp (reduce-scatter by shuffles), over the
 // block in shared memory, then added to global memory with one set of float4
 // atomics per (block, Gaussian). A warp skips list entries beyond the last
-// contributor of its rays.
+// contributor of its rays, and entries that none of its rays hit in the forward
+// (the forward's per-warp hit record; the same FP32 evaluation decides both).
 struct BwdRay {
     float dx, dy, dz, g0, g1, g2, T, S0, S1, S2;
     uint32_t last;
@@ -483,6 +498,7 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
                                               const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
                                               const Params &p, const float4 &col, const float4 &row, int cx, int cy,
                                               uint2 sr, uint2 walk, uint32_t warp_last, uint32_t block_last,
+                                              const uint2 *__restrict__ hit_rec, int64_t hit_entries, int fwarp,
                                               BwdRay &ray, GradAcc *__restrict__ gacc) {
     const int tid = threadIdx.x, lane = tid & 31;
     const float log2_amin = log2f(p.alpha_min);
@@ -499,12 +515,19 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
             const float4 *src = reinterpret_cast<const float4 *>(rec + sm.id[r]);
 #pragma unroll
             for (int k = 0; k < 4; ++k) sm.rec[r * 4 + k] = src[k];
+            // beyond the recorded entries every warp evaluates
+            const uint32_t j = top - 1u - (uint32_t)r;
+            sm.hit[r] = hit_rec && (int64_t)j < hit_entries ? hit_rec[j] : make_uint2(~0u, ~0u);
         }
         for (int i = skip * 17 + tid; i < cnt * 17; i += kThreads) (&s_acc[0][0])[i] = 0.0f;
         __syncthreads();
         // this warp's first entry below its rays' last contributor (warp-uniform)
         const int r0 = max(skip, top > warp_last ? (int)min((uint32_t)cnt, top - warp_last) : 0);
+        const uint8_t *hit_b = reinterpret_cast<const uint8_t *>(sm.hit) + fwarp;
         for (int r = r0; r < cnt; ++r) {
+            // no ray of this warp hit the entry in the forward: the same FP32
+            // decisions here would not either (warp-uniform)
+            if (!hit_b[r * 8]) continue;
             const uint32_t j = top - 1u - (uint32_t)r;
             float gv[16];
 #pragma unroll
@@ -603,6 +626,8 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
                                                                            const float *__restrict__ dL_drgb,
                                                                            const float *__restrict__ Tfin,
                                                                            const uint32_t *__restrict__ last_in,
+                                                                           const uint2 *__restrict__ hit,
+                                                                           int64_t hit_entries,
                                                                            GradAcc *__restrict__ gacc) {
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     __shared__ WalkSmem<kThreads, BATCH> sm;
@@ -633,8 +658,11 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
     __syncthreads();
     const uint32_t block_last = sm.maxlast;
     if (block_last == 0) return;
+    // the forward's warp of these rays: its rows 2w, 2w + 1 of the tile
+    const int fwarp = (part * ROWS * kTile + (int)threadIdx.x) >> 5;
     backward_walk<kThreads, BATCH>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr,
-                                   tile_walk[t], warp_last, block_last, ray, gacc);
+                                   tile_walk[t], warp_last, block_last,
+                                   hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, fwarp, ray, gacc);
 }
 
 }  // namespace
@@ -646,7 +674,7 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_tile_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, rgb, T_final,
-        ws->d_Tfin, ws->d_last, ws->d_evals);
+        ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->hit_entries);
     return cudaGetLastError();
 }
 
@@ -665,7 +693,7 @@ cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cu
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_bwd_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, dL_drgb,
-        ws->d_Tfin, ws->d_last, ws->d_gacc);
+        ws->d_Tfin, ws->d_last, ws->d_hit, ws->hit_entries, ws->d_gacc);
     return cudaGetLastError();
 }
 
