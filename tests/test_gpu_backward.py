@@ -106,6 +106,41 @@ def test_backward_sh_degrees(geer, orc, name, cams, deg):
     _compare(g, ref, f"{name}-deg{deg}")
 
 
+def test_backward_beyond_the_hit_record(geer, orc):
+    """Rays walking more than the 2048 list entries whose per-warp hit bytes the
+    forward records: 3000 broad, faint Gaussians (alpha just above alpha_min)
+    stacked on the axis of a 16x16 pinhole, so that the centre rays composite
+    ~2270 of them before T falls below T_min. The backward evaluates every entry
+    beyond the record. Tolerance: the reverse recovery T_i = T_(i+1) / (1 - a_i)
+    over N ~ 2300 steps, each with an approximate reciprocal (<= 2 ulp) and a
+    rounding, leaves a relative error up to N * 3 * 2^-24 ~ 4e-4 in the front
+    entries' transmittance: 2e-3 here (1e-3 elsewhere)."""
+    n = 3000
+    rng = np.random.default_rng(11)
+    mean = np.stack([rng.normal(0, 0.02, n), rng.normal(0, 0.02, n), rng.uniform(2.0, 5.0, n)], 1)
+    scale = rng.uniform(0.9, 1.1, (n, 3))  # anisotropic: the rotation matters
+    scene = wl.Scene(mean.astype(np.float32), scale.astype(np.float32),
+                     rng.standard_normal((n, 4)).astype(np.float32),
+                     rng.uniform(0.00415, 0.00425, n).astype(np.float32),
+                     rng.normal(0, 0.3, (n, 1, 3)).astype(np.float32), 0)
+    cam = wl.Camera(wl.PINHOLE, 16, 16, math.radians(10))
+    dLdC = np.random.default_rng(12).normal(0, 1, (cam.pixels, 3)).astype(np.float32)
+    r = geer.Renderer([cam], scene.n, scene.sh_degree)
+    g = geer.Gaussians.from_scene(scene)
+    r.forward(g)
+    _, last, walk = r.ws.debug_render_state()
+    assert last.max() > 2048 and walk[0, 1] > 2048, (last.max(), walk[0])
+    grads = r.backward(g, torch.as_tensor(dLdC, device="cuda"))
+    torch.cuda.synchronize()
+    gpu = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
+    ref = orc.render_grad(scene, cam, wl.all_pixels(cam), dLdC.astype(np.float64))
+    for k in BLOCKS:
+        a, b = gpu[k].ravel(), ref[k].ravel()
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        mx = np.abs(a - b).max() / np.abs(b).max()
+        assert rel <= 2e-3 and mx <= 2e-3, (k, rel, mx)
+
+
 def test_backward_workload3_subset_l1(geer, orc):
     """The workload-3 gradient check: 2048 Gaussians of the 1M scene, 64x64
     Kannala-Brandt 190 deg camera, L1 loss against the seeded target."""
