@@ -183,6 +183,8 @@ void build_tables(const geer_camera *cams, int n, CamTables &out, const uint8_t 
         d.tile_base = (int32_t)out.tiles;
         d.pix_base = out.pixels;
         const double fx = c.fov_x, fy = derived_fov_y(c);
+        d.col_ppr = (float)(c.width / fx);
+        d.row_ppr = (float)(c.height / fy);
         d.tcol_off = (int32_t)out.ttab.size();
         for (int tx = 0; tx < d.tiles_x; ++tx) {
             const int i0 = tx * kTile, i1 = std::min(i0 + kTile - 1, c.width - 1);
@@ -940,6 +942,8 @@ bool noalloc_tables(const geer_camera &c, NoAllocState &st, int64_t &ntt, int64_
     if (ntt > kNoAllocMaxTileTab || npt > kNoAllocMaxPixTab || (int64_t)d.tiles_x * d.tiles_y > kNoAllocMaxTiles)
         return false;
     const double fx = c.fov_x, fy = derived_fov_y(c);
+    d.col_ppr = (float)(c.width / fx);
+    d.row_ppr = (float)(c.height / fy);
     d.tcol_off = 0;
     for (int tx = 0; tx < d.tiles_x; ++tx) {
         const int i0 = tx * kTile, i1 = std::min(i0 + kTile - 1, c.width - 1);

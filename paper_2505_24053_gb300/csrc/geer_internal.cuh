@@ -55,6 +55,7 @@ struct DevCam {
     // with cos <= 0 (the w flag): the runs [0, a) and [b, n)
     int32_t zc[2], wc[2], zr[2], wr[2];
     int32_t pad_;
+    float col_ppr, row_ppr;  // BEAP pixels per radian (width / fov_x, height / fov_y)
     int64_t pix_base;    // offset of pixel (0, 0) in the batched image (in pixels)
     float R[9], t[3];    // world -> camera
     float o[3];          // camera centre in world coordinates

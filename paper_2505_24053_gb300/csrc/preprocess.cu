@@ -90,25 +90,34 @@ __device__ Arc shift_arc(Arc a) {
     return r;
 }
 
+// The first tile index k in [0, n] with pred(k) (false before, true from k on:
+// pred is monotone in k), searched from a guess: the guess only sets where the
+// probes start, so the result is exactly the first true index whatever the guess.
+template <typename Pred>
+__device__ __forceinline__ int first_true_from(int guess, int n, Pred pred) {
+    int k = min(max(guess, 0), n);
+    while (k > 0 && pred(k - 1)) --k;
+    while (k < n && !pred(k)) ++k;
+    return k;
+}
+
 // Tile range [lo, hi) whose half-angle span [ta, tb] (tab[i].x, tab[i].y, both
-// increasing in i) meets the arc; prefix u suffix becomes the whole range.
-__device__ void arc_range(Arc a, const float4 *tab, int n, int &olo, int &ohi) {
+// increasing in i) meets the arc; prefix u suffix becomes the whole range. BEAP
+// angles are linear in the pixel index (Sec. 3.3), so the pixel of a bound tau
+// is about (2 atan(tau)) * ppr + (w - 1) / 2: that tile is the first probe
+// (ppr: pixels per radian, half: (w - 1) / 2), and a probe or two more find the
+// first index of each condition exactly.
+__device__ void arc_range(Arc a, const float4 *tab, int n, float ppr, float half, int &olo, int &ohi) {
     olo = 0;
     ohi = 0;
     if (a.kind == 0) return;
     if (a.kind == 3) { ohi = n; return; }
-    int l = 0, h = n;  // first index with tb >= a.lo
-    while (l < h) {
-        int m = (l + h) >> 1;
-        if (tab[m].y >= a.lo) h = m; else l = m + 1;
-    }
-    int first = l;
-    l = 0; h = n;      // first index with ta > a.hi
-    while (l < h) {
-        int m = (l + h) >> 1;
-        if (tab[m].x > a.hi) h = m; else l = m + 1;
-    }
-    int last = l - 1;
+    const float plo = fmaf(2.0f * atanf(a.lo), ppr, half), phi = fmaf(2.0f * atanf(a.hi), ppr, half);
+    // first index with tb >= a.lo (tb: the tile's last ray), then first with ta > a.hi
+    const int first = first_true_from((int)floorf((plo - (kTile - 1)) / kTile), n,
+                                      [&](int k) { return tab[k].y >= a.lo; });
+    const int last = first_true_from((int)floorf(phi / kTile) + 1, n,
+                                     [&](int k) { return tab[k].x > a.hi; }) - 1;
     if (a.kind == 1) {
         if (first <= last) { olo = first; ohi = last + 1; }
         return;
@@ -450,10 +459,11 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
             const float4 *ctab = ttab + cam.tcol_off;
             const float4 *rtab = ttab + cam.trow_off;
             int rg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            arc_range(A, ctab, cam.tiles_x, rg[0], rg[1]);
-            arc_range(B, rtab, cam.tiles_y, rg[4], rg[5]);
-            if (cam.any_row_flip) arc_range(shift_arc(A), ctab, cam.tiles_x, rg[2], rg[3]);
-            if (cam.any_col_flip) arc_range(shift_arc(B), rtab, cam.tiles_y, rg[6], rg[7]);
+            const float chalf = 0.5f * (float)(cam.width - 1), rhalf = 0.5f * (float)(cam.height - 1);
+            arc_range(A, ctab, cam.tiles_x, cam.col_ppr, chalf, rg[0], rg[1]);
+            arc_range(B, rtab, cam.tiles_y, cam.row_ppr, rhalf, rg[4], rg[5]);
+            if (cam.any_row_flip) arc_range(shift_arc(A), ctab, cam.tiles_x, cam.col_ppr, chalf, rg[2], rg[3]);
+            if (cam.any_col_flip) arc_range(shift_arc(B), rtab, cam.tiles_y, cam.row_ppr, rhalf, rg[6], rg[7]);
             if (is_rect(cam, rg))
                 cnt = (uint32_t)(rg[1] - rg[0]) * (uint32_t)(rg[5] - rg[4]);
             else
