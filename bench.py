@@ -237,10 +237,10 @@ def run(args):
         ev[1].record(stream)
         ws.bin_sort(sync=False)
         ev[2].record(stream)
-        # training step: forward, L1 loss gradient, backward (gradients accumulate)
+        # training step: forward, L1 loss gradient, backward (the step's gradients written)
         ws.render_fwd(rgb)
         geer.l1_loss_grad(rgb, target, dL)
-        ws.render_bwd(g, dL, grads)
+        ws.render_bwd(g, dL, grads, accumulate=False)
         ev[3].record(stream)
 
     def fwd_step(ev):
@@ -341,7 +341,7 @@ def run(args):
             ws.render_fwd(rgb_buf[b])
             if have_bwd:
                 geer.l1_loss_grad(rgb_buf[b], target, dL)
-                ws.render_bwd(gk, dL, grads)
+                ws.render_bwd(gk, dL, grads, accumulate=False)
             comp_done[b].record(stream)
             down_s.wait_event(comp_done[b])
             with torch.cuda.stream(down_s):
@@ -397,7 +397,8 @@ def run(args):
         "tile_sort": ("hbm", sort_passes * 20 * int(super_pairs) + 32 * int(super_pairs)),
         "render_fwd": ("alu", FLOPS_TEST * evals + FLOPS_BLEND * applied),
         "render_bwd": ("alu", FLOPS_TEST * walked + FLOPS_BWD * applied),
-        "preprocess_bwd": ("hbm", scene.n * g_bytes * 3 + n_items * 64),
+        # the step writes its gradients: parameters and accumulators read, gradients written
+        "preprocess_bwd": ("hbm", scene.n * g_bytes * 2 + n_items * 64),
     }
     stages = {}
     for name, (bound, amount) in work.items():

@@ -170,13 +170,16 @@ geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *strea
 geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void *stream);
 
 /* Backward of geer_render_fwd (App. C two-stage RenderCUDA / PreprocessCUDA):
- * given dL/drgb (same layout as rgb), ACCUMULATE (+=) the gradients of the
- * Gaussians used in the last forward into d_mean [n][3], d_scale [n][3],
- * d_quat [n][4], d_opacity [n], d_sh [n][(deg+1)^2][3] (device, caller-owned,
- * any of them may be NULL to skip; d_sh 16-byte aligned). Must follow
+ * given dL/drgb (same layout as rgb), the gradients of the Gaussians used in
+ * the last forward go to d_mean [n][3], d_scale [n][3], d_quat [n][4],
+ * d_opacity [n], d_sh [n][(deg+1)^2][3] (device, caller-owned, any of them may
+ * be NULL to skip; d_sh 16-byte aligned). accumulate != 0: added (+=) to the
+ * buffers' contents; accumulate == 0: written, every row (Gaussians without a
+ * gradient get zeros), the buffers' previous contents never read. Must follow
  * geer_render_fwd on the same workspace with the same Gaussians. */
 geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const float *dL_drgb, float *d_mean,
-                            float *d_scale, float *d_quat, float *d_opacity, float *d_sh, void *stream);
+                            float *d_scale, float *d_quat, float *d_opacity, float *d_sh, int32_t accumulate,
+                            void *stream);
 
 /* Synchronise `stream`, then read and clear the device status word: GEER_OK or
  * GEER_ERR_CAPACITY (pairs exceeded capacity). *pairs (may be NULL) receives

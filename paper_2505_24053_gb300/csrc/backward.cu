@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_prep
     const DevCam *__restrict__ cams, int ncams, const float *__restrict__ mean, const float *__restrict__ scale,
     const float *__restrict__ quat, const float *__restrict__ sh, int64_t n, const uint32_t *__restrict__ count,
     const GradAcc *__restrict__ gacc, float *__restrict__ d_mean, float *__restrict__ d_scale,
-    float *__restrict__ d_quat, float *__restrict__ d_opacity, float *__restrict__ d_sh) {
+    float *__restrict__ d_quat, float *__restrict__ d_opacity, float *__restrict__ d_sh, int accumulate) {
     constexpr int NB = (DEG + 1) * (DEG + 1), NC = 3 * NB, ST = NC | 1;
     __shared__ float s_sh[kPBThreads * ST];
     __shared__ float s_dsh[ONE_CAM ? 1 : kPBThreads * ST];
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_prep
     s_live[tid] = any ? 1 : 0;
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     const bool block_any = __syncthreads_or(any);
-    if (!block_any) return;
+    if (!block_any && accumulate) return;
     if (any) {
         float *shc = s_sh + tid * ST;
         float *dsh = ONE_CAM ? shc : s_dsh + tid * ST;
@@ -256,19 +256,21 @@ __global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_prep
         const float gz = 2.0f * (-2.0f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.0f * z * dR[4] +
                                  y * dR[5] + x * dR[6] + y * dR[7]);
         const float proj = gw * w + gx * x + gy * y + gz * z;
-        // the accumulated gradients are all read before any is written, so that
-        // their loads are in flight together
+        // accumulating: the previous gradients are all read before any is written,
+        // so that their loads are in flight together
         float om[3] = {0, 0, 0}, os[3] = {0, 0, 0}, oq[4] = {0, 0, 0, 0}, oo = 0.0f;
-        if (d_mean)
+        if (accumulate) {
+            if (d_mean)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) om[a] = d_mean[3 * g + a];
-        if (d_scale)
+                for (int a = 0; a < 3; ++a) om[a] = d_mean[3 * g + a];
+            if (d_scale)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) os[a] = d_scale[3 * g + a];
-        if (d_quat)
+                for (int a = 0; a < 3; ++a) os[a] = d_scale[3 * g + a];
+            if (d_quat)
 #pragma unroll
-            for (int a = 0; a < 4; ++a) oq[a] = d_quat[4 * g + a];
-        if (d_opacity) oo = d_opacity[g];
+                for (int a = 0; a < 4; ++a) oq[a] = d_quat[4 * g + a];
+            if (d_opacity) oo = d_opacity[g];
+        }
         if (d_quat) {
             d_quat[4 * g + 0] = oq[0] + (gw - w * proj) / qn;
             d_quat[4 * g + 1] = oq[1] + (gx - x * proj) / qn;
@@ -282,16 +284,35 @@ __global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_prep
 #pragma unroll
             for (int a = 0; a < 3; ++a) d_scale[3 * g + a] = os[a] + ds[a];
         if (d_opacity) d_opacity[g] = oo + dsig;
+    } else if (!accumulate && tid < nloc) {  // overwriting: no gradient is a zero gradient
+        if (d_mean)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) d_mean[3 * g + a] = 0.0f;
+        if (d_scale)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) d_scale[3 * g + a] = 0.0f;
+        if (d_quat)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) d_quat[4 * g + a] = 0.0f;
+        if (d_opacity) d_opacity[g] = 0.0f;
     }
     __syncthreads();
     if (d_sh) {
-        // rows of Gaussians without a gradient are left untouched
+        // accumulating, rows of Gaussians without a gradient are left untouched;
+        // overwriting, they are zeroed
         const float *acc = ONE_CAM ? s_sh : s_dsh;
         float *dst = d_sh + g0 * NC;
 #ifndef GEER_PB_BATCH
 #define GEER_PB_BATCH 24
 #endif
         constexpr int kBatch = GEER_PB_BATCH;  // values in flight per thread
+        if (!accumulate) {
+            for (int i = tid; i < nloc * NC; i += kPBThreads) {
+                const int gl = i / NC;
+                dst[i] = s_live[gl] ? acc[gl * ST + (i - gl * NC)] : 0.0f;
+            }
+            return;
+        }
         for (int i0 = tid; i0 < nloc * NC; i0 += kBatch * kPBThreads) {
             float v[kBatch];
 #pragma unroll
@@ -335,18 +356,18 @@ __global__ void __launch_bounds__(256) k_l1_grad(const float *__restrict__ pred,
 }  // namespace
 
 cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians *g, float *d_mean, float *d_scale,
-                                  float *d_quat, float *d_opacity, float *d_sh, cudaStream_t s) {
+                                  float *d_quat, float *d_opacity, float *d_sh, int accumulate, cudaStream_t s) {
     if (g->n == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((g->n + kPBThreads - 1) / kPBThreads);
 #define GEER_PB_LAUNCH(D)                                                                                      \
     if (ws->n_cams == 1)                                                                                       \
         k_preprocess_bwd<D, true><<<blocks, kPBThreads, 0, s>>>(                                               \
             ws->d_cams, 1, g->mean, g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean, d_scale,   \
-            d_quat, d_opacity, d_sh);                                                                          \
+            d_quat, d_opacity, d_sh, accumulate);                                                              \
     else                                                                                                       \
         k_preprocess_bwd<D, false><<<blocks, kPBThreads, 0, s>>>(                                              \
             ws->d_cams, ws->n_cams, g->mean, g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean,  \
-            d_scale, d_quat, d_opacity, d_sh)
+            d_scale, d_quat, d_opacity, d_sh, accumulate)
     switch (g->sh_degree) {
         case 0: GEER_PB_LAUNCH(0); break;
         case 1: GEER_PB_LAUNCH(1); break;

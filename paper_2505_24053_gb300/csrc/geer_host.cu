@@ -639,7 +639,8 @@ geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void
 }
 
 geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const float *dL_drgb, float *d_mean,
-                            float *d_scale, float *d_quat, float *d_opacity, float *d_sh, void *stream) {
+                            float *d_scale, float *d_quat, float *d_opacity, float *d_sh, int32_t accumulate,
+                            void *stream) {
     if (!ws || !dL_drgb) return GEER_ERR_ARG;
     if (ws->stage < 3) return GEER_ERR_STATE;
     geer_status st = check_gaussians(ws, g);
@@ -655,7 +656,7 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
             return GEER_ERR_CUDA;
     }
     StageTimer tm(ws, kStagePreprocessBwd, s);
-    return cuda_status(launch_preprocess_bwd(ws, g, d_mean, d_scale, d_quat, d_opacity, d_sh, s));
+    return cuda_status(launch_preprocess_bwd(ws, g, d_mean, d_scale, d_quat, d_opacity, d_sh, accumulate ? 1 : 0, s));
 }
 
 geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *stream) {

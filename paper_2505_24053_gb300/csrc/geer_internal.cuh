@@ -214,7 +214,7 @@ cudaError_t launch_tile_sort(geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_final, cudaStream_t s);
 cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians *g, float *d_mean, float *d_scale,
-                                  float *d_quat, float *d_opacity, float *d_sh, cudaStream_t s);
+                                  float *d_quat, float *d_opacity, float *d_sh, int accumulate, cudaStream_t s);
 cudaError_t launch_l1_grad(const float *pred, const float *target, int64_t m, float *grad, float *loss, int num_sms,
                            cudaStream_t s);
 cudaError_t launch_remap_to_native(const float *beap, const geer_camera *cam, double fov_y, double focal,

@@ -509,11 +509,17 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
 // chunk serially). mode 0 (live items): total -> misc[kMiscLive]; also clears the
 // per-super-tile pair counts. mode 1 ((super-tile, item) pairs): total ->
 // misc[kMiscPairs] (clamped to cap) with the capacity check. mode 2 ((tile, item)
-// associations P): total -> misc[kMiscTileLo / Hi].
+// associations P): total -> misc[kMiscTileLo / Hi]. With two blocks, block 1
+// scans blocksum_b in mode_b at the same time (one launch for two arrays).
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ blocksum, int64_t m,
                                                       uint32_t *__restrict__ misc, uint2 *__restrict__ srange,
-                                                      int64_t nst, int64_t cap, int mode) {
+                                                      int64_t nst, int64_t cap, int mode,
+                                                      uint32_t *__restrict__ blocksum_b = nullptr, int mode_b = 0) {
     __shared__ unsigned long long warp_tot[32];
+    if (blockIdx.x == 1) {
+        blocksum = blocksum_b;
+        mode = mode_b;
+    }
     const int t = threadIdx.x;
     const int64_t chunk = (m + 1023) / 1024;
     const int64_t b = t * chunk, e = min(m, b + chunk);
@@ -901,10 +907,7 @@ cudaError_t launch_count_pairs(const geer_workspace *ws, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     // super-tile pairs: emission offsets and the capacity check; tile associations: the count P
-    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum2, m, ws->d_misc, nullptr, 0, ws->cap_pairs, 1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum3, m, ws->d_misc, nullptr, 0, ws->cap_pairs, 2);
+    k_scan_blocks<<<2, 1024, 0, s>>>(ws->d_blocksum2, m, ws->d_misc, nullptr, 0, ws->cap_pairs, 1, ws->d_blocksum3, 2);
     return cudaGetLastError();
 }
 

@@ -80,7 +80,7 @@ def lib(build_if_missing: bool = True):
         "geer_preprocess": [P, P, P],
         "geer_bin_sort": [P, P, P],
         "geer_render_fwd": [P, P, P, P],
-        "geer_render_bwd": [P, P, P, P, P, P, P, P, P],
+        "geer_render_bwd": [P, P, P, P, P, P, P, P, I32, P],
         "geer_last_device_status": [P, P, P],
         "geer_debug_preprocess": [P, P, P, P, P, P],
         "geer_debug_pairs": [P, P, P, I64, P, P],
@@ -247,7 +247,8 @@ class Workspace:
                                      C.c_void_p(T.data_ptr()) if T is not None else None, _stream(stream)),
                "geer_render_fwd")
 
-    def render_bwd(self, g: Gaussians, dL_drgb: torch.Tensor, grads: dict, stream=None):
+    def render_bwd(self, g: Gaussians, dL_drgb: torch.Tensor, grads: dict, accumulate: bool = True, stream=None):
+        """Gradients into grads' tensors: added to them (accumulate) or written."""
         gc = g.c_struct()
 
         def ptr(name):
@@ -255,7 +256,8 @@ class Workspace:
             return C.c_void_p(t.data_ptr()) if t is not None else None
 
         _check(lib().geer_render_bwd(self._handle, C.byref(gc), C.c_void_p(dL_drgb.data_ptr()), ptr("mean"),
-                                     ptr("scale"), ptr("quat"), ptr("opacity"), ptr("sh"), _stream(stream)),
+                                     ptr("scale"), ptr("quat"), ptr("opacity"), ptr("sh"), 1 if accumulate else 0,
+                                     _stream(stream)),
                "geer_render_bwd")
 
     def device_status(self, stream=None):
@@ -395,11 +397,13 @@ class Renderer:
         return rgb
 
     def backward(self, g: Gaussians, dL_drgb: torch.Tensor, grads: dict | None = None) -> dict:
-        """Gradients of the last forward (accumulated into grads if given)."""
+        """Gradients of the last forward: accumulated into grads if given, else in
+        new tensors (written, not zero-filled first)."""
+        accumulate = grads is not None
         if grads is None:
-            grads = {k: torch.zeros_like(v) for k, v in (("mean", g.mean), ("scale", g.scale), ("quat", g.quat),
+            grads = {k: torch.empty_like(v) for k, v in (("mean", g.mean), ("scale", g.scale), ("quat", g.quat),
                                                          ("opacity", g.opacity), ("sh", g.sh))}
-        self.ws.render_bwd(g, dL_drgb.contiguous(), grads)
+        self.ws.render_bwd(g, dL_drgb.contiguous(), grads, accumulate=accumulate)
         return grads
 
     def images(self, rgb: torch.Tensor):

@@ -192,6 +192,32 @@ def test_autograd_and_accumulation(geer):
         close(direct[k], 2 * p.grad, k)
 
 
+def test_overwrite_writes_every_row(geer):
+    """accumulate == 0 writes every gradient row (zeros where a Gaussian has no
+    gradient: here the half behind the camera) and never reads the buffers (they
+    start as NaN); equal to accumulating into zeros up to the atomics' order."""
+    scene = _scene(21, 300, 3, zlo=-6.0, zhi=4.0)
+    cam = wl.Camera(wl.PINHOLE, 48, 40, math.radians(80))
+    r = geer.Renderer([cam], scene.n, scene.sh_degree)
+    g = geer.Gaussians.from_scene(scene)
+    rgb = r.forward(g)
+    w = torch.randn_like(rgb)
+    shapes = (("mean", g.mean), ("scale", g.scale), ("quat", g.quat), ("opacity", g.opacity), ("sh", g.sh))
+    acc = {k: torch.zeros_like(v) for k, v in shapes}
+    r.ws.render_bwd(g, w, acc, accumulate=True)
+    out = {k: torch.full_like(v, float("nan")) for k, v in shapes}
+    r.ws.render_bwd(g, w, out, accumulate=False)
+    torch.cuda.synchronize()
+    behind = torch.as_tensor(scene.mean[:, 2] < -3.0, device="cuda")  # beyond any extent
+    assert int(behind.sum()) > 50
+    for k in BLOCKS:
+        a, b = out[k], acc[k]
+        assert not torch.isnan(a).any(), k
+        assert float(a[behind].abs().max()) == 0.0, k
+        scale = float(b.abs().max())
+        assert float((a - b).abs().max()) <= 1e-5 * scale + 1e-9, (k, float((a - b).abs().max()), scale)
+
+
 def _sparse_dl(cams, per_cam, seed):
     rng = np.random.default_rng(seed)
     pixels = sum(c.pixels for c in cams)
