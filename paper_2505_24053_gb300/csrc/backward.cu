@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_prep
     const float *__restrict__ quat, const float *__restrict__ sh, int64_t n, const uint32_t *__restrict__ count,
     const GradAcc *__restrict__ gacc, float *__restrict__ d_mean, float *__restrict__ d_scale,
     float *__restrict__ d_quat, float *__restrict__ d_opacity, float *__restrict__ d_sh, int accumulate) {
+    grid_dep_sync();
     constexpr int NB = (DEG + 1) * (DEG + 1), NC = 3 * NB, ST = NC | 1;
     __shared__ float s_sh[kPBThreads * ST];
     __shared__ float s_dsh[ONE_CAM ? 1 : kPBThreads * ST];
@@ -332,6 +333,7 @@ __global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_prep
 // L1 loss mean |C - target| over all values and its gradient sign(C - target)/m.
 __global__ void __launch_bounds__(256) k_l1_grad(const float *__restrict__ pred, const float *__restrict__ target,
                                                  int64_t m, float *__restrict__ grad, float *__restrict__ loss) {
+    grid_dep_sync();
     __shared__ float red[8];
     const float inv = 1.0f / (float)m;
     float acc = 0.0f;
@@ -361,13 +363,13 @@ cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians
     const unsigned blocks = (unsigned)((g->n + kPBThreads - 1) / kPBThreads);
 #define GEER_PB_LAUNCH(D)                                                                                      \
     if (ws->n_cams == 1)                                                                                       \
-        k_preprocess_bwd<D, true><<<blocks, kPBThreads, 0, s>>>(                                               \
-            ws->d_cams, 1, g->mean, g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean, d_scale,   \
-            d_quat, d_opacity, d_sh, accumulate);                                                              \
+        launch_k(k_preprocess_bwd<D, true>, dim3(blocks), dim3(kPBThreads), 0, s, ws->d_cams, 1, g->mean,      \
+                 g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean, d_scale, d_quat, d_opacity,  \
+                 d_sh, accumulate);                                                                            \
     else                                                                                                       \
-        k_preprocess_bwd<D, false><<<blocks, kPBThreads, 0, s>>>(                                              \
-            ws->d_cams, ws->n_cams, g->mean, g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean,  \
-            d_scale, d_quat, d_opacity, d_sh, accumulate)
+        launch_k(k_preprocess_bwd<D, false>, dim3(blocks), dim3(kPBThreads), 0, s, ws->d_cams, ws->n_cams,     \
+                 g->mean, g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean, d_scale, d_quat,    \
+                 d_opacity, d_sh, accumulate)
     switch (g->sh_degree) {
         case 0: GEER_PB_LAUNCH(0); break;
         case 1: GEER_PB_LAUNCH(1); break;
@@ -386,7 +388,7 @@ cudaError_t launch_l1_grad(const float *pred, const float *target, int64_t m, fl
         if (e != cudaSuccess) return e;
     }
     const int64_t blocks = std::min<int64_t>((m + 255) / 256, (int64_t)num_sms * 8);
-    k_l1_grad<<<(unsigned)blocks, 256, 0, s>>>(pred, target, m, grad, loss);
+    launch_k(k_l1_grad, dim3((unsigned)blocks), dim3(256), 0, s, pred, target, m, grad, loss);
     return cudaGetLastError();
 }
 

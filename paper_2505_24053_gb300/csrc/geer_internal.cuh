@@ -92,6 +92,38 @@ struct Params {
 // PBF association ranges of a (camera, Gaussian) item, packed as u16 pairs:
 // [0,1) columns and [4,5) rows of the direct arcs, [2,3) and [6,7) of the arcs
 // shifted by pi (rays beyond 90 degrees).
+#ifndef GEER_PDL
+#define GEER_PDL 1  // programmatic dependent launch of the library's kernels
+#endif
+
+// Programmatic dependent launch: every kernel first lets the next kernel on its
+// stream begin launching (its blocks may become resident while this grid's last
+// blocks run), then waits until its own predecessor grid has completed and its
+// writes are visible (griddepcontrol). The next grid launches only once every
+// block of this one has started, so a waiting block never keeps a predecessor's
+// block from starting. For an ordinary stream-ordered launch both are no-ops.
+__device__ __forceinline__ void grid_dep_sync() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launches a kernel on stream s with programmatic stream serialization (GEER_PDL).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = GEER_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Asynchronous 4-byte global -> shared copy (completed by cp.async.wait_all).
 __device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);

@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
     const float *__restrict__ opacity, const float *__restrict__ sh, int64_t n, Record *__restrict__ rec,
     uint4 *__restrict__ ranges, uint32_t *__restrict__ count, uint32_t *__restrict__ key,
     uint32_t *__restrict__ blocksum, int64_t nblk) {
+    grid_dep_sync();
     constexpr int NC = 3 * (DEG + 1) * (DEG + 1), ST = PrepSh<DEG>::kStride;
     extern __shared__ float s_sh[];  // [kPrepThreads][ST]
     __shared__ uint32_t red[kPrepThreads / 32];
@@ -515,6 +516,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ blo
                                                       uint32_t *__restrict__ misc, uint2 *__restrict__ srange,
                                                       int64_t nst, int64_t cap, int mode,
                                                       uint32_t *__restrict__ blocksum_b = nullptr, int mode_b = 0) {
+    grid_dep_sync();
     __shared__ unsigned long long warp_tot[32];
     if (blockIdx.x == 1) {
         blocksum = blocksum_b;
@@ -576,6 +578,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_compact(int ncams, int64_t n, 
                                                           const uint32_t *__restrict__ key,
                                                           const uint32_t *__restrict__ blocksum, int64_t nblk,
                                                           uint32_t *__restrict__ okey, uint32_t *__restrict__ oid) {
+    grid_dep_sync();
     __shared__ uint32_t wsum[kPrepThreads / 32];
     const int64_t g = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
     for (int ci = 0; ci < ncams; ++ci) {
@@ -614,6 +617,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_gather_counts(const DevCam *__
                                                                 const uint32_t *__restrict__ misc,
                                                                 uint32_t *__restrict__ bs_super,
                                                                 uint32_t *__restrict__ bs_tile) {
+    grid_dep_sync();
     __shared__ uint32_t red[kPrepThreads / 32];
     const uint32_t L = misc[kMiscLive];
     const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
@@ -643,6 +647,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
     const uint32_t *__restrict__ sorted_id, const uint4 *__restrict__ ranges, const uint32_t *__restrict__ count,
     const uint32_t *__restrict__ misc, const uint32_t *__restrict__ blocksum, uint32_t *__restrict__ okeys,
     uint32_t *__restrict__ ovals, uint32_t *__restrict__ scount, int nst, int64_t cap) {
+    grid_dep_sync();
     __shared__ uint32_t wsum[kPrepThreads / 32];
     extern __shared__ uint32_t sh[];  // per-super-tile pair counts when they fit (nst <= kSmemTiles)
     const bool smem = nst <= kSmemTiles;
@@ -739,6 +744,45 @@ __device__ __forceinline__ int order_bucket(uint32_t c) {
     return 127 - (lg * 4 + (lg >= 2 ? sub : 0));
 }
 
+// Warp-aggregated bucket atomic: the lanes with ok hold bucket bk; one atomic
+// per distinct bucket of the warp adds the lanes' count to hist[bk]. Returns the
+// lane's slot (old value + its rank among the lanes of its bucket). All lanes of
+// the warp must call it.
+__device__ __forceinline__ uint32_t bucket_add(uint32_t *hist, bool ok, int bk) {
+    const unsigned peers = __match_any_sync(0xffffffffu, ok ? bk : -1);
+    const int leader = __ffs(peers) - 1, lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (ok && lane == leader) base = atomicAdd(&hist[bk], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
+// Exclusive scan of the kOrderBuckets bucket sizes in place (warp 0; the block
+// synchronises before and after).
+__device__ __forceinline__ void bucket_scan(uint32_t *hist) {
+    if (threadIdx.x >= 32) return;
+    constexpr int kPer = (kOrderBuckets + 31) / 32;
+    const int lane = threadIdx.x, b0 = lane * kPer;
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        v[k] = b0 + k < kOrderBuckets ? hist[b0 + k] : 0u;
+        sum += v[k];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        if (b0 + k < kOrderBuckets) hist[b0 + k] = run;
+        run += v[k];
+    }
+}
+
 // Exclusive scan over [0, m) of counts held as contiguous per-thread chunks by a
 // 1024-thread block: returns the prefix of the thread's chunk (s = the chunk's sum).
 __device__ __forceinline__ uint32_t block_chunk_prefix(uint32_t s, uint32_t *warp_tot) {
@@ -777,6 +821,7 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
                                                        int ntiles, uint2 *__restrict__ srange, int nst,
                                                        const uint32_t *__restrict__ misc,
                                                        uint32_t *__restrict__ tile_order) {
+    grid_dep_sync();
     __shared__ uint32_t warp_tot[32];
     __shared__ uint32_t hist[kOrderBuckets];
     if (misc[kMiscStatus] & kStatusCapacity) return;
@@ -803,30 +848,24 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
         if (cams[k].tile_base <= b) c = k;
     for (int pass = 0; pass < 2; ++pass) {
         int cc = c;
-        for (int i = b; i < e; ++i) {
-            while (cc + 1 < ncams && cams[cc + 1].tile_base <= i) ++cc;
-            const DevCam &cm = cams[cc];
-            const int lt = i - cm.tile_base;
+        for (int k = 0; k < chunk; ++k) {  // the same trip count in every lane (warp-wide atomics)
+            const int i = b + k;
             uint32_t len = 0;
-            if (lt >= 0 && lt < cm.tiles_x * cm.tiles_y) {
-                const int cy = lt / cm.tiles_x, cx = lt - cy * cm.tiles_x;
-                const uint2 r = srange[cm.stile_base + (cy / S) * cm.stiles_x + cx / S];
-                len = r.y - r.x;
+            if (i < e) {
+                while (cc + 1 < ncams && cams[cc + 1].tile_base <= i) ++cc;
+                const DevCam &cm = cams[cc];
+                const int lt = i - cm.tile_base;
+                if (lt >= 0 && lt < cm.tiles_x * cm.tiles_y) {
+                    const int cy = lt / cm.tiles_x, cx = lt - cy * cm.tiles_x;
+                    const uint2 r = srange[cm.stile_base + (cy / S) * cm.stiles_x + cx / S];
+                    len = r.y - r.x;
+                }
             }
-            if (pass == 0)
-                atomicAdd(&hist[order_bucket(len)], 1u);
-            else
-                tile_order[atomicAdd(&hist[order_bucket(len)], 1u)] = (uint32_t)i;
+            const uint32_t slot = bucket_add(hist, i < e, order_bucket(len));
+            if (pass == 1 && i < e) tile_order[slot] = (uint32_t)i;
         }
         __syncthreads();
-        if (pass == 0 && t == 0) {  // exclusive scan of the bucket sizes (129 entries, one thread)
-            uint32_t run = 0;
-            for (int i = 0; i < kOrderBuckets; ++i) {
-                const uint32_t h = hist[i];
-                hist[i] = run;
-                run += h;
-            }
-        }
+        if (pass == 0) bucket_scan(hist);
         __syncthreads();
     }
 }
@@ -836,6 +875,7 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
 __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ tile_walk, int ntiles,
                                                     const uint32_t *__restrict__ misc,
                                                     uint32_t *__restrict__ order) {
+    grid_dep_sync();
     __shared__ uint32_t hist[kOrderBuckets];
     if (misc[kMiscStatus] & kStatusCapacity) return;
     const int t = threadIdx.x;
@@ -843,18 +883,18 @@ __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ ti
     __syncthreads();
     const int chunk = (ntiles + 1023) / 1024;
     const int b = t * chunk, e = min(ntiles, b + chunk);
-    for (int i = b; i < e; ++i) atomicAdd(&hist[order_bucket(tile_walk[i].y)], 1u);
-    __syncthreads();
-    if (t == 0) {
-        uint32_t run = 0;
-        for (int i = 0; i < kOrderBuckets; ++i) {
-            const uint32_t h = hist[i];
-            hist[i] = run;
-            run += h;
-        }
+    for (int k = 0; k < chunk; ++k) {
+        const int i = b + k;
+        bucket_add(hist, i < e, i < e ? order_bucket(tile_walk[i].y) : 0);
     }
     __syncthreads();
-    for (int i = b; i < e; ++i) order[atomicAdd(&hist[order_bucket(tile_walk[i].y)], 1u)] = (uint32_t)i;
+    bucket_scan(hist);
+    __syncthreads();
+    for (int k = 0; k < chunk; ++k) {
+        const int i = b + k;
+        const uint32_t slot = bucket_add(hist, i < e, i < e ? order_bucket(tile_walk[i].y) : 0);
+        if (i < e) order[slot] = (uint32_t)i;
+    }
 }
 
 }  // namespace
@@ -871,9 +911,9 @@ cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g,
                                                        smem);                                                    \
             if (e != cudaSuccess) return e;                                                                      \
         }                                                                                                        \
-        k_preprocess<D><<<(unsigned)nblk, kPrepThreads, smem, s>>>(                                              \
-            ws->d_cams, ws->n_cams, ws->d_tile_tab, prm, g->mean, g->scale, g->quat, g->opacity, g->sh, g->n,    \
-            ws->d_rec, ws->d_ranges, ws->d_count, ws->d_key, ws->d_blocksum, nblk);                             \
+        launch_k(k_preprocess<D>, dim3((unsigned)nblk), dim3(kPrepThreads), smem, s, ws->d_cams, ws->n_cams,      \
+                 ws->d_tile_tab, prm, g->mean, g->scale, g->quat, g->opacity, g->sh, g->n, ws->d_rec,            \
+                 ws->d_ranges, ws->d_count, ws->d_key, ws->d_blocksum, nblk);                             \
     }
     switch (g->sh_degree) {
         case 0: GEER_PREP_LAUNCH(0); break;
@@ -887,27 +927,27 @@ cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g,
 
 cudaError_t launch_bin_front(const geer_workspace *ws, cudaStream_t s) {
     const int64_t nblk = prep_blocks(ws->n_gauss);
-    k_scan_blocks<<<1, 1024, 0, s>>>(ws->d_blocksum, nblk * ws->n_cams, ws->d_misc, ws->d_srange, ws->n_stiles,
-                                     ws->cap_pairs, 0);
+    launch_k(k_scan_blocks, dim3(1), dim3(1024), 0, s, ws->d_blocksum, nblk * ws->n_cams, ws->d_misc, ws->d_srange,
+             ws->n_stiles, ws->cap_pairs, 0, nullptr, 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || nblk == 0) return e;
-    k_compact<<<(unsigned)nblk, kPrepThreads, 0, s>>>(ws->n_cams, ws->n_gauss, ws->d_count, ws->d_key,
-                                                      ws->d_blocksum, nblk, ws->d_ikey[0], ws->d_iid[0]);
+    launch_k(k_compact, dim3((unsigned)nblk), dim3(kPrepThreads), 0, s, ws->n_cams, ws->n_gauss, ws->d_count,
+             ws->d_key, ws->d_blocksum, nblk, ws->d_ikey[0], ws->d_iid[0]);
     return cudaGetLastError();
 }
 
 cudaError_t launch_count_pairs(const geer_workspace *ws, cudaStream_t s) {
     const int64_t m = prep_blocks((int64_t)ws->n_cams * ws->n_gauss);
     if (m > 0) {
-        k_gather_counts<<<(unsigned)m, kPrepThreads, 0, s>>>(ws->d_cams, ws->d_tile_tab, ws->n_gauss,
-                                                             ws->super_size, ws->d_iid[ws->depth_buf], ws->d_count,
-                                                             ws->d_ranges, ws->d_misc, ws->d_blocksum2,
-                                                             ws->d_blocksum3);
+        launch_k(k_gather_counts, dim3((unsigned)m), dim3(kPrepThreads), 0, s, ws->d_cams, ws->d_tile_tab,
+                 ws->n_gauss, ws->super_size, ws->d_iid[ws->depth_buf], ws->d_count, ws->d_ranges, ws->d_misc,
+                 ws->d_blocksum2, ws->d_blocksum3);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     // super-tile pairs: emission offsets and the capacity check; tile associations: the count P
-    k_scan_blocks<<<2, 1024, 0, s>>>(ws->d_blocksum2, m, ws->d_misc, nullptr, 0, ws->cap_pairs, 1, ws->d_blocksum3, 2);
+    launch_k(k_scan_blocks, dim3(2), dim3(1024), 0, s, ws->d_blocksum2, m, ws->d_misc, nullptr, 0, ws->cap_pairs, 1,
+             ws->d_blocksum3, 2);
     return cudaGetLastError();
 }
 
@@ -916,21 +956,20 @@ cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
     uint32_t *scount = reinterpret_cast<uint32_t *>(ws->d_srange + ws->n_stiles);
     if (m > 0) {
         const size_t smem = ws->n_stiles <= kSmemTiles ? sizeof(uint32_t) * ws->n_stiles : 0;
-        k_duplicate<<<(unsigned)m, kPrepThreads, smem, s>>>(
-            ws->d_cams, ws->d_tile_tab, ws->n_gauss, ws->super_size, ws->d_iid[ws->depth_buf], ws->d_ranges,
-            ws->d_count, ws->d_misc, ws->d_blocksum2, ws->d_keys[0], ws->d_vals[0], scount, (int)ws->n_stiles,
-            ws->cap_pairs);
+        launch_k(k_duplicate, dim3((unsigned)m), dim3(kPrepThreads), smem, s, ws->d_cams, ws->d_tile_tab,
+                 ws->n_gauss, ws->super_size, ws->d_iid[ws->depth_buf], ws->d_ranges, ws->d_count, ws->d_misc,
+                 ws->d_blocksum2, ws->d_keys[0], ws->d_vals[0], scount, (int)ws->n_stiles, ws->cap_pairs);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    k_tile_offsets<<<1, 1024, 0, s>>>(ws->d_cams, ws->n_cams, ws->super_size, (int)ws->n_tiles, ws->d_srange,
-                                      (int)ws->n_stiles, ws->d_misc, ws->d_tile_order);
+    launch_k(k_tile_offsets, dim3(1), dim3(1024), 0, s, ws->d_cams, ws->n_cams, ws->super_size, (int)ws->n_tiles,
+             ws->d_srange, (int)ws->n_stiles, ws->d_misc, ws->d_tile_order);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_order(const geer_workspace *ws, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
-    k_bwd_order<<<1, 1024, 0, s>>>(ws->d_tile_walk, (int)ws->n_tiles, ws->d_misc, ws->d_bwd_order);
+    launch_k(k_bwd_order, dim3(1), dim3(1024), 0, s, ws->d_tile_walk, (int)ws->n_tiles, ws->d_misc, ws->d_bwd_order);
     return cudaGetLastError();
 }
 

@@ -37,6 +37,7 @@ __device__ __forceinline__ float kb_poly(const float k[4], float p, float &dp) {
 
 __global__ void __launch_bounds__(256) k_remap_to_native(const float *__restrict__ beap, RemapCam c,
                                                          float *__restrict__ out) {
+    grid_dep_sync();
     const int64_t n = (int64_t)c.width * c.height;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
@@ -111,7 +112,7 @@ cudaError_t launch_remap_to_native(const float *beap, const geer_camera *cam, do
     for (int i = 0; i < 3; ++i) c.fill[i] = fill ? fill[i] : 0.0f;
     const int64_t n = (int64_t)cam->width * cam->height;
     if (n == 0) return cudaSuccess;
-    k_remap_to_native<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(beap, c, out);
+    launch_k(k_remap_to_native, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, beap, c, out);
     return cudaGetLastError();
 }
 

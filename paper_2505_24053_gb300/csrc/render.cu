@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                                             uint32_t *__restrict__ last_out,
                                                             uint2 *__restrict__ evals, uint2 *__restrict__ hit,
                                                             int64_t hit_entries) {
+    grid_dep_sync();
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     static_assert(kParts == 1, "one block per tile: the block records the tile's walk");
     __shared__ WalkSmem<kThreads, BATCH> sm;
@@ -396,6 +397,7 @@ __global__ void __launch_bounds__(kTilePix) k_expand_tiles(const DevCam *__restr
                                                           const uint32_t *__restrict__ misc,
                                                           uint32_t *__restrict__ count_or_off,
                                                           uint32_t *__restrict__ lists, int64_t cap) {
+    grid_dep_sync();
     __shared__ uint32_t s_id[2 * kTilePix];
     __shared__ uint32_t s_wcnt[kTilePix / 32];
     __shared__ int s_cam;
@@ -629,6 +631,7 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
                                                                            const uint2 *__restrict__ hit,
                                                                            int64_t hit_entries,
                                                                            GradAcc *__restrict__ gacc) {
+    grid_dep_sync();
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     __shared__ WalkSmem<kThreads, BATCH> sm;
     __shared__ float s_acc[BATCH][17];
@@ -670,7 +673,7 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
 cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_final, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
     constexpr int R = GEER_FWD_ROWS, B = GEER_FWD_BATCH;
-    k_render_fwd<R, B><<<(unsigned)(ws->n_tiles * (kTile / R)), R * kTile, 0, s>>>(
+    launch_k(k_render_fwd<R, B>, dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile), 0, s,
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_tile_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, rgb, T_final,
@@ -680,16 +683,16 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
 
 cudaError_t launch_expand_tiles(const geer_workspace *ws, uint32_t *count_or_off, uint32_t *lists, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
-    k_expand_tiles<<<(unsigned)ws->n_tiles, kTilePix, 0, s>>>(ws->d_cams, ws->n_cams, ws->d_tile_tab, ws->super_size,
-                                                             ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges,
-                                                             ws->d_misc, count_or_off, lists, ws->cap_pairs);
+    launch_k(k_expand_tiles, dim3((unsigned)ws->n_tiles), dim3(kTilePix), 0, s, ws->d_cams, ws->n_cams,
+             ws->d_tile_tab, ws->super_size, ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_misc,
+             count_or_off, lists, ws->cap_pairs);
     return cudaGetLastError();
 }
 
 cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
     constexpr int R = GEER_BWD_ROWS, B = GEER_BWD_BATCH;
-    k_render_bwd<R, B><<<(unsigned)(ws->n_tiles * (kTile / R)), R * kTile, 0, s>>>(
+    launch_k(k_render_bwd<R, B>, dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile), 0, s,
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_bwd_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, dL_drgb,

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
                                                              uint32_t *__restrict__ group_sum,
                                                              uint32_t *__restrict__ group_excl,
                                                              uint32_t *__restrict__ digit_base) {
+    grid_dep_sync();
     constexpr int W = kSortThreads / 32, TILE = kSortThreads * ITEMS, GROUP = kGroupTiles;
     __shared__ uint32_t s_h[W][kRadix];
     __shared__ uint32_t s_wsum[W];
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ misc, int count_slot, int check_capacity, int shift,
     const uint32_t *__restrict__ tile_hist, const uint32_t *__restrict__ group_excl,
     const uint32_t *__restrict__ digit_base, const uint4 *__restrict__ ranges, uint4 *__restrict__ rout) {
+    grid_dep_sync();
     constexpr int W = kSortThreads / 32, TILE = kSortThreads * ITEMS, GROUP = kGroupTiles;
     __shared__ uint32_t s_whist[W][kRadix];
     __shared__ uint32_t s_match[W][kRadix];  // lane masks per digit, zero between ranking steps
@@ -258,13 +260,13 @@ static cudaError_t radix_pass_t(geer_workspace *ws, uint32_t *const kbuf[2], uin
                                 int slot, int check, int shift, int64_t cap_keys, uint4 *rout, cudaStream_t s) {
     constexpr int TILE = kSortThreads * ITEMS;
     const unsigned tiles = (unsigned)std::max<int64_t>(1, (cap_keys + TILE - 1) / TILE);
-    k_radix_hist<ITEMS><<<tiles, kSortThreads, 0, s>>>(kbuf[cur], ws->d_misc, slot, check, shift, ws->d_tile_hist,
-                                                       ws->d_group_sum, ws->d_group_excl, ws->d_digit_base);
+    launch_k(k_radix_hist<ITEMS>, dim3(tiles), dim3(kSortThreads), 0, s, kbuf[cur], ws->d_misc, slot, check, shift,
+             ws->d_tile_hist, ws->d_group_sum, ws->d_group_excl, ws->d_digit_base);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_radix_scatter<ITEMS><<<tiles, kSortThreads, 0, s>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1],
-                                                          ws->d_misc, slot, check, shift, ws->d_tile_hist,
-                                                          ws->d_group_excl, ws->d_digit_base, ws->d_ranges, rout);
+    launch_k(k_radix_scatter<ITEMS>, dim3(tiles), dim3(kSortThreads), 0, s, kbuf[cur], vbuf[cur], kbuf[cur ^ 1],
+             vbuf[cur ^ 1], ws->d_misc, slot, check, shift, ws->d_tile_hist, ws->d_group_excl, ws->d_digit_base,
+             ws->d_ranges, rout);
     return cudaGetLastError();
 }
 
