@@ -184,7 +184,7 @@ struct WalkSmem {
     int cam;
 };
 
-// Per-ray forward state.
+// Per-ray forward state (n_eval: entries evaluated, set when the walk ends).
 struct FwdRay {
     float T, cr, cg, cb;
     uint32_t last, n_eval, n_applied;
@@ -248,12 +248,12 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                     if (v[u].hit) hit_b[(j + u) * 8] = 1;
 #pragma unroll
                 for (int u = 0; u < kFwdUnroll; ++u) {
-                    ++f.n_eval;
                     if (!v[u].hit) continue;
                     const float alpha = fminf(exp2f(v[u].arg), p.alpha_max);
                     const float Tn = f.T * (1.0f - alpha);
                     if (Tn < p.T_min) {
                         f.done = true;
+                        f.n_eval = n_list + (uint32_t)(j + u) + 1u;  // entries up to this one
                         break;
                     }
                     const float wgt = alpha * f.T;
@@ -266,7 +266,6 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                 }
             }
             for (; j < cnt && !f.done; ++j) {
-                ++f.n_eval;
                 const float4 a = sm.rec[j * 4 + 0];
                 const float4 b = sm.rec[j * 4 + 1];
                 const float4 c = sm.rec[j * 4 + 2];
@@ -278,6 +277,7 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                 const float Tn = f.T * (1.0f - alpha);
                 if (Tn < p.T_min) {
                     f.done = true;
+                    f.n_eval = n_list + (uint32_t)j + 1u;
                     break;
                 }
                 const float wgt = alpha * f.T;
@@ -300,6 +300,7 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
         shift_list<kThreads>(sm.id, sm.pos, cnt, s_cnt);
         n_list += (uint32_t)cnt;
     }
+    if (!f.done) f.n_eval = n_list;  // a ray that never terminated evaluated every entry walked
     __syncthreads();
 }
 
@@ -519,60 +520,69 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
             for (int k = 0; k < 4; ++k) sm.rec[r * 4 + k] = src[k];
             // beyond the recorded entries every warp evaluates
             const uint32_t j = top - 1u - (uint32_t)r;
-            sm.hit[r] = hit_rec && (int64_t)j < hit_entries ? hit_rec[j] : make_uint2(~0u, ~0u);
+            // transposed to warp-major order: warp w's flags of the batch are contiguous
+            const uint2 h = hit_rec && (int64_t)j < hit_entries ? hit_rec[j] : make_uint2(~0u, ~0u);
+            uint8_t *hw = reinterpret_cast<uint8_t *>(sm.hit);
+#pragma unroll
+            for (int w = 0; w < kTileWarps; ++w)
+                hw[w * BATCH + r] = (uint8_t)((w < 4 ? h.x : h.y) >> (8 * (w & 3)));
         }
         for (int i = skip * 17 + tid; i < cnt * 17; i += kThreads) (&s_acc[0][0])[i] = 0.0f;
         __syncthreads();
         // this warp's first entry below its rays' last contributor (warp-uniform)
         const int r0 = max(skip, top > warp_last ? (int)min((uint32_t)cnt, top - warp_last) : 0);
-        const uint8_t *hit_b = reinterpret_cast<const uint8_t *>(sm.hit) + fwarp;
-        for (int r = r0; r < cnt; ++r) {
-            // no ray of this warp hit the entry in the forward: the same FP32
-            // decisions here would not either (warp-uniform)
-            if (!hit_b[r * 8]) continue;
-            const uint32_t j = top - 1u - (uint32_t)r;
-            float gv[16];
+        // entries none of this warp's rays hit in the forward are skipped (the same
+        // FP32 decisions here would not hit either): 32 entries' flags per ballot
+        const uint8_t *hit_w = reinterpret_cast<const uint8_t *>(sm.hit) + fwarp * BATCH;
+        for (int base = r0; base < cnt; base += 32) {
+            uint32_t todo = __ballot_sync(0xffffffffu, base + lane < cnt && hit_w[base + lane] != 0);
+            while (todo) {
+                const int r = base + __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const uint32_t j = top - 1u - (uint32_t)r;
+                float gv[16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) gv[k] = 0.0f;
-            bool contrib = false;
-            if (j < ray.last) {
-                const float4 a = sm.rec[r * 4 + 0];
-                const float4 b = sm.rec[r * 4 + 1];
-                const float4 c = sm.rec[r * 4 + 2];
-                const float4 e = sm.rec[r * 4 + 3];
-                ray_gradient(ray, a, b, c, e, log2_amin, p.alpha_max, gv, contrib);
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-                // warp reduce-scatter of the 16 values: lane l ends with the sum of value (l >> 1)
+                for (int k = 0; k < 16; ++k) gv[k] = 0.0f;
+                bool contrib = false;
+                if (j < ray.last) {
+                    const float4 a = sm.rec[r * 4 + 0];
+                    const float4 b = sm.rec[r * 4 + 1];
+                    const float4 c = sm.rec[r * 4 + 2];
+                    const float4 e = sm.rec[r * 4 + 3];
+                    ray_gradient(ray, a, b, c, e, log2_amin, p.alpha_max, gv, contrib);
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    // warp reduce-scatter of the 16 values: lane l ends with the sum of value (l >> 1)
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const bool up = lane & 16;
-                    const float send = up ? gv[k] : gv[k + 8];
-                    const float keep = up ? gv[k + 8] : gv[k];
-                    gv[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                }
+                    for (int k = 0; k < 8; ++k) {
+                        const bool up = lane & 16;
+                        const float send = up ? gv[k] : gv[k + 8];
+                        const float keep = up ? gv[k + 8] : gv[k];
+                        gv[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                    }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const bool up = lane & 8;
-                    const float send = up ? gv[k] : gv[k + 4];
-                    const float keep = up ? gv[k + 4] : gv[k];
-                    gv[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-                }
+                    for (int k = 0; k < 4; ++k) {
+                        const bool up = lane & 8;
+                        const float send = up ? gv[k] : gv[k + 4];
+                        const float keep = up ? gv[k + 4] : gv[k];
+                        gv[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                    }
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const bool up = lane & 4;
-                    const float send = up ? gv[k] : gv[k + 2];
-                    const float keep = up ? gv[k + 2] : gv[k];
-                    gv[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    for (int k = 0; k < 2; ++k) {
+                        const bool up = lane & 4;
+                        const float send = up ? gv[k] : gv[k + 2];
+                        const float keep = up ? gv[k + 2] : gv[k];
+                        gv[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    }
+                    {
+                        const bool up = lane & 2;
+                        const float send = up ? gv[0] : gv[1];
+                        const float keep = up ? gv[1] : gv[0];
+                        gv[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+                    }
+                    gv[0] += __shfl_xor_sync(0xffffffffu, gv[0], 1);
+                    if ((lane & 1) == 0) atomicAdd(&s_acc[r][lane >> 1], gv[0]);
                 }
-                {
-                    const bool up = lane & 2;
-                    const float send = up ? gv[0] : gv[1];
-                    const float keep = up ? gv[1] : gv[0];
-                    gv[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-                }
-                gv[0] += __shfl_xor_sync(0xffffffffu, gv[0], 1);
-                if ((lane & 1) == 0) atomicAdd(&s_acc[r][lane >> 1], gv[0]);
             }
         }
         __syncthreads();

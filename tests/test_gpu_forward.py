@@ -158,6 +158,28 @@ def test_render_sh_degrees_full_frame(geer, orc, deg):
     _check_pixels(orc, scene, cam, rgb.reshape(cam.height, cam.width, 3), wl.all_pixels(cam), f"deg{deg}")
 
 
+def test_render_state_counters(geer, orc):
+    """Per-ray counters of the forward: contributors applied equal the oracle's
+    (bar rays whose T_min or alpha_min decision is within rounding), contributors
+    <= last contributor index <= entries evaluated, every ray's last contributor
+    within its tile's walk record, and the totals of geer_render_counts."""
+    cam = TINY[3][1][0]
+    scene = _tiny_scene(77, 500, 1, spread=2.5)
+    r, g, rgb, T = _render(geer, scene, [cam])
+    ev, last, walk = r.ws.debug_render_state()
+    out = orc.render_pixels(scene, cam, wl.all_pixels(cam))
+    n_eval, n_app = ev[:, 0].astype(np.int64), ev[:, 1].astype(np.int64)
+    assert np.all(n_app <= last) and np.all(last <= n_eval), "counter order"
+    assert np.mean(n_app == out["ncontrib"]) >= 0.99, np.mean(n_app == out["ncontrib"])
+    # the tile's walk record ends at its last contributor
+    tx = (cam.width + 15) // 16
+    pix = wl.all_pixels(cam)
+    tiles = (pix[:, 1] // 16) * tx + pix[:, 0] // 16
+    assert np.all(last <= walk[tiles, 1])
+    ev_tot, app_tot, _ = r.ws.render_counts()
+    assert ev_tot == int(n_eval.sum()) and app_tot == int(n_app.sum())
+
+
 def test_render_workload1_full_frame(geer, orc):
     """4096 Gaussians, pinhole 128x128 60 deg: every pixel against the oracle."""
     scene = wl.config_scene(1)
