@@ -208,6 +208,45 @@ def test_empty_and_single_gaussian(geer, orc):
     _check_pixels(orc, one, cam, rgb.reshape(cam.height, cam.width, 3), wl.all_pixels(cam), "one")
 
 
+def test_degenerate_gaussians_are_culled(geer):
+    """Gaussians with a non-finite mean, scale or opacity, a zero or negative
+    scale, a zero quaternion or an opacity below alpha_min contribute nothing:
+    the image is bit-identical to the scene without them (the survivors keep
+    their relative (depth, index) order), their written gradients are zero and
+    no gradient is NaN."""
+    base = _tiny_scene(61, 300, 2, spread=2.5)
+    bad = _tiny_scene(62, 7, 2, spread=2.5)
+    nan, inf = np.float32(np.nan), np.float32(np.inf)
+    bad.mean[0, 1] = nan
+    bad.scale[1, 2] = inf
+    bad.scale[2, 0] = 0.0
+    bad.scale[3, 1] = -0.2
+    bad.quat[4] = 0.0
+    bad.opacity[5] = nan
+    bad.opacity[6] = 0.5 / 255.0  # below alpha_min
+    # interleave the degenerate Gaussians with the others
+    at = np.array([0, 40, 41, 150, 151, 299, 300])
+    keep = np.ones(base.n + bad.n, bool)
+    idx = at + np.arange(bad.n)
+    keep[idx] = False
+    def mix(a, b):
+        out = np.empty((a.shape[0] + b.shape[0],) + a.shape[1:], a.dtype)
+        out[keep], out[~keep] = a, b
+        return out
+    mixed = wl.Scene(mix(base.mean, bad.mean), mix(base.scale, bad.scale), mix(base.quat, bad.quat),
+                     mix(base.opacity, bad.opacity), mix(base.sh, bad.sh), 2)
+    cam = TINY[3][1][0]
+    _, _, rgb_base, T_base = _render(geer, base, [cam])
+    r, g, rgb_mixed, T_mixed = _render(geer, mixed, [cam])
+    assert np.array_equal(rgb_mixed, rgb_base) and np.array_equal(T_mixed, T_base)
+    w = torch.randn(cam.pixels, 3, device="cuda")
+    grads = r.backward(g, w)  # written, not accumulated
+    for k, v in grads.items():
+        v = v.cpu().numpy()
+        assert not np.isnan(v).any(), k
+        assert np.all(v[~keep] == 0.0), k
+
+
 def test_capacity_overflow_is_reported_and_recovered(geer):
     scene = _tiny_scene(5, 200, 0, zmin=1.0)
     cam = wl.Camera(wl.PINHOLE, 64, 64, math.radians(70))
