@@ -258,6 +258,28 @@ const char *geer_stage_name(int32_t stage);
 geer_status geer_remap_to_native(const float *beap_rgb, const geer_camera *cam, const float *fill_rgb,
                                  float *native_rgb, void *stream);
 
+/* Evaluation regions of the camera's native image (the paper's evaluation of
+ * renders reprojected to native fisheye images, appendix on central and
+ * peripheral regions): regions (device [h][w] u8, caller-owned, overwritten)
+ * gets 0 where the pixel's ray has BEAP angles |theta| <= w / (2f) and
+ * |phi| <= h / (2f) (central; f the native focal length of
+ * geer_remap_to_native), 1 for the other rays of the BEAP grid (peripheral) and
+ * 255 where the pixel has no ray in the grid. Asynchronous on `stream`. */
+geer_status geer_native_regions(const geer_camera *cam, uint8_t *regions, void *stream);
+
+/* Image metrics of pred against gt (device [height][width][3] f32, values in
+ * [0, 1]) per region: out (HOST [n_regions][3] f64) gets, for each region
+ * r < n_regions (1..8), the sum of squared errors over its pixels and the
+ * three channels, the sum over its pixels of the SSIM averaged over the
+ * channels, and its pixel count. regions: device [height][width] u8 region id
+ * per pixel (ids >= n_regions are left out) or NULL (every pixel in region 0).
+ * SSIM: 11 x 11 Gaussian window (sigma 1.5, normalised), zero padding,
+ * C1 = 0.01^2, C2 = 0.03^2. acc: device scratch of 3 * n_regions f64
+ * (caller-owned). PSNR of a region = 10 log10(3 count / sum of squared errors).
+ * Synchronises `stream`. */
+geer_status geer_image_metrics(const float *pred, const float *gt, int32_t width, int32_t height,
+                               const uint8_t *regions, int32_t n_regions, double *acc, double *out, void *stream);
+
 /* Render one small camera without allocating anything.
  *
  * For callers that cannot call cudaMalloc or any other allocator at render

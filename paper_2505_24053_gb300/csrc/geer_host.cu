@@ -821,12 +821,11 @@ geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t
     return GEER_OK;
 }
 
-geer_status geer_remap_to_native(const float *beap_rgb, const geer_camera *cam, const float *fill_rgb,
-                                 float *native_rgb, void *stream) {
-    if (!beap_rgb || !cam || !native_rgb || !camera_ok(*cam)) return GEER_ERR_ARG;
-    const double fy = derived_fov_y(*cam);
+// The native camera's vertical BEAP field of view, focal length and largest
+// invertible angle of its distortion (App. E), for the remap kernel.
+static void native_params(const geer_camera *cam, double &fy, double &focal, double &phi_max) {
+    fy = derived_fov_y(*cam);
     const double half = 0.5 * (double)cam->fov_x;
-    double focal, phi_max;
     if (cam->model == GEER_PINHOLE) {
         focal = 0.5 * cam->width / tan(half);
         phi_max = 0.0;
@@ -845,8 +844,35 @@ geer_status geer_remap_to_native(const float *beap_rgb, const geer_camera *cam, 
             prev = val;
         }
     }
-    return cuda_status(
-        launch_remap_to_native(beap_rgb, cam, fy, focal, phi_max, fill_rgb, native_rgb, static_cast<cudaStream_t>(stream)));
+}
+
+geer_status geer_remap_to_native(const float *beap_rgb, const geer_camera *cam, const float *fill_rgb,
+                                 float *native_rgb, void *stream) {
+    if (!beap_rgb || !cam || !native_rgb || !camera_ok(*cam)) return GEER_ERR_ARG;
+    double fy, focal, phi_max;
+    native_params(cam, fy, focal, phi_max);
+    return cuda_status(launch_remap_to_native(beap_rgb, cam, fy, focal, phi_max, fill_rgb, native_rgb, nullptr,
+                                              static_cast<cudaStream_t>(stream)));
+}
+
+geer_status geer_native_regions(const geer_camera *cam, uint8_t *regions, void *stream) {
+    if (!cam || !regions || !camera_ok(*cam)) return GEER_ERR_ARG;
+    double fy, focal, phi_max;
+    native_params(cam, fy, focal, phi_max);
+    return cuda_status(launch_remap_to_native(nullptr, cam, fy, focal, phi_max, nullptr, nullptr, regions,
+                                              static_cast<cudaStream_t>(stream)));
+}
+
+geer_status geer_image_metrics(const float *pred, const float *gt, int32_t width, int32_t height,
+                               const uint8_t *regions, int32_t n_regions, double *acc, double *out, void *stream) {
+    if (!pred || !gt || !acc || !out || width < 0 || height < 0 || n_regions < 1 || n_regions > 8)
+        return GEER_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (launch_image_metrics(pred, gt, width, height, regions, n_regions, acc, s) != cudaSuccess ||
+        cudaMemcpyAsync(out, acc, sizeof(double) * 3 * n_regions, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    return GEER_OK;
 }
 
 static const char *kStageNames[kStageCount] = {"preprocess", "bin_front", "depth_sort", "count_pairs", "duplicate",

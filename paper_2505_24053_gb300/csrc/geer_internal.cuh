@@ -11,6 +11,7 @@ namespace geer {
 constexpr int kTile = 16;                   // BEAP tile edge in rays (a camera sub-frustum)
 constexpr int kTilePix = kTile * kTile;
 constexpr int kTileWarps = kTilePix / 32;    // warps of a tile's rays (one byte each in the hit record)
+constexpr uint8_t kRegionCentral = 0, kRegionPeripheral = 1, kRegionNone = 255;  // native evaluation regions
 constexpr int64_t kHitEntries = 2048;      // tile-list entries per tile whose hit bytes are recorded
 constexpr int kPrepThreads = 256;           // preprocess / duplicate block size
 constexpr int kSortThreads = 256;           // onesweep block size (8 warps)
@@ -250,7 +251,9 @@ cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians
 cudaError_t launch_l1_grad(const float *pred, const float *target, int64_t m, float *grad, float *loss, int num_sms,
                            cudaStream_t s);
 cudaError_t launch_remap_to_native(const float *beap, const geer_camera *cam, double fov_y, double focal,
-                                   double phi_max, const float *fill, float *out, cudaStream_t s);
+                                   double phi_max, const float *fill, float *out, uint8_t *regions, cudaStream_t s);
+cudaError_t launch_image_metrics(const float *pred, const float *gt, int width, int height, const uint8_t *regions,
+                                 int n_regions, double *acc, cudaStream_t s);
 int sort_blocks_per_sm();
 
 inline int64_t prep_blocks(int64_t n) { return (n + kPrepThreads - 1) / kPrepThreads; }

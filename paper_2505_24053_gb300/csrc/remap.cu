@@ -14,6 +14,10 @@
 // u = theta / FoV_x w + w/2 - 1/2 (likewise v), and its colour the bilinear
 // interpolation of the BEAP image there. Rays outside the BEAP grid (beyond half
 // a pixel) or where the distortion cannot be inverted get the fill colour.
+//
+// The same pass can label each native pixel with its evaluation region: central
+// when its ray's BEAP angles satisfy |theta| <= w / (2f), |phi| <= h / (2f) (f the
+// native focal length), peripheral otherwise, none without a ray in the grid.
 #include "geer_internal.cuh"
 
 namespace geer {
@@ -24,6 +28,7 @@ struct RemapCam {
     float f, fov_x, fov_y, phi_max;
     float k[4];
     float fill[3];
+    float cen_th, cen_ph;  // central-region half angles w / (2f), h / (2f)
 };
 
 __device__ __forceinline__ float kb_poly(const float k[4], float p, float &dp) {
@@ -35,8 +40,9 @@ __device__ __forceinline__ float kb_poly(const float k[4], float p, float &dp) {
     return p * s;
 }
 
+// beap / out NULL: regions only; regions NULL: image only.
 __global__ void __launch_bounds__(256) k_remap_to_native(const float *__restrict__ beap, RemapCam c,
-                                                         float *__restrict__ out) {
+                                                         float *__restrict__ out, uint8_t *__restrict__ regions) {
     grid_dep_sync();
     const int64_t n = (int64_t)c.width * c.height;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,12 +70,13 @@ __global__ void __launch_bounds__(256) k_remap_to_native(const float *__restrict
         dz = cp;
     }
     float r = c.fill[0], g = c.fill[1], b = c.fill[2];
+    uint8_t region = kRegionNone;
     if (ok && dz != 0.0f) {
         const float th = atan2f(dx, dz);
         const float ph = atanf(dy / dz);
         const float ub = th / c.fov_x * (float)c.width + 0.5f * (float)c.width - 0.5f;
         const float vb = ph / c.fov_y * (float)c.height + 0.5f * (float)c.height - 0.5f;
-        if (ub >= -0.5f && ub <= (float)c.width - 0.5f && vb >= -0.5f && vb <= (float)c.height - 0.5f) {
+        if (ub >= -0.5f && ub <= (float)c.width - 0.5f && vb >= -0.5f && vb <= (float)c.height - 0.5f && beap) {
             const float uc = fminf(fmaxf(ub, 0.0f), (float)(c.width - 1));
             const float vc = fminf(fmaxf(vb, 0.0f), (float)(c.height - 1));
             const int x0 = min((int)uc, c.width - 2 < 0 ? 0 : c.width - 2);
@@ -89,16 +96,21 @@ __global__ void __launch_bounds__(256) k_remap_to_native(const float *__restrict
             }
             r = o[0]; g = o[1]; b = o[2];
         }
+        if (ub >= -0.5f && ub <= (float)c.width - 0.5f && vb >= -0.5f && vb <= (float)c.height - 0.5f)
+            region = (fabsf(th) <= c.cen_th && fabsf(ph) <= c.cen_ph) ? kRegionCentral : kRegionPeripheral;
     }
-    out[3 * idx + 0] = r;
-    out[3 * idx + 1] = g;
-    out[3 * idx + 2] = b;
+    if (out) {
+        out[3 * idx + 0] = r;
+        out[3 * idx + 1] = g;
+        out[3 * idx + 2] = b;
+    }
+    if (regions) regions[idx] = region;
 }
 
 }  // namespace
 
 cudaError_t launch_remap_to_native(const float *beap, const geer_camera *cam, double fov_y, double focal,
-                                   double phi_max, const float *fill, float *out, cudaStream_t s) {
+                                   double phi_max, const float *fill, float *out, uint8_t *regions, cudaStream_t s) {
     RemapCam c;
     c.model = cam->model;
     c.width = cam->width;
@@ -110,9 +122,11 @@ cudaError_t launch_remap_to_native(const float *beap, const geer_camera *cam, do
     c.phi_max = (float)phi_max;
     for (int i = 0; i < 4; ++i) c.k[i] = cam->model == GEER_KANNALA_BRANDT ? cam->k[i] : 0.0f;
     for (int i = 0; i < 3; ++i) c.fill[i] = fill ? fill[i] : 0.0f;
+    c.cen_th = (float)(0.5 * cam->width / focal);
+    c.cen_ph = (float)(0.5 * cam->height / focal);
     const int64_t n = (int64_t)cam->width * cam->height;
     if (n == 0) return cudaSuccess;
-    launch_k(k_remap_to_native, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, beap, c, out);
+    launch_k(k_remap_to_native, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, beap, c, out, regions);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
            "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc", "geer_set_camera_slots",
            "geer_enable_timing", "geer_stage_times", "geer_stage_name", "geer_remap_to_native",
+           "geer_native_regions", "geer_image_metrics",
            "geer_pair_counts", "geer_debug_render_state"]
 
 _lib = None
@@ -88,6 +89,8 @@ def lib(build_if_missing: bool = True):
         "geer_enable_timing": [P, I32],
         "geer_stage_times": [P, P, I32, P, P],
         "geer_remap_to_native": [P, P, P, P, P],
+        "geer_native_regions": [P, P, P],
+        "geer_image_metrics": [P, P, I32, I32, P, I32, P, P, P],
         "geer_pair_counts": [P, P, P, P, P, P],
         "geer_debug_render_state": [P, P, P, P, P],
         "geer_l1_loss_grad": [P, P, I64, P, P, P],
@@ -360,6 +363,35 @@ def remap_to_native(beap_img: torch.Tensor, cam, fill=(0.0, 0.0, 0.0), out: torc
     _check(lib().geer_remap_to_native(C.c_void_p(beap_img.data_ptr()), C.byref(cc), f, C.c_void_p(out.data_ptr()),
                                       _stream(stream)), "geer_remap_to_native")
     return out
+
+
+def native_regions(cam, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """[h, w] uint8 evaluation region of each native pixel: 0 central, 1 peripheral,
+    255 without a ray in the BEAP grid."""
+    if out is None:
+        out = torch.empty((cam.height, cam.width), dtype=torch.uint8, device="cuda")
+    cc = camera_c(cam)
+    _check(lib().geer_native_regions(C.byref(cc), C.c_void_p(out.data_ptr()), _stream(stream)), "geer_native_regions")
+    return out
+
+
+def image_metrics(pred: torch.Tensor, gt: torch.Tensor, regions: torch.Tensor | None = None, n_regions: int = 1,
+                  stream=None) -> list[dict]:
+    """Per region: PSNR, mean SSIM and pixel count of pred against gt ([h, w, 3] f32)."""
+    h, w = int(pred.shape[0]), int(pred.shape[1])
+    acc = torch.empty(3 * n_regions, dtype=torch.float64, device=pred.device)
+    out = (C.c_double * (3 * n_regions))()
+    reg = C.c_void_p(regions.data_ptr()) if regions is not None else None
+    _check(lib().geer_image_metrics(C.c_void_p(pred.data_ptr()), C.c_void_p(gt.data_ptr()), w, h, reg, n_regions,
+                                    C.c_void_p(acc.data_ptr()), out, _stream(stream)), "geer_image_metrics")
+    res = []
+    for r in range(n_regions):
+        sse, ssim, cnt = out[3 * r], out[3 * r + 1], out[3 * r + 2]
+        mse = sse / (3.0 * cnt) if cnt > 0 else float("nan")
+        res.append({"sse": sse, "ssim_sum": ssim, "count": int(cnt),
+                    "psnr": (10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")) if cnt > 0 else float("nan"),
+                    "ssim": ssim / cnt if cnt > 0 else float("nan")})
+    return res
 
 
 class Renderer:
