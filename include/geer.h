@@ -258,6 +258,41 @@ const char *geer_stage_name(int32_t stage);
 geer_status geer_remap_to_native(const float *beap_rgb, const geer_camera *cam, const float *fill_rgb,
                                  float *native_rgb, void *stream);
 
+/* The supervision of a BEAP render from a native camera image (BEAP ray
+ * sampling with ground-truth interpolation, Algorithm 2): each BEAP pixel's ray
+ * is projected into the native image (the model and intrinsics of
+ * geer_remap_to_native) and the native image (native_rgb: device [h][w][3] f32)
+ * is interpolated bilinearly there into beap_rgb (device [h][w][3] f32,
+ * overwritten). valid (device [h][w] u8, may be NULL) gets 1, or 0 (and black)
+ * where the ray's point is not within half a pixel of the native image or has
+ * no projection. Asynchronous on `stream`. */
+geer_status geer_native_to_beap(const float *native_rgb, const geer_camera *cam, float *beap_rgb, uint8_t *valid,
+                                void *stream);
+
+/* Adam (Kingma and Ba) over the 3DGS parameterisation: learning rates per
+ * parameter group (SH degree 0 and the higher degrees apart), beta1, beta2, eps,
+ * and the 1-based step count of the bias correction. */
+typedef struct {
+    float lr_mean, lr_scale, lr_quat, lr_opacity, lr_sh_dc, lr_sh_rest;
+    float beta1, beta2, eps;
+    int32_t step;
+} geer_adam;
+
+/* One Adam step of n Gaussians (the optimiser of Algorithm 2 as 3DGS runs it).
+ * Raw parameters (device, caller-owned, updated in place): mean [n][3],
+ * log_scale [n][3], quat [n][4], logit_opacity [n], sh [n][(deg+1)^2][3].
+ * d_*: the gradients geer_render_bwd produced, with respect to the activated
+ * parameters (scale = exp(log_scale), opacity = sigmoid(logit)); the chain rule
+ * is applied here. m, v: device [n * (11 + 3 (deg+1)^2)] f32 moments each,
+ * zero before the first step, laid out as [mean | log_scale | quat | logit | sh]
+ * blocks in those shapes. scale [n][3] and opacity [n] (device, may be NULL)
+ * receive the activated values of the updated parameters. Asynchronous on
+ * `stream`. */
+geer_status geer_adam_step(const geer_adam *hp, int64_t n, int32_t sh_degree, float *mean, float *log_scale,
+                           float *quat, float *logit_opacity, float *sh, const float *d_mean, const float *d_scale,
+                           const float *d_quat, const float *d_opacity, const float *d_sh, float *m, float *v,
+                           float *scale, float *opacity, void *stream);
+
 /* Evaluation regions of the camera's native image (the paper's evaluation of
  * renders reprojected to native fisheye images, appendix on central and
  * peripheral regions): regions (device [h][w] u8, caller-owned, overwritten)

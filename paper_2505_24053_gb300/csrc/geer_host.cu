@@ -855,6 +855,30 @@ geer_status geer_remap_to_native(const float *beap_rgb, const geer_camera *cam, 
                                               static_cast<cudaStream_t>(stream)));
 }
 
+geer_status geer_native_to_beap(const float *native_rgb, const geer_camera *cam, float *beap_rgb, uint8_t *valid,
+                                void *stream) {
+    if (!native_rgb || !cam || !beap_rgb || !camera_ok(*cam)) return GEER_ERR_ARG;
+    double fy, focal, phi_max;
+    native_params(cam, fy, focal, phi_max);
+    return cuda_status(launch_native_to_beap(native_rgb, cam, fy, focal, phi_max, beap_rgb, valid,
+                                             static_cast<cudaStream_t>(stream)));
+}
+
+geer_status geer_adam_step(const geer_adam *hp, int64_t n, int32_t sh_degree, float *mean, float *log_scale,
+                           float *quat, float *logit_opacity, float *sh, const float *d_mean, const float *d_scale,
+                           const float *d_quat, const float *d_opacity, const float *d_sh, float *m, float *v,
+                           float *scale, float *opacity, void *stream) {
+    if (!hp || n < 0 || sh_degree < 0 || sh_degree > 3 || hp->step < 1 || !(hp->beta1 >= 0.0f && hp->beta1 < 1.0f) ||
+        !(hp->beta2 >= 0.0f && hp->beta2 < 1.0f) || !(hp->eps >= 0.0f))
+        return GEER_ERR_ARG;
+    if (n > 0 && (!mean || !log_scale || !quat || !logit_opacity || !sh || !d_mean || !d_scale || !d_quat ||
+                  !d_opacity || !d_sh || !m || !v))
+        return GEER_ERR_ARG;
+    return cuda_status(launch_adam_gaussians(hp, n, sh_degree, mean, log_scale, quat, logit_opacity, sh, d_mean,
+                                             d_scale, d_quat, d_opacity, d_sh, m, v, scale, opacity,
+                                             static_cast<cudaStream_t>(stream)));
+}
+
 geer_status geer_native_regions(const geer_camera *cam, uint8_t *regions, void *stream) {
     if (!cam || !regions || !camera_ok(*cam)) return GEER_ERR_ARG;
     double fy, focal, phi_max;

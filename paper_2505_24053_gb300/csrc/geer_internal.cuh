@@ -252,6 +252,13 @@ cudaError_t launch_l1_grad(const float *pred, const float *target, int64_t m, fl
                            cudaStream_t s);
 cudaError_t launch_remap_to_native(const float *beap, const geer_camera *cam, double fov_y, double focal,
                                    double phi_max, const float *fill, float *out, uint8_t *regions, cudaStream_t s);
+cudaError_t launch_native_to_beap(const float *native, const geer_camera *cam, double fov_y, double focal,
+                                  double phi_max, float *beap, uint8_t *valid, cudaStream_t s);
+cudaError_t launch_adam_gaussians(const geer_adam *hp, int64_t n, int32_t sh_degree, float *mean, float *log_scale,
+                                  float *quat, float *logit_opacity, float *sh, const float *d_mean,
+                                  const float *d_scale, const float *d_quat, const float *d_opacity,
+                                  const float *d_sh, float *m, float *v, float *scale, float *opacity,
+                                  cudaStream_t s);
 cudaError_t launch_image_metrics(const float *pred, const float *gt, int width, int height, const uint8_t *regions,
                                  int n_regions, double *acc, cudaStream_t s);
 int sort_blocks_per_sm();

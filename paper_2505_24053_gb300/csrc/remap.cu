@@ -18,6 +18,8 @@
 // The same pass can label each native pixel with its evaluation region: central
 // when its ray's BEAP angles satisfy |theta| <= w / (2f), |phi| <= h / (2f) (f the
 // native focal length), peripheral otherwise, none without a ray in the grid.
+#include <cstring>
+
 #include "geer_internal.cuh"
 
 namespace geer {
@@ -107,7 +109,88 @@ __global__ void __launch_bounds__(256) k_remap_to_native(const float *__restrict
     if (regions) regions[idx] = region;
 }
 
+// The supervision of a BEAP render from a native image (BEAP ray sampling with
+// ground-truth interpolation): each BEAP pixel's ray (Sec. 3.3) projected into
+// the native image (App. E with the intrinsics above: pinhole f (x, y) / z;
+// fisheye f phi_d(p) (x, y) / sqrt(x^2 + y^2) with the polar angle
+// p = atan2(sqrt(x^2 + y^2), z) on the invertible branch) and the native image
+// interpolated bilinearly at pixel-centre coordinates; valid 0 where the point
+// is not within half a pixel of the image or the ray has no projection.
+__global__ void __launch_bounds__(256) k_native_to_beap(const float *__restrict__ native, RemapCam c,
+                                                        float *__restrict__ beap, uint8_t *__restrict__ valid) {
+    grid_dep_sync();
+    const int64_t n = (int64_t)c.width * c.height;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const int i = (int)(idx % c.width), j = (int)(idx / c.width);
+    const float th = (((float)i + 0.5f) / (float)c.width - 0.5f) * c.fov_x;
+    const float ph = (((float)j + 0.5f) / (float)c.height - 0.5f) * c.fov_y;
+    float st, ct, sp, cp;
+    sincosf(th, &st, &ct);
+    sincosf(ph, &sp, &cp);
+    const float dx = st * cp, dy = ct * sp, dz = ct * cp;
+    bool ok;
+    float x = 0.0f, y = 0.0f;
+    if (c.model == GEER_PINHOLE) {
+        ok = dz > 0.0f;
+        if (ok) { x = c.f * dx / dz; y = c.f * dy / dz; }
+    } else {
+        const float rho = sqrtf(dx * dx + dy * dy);
+        const float p = atan2f(rho, dz);
+        ok = p <= c.phi_max;
+        if (ok && rho > 0.0f) {
+            float dp;
+            const float s = c.f * kb_poly(c.k, p, dp) / rho;
+            x = s * dx;
+            y = s * dy;
+        }
+    }
+    const float u = x + 0.5f * (float)c.width - 0.5f, v = y + 0.5f * (float)c.height - 0.5f;
+    ok = ok && u >= -0.5f && u <= (float)c.width - 0.5f && v >= -0.5f && v <= (float)c.height - 0.5f;
+    float o[3] = {0.0f, 0.0f, 0.0f};
+    if (ok) {
+        const float uc = fminf(fmaxf(u, 0.0f), (float)(c.width - 1));
+        const float vc = fminf(fmaxf(v, 0.0f), (float)(c.height - 1));
+        const int x0 = min((int)uc, c.width - 2 < 0 ? 0 : c.width - 2);
+        const int y0 = min((int)vc, c.height - 2 < 0 ? 0 : c.height - 2);
+        const int x1 = min(x0 + 1, c.width - 1), y1 = min(y0 + 1, c.height - 1);
+        const float ax = uc - (float)x0, ay = vc - (float)y0;
+        const float *p00 = native + 3 * ((int64_t)y0 * c.width + x0);
+        const float *p01 = native + 3 * ((int64_t)y0 * c.width + x1);
+        const float *p10 = native + 3 * ((int64_t)y1 * c.width + x0);
+        const float *p11 = native + 3 * ((int64_t)y1 * c.width + x1);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float top = p00[ch] + ax * (p01[ch] - p00[ch]);
+            const float bot = p10[ch] + ax * (p11[ch] - p10[ch]);
+            o[ch] = top + ay * (bot - top);
+        }
+    }
+    beap[3 * idx + 0] = o[0];
+    beap[3 * idx + 1] = o[1];
+    beap[3 * idx + 2] = o[2];
+    if (valid) valid[idx] = ok ? 1 : 0;
+}
+
 }  // namespace
+
+cudaError_t launch_native_to_beap(const float *native, const geer_camera *cam, double fov_y, double focal,
+                                  double phi_max, float *beap, uint8_t *valid, cudaStream_t s) {
+    RemapCam c;
+    memset(&c, 0, sizeof(c));
+    c.model = cam->model;
+    c.width = cam->width;
+    c.height = cam->height;
+    c.f = (float)focal;
+    c.fov_x = cam->fov_x;
+    c.fov_y = (float)fov_y;
+    c.phi_max = (float)phi_max;
+    for (int i = 0; i < 4; ++i) c.k[i] = cam->model == GEER_KANNALA_BRANDT ? cam->k[i] : 0.0f;
+    const int64_t n = (int64_t)cam->width * cam->height;
+    if (n == 0) return cudaSuccess;
+    launch_k(k_native_to_beap, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, native, c, beap, valid);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_remap_to_native(const float *beap, const geer_camera *cam, double fov_y, double focal,
                                    double phi_max, const float *fill, float *out, uint8_t *regions, cudaStream_t s) {

@@ -46,7 +46,7 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_render_bwd", "geer_last_device_status", "geer_debug_preprocess", "geer_debug_pairs",
            "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc", "geer_set_camera_slots",
            "geer_enable_timing", "geer_stage_times", "geer_stage_name", "geer_remap_to_native",
-           "geer_native_regions", "geer_image_metrics",
+           "geer_native_regions", "geer_image_metrics", "geer_native_to_beap", "geer_adam_step",
            "geer_pair_counts", "geer_debug_render_state"]
 
 _lib = None
@@ -90,6 +90,8 @@ def lib(build_if_missing: bool = True):
         "geer_stage_times": [P, P, I32, P, P],
         "geer_remap_to_native": [P, P, P, P, P],
         "geer_native_regions": [P, P, P],
+        "geer_native_to_beap": [P, P, P, P, P],
+        "geer_adam_step": [P, I64, I32, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P],
         "geer_image_metrics": [P, P, I32, I32, P, I32, P, P, P],
         "geer_pair_counts": [P, P, P, P, P, P],
         "geer_debug_render_state": [P, P, P, P, P],
@@ -392,6 +394,66 @@ def image_metrics(pred: torch.Tensor, gt: torch.Tensor, regions: torch.Tensor | 
                     "psnr": (10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")) if cnt > 0 else float("nan"),
                     "ssim": ssim / cnt if cnt > 0 else float("nan")})
     return res
+
+
+def native_to_beap(native_img: torch.Tensor, cam, out: torch.Tensor | None = None,
+                   valid: torch.Tensor | None = None, stream=None):
+    """(BEAP supervision [h, w, 3], valid [h, w] uint8) of a native camera image [h, w, 3]."""
+    if out is None:
+        out = torch.empty_like(native_img)
+    if valid is None:
+        valid = torch.empty((cam.height, cam.width), dtype=torch.uint8, device=native_img.device)
+    cc = camera_c(cam)
+    _check(lib().geer_native_to_beap(C.c_void_p(native_img.data_ptr()), C.byref(cc), C.c_void_p(out.data_ptr()),
+                                     C.c_void_p(valid.data_ptr()), _stream(stream)), "geer_native_to_beap")
+    return out, valid
+
+
+class AdamC(C.Structure):
+    _fields_ = [("lr_mean", C.c_float), ("lr_scale", C.c_float), ("lr_quat", C.c_float), ("lr_opacity", C.c_float),
+                ("lr_sh_dc", C.c_float), ("lr_sh_rest", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("step", C.c_int32)]
+
+
+# 3DGS default rates (the mean's is scaled by the scene extent by the caller)
+ADAM_DEFAULTS = dict(lr_mean=1.6e-4, lr_scale=5e-3, lr_quat=1e-3, lr_opacity=0.05, lr_sh_dc=2.5e-3,
+                     lr_sh_rest=2.5e-3 / 20, beta1=0.9, beta2=0.999, eps=1e-15)
+
+
+class Adam:
+    """Adam over raw Gaussian parameters (mean, log_scale, quat, logit_opacity, sh),
+    through geer_adam_step. `gaussians` shares the raw mean / quat / SH tensors and
+    holds the activated scale and opacity the step writes: render it directly."""
+
+    def __init__(self, mean, log_scale, quat, logit_opacity, sh, sh_degree: int, **hp):
+        def dev(x):
+            t = torch.as_tensor(x, dtype=torch.float32)
+            return (t.cuda() if t.device.type != "cuda" else t).contiguous().clone()
+
+        self.raw = {"mean": dev(mean), "log_scale": dev(log_scale), "quat": dev(quat),
+                    "logit_opacity": dev(logit_opacity), "sh": dev(sh)}
+        self.sh_degree = int(sh_degree)
+        self.n = int(self.raw["mean"].shape[0])
+        self.hp = dict(ADAM_DEFAULTS, **hp)
+        per = 11 + 3 * (self.sh_degree + 1) ** 2
+        self.m = torch.zeros(self.n * per, dtype=torch.float32, device="cuda")
+        self.v = torch.zeros_like(self.m)
+        self.t = 0
+        self.gaussians = Gaussians(self.raw["mean"], torch.exp(self.raw["log_scale"]), self.raw["quat"],
+                                   torch.sigmoid(self.raw["logit_opacity"]), self.raw["sh"], self.sh_degree)
+
+    def step(self, grads: dict, stream=None):
+        """One step from the renderer's gradients (dict of mean, scale, quat, opacity, sh)."""
+        self.t += 1
+        hp = AdamC(**{k: self.hp[k] for k in ("lr_mean", "lr_scale", "lr_quat", "lr_opacity", "lr_sh_dc",
+                                              "lr_sh_rest", "beta1", "beta2", "eps")}, step=self.t)
+        r, g = self.raw, self.gaussians
+        ptr = lambda t: C.c_void_p(t.data_ptr())
+        _check(lib().geer_adam_step(C.byref(hp), self.n, self.sh_degree, ptr(r["mean"]), ptr(r["log_scale"]),
+                                    ptr(r["quat"]), ptr(r["logit_opacity"]), ptr(r["sh"]), ptr(grads["mean"]),
+                                    ptr(grads["scale"]), ptr(grads["quat"]), ptr(grads["opacity"]), ptr(grads["sh"]),
+                                    ptr(self.m), ptr(self.v), ptr(g.scale), ptr(g.opacity), _stream(stream)),
+               "geer_adam_step")
 
 
 class Renderer:
