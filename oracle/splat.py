@@ -1,0 +1,173 @@
+"""Splatting-style association bounds (the association ablation), FP64 numpy.
+
+TEST INFRASTRUCTURE: imported only by the tests and the benchmark's CPU leg;
+the product path never imports it.
+
+The paper sets its PBF association against the projection-based bounds of EWA
+splatting and of the unscented transform (UT), either as the 3-sigma square of
+3DGS or with SnugBox, in the same pipeline (Sec. 4, association runtime table;
+App. A, EWA preliminaries). On the BEAP grid the screen coordinates of a point
+t = (x, y, z) in front of the camera are its BEAP angles
+  theta = atan2(x, z), phi = atan2(y, z)
+(a BEAP ray d = (sin theta cos phi, cos theta sin phi, cos theta cos phi) has
+exactly these for |theta|, |phi| < 90 degrees, Sec. 3.3).
+
+- EWA: the affine approximation of that map at the camera-frame mean mu_c (its
+  Jacobian J, rows d theta / dt = (z, 0, -x) / (x^2 + z^2) and
+  d phi / dt = (0, z, -y) / (y^2 + z^2)) carries Sigma_c = M diag(s^2) M^T
+  (M = R_cw R) to Sigma_2 = J Sigma_c J^T about (theta, phi)(mu_c).
+- UT: the 2n + 1 = 7 sigma points mu_c and mu_c +- sqrt(3) s_k M[:, k]
+  (n = 3, alpha = 1, beta = 2, kappa = 0: lambda = 0, mean weights 0 and 1/6,
+  covariance weights 2 and 1/6) are mapped exactly; each point's angles are
+  taken in the branch within pi of the mean's angles; Sigma_2 and the centre
+  are their weighted covariance and mean.
+- The box: a square of half-side 3 sqrt(largest eigenvalue of Sigma_2), or with
+  SnugBox the bounding box of the ellipse where the density reaches alpha_min,
+  half-sides sqrt(2 ln(sigma / alpha_min) Sigma_2[i, i]).
+- Culling: mean with z <= 0.2 (the splatting near plane), sigma < alpha_min.
+
+Tiles: a column tile spans the angles [theta(i0), theta(i1)] of its first and
+last pixel, theta(i) = ((i + 1/2) / w - 1/2) fov_x. X0 holds the columns whose
+span meets the theta box on the circle, X1 those whose span meets the box
+turned by pi (a ray with cos(phi) < 0 has atan2(x, z) = theta + pi); Y0 and Y1
+likewise for rows. The association is the same flagged product as PBF's: tile
+(cx, cy) is taken when (its row has a ray with cos(phi) >= 0 and cx in X0, or
+one with cos(phi) < 0 and cx in X1) and (the same with columns and Y0, Y1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import oracle as orc
+
+PBF, EWA, UT = 0, 1, 2
+NEAR = 0.2
+TWO_PI = 2.0 * math.pi
+
+
+def _rot(q):
+    q = np.asarray(q, np.float64)
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def _wrap(a):
+    """a mod 2 pi in (-pi, pi]."""
+    r = math.fmod(a + math.pi, TWO_PI)
+    if r <= 0.0:
+        r += TWO_PI
+    return r - math.pi
+
+
+def camera_frame(cam, mu):
+    Rc = np.asarray(cam.R_cw, np.float64).reshape(3, 3)
+    return Rc @ np.asarray(mu, np.float64) + np.asarray(cam.t_cw, np.float64), Rc
+
+
+def screen_cov(cam, mu, scale, quat, mode: int):
+    """(centre (theta, phi), Sigma_2 [2, 2]) of one Gaussian, or None below the near plane."""
+    mu_c, Rc = camera_frame(cam, mu)
+    if not mu_c[2] > NEAR:
+        return None
+    M = Rc @ _rot(quat)
+    s = np.asarray(scale, np.float64)
+    x, y, z = mu_c
+    c0 = np.array([math.atan2(x, z), math.atan2(y, z)])
+    if mode == EWA:
+        J = np.array([[z / (x * x + z * z), 0.0, -x / (x * x + z * z)],
+                      [0.0, z / (y * y + z * z), -y / (y * y + z * z)]])
+        return c0, J @ (M @ np.diag(s * s) @ M.T) @ J.T
+    if mode != UT:
+        raise ValueError(mode)
+    pts = [mu_c] + [mu_c + sg * math.sqrt(3.0) * s[k] * M[:, k] for k in range(3) for sg in (1.0, -1.0)]
+    p = np.array([[c0[0] + _wrap(math.atan2(t[0], t[2]) - c0[0]),
+                   c0[1] + _wrap(math.atan2(t[1], t[2]) - c0[1])] for t in pts])
+    wm = np.array([0.0] + [1.0 / 6.0] * 6)
+    wc = np.array([2.0] + [1.0 / 6.0] * 6)
+    centre = wm @ p
+    d = p - centre
+    return centre, np.einsum("i,ij,ik->jk", wc, d, d)
+
+
+def splat_box(cam, mu, scale, quat, sigma, mode: int, snug: bool, alpha_min: float = 1.0 / 255.0):
+    """(theta_lo, theta_hi, phi_lo, phi_hi) of one Gaussian, or None when culled."""
+    if not sigma >= alpha_min:
+        return None
+    r = screen_cov(cam, mu, scale, quat, mode)
+    if r is None:
+        return None
+    centre, S2 = r
+    if snug:
+        e = np.sqrt(2.0 * math.log(sigma / alpha_min) * np.maximum(np.diag(S2), 0.0))
+    else:
+        e = np.full(2, 3.0 * math.sqrt(max(np.linalg.eigvalsh(S2).max(), 0.0)))
+    return centre[0] - e[0], centre[0] + e[0], centre[1] - e[1], centre[1] + e[1]
+
+
+def beap_angle(i: int, n: int, fov: float) -> float:
+    return ((i + 0.5) / n - 0.5) * fov
+
+
+def meets_on_circle(a: float, b: float, lo: float, hi: float) -> bool:
+    """[a, b] (width < 2 pi) meets [lo, hi] taken modulo 2 pi."""
+    if hi - lo >= TWO_PI:
+        return True
+    return any(b >= lo + TWO_PI * k and a <= hi + TWO_PI * k for k in range(-3, 4))
+
+
+def axis_sets(lo: float, hi: float, n_pix: int, fov: float):
+    """(direct, turned) membership [tiles] of one axis for the angle box [lo, hi]."""
+    tiles = (n_pix + 15) // 16
+    direct = np.zeros(tiles, bool)
+    turned = np.zeros(tiles, bool)
+    for c in range(tiles):
+        a, b = beap_angle(16 * c, n_pix, fov), beap_angle(min(16 * c + 15, n_pix - 1), n_pix, fov)
+        direct[c] = meets_on_circle(a, b, lo, hi)
+        turned[c] = meets_on_circle(a, b, lo + math.pi, hi + math.pi)
+    return direct, turned
+
+
+def cos_flags(n_pix: int, fov: float):
+    """(has0, has1) per tile: some ray with cos >= 0 / with cos <= 0 (1e-12 slack)."""
+    tiles = (n_pix + 15) // 16
+    has0 = np.zeros(tiles, bool)
+    has1 = np.zeros(tiles, bool)
+    for c in range(tiles):
+        for i in range(16 * c, min(16 * c + 16, n_pix)):
+            cs = math.cos(beap_angle(i, n_pix, fov))
+            has0[c] |= cs > -1e-12
+            has1[c] |= cs < 1e-12
+    return has0, has1
+
+
+def box_mask(cam, box, grow: float = 0.0) -> np.ndarray:
+    """Association mask [tiles_y, tiles_x] of one box, its sides moved out by grow
+    (in by -grow)."""
+    ty, tx = (cam.height + 15) // 16, (cam.width + 15) // 16
+    if box is None:
+        return np.zeros((ty, tx), bool)
+    fy = orc.fov_y(cam)
+    t0, t1, p0, p1 = box[0] - grow, box[1] + grow, box[2] - grow, box[3] + grow
+    if t1 < t0 or p1 < p0:
+        return np.zeros((ty, tx), bool)
+    x0, x1 = axis_sets(t0, t1, cam.width, cam.fov_x)
+    y0, y1 = axis_sets(p0, p1, cam.height, fy)
+    c_has0, c_has1 = cos_flags(cam.width, cam.fov_x)
+    r_has0, r_has1 = cos_flags(cam.height, fy)
+    cols_ok = (r_has0[:, None] & x0[None, :]) | (r_has1[:, None] & x1[None, :])
+    rows_ok = (c_has0[None, :] & y0[:, None]) | (c_has1[None, :] & y1[:, None])
+    return cols_ok & rows_ok
+
+
+def scene_boxes(cam, scene, mode: int, snug: bool, alpha_min: float = 1.0 / 255.0):
+    return [splat_box(cam, scene.mean[g], scene.scale[g], scene.quat[g], float(scene.opacity[g]), mode, snug,
+                      alpha_min) for g in range(scene.n)]
+
+
+def scene_masks(cam, boxes, grow: float = 0.0) -> np.ndarray:
+    """[n, tiles_y, tiles_x] association masks of the boxes."""
+    return np.stack([box_mask(cam, b, grow) for b in boxes]) if boxes else np.zeros((0, 0, 0), bool)

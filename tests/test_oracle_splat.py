@@ -1,0 +1,196 @@
+"""Pins of the splatting association bounds (oracle/splat.py): closed forms on
+the optical axis, Monte Carlo moments of the true angle distribution, the
+ellipse geometry of the boxes, and a per-ray brute force of the tile masks."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_24053_gb300 import workloads as wl
+
+from oracle import oracle as orc
+from oracle import splat as S
+
+AMIN = 1.0 / 255.0
+
+
+def _cam(model=wl.PINHOLE, w=64, h=48, fov=math.radians(70), **kw):
+    return wl.Camera(model, w, h, fov, **kw)
+
+
+def _quat_of(rng):
+    q = rng.standard_normal(4)
+    return q / np.linalg.norm(q)
+
+
+@pytest.mark.parametrize("z,s", [(3.0, 0.1), (1.0, 0.4), (10.0, 0.02)])
+def test_ewa_on_axis_isotropic(z, s):
+    """On the axis J = I / z, so an isotropic Gaussian projects to variance s^2 / z^2
+    in both angles, whatever its rotation: the 3DGS square has half-side 3 s / z
+    and SnugBox sqrt(2 ln(sigma / alpha_min)) s / z."""
+    cam = _cam()
+    q = _quat_of(np.random.default_rng(1))
+    box = S.splat_box(cam, (0, 0, z), (s, s, s), q, 0.8, S.EWA, False)
+    assert np.allclose(box, (-3 * s / z, 3 * s / z, -3 * s / z, 3 * s / z), rtol=1e-12, atol=1e-15)
+    e = math.sqrt(2 * math.log(0.8 / AMIN)) * s / z
+    assert np.allclose(S.splat_box(cam, (0, 0, z), (s, s, s), q, 0.8, S.EWA, True), (-e, e, -e, e), rtol=1e-12)
+
+
+@pytest.mark.parametrize("z,s", [(3.0, 0.1), (1.0, 0.4), (0.5, 0.28)])  # sqrt(3) s < z: all points in front
+def test_ut_on_axis_isotropic(z, s):
+    """Axis-aligned on the axis: the two sigma points along x sit at angles
+    +-atan(sqrt(3) s / z), the rest at 0, so the mean angle is 0 and the variance
+    2 / 6 atan(sqrt(3) s / z)^2: the square has half-side sqrt(3) atan(sqrt(3) s / z)
+    (3 s / z for small s / z, the EWA value)."""
+    cam = _cam()
+    box = S.splat_box(cam, (0, 0, z), (s, s, s), (1, 0, 0, 0), 0.8, S.UT, False)
+    e = math.sqrt(3.0) * math.atan(math.sqrt(3.0) * s / z)
+    assert np.allclose(box, (-e, e, -e, e), rtol=1e-12, atol=1e-15)
+
+
+def _angle_samples(cam, mu, scale, quat, n, seed):
+    rng = np.random.default_rng(seed)
+    mu_c, Rc = S.camera_frame(cam, mu)
+    M = Rc @ S._rot(quat)
+    t = mu_c + (rng.standard_normal((n, 3)) * np.asarray(scale)) @ M.T
+    return np.stack([np.arctan2(t[:, 0], t[:, 2]), np.arctan2(t[:, 1], t[:, 2])], 1)
+
+
+CASES = [((0.9, -0.5, 2.0), (0.03, 0.01, 0.02)), ((-1.4, 0.8, 1.5), (0.01, 0.04, 0.015)),
+         ((2.5, 2.0, 0.8), (0.02, 0.005, 0.01))]
+
+
+@pytest.mark.parametrize("mu,s", CASES)
+def test_ewa_covariance_is_the_small_gaussian_limit(mu, s):
+    """For a small Gaussian (s / |mu| ~ 1e-3) the angles of its samples are
+    linear in the offset: their covariance is J Sigma_c J^T (Monte Carlo with
+    4e5 samples, 1.5% on each entry relative to the larger diagonal)."""
+    R_cw, t_cw = wl.pose(wl.rot_z(0.4), (0.1, -0.2, 0.05))
+    cam = _cam(R_cw=R_cw, t_cw=t_cw)
+    q = _quat_of(np.random.default_rng(len(mu)))
+    scale = np.asarray(s) * 1e-1
+    c, S2 = S.screen_cov(cam, mu, scale, q, S.EWA)
+    a = _angle_samples(cam, mu, scale, q, 400000, 3)
+    emp = np.cov(a.T)
+    assert np.abs(emp - S2).max() < 0.015 * max(S2[0, 0], S2[1, 1])
+    assert np.abs(a.mean(0) - c).max() < 3 * math.sqrt(max(S2[0, 0], S2[1, 1]) / 400000) + 1e-9
+
+
+@pytest.mark.parametrize("mu,s", CASES)
+def test_ut_moments_match_monte_carlo(mu, s):
+    """At s / |mu| ~ 1e-2 the angle map is visibly nonlinear: the UT mean and
+    covariance track the Monte Carlo moments of the true angle distribution
+    (1e6 samples) closer than the linearised EWA moments do, and both converge
+    to the same values as the Gaussian shrinks."""
+    cam = _cam()
+    q = _quat_of(np.random.default_rng(7 + len(mu)))
+    scale = np.asarray(s) * 3.0
+    cu, Su = S.screen_cov(cam, mu, scale, q, S.UT)
+    ce, Se = S.screen_cov(cam, mu, scale, q, S.EWA)
+    a = _angle_samples(cam, mu, scale, q, 1000000, 11)
+    mc_mean, mc_cov = a.mean(0), np.cov(a.T)
+    sd = math.sqrt(max(mc_cov[0, 0], mc_cov[1, 1]))
+    assert np.abs(cu - mc_mean).max() < 0.01 * sd
+    assert np.abs(cu - mc_mean).max() < np.abs(ce - mc_mean).max()
+    assert np.abs(Su - mc_cov).max() < 0.03 * sd * sd
+    small = np.asarray(s) * 1e-3
+    cu2, Su2 = S.screen_cov(cam, mu, small, q, S.UT)
+    ce2, Se2 = S.screen_cov(cam, mu, small, q, S.EWA)
+    assert np.abs(Su2 - Se2).max() < 1e-4 * max(Se2[0, 0], Se2[1, 1])
+    assert np.abs(cu2 - ce2).max() < 1e-3 * math.sqrt(max(Se2[0, 0], Se2[1, 1]))
+
+
+@pytest.mark.parametrize("mode", [S.EWA, S.UT])
+def test_boxes_bound_their_ellipses(mode):
+    """SnugBox is the bounding box of the ellipse where sigma exp(-v^T Sigma_2^-1 v / 2)
+    = alpha_min; the 3DGS square's half-side is 3 sqrt(max over unit u of
+    u^T Sigma_2 u). Both checked on the ellipse / the unit circle traced densely."""
+    cam = _cam(wl.EQUIDISTANT, 64, 64, math.radians(180))
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        mu = rng.uniform(-1, 1, 3) + (0, 0, 2.5)
+        s = rng.uniform(0.05, 0.4, 3)
+        q = _quat_of(rng)
+        sigma = rng.uniform(0.05, 0.99)
+        c, S2 = S.screen_cov(cam, mu, s, q, mode)
+        t = np.linspace(0, 2 * np.pi, 200001)
+        L = np.linalg.cholesky(S2)
+        v = (L @ np.stack([np.cos(t), np.sin(t)])) * math.sqrt(2 * math.log(sigma / AMIN))
+        dens = sigma * np.exp(-0.5 * np.einsum("in,ij,jn->n", v, np.linalg.inv(S2), v))
+        assert np.allclose(dens, AMIN, rtol=1e-9)
+        snug = S.splat_box(cam, mu, s, q, sigma, mode, True)
+        assert np.allclose([c[0] + v[0].min(), c[0] + v[0].max(), c[1] + v[1].min(), c[1] + v[1].max()], snug,
+                           rtol=0, atol=1e-9 * (1 + abs(snug[1] - snug[0])))
+        u = np.stack([np.cos(t), np.sin(t)])
+        lam = np.einsum("in,ij,jn->n", u, S2, u).max()
+        sq = S.splat_box(cam, mu, s, q, sigma, mode, False)
+        assert math.isclose(sq[1] - c[0], 3 * math.sqrt(lam), rel_tol=1e-9)
+
+
+def test_culling():
+    cam = _cam()
+    s, q = (0.1, 0.1, 0.1), (1, 0, 0, 0)
+    for mode in (S.EWA, S.UT):
+        assert S.splat_box(cam, (0, 0, 0.2), s, q, 0.5, mode, False) is None
+        assert S.splat_box(cam, (0, 0, 0.2000001), s, q, 0.5, mode, False) is not None
+        assert S.splat_box(cam, (0, 0, -3), s, q, 0.5, mode, False) is None
+        assert S.splat_box(cam, (0, 0, 3), s, q, 0.5 * AMIN, mode, False) is None
+        assert S.splat_box(cam, (0, 0, 3), s, q, AMIN, mode, False) is not None
+        assert not S.box_mask(cam, None).any()
+
+
+def test_meets_on_circle():
+    assert S.meets_on_circle(0.1, 0.2, 0.15, 0.3)
+    assert not S.meets_on_circle(0.1, 0.2, 0.25, 0.3)
+    # wrapped: [3.0, 3.5] reaches -2.78
+    assert S.meets_on_circle(-2.9, -2.8, 3.0, 3.5)
+    assert not S.meets_on_circle(-2.7, -2.6, 3.0, 3.5)
+    assert S.meets_on_circle(-1.0, -0.9, -7.0, -0.2 - 2 * math.pi + 2 * math.pi)
+    assert S.meets_on_circle(5.0, 5.1, -100.0, 100.0)
+
+
+def _pixel_mask(cam, box, grow):
+    """Tiles holding a pixel whose ray's screen angles (atan2(x, z), atan2(y, z))
+    lie in the box grown by `grow`, modulo 2 pi."""
+    ty, tx = (cam.height + 15) // 16, (cam.width + 15) // 16
+    m = np.zeros((ty, tx), bool)
+    lo_t, hi_t, lo_p, hi_p = box[0] - grow, box[1] + grow, box[2] - grow, box[3] + grow
+    for j in range(cam.height):
+        for i in range(cam.width):
+            _, d = orc.pixel_ray(cam, i, j)
+            at, ap = math.atan2(d[0], d[2]), math.atan2(d[1], d[2])
+            if S.meets_on_circle(at, at, lo_t, hi_t) and S.meets_on_circle(ap, ap, lo_p, hi_p):
+                m[j // 16, i // 16] = True
+    return m
+
+
+@pytest.mark.parametrize("cam", [_cam(wl.PINHOLE, 70, 50, math.radians(90)),
+                                 _cam(wl.EQUIDISTANT, 75, 61, math.radians(200), fov_y=math.radians(200))],
+                         ids=["pinhole90", "equi200"])
+def test_masks_against_per_ray_brute_force(cam):
+    """Every tile with a ray inside the box is associated; every associated tile
+    (away from the rows and columns where cos(angle) changes sign) has a ray
+    within one pixel pitch of the box. Random Gaussians, some near and large
+    enough that their boxes pass 90 degrees and wrap past pi."""
+    rng = np.random.default_rng(21)
+    fy = orc.fov_y(cam)
+    pitch = max(cam.fov_x / cam.width, fy / cam.height) * 1.0001
+    has0c, has1c = S.cos_flags(cam.width, cam.fov_x)
+    has0r, has1r = S.cos_flags(cam.height, fy)
+    clean = ~((has0r & has1r)[:, None] | (has0c & has1c)[None, :])
+    checked = 0
+    for k in range(24):
+        near = k % 4 == 0
+        mu = rng.normal(0, 0.6 if near else 1.5, 3) + (0, 0, 0.6 if near else 3.0)
+        s = rng.uniform(0.2, 0.8, 3) if near else rng.uniform(0.05, 0.3, 3)
+        for mode in (S.EWA, S.UT):
+            box = S.splat_box(cam, mu, s, _quat_of(rng), 0.7, mode, k % 2 == 1)
+            if box is None:
+                continue
+            mask = S.box_mask(cam, box)
+            inner = _pixel_mask(cam, box, 0.0)
+            outer = _pixel_mask(cam, box, pitch)
+            assert not (inner & ~mask).any(), (k, mode)
+            assert not (mask & ~outer & clean).any(), (k, mode)
+            checked += int(mask.sum())
+    assert checked > 50
