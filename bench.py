@@ -197,6 +197,62 @@ def run_serving(args, dev):
     return out
 
 
+ASSOC_MODES = (("pbf", 0, False), ("ewa", 1, False), ("ewa_snugbox", 1, True), ("ut", 2, False),
+               ("ut_snugbox", 2, True))
+
+
+def _association_ablation(args, geer, g, cams, rgb_pbf, flush, stream):
+    """The association ablation: the same forward pass with the tile association
+    of PBF or of the splatting bounds (EWA / UT, 3-sigma square or SnugBox).
+    Per method: associated (tile, Gaussian) pairs per tile, the forward stages'
+    times (CUDA events, L2 flushed between steps) and the render's PSNR / SSIM
+    against PBF's (what the splatting bounds lose: contributions above alpha_min
+    on tiles their boxes miss)."""
+    import torch
+    tiles = sum(math.ceil(c.width / 16) * math.ceil(c.height / 16) for c in cams)
+    out = {"tiles": tiles, "steps": 10, "modes": {}}
+    ref = None
+    for name, mode, snug in ASSOC_MODES:
+        rr = geer.Renderer(cams, g.n, g.sh_degree, params=geer.params_c(assoc=mode, snugbox=snug))
+        rr.prepare(g)
+        img = torch.empty_like(rgb_pbf)
+        evs = []
+        for k in range(3 + out["steps"]):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            rr.ws.preprocess(g)
+            ev[1].record(stream)
+            rr.ws.bin_sort(sync=False)
+            ev[2].record(stream)
+            rr.ws.render_fwd(img)
+            ev[3].record(stream)
+            if k >= 3:
+                evs.append(ev)
+        torch.cuda.synchronize()
+        st, _ = rr.ws.device_status()
+        if st != geer.OK:
+            raise RuntimeError(f"association ablation ({name}): {geer.status_string(st)}")
+        pairs, _ = rr.ws.pair_counts()
+        if ref is None:
+            ref = img
+        c0 = cams[0]
+        q = geer.image_metrics(img[:c0.pixels].view(c0.height, c0.width, 3),
+                               ref[:c0.pixels].view(c0.height, c0.width, 3))[0]
+        out["modes"][name] = {
+            "gaussians_per_tile": int(pairs) / tiles, "pairs": int(pairs),
+            "preprocess_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+            "bin_sort_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+            "render_fwd_ms": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
+            "fwd_ms": statistics.mean(e[0].elapsed_time(e[3]) for e in evs),
+            "psnr_vs_pbf": q["psnr"] if ref is not img else None,
+            "ssim_vs_pbf": q["ssim"] if ref is not img else None}
+        if ref is not img:
+            del rr, img
+    torch.cuda.empty_cache()
+    return out
+
+
 def run(args):
     import torch
     import torch.distributed as dist
@@ -485,6 +541,8 @@ def run(args):
     adam_bytes = scene.n * per_g * 28 + scene.n * 16  # p, g, m, v read; p, m, v written; activated scale + opacity
     adam_gbs = adam_bytes / (adam_ms / 1e3) / 1e9
 
+    assoc = _association_ablation(args, geer, g, cams, rgb, flush, stream) if not args.no_ablation else None
+
     remap_gbs = 24 * cam.pixels / (remap_ms / 1e3) / 1e9  # 12 B read + 12 B written per native pixel
     remap = {"ms": remap_ms, "bound": "hbm", "achieved": remap_gbs, "peak": hbm_peak, "unit": "GB/s",
              "frac": remap_gbs / hbm_peak, "algorithmic_bytes": 24 * cam.pixels,
@@ -533,6 +591,7 @@ def run(args):
                     "reprojected render, timed on their own with CUDA events (metrics: the kernel, its "
                     "accumulator reset and the 48 B copy back; 24 B of images + 1 B region read per "
                     "pixel); not in value"},
+        "association": assoc,
         "e2e": {"value": e2e, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "pipeline": "H2D of step k+1 on a copy stream during step k (two device buffers), D2H on a "
                             "third stream; one timed region over all steps; inputs > L2, no flush"},
@@ -559,6 +618,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fwd-only", action="store_true", help="time the forward render only")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the association ablation")
     ap.add_argument("--serving-seconds", type=float, default=8.0, help="serving trace length (0: skip)")
     ap.add_argument("--serving-warmup", type=float, default=1.0)
     ap.add_argument("--serving-rate", type=float, default=200.0)

@@ -81,15 +81,32 @@ typedef struct {
     float bg[3];
 } geer_camera;
 
+/* Tile association methods (Sec. 4, association ablation). GEER_ASSOC_PBF:
+ * the particle bounding frustum (Sec. 3.2), exact for the alpha_min contour.
+ * GEER_ASSOC_EWA / GEER_ASSOC_UT: the splatting bounds it is compared with, a
+ * box in the BEAP screen coordinates (atan2(x, z), atan2(y, z)) of the
+ * Gaussian's projection, linearised at the mean (EWA, App. A) or through the
+ * 7 sigma points of the unscented transform (alpha 1, beta 2, kappa 0); the
+ * box is the 3-sigma square of the larger eigenvalue, or with snugbox != 0
+ * the bounding box of the alpha_min ellipse, half-sides
+ * sqrt(2 ln(sigma/alpha_min) Sigma_ii). The splatting modes cull means with
+ * z <= 0.2 instead of PBF's camera-inside test. A tile is associated when its
+ * rays' angle spans meet the box (rays beyond 90 degrees through the box
+ * turned by pi). Only the association changes: every associated pair is
+ * still rendered with the exact ray integral. */
+enum { GEER_ASSOC_PBF = 0, GEER_ASSOC_EWA = 1, GEER_ASSOC_UT = 2 };
+
 /* Rendering parameters. tile_w = tile_h = 16 (BEAP tiles of 16 x 16 rays,
  * each tile a camera sub-frustum, Sec. 3.2). alpha_min: contributions below it
  * are skipped; alpha_max: alpha clamp; T_min: a ray stops before the
  * contributor that would take its transmittance below it (3DGS conventions
  * 1/255, 0.99, 1e-4). lambda_pad: relative padding of the per-Gaussian PBF
- * contour lambda^2 = 2 ln(sigma/alpha_min) (default 1e-3). */
+ * contour lambda^2 = 2 ln(sigma/alpha_min) (default 1e-3). assoc: a
+ * GEER_ASSOC_* method (default PBF); snugbox: 0 or 1, used by EWA and UT. */
 typedef struct {
     int32_t tile_w, tile_h;
     float alpha_min, T_min, alpha_max, lambda_pad;
+    int32_t assoc, snugbox;
 } geer_params;
 
 typedef struct geer_workspace geer_workspace;
@@ -97,7 +114,7 @@ typedef struct geer_workspace geer_workspace;
 /* Human-readable name of a status code. Never returns NULL. */
 const char *geer_status_string(geer_status s);
 
-/* Fill *p with the defaults (16, 16, 1/255, 1e-4, 0.99, 1e-3). */
+/* Fill *p with the defaults (16, 16, 1/255, 1e-4, 0.99, 1e-3, PBF, 0). */
 geer_status geer_default_params(geer_params *p);
 
 /* Device bytes needed for a workspace rendering `n_cams` cameras (whose sizes

@@ -30,9 +30,12 @@ Tiles: a column tile spans the angles [theta(i0), theta(i1)] of its first and
 last pixel, theta(i) = ((i + 1/2) / w - 1/2) fov_x. X0 holds the columns whose
 span meets the theta box on the circle, X1 those whose span meets the box
 turned by pi (a ray with cos(phi) < 0 has atan2(x, z) = theta + pi); Y0 and Y1
-likewise for rows. The association is the same flagged product as PBF's: tile
-(cx, cy) is taken when (its row has a ray with cos(phi) >= 0 and cx in X0, or
-one with cos(phi) < 0 and cx in X1) and (the same with columns and Y0, Y1).
+likewise for rows. Each of these sets is one interval of tiles (the
+association ranges hold one interval per arc, as PBF's do): a set split in two,
+which a box through pi meeting both ends of a wide axis makes, takes the whole
+axis. The association is the same flagged product as PBF's: tile (cx, cy) is
+taken when (its row has a ray with cos(phi) >= 0 and cx in X0, or one with
+cos(phi) < 0 and cx in X1) and (the same with columns and Y0, Y1).
 """
 from __future__ import annotations
 
@@ -119,7 +122,14 @@ def meets_on_circle(a: float, b: float, lo: float, hi: float) -> bool:
     return any(b >= lo + TWO_PI * k and a <= hi + TWO_PI * k for k in range(-3, 4))
 
 
-def axis_sets(lo: float, hi: float, n_pix: int, fov: float):
+def _one_interval(m: np.ndarray) -> np.ndarray:
+    idx = np.flatnonzero(m)
+    if idx.size and idx[-1] - idx[0] + 1 != idx.size:
+        return np.ones_like(m)
+    return m
+
+
+def axis_sets(lo: float, hi: float, n_pix: int, fov: float, one_interval: bool = True):
     """(direct, turned) membership [tiles] of one axis for the angle box [lo, hi]."""
     tiles = (n_pix + 15) // 16
     direct = np.zeros(tiles, bool)
@@ -128,6 +138,8 @@ def axis_sets(lo: float, hi: float, n_pix: int, fov: float):
         a, b = beap_angle(16 * c, n_pix, fov), beap_angle(min(16 * c + 15, n_pix - 1), n_pix, fov)
         direct[c] = meets_on_circle(a, b, lo, hi)
         turned[c] = meets_on_circle(a, b, lo + math.pi, hi + math.pi)
+    if one_interval:
+        return _one_interval(direct), _one_interval(turned)
     return direct, turned
 
 
@@ -144,9 +156,9 @@ def cos_flags(n_pix: int, fov: float):
     return has0, has1
 
 
-def box_mask(cam, box, grow: float = 0.0) -> np.ndarray:
+def box_mask(cam, box, grow: float = 0.0, one_interval: bool = True) -> np.ndarray:
     """Association mask [tiles_y, tiles_x] of one box, its sides moved out by grow
-    (in by -grow)."""
+    (in by -grow); one_interval=False keeps the exact split sets."""
     ty, tx = (cam.height + 15) // 16, (cam.width + 15) // 16
     if box is None:
         return np.zeros((ty, tx), bool)
@@ -154,8 +166,8 @@ def box_mask(cam, box, grow: float = 0.0) -> np.ndarray:
     t0, t1, p0, p1 = box[0] - grow, box[1] + grow, box[2] - grow, box[3] + grow
     if t1 < t0 or p1 < p0:
         return np.zeros((ty, tx), bool)
-    x0, x1 = axis_sets(t0, t1, cam.width, cam.fov_x)
-    y0, y1 = axis_sets(p0, p1, cam.height, fy)
+    x0, x1 = axis_sets(t0, t1, cam.width, cam.fov_x, one_interval)
+    y0, y1 = axis_sets(p0, p1, cam.height, fy, one_interval)
     c_has0, c_has1 = cos_flags(cam.width, cam.fov_x)
     r_has0, r_has1 = cos_flags(cam.height, fy)
     cols_ok = (r_has0[:, None] & x0[None, :]) | (r_has1[:, None] & x1[None, :])
@@ -168,6 +180,9 @@ def scene_boxes(cam, scene, mode: int, snug: bool, alpha_min: float = 1.0 / 255.
                       alpha_min) for g in range(scene.n)]
 
 
-def scene_masks(cam, boxes, grow: float = 0.0) -> np.ndarray:
-    """[n, tiles_y, tiles_x] association masks of the boxes."""
-    return np.stack([box_mask(cam, b, grow) for b in boxes]) if boxes else np.zeros((0, 0, 0), bool)
+def scene_masks(cam, boxes, grow=0.0) -> np.ndarray:
+    """[n, tiles_y, tiles_x] association masks of the boxes; grow: a scalar or one
+    value per box."""
+    grow = np.broadcast_to(np.asarray(grow, np.float64), (len(boxes),))
+    return np.stack([box_mask(cam, b, float(d)) for b, d in zip(boxes, grow)]) if boxes else \
+        np.zeros((0, 0, 0), bool)

@@ -390,6 +390,8 @@ geer_status check_params(const geer_params *p) {
     if (!(p->alpha_max > 0.0f) || !(p->alpha_max < 1.0f) || p->alpha_max < p->alpha_min) return GEER_ERR_ARG;
     if (!(p->T_min >= 0.0f) || !(p->T_min < 1.0f)) return GEER_ERR_ARG;
     if (!(p->lambda_pad >= 0.0f) || !(p->lambda_pad < 1.0f)) return GEER_ERR_ARG;
+    if (p->assoc != GEER_ASSOC_PBF && p->assoc != GEER_ASSOC_EWA && p->assoc != GEER_ASSOC_UT) return GEER_ERR_ARG;
+    if (p->snugbox != 0 && p->snugbox != 1) return GEER_ERR_ARG;
     return GEER_OK;
 }
 
@@ -457,6 +459,8 @@ geer_status geer_default_params(geer_params *p) {
     p->T_min = 1e-4f;
     p->alpha_max = 0.99f;
     p->lambda_pad = 1e-3f;
+    p->assoc = GEER_ASSOC_PBF;
+    p->snugbox = 0;
     return GEER_OK;
 }
 
@@ -503,7 +507,8 @@ geer_status geer_workspace_init(void *dev_mem, size_t bytes, const geer_camera *
     ws->cap_pairs = pair_capacity;
     ws->cap_sh_degree = sh_degree;
     ws->cap_sort_tiles = c.sort_tiles;
-    ws->params = Params{params->alpha_min, params->T_min, params->alpha_max, params->lambda_pad};
+    ws->params = Params{params->alpha_min, params->T_min, params->alpha_max, params->lambda_pad, params->assoc,
+                        params->snugbox};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1109,7 +1114,8 @@ extern "C" geer_status geer_render_noalloc(const geer_gaussians *g, const geer_c
     ws.cap_pairs = kNoAllocMaxPairs;
     ws.cap_sh_degree = 3;
     ws.cap_sort_tiles = c.sort_tiles;
-    ws.params = Params{params->alpha_min, params->T_min, params->alpha_max, params->lambda_pad};
+    ws.params = Params{params->alpha_min, params->T_min, params->alpha_max, params->lambda_pad, params->assoc,
+                       params->snugbox};
     ws.num_sms = S.num_sms;
     ws.sort_grid = S.num_sms * sort_blocks_per_sm();
     ws.n_cams = 1;

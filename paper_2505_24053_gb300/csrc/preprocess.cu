@@ -144,6 +144,115 @@ __device__ float lambda2(float sigma, float alpha_min, float pad) {
     return fm(fm(2.0f, lnx), fa(1.0f, pad));
 }
 
+// ---- Splatting bounds (the association ablation, Sec. 4) -------------------
+// The EWA and UT alternatives to PBF bound the Gaussian's projection onto the
+// BEAP screen (theta, phi) = (atan2(x, z), atan2(y, z)) by a box; the box's
+// angle intervals become arcs of the same half-angle-tangent form as PBF's,
+// so the tile ranges and everything after them are shared. Plain FP32
+// arithmetic (no reproducibility contract: the bounds are compared with an
+// FP64 definition within a tolerance).
+constexpr float kPiF = 3.14159265358979f, kTwoPiF = 6.28318530717959f;
+constexpr float kSplatNear = 0.2f;  // near plane of the splatting pipelines
+constexpr float kSqrt3 = 1.7320508075688772f;
+
+// tan(a / 2) for a in [-pi, pi]; the half angle is kept below pi / 2 so that the
+// FP32 rounding of pi cannot turn the tangent's sign at the ends.
+__device__ __forceinline__ float tan_half(float a) {
+    return tanf(fminf(fmaxf(0.5f * a, -1.5707962f), 1.5707962f));
+}
+
+// The arc of the angles [lo, hi] taken modulo 2 pi.
+__device__ Arc angle_arc(float lo, float hi) {
+    Arc a{3, 0.0f, 0.0f};
+    if (!(hi - lo < kTwoPiF) || !isfinite(lo) || !isfinite(hi)) return a;
+    const float k = floorf((lo + kPiF) / kTwoPiF);  // lo into [-pi, pi)
+    lo -= k * kTwoPiF;
+    hi -= k * kTwoPiF;
+    if (hi <= kPiF) {
+        a.kind = 1;
+        a.lo = tan_half(lo);
+        a.hi = tan_half(hi);
+    } else {  // through pi: [lo, pi] u (-pi, hi - 2 pi]
+        a.kind = 2;
+        a.lo = tan_half(lo);
+        a.hi = tan_half(hi - kTwoPiF);
+    }
+    return a;
+}
+
+// The splatting box of a live item as four arcs: theta (a), theta turned by pi
+// (a1: rows whose rays have cos(phi) < 0 see atan2(x, z) = theta + pi), phi (b)
+// and phi turned (b1). (x, y, z): camera-frame mean; column k of M: axis k;
+// s: scales. EWA: Sigma_2 = J Sigma_c J^T with the rows of J the gradients of
+// the two angles, summed over the axes as s_k^2 (J M_k)(J M_k)^T. UT: the six
+// off-centre sigma points mu +- sqrt(3) s_k M_k, their angles taken relative to
+// the mean's (atan2 of the cross and dot products with the offset split out,
+// so small Gaussians lose no digits); weights 1/6 each, the centre point 0 for
+// the mean and 2 for the covariance.
+__device__ __forceinline__ void splat_arcs(int mode, int snug, float amin, float sigma, float x, float y, float z,
+                                           const float M[9], const float s[3], Arc &a, Arc &a1, Arc &b, Arc &b1) {
+    float tc = atan2f(x, z), pc = atan2f(y, z);
+    float c00 = 0.0f, c01 = 0.0f, c11 = 0.0f;
+    if (mode == GEER_ASSOC_EWA) {
+        const float rx = 1.0f / (x * x + z * z), ry = 1.0f / (y * y + z * z);
+        const float ja0 = z * rx, ja2 = -x * rx, jb1 = z * ry, jb2 = -y * ry;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float v = ja0 * M[k] + ja2 * M[6 + k], w = jb1 * M[3 + k] + jb2 * M[6 + k];
+            const float s2 = s[k] * s[k];
+            c00 += s2 * v * v;
+            c01 += s2 * v * w;
+            c11 += s2 * w * w;
+        }
+    } else {
+        float dt[6], dp[6], mt = 0.0f, mp = 0.0f;
+        const float rxz = x * x + z * z, ryz = y * y + z * z;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float f = (h == 0 ? kSqrt3 : -kSqrt3) * s[k];
+                const float ox = f * M[k], oy = f * M[3 + k], oz = f * M[6 + k];
+                dt[2 * k + h] = atan2f(ox * z - oz * x, rxz + ox * x + oz * z);
+                dp[2 * k + h] = atan2f(oy * z - oz * y, ryz + oy * y + oz * z);
+                mt += dt[2 * k + h];
+                mp += dp[2 * k + h];
+            }
+        }
+        mt *= (1.0f / 6.0f);
+        mp *= (1.0f / 6.0f);
+        c00 = 2.0f * mt * mt;
+        c01 = 2.0f * mt * mp;
+        c11 = 2.0f * mp * mp;
+        float q00 = 0.0f, q01 = 0.0f, q11 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const float et = dt[i] - mt, ep = dp[i] - mp;
+            q00 += et * et;
+            q01 += et * ep;
+            q11 += ep * ep;
+        }
+        c00 += q00 * (1.0f / 6.0f);
+        c01 += q01 * (1.0f / 6.0f);
+        c11 += q11 * (1.0f / 6.0f);
+        tc += mt;
+        pc += mp;
+    }
+    float et, ep;
+    if (snug) {  // bounding box of the alpha_min ellipse
+        const float t = 2.0f * logf(sigma / amin);
+        et = sqrtf(fmaxf(t * c00, 0.0f));
+        ep = sqrtf(fmaxf(t * c11, 0.0f));
+    } else {  // 3 sqrt of the larger eigenvalue, both axes
+        const float h = 0.5f * (c00 + c11), d = 0.5f * (c00 - c11);
+        et = ep = 3.0f * sqrtf(fmaxf(h + sqrtf(d * d + c01 * c01), 0.0f));
+    }
+    a = angle_arc(tc - et, tc + et);
+    a1 = angle_arc(tc - et + kPiF, tc + et + kPiF);
+    b = angle_arc(pc - ep, pc + ep);
+    b1 = angle_arc(pc - ep + kPiF, pc + ep + kPiF);
+}
+
 
 // Real SH of degree <= 3 in the 3DGS convention (Condon-Shortley phase, index
 // l^2 + l + m), written out as polynomials of the unit direction. The constants
@@ -400,7 +509,7 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
         R[7] = fm(2.0f, fa(fm(y, z), fm(w, x)));
         R[8] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(y, y))));
         lam2 = lambda2(sigma, p.alpha_min, p.lambda_pad);
-        if (!(lam2 > 0.0f)) ok = false;
+        if (p.assoc == GEER_ASSOC_PBF && !(lam2 > 0.0f)) ok = false;
     }
     const float s2[3] = {fm(sc[0], sc[0]), fm(sc[1], sc[1]), fm(sc[2], sc[2])};
     const float ss[3] = {fm(sc[1], sc[2]), fm(sc[0], sc[2]), fm(sc[0], sc[1])};
@@ -428,43 +537,50 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
             for (int k = 0; k < 3; ++k)
                 u[k] = fdv(fa(fa(fm(M[k], m0), fm(M[3 + k], m1)), fm(M[6 + k], m2)), sc[k]);
             float ou2 = fa(fa(fm(u[0], u[0]), fm(u[1], u[1])), fm(u[2], u[2]));
-            if (!(ou2 > lam2)) live = false;
+            if (p.assoc == GEER_ASSOC_PBF ? !(ou2 > lam2) : !(m2 > kSplatNear)) live = false;
         }
         if (live) {
-            auto SIG = [&](int a, int b) {
-                return fa(fa(fm(s2[0], fm(M[3 * a], M[3 * b])), fm(s2[1], fm(M[3 * a + 1], M[3 * b + 1]))),
-                          fm(s2[2], fm(M[3 * a + 2], M[3 * b + 2])));
-            };
-            float Sxx = SIG(0, 0), Syy = SIG(1, 1), Szz = SIG(2, 2), Sxz = SIG(0, 2), Syz = SIG(1, 2);
-            float T00 = fs(fm(lam2, Sxx), fm(m0, m0));
-            float T11 = fs(fm(lam2, Syy), fm(m1, m1));
-            float T22 = fs(fm(lam2, Szz), fm(m2, m2));
-            float T02 = fs(fm(lam2, Sxz), fm(m0, m2));
-            float T12 = fs(fm(lam2, Syz), fm(m1, m2));
-            float pxz[3], pyz[3], dxz[3], dyz[3];
+            Arc A, B, A1, B1;
+            if (p.assoc == GEER_ASSOC_PBF) {
+                auto SIG = [&](int a, int b) {
+                    return fa(fa(fm(s2[0], fm(M[3 * a], M[3 * b])), fm(s2[1], fm(M[3 * a + 1], M[3 * b + 1]))),
+                              fm(s2[2], fm(M[3 * a + 2], M[3 * b + 2])));
+                };
+                float Sxx = SIG(0, 0), Syy = SIG(1, 1), Szz = SIG(2, 2), Sxz = SIG(0, 2), Syz = SIG(1, 2);
+                float T00 = fs(fm(lam2, Sxx), fm(m0, m0));
+                float T11 = fs(fm(lam2, Syy), fm(m1, m1));
+                float T22 = fs(fm(lam2, Szz), fm(m2, m2));
+                float T02 = fs(fm(lam2, Sxz), fm(m0, m2));
+                float T12 = fs(fm(lam2, Syz), fm(m1, m2));
+                float pxz[3], pyz[3], dxz[3], dyz[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float cx = fs(fm(m0, M[6 + k]), fm(m2, M[k]));
-                float cy = fs(fm(m1, M[6 + k]), fm(m2, M[3 + k]));
-                pxz[k] = fm(s2[k], fm(cx, cx));
-                pyz[k] = fm(s2[k], fm(cy, cy));
-                float ax = fm(ss[k], M[3 + k]);
-                float ay = fm(ss[k], M[k]);
-                dxz[k] = fm(ax, ax);
-                dyz[k] = fm(ay, ay);
+                for (int k = 0; k < 3; ++k) {
+                    float cx = fs(fm(m0, M[6 + k]), fm(m2, M[k]));
+                    float cy = fs(fm(m1, M[6 + k]), fm(m2, M[3 + k]));
+                    pxz[k] = fm(s2[k], fm(cx, cx));
+                    pyz[k] = fm(s2[k], fm(cy, cy));
+                    float ax = fm(ss[k], M[3 + k]);
+                    float ay = fm(ss[k], M[k]);
+                    dxz[k] = fm(ax, ax);
+                    dyz[k] = fm(ay, ay);
+                }
+                float Pxz = fa(fa(pxz[0], pxz[1]), pxz[2]), Pyz = fa(fa(pyz[0], pyz[1]), pyz[2]);
+                float Dxz = fa(fa(dxz[0], dxz[1]), dxz[2]), Dyz = fa(fa(dyz[0], dyz[1]), dyz[2]);
+                A = pbf_arc(m0, m2, T00, T02, T22, Pxz, Dxz, lam2);
+                B = pbf_arc(m1, m2, T11, T12, T22, Pyz, Dyz, lam2);
+                A1 = shift_arc(A);
+                B1 = shift_arc(B);
+            } else {
+                splat_arcs(p.assoc, p.snug, p.alpha_min, sigma, m0, m1, m2, M, sc, A, A1, B, B1);
             }
-            float Pxz = fa(fa(pxz[0], pxz[1]), pxz[2]), Pyz = fa(fa(pyz[0], pyz[1]), pyz[2]);
-            float Dxz = fa(fa(dxz[0], dxz[1]), dxz[2]), Dyz = fa(fa(dyz[0], dyz[1]), dyz[2]);
-            Arc A = pbf_arc(m0, m2, T00, T02, T22, Pxz, Dxz, lam2);
-            Arc B = pbf_arc(m1, m2, T11, T12, T22, Pyz, Dyz, lam2);
             const float4 *ctab = ttab + cam.tcol_off;
             const float4 *rtab = ttab + cam.trow_off;
             int rg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             const float chalf = 0.5f * (float)(cam.width - 1), rhalf = 0.5f * (float)(cam.height - 1);
             arc_range(A, ctab, cam.tiles_x, cam.col_ppr, chalf, rg[0], rg[1]);
             arc_range(B, rtab, cam.tiles_y, cam.row_ppr, rhalf, rg[4], rg[5]);
-            if (cam.any_row_flip) arc_range(shift_arc(A), ctab, cam.tiles_x, cam.col_ppr, chalf, rg[2], rg[3]);
-            if (cam.any_col_flip) arc_range(shift_arc(B), rtab, cam.tiles_y, cam.row_ppr, rhalf, rg[6], rg[7]);
+            if (cam.any_row_flip) arc_range(A1, ctab, cam.tiles_x, cam.col_ppr, chalf, rg[2], rg[3]);
+            if (cam.any_col_flip) arc_range(B1, rtab, cam.tiles_y, cam.row_ppr, rhalf, rg[6], rg[7]);
             if (is_rect(cam, rg))
                 cnt = (uint32_t)(rg[1] - rg[0]) * (uint32_t)(rg[5] - rg[4]);
             else
@@ -902,7 +1018,7 @@ __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ ti
 cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g, cudaStream_t s) {
     const int64_t nblk = prep_blocks(g->n);
     if (nblk == 0) return cudaSuccess;
-    const Params prm{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad};
+    const Params prm = ws->params;
 #define GEER_PREP_LAUNCH(D)                                                                                      \
     {                                                                                                            \
         const int smem = kPrepThreads * PrepSh<D>::kStride * (int)sizeof(float);                               \

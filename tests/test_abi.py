@@ -42,7 +42,23 @@ def test_status_strings_and_defaults(geer):
     assert (p.tile_w, p.tile_h) == (16, 16)
     assert p.alpha_min == pytest.approx(1 / 255) and p.alpha_max == pytest.approx(0.99)
     assert p.T_min == pytest.approx(1e-4) and p.lambda_pad == pytest.approx(1e-3)
+    assert (p.assoc, p.snugbox) == (geer.ASSOC_PBF, 0)
     assert L.geer_default_params(None) == geer.ERR_ARG
+
+
+def test_association_modes_are_validated_on_host(geer):
+    """Unknown association methods and SnugBox flags are rejected before any
+    device work (the no-allocation entry checks its parameters first)."""
+    from paper_2505_24053_gb300 import workloads as wl
+    L = geer.lib()
+    cam = geer.camera_c(wl.Camera(wl.PINHOLE, 32, 32, math.radians(60)))
+    g = geer.GaussiansC()
+    g.n, g.sh_degree = 0, 0
+    for assoc, snug in ((3, 0), (-1, 0), (1, 2), (2, -1)):
+        p = geer.params_c()
+        p.assoc, p.snugbox = assoc, snug
+        assert L.geer_render_noalloc(C.byref(g), C.byref(cam), C.byref(p), C.c_void_p(256), None, None) == \
+            geer.ERR_ARG, (assoc, snug)
 
 
 def test_workspace_size_checks_arguments_on_host(geer):

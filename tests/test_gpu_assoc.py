@@ -1,0 +1,160 @@
+"""GPU parity of the splatting association modes (EWA, UT, each with and
+without SnugBox) against the FP64 oracle (oracle/splat.py, pinned in
+tests/test_oracle_splat.py), through the C ABI.
+
+- Masks: the GPU's boxes are FP32, the oracle's FP64, so a tile may differ only
+  where a box edge lies within delta of the tile's edge ray: the oracle's mask
+  of the box shrunk by delta lies inside the GPU's mask, and the GPU's inside
+  the oracle's mask of the box grown by delta (delta = 2e-5 rad + 1e-4 of the
+  box's larger half-side). The GPU's per-item tile counts equal its masks'
+  sizes exactly.
+- Render and backward: on every tile whose association is the same under the
+  shrunk and grown boxes, the pixels match the brute-force oracle render over
+  that tile's associated Gaussians (within 2e-4 of an admissible result, as in
+  the PBF forward tests), and the gradients of a loss on those pixels match the
+  oracle's (relative L2 and max error 1e-3, as in the PBF backward tests).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_24053_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def geer():
+    from paper_2505_24053_gb300 import geer
+    geer.lib()
+    assert torch.cuda.is_available()
+    return geer
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle
+    return oracle
+
+
+@pytest.fixture(scope="module")
+def S():
+    from oracle import splat
+    return splat
+
+
+def _scene(seed, n, deg, near_frac=0.1, spread=2.5):
+    """Far Gaussians around the camera plus a share of near, large ones (whose
+    boxes reach past 90 degrees and wrap)."""
+    rng = np.random.default_rng(seed)
+    n_near = int(n * near_frac)
+    mean = rng.uniform(-spread, spread, (n, 3))
+    mean[:n_near] = rng.normal(0, 0.5, (n_near, 3)) + (0, 0, 0.7)
+    log_s = rng.normal(-1.8, 0.5, (n, 3))
+    log_s[:n_near] = rng.normal(-1.0, 0.3, (n_near, 3))
+    quat = rng.standard_normal((n, 4))
+    opacity = 1 / (1 + np.exp(-rng.normal(0.5, 1.5, n)))
+    sh = rng.normal(0, 0.3, (n, (deg + 1) ** 2, 3))
+    return wl.Scene(mean.astype(np.float32), np.exp(log_s).astype(np.float32), quat.astype(np.float32),
+                    opacity.astype(np.float32), sh.astype(np.float32), deg)
+
+
+def _delta(boxes):
+    return np.array([0.0 if b is None else 2e-5 + 1e-4 * max(b[1] - b[0], b[3] - b[2]) * 0.5 for b in boxes])
+
+
+MODES = [("ewa", 1, False), ("ewa_snug", 1, True), ("ut", 2, False), ("ut_snug", 2, True)]
+MASK_CAMS = [
+    ("pinhole90", wl.Camera(wl.PINHOLE, 150, 100, math.radians(90))),
+    ("equi200", wl.Camera(wl.EQUIDISTANT, 128, 120, math.radians(200))),
+    ("kb190", wl.Camera(wl.KANNALA_BRANDT, 160, 120, math.radians(190), k=wl.kb_coeffs(3))),
+]
+
+
+@pytest.mark.parametrize("mname,mode,snug", MODES, ids=[m[0] for m in MODES])
+@pytest.mark.parametrize("cname,cam", MASK_CAMS, ids=[c[0] for c in MASK_CAMS])
+def test_splat_masks_match_oracle(geer, orc, S, cname, cam, mname, mode, snug):
+    scene = _scene(len(cname) * 7 + mode, 1500, 1)
+    r = geer.Renderer([cam], scene.n, scene.sh_degree, params=geer.params_c(assoc=mode, snugbox=snug))
+    r.prepare(geer.Gaussians.from_scene(scene))
+    _, _, ranges, counts = r.ws.debug_preprocess()
+    got = orc.assoc_mask(cam, ranges).astype(bool)
+    assert np.array_equal(got.reshape(scene.n, -1).sum(1), counts), "tile counts vs ranges"
+    boxes = S.scene_boxes(cam, scene, mode, snug)
+    d = _delta(boxes)
+    lo = S.scene_masks(cam, boxes, -d)
+    hi = S.scene_masks(cam, boxes, d)
+    miss = (lo & ~got).reshape(scene.n, -1).any(1)
+    extra = (got & ~hi).reshape(scene.n, -1).any(1)
+    assert not miss.any(), (cname, mname, np.flatnonzero(miss)[:5])
+    assert not extra.any(), (cname, mname, np.flatnonzero(extra)[:5])
+    live = np.array([b is not None for b in boxes])
+    assert live.sum() > scene.n // 4 and got.sum() > 10 * scene.n // 4
+
+
+def _key_and_filter(orc, scene, cam):
+    """The replica's depth keys; the scene keeps only Gaussians whose PBF cull and
+    splatting cull agree (no camera inside a contour), so the keys are defined
+    for every splatting-live Gaussian."""
+    Rc = np.asarray(cam.R_cw, np.float64)
+    z = (np.asarray(scene.mean, np.float64) @ Rc.T + np.asarray(cam.t_cw, np.float64))[:, 2]
+    rc, rk, _, _ = orc.replica(scene, cam)
+    keep = (rc == 0) | (z <= 0.2) | (scene.opacity < 1 / 255)
+    scene = scene.subset(np.flatnonzero(keep))
+    rc, rk, _, _ = orc.replica(scene, cam)
+    return scene, rk
+
+
+def _tiles(cam):
+    for cy in range((cam.height + 15) // 16):
+        for cx in range((cam.width + 15) // 16):
+            ii, jj = np.meshgrid(np.arange(16 * cx, min(16 * cx + 16, cam.width)),
+                                 np.arange(16 * cy, min(16 * cy + 16, cam.height)))
+            yield cx, cy, np.stack([ii.ravel(), jj.ravel()], 1).astype(np.int32)
+
+
+RENDER_CASES = [
+    ("pinhole_ewa", wl.Camera(wl.PINHOLE, 64, 48, math.radians(70), bg=(0.2, 0.3, 0.4)), 1, False),
+    ("equi200_ut", wl.Camera(wl.EQUIDISTANT, 48, 48, math.radians(200)), 2, False),
+    ("kb190_ewa_snug", wl.Camera(wl.KANNALA_BRANDT, 64, 48, math.radians(190), k=wl.kb_coeffs(3)), 1, True),
+    ("pinhole_ut_snug", wl.Camera(wl.PINHOLE, 50, 37, math.radians(80)), 2, True),
+]
+
+
+@pytest.mark.parametrize("name,cam,mode,snug", RENDER_CASES, ids=[c[0] for c in RENDER_CASES])
+def test_splat_render_and_backward_match_oracle(geer, orc, S, name, cam, mode, snug):
+    scene, key = _key_and_filter(orc, cam=cam, scene=_scene(len(name), 400, 2, near_frac=0.03, spread=3.0))
+    boxes = S.scene_boxes(cam, scene, mode, snug)
+    d = _delta(boxes)
+    lo, hi = S.scene_masks(cam, boxes, -d), S.scene_masks(cam, boxes, d)
+    r = geer.Renderer([cam], scene.n, scene.sh_degree, params=geer.params_c(assoc=mode, snugbox=snug))
+    g = geer.Gaussians.from_scene(scene)
+    rgb = r.forward(g)
+    img = rgb.cpu().numpy().reshape(cam.height, cam.width, 3)
+    rng = np.random.default_rng(3)
+    dL = rng.normal(0, 1, (cam.height, cam.width, 3))
+    ref = None
+    checked = 0
+    for cx, cy, pix in _tiles(cam):
+        if (lo[:, cy, cx] != hi[:, cy, cx]).any():
+            dL[pix[:, 1], pix[:, 0]] = 0.0  # an ambiguous tile: left out of both sides
+            continue
+        rep = ((~hi[:, cy, cx]).astype(np.uint8), key)
+        out = orc.render_pixels(scene, cam, pix, rep=rep)
+        ok, err, _, und = orc.match_pixels(img[pix[:, 1], pix[:, 0]].astype(np.float64), out, 2e-4,
+                                           cond_limit=np.inf)
+        assert ok.all() and und.sum() == 0, (name, cx, cy, err.max())
+        gr = orc.render_grad(scene, cam, pix, dL[pix[:, 1], pix[:, 0]], rep=rep)
+        ref = gr if ref is None else {k: ref[k] + gr[k] for k in ref}
+        checked += pix.shape[0]
+    assert checked >= cam.pixels // 2, (name, checked)
+    grads = r.backward(g, torch.as_tensor(dL.reshape(-1, 3), dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    for k in ("mean", "scale", "quat", "opacity", "sh"):
+        a = grads[k].cpu().numpy().astype(np.float64).ravel()
+        b = ref[k].ravel()
+        nb = np.linalg.norm(b)
+        assert nb > 0, (name, k)
+        assert np.linalg.norm(a - b) / nb <= 1e-3 and np.abs(a - b).max() <= 1e-3 * np.abs(b).max(), (name, k)
