@@ -201,23 +201,32 @@ ASSOC_MODES = (("pbf", 0, False), ("ewa", 1, False), ("ewa_snugbox", 1, True), (
                ("ut_snugbox", 2, True))
 
 
-def _association_ablation(args, geer, g, cams, rgb_pbf, flush, stream):
+def _association_ablation(args, geer, wl, g, cams, rgb_pbf, flush, stream):
     """The association ablation: the same forward pass with the tile association
-    of PBF or of the splatting bounds (EWA / UT, 3-sigma square or SnugBox).
-    Per method: associated (tile, Gaussian) pairs per tile, the forward stages'
-    times (CUDA events, L2 flushed between steps) and the render's PSNR / SSIM
-    against PBF's (what the splatting bounds lose: contributions above alpha_min
-    on tiles their boxes miss)."""
-    import torch
+    of PBF or of the splatting bounds (EWA / UT, 3-sigma square or SnugBox), on
+    the bench scene and on an indoor room of the same size (wall surfels and
+    clutter around the camera). Per method: associated (tile, Gaussian) pairs
+    per tile, the forward stages' times (CUDA events, L2 flushed between steps)
+    and the render's PSNR / SSIM against PBF's (what the splatting bounds lose:
+    contributions above alpha_min on tiles their boxes miss)."""
+    room = geer.Gaussians.from_scene(wl.room_scene(g.n, 6, g.sh_degree))
     tiles = sum(math.ceil(c.width / 16) * math.ceil(c.height / 16) for c in cams)
-    out = {"tiles": tiles, "steps": 10, "modes": {}}
+    return {"tiles": tiles, "steps": 10,
+            "scenes": {"bench": _ablate_scene(geer, g, cams, rgb_pbf, flush, stream, tiles),
+                       "room": _ablate_scene(geer, room, cams, rgb_pbf, flush, stream, tiles)},
+            "room": "room_scene: 80% wall surfels (box 5 x 2.8 x 6 m around the camera), 20% clutter"}
+
+
+def _ablate_scene(geer, g, cams, rgb_pbf, flush, stream, tiles):
+    import torch
+    out = {"modes": {}}
     ref = None
     for name, mode, snug in ASSOC_MODES:
         rr = geer.Renderer(cams, g.n, g.sh_degree, params=geer.params_c(assoc=mode, snugbox=snug))
         rr.prepare(g)
         img = torch.empty_like(rgb_pbf)
         evs = []
-        for k in range(3 + out["steps"]):
+        for k in range(3 + 10):
             flush.zero_()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record(stream)
@@ -240,7 +249,7 @@ def _association_ablation(args, geer, g, cams, rgb_pbf, flush, stream):
         q = geer.image_metrics(img[:c0.pixels].view(c0.height, c0.width, 3),
                                ref[:c0.pixels].view(c0.height, c0.width, 3))[0]
         out["modes"][name] = {
-            "gaussians_per_tile": int(pairs) / tiles, "pairs": int(pairs),
+            "gaussians_per_tile": int(pairs) / tiles, "pairs": int(pairs), "live_items": rr.ws.live_items(),
             "preprocess_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
             "bin_sort_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
             "render_fwd_ms": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
@@ -541,7 +550,7 @@ def run(args):
     adam_bytes = scene.n * per_g * 28 + scene.n * 16  # p, g, m, v read; p, m, v written; activated scale + opacity
     adam_gbs = adam_bytes / (adam_ms / 1e3) / 1e9
 
-    assoc = _association_ablation(args, geer, g, cams, rgb, flush, stream) if not args.no_ablation else None
+    assoc = _association_ablation(args, geer, wl, g, cams, rgb, flush, stream) if not args.no_ablation else None
 
     remap_gbs = 24 * cam.pixels / (remap_ms / 1e3) / 1e9  # 12 B read + 12 B written per native pixel
     remap = {"ms": remap_ms, "bound": "hbm", "achieved": remap_gbs, "peak": hbm_peak, "unit": "GB/s",

@@ -89,11 +89,13 @@ typedef struct {
  * 7 sigma points of the unscented transform (alpha 1, beta 2, kappa 0); the
  * box is the 3-sigma square of the larger eigenvalue, or with snugbox != 0
  * the bounding box of the alpha_min ellipse, half-sides
- * sqrt(2 ln(sigma/alpha_min) Sigma_ii). The splatting modes cull means with
- * z <= 0.2 instead of PBF's camera-inside test. A tile is associated when its
+ * sqrt(2 ln(sigma/alpha_min) Sigma_ii). Only the association step changes:
+ * every mode culls as PBF does (sigma < alpha_min, camera inside the alpha_min
+ * contour), and the splatting modes also cull means with z <= 0.2 (their near
+ * plane: the projection divides by z). A tile is associated when its
  * rays' angle spans meet the box (rays beyond 90 degrees through the box
- * turned by pi). Only the association changes: every associated pair is
- * still rendered with the exact ray integral. */
+ * turned by pi). Every associated pair is still rendered with the exact ray
+ * integral. */
 enum { GEER_ASSOC_PBF = 0, GEER_ASSOC_EWA = 1, GEER_ASSOC_UT = 2 };
 
 /* Rendering parameters. tile_w = tile_h = 16 (BEAP tiles of 16 x 16 rays,

@@ -24,7 +24,12 @@ exactly these for |theta|, |phi| < 90 degrees, Sec. 3.3).
 - The box: a square of half-side 3 sqrt(largest eigenvalue of Sigma_2), or with
   SnugBox the bounding box of the ellipse where the density reaches alpha_min,
   half-sides sqrt(2 ln(sigma / alpha_min) Sigma_2[i, i]).
-- Culling: mean with z <= 0.2 (the splatting near plane), sigma < alpha_min.
+- Culling: the pipeline's own (Algorithm 1, CullGaussian: sigma < alpha_min or
+  the camera inside the contour lambda^2 = 2 ln(sigma / alpha_min) (1 + 1e-3)),
+  plus the splatting near plane, mean with z <= 0.2 (the projection divides by
+  z). Only the association step differs from the PBF pipeline. For a whole scene
+  the camera-inside decision is the FP32 replica's (oracle.replica), the
+  precision the kernel takes it in; splat_box alone takes it in FP64.
 
 Tiles: a column tile spans the angles [theta(i0), theta(i1)] of its first and
 last pixel, theta(i) = ((i + 1/2) / w - 1/2) fov_x. X0 holds the columns whose
@@ -96,9 +101,20 @@ def screen_cov(cam, mu, scale, quat, mode: int):
     return centre, np.einsum("i,ij,ik->jk", wc, d, d)
 
 
-def splat_box(cam, mu, scale, quat, sigma, mode: int, snug: bool, alpha_min: float = 1.0 / 255.0):
-    """(theta_lo, theta_hi, phi_lo, phi_hi) of one Gaussian, or None when culled."""
-    if not sigma >= alpha_min:
+def camera_inside(cam, mu, scale, quat, sigma, alpha_min: float = 1.0 / 255.0, pad: float = 1e-3) -> bool:
+    """The camera (origin) lies inside the Gaussian's contour |S^-1 M^T mu_c|^2 <= lambda^2."""
+    mu_c, Rc = camera_frame(cam, mu)
+    u = (Rc @ _rot(quat)).T @ mu_c / np.asarray(scale, np.float64)
+    return float(u @ u) <= 2.0 * math.log(sigma / alpha_min) * (1.0 + pad)
+
+
+def splat_box(cam, mu, scale, quat, sigma, mode: int, snug: bool, alpha_min: float = 1.0 / 255.0,
+              inside=None):
+    """(theta_lo, theta_hi, phi_lo, phi_hi) of one Gaussian, or None when culled
+    (inside: a camera-inside decision taken elsewhere, else FP64 here)."""
+    if not sigma > alpha_min:
+        return None
+    if camera_inside(cam, mu, scale, quat, sigma, alpha_min) if inside is None else inside:
         return None
     r = screen_cov(cam, mu, scale, quat, mode)
     if r is None:
@@ -176,8 +192,11 @@ def box_mask(cam, box, grow: float = 0.0, one_interval: bool = True) -> np.ndarr
 
 
 def scene_boxes(cam, scene, mode: int, snug: bool, alpha_min: float = 1.0 / 255.0):
-    return [splat_box(cam, scene.mean[g], scene.scale[g], scene.quat[g], float(scene.opacity[g]), mode, snug,
-                      alpha_min) for g in range(scene.n)]
+    """Boxes of a scene's Gaussians, the pipeline's cull taken from the FP32 replica."""
+    cull = orc.replica(scene, cam, alpha_min=alpha_min)[0]
+    return [None if cull[g] else
+            splat_box(cam, scene.mean[g], scene.scale[g], scene.quat[g], float(scene.opacity[g]), mode, snug,
+                      alpha_min, inside=False) for g in range(scene.n)]
 
 
 def scene_masks(cam, boxes, grow=0.0) -> np.ndarray:

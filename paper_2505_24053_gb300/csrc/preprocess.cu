@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
         R[7] = fm(2.0f, fa(fm(y, z), fm(w, x)));
         R[8] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(y, y))));
         lam2 = lambda2(sigma, p.alpha_min, p.lambda_pad);
-        if (p.assoc == GEER_ASSOC_PBF && !(lam2 > 0.0f)) ok = false;
+        if (!(lam2 > 0.0f)) ok = false;
     }
     const float s2[3] = {fm(sc[0], sc[0]), fm(sc[1], sc[1]), fm(sc[2], sc[2])};
     const float ss[3] = {fm(sc[1], sc[2]), fm(sc[0], sc[2]), fm(sc[0], sc[1])};
@@ -537,7 +537,9 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
             for (int k = 0; k < 3; ++k)
                 u[k] = fdv(fa(fa(fm(M[k], m0), fm(M[3 + k], m1)), fm(M[6 + k], m2)), sc[k]);
             float ou2 = fa(fa(fm(u[0], u[0]), fm(u[1], u[1])), fm(u[2], u[2]));
-            if (p.assoc == GEER_ASSOC_PBF ? !(ou2 > lam2) : !(m2 > kSplatNear)) live = false;
+            if (!(ou2 > lam2)) live = false;
+            // the splatting bounds project through z: their near plane as well
+            if (p.assoc != GEER_ASSOC_PBF && !(m2 > kSplatNear)) live = false;
         }
         if (live) {
             Arc A, B, A1, B1;

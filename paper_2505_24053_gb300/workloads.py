@@ -25,6 +25,10 @@ which are not available here):
      log-scale ~ N(-3.5, 1), SH degree 3; four equidistant fisheye cameras
      1920x1536, 210 deg, yaw 0/90/180/270 deg at the origin.
 
+Besides these, room_scene() draws an indoor room of wall surfels and clutter
+around the camera, the structure of trained indoor fisheye scenes, for the
+association ablation (it has no counterpart among the numbered workloads).
+
 The DC SH coefficient is drawn uniformly in [-sqrt(pi), sqrt(pi)], which is the
 range that makes the degree-0 colour uniform in [0, 1] under the 3DGS colour
 convention (colour = Y_00 * dc + 1/2, Y_00 = 1/(2 sqrt(pi))).
@@ -129,6 +133,63 @@ def slab_scene(n: int, seed: int, deg: int = 3) -> Scene:
     log_s = rng.normal(-3.5, 1.0, (n, 3))
     quat = _quats(rng, n)
     opacity = _sigmoid(rng.normal(0.0, 1.0, n))
+    return _pack(mean, log_s, quat, opacity, _sh(rng, n, deg), deg)
+
+
+def _quat_mul(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Hamilton products of quaternion arrays (w, x, y, z) [n, 4]."""
+    aw, ax, ay, az = a.T
+    bw, bx, by, bz = b.T
+    return np.stack([aw * bw - ax * bx - ay * by - az * bz, aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx, aw * bz + ax * by - ay * bx + az * bw], 1)
+
+
+def _quats_with_axis(rng, normal: np.ndarray) -> np.ndarray:
+    """Quaternions whose rotation takes the local z axis to +-normal (unit, [n, 3]),
+    spun by a uniform angle about it."""
+    n = normal * np.where(normal[:, 2:3] < 0, -1.0, 1.0)  # an ellipsoid is symmetric in its axis' sign
+    axis = np.stack([-n[:, 1], n[:, 0], np.zeros(len(n))], 1)  # e_z x n
+    s = np.linalg.norm(axis, axis=1, keepdims=True)
+    ang = np.arctan2(s[:, 0], n[:, 2])
+    axis = np.where(s > 1e-12, axis / np.maximum(s, 1e-300), np.array([1.0, 0.0, 0.0]))
+    align = np.concatenate([np.cos(ang / 2)[:, None], np.sin(ang / 2)[:, None] * axis], 1)
+    spin_a = rng.uniform(0, 2 * math.pi, len(n))
+    spin = np.stack([np.cos(spin_a / 2), np.zeros(len(n)), np.zeros(len(n)), np.sin(spin_a / 2)], 1)
+    return _quat_mul(align, spin)
+
+
+def room_scene(n: int, seed: int, deg: int = 3, half=(2.5, 1.4, 3.0)) -> Scene:
+    """An indoor room around the camera (a stand-in for the structure of trained
+    indoor fisheye scenes): 80% flat surfels on the six walls of a box of half
+    extents `half` centred at the origin (area-weighted; thin axis along the wall
+    normal tilted by N(0, 0.15) rad; in-plane log-scales ~ N(-3, 0.8), normal
+    log-scale ~ N(-5.5, 0.5); 1 cm of jitter off the wall) and 20% clutter inside
+    70% of the box (log-scales ~ N(-3, 0.7) per axis, random rotations); opacity
+    = sigmoid(N(1, 1.5)), SH of the other workloads."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hx, hy, hz = half
+    n_s = int(round(0.8 * n))
+    n_c = n - n_s
+    areas = np.array([hy * hz, hy * hz, hx * hz, hx * hz, hx * hy, hx * hy])
+    face = rng.choice(6, size=n_s, p=areas / areas.sum())
+    ax = face // 2  # 0: x walls, 1: floor / ceiling, 2: front / back
+    sign = np.where(face % 2 == 0, -1.0, 1.0)
+    h = np.array(half)
+    mean_s = rng.uniform(-1, 1, (n_s, 3)) * h
+    mean_s[np.arange(n_s), ax] = sign * h[ax] + rng.normal(0, 0.01, n_s)
+    normal = np.zeros((n_s, 3))
+    normal[np.arange(n_s), ax] = 1.0
+    normal += rng.normal(0, 0.15, (n_s, 3))
+    normal /= np.linalg.norm(normal, axis=1, keepdims=True)
+    q_s = _quats_with_axis(rng, normal)
+    log_s_s = np.stack([rng.normal(-3.0, 0.8, n_s), rng.normal(-3.0, 0.8, n_s), rng.normal(-5.5, 0.5, n_s)], 1)
+    mean_c = rng.uniform(-0.7, 0.7, (n_c, 3)) * h
+    log_s_c = rng.normal(-3.0, 0.7, (n_c, 3))
+    q_c = _quats(rng, n_c)
+    mean = np.concatenate([mean_s, mean_c])
+    log_s = np.concatenate([log_s_s, log_s_c])
+    quat = np.concatenate([q_s, q_c])
+    opacity = _sigmoid(rng.normal(1.0, 1.5, n))
     return _pack(mean, log_s, quat, opacity, _sh(rng, n, deg), deg)
 
 

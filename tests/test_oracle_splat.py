@@ -23,7 +23,7 @@ def _quat_of(rng):
     return q / np.linalg.norm(q)
 
 
-@pytest.mark.parametrize("z,s", [(3.0, 0.1), (1.0, 0.4), (10.0, 0.02)])
+@pytest.mark.parametrize("z,s", [(3.0, 0.1), (1.0, 0.25), (10.0, 0.02)])
 def test_ewa_on_axis_isotropic(z, s):
     """On the axis J = I / z, so an isotropic Gaussian projects to variance s^2 / z^2
     in both angles, whatever its rotation: the 3DGS square has half-side 3 s / z
@@ -36,7 +36,7 @@ def test_ewa_on_axis_isotropic(z, s):
     assert np.allclose(S.splat_box(cam, (0, 0, z), (s, s, s), q, 0.8, S.EWA, True), (-e, e, -e, e), rtol=1e-12)
 
 
-@pytest.mark.parametrize("z,s", [(3.0, 0.1), (1.0, 0.4), (0.5, 0.28)])  # sqrt(3) s < z: all points in front
+@pytest.mark.parametrize("z,s", [(3.0, 0.1), (1.0, 0.25), (0.5, 0.14)])  # camera outside the contour
 def test_ut_on_axis_isotropic(z, s):
     """Axis-aligned on the axis: the two sigma points along x sit at angles
     +-atan(sqrt(3) s / z), the rest at 0, so the mean angle is 0 and the variance
@@ -131,12 +131,42 @@ def test_culling():
     cam = _cam()
     s, q = (0.1, 0.1, 0.1), (1, 0, 0, 0)
     for mode in (S.EWA, S.UT):
-        assert S.splat_box(cam, (0, 0, 0.2), s, q, 0.5, mode, False) is None
-        assert S.splat_box(cam, (0, 0, 0.2000001), s, q, 0.5, mode, False) is not None
+        small = (0.04, 0.04, 0.04)  # the camera outside the contour
+        assert S.splat_box(cam, (0, 0, 0.2), small, q, 0.5, mode, False) is None
+        assert S.splat_box(cam, (0, 0, 0.2000001), small, q, 0.5, mode, False) is not None
         assert S.splat_box(cam, (0, 0, -3), s, q, 0.5, mode, False) is None
         assert S.splat_box(cam, (0, 0, 3), s, q, 0.5 * AMIN, mode, False) is None
-        assert S.splat_box(cam, (0, 0, 3), s, q, AMIN, mode, False) is not None
+        assert S.splat_box(cam, (0, 0, 3), s, q, AMIN, mode, False) is None  # contour of radius 0
+        assert S.splat_box(cam, (0, 0, 3), s, q, 1.01 * AMIN, mode, False) is not None
+        # the camera inside the contour: culled as in the PBF pipeline (lambda = 3.2 here)
+        assert S.splat_box(cam, (0, 0, 0.5), (0.2, 0.2, 0.2), q, 0.5, mode, False) is None
+        assert S.splat_box(cam, (0, 0, 0.5), (0.1, 0.1, 0.1), q, 0.5, mode, False) is not None
         assert not S.box_mask(cam, None).any()
+
+
+def test_camera_inside_matches_the_replica():
+    """The FP64 camera-inside test takes the FP32 replica's decision away from
+    the contour (|u|^2 / lambda^2 outside [0.999, 1.001])."""
+    rng = np.random.default_rng(9)
+    n = 400
+    mean = rng.normal(0, 0.6, (n, 3)).astype(np.float32)
+    scale = np.exp(rng.normal(-1.5, 0.5, (n, 3))).astype(np.float32)
+    quat = rng.standard_normal((n, 4)).astype(np.float32)
+    op = rng.uniform(0.01, 0.99, n).astype(np.float32)
+    scene = wl.Scene(mean, scale, quat, op, np.zeros((n, 1, 3), np.float32), 0)
+    cam = _cam()
+    cull = orc.replica(scene, cam)[0]
+    both = 0
+    for g in range(n):
+        mu_c, Rc = S.camera_frame(cam, mean[g])
+        u = (Rc @ S._rot(quat[g])).T @ mu_c / scale[g].astype(np.float64)
+        r = float(u @ u) / (2 * math.log(op[g] / AMIN) * 1.001)
+        if abs(r - 1) < 1e-3:
+            continue
+        inside = S.camera_inside(cam, mean[g], scale[g], quat[g], float(op[g]))
+        assert inside == bool(cull[g]), g
+        both += inside
+    assert 20 < both < n - 20
 
 
 def test_meets_on_circle():
