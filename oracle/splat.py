@@ -31,6 +31,16 @@ exactly these for |theta|, |phi| < 90 degrees, Sec. 3.3).
   the camera-inside decision is the FP32 replica's (oracle.replica), the
   precision the kernel takes it in; splat_box alone takes it in FP64.
 
+The splat alpha (the local-affine model the paper swaps in at render time,
+Sec. 4): alpha = sigma exp(-D^T Sigma_2^-1 D / 2) with Sigma_2 the EWA
+covariance above and D the ray's screen angles (atan2(x, z), atan2(y, z)) of
+its camera-frame direction minus the mean's, wrapped into [-pi, pi]; Gaussians
+below the near plane or with a singular Sigma_2 are culled. splat_render
+composites these alphas exactly as the exact renderer does (contributors with
+alpha >= alpha_min among the Gaussians associated with the pixel's tile, in
+depth-key order, alpha clamped at alpha_max, stop before T < T_min, background
+behind).
+
 Tiles: a column tile spans the angles [theta(i0), theta(i1)] of its first and
 last pixel, theta(i) = ((i + 1/2) / w - 1/2) fov_x. X0 holds the columns whose
 span meets the theta box on the circle, X1 those whose span meets the box
@@ -205,3 +215,67 @@ def scene_masks(cam, boxes, grow=0.0) -> np.ndarray:
     grow = np.broadcast_to(np.asarray(grow, np.float64), (len(boxes),))
     return np.stack([box_mask(cam, b, float(d)) for b, d in zip(boxes, grow)]) if boxes else \
         np.zeros((0, 0, 0), bool)
+
+
+def _wrap_pi(a):
+    return (a + math.pi) % TWO_PI - math.pi
+
+
+def splat_alpha(cam, mu, scale, quat, sigma, d_cam):
+    """Splat alpha (unclamped) of one Gaussian for a camera-frame ray direction."""
+    r = screen_cov(cam, mu, scale, quat, EWA)
+    if r is None:
+        return 0.0
+    c, S2 = r
+    dv = np.array([_wrap_pi(math.atan2(d_cam[0], d_cam[2]) - c[0]), _wrap_pi(math.atan2(d_cam[1], d_cam[2]) - c[1])])
+    return float(sigma) * math.exp(-0.5 * float(dv @ np.linalg.solve(S2, dv)))
+
+
+def splat_render(scene, cam, pix, mask, key, alpha_min=1.0 / 255.0, T_min=1e-4, alpha_max=0.99, margin=1e-3):
+    """Splat-alpha render of the listed pixels ([m, 2] column, row). mask: the
+    association [n, tiles_y, tiles_x]; key: depth keys [n] (ties by index); the
+    pipeline's cull is the FP32 replica's. Returns (rgb [m, 3], near [m]): near
+    marks pixels with an alpha within `margin` (relative) of alpha_min or a
+    transmittance within it of T_min, where FP32 may take the other branch."""
+    Rc = np.asarray(cam.R_cw, np.float64).reshape(3, 3)
+    o_w = -Rc.T @ np.asarray(cam.t_cw, np.float64)
+    cull = orc.replica(scene, cam, alpha_min=alpha_min)[0]
+    n = scene.n
+    live = np.zeros(n, bool)
+    centre = np.zeros((n, 2))
+    conic = np.zeros((n, 2, 2))
+    rgb = np.zeros((n, 3))
+    for g in range(n):
+        if cull[g]:
+            continue
+        r = screen_cov(cam, scene.mean[g], scene.scale[g], scene.quat[g], EWA)
+        if r is None or not np.linalg.det(r[1]) > 0:
+            continue
+        live[g] = True
+        centre[g], conic[g] = r[0], np.linalg.inv(r[1])
+        rgb[g] = orc.colour(scene.sh_degree, scene.sh[g], scene.mean[g], o_w)[0]
+    order = np.lexsort((np.arange(n), np.asarray(key, np.int64)))
+    out = np.zeros((len(pix), 3))
+    near = np.zeros(len(pix), bool)
+    bg = np.asarray(cam.bg, np.float64)
+    for m, (i, j) in enumerate(np.asarray(pix)):
+        _, d_w = orc.pixel_ray(cam, int(i), int(j))
+        d = Rc @ d_w
+        ts, ps = math.atan2(d[0], d[2]), math.atan2(d[1], d[2])
+        cand = order[live[order] & mask[order, j // 16, i // 16]]
+        dv = np.stack([_wrap_pi(ts - centre[cand, 0]), _wrap_pi(ps - centre[cand, 1])], 1)
+        q = np.einsum("ki,kij,kj->k", dv, conic[cand], dv)
+        a = np.asarray(scene.opacity, np.float64)[cand] * np.exp(-0.5 * q)
+        near[m] = bool(np.any(np.abs(a / alpha_min - 1.0) < margin))
+        T, C = 1.0, np.zeros(3)
+        for k in np.flatnonzero(a >= alpha_min):
+            al = min(a[k], alpha_max)
+            Tn = T * (1.0 - al)
+            near[m] |= abs(Tn / T_min - 1.0) < margin
+            if Tn < T_min:
+                break
+            C += T * al * rgb[cand[k]]
+            T = Tn
+        out[m] = C + T * bg
+    return out, near
+
