@@ -197,18 +197,23 @@ def run_serving(args, dev):
     return out
 
 
-ASSOC_MODES = (("pbf", 0, False), ("ewa", 1, False), ("ewa_snugbox", 1, True), ("ut", 2, False),
-               ("ut_snugbox", 2, True))
+# (name, association, SnugBox, alpha model): the association methods with the
+# exact ray integral, then the render-time splat alpha with PBF association
+# (the swap at render time) and with EWA association (splatting on the BEAP grid)
+ASSOC_MODES = (("pbf", 0, False, 0), ("ewa", 1, False, 0), ("ewa_snugbox", 1, True, 0), ("ut", 2, False, 0),
+               ("ut_snugbox", 2, True, 0), ("pbf_splat_alpha", 0, False, 1), ("ewa_splat_alpha", 1, False, 1))
 
 
 def _association_ablation(args, geer, wl, g, cams, rgb_pbf, flush, stream):
     """The association ablation: the same forward pass with the tile association
-    of PBF or of the splatting bounds (EWA / UT, 3-sigma square or SnugBox), on
-    the bench scene and on an indoor room of the same size (wall surfels and
-    clutter around the camera). Per method: associated (tile, Gaussian) pairs
-    per tile, the forward stages' times (CUDA events, L2 flushed between steps)
-    and the render's PSNR / SSIM against PBF's (what the splatting bounds lose:
-    contributions above alpha_min on tiles their boxes miss)."""
+    of PBF or of the splatting bounds (EWA / UT, 3-sigma square or SnugBox), and
+    with the render-time splat alpha in place of the ray integral, on the bench
+    scene and on an indoor room of the same size (wall surfels and clutter
+    around the camera). Per method: associated (tile, Gaussian) pairs per tile,
+    the forward stages' times (CUDA events, L2 flushed between steps) and the
+    render's PSNR / SSIM against the exact PBF render (what the splatting bounds
+    lose: contributions above alpha_min on tiles their boxes miss; what the
+    splat alpha changes)."""
     room = geer.Gaussians.from_scene(wl.room_scene(g.n, 6, g.sh_degree))
     tiles = sum(math.ceil(c.width / 16) * math.ceil(c.height / 16) for c in cams)
     return {"tiles": tiles, "steps": 10,
@@ -221,8 +226,8 @@ def _ablate_scene(geer, g, cams, rgb_pbf, flush, stream, tiles):
     import torch
     out = {"modes": {}}
     ref = None
-    for name, mode, snug in ASSOC_MODES:
-        rr = geer.Renderer(cams, g.n, g.sh_degree, params=geer.params_c(assoc=mode, snugbox=snug))
+    for name, mode, snug, alpha in ASSOC_MODES:
+        rr = geer.Renderer(cams, g.n, g.sh_degree, params=geer.params_c(assoc=mode, snugbox=snug, alpha_model=alpha))
         rr.prepare(g)
         img = torch.empty_like(rgb_pbf)
         evs = []

@@ -98,17 +98,30 @@ typedef struct {
  * integral. */
 enum { GEER_ASSOC_PBF = 0, GEER_ASSOC_EWA = 1, GEER_ASSOC_UT = 2 };
 
+/* Per-ray alpha models (Sec. 4, local affine approximation vs projective-exact
+ * integral). GEER_ALPHA_EXACT: the closed-form ray integral (Sec. 3.1).
+ * GEER_ALPHA_SPLAT: the local-affine splat of EWA (App. A) on the BEAP screen,
+ * alpha = min(alpha_max, sigma exp(-D^T Sigma_2^-1 D / 2)) with D the ray's
+ * screen angles (atan2(x, z), atan2(y, z)) minus the mean's (wrapped into
+ * [-pi, pi]) and Sigma_2 the EWA covariance of GEER_ASSOC_EWA; Gaussians with
+ * z <= 0.2 are culled (the splat divides by z). Render-time only: forward
+ * renders take it, geer_render_bwd returns GEER_ERR_UNSUPPORTED. It combines
+ * with any association method (with PBF, the paper's render-time swap; with
+ * EWA, splatting on the BEAP grid). */
+enum { GEER_ALPHA_EXACT = 0, GEER_ALPHA_SPLAT = 1 };
+
 /* Rendering parameters. tile_w = tile_h = 16 (BEAP tiles of 16 x 16 rays,
  * each tile a camera sub-frustum, Sec. 3.2). alpha_min: contributions below it
  * are skipped; alpha_max: alpha clamp; T_min: a ray stops before the
  * contributor that would take its transmittance below it (3DGS conventions
  * 1/255, 0.99, 1e-4). lambda_pad: relative padding of the per-Gaussian PBF
  * contour lambda^2 = 2 ln(sigma/alpha_min) (default 1e-3). assoc: a
- * GEER_ASSOC_* method (default PBF); snugbox: 0 or 1, used by EWA and UT. */
+ * GEER_ASSOC_* method (default PBF); snugbox: 0 or 1, used by EWA and UT;
+ * alpha_model: GEER_ALPHA_EXACT (default) or GEER_ALPHA_SPLAT. */
 typedef struct {
     int32_t tile_w, tile_h;
     float alpha_min, T_min, alpha_max, lambda_pad;
-    int32_t assoc, snugbox;
+    int32_t assoc, snugbox, alpha_model;
 } geer_params;
 
 typedef struct geer_workspace geer_workspace;
@@ -116,7 +129,7 @@ typedef struct geer_workspace geer_workspace;
 /* Human-readable name of a status code. Never returns NULL. */
 const char *geer_status_string(geer_status s);
 
-/* Fill *p with the defaults (16, 16, 1/255, 1e-4, 0.99, 1e-3, PBF, 0). */
+/* Fill *p with the defaults (16, 16, 1/255, 1e-4, 0.99, 1e-3, PBF, 0, EXACT). */
 geer_status geer_default_params(geer_params *p);
 
 /* Device bytes needed for a workspace rendering `n_cams` cameras (whose sizes
@@ -183,7 +196,8 @@ geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *strea
 /* Render every BEAP ray (Algorithm 1 per-CSF loop: Cano_Ray, Dist,
  * BlendInOrder): o_u, d_u = W d, m_u = o_u x d_u, kappa = |m_u|^2/|d_u|^2,
  * alpha = min(alpha_max, sigma exp(-kappa/2)) (Sec. 3.1), composited front to
- * back in depth order (App. B.1 colour equation) with early termination.
+ * back in depth order (App. B.1 colour equation) with early termination
+ * (with params alpha_model GEER_ALPHA_SPLAT, alpha is the EWA splat instead).
  * rgb: device [sum of h*w over cameras][3] f32, cameras in order, row-major.
  * T_final: device [sum h*w] f32 or NULL. Both caller-owned, overwritten. */
 geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void *stream);
@@ -195,7 +209,9 @@ geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void
  * be NULL to skip; d_sh 16-byte aligned). accumulate != 0: added (+=) to the
  * buffers' contents; accumulate == 0: written, every row (Gaussians without a
  * gradient get zeros), the buffers' previous contents never read. Must follow
- * geer_render_fwd on the same workspace with the same Gaussians. */
+ * geer_render_fwd on the same workspace with the same Gaussians.
+ * GEER_ERR_UNSUPPORTED when the workspace's alpha_model is not
+ * GEER_ALPHA_EXACT (the splat alpha is a render-time model). */
 geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const float *dL_drgb, float *d_mean,
                             float *d_scale, float *d_quat, float *d_opacity, float *d_sh, int32_t accumulate,
                             void *stream);

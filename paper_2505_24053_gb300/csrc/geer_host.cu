@@ -392,6 +392,7 @@ geer_status check_params(const geer_params *p) {
     if (!(p->lambda_pad >= 0.0f) || !(p->lambda_pad < 1.0f)) return GEER_ERR_ARG;
     if (p->assoc != GEER_ASSOC_PBF && p->assoc != GEER_ASSOC_EWA && p->assoc != GEER_ASSOC_UT) return GEER_ERR_ARG;
     if (p->snugbox != 0 && p->snugbox != 1) return GEER_ERR_ARG;
+    if (p->alpha_model != GEER_ALPHA_EXACT && p->alpha_model != GEER_ALPHA_SPLAT) return GEER_ERR_ARG;
     return GEER_OK;
 }
 
@@ -461,6 +462,7 @@ geer_status geer_default_params(geer_params *p) {
     p->lambda_pad = 1e-3f;
     p->assoc = GEER_ASSOC_PBF;
     p->snugbox = 0;
+    p->alpha_model = GEER_ALPHA_EXACT;
     return GEER_OK;
 }
 
@@ -508,7 +510,7 @@ geer_status geer_workspace_init(void *dev_mem, size_t bytes, const geer_camera *
     ws->cap_sh_degree = sh_degree;
     ws->cap_sort_tiles = c.sort_tiles;
     ws->params = Params{params->alpha_min, params->T_min, params->alpha_max, params->lambda_pad, params->assoc,
-                        params->snugbox};
+                        params->snugbox, params->alpha_model};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -648,6 +650,7 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
                             void *stream) {
     if (!ws || !dL_drgb) return GEER_ERR_ARG;
     if (ws->stage < 3) return GEER_ERR_STATE;
+    if (ws->params.alpha_model != GEER_ALPHA_EXACT) return GEER_ERR_UNSUPPORTED;  // render-time only
     geer_status st = check_gaussians(ws, g);
     if (st != GEER_OK) return st;
     if (g->n != ws->n_gauss || g->sh_degree != ws->sh_degree) return GEER_ERR_ARG;
@@ -1115,7 +1118,7 @@ extern "C" geer_status geer_render_noalloc(const geer_gaussians *g, const geer_c
     ws.cap_sh_degree = 3;
     ws.cap_sort_tiles = c.sort_tiles;
     ws.params = Params{params->alpha_min, params->T_min, params->alpha_max, params->lambda_pad, params->assoc,
-                       params->snugbox};
+                       params->snugbox, params->alpha_model};
     ws.num_sms = S.num_sms;
     ws.sort_grid = S.num_sms * sort_blocks_per_sm();
     ws.n_cams = 1;

@@ -89,6 +89,7 @@ static_assert(sizeof(GradAcc) == 64, "grad accumulator must be 64 bytes");
 struct Params {
     float alpha_min, T_min, alpha_max, lambda_pad;
     int32_t assoc, snug;  // GEER_ASSOC_*, SnugBox flag
+    int32_t alpha_model;  // GEER_ALPHA_*
 };
 
 // PBF association ranges of a (camera, Gaussian) item, packed as u16 pairs:

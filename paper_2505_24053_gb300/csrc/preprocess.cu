@@ -189,20 +189,60 @@ __device__ Arc angle_arc(float lo, float hi) {
 // the mean's (atan2 of the cross and dot products with the offset split out,
 // so small Gaussians lose no digits); weights 1/6 each, the centre point 0 for
 // the mean and 2 for the covariance.
+// The EWA factor of Sigma_2 = sum_k f_k f_k^T: f_k = s_k J M_k, J the gradients
+// of the two screen angles at the mean (x, y, z).
+__device__ __forceinline__ void ewa_factor(float x, float y, float z, const float M[9], const float s[3], float fx[3],
+                                           float fy[3]) {
+    const float rx = 1.0f / (x * x + z * z), ry = 1.0f / (y * y + z * z);
+    const float ja0 = z * rx, ja2 = -x * rx, jb1 = z * ry, jb2 = -y * ry;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        fx[k] = s[k] * (ja0 * M[k] + ja2 * M[6 + k]);
+        fy[k] = s[k] * (jb1 * M[3 + k] + jb2 * M[6 + k]);
+    }
+}
+
+// The EWA splat of a live item for GEER_ALPHA_SPLAT: the mean's screen angles
+// and the conic Sigma_2^-1 = (A, B; B, C), out = {theta, phi, A, B, C}. The
+// determinant is the sum of the squared 2 x 2 minors of the factor
+// (Cauchy-Binet), free of the cancellation of c00 c11 - c01^2. False when
+// Sigma_2 is singular (the item is culled).
+__device__ __forceinline__ bool splat_conic(float x, float y, float z, const float M[9], const float s[3],
+                                            float out[5]) {
+    float fx[3], fy[3];
+    ewa_factor(x, y, z, M, s, fx, fy);
+    float c00 = 0.0f, c01 = 0.0f, c11 = 0.0f, det = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c00 += fx[k] * fx[k];
+        c01 += fx[k] * fy[k];
+        c11 += fy[k] * fy[k];
+        const int l = (k + 1) % 3;
+        const float mk = fx[k] * fy[l] - fy[k] * fx[l];
+        det += mk * mk;
+    }
+    if (!(det > 0.0f) || !isfinite(det)) return false;
+    const float inv = 1.0f / det;
+    out[0] = atan2f(x, z);
+    out[1] = atan2f(y, z);
+    out[2] = c11 * inv;
+    out[3] = -c01 * inv;
+    out[4] = c00 * inv;
+    return isfinite(out[2]) && isfinite(out[4]);
+}
+
 __device__ __forceinline__ void splat_arcs(int mode, int snug, float amin, float sigma, float x, float y, float z,
                                            const float M[9], const float s[3], Arc &a, Arc &a1, Arc &b, Arc &b1) {
     float tc = atan2f(x, z), pc = atan2f(y, z);
     float c00 = 0.0f, c01 = 0.0f, c11 = 0.0f;
     if (mode == GEER_ASSOC_EWA) {
-        const float rx = 1.0f / (x * x + z * z), ry = 1.0f / (y * y + z * z);
-        const float ja0 = z * rx, ja2 = -x * rx, jb1 = z * ry, jb2 = -y * ry;
+        float fx[3], fy[3];
+        ewa_factor(x, y, z, M, s, fx, fy);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float v = ja0 * M[k] + ja2 * M[6 + k], w = jb1 * M[3 + k] + jb2 * M[6 + k];
-            const float s2 = s[k] * s[k];
-            c00 += s2 * v * v;
-            c01 += s2 * v * w;
-            c11 += s2 * w * w;
+            c00 += fx[k] * fx[k];
+            c01 += fx[k] * fy[k];
+            c11 += fy[k] * fy[k];
         }
     } else {
         float dt[6], dp[6], mt = 0.0f, mp = 0.0f;
@@ -538,9 +578,11 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
                 u[k] = fdv(fa(fa(fm(M[k], m0), fm(M[3 + k], m1)), fm(M[6 + k], m2)), sc[k]);
             float ou2 = fa(fa(fm(u[0], u[0]), fm(u[1], u[1])), fm(u[2], u[2]));
             if (!(ou2 > lam2)) live = false;
-            // the splatting bounds project through z: their near plane as well
-            if (p.assoc != GEER_ASSOC_PBF && !(m2 > kSplatNear)) live = false;
+            // the splatting bounds and the splat alpha project through z: their near plane as well
+            if ((p.assoc != GEER_ASSOC_PBF || p.alpha_model != GEER_ALPHA_EXACT) && !(m2 > kSplatNear)) live = false;
         }
+        float sp[5];  // GEER_ALPHA_SPLAT: the splat's centre and conic
+        if (live && p.alpha_model != GEER_ALPHA_EXACT && !splat_conic(m0, m1, m2, M, sc, sp)) live = false;
         if (live) {
             Arc A, B, A1, B1;
             if (p.assoc == GEER_ASSOC_PBF) {
@@ -591,14 +633,22 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
             key[idx] = __float_as_uint(dist);
             ranges[idx] = make_uint4((uint32_t)rg[0] | ((uint32_t)rg[1] << 16), (uint32_t)rg[2] | ((uint32_t)rg[3] << 16),
                                      (uint32_t)rg[4] | ((uint32_t)rg[5] << 16), (uint32_t)rg[6] | ((uint32_t)rg[7] << 16));
-            // render record: W = S^-1 M^T (camera frame), o_u = -W mu_c = -u
+            // render record: W = S^-1 M^T (camera frame), o_u = -W mu_c = -u; for the
+            // splat alpha, W[0..4] = the splat's centre and conic instead
+            if (p.alpha_model == GEER_ALPHA_EXACT) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float inv = 1.0f / sc[k];
-                r.W[3 * k + 0] = M[k] * inv;
-                r.W[3 * k + 1] = M[3 + k] * inv;
-                r.W[3 * k + 2] = M[6 + k] * inv;
-                r.ou[k] = -u[k];
+                for (int k = 0; k < 3; ++k) {
+                    float inv = 1.0f / sc[k];
+                    r.W[3 * k + 0] = M[k] * inv;
+                    r.W[3 * k + 1] = M[3 + k] * inv;
+                    r.W[3 * k + 2] = M[6 + k] * inv;
+                    r.ou[k] = -u[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) r.W[k] = k < 5 ? sp[k] : 0.0f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) r.ou[k] = 0.0f;
             }
             r.log2_sigma = log2f(sigma);
         } else if (g < n) {

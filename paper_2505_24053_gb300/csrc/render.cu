@@ -72,6 +72,24 @@ __device__ __forceinline__ Eval evaluate(const float4 &a, const float4 &b, const
     return v;
 }
 
+// The splat alpha (GEER_ALPHA_SPLAT, the local-affine model of EWA): the record
+// holds the mean's screen angles and the conic (a = theta, phi, A, B; b.x = C);
+// (ts, ps) are the ray's screen angles (atan2(x, z), atan2(y, z)). The exponent
+// argument is log2(sigma) - D^T conic D log2(e) / 2 with D wrapped into
+// [-pi, pi]. Only arg and hit are set (the forward uses nothing else).
+__device__ __forceinline__ Eval evaluate_splat(const float4 &a, const float4 &b, const float4 &e, float ts, float ps,
+                                               float log2_amin) {
+    constexpr float kTwoPi = 6.28318530717959f, kInvTwoPi = 0.159154943091895f;
+    float dt = ts - a.x, dp = ps - a.y;
+    dt = fmaf(-kTwoPi, rintf(dt * kInvTwoPi), dt);
+    dp = fmaf(-kTwoPi, rintf(dp * kInvTwoPi), dp);
+    Eval v{};
+    const float q = fmaf(a.z * dt, dt, fmaf(2.0f * a.w * dt, dp, b.x * dp * dp));
+    v.arg = fmaf(q, kNegHalfLog2e, e.x);
+    v.hit = !(v.arg < log2_amin);
+    return v;
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -197,7 +215,9 @@ struct FwdRay {
 // back until it terminates. On return sm.maxlast / sm.walkpos hold the tile's
 // walk record: [sr.x, walkpos) of the super-tile list holds tile-list entries
 // 0 .. maxlast - 1.
-template <int kThreads, int BATCH>
+// SPLAT: the splat alpha (GEER_ALPHA_SPLAT) in place of the ray integral;
+// (dx, dy) then carry the ray's screen angles.
+template <int kThreads, int BATCH, bool SPLAT>
 __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, const uint32_t *__restrict__ svals,
                                              const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
                                              const Params &p, const float4 &col, const float4 &row, int cx, int cy,
@@ -239,7 +259,8 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                     const float4 b = sm.rec[(j + u) * 4 + 1];  // W11 W12 W20 W21
                     const float4 c = sm.rec[(j + u) * 4 + 2];  // W22 ou0 ou1 ou2
                     e[u] = sm.rec[(j + u) * 4 + 3];            // log2 sigma, r, g, b
-                    v[u] = evaluate(a, b, c, e[u], dx, dy, dz, log2_amin);
+                    v[u] = SPLAT ? evaluate_splat(a, b, e[u], dx, dy, log2_amin)
+                                 : evaluate(a, b, c, e[u], dx, dy, dz, log2_amin);
                 }
                 // after the group's record loads (a byte store may alias them); the
                 // same value from every lane of the warp: no race
@@ -270,7 +291,8 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                 const float4 b = sm.rec[j * 4 + 1];
                 const float4 c = sm.rec[j * 4 + 2];
                 const float4 e = sm.rec[j * 4 + 3];
-                const Eval v = evaluate(a, b, c, e, dx, dy, dz, log2_amin);
+                const Eval v = SPLAT ? evaluate_splat(a, b, e, dx, dy, log2_amin)
+                                     : evaluate(a, b, c, e, dx, dy, dz, log2_amin);
                 if (!v.hit) continue;
                 hit_b[j * 8] = 1;
                 const float alpha = fminf(exp2f(v.arg), p.alpha_max);
@@ -341,7 +363,7 @@ __device__ __forceinline__ bool tile_ray(const DevCam &cam, int t, int row0, con
     return true;
 }
 
-template <int ROWS, int BATCH>
+template <int ROWS, int BATCH, bool SPLAT>
 __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
                                                             const float2 *__restrict__ ptab,
                                                             const float4 *__restrict__ ttab, int S,
@@ -372,8 +394,13 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         return;
     }
     FwdRay f{1.0f, 0.0f, 0.0f, 0.0f, 0u, 0u, 0u, !tr.inside};
-    forward_walk<kThreads, BATCH>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy, tr.dz,
-                                  hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, f);
+    if (SPLAT) {  // the ray's screen angles
+        const float ts = atan2f(tr.dx, tr.dz), ps = atan2f(tr.dy, tr.dz);
+        tr.dx = ts;
+        tr.dy = ps;
+    }
+    forward_walk<kThreads, BATCH, SPLAT>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy,
+                                         tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, f);
     if (threadIdx.x == 0) tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
     if (tr.inside) {
         const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
@@ -683,10 +710,11 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
 cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_final, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
     constexpr int R = GEER_FWD_ROWS, B = GEER_FWD_BATCH;
-    launch_k(k_render_fwd<R, B>, dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile), 0, s,
+    launch_k(ws->params.alpha_model == GEER_ALPHA_EXACT ? k_render_fwd<R, B, false> : k_render_fwd<R, B, true>,
+        dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile), 0, s,
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_tile_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
-        Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, rgb, T_final,
+        ws->params, rgb, T_final,
         ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->hit_entries);
     return cudaGetLastError();
 }
@@ -705,7 +733,7 @@ cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cu
     launch_k(k_render_bwd<R, B>, dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile), 0, s,
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_bwd_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
-        Params{ws->params.alpha_min, ws->params.T_min, ws->params.alpha_max, ws->params.lambda_pad}, dL_drgb,
+        ws->params, dL_drgb,
         ws->d_Tfin, ws->d_last, ws->d_hit, ws->hit_entries, ws->d_gacc);
     return cudaGetLastError();
 }

@@ -38,7 +38,8 @@ class GaussiansC(C.Structure):
 
 class ParamsC(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("alpha_min", C.c_float), ("T_min", C.c_float),
-                ("alpha_max", C.c_float), ("lambda_pad", C.c_float), ("assoc", C.c_int32), ("snugbox", C.c_int32)]
+                ("alpha_max", C.c_float), ("lambda_pad", C.c_float), ("assoc", C.c_int32), ("snugbox", C.c_int32),
+                ("alpha_model", C.c_int32)]
 
 
 EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "geer_workspace_init",
@@ -143,14 +144,15 @@ def cameras_c(cams):
 
 
 ASSOC_PBF, ASSOC_EWA, ASSOC_UT = 0, 1, 2  # tile association methods (GEER_ASSOC_*)
+ALPHA_EXACT, ALPHA_SPLAT = 0, 1  # per-ray alpha models (GEER_ALPHA_*)
 
 
 def params_c(alpha_min=1 / 255, T_min=1e-4, alpha_max=0.99, lambda_pad=1e-3, assoc: int = ASSOC_PBF,
-             snugbox: bool = False) -> ParamsC:
+             snugbox: bool = False, alpha_model: int = ALPHA_EXACT) -> ParamsC:
     p = ParamsC()
     p.tile_w = p.tile_h = 16
     p.alpha_min, p.T_min, p.alpha_max, p.lambda_pad = alpha_min, T_min, alpha_max, lambda_pad
-    p.assoc, p.snugbox = int(assoc), int(bool(snugbox))
+    p.assoc, p.snugbox, p.alpha_model = int(assoc), int(bool(snugbox)), int(alpha_model)
     return p
 
 

@@ -13,6 +13,8 @@ tests/test_oracle_splat.py), through the C ABI.
   that tile's associated Gaussians (within 2e-4 of an admissible result, as in
   the PBF forward tests), and the gradients of a loss on those pixels match the
   oracle's (relative L2 and max error 1e-3, as in the PBF backward tests).
+- Splat alpha (render-time local-affine model): pixels within 2e-4 of the FP64
+  splat render (mean 1e-5) away from alpha_min / T_min decisions; no backward.
 """
 import math
 
@@ -148,3 +150,50 @@ def test_splat_render_and_backward_match_oracle(geer, orc, S, name, cam, mode, s
         nb = np.linalg.norm(b)
         assert nb > 0, (name, k)
         assert np.linalg.norm(a - b) / nb <= 1e-3 and np.abs(a - b).max() <= 1e-3 * np.abs(b).max(), (name, k)
+
+
+SPLAT_ALPHA_CASES = [
+    ("pinhole_pbf", wl.Camera(wl.PINHOLE, 64, 48, math.radians(70), bg=(0.2, 0.3, 0.4)), 0),
+    ("equi200_pbf", wl.Camera(wl.EQUIDISTANT, 64, 64, math.radians(200)), 0),
+    ("kb190_ewa", wl.Camera(wl.KANNALA_BRANDT, 64, 48, math.radians(190), k=wl.kb_coeffs(3)), 1),
+]
+
+
+@pytest.mark.parametrize("name,cam,assoc", SPLAT_ALPHA_CASES, ids=[c[0] for c in SPLAT_ALPHA_CASES])
+def test_splat_alpha_render_matches_oracle(geer, orc, S, name, cam, assoc):
+    """The render-time splat alpha (GEER_ALPHA_SPLAT) with PBF association (the
+    FP32 replica's, bit-exact) or EWA association (tiles where the delta
+    sandwich is ambiguous left out): every pixel within 2e-4 of the FP64 splat
+    render, mean error <= 1e-5, except pixels with an alpha or a transmittance
+    within 1e-3 (relative) of alpha_min / T_min."""
+    scene = _scene(len(name) + 11, 400, 2, near_frac=0.03, spread=3.0)
+    _, key, ranges, _ = orc.replica(scene, cam)
+    ty, tx = (cam.height + 15) // 16, (cam.width + 15) // 16
+    if assoc == 0:
+        mask = orc.assoc_mask(cam, ranges).astype(bool)
+        amb = np.zeros((ty, tx), bool)
+    else:
+        boxes = S.scene_boxes(cam, scene, assoc, False)
+        d = _delta(boxes)
+        lo, mask = S.scene_masks(cam, boxes, -d), S.scene_masks(cam, boxes, d)
+        amb = (lo != mask).any(0)
+    r = geer.Renderer([cam], scene.n, scene.sh_degree, params=geer.params_c(assoc=assoc, alpha_model=geer.ALPHA_SPLAT))
+    img = r.forward(geer.Gaussians.from_scene(scene)).cpu().numpy().astype(np.float64)
+    pix = wl.all_pixels(cam)
+    pix = pix[~amb[pix[:, 1] // 16, pix[:, 0] // 16]]
+    ref, near = S.splat_render(scene, cam, pix, mask, key)
+    err = np.abs(img.reshape(cam.height, cam.width, 3)[pix[:, 1], pix[:, 0]] - ref)[~near]
+    assert near.sum() < 0.02 * len(pix) and len(err) > cam.pixels // 2, (name, near.sum(), len(err))
+    assert err.max() <= 2e-4 and err.mean() <= 1e-5, (name, err.max(), err.mean())
+    assert np.abs(ref - np.asarray(cam.bg)).max() > 0.2, name
+
+
+def test_splat_alpha_has_no_backward(geer):
+    cam = wl.Camera(wl.PINHOLE, 32, 32, math.radians(60))
+    scene = _scene(5, 100, 0)
+    r = geer.Renderer([cam], scene.n, 0, params=geer.params_c(alpha_model=geer.ALPHA_SPLAT))
+    g = geer.Gaussians.from_scene(scene)
+    rgb = r.forward(g)
+    with pytest.raises(geer.GeerError) as e:
+        r.backward(g, torch.ones_like(rgb))
+    assert e.value.status == geer.ERR_UNSUPPORTED
