@@ -85,7 +85,7 @@ typedef struct {
  * the particle bounding frustum (Sec. 3.2), exact for the alpha_min contour.
  * GEER_ASSOC_EWA / GEER_ASSOC_UT: the splatting bounds it is compared with, a
  * box in the BEAP screen coordinates (atan2(x, z), atan2(y, z)) of the
- * Gaussian's projection, linearised at the mean (EWA, App. A) or through the
+ * Gaussian's projection, linearised at the mean (EWA, App. H) or through the
  * 7 sigma points of the unscented transform (alpha 1, beta 2, kappa 0); the
  * box is the 3-sigma square of the larger eigenvalue, or with snugbox != 0
  * the bounding box of the alpha_min ellipse, half-sides
@@ -100,7 +100,7 @@ enum { GEER_ASSOC_PBF = 0, GEER_ASSOC_EWA = 1, GEER_ASSOC_UT = 2 };
 
 /* Per-ray alpha models (Sec. 4, local affine approximation vs projective-exact
  * integral). GEER_ALPHA_EXACT: the closed-form ray integral (Sec. 3.1).
- * GEER_ALPHA_SPLAT: the local-affine splat of EWA (App. A) on the BEAP screen,
+ * GEER_ALPHA_SPLAT: the local-affine splat of EWA (App. H) on the BEAP screen,
  * alpha = min(alpha_max, sigma exp(-D^T Sigma_2^-1 D / 2)) with D the ray's
  * screen angles (atan2(x, z), atan2(y, z)) minus the mean's (wrapped into
  * [-pi, pi]) and Sigma_2 the EWA covariance of GEER_ASSOC_EWA; Gaussians with

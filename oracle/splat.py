@@ -6,7 +6,7 @@ the product path never imports it.
 The paper sets its PBF association against the projection-based bounds of EWA
 splatting and of the unscented transform (UT), either as the 3-sigma square of
 3DGS or with SnugBox, in the same pipeline (Sec. 4, association runtime table;
-App. A, EWA preliminaries). On the BEAP grid the screen coordinates of a point
+App. H, EWA splatting preliminaries). On the BEAP grid the screen coordinates of a point
 t = (x, y, z) in front of the camera are its BEAP angles
   theta = atan2(x, z), phi = atan2(y, z)
 (a BEAP ray d = (sin theta cos phi, cos theta sin phi, cos theta cos phi) has
