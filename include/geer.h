@@ -328,6 +328,64 @@ geer_status geer_adam_step(const geer_adam *hp, int64_t n, int32_t sh_degree, fl
                            const float *d_quat, const float *d_opacity, const float *d_sh, float *m, float *v,
                            float *scale, float *opacity, void *stream);
 
+/* Adaptive density control (Algorithm 2's refinement iterations, the 3DGS
+ * rules driven by the gradient of the view-space mean3D instead of the
+ * screen-space mean2D, App. G). With g = accum / denom (0 where denom = 0) and
+ * s the activated scales, a Gaussian is pruned when sigmoid(logit) <
+ * min_opacity or (max_scale > 0) max(s) > max_scale, else densified when
+ * g >= grad_threshold: cloned when max(s) <= clone_max_scale (3DGS:
+ * percent_dense x scene extent), split otherwise; else kept. */
+typedef struct {
+    float grad_threshold, clone_max_scale, min_opacity, max_scale;
+} geer_densify_params;
+
+/* The densification statistics of a step: for every Gaussian that the
+ * workspace's last geer_preprocess associated with at least one tile (any of
+ * its cameras), accum[i] += |d_mean[i]| and denom[i] += 1 (device [n] f32,
+ * caller-owned, zero at the start; n = the workspace's Gaussian count). d_mean:
+ * the step's mean gradient (geer_render_bwd); its norm is that of the
+ * view-space mean3D gradient, the world-to-camera map being rigid.
+ * Asynchronous on `stream`. */
+geer_status geer_densify_accumulate(geer_workspace *ws, const float *d_mean, float *accum, float *denom,
+                                    void *stream);
+
+/* Device scratch bytes that geer_densify_plan / geer_densify_apply need for n
+ * Gaussians. Host-only. */
+size_t geer_densify_scratch_bytes(int64_t n);
+
+/* Classify n Gaussians (log_scale [n][3], logit_opacity [n], accum, denom:
+ * device) and count the outputs: *n_out (HOST) receives the number of
+ * Gaussians after densification. The plan stays in scratch (device,
+ * caller-owned, geer_densify_scratch_bytes(n) bytes, 16-byte aligned) for
+ * geer_densify_apply. Synchronises `stream`. */
+geer_status geer_densify_plan(const geer_densify_params *hp, int64_t n, const float *log_scale,
+                              const float *logit_opacity, const float *accum, const float *denom, void *scratch,
+                              size_t scratch_bytes, int64_t *n_out, void *stream);
+
+/* Write the plan's n_out Gaussians into new arrays (device, caller-owned,
+ * disjoint from the inputs): o_mean [n_out][3], o_log_scale [n_out][3], o_quat
+ * [n_out][4], o_logit [n_out], o_sh [n_out][(deg+1)^2][3], the Adam moments
+ * o_m, o_v in geer_adam_step's layout for n_out, and (may be NULL) the
+ * activated o_scale [n_out][3] and o_opacity [n_out]. The outputs follow the
+ * originals' order, each original's outputs together: a kept or cloned
+ * Gaussian with its moments, a clone's identical copy with zero moments, a
+ * split Gaussian's two children with zero moments, child i at
+ * mean + R(q) (s * z[i]) with log-scale - ln 1.6 (3DGS: s / (0.8 N), N = 2).
+ * z: device [n][2][3] standard normals (drawn by the caller). m, v: the inputs'
+ * moments (geer_adam_step layout for n). Asynchronous on `stream`. */
+geer_status geer_densify_apply(int64_t n, int32_t sh_degree, const float *mean, const float *log_scale,
+                               const float *quat, const float *logit_opacity, const float *sh, const float *m,
+                               const float *v, const float *z, const void *scratch, size_t scratch_bytes,
+                               int64_t n_out, float *o_mean, float *o_log_scale, float *o_quat, float *o_logit,
+                               float *o_sh, float *o_m, float *o_v, float *o_scale, float *o_opacity, void *stream);
+
+/* The 3DGS opacity reset: logit_opacity <- min(logit_opacity, logit(value))
+ * (0 < value < 1), and the opacity moments (m, v in geer_adam_step's layout)
+ * of the Gaussians it lowered restart at zero; opacity (device [n], may be
+ * NULL) receives the activated values. Asynchronous on `stream`. */
+geer_status geer_opacity_reset(int64_t n, int32_t sh_degree, float value, float *logit_opacity, float *m, float *v,
+                               float *opacity, void *stream);
+
 /* Evaluation regions of the camera's native image (the paper's evaluation of
  * renders reprojected to native fisheye images, appendix on central and
  * peripheral regions): regions (device [h][w] u8, caller-owned, overwritten)

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgeer.so")
-SOURCES = ["geer_host.cu", "preprocess.cu", "sort.cu", "render.cu", "backward.cu", "remap.cu", "metrics.cu", "train.cu"]
+SOURCES = ["geer_host.cu", "preprocess.cu", "sort.cu", "render.cu", "backward.cu", "remap.cu", "metrics.cu", "train.cu", "densify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "geer_internal.cuh"
@@ -885,6 +886,68 @@ geer_status geer_adam_step(const geer_adam *hp, int64_t n, int32_t sh_degree, fl
     return cuda_status(launch_adam_gaussians(hp, n, sh_degree, mean, log_scale, quat, logit_opacity, sh, d_mean,
                                              d_scale, d_quat, d_opacity, d_sh, m, v, scale, opacity,
                                              static_cast<cudaStream_t>(stream)));
+}
+
+geer_status geer_densify_accumulate(geer_workspace *ws, const float *d_mean, float *accum, float *denom,
+                                    void *stream) {
+    if (!ws || (ws->n_gauss > 0 && (!d_mean || !accum || !denom))) return GEER_ERR_ARG;
+    if (ws->stage < 1) return GEER_ERR_STATE;  // needs a preprocess
+    return cuda_status(launch_densify_accum(ws, d_mean, accum, denom, static_cast<cudaStream_t>(stream)));
+}
+
+size_t geer_densify_scratch_bytes(int64_t n) { return n < 0 ? 0 : densify_scratch_bytes(n); }
+
+namespace {
+bool densify_params_ok(const geer_densify_params *hp) {
+    return hp && hp->grad_threshold >= 0.0f && std::isfinite(hp->grad_threshold) && hp->clone_max_scale > 0.0f &&
+           std::isfinite(hp->clone_max_scale) && hp->min_opacity > 0.0f && hp->min_opacity < 1.0f &&
+           hp->max_scale >= 0.0f && std::isfinite(hp->max_scale);
+}
+bool scratch_ok(const void *scratch, size_t bytes, int64_t n) {
+    return scratch && (reinterpret_cast<uintptr_t>(scratch) & 15) == 0 && bytes >= densify_scratch_bytes(n);
+}
+}  // namespace
+
+geer_status geer_densify_plan(const geer_densify_params *hp, int64_t n, const float *log_scale,
+                              const float *logit_opacity, const float *accum, const float *denom, void *scratch,
+                              size_t scratch_bytes, int64_t *n_out, void *stream) {
+    if (!densify_params_ok(hp) || n < 0 || n > ((int64_t)1 << 31) || !n_out || !scratch_ok(scratch, scratch_bytes, n))
+        return GEER_ERR_ARG;
+    if (n > 0 && (!log_scale || !logit_opacity || !accum || !denom)) return GEER_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto *total = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + densify_scratch_bytes(n) - 16);
+    unsigned long long h = 0;
+    if (launch_densify_plan(hp, n, log_scale, logit_opacity, accum, denom, scratch, total, s) != cudaSuccess ||
+        cudaMemcpyAsync(&h, total, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    *n_out = (int64_t)h;
+    return GEER_OK;
+}
+
+geer_status geer_densify_apply(int64_t n, int32_t sh_degree, const float *mean, const float *log_scale,
+                               const float *quat, const float *logit_opacity, const float *sh, const float *m,
+                               const float *v, const float *z, const void *scratch, size_t scratch_bytes,
+                               int64_t n_out, float *o_mean, float *o_log_scale, float *o_quat, float *o_logit,
+                               float *o_sh, float *o_m, float *o_v, float *o_scale, float *o_opacity, void *stream) {
+    if (n < 0 || n > ((int64_t)1 << 31) || n_out < 0 || n_out > 2 * n || sh_degree < 0 || sh_degree > 3 ||
+        !scratch_ok(scratch, scratch_bytes, n))
+        return GEER_ERR_ARG;
+    if (n > 0 && (!mean || !log_scale || !quat || !logit_opacity || !sh || !m || !v || !z))
+        return GEER_ERR_ARG;
+    if (n_out > 0 && (!o_mean || !o_log_scale || !o_quat || !o_logit || !o_sh || !o_m || !o_v)) return GEER_ERR_ARG;
+    return cuda_status(launch_densify_apply(n, sh_degree, mean, log_scale, quat, logit_opacity, sh, m, v, z, scratch,
+                                            n_out, o_mean, o_log_scale, o_quat, o_logit, o_sh, o_m, o_v, o_scale,
+                                            o_opacity, static_cast<cudaStream_t>(stream)));
+}
+
+geer_status geer_opacity_reset(int64_t n, int32_t sh_degree, float value, float *logit_opacity, float *m, float *v,
+                               float *opacity, void *stream) {
+    if (n < 0 || sh_degree < 0 || sh_degree > 3 || !(value > 0.0f && value < 1.0f)) return GEER_ERR_ARG;
+    if (n > 0 && (!logit_opacity || !m || !v)) return GEER_ERR_ARG;
+    // the opacity block of the moments starts at 10 n (after mean, log-scale and quaternion)
+    return cuda_status(launch_opacity_reset(n, value, logit_opacity, m + 10 * n, v + 10 * n, opacity,
+                                            static_cast<cudaStream_t>(stream)));
 }
 
 geer_status geer_native_regions(const geer_camera *cam, uint8_t *regions, void *stream) {

@@ -261,6 +261,19 @@ cudaError_t launch_adam_gaussians(const geer_adam *hp, int64_t n, int32_t sh_deg
                                   const float *d_scale, const float *d_quat, const float *d_opacity,
                                   const float *d_sh, float *m, float *v, float *scale, float *opacity,
                                   cudaStream_t s);
+size_t densify_scratch_bytes(int64_t n);
+cudaError_t launch_densify_accum(const geer_workspace *ws, const float *d_mean, float *accum, float *denom,
+                                 cudaStream_t s);
+cudaError_t launch_densify_plan(const geer_densify_params *hp, int64_t n, const float *log_scale, const float *logit,
+                                const float *accum, const float *denom, void *scratch, unsigned long long *total,
+                                cudaStream_t s);
+cudaError_t launch_densify_apply(int64_t n, int32_t sh_degree, const float *mean, const float *log_scale,
+                                 const float *quat, const float *logit, const float *sh, const float *m,
+                                 const float *v, const float *z, const void *scratch, int64_t n_out, float *o_mean,
+                                 float *o_log_scale, float *o_quat, float *o_logit, float *o_sh, float *o_m,
+                                 float *o_v, float *o_scale, float *o_opacity, cudaStream_t s);
+cudaError_t launch_opacity_reset(int64_t n, float value, float *logit, float *m_op, float *v_op, float *opacity,
+                                 cudaStream_t s);
 cudaError_t launch_image_metrics(const float *pred, const float *gt, int width, int height, const uint8_t *regions,
                                  int n_regions, double *acc, cudaStream_t s);
 int sort_blocks_per_sm();

@@ -48,7 +48,8 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_render_counts", "geer_l1_loss_grad", "geer_render_noalloc", "geer_set_camera_slots",
            "geer_enable_timing", "geer_stage_times", "geer_stage_name", "geer_remap_to_native",
            "geer_native_regions", "geer_image_metrics", "geer_native_to_beap", "geer_adam_step",
-           "geer_pair_counts", "geer_debug_render_state"]
+           "geer_pair_counts", "geer_debug_render_state", "geer_densify_accumulate", "geer_densify_scratch_bytes",
+           "geer_densify_plan", "geer_densify_apply", "geer_opacity_reset"]
 
 _lib = None
 
@@ -99,11 +100,17 @@ def lib(build_if_missing: bool = True):
         "geer_l1_loss_grad": [P, P, I64, P, P, P],
         "geer_render_noalloc": [P, P, P, P, P, P],
         "geer_set_camera_slots": [P, P, I32, P, I64, I64, P],
+        "geer_densify_accumulate": [P, P, P, P, P],
+        "geer_densify_plan": [P, I64, P, P, P, P, P, C.c_size_t, P, P],
+        "geer_densify_apply": [I64, I32, P, P, P, P, P, P, P, P, P, C.c_size_t, I64, P, P, P, P, P, P, P, P, P, P],
+        "geer_opacity_reset": [I64, I32, C.c_float, P, P, P, P, P],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
         f.restype = C.c_int
         f.argtypes = args
+    L.geer_densify_scratch_bytes.restype = C.c_size_t
+    L.geer_densify_scratch_bytes.argtypes = [I64]
     _lib = L
     return L
 
@@ -461,6 +468,64 @@ class Adam:
                                     ptr(grads["scale"]), ptr(grads["quat"]), ptr(grads["opacity"]), ptr(grads["sh"]),
                                     ptr(self.m), ptr(self.v), ptr(g.scale), ptr(g.opacity), _stream(stream)),
                "geer_adam_step")
+
+
+    def densify(self, accum: torch.Tensor, denom: torch.Tensor, z: torch.Tensor, stream=None, **hp) -> int:
+        """Densify and prune (geer_densify_plan / geer_densify_apply) with the
+        statistics accum / denom and the split normals z [n, 2, 3]: the raw
+        parameters, moments and `gaussians` are replaced by the new set.
+        Returns the new count (synchronises)."""
+        d = DensifyC(**dict(DENSIFY_DEFAULTS, **hp))
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        L = lib()
+        nbytes = L.geer_densify_scratch_bytes(self.n)
+        scratch = torch.empty(max(nbytes, 16), dtype=torch.uint8, device="cuda")
+        n_out = C.c_int64()
+        r = self.raw
+        _check(L.geer_densify_plan(C.byref(d), self.n, ptr(r["log_scale"]), ptr(r["logit_opacity"]), ptr(accum),
+                                   ptr(denom), ptr(scratch), nbytes, C.byref(n_out), _stream(stream)),
+               "geer_densify_plan")
+        no = int(n_out.value)
+        k = (self.sh_degree + 1) ** 2
+        new = {"mean": torch.empty((no, 3), device="cuda"), "log_scale": torch.empty((no, 3), device="cuda"),
+               "quat": torch.empty((no, 4), device="cuda"), "logit_opacity": torch.empty(no, device="cuda"),
+               "sh": torch.empty((no, k, 3), device="cuda")}
+        m = torch.empty(no * (11 + 3 * k), device="cuda")
+        v = torch.empty_like(m)
+        scale, opacity = torch.empty((no, 3), device="cuda"), torch.empty(no, device="cuda")
+        _check(L.geer_densify_apply(self.n, self.sh_degree, ptr(r["mean"]), ptr(r["log_scale"]), ptr(r["quat"]),
+                                    ptr(r["logit_opacity"]), ptr(r["sh"]), ptr(self.m), ptr(self.v),
+                                    ptr(z.contiguous()), ptr(scratch), nbytes, no, ptr(new["mean"]),
+                                    ptr(new["log_scale"]), ptr(new["quat"]), ptr(new["logit_opacity"]),
+                                    ptr(new["sh"]), ptr(m), ptr(v), ptr(scale), ptr(opacity), _stream(stream)),
+               "geer_densify_apply")
+        self.raw, self.m, self.v, self.n = new, m, v, no
+        self.gaussians = Gaussians(new["mean"], scale, new["quat"], opacity, new["sh"], self.sh_degree)
+        return no
+
+    def opacity_reset(self, value: float = 0.01, stream=None):
+        """3DGS opacity reset of the raw logits, their moments and `gaussians`."""
+        ptr = lambda t: C.c_void_p(t.data_ptr())
+        _check(lib().geer_opacity_reset(self.n, self.sh_degree, value, ptr(self.raw["logit_opacity"]), ptr(self.m),
+                                        ptr(self.v), ptr(self.gaussians.opacity), _stream(stream)),
+               "geer_opacity_reset")
+
+
+class DensifyC(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("clone_max_scale", C.c_float), ("min_opacity", C.c_float),
+                ("max_scale", C.c_float)]
+
+
+# 3DGS's thresholds (its gradient threshold is for mean2D; ours bounds the
+# view-space mean3D gradient norm, a different unit: tune per scene); the clone
+# scale is 3DGS's percent_dense (0.01) x the scene extent, here for a 1 m extent
+DENSIFY_DEFAULTS = dict(grad_threshold=2e-4, clone_max_scale=0.01, min_opacity=0.005, max_scale=0.0)
+
+
+def densify_accumulate(ws: "Workspace", d_mean: torch.Tensor, accum: torch.Tensor, denom: torch.Tensor, stream=None):
+    """The step's densification statistics (geer_densify_accumulate)."""
+    _check(lib().geer_densify_accumulate(ws.handle, C.c_void_p(d_mean.data_ptr()), C.c_void_p(accum.data_ptr()),
+                                         C.c_void_p(denom.data_ptr()), _stream(stream)), "geer_densify_accumulate")
 
 
 class Renderer:

@@ -87,3 +87,23 @@ def test_workspace_size_checks_arguments_on_host(geer):
     assert L.geer_bin_sort(None, None, None) == geer.ERR_ARG
     assert L.geer_render_fwd(None, None, None, None) == geer.ERR_ARG
     assert L.geer_workspace_destroy(None) == geer.ERR_ARG
+
+
+def test_densify_arguments_are_checked_on_host(geer):
+    """Density control rejects bad thresholds and scratch before any device work."""
+    L = geer.lib()
+    assert L.geer_densify_scratch_bytes(1000) >= 1000 + 16 and L.geer_densify_scratch_bytes(-1) == 0
+    n_out = C.c_int64()
+    nb = L.geer_densify_scratch_bytes(10)
+    fake = C.c_void_p(1 << 20)  # never dereferenced: every call below fails its checks first
+    for bad in (dict(grad_threshold=-1.0), dict(min_opacity=0.0), dict(min_opacity=1.0), dict(clone_max_scale=0.0),
+                dict(max_scale=-1.0)):
+        d = geer.DensifyC(**dict(geer.DENSIFY_DEFAULTS, **bad))
+        assert L.geer_densify_plan(C.byref(d), 10, fake, fake, fake, fake, fake, nb, C.byref(n_out), None) == \
+            geer.ERR_ARG, bad
+    d = geer.DensifyC(**geer.DENSIFY_DEFAULTS)
+    assert L.geer_densify_plan(C.byref(d), 10, fake, fake, fake, fake, C.c_void_p((1 << 20) + 4), nb,
+                               C.byref(n_out), None) == geer.ERR_ARG  # misaligned scratch
+    assert L.geer_densify_plan(C.byref(d), 10, fake, fake, fake, fake, fake, nb - 1, C.byref(n_out), None) == \
+        geer.ERR_ARG  # too small
+    assert L.geer_opacity_reset(10, 0, 1.5, fake, fake, fake, None, None) == geer.ERR_ARG
