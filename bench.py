@@ -557,6 +557,41 @@ def run(args):
 
     assoc = _association_ablation(args, geer, wl, g, cams, rgb, flush, stream) if not args.no_ablation else None
 
+    # a refinement iteration at this size (Algorithm 2, 3DGS density control):
+    # plan (classify + count, synchronous) and apply over the trained Gaussians,
+    # with statistics drawn so that about 10% are densified; timed on its own
+    dens = None
+    if not args.no_ablation:
+        drng = torch.Generator(device=dev).manual_seed(9)
+        accum = torch.rand(adam.n, device=dev, generator=drng) * 2.2e-4  # g >= 2e-4 for ~9%
+        denom = torch.ones(adam.n, device=dev)
+        zd = torch.randn((adam.n, 2, 3), device=dev, generator=drng)
+        n_in = adam.n
+        base = {k: v.clone() for k, v in adam.raw.items()}
+        m0, v0 = adam.m.clone(), adam.v.clone()
+        d_ms = []
+        for k in range(3 + 5):
+            adam.raw = {k2: v2.clone() for k2, v2 in base.items()}
+            adam.m, adam.v, adam.n = m0.clone(), v0.clone(), n_in
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            n_out = adam.densify(accum, denom, zd, grad_threshold=2e-4, clone_max_scale=0.08, min_opacity=0.005)
+            e1.record(stream)
+            if k >= 3:
+                d_ms.append((e0, e1))
+        torch.cuda.synchronize()
+        dms = statistics.mean(a.elapsed_time(c) for a, c in d_ms)
+        row = 4 * (11 + 3 * (scene.sh_degree + 1) ** 2)  # raw parameters, one Gaussian
+        # read: parameters + 2 moment rows + statistics and normals (4 + 4 + 24 B, plan reads 16 B) per input;
+        # written: parameters + 2 moment rows + activated scale and opacity (16 B) per output
+        dbytes = n_in * (3 * row + 48) + n_out * (3 * row + 16)
+        dens = {"ms": dms, "n_in": n_in, "n_out": n_out, "bound": "hbm", "algorithmic_bytes": dbytes,
+                "achieved": dbytes / (dms / 1e3) / 1e9, "peak": hbm_peak,
+                "frac": dbytes / (dms / 1e3) / 1e9 / hbm_peak,
+                "note": "geer_densify_plan (classify, scan, synchronous count) + geer_densify_apply + the new "
+                        "tensors' allocation, timed on its own; not in value"}
+
     remap_gbs = 24 * cam.pixels / (remap_ms / 1e3) / 1e9  # 12 B read + 12 B written per native pixel
     remap = {"ms": remap_ms, "bound": "hbm", "achieved": remap_gbs, "peak": hbm_peak, "unit": "GB/s",
              "frac": remap_gbs / hbm_peak, "algorithmic_bytes": 24 * cam.pixels,
@@ -595,6 +630,7 @@ def run(args):
             "value": pixels / (train_ms / 1e3) / 1e6, "unit": "Mpix/s", "ms": train_ms,
             "adam": {"ms": adam_ms, "bound": "hbm", "achieved": adam_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": adam_gbs / hbm_peak, "algorithmic_bytes": adam_bytes},
+            "densify": dens,
             "note": "fwd + L1 + bwd (gradients written) + one Adam step over mean, log-scale, quat, "
                     "logit-opacity and SH (geer_adam_step), timed on its own; not in value"},
         "evaluation": {
