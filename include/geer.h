@@ -372,10 +372,11 @@ geer_status geer_densify_plan(const geer_densify_params *hp, int64_t n, const fl
  * split Gaussian's two children with zero moments, child i at
  * mean + R(q) (s * z[i]) with log-scale - ln 1.6 (3DGS: s / (0.8 N), N = 2).
  * z: device [n][2][3] standard normals (drawn by the caller). m, v: the inputs'
- * moments (geer_adam_step layout for n). Asynchronous on `stream`. */
+ * moments (geer_adam_step layout for n). scratch: the plan's (apply also keeps
+ * its output offsets there). Asynchronous on `stream`. */
 geer_status geer_densify_apply(int64_t n, int32_t sh_degree, const float *mean, const float *log_scale,
                                const float *quat, const float *logit_opacity, const float *sh, const float *m,
-                               const float *v, const float *z, const void *scratch, size_t scratch_bytes,
+                               const float *v, const float *z, void *scratch, size_t scratch_bytes,
                                int64_t n_out, float *o_mean, float *o_log_scale, float *o_quat, float *o_logit,
                                float *o_sh, float *o_m, float *o_v, float *o_scale, float *o_opacity, void *stream);
 

@@ -16,7 +16,9 @@
 // The decisions are FP32 comparisons on FP32 values: accum / denom, the largest
 // log-scale against ln of the scale thresholds, the logit against
 // logit(min_opacity) (host: FP64 ln of the FP32 parameters, rounded to FP32).
-// Elementwise and HBM-bound; a thread per Gaussian.
+// HBM-bound: the statistics, classification and split children take a thread
+// per Gaussian; the copies of the parameters and moments an element-parallel
+// pass per array (coalesced reads and writes).
 #include <cmath>
 
 #include "geer_internal.cuh"
@@ -137,79 +139,90 @@ __global__ void __launch_bounds__(1024) k_densify_scan(uint32_t *__restrict__ bl
     if (t == 1023) *total = ex;
 }
 
-struct DensIn {
-    const float *mean, *log_scale, *quat, *logit, *sh, *m, *v, *z;
-};
-struct DensOut {
-    float *mean, *log_scale, *quat, *logit, *sh, *m, *v, *scale, *opacity;
-};
-
-// One output row: parameters of Gaussian g (mean and log-scale given), moments
-// of g (with_moments) or zeros.
-__device__ __forceinline__ void emit(const DensIn &in, const DensOut &out, int64_t n, int64_t no, int K3, int64_t g,
-                                     int64_t o, const float mu[3], const float ls[3], bool with_moments) {
-    // the flat group offsets of the moments: [mean 3n | log-scale 3n | quat 4n | logit n | sh K3 n]
-    const int64_t gi[5] = {0, 3 * n, 6 * n, 10 * n, 11 * n};
-    const int64_t go[5] = {0, 3 * no, 6 * no, 10 * no, 11 * no};
-    const int width[5] = {3, 3, 4, 1, K3};
-    for (int a = 0; a < 3; ++a) {
-        out.mean[3 * o + a] = mu[a];
-        out.log_scale[3 * o + a] = ls[a];
-        if (out.scale) out.scale[3 * o + a] = expf(ls[a]);
-    }
-    for (int a = 0; a < 4; ++a) out.quat[4 * o + a] = in.quat[4 * g + a];
-    const float lg = in.logit[g];
-    out.logit[o] = lg;
-    if (out.opacity) out.opacity[o] = 1.0f / (1.0f + expf(-lg));
-    for (int a = 0; a < K3; ++a) out.sh[(int64_t)K3 * o + a] = in.sh[(int64_t)K3 * g + a];
-    for (int grp = 0; grp < 5; ++grp) {
-        const int wdt = width[grp];
-        for (int a = 0; a < wdt; ++a) {
-            const int64_t src = gi[grp] + (int64_t)wdt * g + a, dst = go[grp] + (int64_t)wdt * o + a;
-            out.m[dst] = with_moments ? in.m[src] : 0.0f;
-            out.v[dst] = with_moments ? in.v[src] : 0.0f;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kDensThreads) k_densify_apply(int64_t n, int64_t no, int K3, DensIn in, DensOut out,
-                                                                const uint8_t *__restrict__ action,
-                                                                const uint32_t *__restrict__ blockoff) {
+// Each original's first output row (the block's offset from the scan plus the
+// exclusive prefix of the outputs within the block).
+__global__ void __launch_bounds__(kDensThreads) k_densify_offsets(int64_t n, const uint8_t *__restrict__ action,
+                                                                  const uint32_t *__restrict__ blockoff,
+                                                                  uint32_t *__restrict__ out_off) {
     grid_dep_sync();
     __shared__ uint32_t wsum[kDensThreads / 32];
     const int64_t g = (int64_t)blockIdx.x * kDensThreads + threadIdx.x;
-    const uint8_t a = g < n ? action[g] : kActPrune;
     uint32_t tot;
-    const uint32_t pre = block_excl(outputs_of(a), wsum, tot);
-    if (g >= n || a == kActPrune) return;
-    const int64_t o = (int64_t)blockoff[blockIdx.x] + pre;
-    if (o + (int64_t)outputs_of(a) > no) return;  // a plan that does not match: nothing written out of bounds
-    float mu[3], ls[3];
-    for (int k = 0; k < 3; ++k) {
-        mu[k] = in.mean[3 * g + k];
-        ls[k] = in.log_scale[3 * g + k];
+    const uint32_t pre = block_excl(g < n ? outputs_of(action[g]) : 0u, wsum, tot);
+    if (g < n) out_off[g] = blockoff[blockIdx.x] + pre;
+}
+
+// One array of `width` floats per Gaussian (a parameter or a moment group),
+// element-parallel so that reads and writes are coalesced: a kept Gaussian's
+// row to its output row, a clone's to both rows, a split Gaussian's to both
+// children (mean and log-scale: skip_split, written by k_densify_split).
+// zero_new: a moment group (the clone's copy and split children start at 0).
+// act 1: also write exp of the values (activated scale), 2: their sigmoid
+// (activated opacity) into aux.
+__global__ void __launch_bounds__(kDensThreads) k_densify_copy(int64_t n, int64_t no, int width,
+                                                               const float *__restrict__ src, float *__restrict__ dst,
+                                                               int zero_new, int skip_split, int act,
+                                                               float *__restrict__ aux,
+                                                               const uint8_t *__restrict__ action,
+                                                               const uint32_t *__restrict__ out_off) {
+    grid_dep_sync();
+    const int64_t idx = (int64_t)blockIdx.x * kDensThreads + threadIdx.x;
+    if (idx >= n * width) return;
+    const int64_t g = idx / width;
+    const int a = (int)(idx - g * width);
+    const uint8_t ac = action[g];
+    if (ac == kActPrune || (skip_split && ac == kActSplit)) return;
+    const int64_t o = out_off[g];
+    if (o + (int64_t)outputs_of(ac) > no) return;  // a plan that does not match: nothing written out of bounds
+    const float x = src[idx];
+    const float x0 = (zero_new && ac == kActSplit) ? 0.0f : x, x1 = zero_new ? 0.0f : x;
+    dst[o * width + a] = x0;
+    if (ac != kActKeep) dst[(o + 1) * width + a] = x1;
+    if (act && aux) {
+        const float y = act == 1 ? expf(x) : 1.0f / (1.0f + expf(-x));
+        aux[o * width + a] = y;
+        if (ac != kActKeep) aux[(o + 1) * width + a] = y;
     }
-    if (a != kActSplit) {
-        emit(in, out, n, no, K3, g, o, mu, ls, true);
-        if (a == kActClone) emit(in, out, n, no, K3, g, o + 1, mu, ls, false);
-        return;
-    }
-    // split: the rotation of the normalised quaternion, children at mu + R (s * z_i)
-    float q0 = in.quat[4 * g], q1 = in.quat[4 * g + 1], q2 = in.quat[4 * g + 2], q3 = in.quat[4 * g + 3];
+}
+
+// Split children's means and log-scales (and activated scales): child i at
+// mu + R(q) (s * z_i), log-scale - ln 1.6.
+__global__ void __launch_bounds__(kDensThreads) k_densify_split(int64_t n, int64_t no, const float *__restrict__ mean,
+                                                                const float *__restrict__ log_scale,
+                                                                const float *__restrict__ quat,
+                                                                const float *__restrict__ z,
+                                                                const uint8_t *__restrict__ action,
+                                                                const uint32_t *__restrict__ out_off,
+                                                                float *__restrict__ o_mean,
+                                                                float *__restrict__ o_log_scale,
+                                                                float *__restrict__ o_scale) {
+    grid_dep_sync();
+    const int64_t g = (int64_t)blockIdx.x * kDensThreads + threadIdx.x;
+    if (g >= n || action[g] != kActSplit) return;
+    const int64_t o = out_off[g];
+    if (o + 2 > no) return;
+    const float q0 = quat[4 * g], q1 = quat[4 * g + 1], q2 = quat[4 * g + 2], q3 = quat[4 * g + 3];
     const float qn = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
-    const float w = q0 * qn, x = q1 * qn, y = q2 * qn, z = q3 * qn;
-    const float R[9] = {1.0f - 2.0f * (y * y + z * z), 2.0f * (x * y - w * z), 2.0f * (x * z + w * y),
-                        2.0f * (x * y + w * z), 1.0f - 2.0f * (x * x + z * z), 2.0f * (y * z - w * x),
-                        2.0f * (x * z - w * y), 2.0f * (y * z + w * x), 1.0f - 2.0f * (x * x + y * y)};
-    const float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+    const float w = q0 * qn, x = q1 * qn, y = q2 * qn, zq = q3 * qn;
+    const float R[9] = {1.0f - 2.0f * (y * y + zq * zq), 2.0f * (x * y - w * zq), 2.0f * (x * zq + w * y),
+                        2.0f * (x * y + w * zq), 1.0f - 2.0f * (x * x + zq * zq), 2.0f * (y * zq - w * x),
+                        2.0f * (x * zq - w * y), 2.0f * (y * zq + w * x), 1.0f - 2.0f * (x * x + y * y)};
+    float mu[3], ls[3], s[3];
+    for (int k = 0; k < 3; ++k) {
+        mu[k] = mean[3 * g + k];
+        ls[k] = log_scale[3 * g + k];
+        s[k] = expf(ls[k]);
+    }
     constexpr float kLn16 = 0.470003629245735553f;  // ln 1.6
-    const float lsc[3] = {ls[0] - kLn16, ls[1] - kLn16, ls[2] - kLn16};
     for (int i = 0; i < 2; ++i) {
-        const float *zi = in.z + 6 * g + 3 * i;
+        const float *zi = z + 6 * g + 3 * i;
         const float t0 = s[0] * zi[0], t1 = s[1] * zi[1], t2 = s[2] * zi[2];
-        float c[3];
-        for (int k = 0; k < 3; ++k) c[k] = mu[k] + (R[3 * k] * t0 + R[3 * k + 1] * t1 + R[3 * k + 2] * t2);
-        emit(in, out, n, no, K3, g, o + i, c, lsc, false);
+        for (int k = 0; k < 3; ++k) {
+            o_mean[3 * (o + i) + k] = mu[k] + (R[3 * k] * t0 + R[3 * k + 1] * t1 + R[3 * k + 2] * t2);
+            const float lc = ls[k] - kLn16;
+            o_log_scale[3 * (o + i) + k] = lc;
+            if (o_scale) o_scale[3 * (o + i) + k] = expf(lc);
+        }
     }
 }
 
@@ -233,10 +246,10 @@ inline int64_t dens_blocks(int64_t n) { return (n + kDensThreads - 1) / kDensThr
 
 }  // namespace
 
-size_t densify_scratch_bytes(int64_t n) {
-    const int64_t nb = dens_blocks(n);
-    return (size_t)(((n + 15) / 16) * 16 + 4 * ((nb + 3) / 4) * 4 + 16);
-}
+// Scratch: action u8[n] | block sums / offsets u32[blocks] | first output row
+// u32[n] | the total (u64), each part 16-byte aligned.
+inline int64_t r16(int64_t b) { return (b + 15) / 16 * 16; }
+size_t densify_scratch_bytes(int64_t n) { return (size_t)(r16(n) + r16(4 * dens_blocks(n)) + r16(4 * n) + 16); }
 
 cudaError_t launch_densify_accum(const geer_workspace *ws, const float *d_mean, float *accum, float *denom,
                                  cudaStream_t s) {
@@ -258,7 +271,7 @@ cudaError_t launch_densify_plan(const geer_densify_params *hp, int64_t n, const 
     c.log_max = c.big ? (float)std::log((double)hp->max_scale) : 0.0f;
     const int64_t nb = dens_blocks(n);
     uint8_t *action = static_cast<uint8_t *>(scratch);
-    uint32_t *bsum = reinterpret_cast<uint32_t *>(action + ((n + 15) / 16) * 16);
+    uint32_t *bsum = reinterpret_cast<uint32_t *>(action + r16(n));
     if (n > 0)
         launch_k(k_densify_classify, dim3((unsigned)nb), dim3(kDensThreads), 0, s, c, n, log_scale, logit, accum,
                  denom, action, bsum);
@@ -268,17 +281,41 @@ cudaError_t launch_densify_plan(const geer_densify_params *hp, int64_t n, const 
 
 cudaError_t launch_densify_apply(int64_t n, int32_t sh_degree, const float *mean, const float *log_scale,
                                  const float *quat, const float *logit, const float *sh, const float *m,
-                                 const float *v, const float *z, const void *scratch, int64_t n_out, float *o_mean,
+                                 const float *v, const float *z, void *scratch, int64_t n_out, float *o_mean,
                                  float *o_log_scale, float *o_quat, float *o_logit, float *o_sh, float *o_m,
                                  float *o_v, float *o_scale, float *o_opacity, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const uint8_t *action = static_cast<const uint8_t *>(scratch);
-    const uint32_t *boff = reinterpret_cast<const uint32_t *>(action + ((n + 15) / 16) * 16);
+    const uint32_t *boff = reinterpret_cast<const uint32_t *>(action + r16(n));
+    uint32_t *off = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + r16(n) + r16(4 * dens_blocks(n)));
     const int K3 = 3 * (sh_degree + 1) * (sh_degree + 1);
-    DensIn in{mean, log_scale, quat, logit, sh, m, v, z};
-    DensOut out{o_mean, o_log_scale, o_quat, o_logit, o_sh, o_m, o_v, o_scale, o_opacity};
-    launch_k(k_densify_apply, dim3((unsigned)dens_blocks(n)), dim3(kDensThreads), 0, s, n, n_out, K3, in, out, action,
-             boff);
+    launch_k(k_densify_offsets, dim3((unsigned)dens_blocks(n)), dim3(kDensThreads), 0, s, n, action, boff, off);
+    const int64_t no = n_out;
+    // the moments' flat groups: [mean 3 | log-scale 3 | quat 4 | logit 1 | sh K3] per Gaussian
+    const int wd[5] = {3, 3, 4, 1, K3};
+    int64_t gi = 0, go = 0;
+    for (int grp = 0; grp < 5; ++grp) {
+        const int w = wd[grp];
+        const unsigned blocks = (unsigned)((n * w + kDensThreads - 1) / kDensThreads);
+        launch_k(k_densify_copy, dim3(blocks), dim3(kDensThreads), 0, s, n, no, w, m + gi, o_m + go, 1, 0, 0,
+                 (float *)nullptr, action, (const uint32_t *)off);
+        launch_k(k_densify_copy, dim3(blocks), dim3(kDensThreads), 0, s, n, no, w, v + gi, o_v + go, 1, 0, 0,
+                 (float *)nullptr, action, (const uint32_t *)off);
+        gi += w * n;
+        go += w * no;
+    }
+    const float *src[5] = {mean, log_scale, quat, logit, sh};
+    float *dst[5] = {o_mean, o_log_scale, o_quat, o_logit, o_sh};
+    float *aux[5] = {nullptr, o_scale, nullptr, o_opacity, nullptr};
+    const int act[5] = {0, 1, 0, 2, 0};
+    for (int grp = 0; grp < 5; ++grp) {
+        const int w = wd[grp];
+        const unsigned blocks = (unsigned)((n * w + kDensThreads - 1) / kDensThreads);
+        launch_k(k_densify_copy, dim3(blocks), dim3(kDensThreads), 0, s, n, no, w, src[grp], dst[grp], 0,
+                 grp < 2 ? 1 : 0, act[grp], aux[grp], action, (const uint32_t *)off);
+    }
+    launch_k(k_densify_split, dim3((unsigned)dens_blocks(n)), dim3(kDensThreads), 0, s, n, no, mean, log_scale, quat,
+             z, action, (const uint32_t *)off, o_mean, o_log_scale, o_scale);
     return cudaGetLastError();
 }
 

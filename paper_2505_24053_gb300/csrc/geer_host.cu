@@ -927,7 +927,7 @@ geer_status geer_densify_plan(const geer_densify_params *hp, int64_t n, const fl
 
 geer_status geer_densify_apply(int64_t n, int32_t sh_degree, const float *mean, const float *log_scale,
                                const float *quat, const float *logit_opacity, const float *sh, const float *m,
-                               const float *v, const float *z, const void *scratch, size_t scratch_bytes,
+                               const float *v, const float *z, void *scratch, size_t scratch_bytes,
                                int64_t n_out, float *o_mean, float *o_log_scale, float *o_quat, float *o_logit,
                                float *o_sh, float *o_m, float *o_v, float *o_scale, float *o_opacity, void *stream) {
     if (n < 0 || n > ((int64_t)1 << 31) || n_out < 0 || n_out > 2 * n || sh_degree < 0 || sh_degree > 3 ||

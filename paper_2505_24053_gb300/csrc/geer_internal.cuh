@@ -269,7 +269,7 @@ cudaError_t launch_densify_plan(const geer_densify_params *hp, int64_t n, const 
                                 cudaStream_t s);
 cudaError_t launch_densify_apply(int64_t n, int32_t sh_degree, const float *mean, const float *log_scale,
                                  const float *quat, const float *logit, const float *sh, const float *m,
-                                 const float *v, const float *z, const void *scratch, int64_t n_out, float *o_mean,
+                                 const float *v, const float *z, void *scratch, int64_t n_out, float *o_mean,
                                  float *o_log_scale, float *o_quat, float *o_logit, float *o_sh, float *o_m,
                                  float *o_v, float *o_scale, float *o_opacity, cudaStream_t s);
 cudaError_t launch_opacity_reset(int64_t n, float value, float *logit, float *m_op, float *v_op, float *opacity,
