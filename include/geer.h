@@ -40,8 +40,8 @@ typedef enum {
     GEER_ERR_ARG = 1,         /* invalid argument (null, negative size, bad camera, ...) */
     GEER_ERR_CAPACITY = 2,    /* more (tile, Gaussian) pairs than the workspace holds */
     GEER_ERR_CUDA = 3,        /* a CUDA runtime call failed */
-    GEER_ERR_TIMEOUT = 4,     /* reserved: this build has no device-side waits */
-    GEER_ERR_UNSUPPORTED = 5, /* a valid request this build does not implement */
+    GEER_ERR_TIMEOUT = 4,     /* reserved: the library has no device-side waits */
+    GEER_ERR_UNSUPPORTED = 5, /* a valid request the library does not implement */
     GEER_ERR_STATE = 6        /* call out of order (e.g. render before bin_sort) */
 } geer_status;
 
