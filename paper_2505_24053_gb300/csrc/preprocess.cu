@@ -493,7 +493,10 @@ struct PrepSh {
 #ifndef GEER_PREP_MINB
 #define GEER_PREP_MINB 3  // resident blocks per SM: caps registers at 80
 #endif
-template <int DEG>
+// SPLAT: the instance for the association ablation and the splat alpha (any
+// GEER_ASSOC_* / GEER_ALPHA_*); the PBF / exact-integral instance (SPLAT false)
+// holds none of that code.
+template <int DEG, bool SPLAT>
 __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
     const DevCam *__restrict__ cams, int ncams, const float4 *__restrict__ ttab, Params p,
     const float *__restrict__ mean, const float *__restrict__ scale, const float *__restrict__ quat,
@@ -579,13 +582,14 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
             float ou2 = fa(fa(fm(u[0], u[0]), fm(u[1], u[1])), fm(u[2], u[2]));
             if (!(ou2 > lam2)) live = false;
             // the splatting bounds and the splat alpha project through z: their near plane as well
-            if ((p.assoc != GEER_ASSOC_PBF || p.alpha_model != GEER_ALPHA_EXACT) && !(m2 > kSplatNear)) live = false;
+            if (SPLAT && (p.assoc != GEER_ASSOC_PBF || p.alpha_model != GEER_ALPHA_EXACT) && !(m2 > kSplatNear))
+                live = false;
         }
         float sp[5];  // GEER_ALPHA_SPLAT: the splat's centre and conic
-        if (live && p.alpha_model != GEER_ALPHA_EXACT && !splat_conic(m0, m1, m2, M, sc, sp)) live = false;
+        if (SPLAT && live && p.alpha_model != GEER_ALPHA_EXACT && !splat_conic(m0, m1, m2, M, sc, sp)) live = false;
         if (live) {
             Arc A, B, A1, B1;
-            if (p.assoc == GEER_ASSOC_PBF) {
+            if (!SPLAT || p.assoc == GEER_ASSOC_PBF) {
                 auto SIG = [&](int a, int b) {
                     return fa(fa(fm(s2[0], fm(M[3 * a], M[3 * b])), fm(s2[1], fm(M[3 * a + 1], M[3 * b + 1]))),
                               fm(s2[2], fm(M[3 * a + 2], M[3 * b + 2])));
@@ -635,7 +639,7 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
                                      (uint32_t)rg[4] | ((uint32_t)rg[5] << 16), (uint32_t)rg[6] | ((uint32_t)rg[7] << 16));
             // render record: W = S^-1 M^T (camera frame), o_u = -W mu_c = -u; for the
             // splat alpha, W[0..4] = the splat's centre and conic instead
-            if (p.alpha_model == GEER_ALPHA_EXACT) {
+            if (!SPLAT || p.alpha_model == GEER_ALPHA_EXACT) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     float inv = 1.0f / sc[k];
@@ -1071,15 +1075,16 @@ cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g,
     const int64_t nblk = prep_blocks(g->n);
     if (nblk == 0) return cudaSuccess;
     const Params prm = ws->params;
+    const bool splat = prm.assoc != GEER_ASSOC_PBF || prm.alpha_model != GEER_ALPHA_EXACT;
 #define GEER_PREP_LAUNCH(D)                                                                                      \
     {                                                                                                            \
         const int smem = kPrepThreads * PrepSh<D>::kStride * (int)sizeof(float);                               \
+        auto *kern = splat ? k_preprocess<D, true> : k_preprocess<D, false>;                                     \
         if (smem > 48 * 1024) {                                                                                  \
-            const cudaError_t e = cudaFuncSetAttribute(k_preprocess<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                       smem);                                                    \
+            const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);  \
             if (e != cudaSuccess) return e;                                                                      \
         }                                                                                                        \
-        launch_k(k_preprocess<D>, dim3((unsigned)nblk), dim3(kPrepThreads), smem, s, ws->d_cams, ws->n_cams,      \
+        launch_k(kern, dim3((unsigned)nblk), dim3(kPrepThreads), smem, s, ws->d_cams, ws->n_cams,                 \
                  ws->d_tile_tab, prm, g->mean, g->scale, g->quat, g->opacity, g->sh, g->n, ws->d_rec,            \
                  ws->d_ranges, ws->d_count, ws->d_key, ws->d_blocksum, nblk);                             \
     }

@@ -270,3 +270,32 @@ def test_training_with_densification(geer):
             denom = torch.zeros(adam.n, device="cuda")
     assert counts[-1] > counts[0], counts
     assert losses[-1] < 0.6 * losses[0], (losses[0], losses[-1])
+
+
+def test_densify_edge_cases(geer, DN):
+    """No Gaussians; every Gaussian pruned (no outputs); every Gaussian split
+    (twice as many, all moments zero)."""
+    dev = lambda a: torch.as_tensor(np.asarray(a, np.float32), device="cuda")
+    empty = geer.Adam(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros((0, 4)), np.zeros(0), np.zeros((0, 1, 3)), 0)
+    assert empty.densify(dev(np.zeros(0)), dev(np.zeros(0)), dev(np.zeros((0, 2, 3)))) == 0
+    rng = np.random.default_rng(2)
+    n = 700
+    mean, log_s, quat = rng.normal(0, 1, (n, 3)), np.full((n, 3), -1.0), rng.normal(0, 1, (n, 4))
+    sh = rng.normal(0, 0.3, (n, 1, 3))
+    pruned = geer.Adam(mean, log_s, quat, np.full(n, -9.0), sh, 0)
+    assert pruned.densify(dev(np.ones(n)), dev(np.ones(n)), dev(rng.standard_normal((n, 2, 3)))) == 0
+    assert pruned.gaussians.n == 0 and pruned.m.numel() == 0
+    split = geer.Adam(mean, log_s, quat, np.full(n, 2.0), sh, 0)
+    split.m.fill_(1.0)
+    z = rng.standard_normal((n, 2, 3)).astype(np.float32)
+    assert split.densify(dev(np.ones(n)), dev(np.ones(n)), dev(z), clone_max_scale=0.01) == 2 * n
+    torch.cuda.synchronize()
+    assert not split.m.any() and not split.v.any()
+    raw = {"mean": mean, "log_scale": log_s, "quat": quat, "logit_opacity": np.full(n, 2.0), "sh": sh}
+    raw = {k: v.astype(np.float32) for k, v in raw.items()}
+    zero = {k: np.zeros_like(v) for k, v in raw.items()}
+    r2, _, _, _, act = DN.apply(dict(geer.DENSIFY_DEFAULTS, clone_max_scale=0.01), raw, zero, zero, np.ones(n),
+                                np.ones(n), z)
+    assert (act == DN.SPLIT).all()
+    got = split.raw["mean"].cpu().numpy()
+    assert np.all(np.abs(got - r2["mean"]) <= 1e-6 * (1 + np.abs(r2["mean"])))
