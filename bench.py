@@ -629,10 +629,10 @@ def run(args):
                                else f"copy bandwidth, {peak_src}",
                 "work": {"evaluations": evals, "applied": applied, "walked_back": walked}}
     tiles = math.ceil(cam.width / 16) * math.ceil(cam.height / 16)
-    # preprocess, live scan, compact, 4 depth passes x 2, gather, 2 scans, emit, offsets,
+    # preprocess, live scan, compact, 4 depth passes x 2, gather, pair scan, emit, offsets,
     # super-tile sort passes x 2, render forward (+ L1 gradient, backward order, render backward,
-    # preprocess backward)
-    launches_per_step = 17 + 2 * sort_passes + (4 if have_bwd else 0)
+    # preprocess backward): 22 per training step with one super-tile pass, as the ncu launch list shows
+    launches_per_step = 16 + 2 * sort_passes + (4 if have_bwd else 0)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
