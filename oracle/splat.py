@@ -39,7 +39,10 @@ below the near plane or with a singular Sigma_2 are culled. splat_render
 composites these alphas exactly as the exact renderer does (contributors with
 alpha >= alpha_min among the Gaussians associated with the pixel's tile, in
 depth-key order, alpha clamped at alpha_max, stop before T < T_min, background
-behind).
+behind). splat_render_grad is its gradient: the compositing and the splat's
+centre and conic differentiated analytically per pixel, the map from a
+Gaussian's parameters to its centre, conic and colour by FP64 central
+differences of screen_cov and of an FP64 colour (the oracle's SH basis).
 
 Tiles: a column tile spans the angles [theta(i0), theta(i1)] of its first and
 last pixel, theta(i) = ((i + 1/2) / w - 1/2) fov_x. X0 holds the columns whose
@@ -253,7 +256,7 @@ def splat_render(scene, cam, pix, mask, key, alpha_min=1.0 / 255.0, T_min=1e-4, 
             continue
         live[g] = True
         centre[g], conic[g] = r[0], np.linalg.inv(r[1])
-        rgb[g] = orc.colour(scene.sh_degree, scene.sh[g], scene.mean[g], o_w)[0]
+        rgb[g] = _colour64(scene.sh_degree, scene.sh[g], scene.mean[g], o_w)
     order = np.lexsort((np.arange(n), np.asarray(key, np.int64)))
     out = np.zeros((len(pix), 3))
     near = np.zeros(len(pix), bool)
@@ -278,4 +281,105 @@ def splat_render(scene, cam, pix, mask, key, alpha_min=1.0 / 255.0, T_min=1e-4, 
             T = Tn
         out[m] = C + T * bg
     return out, near
+
+
+def _colour64(deg, sh, mu, o):
+    """FP64 colour max(0, sum_k Y_k(dir) sh_k + 1/2), dir = (mu - o) / |mu - o| (the
+    oracle's SH basis, pinned to scipy's harmonics)."""
+    v = np.asarray(mu, np.float64) - o
+    Y = orc.sh_basis(deg, v / np.linalg.norm(v))
+    return np.maximum(Y @ np.asarray(sh, np.float64).reshape(-1, 3) + 0.5, 0.0)
+
+
+def _splat_features(cam, mu, scale, quat, sigma_unused=None):
+    """(theta_c, phi_c, A, B, C) of one Gaussian: the EWA centre and the conic."""
+    c, S2 = screen_cov(cam, mu, scale, quat, EWA)
+    K = np.linalg.inv(S2)
+    return np.array([c[0], c[1], K[0, 0], K[0, 1], K[1, 1]])
+
+
+def splat_render_grad(scene, cam, pix, mask, key, dLdC, alpha_min=1.0 / 255.0, T_min=1e-4, alpha_max=0.99,
+                      rel_step=1e-6):
+    """Gradient of sum(dLdC * C) over the listed pixels of the splat render:
+    dict of mean [n, 3], scale [n, 3], quat [n, 4], opacity [n], sh [n, K, 3]."""
+    Rc = np.asarray(cam.R_cw, np.float64).reshape(3, 3)
+    o_w = -Rc.T @ np.asarray(cam.t_cw, np.float64)
+    cull = orc.replica(scene, cam, alpha_min=alpha_min)[0]
+    n, deg = scene.n, scene.sh_degree
+    nb = (deg + 1) ** 2
+    f64 = lambda a: np.asarray(a, np.float64)
+    live = np.zeros(n, bool)
+    feat = np.zeros((n, 5))
+    rgb = np.zeros((n, 3))
+    for g in range(n):
+        if cull[g]:
+            continue
+        r = screen_cov(cam, scene.mean[g], scene.scale[g], scene.quat[g], EWA)
+        if r is None or not np.linalg.det(r[1]) > 0:
+            continue
+        live[g] = True
+        feat[g] = _splat_features(cam, scene.mean[g], scene.scale[g], scene.quat[g])
+        rgb[g] = _colour64(deg, scene.sh[g], scene.mean[g], o_w)
+    order = np.lexsort((np.arange(n), np.asarray(key, np.int64)))
+    sig = f64(scene.opacity)
+    g_feat = np.zeros((n, 5))
+    g_sig = np.zeros(n)
+    g_rgb = np.zeros((n, 3))
+    bg = f64(cam.bg)
+    for m, (i, j) in enumerate(np.asarray(pix)):
+        _, d_w = orc.pixel_ray(cam, int(i), int(j))
+        d = Rc @ d_w
+        ts, ps = math.atan2(d[0], d[2]), math.atan2(d[1], d[2])
+        cand = order[live[order] & mask[order, j // 16, i // 16]]
+        steps = []  # (gaussian, alpha_raw, alpha, T before, d0, d1, q)
+        T = 1.0
+        for g in cand:
+            d0, d1 = _wrap_pi(ts - feat[g, 0]), _wrap_pi(ps - feat[g, 1])
+            q = feat[g, 2] * d0 * d0 + 2 * feat[g, 3] * d0 * d1 + feat[g, 4] * d1 * d1
+            ar = sig[g] * math.exp(-0.5 * q)
+            if ar < alpha_min:
+                continue
+            al = min(ar, alpha_max)
+            if T * (1 - al) < T_min:
+                break
+            steps.append((g, ar, al, T, d0, d1, q))
+            T *= 1 - al
+        gC = f64(dLdC[m])
+        S = T * bg  # what lies behind the current contributor, walking back
+        for g, ar, al, Tk, d0, d1, q in reversed(steps):
+            g_rgb[g] += Tk * al * gC
+            dLda = float(gC @ (Tk * rgb[g] - S / (1 - al)))
+            S = S + Tk * al * rgb[g]
+            if ar < alpha_max:
+                g_sig[g] += dLda * math.exp(-0.5 * q)
+                dLdq = -0.5 * dLda * ar
+                A, B, C = feat[g, 2:]
+                g_feat[g] += dLdq * np.array([-2 * (A * d0 + B * d1), -2 * (B * d0 + C * d1), d0 * d0, 2 * d0 * d1,
+                                              d1 * d1])
+    out = dict(mean=np.zeros((n, 3)), scale=np.zeros((n, 3)), quat=np.zeros((n, 4)), opacity=g_sig,
+               sh=np.zeros((n, nb, 3)))
+    for g in np.flatnonzero(live & ((np.abs(g_feat).sum(1) > 0) | (np.abs(g_rgb).sum(1) > 0))):
+        mu, s, qt, sh = f64(scene.mean[g]), f64(scene.scale[g]), f64(scene.quat[g]), f64(scene.sh[g])
+
+        def central(fun, x, k, h):
+            xp, xm = x.copy(), x.copy()
+            xp[k] += h
+            xm[k] -= h
+            return (fun(xp) - fun(xm)) / (2 * h)
+
+        for k in range(3):
+            h = rel_step * max(1.0, abs(mu[k]))
+            dfe = central(lambda x: _splat_features(cam, x, s, qt), mu, k, h)
+            dco = central(lambda x: _colour64(deg, sh, x, o_w), mu, k, h)
+            out["mean"][g, k] = g_feat[g] @ dfe + g_rgb[g] @ dco
+            h = rel_step * s[k]
+            out["scale"][g, k] = g_feat[g] @ central(lambda x: _splat_features(cam, mu, x, qt), s, k, h)
+        for k in range(4):
+            out["quat"][g, k] = g_feat[g] @ central(lambda x: _splat_features(cam, mu, s, x), qt, k, rel_step)
+        for k in range(nb):
+            for ch in range(3):
+                flat = sh.reshape(-1).copy()
+                idx = 3 * k + ch
+                out["sh"][g, k, ch] = g_rgb[g] @ central(lambda x: _colour64(deg, x, mu, o_w), flat, idx, 1e-4)
+    return out
 

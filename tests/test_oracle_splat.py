@@ -293,3 +293,52 @@ def test_splat_render_converges_to_the_exact_render():
     assert errs[0].max() < 1e-2, errs[0].max()
     assert errs[1].max() < errs[0].max() / 5 and errs[1].mean() < errs[0].mean() / 5, \
         (errs[0].max(), errs[1].max(), errs[0].mean(), errs[1].mean())
+
+
+def test_splat_render_gradient_matches_finite_differences():
+    """The splat render's gradient (analytic compositing and splat, FP64 central
+    differences for the parameter-to-splat map) equals central differences of
+    the splat render itself, parameter by parameter, on a few Gaussians and
+    pixels away from the alpha_min / T_min decisions."""
+    cam = _cam(wl.PINHOLE, 32, 32, math.radians(30))
+    rng = np.random.default_rng(12)
+    n = 5
+    z = rng.uniform(3.0, 4.0, n)
+    mean = np.stack([rng.uniform(-0.15, 0.15, n) * z, rng.uniform(-0.15, 0.15, n) * z, z], 1)
+    scale = np.exp(rng.normal(0, 0.3, (n, 3))) * 0.12
+    scene = wl.Scene(mean.astype(np.float32), scale.astype(np.float32), rng.standard_normal((n, 4)).astype(np.float32),
+                     rng.uniform(0.3, 0.8, n).astype(np.float32), rng.normal(0, 0.5, (n, 4, 3)).astype(np.float32), 1)
+    cull, key, ranges, _ = orc.replica(scene, cam)
+    mask = orc.assoc_mask(cam, ranges).astype(bool)
+    pix = wl.random_pixels(cam, 40, 3)
+    _, near = S.splat_render(scene, cam, pix, mask, key, margin=1e-2)
+    pix = pix[~near]
+    dLdC = rng.normal(0, 1, (len(pix), 3))
+    got = S.splat_render_grad(scene, cam, pix, mask, key, dLdC)
+
+    def loss(sc):
+        rgb, _ = S.splat_render(sc, cam, pix, mask, key)
+        return float((rgb * dLdC).sum())
+
+    def with_param(field, g, idx, val):
+        arrs = {f: np.asarray(getattr(scene, f), np.float64).copy() for f in ("mean", "scale", "quat", "opacity", "sh")}
+        a = arrs[field][g].reshape(-1) if field != "opacity" else arrs[field]
+        if field == "opacity":
+            a[g] = val
+        else:
+            a[idx] = val
+            arrs[field][g] = a.reshape(arrs[field][g].shape)
+        return wl.Scene(arrs["mean"], arrs["scale"], arrs["quat"], arrs["opacity"], arrs["sh"], scene.sh_degree)
+
+    checked = 0
+    for field, size in (("mean", 3), ("scale", 3), ("quat", 4), ("opacity", 1), ("sh", 12)):
+        for g in range(n):
+            for idx in range(size):
+                base = float(np.asarray(getattr(scene, field), np.float64)[g].reshape(-1)[idx]) if field != "opacity" \
+                    else float(scene.opacity[g])
+                h = 1e-5 * max(abs(base), 0.1)
+                fd = (loss(with_param(field, g, idx, base + h)) - loss(with_param(field, g, idx, base - h))) / (2 * h)
+                an = got[field][g].reshape(-1)[idx] if field != "opacity" else got["opacity"][g]
+                assert abs(an - fd) <= 1e-5 + 1e-4 * abs(fd), (field, g, idx, an, fd)
+                checked += abs(fd) > 1e-6
+    assert checked > 30
