@@ -104,10 +104,10 @@ enum { GEER_ASSOC_PBF = 0, GEER_ASSOC_EWA = 1, GEER_ASSOC_UT = 2 };
  * alpha = min(alpha_max, sigma exp(-D^T Sigma_2^-1 D / 2)) with D the ray's
  * screen angles (atan2(x, z), atan2(y, z)) minus the mean's (wrapped into
  * [-pi, pi]) and Sigma_2 the EWA covariance of GEER_ASSOC_EWA; Gaussians with
- * z <= 0.2 are culled (the splat divides by z). Render-time only: forward
- * renders take it, geer_render_bwd returns GEER_ERR_UNSUPPORTED. It combines
- * with any association method (with PBF, the paper's render-time swap; with
- * EWA, splatting on the BEAP grid). */
+ * z <= 0.2 are culled (the splat divides by z). geer_render_bwd differentiates
+ * it (the paper's training-time approximation). It combines with any
+ * association method (with PBF, the paper's swap; with EWA, splatting on the
+ * BEAP grid). */
 enum { GEER_ALPHA_EXACT = 0, GEER_ALPHA_SPLAT = 1 };
 
 /* Rendering parameters. tile_w = tile_h = 16 (BEAP tiles of 16 x 16 rays,
@@ -209,9 +209,8 @@ geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void
  * be NULL to skip; d_sh 16-byte aligned). accumulate != 0: added (+=) to the
  * buffers' contents; accumulate == 0: written, every row (Gaussians without a
  * gradient get zeros), the buffers' previous contents never read. Must follow
- * geer_render_fwd on the same workspace with the same Gaussians.
- * GEER_ERR_UNSUPPORTED when the workspace's alpha_model is not
- * GEER_ALPHA_EXACT (the splat alpha is a render-time model). */
+ * geer_render_fwd on the same workspace with the same Gaussians (and the
+ * same alpha model). */
 geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const float *dL_drgb, float *d_mean,
                             float *d_scale, float *d_quat, float *d_opacity, float *d_sh, int32_t accumulate,
                             void *stream);

@@ -1,5 +1,6 @@
 // backward.cu -- PreprocessCUDA backward (App. C): per Gaussian, sum over the
-// cameras of the chain from the render-stage accumulators to the parameters.
+// cameras of the chain from the render-stage accumulators to the parameters
+// (for the splat alpha, from its centre and conic: splat_chain).
 //
 //   o_u = -W mu_c, mu_c = R_cw mu + t:  dL/dW += dL/do_u (-mu_c)^T,
 //                                       dL/dmu += -R_cw^T W^T dL/do_u;
@@ -94,7 +95,64 @@ constexpr int kPBThreads = 64;
 #define GEER_PB_MINB 14  // resident blocks of the one-camera variant: caps registers at 72
 #endif
 
-template <int DEG, bool ONE_CAM>
+// The splat alpha's chain (GEER_ALPHA_SPLAT) from dL/d(theta_c, phi_c) and
+// dL/d(A, B, C) (the conic K = Sigma_2^-1, B its off-diagonal) to the camera-frame
+// mean, the axes M and the scales: dL/dSigma_2 = -K G K with G the symmetric
+// gradient [[gA, gB/2], [gB/2, gC]]; Sigma_2 = sum_k f_k f_k^T with
+// f_k = s_k J M_k, J the gradients of the screen angles at the mean (the EWA
+// covariance of the forward); then J and the centre (atan2(x, z), atan2(y, z))
+// differentiated with respect to the mean.
+__device__ __forceinline__ void splat_chain(const float mc[3], const float M[9], const float s[3], float gt, float gp,
+                                            float gA, float gB, float gC, float dmc[3], float dM[9], float ds[3]) {
+    const float x = mc[0], y = mc[1], z = mc[2];
+    const float qx = x * x + z * z, qy = y * y + z * z, rx = 1.0f / qx, ry = 1.0f / qy;
+    const float ja0 = z * rx, ja2 = -x * rx, jb1 = z * ry, jb2 = -y * ry;
+    float fx[3], fy[3], c00 = 0.0f, c01 = 0.0f, c11 = 0.0f, det = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        fx[k] = s[k] * (ja0 * M[k] + ja2 * M[6 + k]);
+        fy[k] = s[k] * (jb1 * M[3 + k] + jb2 * M[6 + k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c00 += fx[k] * fx[k];
+        c01 += fx[k] * fy[k];
+        c11 += fy[k] * fy[k];
+        const int l = (k + 1) % 3;
+        const float mk = fx[k] * fy[l] - fy[k] * fx[l];
+        det += mk * mk;
+    }
+    const float id = 1.0f / det;
+    const float K00 = c11 * id, K01 = -c01 * id, K11 = c00 * id;
+    // H = -K G K (symmetric): dL = tr(H dSigma_2)
+    const float G01 = 0.5f * gB;
+    const float t00 = gA * K00 + G01 * K01, t01 = gA * K01 + G01 * K11;  // (G K) rows
+    const float t10 = G01 * K00 + gC * K01, t11 = G01 * K01 + gC * K11;
+    const float h00 = -(K00 * t00 + K01 * t10), h01 = -(K00 * t01 + K01 * t11), h11 = -(K01 * t01 + K11 * t11);
+    // dL/df_k from c00 = sum fx^2, c01 = sum fx fy (both off-diagonal slots), c11 = sum fy^2
+    float dja0 = 0.0f, dja2 = 0.0f, djb1 = 0.0f, djb2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float dfx = 2.0f * (h00 * fx[k] + h01 * fy[k]);
+        const float dfy = 2.0f * (h11 * fy[k] + h01 * fx[k]);
+        ds[k] += dfx * (ja0 * M[k] + ja2 * M[6 + k]) + dfy * (jb1 * M[3 + k] + jb2 * M[6 + k]);
+        dM[k] = dfx * s[k] * ja0;
+        dM[3 + k] = dfy * s[k] * jb1;
+        dM[6 + k] = s[k] * (dfx * ja2 + dfy * jb2);
+        dja0 += dfx * s[k] * M[k];
+        dja2 += dfx * s[k] * M[6 + k];
+        djb1 += dfy * s[k] * M[3 + k];
+        djb2 += dfy * s[k] * M[6 + k];
+    }
+    const float rx2 = rx * rx, ry2 = ry * ry;
+    // J = (z, 0, -x) / (x^2 + z^2), (0, z, -y) / (y^2 + z^2); centre angles atan2(x, z), atan2(y, z)
+    dmc[0] = dja0 * (-2.0f * x * z * rx2) + dja2 * ((x * x - z * z) * rx2) + gt * z * rx;
+    dmc[1] = djb1 * (-2.0f * y * z * ry2) + djb2 * ((y * y - z * z) * ry2) + gp * z * ry;
+    dmc[2] = dja0 * ((x * x - z * z) * rx2) + dja2 * (2.0f * x * z * rx2) + djb1 * ((y * y - z * z) * ry2) +
+             djb2 * (2.0f * y * z * ry2) - gt * x * rx - gp * y * ry;
+}
+
+template <int DEG, bool ONE_CAM, bool SPLAT>
 __global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_preprocess_bwd(
     const DevCam *__restrict__ cams, int ncams, const float *__restrict__ mean, const float *__restrict__ scale,
     const float *__restrict__ quat, const float *__restrict__ sh, int64_t n, const uint32_t *__restrict__ count,
@@ -179,31 +237,36 @@ __global__ void __launch_bounds__(kPBThreads, ONE_CAM ? GEER_PB_MINB : 1) k_prep
                 for (int j = 0; j < 3; ++j)
                     M[3 * i + j] = Rc[3 * i] * R[j] + Rc[3 * i + 1] * R[3 + j] + Rc[3 * i + 2] * R[6 + j];
             }
-            const float dou[3] = {a3.y, a3.z, a3.w};
-            const float dWr[9] = {a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3.x};
-            // o_u = -W mu_c: dL/dW = dW|RC - dL/do_u mu_c^T, dL/dmu_c = -W^T dL/do_u, dL/dmu += R_cw^T dL/dmu_c
-            float dW[9], dmc[3];
+            float dmc[3], dM[9];
+            if (SPLAT) {
+                splat_chain(mc, M, s, a1.x, a1.y, a1.z, a1.w, a2.x, dmc, dM, ds);
+            } else {
+                const float dou[3] = {a3.y, a3.z, a3.w};
+                const float dWr[9] = {a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3.x};
+                // o_u = -W mu_c: dL/dW = dW|RC - dL/do_u mu_c^T, dL/dmu_c = -W^T dL/do_u
+                float dW[9];
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
+                for (int k = 0; k < 3; ++k)
 #pragma unroll
-                for (int i = 0; i < 3; ++i) dW[3 * k + i] = dWr[3 * k + i] - dou[k] * mc[i];
+                    for (int i = 0; i < 3; ++i) dW[3 * k + i] = dWr[3 * k + i] - dou[k] * mc[i];
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-                dmc[i] = -(M[3 * i] * is[0] * dou[0] + M[3 * i + 1] * is[1] * dou[1] + M[3 * i + 2] * is[2] * dou[2]);
+                for (int i = 0; i < 3; ++i)
+                    dmc[i] = -(M[3 * i] * is[0] * dou[0] + M[3 * i + 1] * is[1] * dou[1] + M[3 * i + 2] * is[2] * dou[2]);
+                // W_ki = M_ik / s_k: scales and the rotation
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float acc_s = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        acc_s += dW[3 * k + i] * M[3 * i + k];
+                        dM[3 * i + k] = dW[3 * k + i] * is[k];
+                    }
+                    ds[k] -= acc_s * is[k] * is[k];
+                }
+            }
+            // dL/dmu += R_cw^T dL/dmu_c
 #pragma unroll
             for (int j = 0; j < 3; ++j) dmu[j] += Rc[j] * dmc[0] + Rc[3 + j] * dmc[1] + Rc[6 + j] * dmc[2];
-            // W_ki = M_ik / s_k: scales and the rotation
-            float dM[9];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float acc_s = 0.0f;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    acc_s += dW[3 * k + i] * M[3 * i + k];
-                    dM[3 * i + k] = dW[3 * k + i] * is[k];
-                }
-                ds[k] -= acc_s * is[k] * is[k];
-            }
 #pragma unroll
             for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -361,15 +424,16 @@ cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians
                                   float *d_quat, float *d_opacity, float *d_sh, int accumulate, cudaStream_t s) {
     if (g->n == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((g->n + kPBThreads - 1) / kPBThreads);
+    const bool splat = ws->params.alpha_model != GEER_ALPHA_EXACT;
 #define GEER_PB_LAUNCH(D)                                                                                      \
     if (ws->n_cams == 1)                                                                                       \
-        launch_k(k_preprocess_bwd<D, true>, dim3(blocks), dim3(kPBThreads), 0, s, ws->d_cams, 1, g->mean,      \
-                 g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean, d_scale, d_quat, d_opacity,  \
-                 d_sh, accumulate);                                                                            \
+        launch_k(splat ? k_preprocess_bwd<D, true, true> : k_preprocess_bwd<D, true, false>, dim3(blocks),     \
+                 dim3(kPBThreads), 0, s, ws->d_cams, 1, g->mean, g->scale, g->quat, g->sh, g->n, ws->d_count,   \
+                 ws->d_gacc, d_mean, d_scale, d_quat, d_opacity, d_sh, accumulate);                             \
     else                                                                                                       \
-        launch_k(k_preprocess_bwd<D, false>, dim3(blocks), dim3(kPBThreads), 0, s, ws->d_cams, ws->n_cams,     \
-                 g->mean, g->scale, g->quat, g->sh, g->n, ws->d_count, ws->d_gacc, d_mean, d_scale, d_quat,    \
-                 d_opacity, d_sh, accumulate)
+        launch_k(splat ? k_preprocess_bwd<D, false, true> : k_preprocess_bwd<D, false, false>, dim3(blocks),   \
+                 dim3(kPBThreads), 0, s, ws->d_cams, ws->n_cams, g->mean, g->scale, g->quat, g->sh, g->n,       \
+                 ws->d_count, ws->d_gacc, d_mean, d_scale, d_quat, d_opacity, d_sh, accumulate)
     switch (g->sh_degree) {
         case 0: GEER_PB_LAUNCH(0); break;
         case 1: GEER_PB_LAUNCH(1); break;

@@ -651,7 +651,6 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
                             void *stream) {
     if (!ws || !dL_drgb) return GEER_ERR_ARG;
     if (ws->stage < 3) return GEER_ERR_STATE;
-    if (ws->params.alpha_model != GEER_ALPHA_EXACT) return GEER_ERR_UNSUPPORTED;  // render-time only
     geer_status st = check_gaussians(ws, g);
     if (st != GEER_OK) return st;
     if (g->n != ws->n_gauss || g->sh_degree != ws->sh_degree) return GEER_ERR_ARG;

@@ -76,7 +76,7 @@ __device__ __forceinline__ Eval evaluate(const float4 &a, const float4 &b, const
 // holds the mean's screen angles and the conic (a = theta, phi, A, B; b.x = C);
 // (ts, ps) are the ray's screen angles (atan2(x, z), atan2(y, z)). The exponent
 // argument is log2(sigma) - D^T conic D log2(e) / 2 with D wrapped into
-// [-pi, pi]. Only arg and hit are set (the forward uses nothing else).
+// [-pi, pi]. Sets arg and hit, and for the backward du0, du1 = D and kappa = q.
 __device__ __forceinline__ Eval evaluate_splat(const float4 &a, const float4 &b, const float4 &e, float ts, float ps,
                                                float log2_amin) {
     constexpr float kTwoPi = 6.28318530717959f, kInvTwoPi = 0.159154943091895f;
@@ -85,6 +85,9 @@ __device__ __forceinline__ Eval evaluate_splat(const float4 &a, const float4 &b,
     dp = fmaf(-kTwoPi, rintf(dp * kInvTwoPi), dp);
     Eval v{};
     const float q = fmaf(a.z * dt, dt, fmaf(2.0f * a.w * dt, dp, b.x * dp * dp));
+    v.du0 = dt;
+    v.du1 = dp;
+    v.kappa = q;
     v.arg = fmaf(q, kNegHalfLog2e, e.x);
     v.hit = !(v.arg < log2_amin);
     return v;
@@ -477,10 +480,16 @@ struct BwdRay {
 
 // One ray's contribution to the 16 accumulators of the Gaussian in (a, b, c, e)
 // (GradAcc order), and the step of the ray's reverse compositing state.
+// SPLAT: the splat alpha (r.dx, r.dy the ray's screen angles); its record is
+// the centre and conic, and gv[4..8] take dL/d(theta_c, phi_c, A, B, C):
+// dq/dtheta_c = -2 (A D0 + B D1), dq/dphi_c = -2 (B D0 + C D1),
+// dq/dA = D0^2, dq/dB = 2 D0 D1, dq/dC = D1^2.
+template <bool SPLAT>
 __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const float4 &b, const float4 &c,
                                              const float4 &e, float log2_amin, float alpha_max, float gv[16],
                                              bool &contrib) {
-    const Eval v = evaluate(a, b, c, e, r.dx, r.dy, r.dz, log2_amin);
+    const Eval v = SPLAT ? evaluate_splat(a, b, e, r.dx, r.dy, log2_amin)
+                         : evaluate(a, b, c, e, r.dx, r.dy, r.dz, log2_amin);
     if (!v.hit) return;
     contrib = true;
     const float ae = exp2f(v.arg);
@@ -502,6 +511,15 @@ __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const f
     if (ae < alpha_max) {
         gv[0] = fmaf(dLda, exp2f(v.kappa * kNegHalfLog2e), gv[0]);  // dL/dsigma = dL/da e^{-kappa/2}
         const float dLdk = -0.5f * dLda * ae;
+        if (SPLAT) {
+            const float d0 = v.du0, d1 = v.du1;
+            gv[4] = fmaf(-2.0f * dLdk, fmaf(a.z, d0, a.w * d1), gv[4]);
+            gv[5] = fmaf(-2.0f * dLdk, fmaf(a.w, d0, b.x * d1), gv[5]);
+            gv[6] = fmaf(dLdk, d0 * d0, gv[6]);
+            gv[7] = fmaf(2.0f * dLdk, d0 * d1, gv[7]);
+            gv[8] = fmaf(dLdk, d1 * d1, gv[8]);
+            return;
+        }
         // with g_m = 2 m_u / |d_u|^2 (dkappa/dm_u), scaled by dL/dkappa:
         //   dL/dd_u = dL/dkappa (-(2 kappa / |d_u|^2) d_u + g_m x o_u),  dL/do_u = dL/dkappa (d_u x g_m)
         const float h = 2.0f * dLdk * __fdividef(1.0f, v.dd);
@@ -522,7 +540,7 @@ __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const f
 // The tile's backward walk: its list read back to front from the walk record
 // (walk.x: super-list position just past the tile's last contributor, walk.y:
 // that contributor's list index + 1), filtered as in the forward.
-template <int kThreads, int BATCH>
+template <int kThreads, int BATCH, bool SPLAT>
 __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, float (*s_acc)[17],
                                               const uint32_t *__restrict__ svals,
                                               const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
@@ -576,7 +594,7 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
                     const float4 b = sm.rec[r * 4 + 1];
                     const float4 c = sm.rec[r * 4 + 2];
                     const float4 e = sm.rec[r * 4 + 3];
-                    ray_gradient(ray, a, b, c, e, log2_amin, p.alpha_max, gv, contrib);
+                    ray_gradient<SPLAT>(ray, a, b, c, e, log2_amin, p.alpha_max, gv, contrib);
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
                     // warp reduce-scatter of the 16 values: lane l ends with the sum of value (l >> 1)
@@ -651,7 +669,7 @@ __device__ __forceinline__ BwdRay bwd_ray(const TileRay &tr, const DevCam &cam, 
     return r;
 }
 
-template <int ROWS, int BATCH>
+template <int ROWS, int BATCH, bool SPLAT>
 __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(const DevCam *__restrict__ cams, int ncams,
                                                                            const float2 *__restrict__ ptab,
                                                                            const float4 *__restrict__ ttab, int S,
@@ -692,6 +710,11 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
         T = Tfin[pix];
         last = last_in[pix];
     }
+    if (SPLAT) {  // the ray's screen angles
+        const float ts = atan2f(tr.dx, tr.dz), ps = atan2f(tr.dy, tr.dz);
+        tr.dx = ts;
+        tr.dy = ps;
+    }
     BwdRay ray = bwd_ray(tr, cam, g0, g1, g2, T, last);
     const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
     if ((threadIdx.x & 31) == 0) atomicMax(&sm.maxlast, warp_last);
@@ -700,7 +723,7 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
     if (block_last == 0) return;
     // the forward's warp of these rays: its rows 2w, 2w + 1 of the tile
     const int fwarp = (part * ROWS * kTile + (int)threadIdx.x) >> 5;
-    backward_walk<kThreads, BATCH>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr,
+    backward_walk<kThreads, BATCH, SPLAT>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr,
                                    tile_walk[t], warp_last, block_last,
                                    hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, fwarp, ray, gacc);
 }
@@ -730,7 +753,8 @@ cudaError_t launch_expand_tiles(const geer_workspace *ws, uint32_t *count_or_off
 cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
     constexpr int R = GEER_BWD_ROWS, B = GEER_BWD_BATCH;
-    launch_k(k_render_bwd<R, B>, dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile), 0, s,
+    launch_k(ws->params.alpha_model == GEER_ALPHA_EXACT ? k_render_bwd<R, B, false> : k_render_bwd<R, B, true>,
+        dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile), 0, s,
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_bwd_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         ws->params, dL_drgb,

@@ -13,8 +13,9 @@ tests/test_oracle_splat.py), through the C ABI.
   that tile's associated Gaussians (within 2e-4 of an admissible result, as in
   the PBF forward tests), and the gradients of a loss on those pixels match the
   oracle's (relative L2 and max error 1e-3, as in the PBF backward tests).
-- Splat alpha (render-time local-affine model): pixels within 2e-4 of the FP64
-  splat render (mean 1e-5) away from alpha_min / T_min decisions; no backward.
+- Splat alpha (the local-affine model): pixels within 2e-4 of the FP64 splat
+  render (mean 1e-5) away from alpha_min / T_min decisions; its gradient within
+  1e-3 (relative L2 and max) of the FP64 oracle gradient.
 """
 import math
 
@@ -188,12 +189,66 @@ def test_splat_alpha_render_matches_oracle(geer, orc, S, name, cam, assoc):
     assert np.abs(ref - np.asarray(cam.bg)).max() > 0.2, name
 
 
-def test_splat_alpha_has_no_backward(geer):
-    cam = wl.Camera(wl.PINHOLE, 32, 32, math.radians(60))
-    scene = _scene(5, 100, 0)
-    r = geer.Renderer([cam], scene.n, 0, params=geer.params_c(alpha_model=geer.ALPHA_SPLAT))
+SPLAT_GRAD_CASES = [
+    ("pinhole_pbf", wl.Camera(wl.PINHOLE, 48, 40, math.radians(60), bg=(0.2, 0.3, 0.4))),
+    ("equi200_pbf", wl.Camera(wl.EQUIDISTANT, 48, 48, math.radians(200))),
+]
+
+
+@pytest.mark.parametrize("name,cam", SPLAT_GRAD_CASES, ids=[c[0] for c in SPLAT_GRAD_CASES])
+def test_splat_alpha_backward_matches_oracle(geer, orc, S, name, cam):
+    """geer_render_bwd with the splat alpha (the training-time approximation)
+    against the FP64 oracle gradient (pinned by finite differences): relative
+    L2 and max error 1e-3 per parameter block, as for the exact backward; pixels
+    with an alpha or transmittance within 1e-3 of alpha_min / T_min carry no
+    loss gradient."""
+    scene = _scene(len(name) + 21, 120, 1, near_frac=0.0, spread=2.0)
+    _, key, ranges, _ = orc.replica(scene, cam)
+    mask = orc.assoc_mask(cam, ranges).astype(bool)
+    pix = wl.all_pixels(cam)
+    _, near = S.splat_render(scene, cam, pix, mask, key)
+    rng = np.random.default_rng(4)
+    dL = rng.normal(0, 1, (len(pix), 3))
+    dL[near] = 0.0
+    ref = S.splat_render_grad(scene, cam, pix, mask, key, dL)
+    r = geer.Renderer([cam], scene.n, scene.sh_degree, params=geer.params_c(alpha_model=geer.ALPHA_SPLAT))
     g = geer.Gaussians.from_scene(scene)
-    rgb = r.forward(g)
-    with pytest.raises(geer.GeerError) as e:
-        r.backward(g, torch.ones_like(rgb))
-    assert e.value.status == geer.ERR_UNSUPPORTED
+    r.forward(g)
+    dev = torch.zeros((cam.pixels, 3), dtype=torch.float32, device="cuda")
+    dev[torch.as_tensor(pix[:, 1] * cam.width + pix[:, 0], device="cuda")] = torch.as_tensor(dL, dtype=torch.float32,
+                                                                                           device="cuda")
+    grads = r.backward(g, dev)
+    torch.cuda.synchronize()
+    for k in ("mean", "scale", "quat", "opacity", "sh"):
+        a = grads[k].cpu().numpy().astype(np.float64).ravel()
+        b = ref[k].ravel()
+        nb = np.linalg.norm(b)
+        assert nb > 0, (name, k)
+        rel, mx = np.linalg.norm(a - b) / nb, np.abs(a - b).max() / np.abs(b).max()
+        assert rel <= 1e-3 and mx <= 1e-3, (name, k, rel, mx)
+
+
+def test_training_with_the_splat_alpha(geer):
+    """The training-time approximation: a scene trained with the splat alpha in
+    both the forward and the backward still fits its target."""
+    cam = wl.Camera(wl.PINHOLE, 64, 48, math.radians(70))
+    rng = np.random.default_rng(8)
+    n = 300
+    mean = np.stack([rng.uniform(-1.5, 1.5, n), rng.uniform(-1.0, 1.0, n), rng.uniform(3, 5, n)], 1).astype(np.float32)
+    log_s = rng.normal(-2.0, 0.3, (n, 3)).astype(np.float32)
+    quat = rng.standard_normal((n, 4)).astype(np.float32)
+    logit = rng.normal(1.0, 0.5, n).astype(np.float32)
+    sh = rng.normal(0, 0.4, (n, 1, 3)).astype(np.float32)
+    true = geer.Gaussians(mean, np.exp(log_s), quat, 1 / (1 + np.exp(-logit)), sh, 0)
+    params = geer.params_c(alpha_model=geer.ALPHA_SPLAT)
+    r = geer.Renderer([cam], n, 0, params=params)
+    target = r.forward(true).clone()
+    adam = geer.Adam(mean + rng.normal(0, 0.05, mean.shape).astype(np.float32), log_s, quat, logit - 1.0,
+                     rng.normal(0, 0.4, sh.shape).astype(np.float32), 0, lr_mean=2e-3)
+    losses = []
+    for _ in range(80):
+        rgb = r.forward(adam.gaussians)
+        loss, dL = geer.l1_loss_grad(rgb, target)
+        losses.append(float(loss))
+        adam.step(r.backward(adam.gaussians, dL))
+    assert losses[-1] < 0.6 * losses[0], (losses[0], losses[-1])
