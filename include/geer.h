@@ -354,7 +354,7 @@ size_t geer_densify_scratch_bytes(int64_t n);
 
 /* Classify n Gaussians (log_scale [n][3], logit_opacity [n], accum, denom:
  * device) and count the outputs: *n_out (HOST) receives the number of
- * Gaussians after densification. The plan stays in scratch (device,
+ * Gaussians after densification (n <= 2^30). The plan stays in scratch (device,
  * caller-owned, geer_densify_scratch_bytes(n) bytes, 16-byte aligned) for
  * geer_densify_apply. Synchronises `stream`. */
 geer_status geer_densify_plan(const geer_densify_params *hp, int64_t n, const float *log_scale,

@@ -910,7 +910,8 @@ bool scratch_ok(const void *scratch, size_t bytes, int64_t n) {
 geer_status geer_densify_plan(const geer_densify_params *hp, int64_t n, const float *log_scale,
                               const float *logit_opacity, const float *accum, const float *denom, void *scratch,
                               size_t scratch_bytes, int64_t *n_out, void *stream) {
-    if (!densify_params_ok(hp) || n < 0 || n > ((int64_t)1 << 31) || !n_out || !scratch_ok(scratch, scratch_bytes, n))
+    // n <= 2^30: the outputs (at most 2 n) are indexed in 32 bits
+    if (!densify_params_ok(hp) || n < 0 || n > ((int64_t)1 << 30) || !n_out || !scratch_ok(scratch, scratch_bytes, n))
         return GEER_ERR_ARG;
     if (n > 0 && (!log_scale || !logit_opacity || !accum || !denom)) return GEER_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -929,7 +930,7 @@ geer_status geer_densify_apply(int64_t n, int32_t sh_degree, const float *mean, 
                                const float *v, const float *z, void *scratch, size_t scratch_bytes,
                                int64_t n_out, float *o_mean, float *o_log_scale, float *o_quat, float *o_logit,
                                float *o_sh, float *o_m, float *o_v, float *o_scale, float *o_opacity, void *stream) {
-    if (n < 0 || n > ((int64_t)1 << 31) || n_out < 0 || n_out > 2 * n || sh_degree < 0 || sh_degree > 3 ||
+    if (n < 0 || n > ((int64_t)1 << 30) || n_out < 0 || n_out > 2 * n || sh_degree < 0 || sh_degree > 3 ||
         !scratch_ok(scratch, scratch_bytes, n))
         return GEER_ERR_ARG;
     if (n > 0 && (!mean || !log_scale || !quat || !logit_opacity || !sh || !m || !v || !z))
