@@ -252,6 +252,7 @@ def test_training_with_densification(geer):
     accum = torch.zeros(adam.n, device="cuda")
     denom = torch.zeros(adam.n, device="cuda")
     losses, counts = [], [adam.n]
+    gen = torch.Generator(device="cuda").manual_seed(0)
     for it in range(1, 81):
         rgb = r.forward(adam.gaussians)
         loss, dL = geer.l1_loss_grad(rgb, target)
@@ -262,7 +263,7 @@ def test_training_with_densification(geer):
         if it % 20 == 0 and it < 80:
             avg = (accum / denom.clamp(min=1)).cpu().numpy()
             thr = float(np.quantile(avg[avg > 0], 0.8))
-            z = torch.randn((adam.n, 2, 3), device="cuda")
+            z = torch.randn((adam.n, 2, 3), device="cuda", generator=gen)
             adam.densify(accum, denom, z, grad_threshold=thr, clone_max_scale=0.15, min_opacity=0.005)
             counts.append(adam.n)
             r = geer.Renderer([cam], adam.n, 0)
