@@ -117,7 +117,11 @@ enum { GEER_ALPHA_EXACT = 0, GEER_ALPHA_SPLAT = 1 };
  * 1/255, 0.99, 1e-4). lambda_pad: relative padding of the per-Gaussian PBF
  * contour lambda^2 = 2 ln(sigma/alpha_min) (default 1e-3). assoc: a
  * GEER_ASSOC_* method (default PBF); snugbox: 0 or 1, used by EWA and UT;
- * alpha_model: GEER_ALPHA_EXACT (default) or GEER_ALPHA_SPLAT. */
+ * alpha_model: GEER_ALPHA_EXACT (default) or GEER_ALPHA_SPLAT. Calls taking
+ * params return GEER_ERR_UNSUPPORTED for tiles other than 16 x 16 and
+ * GEER_ERR_ARG for alpha_min or alpha_max outside (0, 1), alpha_max <
+ * alpha_min, T_min or lambda_pad outside [0, 1), or an unknown assoc,
+ * snugbox or alpha_model. */
 typedef struct {
     int32_t tile_w, tile_h;
     float alpha_min, T_min, alpha_max, lambda_pad;
@@ -333,7 +337,14 @@ geer_status geer_adam_step(const geer_adam *hp, int64_t n, int32_t sh_degree, fl
  * s the activated scales, a Gaussian is pruned when sigmoid(logit) <
  * min_opacity or (max_scale > 0) max(s) > max_scale, else densified when
  * g >= grad_threshold: cloned when max(s) <= clone_max_scale (3DGS:
- * percent_dense x scene extent), split otherwise; else kept. */
+ * percent_dense x scene extent), split otherwise; else kept.
+ * Errors of the calls below: GEER_ERR_ARG for invalid thresholds
+ * (grad_threshold < 0, clone_max_scale <= 0, min_opacity outside (0, 1),
+ * max_scale < 0, any of them not finite), n outside [0, 2^30], a NULL array
+ * that the sizes require, a scratch buffer misaligned or too small, n_out
+ * outside [0, 2 n]; GEER_ERR_STATE when the workspace has no preprocess yet;
+ * GEER_ERR_CUDA when a launch or a copy fails. Nothing is written on an
+ * argument error. */
 typedef struct {
     float grad_threshold, clone_max_scale, min_opacity, max_scale;
 } geer_densify_params;
@@ -382,7 +393,8 @@ geer_status geer_densify_apply(int64_t n, int32_t sh_degree, const float *mean, 
 /* The 3DGS opacity reset: logit_opacity <- min(logit_opacity, logit(value))
  * (0 < value < 1), and the opacity moments (m, v in geer_adam_step's layout)
  * of the Gaussians it lowered restart at zero; opacity (device [n], may be
- * NULL) receives the activated values. Asynchronous on `stream`. */
+ * NULL) receives the activated values. GEER_ERR_ARG for value outside (0, 1),
+ * n < 0 or NULL arrays with n > 0. Asynchronous on `stream`. */
 geer_status geer_opacity_reset(int64_t n, int32_t sh_degree, float value, float *logit_opacity, float *m, float *v,
                                float *opacity, void *stream);
 
