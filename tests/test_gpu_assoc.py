@@ -69,8 +69,10 @@ def _delta(boxes):
 
 
 MODES = [("ewa", 1, False), ("ewa_snug", 1, True), ("ut", 2, False), ("ut_snug", 2, True)]
+_R, _t = wl.pose(wl.rot_y(math.radians(25)) @ wl.rot_x(math.radians(-10)), (0.3, -0.2, 0.4))
 MASK_CAMS = [
     ("pinhole90", wl.Camera(wl.PINHOLE, 150, 100, math.radians(90))),
+    ("equi190_posed", wl.Camera(wl.EQUIDISTANT, 112, 96, math.radians(190), R_cw=_R, t_cw=_t)),
     ("equi200", wl.Camera(wl.EQUIDISTANT, 128, 120, math.radians(200))),
     ("kb190", wl.Camera(wl.KANNALA_BRANDT, 160, 120, math.radians(190), k=wl.kb_coeffs(3))),
 ]
@@ -94,7 +96,7 @@ def test_splat_masks_match_oracle(geer, orc, S, cname, cam, mname, mode, snug):
     assert not miss.any(), (cname, mname, np.flatnonzero(miss)[:5])
     assert not extra.any(), (cname, mname, np.flatnonzero(extra)[:5])
     live = np.array([b is not None for b in boxes])
-    assert live.sum() > scene.n // 4 and got.sum() > 10 * scene.n // 4
+    assert live.sum() > scene.n // 4 and got.sum() > 2 * scene.n
 
 
 
@@ -157,6 +159,7 @@ SPLAT_ALPHA_CASES = [
     ("pinhole_pbf", wl.Camera(wl.PINHOLE, 64, 48, math.radians(70), bg=(0.2, 0.3, 0.4)), 0),
     ("equi200_pbf", wl.Camera(wl.EQUIDISTANT, 64, 64, math.radians(200)), 0),
     ("kb190_ewa", wl.Camera(wl.KANNALA_BRANDT, 64, 48, math.radians(190), k=wl.kb_coeffs(3)), 1),
+    ("equi190_posed_ut", wl.Camera(wl.EQUIDISTANT, 64, 64, math.radians(190), R_cw=_R, t_cw=_t), 2),
 ]
 
 
@@ -191,6 +194,7 @@ def test_splat_alpha_render_matches_oracle(geer, orc, S, name, cam, assoc):
 
 SPLAT_GRAD_CASES = [
     ("pinhole_pbf", wl.Camera(wl.PINHOLE, 48, 40, math.radians(60), bg=(0.2, 0.3, 0.4))),
+    ("kb190_posed_pbf", wl.Camera(wl.KANNALA_BRANDT, 48, 40, math.radians(190), k=wl.kb_coeffs(3), R_cw=_R, t_cw=_t)),
     ("equi200_pbf", wl.Camera(wl.EQUIDISTANT, 48, 48, math.radians(200))),
 ]
 
