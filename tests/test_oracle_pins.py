@@ -499,3 +499,143 @@ def test_remap_of_a_linear_beap_image_is_exact(orc):
                 continue
             exp = [0.01 * u + 0.02 * v, 0.5 - 0.01 * v, 0.003 * u]
             assert np.allclose(out[j, i], exp, atol=1e-6), (i, j)
+
+
+# ---------------------------------------------------------------------------
+# The depth key (Algorithm 1 sorts by "frustum id + depth"; the depth is read as
+# the distance from the camera centre to the Gaussian's mean, since view z
+# orders Gaussians wrongly beyond 90 degrees off axis). The replica's FP32 key
+# decides every pixel's compositing order on both sides, so it is pinned here
+# against the geometry alone and against an order-sensitive image.
+
+_U32 = 2.0 ** -24
+
+
+def _posed_camera(rng, model, fov_deg, w=40, h=36):
+    R_wc = wl.rot_y(rng.uniform(-math.pi, math.pi)) @ wl.rot_x(rng.uniform(-0.6, 0.6)) @ wl.rot_z(
+        rng.uniform(-0.5, 0.5))
+    centre = rng.uniform(-4, 4, 3)
+    R, t = wl.pose(R_wc, centre)
+    return wl.Camera(model, w, h, math.radians(fov_deg), R_cw=R, t_cw=t), centre
+
+
+def _key_bound(R, t, mu, D):
+    """Error bound of an FP32 evaluation of |R mu + t| against the FP64 distance D
+    from mu to the camera centre o = -R^T t: each component of R mu + t is a
+    sum of four rounded terms (gamma_4 of their magnitudes), R differs from a
+    rotation by its FP32 rounding (|I - R R^T| |t| and the spread of R's
+    singular values times D), and the norm adds three roundings of D."""
+    R64, t64, mu64 = R.astype(np.float64), t.astype(np.float64), mu.astype(np.float64)
+    g4 = 4 * _U32 / (1 - 4 * _U32)
+    comp = g4 * (np.abs(mu64) @ np.abs(R64).T + np.abs(t64)[None, :])
+    E = np.eye(3) - R64 @ R64.T
+    sv = np.linalg.svd(R64, compute_uv=False)
+    rot = np.linalg.norm(E, 2) * np.linalg.norm(t64) + max(abs(sv[0] - 1), abs(sv[-1] - 1)) * D
+    return np.linalg.norm(comp, axis=1) + rot + 3 * _U32 * D
+
+
+def _key_violations(keys_f32, R, t, mu):
+    o = -R.astype(np.float64).T @ t.astype(np.float64)
+    D = np.linalg.norm(mu.astype(np.float64) - o[None, :], axis=1)
+    err = np.abs(keys_f32.astype(np.float64) - D)
+    return err > _key_bound(R, t, mu, D), err / np.spacing(keys_f32).astype(np.float64)
+
+
+@pytest.mark.parametrize("model,fov", [(wl.EQUIDISTANT, 200), (wl.EQUIDISTANT, 210), (wl.KANNALA_BRANDT, 190),
+                                       (wl.PINHOLE, 90)])
+def test_depth_key_is_distance_to_camera_centre(orc, model, fov):
+    """For posed cameras (rotated, translated; fields of view up to 210 degrees)
+    and Gaussians all around the camera centre, behind it included, the replica's
+    key equals the FP64 distance |mu - o| (o = -R_cw^T t_cw, the camera centre)
+    within the FP32 error bound of its evaluation. View z, a dropped t_cw and a
+    transposed R_cw each violate it."""
+    rng = np.random.default_rng(1000 + fov + model)
+    cam, centre = _posed_camera(rng, model, fov, w=40, h=36 if model != wl.KANNALA_BRANDT else 30)
+    if model == wl.KANNALA_BRANDT:
+        cam.k = wl.kb_coeffs(5)
+    n = 4000
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    mu = (centre[None, :] + d * rng.uniform(0.3, 30.0, (n, 1))).astype(np.float32)
+    scene = wl.Scene(mu, np.full((n, 3), 0.02, np.float32), np.tile(np.float32([[1, 0, 0, 0]]), (n, 1)),
+                     np.full(n, 0.8, np.float32), np.zeros((n, 1, 3), np.float32), 0)
+    cull, key, _, _ = orc.replica(scene, cam)
+    live = cull == 0
+    assert live.sum() == n  # none inside its contour, all opaque enough
+    keys = key.view(np.float32)
+    bad, ulps = _key_violations(keys, cam.R_cw, cam.t_cw, mu)
+    assert not bad.any(), f"{int(bad.sum())} keys off the distance (max {ulps.max():.1f} ulp)"
+    assert np.median(ulps) <= 1.0
+    # behind-the-camera Gaussians exist and are keyed by their distance, not their z
+    mc = mu.astype(np.float64) @ cam.R_cw.astype(np.float64).T + cam.t_cw.astype(np.float64)
+    assert (mc[:, 2] < 0).sum() > n // 4
+
+    # planted mistakes in the key alone fail the same check
+    Rf, tf = cam.R_cw.astype(np.float32), cam.t_cw.astype(np.float32)
+    m = mu @ Rf.T + tf
+    planted = {
+        "view z": m[:, 2].astype(np.float32),
+        "no t_cw": np.linalg.norm(mu @ Rf.T, axis=1).astype(np.float32),
+        "R_cw transposed": np.linalg.norm(mu @ Rf + tf, axis=1).astype(np.float32),
+    }
+    for name, k in planted.items():
+        assert _key_violations(k, cam.R_cw, cam.t_cw, mu)[0].mean() > 0.5, name
+
+
+def _ray_pair_scene(o, d, t_near, t_far, rgb_near, rgb_far, sigma=0.9, r=0.05):
+    """Two isotropic Gaussians centred on the ray o + t d (t_near < t_far)."""
+    mu = np.stack([o + t_near * d, o + t_far * d]).astype(np.float32)
+    dc = (np.stack([rgb_near, rgb_far]) - 0.5) * 2 * math.sqrt(math.pi)
+    return wl.Scene(mu, np.full((2, 3), r, np.float32), np.float32([[1, 0, 0, 0], [0.6, 0.0, 0.8, 0.0]]),
+                    np.full(2, sigma, np.float32), dc.reshape(2, 1, 3).astype(np.float32), 0)
+
+
+def _composite_expected(scene, o, d, bg, alpha_max=0.99):
+    """App. B.1's colour equation over the two Gaussians in the order of their
+    distance along the ray, with alpha = min(alpha_max, sigma exp(-D^2 / (2 r^2)))
+    from the point-line distance D (App. B.3 Theorem, isotropic case)."""
+    mu = scene.mean.astype(np.float64)
+    t = (mu - o[None, :]) @ d
+    order = np.argsort(t)
+    C, T = np.zeros(3), 1.0
+    for g in order:
+        D = np.linalg.norm(np.cross(mu[g] - o, d))
+        a = min(alpha_max, float(scene.opacity[g]) * math.exp(-0.5 * D * D / float(scene.scale[g, 0]) ** 2))
+        colour = scene.sh[g, 0].astype(np.float64) * 0.5 / math.sqrt(math.pi) + 0.5
+        C += T * a * colour
+        T *= 1 - a
+    return C + T * np.asarray(bg, np.float64), T
+
+
+@pytest.mark.parametrize("theta_px", [39, 41, 1])
+def test_depth_order_decides_the_composited_colour(orc, theta_px):
+    """Two nearly opaque Gaussians on one ray of a rotated, translated 210 degree
+    camera, the ray 92.5 to 102.5 degrees off the optical axis (beside and behind
+    the image plane): the nearer one's colour dominates, as App. B.1's front-to-back
+    equation gives. View z orders this pair the other way round, and an image
+    composited in that order is far from the expected one."""
+    rng = np.random.default_rng(77 + theta_px)
+    cam, _ = _posed_camera(rng, wl.EQUIDISTANT, 210, w=42, h=20)
+    cam.bg = (0.2, 0.3, 0.9)
+    i, j = theta_px, 10
+    o, d = orc.pixel_ray(cam, i, j)
+    d = d / np.linalg.norm(d)
+    dc_ = d @ cam.R_cw.astype(np.float64).T  # ray direction in the camera frame
+    assert dc_[2] < 0 and abs(math.atan2(dc_[0], dc_[2])) > math.radians(92)
+    scene = _ray_pair_scene(o, d, 1.5, 3.0, np.array([0.95, 0.05, 0.05]), np.array([0.05, 0.95, 0.05]))
+    expected, T = _composite_expected(scene, o, d, cam.bg)
+    pix = np.array([[i, j]], np.int32)
+    rep = orc.replica(scene, cam)
+    out = orc.render_pixels(scene, cam, pix, rep=rep)
+    assert out["ncontrib"][0] == 2
+    assert np.allclose(out["rgb"][0], expected, atol=1e-9)
+    assert math.isclose(out["T"][0], T, abs_tol=1e-12)
+    assert expected[0] > 0.85 > expected[1]  # the near (red) Gaussian dominates
+
+    # the view-z key orders the pair the other way round here, and that image fails
+    mc = scene.mean.astype(np.float64) @ cam.R_cw.astype(np.float64).T + cam.t_cw.astype(np.float64)
+    viewz = mc[:, 2].astype(np.float32)
+    assert viewz[1] < viewz[0]  # ascending view z puts the far Gaussian first
+    planted = (rep[0], np.argsort(np.argsort(viewz)).astype(np.uint32))  # keys ordered as view z
+    out_z = orc.render_pixels(scene, cam, pix, rep=planted)
+    assert np.abs(out_z["rgb"][0] - expected).max() > 0.5
