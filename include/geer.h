@@ -423,9 +423,10 @@ geer_status geer_image_metrics(const float *pred, const float *gt, int32_t width
 /* Render one small camera without allocating anything.
  *
  * For callers that cannot call cudaMalloc or any other allocator at render
- * time: code running while a CUDA stream is being captured, plugins whose host
- * application owns all device memory, and latency-critical loops that must not
- * synchronise with an allocator. This entry point takes no workspace: every
+ * time: plugins and embedded renderers whose host application owns all device
+ * memory (and forbids a library's own allocations), and latency-critical loops
+ * that must not synchronise with an allocator or risk an out-of-memory error
+ * halfway through a frame. This entry point takes no workspace: every
  * piece of device scratch it needs lives in one fixed array inside the library
  * (28 MiB per GPU that loads the library, held until the process exits), and
  * its host-side state is static too. No paper counterpart: it is a packaging
@@ -440,7 +441,8 @@ geer_status geer_image_metrics(const float *pred, const float *gt, int32_t width
  *
  * The first call on a device sets that device up (it looks up the address of the
  * scratch array with that device current); make that first call before any
- * stream capture. Each call synchronises `stream` once, to check the pair count.
+ * stream capture. Every call synchronises `stream` once, to read the pair count
+ * back before it sorts.
  * All calls on a device share the one scratch array, which keeps the last
  * call's contents: calls that overlap on the GPU (different streams, or host
  * threads) race and corrupt each other's results; serialise them. */
