@@ -179,14 +179,20 @@ def aggregate(local_ms: float, pixels_per_rank: int, steps: int, world: int, dis
     return world * pixels_per_rank * steps / (t / 1e3) / 1e6, t
 
 
+SERVING_MODES = (("concurrent", 1, 2), ("batched", 4, 2), ("one_at_a_time", 1, 1))
+
+
 def run_serving(args, dev):
     """Workload 4: 2M-Gaussian resident scene, Poisson request stream (pinhole
     1920x1080 70 deg / equidistant 1280x1280 200 deg / Kannala-Brandt 640x480
     150 deg, random poses within 1 m), served by the engine (captured CUDA graphs)
-    with one request per launch on two concurrent streams ("concurrent", the
-    fastest configuration measured), with batches of up to four cameras on two
-    streams ("batched") and one request at a time ("one_at_a_time"), on the same
-    trace."""
+    with one request per launch on two concurrent streams ("concurrent"), with
+    batches of up to four cameras on two streams ("batched") and one request at a
+    time ("one_at_a_time"), on the same trace: at the workload's 200 req/s and
+    at a rate beyond what one request at a time sustains (--serving-sat-rate).
+    Per mode: latency percentiles, the sustained completion rate while requests
+    keep arriving, the backlog's drain time, and where latency went (queue,
+    host launch, GPU, completion noticed) at p50 / p99 / max."""
     import torch
 
     from paper_2505_24053_gb300 import geer, serve
@@ -194,30 +200,37 @@ def run_serving(args, dev):
 
     scene = wl.config_scene(4)
     g = geer.Gaussians.from_scene(scene)
-    n_req = int(round(args.serving_rate * args.serving_seconds))
-    trace = wl.serving_requests(n_req, seed=4, rate_hz=args.serving_rate)
     models = [k[0] for k in wl.SERVING_KINDS]
-
-    def requests():
-        return [serve.Request(i, t, c, kind=models.index(c.model)) for i, (t, c) in enumerate(trace)]
-
     warm = args.serving_warmup
-    out = {"trace": f"Poisson {args.serving_rate:g} req/s, {n_req} requests over {args.serving_seconds:g} s "
-                    f"(first {warm:g} s excluded), equal mix of pinhole 1920x1080 70deg, equidistant 1280x1280 "
-                    f"200deg, Kannala-Brandt 640x480 150deg; 2M Gaussians resident"}
-    for name, slots, bufs in (("concurrent", 1, 2), ("batched", 4, 2), ("one_at_a_time", 1, 1)):
+    engines = {}
+    for name, slots, bufs in SERVING_MODES:
         # capacity in (super-tile, Gaussian) pairs: ~37M for the largest request kind alone
         eng = serve.Engine(g, n_slots=slots, n_buffers=bufs, pair_capacity=slots * 60_000_000)
-        eng.calibrate(requests()[:24])
+        calib = wl.serving_requests(24, seed=4, rate_hz=args.serving_rate)
+        eng.calibrate([serve.Request(i, t, c, kind=models.index(c.model)) for i, (t, c) in enumerate(calib)])
         eng.prepare()
-        reqs = requests()
-        done = eng.run(reqs)
-        keep = [r for r in done if r.arrival >= warm]
-        st = serve.summarize(keep, max(1e-9, args.serving_seconds - warm))
-        st.update({"slots": slots, "buffers": bufs, "graphs": True, "failed": len(eng.failed)})
-        out[name] = st
-        del eng
-        torch.cuda.empty_cache()
+        engines[name] = eng
+    out = {"scene": "2M Gaussians resident (workload-1 distribution, SH degree 3)",
+           "mix": "equal mix of pinhole 1920x1080 70deg, equidistant 1280x1280 200deg, Kannala-Brandt 640x480 "
+                  "150deg, random poses within 1 m"}
+    rates = [(f"{args.serving_rate:g}_req_s", args.serving_rate, args.serving_seconds)]
+    if args.serving_sat_rate > 0:
+        rates.append((f"{args.serving_sat_rate:g}_req_s", args.serving_sat_rate, args.serving_sat_seconds))
+    for label, rate, seconds in rates:
+        n_req = int(round(rate * seconds))
+        trace = wl.serving_requests(n_req, seed=4, rate_hz=rate)
+        res = {"trace": f"Poisson {rate:g} req/s, {n_req} requests over {seconds:g} s (first {warm:g} s excluded)"}
+        for name, slots, bufs in SERVING_MODES:
+            eng = engines[name]
+            reqs = [serve.Request(i, t, c, kind=models.index(c.model)) for i, (t, c) in enumerate(trace)]
+            done = eng.run(reqs)
+            keep = [r for r in done if r.arrival >= warm]
+            st = serve.summarize(keep, max(1e-9, seconds - warm), window=(warm, seconds))
+            st.update({"slots": slots, "buffers": bufs, "graphs": True, "failed": len(eng.failed)})
+            res[name] = st
+        out[label] = res
+    engines.clear()
+    torch.cuda.empty_cache()
     return out
 
 
@@ -696,6 +709,9 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=8.0, help="serving trace length (0: skip)")
     ap.add_argument("--serving-warmup", type=float, default=1.0)
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--serving-sat-rate", type=float, default=700.0,
+                    help="second, saturating serving trace (0: skip)")
+    ap.add_argument("--serving-sat-seconds", type=float, default=5.0)
     ap.add_argument("--ref-pixels", type=int, default=24)
     ap.add_argument("--gaussians", type=int, default=None,
                     help="scene size override (the workload's distribution with fewer Gaussians; profiling)")

@@ -219,6 +219,58 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
                             float *d_scale, float *d_quat, float *d_opacity, float *d_sh, int32_t accumulate,
                             void *stream);
 
+/* The two stages of geer_render_bwd, callable apart (App. C: RenderCUDA, then
+ * PreprocessCUDA), so that a caller can combine the render stage's
+ * accumulators across processes before the second stage (a step split by tiles
+ * over several GPUs sums them with one all-reduce).
+ *
+ * geer_render_bwd_tiles: the render stage over the tiles rendered by the last
+ * geer_render_fwd. It overwrites the workspace's per-(camera, Gaussian)
+ * accumulators (16 f32 each: dL/dsigma, dL/drgb, dL/dW through d_u, dL/do_u)
+ * with the sums over those tiles' rays. dL_drgb as for geer_render_bwd.
+ * GEER_ERR_STATE before a geer_render_fwd. Asynchronous on `stream`. */
+geer_status geer_render_bwd_tiles(geer_workspace *ws, const float *dL_drgb, void *stream);
+
+/* Device address and size (in f32) of the accumulators geer_render_bwd_tiles
+ * writes: [n_cams * n][16] f32 inside the workspace memory, n the Gaussian
+ * count of the last geer_preprocess. The caller may read and overwrite them
+ * (e.g. replace them by their sum over processes) before
+ * geer_preprocess_bwd. Host-only; *acc and *n_floats must be non-NULL. */
+geer_status geer_grad_accumulators(geer_workspace *ws, float **acc, int64_t *n_floats);
+
+/* The preprocess stage: chains the accumulators to the Gaussians' parameters
+ * (through o_u = -W mu_c, W = S^-1 R^T with the normalised quaternion, and the
+ * SH colour), summing over cameras, into d_mean .. d_sh as geer_render_bwd does
+ * (same layouts, NULL to skip, accumulate as there). g: the Gaussians of the
+ * last geer_preprocess. GEER_ERR_STATE unless geer_render_bwd_tiles ran after
+ * the last geer_render_fwd. Asynchronous on `stream`. */
+geer_status geer_preprocess_bwd(geer_workspace *ws, const geer_gaussians *g, float *d_mean, float *d_scale,
+                                float *d_quat, float *d_opacity, float *d_sh, int32_t accumulate, void *stream);
+
+/* Splitting a camera set's tiles over n_parts processes (one GPU each): the
+ * (camera, tile) key space is partitioned, every process preprocesses and
+ * bins all Gaussians, renders only its own tiles (geer_set_tile_mask), and
+ * the render-stage accumulators are summed across processes before
+ * geer_preprocess_bwd, which then gives every process the full gradient.
+ *
+ * geer_tile_owners: owner[t] in [0, n_parts) for every tile of the camera set
+ * in the tile order of geer_set_cameras (cameras in order, each one's tiles row
+ * by row, ceil(w/16) x ceil(h/16)): tile (cx, cy) of camera c belongs to part
+ * (cx + cy + c) mod n_parts, diagonal stripes that give every part a share of
+ * every region of every image. owner: HOST int32 [total tiles]. Host-only (no
+ * device work); GEER_ERR_ARG for n_parts < 1 or an invalid camera. */
+geer_status geer_tile_owners(const geer_camera *cams, int32_t n_cams, int32_t n_parts, int32_t *owner);
+
+/* Restrict geer_render_fwd to the tiles t with mask[t] != 0 (HOST u8 [n_tiles],
+ * n_tiles the current camera set's tile count; NULL: all tiles). Rays of the
+ * other tiles get rgb = 0 and T_final = 0 and are skipped by the backward, so
+ * the renders of a partition of the tiles sum to the full render and their
+ * accumulators to the full accumulators. The mask stays in effect until it
+ * is replaced or the camera set changes (geer_set_cameras and
+ * geer_set_camera_slots clear it). Synchronous (copies the mask and
+ * synchronises `stream`). */
+geer_status geer_set_tile_mask(geer_workspace *ws, const uint8_t *mask, int64_t n_tiles, void *stream);
+
 /* Synchronise `stream`, then read and clear the device status word: GEER_OK or
  * GEER_ERR_CAPACITY (pairs exceeded capacity). *pairs (may be NULL) receives
  * the last pair count. */

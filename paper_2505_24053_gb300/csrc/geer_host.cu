@@ -317,6 +317,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_ev = L.take(sizeof(uint2) * c.pixels);
     size_t o_gacc = L.take(sizeof(GradAcc) * cg);
     size_t o_hit = L.take(sizeof(uint2) * c.tiles * c.hit_entries);
+    size_t o_mask = L.take(c.hit_entries > 0 ? sizeof(uint8_t) * c.tiles : 0);  // not in the forward-only layout
     if (base && ws) {
         ws->d_cams = reinterpret_cast<DevCam *>(base + o_cams);
         ws->d_tile_tab = reinterpret_cast<float4 *>(base + o_ttab);
@@ -352,6 +353,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_gacc = reinterpret_cast<GradAcc *>(base + o_gacc);
         ws->d_hit = c.hit_entries > 0 ? reinterpret_cast<uint2 *>(base + o_hit) : nullptr;
         ws->hit_entries = c.hit_entries;
+        ws->d_tile_mask = c.hit_entries > 0 ? reinterpret_cast<uint8_t *>(base + o_mask) : nullptr;
     }
     return L.off;
 }
@@ -433,6 +435,7 @@ geer_status upload_cams(geer_workspace *ws, const CamTables &t, cudaStream_t s) 
     ws->n_stiles = t.stiles;
     ws->n_sort_passes = sort_passes(t.stiles);
     ws->stage = 0;
+    ws->tile_mask_on = 0;  // tile indices refer to the new camera set
     return GEER_OK;
 }
 
@@ -655,6 +658,13 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
     if (st != GEER_OK) return st;
     if (g->n != ws->n_gauss || g->sh_degree != ws->sh_degree) return GEER_ERR_ARG;
     if (d_sh && (reinterpret_cast<uintptr_t>(d_sh) & 15)) return GEER_ERR_ARG;
+    if ((st = geer_render_bwd_tiles(ws, dL_drgb, stream)) != GEER_OK) return st;
+    return geer_preprocess_bwd(ws, g, d_mean, d_scale, d_quat, d_opacity, d_sh, accumulate, stream);
+}
+
+geer_status geer_render_bwd_tiles(geer_workspace *ws, const float *dL_drgb, void *stream) {
+    if (!ws || !dL_drgb) return GEER_ERR_ARG;
+    if (ws->stage < 3) return GEER_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
     if (items > 0 && cudaMemsetAsync(ws->d_gacc, 0, sizeof(GradAcc) * items, s) != cudaSuccess) return GEER_ERR_CUDA;
@@ -663,8 +673,57 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
         if (launch_bwd_order(ws, s) != cudaSuccess || launch_render_bwd(ws, dL_drgb, s) != cudaSuccess)
             return GEER_ERR_CUDA;
     }
+    ws->stage = 4;
+    return GEER_OK;
+}
+
+geer_status geer_grad_accumulators(geer_workspace *ws, float **acc, int64_t *n_floats) {
+    if (!ws || !acc || !n_floats) return GEER_ERR_ARG;
+    *acc = reinterpret_cast<float *>(ws->d_gacc);
+    *n_floats = (int64_t)ws->n_cams * ws->n_gauss * (int64_t)(sizeof(GradAcc) / sizeof(float));
+    return GEER_OK;
+}
+
+geer_status geer_preprocess_bwd(geer_workspace *ws, const geer_gaussians *g, float *d_mean, float *d_scale,
+                                float *d_quat, float *d_opacity, float *d_sh, int32_t accumulate, void *stream) {
+    if (!ws) return GEER_ERR_ARG;
+    if (ws->stage != 4) return GEER_ERR_STATE;
+    geer_status st = check_gaussians(ws, g);
+    if (st != GEER_OK) return st;
+    if (g->n != ws->n_gauss || g->sh_degree != ws->sh_degree) return GEER_ERR_ARG;
+    if (d_sh && (reinterpret_cast<uintptr_t>(d_sh) & 15)) return GEER_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     StageTimer tm(ws, kStagePreprocessBwd, s);
     return cuda_status(launch_preprocess_bwd(ws, g, d_mean, d_scale, d_quat, d_opacity, d_sh, accumulate ? 1 : 0, s));
+}
+
+geer_status geer_tile_owners(const geer_camera *cams, int32_t n_cams, int32_t n_parts, int32_t *owner) {
+    if (!owner || n_parts < 1) return GEER_ERR_ARG;
+    geer_status st = check_cams(cams, n_cams);
+    if (st != GEER_OK) return st;
+    int64_t t = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        const int64_t tx = ceil_div(cams[c].width, kTile), ty = ceil_div(cams[c].height, kTile);
+        for (int64_t cy = 0; cy < ty; ++cy)
+            for (int64_t cx = 0; cx < tx; ++cx) owner[t++] = (int32_t)((cx + cy + c) % n_parts);
+    }
+    return GEER_OK;
+}
+
+geer_status geer_set_tile_mask(geer_workspace *ws, const uint8_t *mask, int64_t n_tiles, void *stream) {
+    if (!ws) return GEER_ERR_ARG;
+    if (!mask) {
+        ws->tile_mask_on = 0;
+        return GEER_OK;
+    }
+    if (n_tiles != ws->n_tiles || !ws->d_tile_mask) return GEER_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_tiles > 0 && (cudaMemcpyAsync(ws->d_tile_mask, mask, (size_t)n_tiles, cudaMemcpyHostToDevice, s) !=
+                            cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+        return GEER_ERR_CUDA;
+    ws->tile_mask_on = 1;
+    return GEER_OK;
 }
 
 geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *stream) {

@@ -215,11 +215,13 @@ struct geer_workspace {
     uint2 *d_hit;           // [cap_tiles][hit_entries] per tile-list entry, one byte per warp of the tile:
                             // nonzero when one of the warp's rays hit the entry in the forward (or null)
     int64_t hit_entries;    // list entries recorded per tile (0: none)
+    uint8_t *d_tile_mask;   // [cap_tiles] tiles the forward renders (geer_set_tile_mask; null: no mask room)
+    int tile_mask_on;       // the mask is in effect for the current camera set
 
     // state of the last calls
     int64_t n_gauss;
     int32_t sh_degree;
-    int stage;               // 0 none, 1 preprocessed, 2 sorted, 3 rendered
+    int stage;               // 0 none, 1 preprocessed, 2 sorted, 3 rendered, 4 render-stage gradients
     int sorted_buf;          // which ping-pong buffer holds the sorted super-tile pairs
     int depth_buf;           // which ping-pong buffer holds the depth-sorted items
     int sort_grid;           // grid of the radix kernels (grid-stride over sort tiles)

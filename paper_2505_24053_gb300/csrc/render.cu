@@ -381,7 +381,8 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                                             float *__restrict__ Tout, float *__restrict__ Tfin,
                                                             uint32_t *__restrict__ last_out,
                                                             uint2 *__restrict__ evals, uint2 *__restrict__ hit,
-                                                            int64_t hit_entries) {
+                                                            int64_t hit_entries,
+                                                            const uint8_t *__restrict__ tile_mask) {
     grid_dep_sync();
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     static_assert(kParts == 1, "one block per tile: the block records the tile's walk");
@@ -394,6 +395,20 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
     TileRay tr;
     if (!tile_ray(cam, t, 0, ptab, ttab, srange, S, tr)) {
         if (threadIdx.x == 0) tile_walk[t] = make_uint2(0u, 0u);
+        return;
+    }
+    if (tile_mask && !tile_mask[t]) {  // another part's tile: zeros, nothing for the backward to walk
+        if (threadIdx.x == 0) tile_walk[t] = make_uint2(0u, 0u);
+        if (tr.inside) {
+            const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
+            rgb[3 * pix + 0] = 0.0f;
+            rgb[3 * pix + 1] = 0.0f;
+            rgb[3 * pix + 2] = 0.0f;
+            if (Tout) Tout[pix] = 0.0f;
+            Tfin[pix] = 0.0f;
+            last_out[pix] = 0u;
+            evals[pix] = make_uint2(0u, 0u);
+        }
         return;
     }
     FwdRay f{1.0f, 0.0f, 0.0f, 0.0f, 0u, 0u, 0u, !tr.inside};
@@ -738,7 +753,8 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_tile_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         ws->params, rgb, T_final,
-        ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->hit_entries);
+        ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->hit_entries,
+        ws->tile_mask_on ? static_cast<const uint8_t *>(ws->d_tile_mask) : nullptr);
     return cudaGetLastError();
 }
 

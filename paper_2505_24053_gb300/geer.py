@@ -49,7 +49,8 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_enable_timing", "geer_stage_times", "geer_stage_name", "geer_remap_to_native",
            "geer_native_regions", "geer_image_metrics", "geer_native_to_beap", "geer_adam_step",
            "geer_pair_counts", "geer_debug_render_state", "geer_densify_accumulate", "geer_densify_scratch_bytes",
-           "geer_densify_plan", "geer_densify_apply", "geer_opacity_reset"]
+           "geer_densify_plan", "geer_densify_apply", "geer_opacity_reset", "geer_render_bwd_tiles",
+           "geer_grad_accumulators", "geer_preprocess_bwd", "geer_tile_owners", "geer_set_tile_mask"]
 
 _lib = None
 
@@ -104,6 +105,11 @@ def lib(build_if_missing: bool = True):
         "geer_densify_plan": [P, I64, P, P, P, P, P, C.c_size_t, P, P],
         "geer_densify_apply": [I64, I32, P, P, P, P, P, P, P, P, P, C.c_size_t, I64, P, P, P, P, P, P, P, P, P, P],
         "geer_opacity_reset": [I64, I32, C.c_float, P, P, P, P, P],
+        "geer_render_bwd_tiles": [P, P, P],
+        "geer_grad_accumulators": [P, P, P],
+        "geer_preprocess_bwd": [P, P, P, P, P, P, P, I32, P],
+        "geer_tile_owners": [P, I32, I32, P],
+        "geer_set_tile_mask": [P, P, I64, P],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -279,6 +285,48 @@ class Workspace:
                                      _stream(stream)),
                "geer_render_bwd")
 
+    def render_bwd_tiles(self, dL_drgb: torch.Tensor, stream=None):
+        """The render stage of the backward (geer_render_bwd_tiles): the
+        per-(camera, Gaussian) accumulators over the rendered tiles' rays."""
+        _check(lib().geer_render_bwd_tiles(self._handle, C.c_void_p(dL_drgb.data_ptr()), _stream(stream)),
+               "geer_render_bwd_tiles")
+
+    def grad_accumulators(self) -> torch.Tensor:
+        """The render stage's accumulators [n_cams * n, 16] f32 as a view of the
+        workspace's own memory (reading or replacing them, e.g. by an all-reduce
+        over processes, acts on the workspace)."""
+        ptr = C.c_void_p()
+        n = C.c_int64()
+        _check(lib().geer_grad_accumulators(self._handle, C.byref(ptr), C.byref(n)), "geer_grad_accumulators")
+        off = int(ptr.value or 0) - self.buf.data_ptr()
+        nbytes = 4 * int(n.value)
+        if n.value == 0:
+            return torch.empty((0, 16), dtype=torch.float32, device=self.buf.device)
+        assert 0 <= off and off + nbytes <= self.buf.numel()
+        return self.buf[off:off + nbytes].view(torch.float32).view(-1, 16)
+
+    def preprocess_bwd(self, g: Gaussians, grads: dict, accumulate: bool = True, stream=None):
+        """The preprocess stage of the backward (geer_preprocess_bwd) from the accumulators."""
+        gc = g.c_struct()
+
+        def ptr(name):
+            t = grads.get(name)
+            return C.c_void_p(t.data_ptr()) if t is not None else None
+
+        _check(lib().geer_preprocess_bwd(self._handle, C.byref(gc), ptr("mean"), ptr("scale"), ptr("quat"),
+                                         ptr("opacity"), ptr("sh"), 1 if accumulate else 0, _stream(stream)),
+               "geer_preprocess_bwd")
+
+    def set_tile_mask(self, mask, stream=None):
+        """Render only the tiles with mask != 0 (host array of the camera set's
+        tile count), or all tiles with mask=None (geer_set_tile_mask)."""
+        if mask is None:
+            _check(lib().geer_set_tile_mask(self._handle, None, 0, _stream(stream)), "geer_set_tile_mask")
+            return
+        m = np.ascontiguousarray(np.asarray(mask).astype(np.uint8))
+        _check(lib().geer_set_tile_mask(self._handle, C.c_void_p(m.ctypes.data), int(m.size), _stream(stream)),
+               "geer_set_tile_mask")
+
     def device_status(self, stream=None):
         pairs = C.c_int64()
         st = lib().geer_last_device_status(self._handle, C.byref(pairs), _stream(stream))
@@ -355,6 +403,16 @@ class Workspace:
                                       C.byref(count), _stream(stream)), "geer_debug_pairs")
         n = min(int(count.value), cap)
         return keys[:n], vals[:n]
+
+
+def tile_owners(cams, n_parts: int) -> np.ndarray:
+    """Owner part of every tile of the camera set (geer_tile_owners, host only):
+    int32 [total tiles] in geer_set_cameras' tile order."""
+    arr = cameras_c(cams)
+    n = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in cams)
+    out = np.zeros(n, np.int32)
+    _check(lib().geer_tile_owners(arr, len(cams), int(n_parts), C.c_void_p(out.ctypes.data)), "geer_tile_owners")
+    return out
 
 
 def l1_loss_grad(rgb: torch.Tensor, target: torch.Tensor, grad: torch.Tensor | None = None, stream=None):

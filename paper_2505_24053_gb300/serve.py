@@ -16,10 +16,18 @@ capacity. A batch that overflows anyway (the device status says so) is split and
 its requests go back to the head of the queue.
 
 Latency = request arrival -> completion event of its batch, measured with CUDA
-events against a start event recorded when the trace starts.
+events against a start event recorded when the trace starts. Each request also
+carries host timestamps (admitted into a batch, launch call returned, completion
+seen by the loop) and the GPU time its batch started, so that a slow request can
+be traced to the step that held it: the queue, the host's launch, the GPU or the
+loop noticing completion. The cyclic garbage collector is paused while a trace
+runs (objects alive before it are frozen out of later collections): a full
+collection over a large process heap can hold the loop for tens of
+milliseconds.
 """
 from __future__ import annotations
 
+import gc
 import math
 import statistics
 import time
@@ -41,6 +49,12 @@ class Request:
     batch: int = -1
     image: object = None
     error: str | None = None
+    # host clock, ms after the trace start: admitted into a batch, launch call
+    # returned, completion seen by the loop; GPU clock: the batch's first work
+    admit_ms: float | None = None
+    launch_ms: float | None = None
+    seen_ms: float | None = None
+    gpu_start_ms: float | None = None
 
     @property
     def latency_ms(self) -> float | None:
@@ -104,6 +118,7 @@ class _Buffer:
         self.graph = False
         self.graphs = {}
         self.done = None
+        self.start = None
         self.batch = []
         self.batch_id = -1
 
@@ -138,8 +153,11 @@ class _Buffer:
 
     def launch(self, reqs, batch_id):
         import torch
+        self.start = torch.cuda.Event(enable_timing=True)
         self.load(reqs)
         with torch.cuda.stream(self.stream):
+            # recorded after load's camera-table copies: start -> done spans the step
+            self.start.record(self.stream)
             if self.graph:
                 self.graphs[len(reqs)].replay()
             else:
@@ -203,10 +221,10 @@ class Engine:
         off = k * self.slot_pixels
         return buf.rgb[off:off + n].view(cam.height, cam.width, 3)
 
-    def _complete(self, buf, t0, keep_images, out_done):
-        import torch
+    def _complete(self, buf, t0, keep_images, out_done, seen_ms=None):
         st, pairs = buf.ws.device_status(stream=buf.stream)
         t_ms = t0.elapsed_time(buf.done)
+        s_ms = t0.elapsed_time(buf.start)
         if st == geer.ERR_CAPACITY and len(buf.batch) == 1:
             # a single request beyond the pair capacity can never be served here
             buf.batch[0].error = "pair capacity exceeded"
@@ -223,6 +241,8 @@ class Engine:
             requeue = []
             for k, r in enumerate(buf.batch):
                 r.done_ms = t_ms
+                r.gpu_start_ms = s_ms
+                r.seen_ms = seen_ms
                 r.batch = buf.batch_id
                 if keep_images:
                     r.image = self._slot_view(buf, k, r.camera).clone()
@@ -238,50 +258,105 @@ class Engine:
         pending = sorted(requests, key=lambda r: r.arrival)
         queue: deque = deque()
         done: list = []
-        t0 = torch.cuda.Event(enable_timing=True)
-        t0.record(torch.cuda.current_stream())
-        torch.cuda.synchronize()
-        wall0 = time.perf_counter()
-        i = 0
-        batch_id = 0
-        while i < len(pending) or queue or any(b.batch for b in self.buffers):
-            now = time.perf_counter() - wall0 if realtime else float("inf")
-            while i < len(pending) and pending[i].arrival <= now:
-                queue.append(pending[i])
-                i += 1
-            progressed = False
-            for b in self.buffers:
-                if b.batch and not b.busy():
-                    requeue = self._complete(b, t0, keep_images, done)
-                    for r in reversed(requeue):
-                        queue.appendleft(r)
-                    progressed = True
-            for b in self.buffers:
-                if not b.batch and queue:
-                    reqs = self.scheduler.admit(queue)
-                    if reqs:
-                        b.launch(reqs, batch_id)
-                        batch_id += 1
+        gc_was_enabled = gc.isenabled()
+        gc.collect()
+        gc.freeze()
+        gc.disable()
+        try:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t0.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            wall0 = time.perf_counter()
+
+            def host_ms():
+                return 1e3 * (time.perf_counter() - wall0)
+
+            i = 0
+            batch_id = 0
+            while i < len(pending) or queue or any(b.batch for b in self.buffers):
+                now = time.perf_counter() - wall0 if realtime else float("inf")
+                while i < len(pending) and pending[i].arrival <= now:
+                    queue.append(pending[i])
+                    i += 1
+                progressed = False
+                for b in self.buffers:
+                    if b.batch and not b.busy():
+                        requeue = self._complete(b, t0, keep_images, done, seen_ms=host_ms())
+                        for r in reversed(requeue):
+                            queue.appendleft(r)
                         progressed = True
-            if not progressed:
-                if realtime and not queue and i < len(pending):
-                    wait = pending[i].arrival - (time.perf_counter() - wall0)
-                    if wait > 2e-4:
-                        time.sleep(min(wait, 1e-3))
-                else:
-                    time.sleep(2e-5)
-        torch.cuda.synchronize()
+                for b in self.buffers:
+                    if not b.batch and queue:
+                        reqs = self.scheduler.admit(queue)
+                        if reqs:
+                            t_admit = host_ms()
+                            b.launch(reqs, batch_id)
+                            t_launch = host_ms()
+                            for r in reqs:
+                                r.admit_ms, r.launch_ms = t_admit, t_launch
+                            batch_id += 1
+                            progressed = True
+                if not progressed:
+                    if realtime and not queue and i < len(pending):
+                        wait = pending[i].arrival - (time.perf_counter() - wall0)
+                        if wait > 2e-4:
+                            time.sleep(min(wait, 1e-3))
+                    else:
+                        time.sleep(2e-5)
+            torch.cuda.synchronize()
+        finally:
+            gc.unfreeze()
+            if gc_was_enabled:
+                gc.enable()
         return done
 
 
-def summarize(done, duration_s: float) -> dict:
+def _pct(values, p):
+    v = sorted(values)
+    k = min(len(v) - 1, max(0, int(math.ceil(p / 100.0 * len(v))) - 1))
+    return v[k]
+
+
+def breakdown(r: Request) -> dict | None:
+    """Where a request's latency went (ms): waiting in the queue (arrival ->
+    admitted), the host's launch (admitted -> launch call returned), waiting
+    for and running on the GPU (launch returned -> its batch done), and the loop
+    noticing completion (done -> seen). None without timestamps."""
+    if None in (r.admit_ms, r.launch_ms, r.done_ms, r.seen_ms):
+        return None
+    arr = 1e3 * r.arrival
+    return {"queue": r.admit_ms - arr, "launch": r.launch_ms - r.admit_ms, "gpu": r.done_ms - r.launch_ms,
+            "gpu_run": None if r.gpu_start_ms is None else r.done_ms - r.gpu_start_ms,
+            "seen": r.seen_ms - r.done_ms}
+
+
+def summarize(done, duration_s: float, window: tuple | None = None) -> dict:
+    """Latency percentiles and throughput of served requests. duration_s: the
+    trace's span the rates are taken over. window (start_s, end_s), if given:
+    sustained throughput = requests completed inside the window per second of
+    it (the service rate while requests keep arriving; below the arrival rate
+    when the server saturates), and drain = time past the window's end until
+    the last completion."""
     lat = sorted(r.latency_ms for r in done)
     pix = sum(r.camera.width * r.camera.height for r in done)
-
-    def pct(p):
-        k = min(len(lat) - 1, max(0, int(math.ceil(p / 100.0 * len(lat))) - 1))
-        return lat[k]
-
-    return {"requests": len(done), "p50_ms": pct(50), "p99_ms": pct(99), "mean_ms": statistics.mean(lat),
-            "max_ms": lat[-1], "req_per_s": len(done) / duration_s, "mpix_per_s": pix / duration_s / 1e6,
-            "batches": len({r.batch for r in done})}
+    out = {"requests": len(done), "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "mean_ms": statistics.mean(lat),
+           "max_ms": lat[-1], "req_per_s": len(done) / duration_s, "mpix_per_s": pix / duration_s / 1e6,
+           "batches": len({r.batch for r in done})}
+    if window is not None:
+        a, b = window
+        inside = [r for r in done if a * 1e3 <= r.done_ms <= b * 1e3]
+        out["completed_per_s"] = len(inside) / max(1e-9, b - a)
+        out["completed_mpix_per_s"] = sum(r.camera.width * r.camera.height for r in inside) / max(1e-9, b - a) / 1e6
+        out["drain_ms"] = max(0.0, max(r.done_ms for r in done) - b * 1e3)
+    parts = [x for x in (breakdown(r) for r in done) if x is not None]
+    if parts:
+        comp = {}
+        for k in ("queue", "launch", "gpu", "gpu_run", "seen"):
+            v = [x[k] for x in parts if x[k] is not None]
+            if v:
+                comp[k] = {"p50": _pct(v, 50), "p99": _pct(v, 99), "max": max(v)}
+        out["breakdown_ms"] = comp
+        worst = max(done, key=lambda r: r.latency_ms)
+        out["slowest"] = {"latency_ms": worst.latency_ms, "arrival_s": worst.arrival, "kind": worst.kind,
+                          **(breakdown(worst) or {})}
+    return out
