@@ -167,16 +167,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def aggregate(local_ms: float, pixels_per_rank: int, steps: int, world: int, dist=None, device=None):
+def aggregate(local_ms: float, pixels_per_rank: int, steps: int, world: int, dist=None, device=None,
+              shared: bool = False):
     """Whole-job Mpix/s from per-rank device time: time = max over ranks, work =
-    all ranks' pixels (replicas, weak scaling)."""
+    all ranks' pixels (replicas, weak scaling), or, with shared (the tile split:
+    the ranks share one frame's pixels, strong scaling), the frame's pixels."""
     t = local_ms
     if world > 1:
         import torch
         x = torch.tensor([local_ms], dtype=torch.float64, device=device)
         dist.all_reduce(x, op=dist.ReduceOp.MAX)
         t = float(x.item())
-    return world * pixels_per_rank * steps / (t / 1e3) / 1e6, t
+    frames = 1 if shared else world
+    return frames * pixels_per_rank * steps / (t / 1e3) / 1e6, t
 
 
 SERVING_MODES = (("concurrent", 1, 2), ("batched", 4, 2), ("one_at_a_time", 1, 1))
@@ -304,11 +307,24 @@ def _ablate_scene(geer, g, cams, rgb_pbf, flush, stream, tiles):
     return out
 
 
+def _tile_stats(ws, cams):
+    """Gaussians per tile (mean and standard deviation over every tile of the
+    cameras: the (tile, Gaussian) associations each tile's list holds, as the
+    paper's association tables report them) and the render's device memory: the
+    workspace (every buffer the render and its backward use) beside the
+    Gaussians' own arrays. Read after the timed steps (synchronous copies)."""
+    per_tile = ws.tile_counts().astype(np.float64)
+    ntiles = per_tile.size
+    return {"gaussians_per_tile_mean": float(per_tile.mean()), "gaussians_per_tile_std": float(per_tile.std()),
+            "gaussians_per_tile_max": int(per_tile.max()), "tiles": int(ntiles),
+            "workspace_bytes": int(ws.nbytes), "workspace_gb": ws.nbytes / 1e9}
+
+
 def run(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2505_24053_gb300 import geer
+    from paper_2505_24053_gb300 import geer, tilesplit
     from paper_2505_24053_gb300 import workloads as wl
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -337,6 +353,21 @@ def run(args):
                              device=dev)
     dL = torch.empty_like(rgb)
     loss = torch.empty(1, device=dev)
+    split = args.split == "tiles"
+    target_step = target
+    if split:
+        # this rank renders its share of the tiles; the backward's render-stage
+        # accumulators are summed over the ranks (NCCL) before its preprocess stage
+        ts = tilesplit.TileSplit(ws, rank, world)
+        target_step = ts.masked_target(target)
+
+    def backward(gk):
+        if split:
+            ws.render_bwd_tiles(dL)
+            tilesplit.reduce_sum(ws.grad_accumulators(), None, world)
+            ws.preprocess_bwd(gk, grads, accumulate=False)
+        else:
+            ws.render_bwd(gk, dL, grads, accumulate=False)
 
     def train_step(ev):
         ev[0].record(stream)
@@ -346,8 +377,8 @@ def run(args):
         ev[2].record(stream)
         # training step: forward, L1 loss gradient, backward (the step's gradients written)
         ws.render_fwd(rgb)
-        geer.l1_loss_grad(rgb, target, dL)
-        ws.render_bwd(g, dL, grads, accumulate=False)
+        geer.l1_loss_grad(rgb, target_step, dL)
+        backward(g)
         ev[3].record(stream)
 
     def fwd_step(ev):
@@ -393,6 +424,7 @@ def run(args):
     if not have_bwd:
         t_wall, clk = fwd_wall, fclk
     pairs, super_pairs = ws.pair_counts()
+    tile_stats = _tile_stats(ws, cams)
     stage_ms = {k: v[0] for k, v in ws.stage_times().items()}  # mean of the last 64 recorded occurrences
     ws.enable_timing(False)
     main_evs = train_evs if have_bwd else fwd_evs
@@ -400,7 +432,7 @@ def run(args):
     prep_ms = [e[0].elapsed_time(e[1]) for e in main_evs]
     sort_ms = [e[1].elapsed_time(e[2]) for e in main_evs]
     rend_ms = [e[2].elapsed_time(e[3]) for e in main_evs]
-    value, total_ms = aggregate(float(sum(step_ms)), pixels, args.steps, world, dist, dev)
+    value, total_ms = aggregate(float(sum(step_ms)), pixels, args.steps, world, dist, dev, shared=split)
     fwd_ms = [e[0].elapsed_time(e[3]) for e in fwd_evs]
     fwd_value = pixels / (statistics.mean(fwd_ms) / 1e3) / 1e6
     fwd_render_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in fwd_evs)
@@ -447,8 +479,8 @@ def run(args):
             ws.bin_sort(sync=False)
             ws.render_fwd(rgb_buf[b])
             if have_bwd:
-                geer.l1_loss_grad(rgb_buf[b], target, dL)
-                ws.render_bwd(gk, dL, grads, accumulate=False)
+                geer.l1_loss_grad(rgb_buf[b], target_step, dL)
+                backward(gk)
             comp_done[b].record(stream)
             down_s.wait_event(comp_done[b])
             with torch.cuda.stream(down_s):
@@ -465,7 +497,10 @@ def run(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e_evs = [(e0, e1)]
-    e2e, e2e_ms = aggregate(sum(a.elapsed_time(b) for a, b in e_evs), pixels, args.steps, world, dist, dev)
+    e2e, e2e_ms = aggregate(sum(a.elapsed_time(b) for a, b in e_evs), pixels, args.steps, world, dist, dev,
+                            shared=split)
+    if split:
+        ws.set_tile_mask(None)  # the measurements below render whole frames
 
     # remap of the BEAP render to the native camera image: an optional output
     # stage, timed on its own (not part of the step or of Mpix/s)
@@ -649,18 +684,22 @@ def run(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if split else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.workload == 3 else f"workload {args.workload}",
                    "pass": "fwd+L1+bwd" if have_bwd else "fwd", "gaussians": scene.n,
                    "pixels_per_gpu": pixels, "pairs": int(pairs), "super_pairs": int(super_pairs),
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": (f"tile split x{world}: each rank renders 1/{world} of the tiles, the "
+                                   f"backward's render-stage accumulators all-reduced (NCCL)") if split
+                                  else f"replicas x{world}",
                    "l2": "512 MB buffer written between timed steps (outside step events); inputs 236 MB > L2"},
         "fwd_only": {"value": fwd_value, "unit": "Mpix/s", "ms": statistics.mean(fwd_ms)},
         "stages_ms": {"preprocess": statistics.mean(prep_ms), "bin_sort": statistics.mean(sort_ms),
                       "render_fwd": fwd_render_ms,
                       "render_fwd_l1_bwd": statistics.mean(rend_ms) if have_bwd else None},
         "roofline": roofline,
+        "association": tile_stats,
         "stages": stages,
         "remap": remap,
         "train_step": {
@@ -678,7 +717,7 @@ def run(args):
                     "reprojected render, timed on their own with CUDA events (metrics: the kernel, its "
                     "accumulator reset and the 48 B copy back; 24 B of images + 1 B region read per "
                     "pixel); not in value"},
-        "association": assoc,
+        "association_ablation": assoc,
         "e2e": {"value": e2e, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "pipeline": "H2D of step k+1 on a copy stream during step k (two device buffers), D2H on a "
                             "third stream; one timed region over all steps; inputs > L2, no flush"},
@@ -713,6 +752,9 @@ def main():
                     help="second, saturating serving trace (0: skip)")
     ap.add_argument("--serving-sat-seconds", type=float, default=5.0)
     ap.add_argument("--ref-pixels", type=int, default=24)
+    ap.add_argument("--split", default="replicas", choices=["replicas", "tiles"],
+                    help="N > 1: independent replicas (weak scaling) or one frame's tiles split over the ranks with "
+                         "the gradient accumulators all-reduced (strong scaling)")
     ap.add_argument("--gaussians", type=int, default=None,
                     help="scene size override (the workload's distribution with fewer Gaussians; profiling)")
     ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3, 5],

@@ -318,6 +318,12 @@ geer_status geer_debug_render_state(geer_workspace *ws, uint32_t *evals, uint32_
 geer_status geer_pair_counts(geer_workspace *ws, int64_t *tile_pairs, int64_t *super_pairs, int32_t *sort_passes,
                              int64_t *live_items, void *stream);
 
+/* Measurement (synchronous): after geer_bin_sort, the length of every tile's
+ * list, i.e. its number of (tile, Gaussian) associations (counts: HOST u32
+ * [n_tiles], tiles of the current camera set in order). Leaves the render state
+ * intact. GEER_ERR_CAPACITY after a pair-capacity overflow. */
+geer_status geer_tile_counts(geer_workspace *ws, uint32_t *counts, void *stream);
+
 /* Measurement (synchronous): totals over all rays of the last geer_render_fwd
  * of the ray-Gaussian evaluations executed (list entries walked up to early
  * termination), of the contributors composited, and (walked_back, may be NULL)
@@ -460,15 +466,16 @@ geer_status geer_opacity_reset(int64_t n, int32_t sh_degree, float value, float 
 geer_status geer_native_regions(const geer_camera *cam, uint8_t *regions, void *stream);
 
 /* Image metrics of pred against gt (device [height][width][3] f32, values in
- * [0, 1]) per region: out (HOST [n_regions][3] f64) gets, for each region
+ * [0, 1]) per region: out (HOST [n_regions][5] f64) gets, for each region
  * r < n_regions (1..8), the sum of squared errors over its pixels and the
  * three channels, the sum over its pixels of the SSIM averaged over the
- * channels, and its pixel count. regions: device [height][width] u8 region id
- * per pixel (ids >= n_regions are left out) or NULL (every pixel in region 0).
- * SSIM: 11 x 11 Gaussian window (sigma 1.5, normalised), zero padding,
- * C1 = 0.01^2, C2 = 0.03^2. acc: device scratch of 3 * n_regions f64
- * (caller-owned). PSNR of a region = 10 log10(3 count / sum of squared errors).
- * Synchronises `stream`. */
+ * channels, its pixel count, its PSNR = 10 log10(1 / MSE) = 10 log10(3 count /
+ * sum of squared errors) (+inf for identical images, NaN for an empty region)
+ * and its mean SSIM (sum / count; NaN for an empty region). regions: device
+ * [height][width] u8 region id per pixel (ids >= n_regions are left out) or
+ * NULL (every pixel in region 0). SSIM: 11 x 11 Gaussian window (sigma 1.5,
+ * normalised), zero padding, C1 = 0.01^2, C2 = 0.03^2. acc: device scratch of
+ * 3 * n_regions f64 (caller-owned). Synchronises `stream`. */
 geer_status geer_image_metrics(const float *pred, const float *gt, int32_t width, int32_t height,
                                const uint8_t *regions, int32_t n_regions, double *acc, double *out, void *stream);
 

@@ -64,8 +64,12 @@ def _phi_max(k, steps=4096):
     return math.pi
 
 
-def native_to_beap(cam, native: np.ndarray):
-    """(beap [h, w, 3] float64, valid [h, w] uint8) of a native image [h, w, 3]."""
+def native_to_beap(cam, native: np.ndarray, coords: bool = False):
+    """(beap [h, w, 3] float64, valid [h, w] uint8) of a native image [h, w, 3].
+    With coords=True also the native coordinates (u, v) of each BEAP pixel's
+    ray [h, w, 2] (NaN where the ray has no projection) and, for the fisheye
+    models, the ray's angle off the axis minus the end of the invertible range
+    [h, w] (NaN for the pinhole)."""
     w, h = cam.width, cam.height
     fx = cam.fov_x
     fy = orc.fov_y(cam)
@@ -76,6 +80,8 @@ def native_to_beap(cam, native: np.ndarray):
     native = np.asarray(native, np.float64)
     out = np.zeros((h, w, 3))
     valid = np.zeros((h, w), np.uint8)
+    uv = np.full((h, w, 2), np.nan)
+    pmargin = np.full((h, w), np.nan)
     for j in range(h):
         ph = ((j + 0.5) / h - 0.5) * fy
         for i in range(w):
@@ -88,6 +94,7 @@ def native_to_beap(cam, native: np.ndarray):
             else:
                 rho = math.hypot(d[0], d[1])
                 p = math.atan2(rho, d[2])
+                pmargin[j, i] = p - pmax
                 if p > pmax:
                     continue
                 if rho > 0:
@@ -96,6 +103,7 @@ def native_to_beap(cam, native: np.ndarray):
                 else:
                     x, y = 0.0, 0.0
             u, v = x + 0.5 * w - 0.5, y + 0.5 * h - 0.5
+            uv[j, i] = (u, v)
             if not (-0.5 <= u <= w - 0.5 and -0.5 <= v <= h - 0.5):
                 continue
             uc, vc = min(max(u, 0.0), w - 1.0), min(max(v, 0.0), h - 1.0)
@@ -106,6 +114,8 @@ def native_to_beap(cam, native: np.ndarray):
             bot = native[y1, x0] + ax * (native[y1, x1] - native[y1, x0])
             out[j, i] = top + ay * (bot - top)
             valid[j, i] = 1
+    if coords:
+        return out, valid, uv, pmargin
     return out, valid
 
 

@@ -821,6 +821,24 @@ geer_status geer_debug_pairs(geer_workspace *ws, uint64_t *keys, uint32_t *value
     return GEER_OK;
 }
 
+geer_status geer_tile_counts(geer_workspace *ws, uint32_t *counts, void *stream) {
+    if (!ws || !counts) return GEER_ERR_ARG;
+    if (ws->stage < 2) return GEER_ERR_STATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t m[kMiscCount];
+    if (cudaMemcpyAsync(m, ws->d_misc, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    if (m[kMiscStatus] & kStatusCapacity) return GEER_ERR_CAPACITY;
+    if (ws->n_tiles == 0) return GEER_OK;
+    uint32_t *scratch = reinterpret_cast<uint32_t *>(ws->d_tile_walk + ws->n_tiles);
+    if (launch_expand_tiles(ws, scratch, nullptr, s) != cudaSuccess ||
+        cudaMemcpyAsync(counts, scratch, sizeof(uint32_t) * ws->n_tiles, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    return GEER_OK;
+}
+
 geer_status geer_debug_render_state(geer_workspace *ws, uint32_t *evals, uint32_t *last, uint32_t *walk,
                                     void *stream) {
     if (!ws) return GEER_ERR_ARG;
@@ -1022,10 +1040,21 @@ geer_status geer_image_metrics(const float *pred, const float *gt, int32_t width
     if (!pred || !gt || !acc || !out || width < 0 || height < 0 || n_regions < 1 || n_regions > 8)
         return GEER_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double sums[3 * 8];
     if (launch_image_metrics(pred, gt, width, height, regions, n_regions, acc, s) != cudaSuccess ||
-        cudaMemcpyAsync(out, acc, sizeof(double) * 3 * n_regions, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(sums, acc, sizeof(double) * 3 * n_regions, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return GEER_ERR_CUDA;
+    for (int r = 0; r < n_regions; ++r) {
+        const double sse = sums[3 * r], ssim = sums[3 * r + 1], cnt = sums[3 * r + 2];
+        double *o = out + 5 * r;
+        o[0] = sse;
+        o[1] = ssim;
+        o[2] = cnt;
+        // PSNR of values in [0, 1]: 10 log10(1 / MSE), MSE over the region's pixels and 3 channels
+        o[3] = cnt > 0.0 ? (sse > 0.0 ? 10.0 * log10(3.0 * cnt / sse) : INFINITY) : NAN;
+        o[4] = cnt > 0.0 ? ssim / cnt : NAN;
+    }
     return GEER_OK;
 }
 

@@ -7,7 +7,6 @@ missing the first call raises.
 from __future__ import annotations
 
 import ctypes as C
-import math
 import os
 
 import numpy as np
@@ -50,7 +49,8 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_native_regions", "geer_image_metrics", "geer_native_to_beap", "geer_adam_step",
            "geer_pair_counts", "geer_debug_render_state", "geer_densify_accumulate", "geer_densify_scratch_bytes",
            "geer_densify_plan", "geer_densify_apply", "geer_opacity_reset", "geer_render_bwd_tiles",
-           "geer_grad_accumulators", "geer_preprocess_bwd", "geer_tile_owners", "geer_set_tile_mask"]
+           "geer_grad_accumulators", "geer_preprocess_bwd", "geer_tile_owners", "geer_set_tile_mask",
+           "geer_tile_counts"]
 
 _lib = None
 
@@ -110,6 +110,7 @@ def lib(build_if_missing: bool = True):
         "geer_preprocess_bwd": [P, P, P, P, P, P, P, I32, P],
         "geer_tile_owners": [P, I32, I32, P],
         "geer_set_tile_mask": [P, P, I64, P],
+        "geer_tile_counts": [P, P, P],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -371,6 +372,13 @@ class Workspace:
         _check(lib().geer_pair_counts(self._handle, None, None, C.byref(p), None, _stream(stream)), "geer_pair_counts")
         return int(p.value)
 
+    def tile_counts(self, stream=None) -> np.ndarray:
+        """Every tile's list length ((tile, Gaussian) associations) after bin_sort."""
+        n = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in self.cams)
+        out = np.zeros(n, np.uint32)
+        _check(lib().geer_tile_counts(self._handle, C.c_void_p(out.ctypes.data), _stream(stream)), "geer_tile_counts")
+        return out
+
     def debug_render_state(self, stream=None):
         """Per ray (evaluations, contributors) [n_pixels, 2] and last [n_pixels]; per tile
         the forward's walk record [n_tiles, 2] (super-list position, entries)."""
@@ -454,18 +462,12 @@ def image_metrics(pred: torch.Tensor, gt: torch.Tensor, regions: torch.Tensor | 
     """Per region: PSNR, mean SSIM and pixel count of pred against gt ([h, w, 3] f32)."""
     h, w = int(pred.shape[0]), int(pred.shape[1])
     acc = torch.empty(3 * n_regions, dtype=torch.float64, device=pred.device)
-    out = (C.c_double * (3 * n_regions))()
+    out = (C.c_double * (5 * n_regions))()
     reg = C.c_void_p(regions.data_ptr()) if regions is not None else None
     _check(lib().geer_image_metrics(C.c_void_p(pred.data_ptr()), C.c_void_p(gt.data_ptr()), w, h, reg, n_regions,
                                     C.c_void_p(acc.data_ptr()), out, _stream(stream)), "geer_image_metrics")
-    res = []
-    for r in range(n_regions):
-        sse, ssim, cnt = out[3 * r], out[3 * r + 1], out[3 * r + 2]
-        mse = sse / (3.0 * cnt) if cnt > 0 else float("nan")
-        res.append({"sse": sse, "ssim_sum": ssim, "count": int(cnt),
-                    "psnr": (10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf")) if cnt > 0 else float("nan"),
-                    "ssim": ssim / cnt if cnt > 0 else float("nan")})
-    return res
+    return [{"sse": out[5 * r], "ssim_sum": out[5 * r + 1], "count": int(out[5 * r + 2]), "psnr": out[5 * r + 3],
+             "ssim": out[5 * r + 4]} for r in range(n_regions)]
 
 
 def native_to_beap(native_img: torch.Tensor, cam, out: torch.Tensor | None = None,

@@ -297,7 +297,10 @@ class Engine:
                             batch_id += 1
                             progressed = True
                 if not progressed:
-                    if realtime and not queue and i < len(pending):
+                    # idle until the next arrival, but poll finely while a batch is on
+                    # the GPU: its completion is noticed within tens of microseconds
+                    in_flight = any(b.batch for b in self.buffers)
+                    if realtime and not queue and i < len(pending) and not in_flight:
                         wait = pending[i].arrival - (time.perf_counter() - wall0)
                         if wait > 2e-4:
                             time.sleep(min(wait, 1e-3))

@@ -250,3 +250,39 @@ def test_backward_full_size_sampled_pixels(geer, orc, cfg, per_cam):
         off += cam.pixels
     _compare(g, ref, f"workload{cfg}")
 
+
+
+@pytest.mark.parametrize("cfg,n_tiles,per_tile", [(3, 32, 8), (5, 32, 8)])
+def test_backward_heaviest_tiles_full_size(geer, orc, cfg, n_tiles, per_tile):
+    """The backward on the full-size workloads' hardest rays: dL/dC is non-zero on
+    256 rays of the tiles with the longest walks (and on any ray walking past the
+    hit record), in the bench's launch configuration; the oracle's gradient over
+    those rays is the exact answer, checked at the 1e-3 tolerance."""
+    from heavy_pixels import heavy_pixels
+    scene = wl.config_scene(cfg)
+    cams = wl.config_cameras(cfg)
+    r = geer.Renderer(cams, scene.n, scene.sh_degree)
+    g = geer.Gaussians.from_scene(scene)
+    r.forward(g)
+    picks, walks, beyond = heavy_pixels(r.ws, cams, n_tiles, per_tile, seed=950 + cfg)
+    assert sum(len(p) for p in picks) >= n_tiles * per_tile
+    rng = np.random.default_rng(960 + cfg)
+    dL = np.zeros((r.pixels, 3), np.float32)
+    off, rows_all = 0, []
+    for cam, pix in zip(cams, picks):
+        rows = off + pix[:, 1] * cam.width + pix[:, 0]
+        dL[rows] = rng.normal(0, 1, (len(rows), 3)).astype(np.float32)
+        rows_all.append(rows)
+        off += cam.pixels
+    grads = r.backward(g, torch.as_tensor(dL, device="cuda"))
+    torch.cuda.synchronize()
+    gpu = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
+    ref = None
+    for cam, pix, rows in zip(cams, picks, rows_all):
+        if len(pix) == 0:
+            continue
+        gi = orc.render_grad(scene, cam, pix, dL[rows].astype(np.float64))
+        ref = gi if ref is None else {k: ref[k] + gi[k] for k in ref}
+    print(f"workload {cfg}: {sum(len(p) for p in picks)} rays of the {n_tiles} heaviest tiles "
+          f"(walks {int(walks.min())}..{int(walks.max())}), {beyond} rays beyond the hit record")
+    _compare(gpu, ref, f"workload{cfg}/heavy")

@@ -53,7 +53,7 @@ def test_native_regions_match_oracle(geer, orc, M, name, cam):
     gpu = geer.native_regions(cam).cpu().numpy()
     ref = M.native_regions(cam)
     bad = np.nonzero(gpu != ref)
-    assert bad[0].size <= max(2, ref.size // 1000), (name, bad[0].size)
+    # decided pixel by pixel: each disagreement lies within rounding of a boundary
     if bad[0].size:
         th, ph, u, v = _oracle_angles(orc, cam)
         f = orc.native_focal(cam)
@@ -79,6 +79,9 @@ def test_image_metrics_match_oracle(geer, M, h, w):
         assert res[r]["count"] == int(ref[r, 2])
         assert abs(res[r]["sse"] - ref[r, 0]) <= 1e-5 * ref[r, 0] + 1e-9, (r, res[r]["sse"], ref[r, 0])
         assert abs(res[r]["ssim_sum"] - ref[r, 1]) <= 1e-5 * ref[r, 2], (r, res[r]["ssim_sum"], ref[r, 1])
+        # PSNR and mean SSIM from the library: 10 log10(1 / MSE) and the mean (R20)
+        assert res[r]["psnr"] == pytest.approx(10 * math.log10(3 * ref[r, 2] / ref[r, 0]), abs=1e-4)
+        assert res[r]["ssim"] == pytest.approx(ref[r, 1] / ref[r, 2], abs=1e-5)
 
 
 def test_image_metrics_identical_images(geer):

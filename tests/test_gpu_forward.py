@@ -136,6 +136,10 @@ def test_sorted_pairs_match_cpu_sort(geer, orc, name, cams):
     assert P == ek.size
     assert np.array_equal(k, ek)
     assert np.array_equal(v, ev)
+    # every tile's list length (geer_tile_counts) is its count of replica pairs
+    counts = r.ws.tile_counts()
+    ntiles = counts.size
+    assert np.array_equal(counts, np.bincount((ek >> np.uint64(32)).astype(np.int64), minlength=ntiles)[:ntiles])
 
 
 @pytest.mark.parametrize("name,cams", TINY, ids=[t[0] for t in TINY])
@@ -308,9 +312,34 @@ def test_render_workload5_sampled_pixels(geer, orc):
     off = 0
     for ci, cam in enumerate(cams):
         img = rgb[off:off + cam.pixels].reshape(cam.height, cam.width, 3)
-        pix = wl.random_pixels(cam, 48, seed=500 + ci)
+        pix = wl.random_pixels(cam, 16, seed=500 + ci)
         err, ill = _check_pixels(orc, scene, cam, img, pix, f"workload5/{ci}")
         strict = int((err.max(axis=1) > TOL_MAX).sum())
         print(f"workload 5 cam {ci}: max err {err.max():.3g}, ill-conditioned {ill.sum()}/{len(ill)}, "
               f"above 2e-4: {strict}")
         off += cam.pixels
+
+
+@pytest.mark.parametrize("cfg,n_tiles,per_tile", [(3, 32, 32), (5, 32, 8)])
+def test_render_heaviest_tiles_full_size(geer, orc, cfg, n_tiles, per_tile):
+    """The full-size workloads' hardest rays, in the bench's launch configuration:
+    the rays of the tiles with the longest forward walks (their heaviest rays and
+    random ones) and any ray walking past the backward's hit record, each within
+    2e-4 of an admissible oracle result (1024 rays on workload 3; 256 over
+    workload 5's four cameras, whose brute force costs 6M Gaussians a ray)."""
+    from heavy_pixels import heavy_pixels
+    scene = wl.config_scene(cfg)
+    cams = wl.config_cameras(cfg)
+    r, g, rgb, T = _render(geer, scene, cams)
+    picks, walks, beyond = heavy_pixels(r.ws, cams, n_tiles, per_tile, seed=900 + cfg)
+    total = sum(len(p) for p in picks)
+    assert total >= n_tiles * per_tile
+    off, worst = 0, 0.0
+    for ci, (cam, pix) in enumerate(zip(cams, picks)):
+        if len(pix):
+            img = rgb[off:off + cam.pixels].reshape(cam.height, cam.width, 3)
+            err, ill = _check_pixels(orc, scene, cam, img, pix, f"workload{cfg}/heavy/{ci}")
+            worst = max(worst, float(err.max()))
+        off += cam.pixels
+    print(f"workload {cfg}: {total} rays of the {n_tiles} heaviest tiles (walks {int(walks.min())}.."
+          f"{int(walks.max())} entries), {beyond} rays beyond the hit record, max err {worst:.3g}")

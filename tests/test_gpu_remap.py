@@ -11,11 +11,15 @@ y^2 + z^2 -> 0 (at +-x), so
   dv = 2e-3 + h / FoV_y * 1e-6 / sqrt(y^2 + z^2)      (unit direction),
 and a colour may differ by max(du, dv) times the image's local slope (the
 largest difference between neighbours around the sampled cell) plus 1e-5.
-Pixels with max(du, dv) > 0.5 px (within about 1e-4 rad of a pole) are not
-compared; they stay below 0.5 % of the pixels. A pixel may switch between fill
-and interpolation only where the oracle puts it within max(du, dv) of the
-grid's edge or where it has no ray (the end of the distortion's invertible
-range); such switches stay below 0.2 % of the pixels.
+Pixels with max(du, dv) > 0.5 px (within about 1e-4 rad of a pole), where the
+coordinate itself is ill-conditioned, must hold a value that bilinear
+interpolation can produce within max(du, dv) + 1 px of the oracle's
+coordinate (between the smallest and the largest BEAP value there). A pixel
+may switch between fill and interpolation only where the oracle puts it within
+max(du, dv) of the grid's edge or where it has no ray (the end of the
+distortion's invertible range), and its value is then the fill colour or such
+an interpolated value. Every pixel is decided on its own: no share of the
+pixels is excused.
 """
 import math
 
@@ -80,14 +84,29 @@ def test_remap_matches_oracle(geer, orc, name, cam):
         dv = 2e-3 + h / orc.fov_y(cam) * 1e-6 / rho_y
     delta = np.maximum(du, dv)
     pole = has & (delta > 0.5)
-    assert pole.sum() <= 0.005 * cam.pixels, (name, int(pole.sum()))
     tol = 1e-5 + delta * slope[ys, xs]
     err = np.abs(got - ref).max(-1)
     bad = (err > tol) & ~pole
     edge = (~has) | (np.minimum.reduce([np.abs(u + 0.5), np.abs(u - (w - 0.5)), np.abs(v + 0.5),
                                         np.abs(v - (h - 0.5))]) <= np.maximum(delta, 0.01))
     assert not (bad & ~edge).any(), (name, np.argwhere(bad & ~edge)[:5], err[bad & ~edge].max())
-    assert bad.sum() <= 0.002 * cam.pixels, (name, int(bad.sum()))
+
+    def interpolable(j, i, radius):
+        # a value bilinear interpolation can give near the oracle's coordinate
+        x0, x1 = int(max(0, math.floor(u[j, i] - radius))), int(min(w - 1, math.ceil(u[j, i] + radius)))
+        y0, y1 = int(max(0, math.floor(v[j, i] - radius))), int(min(h - 1, math.ceil(v[j, i] + radius)))
+        win = beap[y0:y1 + 1, x0:x1 + 1].reshape(-1, 3).astype(np.float64)
+        return x0 <= x1 and y0 <= y1 and np.all(got[j, i] >= win.min(0) - 1e-6) and np.all(
+            got[j, i] <= win.max(0) + 1e-6)
+
+    fill64 = np.float32(FILL).astype(np.float64)
+    for j, i in np.argwhere(bad):  # edge pixels: the fill colour or an interpolated value
+        if np.array_equal(got[j, i], fill64):
+            continue
+        assert has[j, i] and interpolable(j, i, min(delta[j, i], 4.0) + 1.0), (name, j, i, got[j, i])
+    for j, i in np.argwhere(pole):  # ill-conditioned coordinate: an interpolated value near it
+        assert np.array_equal(got[j, i], fill64) and not inside[j, i] or interpolable(
+            j, i, min(delta[j, i], 4.0) + 1.0), (name, j, i, got[j, i], delta[j, i])
     # outside the BEAP grid: exactly the fill colour
     far = has & ~inside & ~edge & ~pole
     assert np.array_equal(got[far], np.broadcast_to(np.float32(FILL).astype(np.float64), got[far].shape))

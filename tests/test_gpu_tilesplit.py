@@ -48,12 +48,13 @@ def _full(geer, scene, cams, g, target):
     ws.render_bwd_tiles(dL)
     acc = ws.grad_accumulators().clone()
     ws.preprocess_bwd(g, grads, accumulate=False)
-    # the two stages equal the one-call backward (same kernels, same order)
+    # the two stages equal the one-call backward (the same kernels; FP32 atomics
+    # may sum in another order)
     one = _grads(g)
     ws.render_bwd(g, dL, one, accumulate=False)
     torch.cuda.synchronize()
     for k in one:
-        assert torch.equal(one[k], grads[k]), k
+        assert _rel(one[k], grads[k]) <= 1e-5, k
     return ws, rgb, T, float(loss.item()), acc, grads
 
 

@@ -2,8 +2,10 @@
 in tests/test_oracle_training.py), and a synthetic training run.
 
 Sampling: FP32 projection against FP64; a BEAP pixel's validity may only differ
-where its point lies within rounding of the half-pixel edge, values within 1e-3
-on a random image (position error x image gradient) and 1e-5 on a linear one.
+where its point lies within 1e-3 px of the half-pixel edge of the native image
+or its ray within 1e-5 rad of the end of the projection's invertible range
+(decided pixel by pixel from the oracle's coordinates), values within 1e-3 on a
+random image (position error x image gradient) and 1e-5 on a linear one.
 Adam: FP32 against FP64, moments within 1e-5 relative, parameters within
 1e-6 + 1e-5 relative."""
 import math
@@ -42,10 +44,18 @@ def test_native_to_beap_matches_oracle(geer, T, name, cam):
     rng = np.random.default_rng(len(name))
     native = rng.uniform(0, 1, (cam.height, cam.width, 3)).astype(np.float32)
     out, valid = geer.native_to_beap(torch.as_tensor(native, device="cuda"), cam)
-    ref, rvalid = T.native_to_beap(cam, native)
+    ref, rvalid, uv, pmargin = T.native_to_beap(cam, native, coords=True)
     out, valid = out.cpu().numpy(), valid.cpu().numpy()
     both = (valid == 1) & (rvalid == 1)
-    assert (valid != rvalid).sum() <= max(2, cam.pixels // 500), (name, (valid != rvalid).sum())
+    # every pixel whose validity differs lies within FP32 rounding of a decision edge
+    u, v = uv[..., 0], uv[..., 1]
+    w, h = cam.width, cam.height
+    with np.errstate(invalid="ignore"):
+        edge_px = np.minimum.reduce([np.abs(u + 0.5), np.abs(u - (w - 0.5)), np.abs(v + 0.5),
+                                     np.abs(v - (h - 0.5))])
+    near = (np.nan_to_num(edge_px, nan=np.inf) <= 1e-3) | (np.abs(np.nan_to_num(pmargin, nan=np.inf)) <= 1e-5)
+    differ = valid != rvalid
+    assert not (differ & ~near).any(), (name, np.argwhere(differ & ~near)[:5])
     assert np.abs(out[both] - ref[both]).max() < 1e-3, name
     assert np.all(out[valid == 0] == 0.0)
     # exact on a linear image: only the FP32 position error remains

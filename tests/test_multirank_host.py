@@ -1,6 +1,7 @@
-"""The N > 1 path of bench.py on CPU with world-size-2 gloo ranks: every rank
-renders its own replica, the step time is the maximum over ranks and the value
-counts every rank's pixels (no GPU, no data-path collective)."""
+"""The N > 1 path of bench.py on CPU with world-size-2 gloo ranks: the step time
+is the maximum over ranks; with replicas the value counts every rank's pixels
+(no data-path collective), with the tile split the ranks share one frame's
+pixels (no GPU)."""
 import os
 import socket
 
@@ -23,7 +24,10 @@ def _worker(rank, world, port, q):
     import bench
     local_ms = [120.0, 150.0][rank]
     value, t = bench.aggregate(local_ms, pixels_per_rank=1_000_000, steps=10, world=world, dist=dist, device="cpu")
-    q.put((rank, value, t))
+    # the tile split: the ranks share one frame (strong scaling)
+    shared, ts = bench.aggregate(local_ms, pixels_per_rank=1_000_000, steps=10, world=world, dist=dist,
+                                 device="cpu", shared=True)
+    q.put((rank, value, t, shared, ts))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -39,9 +43,10 @@ def test_aggregate_max_over_two_gloo_ranks():
         p.join(120)
         assert p.exitcode == 0
     res = sorted(q.get(timeout=10) for _ in range(2))
-    for rank, value, t in res:
-        assert t == pytest.approx(150.0)
+    for rank, value, t, shared, ts in res:
+        assert t == pytest.approx(150.0) and ts == pytest.approx(150.0)
         assert value == pytest.approx(2 * 1_000_000 * 10 / 0.150 / 1e6)
+        assert shared == pytest.approx(1_000_000 * 10 / 0.150 / 1e6)
 
 
 def test_single_rank_aggregate_is_local():
