@@ -42,7 +42,8 @@ typedef enum {
     GEER_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     GEER_ERR_TIMEOUT = 4,     /* reserved: the library has no device-side waits */
     GEER_ERR_UNSUPPORTED = 5, /* a valid request the library does not implement */
-    GEER_ERR_STATE = 6        /* call out of order (e.g. render before bin_sort) */
+    GEER_ERR_STATE = 6,       /* call out of order (e.g. render before bin_sort) */
+    GEER_ERR_BOUNDS = 7       /* checked build: a device bounds guard skipped an access */
 } geer_status;
 
 /* Camera models (App. E): pinhole K (tan theta, tan phi, 1); equidistant
@@ -271,10 +272,39 @@ geer_status geer_tile_owners(const geer_camera *cams, int32_t n_cams, int32_t n_
  * synchronises `stream`). */
 geer_status geer_set_tile_mask(geer_workspace *ws, const uint8_t *mask, int64_t n_tiles, void *stream);
 
-/* Synchronise `stream`, then read and clear the device status word: GEER_OK or
- * GEER_ERR_CAPACITY (pairs exceeded capacity). *pairs (may be NULL) receives
- * the last pair count. */
+/* Synchronise `stream`, then read and clear the device status word: GEER_OK,
+ * GEER_ERR_CAPACITY (pairs exceeded capacity) or, in the checked build,
+ * GEER_ERR_BOUNDS (a bounds guard skipped an access; geer_bounds_violation
+ * tells where). *pairs (may be NULL) receives the last pair count. */
 geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *stream);
+
+/* The checked build. Every kernel index that comes from an earlier kernel's
+ * output (a tile from the render order, a super-tile list range, an item id of
+ * a sorted pair, a super-tile id of an emitted pair) is guarded: when it lies
+ * outside its array the access is skipped (an unrendered tile, an empty list,
+ * a record no ray hits, an uncounted pair) instead of reading or writing out
+ * of bounds. libgeer.so keeps the guards silent; libgeer_checked.so (the same
+ * sources built with GEER_CHECKED=1, the stand-in for a memory checker) also
+ * records the first failing guard: its site and index, with the status bit that
+ * geer_last_device_status reports as GEER_ERR_BOUNDS.
+ *
+ * geer_checked_build: 1 in libgeer_checked.so, 0 in libgeer.so. */
+int32_t geer_checked_build(void);
+
+/* Synchronise `stream`, then read the first recorded bounds violation: *site
+ * (0: none; 1 forward tile, 2 forward list range, 3 forward item, 4 backward
+ * tile, 5 backward list range, 6 backward item, 7 duplicated pair's super-tile)
+ * and *index (the offending value). A violation read is cleared, with its
+ * status bit. Always GEER_OK with *site = 0 in libgeer.so. */
+geer_status geer_bounds_violation(geer_workspace *ws, uint32_t *site, int64_t *index, void *stream);
+
+/* Inspection (synchronous): after geer_bin_sort, replace the order in which
+ * the forward's blocks take the tiles (order: HOST u32 [n], n the camera set's
+ * tile count). Every permutation of the tiles renders the same image; the
+ * order only schedules. GEER_ERR_ARG for an entry beyond the current tiles
+ * (libgeer.so) or beyond the workspace's tile capacity (libgeer_checked.so,
+ * which lets the tiles in between through to exercise its device guards). */
+geer_status geer_debug_set_render_order(geer_workspace *ws, const uint32_t *order, int64_t n, void *stream);
 
 /* Debug/inspection (synchronous): copy the per-(camera, Gaussian) preprocess
  * results into HOST buffers, each sized n_cams * n (any may be NULL):

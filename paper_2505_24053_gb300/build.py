@@ -16,6 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgeer.so")
+# the checked build: the same sources with GEER_CHECKED=1 (bounds guards record
+# their first violation in the device status word)
+OUT_CHECKED = os.path.join(OUT, "checked")
+LIB_CHECKED = os.path.join(OUT, "libgeer_checked.so")
 SOURCES = ["geer_host.cu", "preprocess.cu", "sort.cu", "render.cu", "backward.cu", "remap.cu", "metrics.cu", "train.cu", "densify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -42,34 +46,44 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, checked: bool | None = False) -> str:
+    """Compile and link libgeer.so (checked=False), libgeer_checked.so
+    (checked=True) or both (checked=None: all translation units of both
+    compiled in parallel). Returns the path of the last library linked."""
+    variants = [False, True] if checked is None else [bool(checked)]
     cc = nvcc()
-    procs = []
-    objs = []
-    for src in SOURCES:
-        s = os.path.join(CSRC, src)
-        o = os.path.join(OUT, src.replace(".cu", ".o"))
-        objs.append(o)
-        if force or verbose_ptxas or _stale(o, s):
-            cmd = [cc, *flags(verbose_ptxas), "-c", s, "-o", o]
-            procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+    jobs = []  # (variant, source, process)
+    objs = {v: [] for v in variants}
+    for v in variants:
+        out_dir = OUT_CHECKED if v else OUT
+        os.makedirs(out_dir, exist_ok=True)
+        for src in SOURCES:
+            s = os.path.join(CSRC, src)
+            o = os.path.join(out_dir, src.replace(".cu", ".o"))
+            objs[v].append(o)
+            if force or verbose_ptxas or _stale(o, s):
+                cmd = [cc, *flags(verbose_ptxas), *(["-DGEER_CHECKED=1"] if v else []), "-c", s, "-o", o]
+                jobs.append((v, src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
+                                                      text=True)))
     failed = []
-    for src, p in procs:
+    for v, src, p in jobs:
         out, _ = p.communicate()
         if out.strip():
-            sys.stderr.write(f"--- nvcc {src}\n{out}")
+            sys.stderr.write(f"--- nvcc {src}{' (checked)' if v else ''}\n{out}")
         if p.returncode != 0:
-            failed.append(src)
+            failed.append(src + (" (checked)" if v else ""))
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    if procs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp"
-        subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-        os.replace(tmp, LIB)
-    return LIB
+    lib = LIB
+    for v in variants:
+        lib = LIB_CHECKED if v else LIB
+        if any(jv == v for jv, _, _ in jobs) or not os.path.exists(lib):
+            tmp = lib + ".tmp"
+            subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs[v]], check=True)
+            os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv)
-    print(LIB)
+    build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, checked=None)
+    print(LIB, LIB_CHECKED)

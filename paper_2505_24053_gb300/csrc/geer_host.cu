@@ -452,6 +452,7 @@ const char *geer_status_string(geer_status s) {
         case GEER_ERR_TIMEOUT: return "bounded device wait timed out";
         case GEER_ERR_UNSUPPORTED: return "unsupported";
         case GEER_ERR_STATE: return "call out of order";
+        case GEER_ERR_BOUNDS: return "a device bounds guard skipped an access";
     }
     return "unknown status";
 }
@@ -741,6 +742,48 @@ geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *st
             return GEER_ERR_CUDA;
     }
     if (m[kMiscStatus] & kStatusCapacity) return GEER_ERR_CAPACITY;
+    if (m[kMiscStatus] & kStatusBounds) return GEER_ERR_BOUNDS;
+    return GEER_OK;
+}
+
+int32_t geer_checked_build(void) { return GEER_CHECKED; }
+
+geer_status geer_bounds_violation(geer_workspace *ws, uint32_t *site, int64_t *index, void *stream) {
+    if (!ws || !site || !index) return GEER_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t m[kMiscCount];
+    if (cudaMemcpyAsync(m, ws->d_misc, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    *site = m[kMiscCheckSite];
+    *index = (int64_t)(((uint64_t)m[kMiscCheckHi] << 32) | (uint64_t)m[kMiscCheckLo]);
+    if (*site != 0) {
+        const uint32_t zero[3] = {0u, 0u, 0u};
+        const uint32_t status = m[kMiscStatus] & ~kStatusBounds;
+        if (cudaMemcpyAsync(ws->d_misc + kMiscCheckSite, zero, sizeof(zero), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(ws->d_misc + kMiscStatus, &status, sizeof(status), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return GEER_ERR_CUDA;
+    }
+    return GEER_OK;
+}
+
+geer_status geer_debug_set_render_order(geer_workspace *ws, const uint32_t *order, int64_t n, void *stream) {
+    if (!ws || (!order && n > 0)) return GEER_ERR_ARG;
+    if (ws->stage < 2) return GEER_ERR_STATE;
+    if (n != ws->n_tiles) return GEER_ERR_ARG;
+    // tile indices must lie within the current camera set; a checked build lets
+    // through indices within the workspace's tile capacity, for its device guards
+    const int64_t limit = GEER_CHECKED ? ws->cap_tiles : ws->n_tiles;
+    for (int64_t i = 0; i < n; ++i)
+        if ((int64_t)order[i] >= limit) return GEER_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n > 0 && (cudaMemcpyAsync(ws->d_tile_order, order, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s) !=
+                      cudaSuccess ||
+                  cudaStreamSynchronize(s) != cudaSuccess))
+        return GEER_ERR_CUDA;
     return GEER_OK;
 }
 

@@ -26,6 +26,7 @@ constexpr int kSmemTiles = 12288;          // per-block tile histogram in shared
 // Device status word bits.
 constexpr uint32_t kStatusCapacity = 1u;
 constexpr uint32_t kStatusListOverflow = 2u;  // inspection: a tile list differs from its counted length
+constexpr uint32_t kStatusBounds = 4u;        // GEER_CHECKED build: a bounds guard skipped an access
 
 // Indices into the misc u32 array of the workspace.
 enum Misc : int {
@@ -38,8 +39,45 @@ enum Misc : int {
     kMiscTileHi = 7,      // P / 2^32
     kMiscSortDone = 8,    // radix histogram blocks finished in the current pass
     kMiscSortSame = 9,    // the current pass's digit is the same for every key (an identity pass)
+    kMiscCheckSite = 10,  // GEER_CHECKED build: site of the first bounds violation (0: none)
+    kMiscCheckLo = 11,    // its index mod 2^32
+    kMiscCheckHi = 12,    // its index / 2^32
     kMiscCount = 32
 };
+
+#ifndef GEER_CHECKED
+#define GEER_CHECKED 0  // 1: bounds guards record their first violation (libgeer_checked.so)
+#endif
+
+// Sites of the bounds guards (reported by geer_bounds_violation).
+enum CheckSite : uint32_t {
+    kSiteFwdTile = 1,     // render forward: tile index from the render order
+    kSiteFwdList = 2,     // render forward: super-tile list range [start, end) against the pair capacity
+    kSiteFwdItem = 3,     // render forward: item id from the sorted pairs
+    kSiteBwdTile = 4,     // render backward: tile index from the backward order
+    kSiteBwdList = 5,     // render backward: super-tile list range
+    kSiteBwdItem = 6,     // render backward: item id (record gather, accumulator scatter)
+    kSiteDupSuper = 7,    // duplicate: super-tile id of an emitted pair
+};
+
+// Guard of an index that comes from an earlier kernel (or from the caller's
+// data): true when i < n; otherwise the caller skips the access. In a
+// GEER_CHECKED build a failing guard also records the first violation (site,
+// index) next to the device status word, where geer_bounds_violation reads it.
+__device__ __forceinline__ bool in_bounds(uint64_t i, uint64_t n, uint32_t site, uint32_t *misc) {
+    if (i < n) return true;
+#if GEER_CHECKED
+    if (atomicCAS(misc + kMiscCheckSite, 0u, site) == 0u) {
+        misc[kMiscCheckLo] = (uint32_t)i;
+        misc[kMiscCheckHi] = (uint32_t)(i >> 32);
+    }
+    atomicOr(misc + kMiscStatus, kStatusBounds);
+#else
+    (void)site;
+    (void)misc;
+#endif
+    return false;
+}
 
 // One camera as the kernels see it. Angles and tables are precomputed on the
 // host in FP64 and rounded to FP32.

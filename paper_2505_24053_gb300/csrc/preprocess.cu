@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_gather_counts(const DevCam *__
 __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
     const DevCam *__restrict__ cams, const float4 *__restrict__ ttab, int64_t n, int S,
     const uint32_t *__restrict__ sorted_id, const uint4 *__restrict__ ranges, const uint32_t *__restrict__ count,
-    const uint32_t *__restrict__ misc, const uint32_t *__restrict__ blocksum, uint32_t *__restrict__ okeys,
+    uint32_t *__restrict__ misc, const uint32_t *__restrict__ blocksum, uint32_t *__restrict__ okeys,
     uint32_t *__restrict__ ovals, uint32_t *__restrict__ scount, int nst, int64_t cap) {
     grid_dep_sync();
     __shared__ uint32_t wsum[kPrepThreads / 32];
@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
             const uint32_t st = o_sb + ky * (uint32_t)o_sx + kx;
             okeys[o_off + k] = st;
             ovals[o_off + k] = o_item;
-            atomicAdd(smem ? &sh[st] : &scount[st], 1u);
+            if (in_bounds(st, (uint64_t)nst, kSiteDupSuper, misc)) atomicAdd(smem ? &sh[st] : &scount[st], 1u);
         }
     }
     // per-thread emission of the other items (flipped angular ranges)
@@ -895,7 +895,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
                 const uint32_t st = (uint32_t)(cam.stile_base + sy * cam.stiles_x + sx);
                 okeys[o] = st;
                 ovals[o] = item;
-                atomicAdd(smem ? &sh[st] : &scount[st], 1u);
+                if (in_bounds(st, (uint64_t)nst, kSiteDupSuper, misc)) atomicAdd(smem ? &sh[st] : &scount[st], 1u);
                 ++o;
             }
         });

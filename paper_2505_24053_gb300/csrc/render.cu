@@ -205,6 +205,30 @@ struct WalkSmem {
     int cam;
 };
 
+// Copies item `id`'s 64-byte record into shared memory (4 x 16 B). An id beyond
+// the items (a guard failure) stages a record that no ray hits: W = 0 gives
+// kappa = 0/0 and o_u . d_u = 0 (the exact integral's test fails), and
+// log2(sigma) = -inf fails the splat alpha's.
+__device__ __forceinline__ void stage_record(float4 *dst, const Record *__restrict__ rec, uint32_t id, uint64_t items,
+                                             uint32_t site, uint32_t *misc) {
+    if (in_bounds(id, items, site, misc)) {
+        const float4 *src = reinterpret_cast<const float4 *>(rec + id);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = src[k];
+    } else {
+        dst[0] = dst[1] = dst[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        dst[3] = make_float4(-INFINITY, 0.0f, 0.0f, 0.0f);
+    }
+}
+
+// A tile's super-tile list range must lie within the sorted pairs; a guard
+// failure leaves the tile an empty list.
+__device__ __forceinline__ uint2 checked_range(uint2 sr, int64_t cap_pairs, uint32_t site, uint32_t *misc) {
+    if (!in_bounds(sr.y, (uint64_t)cap_pairs + 1u, site, misc) || !in_bounds(sr.x, (uint64_t)sr.y + 1u, site, misc))
+        return make_uint2(0u, 0u);
+    return sr;
+}
+
 // Per-ray forward state (n_eval: entries evaluated, set when the walk ends).
 struct FwdRay {
     float T, cr, cg, cb;
@@ -225,7 +249,7 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                                              const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
                                              const Params &p, const float4 &col, const float4 &row, int cx, int cy,
                                              uint2 sr, float dx, float dy, float dz, uint2 *__restrict__ hit_rec,
-                                             int64_t hit_entries, FwdRay &f) {
+                                             int64_t hit_entries, uint64_t items, uint32_t *misc, FwdRay &f) {
     const int tid = threadIdx.x;
     uint8_t *const hit_b = reinterpret_cast<uint8_t *>(sm.hit) + (tid >> 5);  // this warp's byte of entry 0
     if (tid == 0) {
@@ -243,9 +267,7 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
         const int cnt = min(s_cnt, BATCH);
         if (cnt == 0) break;
         for (int r = tid; r < cnt; r += kThreads) {
-            const float4 *src = reinterpret_cast<const float4 *>(rec + sm.id[r]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) sm.rec[r * 4 + k] = src[k];
+            stage_record(sm.rec + r * 4, rec, sm.id[r], items, kSiteFwdItem, misc);
             sm.hit[r] = make_uint2(0u, 0u);
         }
         __syncthreads();
@@ -376,19 +398,22 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                                             const uint32_t *__restrict__ svals,
                                                             const uint4 *__restrict__ sranges,
                                                             const Record *__restrict__ rec,
-                                                            const uint32_t *__restrict__ misc, Params p,
+                                                            uint32_t *__restrict__ misc, Params p,
                                                             float *__restrict__ rgb,
                                                             float *__restrict__ Tout, float *__restrict__ Tfin,
                                                             uint32_t *__restrict__ last_out,
                                                             uint2 *__restrict__ evals, uint2 *__restrict__ hit,
                                                             int64_t hit_entries,
-                                                            const uint8_t *__restrict__ tile_mask) {
+                                                            const uint8_t *__restrict__ tile_mask, int64_t ntiles,
+                                                            uint64_t items, int64_t cap_pairs) {
     grid_dep_sync();
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     static_assert(kParts == 1, "one block per tile: the block records the tile's walk");
     __shared__ WalkSmem<kThreads, BATCH> sm;
     if (misc[kMiscStatus] & kStatusCapacity) return;
-    const int t = (int)tile_order[blockIdx.x];
+    const uint32_t t_id = tile_order[blockIdx.x];
+    if (!in_bounds(t_id, (uint64_t)ntiles, kSiteFwdTile, misc)) return;  // block-uniform
+    const int t = (int)t_id;
     if (threadIdx.x == 0) sm.cam = find_cam(cams, ncams, t);
     __syncthreads();
     const DevCam &cam = cams[sm.cam];
@@ -397,6 +422,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         if (threadIdx.x == 0) tile_walk[t] = make_uint2(0u, 0u);
         return;
     }
+    tr.sr = checked_range(tr.sr, cap_pairs, kSiteFwdList, misc);
     if (tile_mask && !tile_mask[t]) {  // another part's tile: zeros, nothing for the backward to walk
         if (threadIdx.x == 0) tile_walk[t] = make_uint2(0u, 0u);
         if (tr.inside) {
@@ -418,7 +444,8 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         tr.dy = ps;
     }
     forward_walk<kThreads, BATCH, SPLAT>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy,
-                                         tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, f);
+                                         tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, items,
+                                         misc, f);
     if (threadIdx.x == 0) tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
     if (tr.inside) {
         const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
@@ -562,7 +589,8 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
                                               const Params &p, const float4 &col, const float4 &row, int cx, int cy,
                                               uint2 sr, uint2 walk, uint32_t warp_last, uint32_t block_last,
                                               const uint2 *__restrict__ hit_rec, int64_t hit_entries, int fwarp,
-                                              BwdRay &ray, GradAcc *__restrict__ gacc) {
+                                              BwdRay &ray, GradAcc *__restrict__ gacc, uint64_t items,
+                                              uint32_t *misc) {
     const int tid = threadIdx.x, lane = tid & 31;
     const float log2_amin = log2f(p.alpha_min);
     // entry r of a batch has list index top - 1 - r
@@ -575,9 +603,7 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
         // entries at or beyond the block's last contributor are not walked
         const int skip = top > block_last ? (int)min((uint32_t)cnt, top - block_last) : 0;
         for (int r = skip + tid; r < cnt; r += kThreads) {
-            const float4 *src = reinterpret_cast<const float4 *>(rec + sm.id[r]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) sm.rec[r * 4 + k] = src[k];
+            stage_record(sm.rec + r * 4, rec, sm.id[r], items, kSiteBwdItem, misc);
             // beyond the recorded entries every warp evaluates
             const uint32_t j = top - 1u - (uint32_t)r;
             // transposed to warp-major order: warp w's flags of the batch are contiguous
@@ -652,7 +678,7 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
             bool any = false;
 #pragma unroll
             for (int k = 0; k < 16; ++k) any |= v[k] != 0.0f;
-            if (any) {
+            if (any && in_bounds(sm.id[r], items, kSiteBwdItem, misc)) {
                 float4 *dst = reinterpret_cast<float4 *>(gacc + sm.id[r]);
                 atomicAdd(dst + 0, make_float4(v[0], v[1], v[2], v[3]));
                 atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
@@ -694,19 +720,22 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
                                                                            const uint32_t *__restrict__ svals,
                                                                            const uint4 *__restrict__ sranges,
                                                                            const Record *__restrict__ rec,
-                                                                           const uint32_t *__restrict__ misc, Params p,
+                                                                           uint32_t *__restrict__ misc, Params p,
                                                                            const float *__restrict__ dL_drgb,
                                                                            const float *__restrict__ Tfin,
                                                                            const uint32_t *__restrict__ last_in,
                                                                            const uint2 *__restrict__ hit,
                                                                            int64_t hit_entries,
-                                                                           GradAcc *__restrict__ gacc) {
+                                                                           GradAcc *__restrict__ gacc, int64_t ntiles,
+                                                                           uint64_t items, int64_t cap_pairs) {
     grid_dep_sync();
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     __shared__ WalkSmem<kThreads, BATCH> sm;
     __shared__ float s_acc[BATCH][17];
     if (misc[kMiscStatus] & kStatusCapacity) return;
-    const int t = (int)tile_order[blockIdx.x / kParts], part = blockIdx.x % kParts;
+    const uint32_t t_id = tile_order[blockIdx.x / kParts];
+    if (!in_bounds(t_id, (uint64_t)ntiles, kSiteBwdTile, misc)) return;  // block-uniform
+    const int t = (int)t_id, part = blockIdx.x % kParts;
     if (threadIdx.x == 0) {
         sm.cam = find_cam(cams, ncams, t);
         sm.maxlast = 0u;
@@ -715,6 +744,7 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
     const DevCam &cam = cams[sm.cam];
     TileRay tr;
     if (!tile_ray(cam, t, part * ROWS, ptab, ttab, srange, S, tr)) return;
+    tr.sr = checked_range(tr.sr, cap_pairs, kSiteBwdList, misc);
     float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, T = 1.0f;
     uint32_t last = 0;
     if (tr.inside) {
@@ -738,9 +768,12 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
     if (block_last == 0) return;
     // the forward's warp of these rays: its rows 2w, 2w + 1 of the tile
     const int fwarp = (part * ROWS * kTile + (int)threadIdx.x) >> 5;
+    uint2 walk = tile_walk[t];
+    if (!in_bounds(walk.x, (uint64_t)tr.sr.y + 1u, kSiteBwdList, misc)) walk = make_uint2(0u, 0u);
     backward_walk<kThreads, BATCH, SPLAT>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr,
-                                   tile_walk[t], warp_last, block_last,
-                                   hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, fwarp, ray, gacc);
+                                   walk, warp_last, block_last,
+                                   hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, fwarp, ray, gacc,
+                                   items, misc);
 }
 
 }  // namespace
@@ -754,7 +787,8 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         ws->params, rgb, T_final,
         ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->hit_entries,
-        ws->tile_mask_on ? static_cast<const uint8_t *>(ws->d_tile_mask) : nullptr);
+        ws->tile_mask_on ? static_cast<const uint8_t *>(ws->d_tile_mask) : nullptr, ws->n_tiles,
+        (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs);
     return cudaGetLastError();
 }
 
@@ -774,7 +808,8 @@ cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cu
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_bwd_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         ws->params, dL_drgb,
-        ws->d_Tfin, ws->d_last, ws->d_hit, ws->hit_entries, ws->d_gacc);
+        ws->d_Tfin, ws->d_last, ws->d_hit, ws->hit_entries, ws->d_gacc, ws->n_tiles,
+        (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs);
     return cudaGetLastError();
 }
 

@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_STATE = range(7)
+OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_STATE, ERR_BOUNDS = range(8)
 PINHOLE, EQUIDISTANT, KANNALA_BRANDT = 0, 1, 2
 
 
@@ -50,25 +50,32 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_pair_counts", "geer_debug_render_state", "geer_densify_accumulate", "geer_densify_scratch_bytes",
            "geer_densify_plan", "geer_densify_apply", "geer_opacity_reset", "geer_render_bwd_tiles",
            "geer_grad_accumulators", "geer_preprocess_bwd", "geer_tile_owners", "geer_set_tile_mask",
-           "geer_tile_counts"]
+           "geer_tile_counts", "geer_checked_build", "geer_bounds_violation", "geer_debug_set_render_order"]
 
 _lib = None
 
 
-def library_path() -> str:
-    return _build.LIB
+_lib_checked = None
 
 
-def lib(build_if_missing: bool = True):
-    """Load libgeer.so (building it in-tree first if it is missing)."""
-    global _lib
-    if _lib is not None:
+def library_path(checked: bool = False) -> str:
+    return _build.LIB_CHECKED if checked else _build.LIB
+
+
+def lib(build_if_missing: bool = True, checked: bool = False):
+    """Load libgeer.so, or with checked=True libgeer_checked.so (the build whose
+    bounds guards record their first violation), building it in-tree first if
+    it is missing."""
+    global _lib, _lib_checked
+    if checked and _lib_checked is not None:
+        return _lib_checked
+    if not checked and _lib is not None:
         return _lib
-    path = library_path()
+    path = library_path(checked)
     if not os.path.exists(path):
         if not build_if_missing:
-            raise RuntimeError(f"libgeer.so not built ({path}); run paper_2505_24053_gb300/build.py")
-        _build.build()
+            raise RuntimeError(f"{os.path.basename(path)} not built ({path}); run paper_2505_24053_gb300/build.py")
+        _build.build(checked=checked)
     L = C.CDLL(path)
     P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
     L.geer_status_string.restype = C.c_char_p
@@ -111,6 +118,8 @@ def lib(build_if_missing: bool = True):
         "geer_tile_owners": [P, I32, I32, P],
         "geer_set_tile_mask": [P, P, I64, P],
         "geer_tile_counts": [P, P, P],
+        "geer_bounds_violation": [P, P, P, P],
+        "geer_debug_set_render_order": [P, P, I64, P],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -118,7 +127,12 @@ def lib(build_if_missing: bool = True):
         f.argtypes = args
     L.geer_densify_scratch_bytes.restype = C.c_size_t
     L.geer_densify_scratch_bytes.argtypes = [I64]
-    _lib = L
+    L.geer_checked_build.restype = C.c_int32
+    L.geer_checked_build.argtypes = []
+    if checked:
+        _lib_checked = L
+    else:
+        _lib = L
     return L
 
 
@@ -205,8 +219,8 @@ class Workspace:
     """A geer workspace in a torch-owned device buffer."""
 
     def __init__(self, cams, n_gauss: int, sh_degree: int, pair_capacity: int, params: ParamsC | None = None,
-                 device=None):
-        L = lib()
+                 device=None, library=None):
+        L = self._L = library or lib()
         self.cams = list(cams)
         self._cams_c = cameras_c(self.cams)
         self.n_gauss, self.sh_degree, self.pair_capacity = int(n_gauss), int(sh_degree), int(pair_capacity)
@@ -227,8 +241,9 @@ class Workspace:
 
     def __del__(self):
         h = getattr(self, "_handle", None)
-        if h is not None and h.value and _lib is not None:
-            _lib.geer_workspace_destroy(h)
+        L = getattr(self, "_L", None)
+        if h is not None and h.value and L is not None:
+            L.geer_workspace_destroy(h)
             self._handle = None
 
     @property
@@ -238,7 +253,7 @@ class Workspace:
     def set_cameras(self, cams, stream=None):
         self.cams = list(cams)
         self._cams_c = cameras_c(self.cams)
-        _check(lib().geer_set_cameras(self._handle, self._cams_c, len(self.cams), _stream(stream)),
+        _check(self._L.geer_set_cameras(self._handle, self._cams_c, len(self.cams), _stream(stream)),
                "geer_set_cameras")
         self.pixels = sum(c.width * c.height for c in self.cams)
 
@@ -246,7 +261,7 @@ class Workspace:
         """Place camera i at fixed slot i (see geer_set_camera_slots); active: list of bools."""
         arr = cameras_c(cams)
         act = (C.c_uint8 * len(cams))(*[1 if a else 0 for a in active])
-        _check(lib().geer_set_camera_slots(self._handle, arr, len(cams), act, int(slot_tiles), int(slot_pixels),
+        _check(self._L.geer_set_camera_slots(self._handle, arr, len(cams), act, int(slot_tiles), int(slot_pixels),
                                            _stream(stream)), "geer_set_camera_slots")
         self.cams = list(cams)
         self._slots = (list(active), int(slot_tiles), int(slot_pixels))
@@ -254,22 +269,22 @@ class Workspace:
     def preprocess(self, g: Gaussians, stream=None):
         self._g = g
         self._gc = g.c_struct()
-        _check(lib().geer_preprocess(self._handle, C.byref(self._gc), _stream(stream)), "geer_preprocess")
+        _check(self._L.geer_preprocess(self._handle, C.byref(self._gc), _stream(stream)), "geer_preprocess")
 
     def bin_sort(self, sync: bool = True, stream=None) -> int | None:
         """Duplicate, sort and range. With sync=True returns the pair count and
         raises GeerError(ERR_CAPACITY) if it exceeds the capacity."""
         if sync:
             need = C.c_int64()
-            st = lib().geer_bin_sort(self._handle, C.byref(need), _stream(stream))
+            st = self._L.geer_bin_sort(self._handle, C.byref(need), _stream(stream))
             self.last_pairs = int(need.value)
             _check(st, "geer_bin_sort")
             return self.last_pairs
-        _check(lib().geer_bin_sort(self._handle, None, _stream(stream)), "geer_bin_sort")
+        _check(self._L.geer_bin_sort(self._handle, None, _stream(stream)), "geer_bin_sort")
         return None
 
     def render_fwd(self, rgb: torch.Tensor, T: torch.Tensor | None = None, stream=None):
-        _check(lib().geer_render_fwd(self._handle, C.c_void_p(rgb.data_ptr()),
+        _check(self._L.geer_render_fwd(self._handle, C.c_void_p(rgb.data_ptr()),
                                      C.c_void_p(T.data_ptr()) if T is not None else None, _stream(stream)),
                "geer_render_fwd")
 
@@ -281,7 +296,7 @@ class Workspace:
             t = grads.get(name)
             return C.c_void_p(t.data_ptr()) if t is not None else None
 
-        _check(lib().geer_render_bwd(self._handle, C.byref(gc), C.c_void_p(dL_drgb.data_ptr()), ptr("mean"),
+        _check(self._L.geer_render_bwd(self._handle, C.byref(gc), C.c_void_p(dL_drgb.data_ptr()), ptr("mean"),
                                      ptr("scale"), ptr("quat"), ptr("opacity"), ptr("sh"), 1 if accumulate else 0,
                                      _stream(stream)),
                "geer_render_bwd")
@@ -289,7 +304,7 @@ class Workspace:
     def render_bwd_tiles(self, dL_drgb: torch.Tensor, stream=None):
         """The render stage of the backward (geer_render_bwd_tiles): the
         per-(camera, Gaussian) accumulators over the rendered tiles' rays."""
-        _check(lib().geer_render_bwd_tiles(self._handle, C.c_void_p(dL_drgb.data_ptr()), _stream(stream)),
+        _check(self._L.geer_render_bwd_tiles(self._handle, C.c_void_p(dL_drgb.data_ptr()), _stream(stream)),
                "geer_render_bwd_tiles")
 
     def grad_accumulators(self) -> torch.Tensor:
@@ -298,7 +313,7 @@ class Workspace:
         over processes, acts on the workspace)."""
         ptr = C.c_void_p()
         n = C.c_int64()
-        _check(lib().geer_grad_accumulators(self._handle, C.byref(ptr), C.byref(n)), "geer_grad_accumulators")
+        _check(self._L.geer_grad_accumulators(self._handle, C.byref(ptr), C.byref(n)), "geer_grad_accumulators")
         off = int(ptr.value or 0) - self.buf.data_ptr()
         nbytes = 4 * int(n.value)
         if n.value == 0:
@@ -314,7 +329,7 @@ class Workspace:
             t = grads.get(name)
             return C.c_void_p(t.data_ptr()) if t is not None else None
 
-        _check(lib().geer_preprocess_bwd(self._handle, C.byref(gc), ptr("mean"), ptr("scale"), ptr("quat"),
+        _check(self._L.geer_preprocess_bwd(self._handle, C.byref(gc), ptr("mean"), ptr("scale"), ptr("quat"),
                                          ptr("opacity"), ptr("sh"), 1 if accumulate else 0, _stream(stream)),
                "geer_preprocess_bwd")
 
@@ -322,15 +337,29 @@ class Workspace:
         """Render only the tiles with mask != 0 (host array of the camera set's
         tile count), or all tiles with mask=None (geer_set_tile_mask)."""
         if mask is None:
-            _check(lib().geer_set_tile_mask(self._handle, None, 0, _stream(stream)), "geer_set_tile_mask")
+            _check(self._L.geer_set_tile_mask(self._handle, None, 0, _stream(stream)), "geer_set_tile_mask")
             return
         m = np.ascontiguousarray(np.asarray(mask).astype(np.uint8))
-        _check(lib().geer_set_tile_mask(self._handle, C.c_void_p(m.ctypes.data), int(m.size), _stream(stream)),
+        _check(self._L.geer_set_tile_mask(self._handle, C.c_void_p(m.ctypes.data), int(m.size), _stream(stream)),
                "geer_set_tile_mask")
+
+    def bounds_violation(self, stream=None):
+        """(site, index) of the first failing bounds guard since the last read
+        ((0, 0) if none; always none outside the checked build)."""
+        site, index = C.c_uint32(), C.c_int64()
+        _check(self._L.geer_bounds_violation(self._handle, C.byref(site), C.byref(index), _stream(stream)),
+               "geer_bounds_violation")
+        return int(site.value), int(index.value)
+
+    def set_render_order(self, order, stream=None):
+        """Replace the forward's tile schedule (geer_debug_set_render_order)."""
+        o = np.ascontiguousarray(np.asarray(order, np.uint32))
+        _check(self._L.geer_debug_set_render_order(self._handle, C.c_void_p(o.ctypes.data), int(o.size),
+                                                   _stream(stream)), "geer_debug_set_render_order")
 
     def device_status(self, stream=None):
         pairs = C.c_int64()
-        st = lib().geer_last_device_status(self._handle, C.byref(pairs), _stream(stream))
+        st = self._L.geer_last_device_status(self._handle, C.byref(pairs), _stream(stream))
         return st, int(pairs.value)
 
     def debug_preprocess(self, stream=None):
@@ -340,7 +369,7 @@ class Workspace:
         keys = np.zeros(m, np.uint32)
         cull = np.zeros(m, np.uint8)
         P = C.c_void_p
-        _check(lib().geer_debug_preprocess(self._handle, P(ranges.ctypes.data), P(counts.ctypes.data),
+        _check(self._L.geer_debug_preprocess(self._handle, P(ranges.ctypes.data), P(counts.ctypes.data),
                                            P(keys.ctypes.data), P(cull.ctypes.data), _stream(stream)),
                "geer_debug_preprocess")
         return cull, keys, ranges, counts
@@ -349,34 +378,34 @@ class Workspace:
         """(evaluations executed, contributors applied, entries walked by the backward)
         of the last forward render."""
         e, a, w = C.c_uint64(), C.c_uint64(), C.c_uint64()
-        _check(lib().geer_render_counts(self._handle, C.byref(e), C.byref(a), C.byref(w), _stream(stream)),
+        _check(self._L.geer_render_counts(self._handle, C.byref(e), C.byref(a), C.byref(w), _stream(stream)),
                "geer_render_counts")
         return int(e.value), int(a.value), int(w.value)
 
     def pair_counts(self, stream=None):
         """(tile-Gaussian associations P, super-tile pairs sorted) of the last bin_sort."""
         t, u = C.c_int64(), C.c_int64()
-        _check(lib().geer_pair_counts(self._handle, C.byref(t), C.byref(u), None, None, _stream(stream)),
+        _check(self._L.geer_pair_counts(self._handle, C.byref(t), C.byref(u), None, None, _stream(stream)),
                "geer_pair_counts")
         return int(t.value), int(u.value)
 
     def live_items(self, stream=None) -> int:
         """Live (camera, Gaussian) items of the last bin_sort."""
         n = C.c_int64()
-        _check(lib().geer_pair_counts(self._handle, None, None, None, C.byref(n), _stream(stream)), "geer_pair_counts")
+        _check(self._L.geer_pair_counts(self._handle, None, None, None, C.byref(n), _stream(stream)), "geer_pair_counts")
         return int(n.value)
 
     def sort_passes(self, stream=None) -> int:
         """Radix passes of the super-tile sort for the current cameras."""
         p = C.c_int32()
-        _check(lib().geer_pair_counts(self._handle, None, None, C.byref(p), None, _stream(stream)), "geer_pair_counts")
+        _check(self._L.geer_pair_counts(self._handle, None, None, C.byref(p), None, _stream(stream)), "geer_pair_counts")
         return int(p.value)
 
     def tile_counts(self, stream=None) -> np.ndarray:
         """Every tile's list length ((tile, Gaussian) associations) after bin_sort."""
         n = sum(((c.width + 15) // 16) * ((c.height + 15) // 16) for c in self.cams)
         out = np.zeros(n, np.uint32)
-        _check(lib().geer_tile_counts(self._handle, C.c_void_p(out.ctypes.data), _stream(stream)), "geer_tile_counts")
+        _check(self._L.geer_tile_counts(self._handle, C.c_void_p(out.ctypes.data), _stream(stream)), "geer_tile_counts")
         return out
 
     def debug_render_state(self, stream=None):
@@ -387,27 +416,27 @@ class Workspace:
         ev = np.zeros((npix, 2), np.uint32)
         last = np.zeros(npix, np.uint32)
         walk = np.zeros((ntiles, 2), np.uint32)
-        _check(lib().geer_debug_render_state(self._handle, C.c_void_p(ev.ctypes.data), C.c_void_p(last.ctypes.data),
+        _check(self._L.geer_debug_render_state(self._handle, C.c_void_p(ev.ctypes.data), C.c_void_p(last.ctypes.data),
                                              C.c_void_p(walk.ctypes.data), _stream(stream)),
                "geer_debug_render_state")
         return ev, last, walk
 
     def enable_timing(self, on: bool = True):
-        _check(lib().geer_enable_timing(self._handle, 1 if on else 0), "geer_enable_timing")
+        _check(self._L.geer_enable_timing(self._handle, 1 if on else 0), "geer_enable_timing")
 
     def stage_times(self, stream=None) -> dict:
         """Mean ms of the recorded occurrences of each stage (timing must be enabled)."""
         ms = (C.c_float * 16)()
         cnt = (C.c_int32 * 16)()
-        _check(lib().geer_stage_times(self._handle, ms, 16, cnt, _stream(stream)), "geer_stage_times")
-        return {lib().geer_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(9)}
+        _check(self._L.geer_stage_times(self._handle, ms, 16, cnt, _stream(stream)), "geer_stage_times")
+        return {self._L.geer_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(9)}
 
     def debug_pairs(self, cap: int | None = None, stream=None):
         cap = self.pair_capacity if cap is None else cap
         keys = np.zeros(cap, np.uint64)
         vals = np.zeros(cap, np.uint32)
         count = C.c_int64()
-        _check(lib().geer_debug_pairs(self._handle, C.c_void_p(keys.ctypes.data), C.c_void_p(vals.ctypes.data), cap,
+        _check(self._L.geer_debug_pairs(self._handle, C.c_void_p(keys.ctypes.data), C.c_void_p(vals.ctypes.data), cap,
                                       C.byref(count), _stream(stream)), "geer_debug_pairs")
         n = min(int(count.value), cap)
         return keys[:n], vals[:n]
@@ -584,7 +613,7 @@ DENSIFY_DEFAULTS = dict(grad_threshold=2e-4, clone_max_scale=0.01, min_opacity=0
 
 def densify_accumulate(ws: "Workspace", d_mean: torch.Tensor, accum: torch.Tensor, denom: torch.Tensor, stream=None):
     """The step's densification statistics (geer_densify_accumulate)."""
-    _check(lib().geer_densify_accumulate(ws.handle, C.c_void_p(d_mean.data_ptr()), C.c_void_p(accum.data_ptr()),
+    _check(ws._L.geer_densify_accumulate(ws.handle, C.c_void_p(d_mean.data_ptr()), C.c_void_p(accum.data_ptr()),
                                          C.c_void_p(denom.data_ptr()), _stream(stream)), "geer_densify_accumulate")
 
 
