@@ -26,9 +26,6 @@ namespace {
 #ifndef GEER_FWD_UNROLL
 #define GEER_FWD_UNROLL 4
 #endif
-#ifndef GEER_FWD_HALVES
-#define GEER_FWD_HALVES 2  // threads per ray in the forward: each batch's entries split between them
-#endif
 constexpr int kFwdUnroll = GEER_FWD_UNROLL;
 #ifndef GEER_BWD_ROWS
 #define GEER_BWD_ROWS 16
@@ -310,42 +307,22 @@ __device__ __forceinline__ void walk_entries(const float4 *srec, int j0, int j1,
     }
 }
 
-// Ray states exchanged between the two halves of a block (HALVES == 2).
-template <int kRays>
-struct HalfSmem {
-    FwdRay front[kRays];  // the first half's state after its entries
-    FwdRay back[kRays];   // the second half's entries composited from T = 1, C = 0 (or its redo)
-};
-
 // The tile's forward walk (the per-CSF loop of Algorithm 1): its list is the
 // super-tile list [sr.x, sr.y) filtered by the association test; batches of
 // records are staged in shared memory and each ray composites them front to
 // back until it terminates. On return sm.maxlast / sm.walkpos hold the tile's
 // walk record: [sr.x, walkpos) of the super-tile list holds tile-list entries
 // 0 .. maxlast - 1.
-//
-// HALVES == 2: the block has two threads per ray, and each batch's entries are
-// split between them. The front half composites the first half of the batch
-// from the ray's state; the back half composites the second half from T = 1,
-// C = 0 at the same time. Front-to-back compositing is associative, (C, T)
-// followed by (C', T') is (C + T C', T T'), so the two parts combine into the
-// ray's state after the batch unless the ray terminates in the back half: a
-// back part whose own transmittance fell below T_min, or whose product with
-// the front's does, is composited again from the front's state with the
-// termination decided entry by entry. A ray of a long, sparse walk thus moves
-// through the list twice as fast; the heaviest tiles end the kernel.
 // SPLAT: the splat alpha (GEER_ALPHA_SPLAT) in place of the ray integral;
 // (dx, dy) then carry the ray's screen angles.
-template <int kRays, int HALVES, int BATCH, bool SPLAT>
-__device__ __forceinline__ void forward_walk(WalkSmem<kRays * HALVES, BATCH> &sm, HalfSmem<kRays> *hx,
-                                             const uint32_t *__restrict__ svals,
+template <int kThreads, int BATCH, bool SPLAT>
+__device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, const uint32_t *__restrict__ svals,
                                              const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
                                              const Params &p, const float4 &col, const float4 &row, int cx, int cy,
                                              uint2 sr, float dx, float dy, float dz, uint2 *__restrict__ hit_rec,
                                              int64_t hit_entries, uint64_t items, uint32_t *misc, FwdRay &f) {
-    constexpr int kThreads = kRays * HALVES;
-    const int tid = threadIdx.x, ray = tid % kRays, half = tid / kRays;
-    uint8_t *const hit_b = reinterpret_cast<uint8_t *>(sm.hit) + (ray >> 5);  // the ray's warp's byte of entry 0
+    const int tid = threadIdx.x;
+    uint8_t *const hit_b = reinterpret_cast<uint8_t *>(sm.hit) + (tid >> 5);  // this warp's byte of entry 0
     if (tid == 0) {
         sm.maxlast = 0u;
         sm.walkpos = sr.x;
@@ -365,49 +342,7 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kRays * HALVES, BATCH> &sm
             sm.hit[r] = make_uint2(0u, 0u);
         }
         __syncthreads();
-        if (HALVES == 1) {
-            if (!f.done) walk_entries<SPLAT>(sm.rec, 0, cnt, n_list, hit_b, p, log2_amin, dx, dy, dz, f);
-        } else {
-            const int h = (cnt + 1) >> 1;  // front: [0, h), back: [h, cnt)
-            FwdRay part = f;
-            if (half) {
-                part.T = 1.0f;
-                part.cr = part.cg = part.cb = 0.0f;
-                part.n_applied = 0u;
-            }
-            if (!f.done)
-                walk_entries<SPLAT>(sm.rec, half ? h : 0, half ? cnt : h, n_list, hit_b, p, log2_amin, dx, dy, dz,
-                                    part);
-            (half ? hx->back : hx->front)[ray] = part;
-            __syncthreads();
-            bool redo = false;
-            if (!f.done) {
-                const FwdRay &a = hx->front[ray];  // after the front entries
-                const FwdRay &b = hx->back[ray];   // the back entries alone
-                if (a.done) {
-                    f = a;
-                } else if (!b.done && a.T * b.T >= p.T_min) {
-                    const float aT = a.T;
-                    f.cr = fmaf(aT, b.cr, a.cr);
-                    f.cg = fmaf(aT, b.cg, a.cg);
-                    f.cb = fmaf(aT, b.cb, a.cb);
-                    f.T = aT * b.T;
-                    f.n_applied = a.n_applied + b.n_applied;
-                    f.last = b.n_applied ? b.last : a.last;
-                } else {
-                    redo = true;  // the ray terminates in the back entries
-                }
-            }
-            if (__syncthreads_or(redo)) {
-                if (redo && half) {
-                    FwdRay r = hx->front[ray];
-                    walk_entries<SPLAT>(sm.rec, h, cnt, n_list, hit_b, p, log2_amin, dx, dy, dz, r);
-                    hx->back[ray] = r;
-                }
-                __syncthreads();
-                if (redo) f = hx->back[ray];
-            }
-        }
+        if (!f.done) walk_entries<SPLAT>(sm.rec, 0, cnt, n_list, hit_b, p, log2_amin, dx, dy, dz, f);
         // the tile's last contributor so far and where it lies in the super-tile list
         const uint32_t wl = __reduce_max_sync(0xffffffffu, f.last);
         if ((tid & 31) == 0) atomicMax(&sm.maxlast, wl);
@@ -460,8 +395,8 @@ __device__ __forceinline__ bool tile_ray(const DevCam &cam, int t, int row0, con
     return true;
 }
 
-template <int ROWS, int HALVES, int BATCH, bool SPLAT>
-__global__ void __launch_bounds__(ROWS * kTile * HALVES, HALVES == 2 ? 2 : 1) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
+template <int ROWS, int BATCH, bool SPLAT>
+__global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
                                                             const float2 *__restrict__ ptab,
                                                             const float4 *__restrict__ ttab, int S,
                                                             uint2 *__restrict__ tile_walk,
@@ -479,29 +414,25 @@ __global__ void __launch_bounds__(ROWS * kTile * HALVES, HALVES == 2 ? 2 : 1) k_
                                                             const uint8_t *__restrict__ tile_mask, int64_t ntiles,
                                                             uint64_t items, int64_t cap_pairs) {
     grid_dep_sync();
-    constexpr int kRays = ROWS * kTile, kParts = kTile / ROWS;
+    constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     static_assert(kParts == 1, "one block per tile: the block records the tile's walk");
-    static_assert(HALVES == 1 || HALVES == 2, "one or two threads per ray");
-    __shared__ WalkSmem<kRays * HALVES, BATCH> sm;
-    __shared__ HalfSmem<HALVES == 2 ? kRays : 1> hx;
+    __shared__ WalkSmem<kThreads, BATCH> sm;
     if (misc[kMiscStatus] & kStatusCapacity) return;
     const uint32_t t_id = tile_order[blockIdx.x];
     if (!in_bounds(t_id, (uint64_t)ntiles, kSiteFwdTile, misc)) return;  // block-uniform
     const int t = (int)t_id;
-    const int ray = (int)threadIdx.x % kRays;
-    const bool writer = (int)threadIdx.x < kRays;  // the front half writes the rays' results
     if (threadIdx.x == 0) sm.cam = find_cam(cams, ncams, t);
     __syncthreads();
     const DevCam &cam = cams[sm.cam];
     TileRay tr;
-    if (!tile_ray(cam, t, 0, ptab, ttab, srange, S, tr, ray)) {
+    if (!tile_ray(cam, t, 0, ptab, ttab, srange, S, tr, (int)threadIdx.x)) {
         if (threadIdx.x == 0) tile_walk[t] = make_uint2(0u, 0u);
         return;
     }
     tr.sr = checked_range(tr.sr, cap_pairs, kSiteFwdList, misc);
     if (tile_mask && !tile_mask[t]) {  // another part's tile: zeros, nothing for the backward to walk
         if (threadIdx.x == 0) tile_walk[t] = make_uint2(0u, 0u);
-        if (tr.inside && writer) {
+        if (tr.inside) {
             const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
             rgb[3 * pix + 0] = 0.0f;
             rgb[3 * pix + 1] = 0.0f;
@@ -519,12 +450,11 @@ __global__ void __launch_bounds__(ROWS * kTile * HALVES, HALVES == 2 ? 2 : 1) k_
         tr.dx = ts;
         tr.dy = ps;
     }
-    forward_walk<kRays, HALVES, BATCH, SPLAT>(sm, HALVES == 2 ? reinterpret_cast<HalfSmem<kRays> *>(&hx) : nullptr,
-                                              svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx,
-                                              tr.dy, tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr,
-                                              hit_entries, items, misc, f);
+    forward_walk<kThreads, BATCH, SPLAT>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy,
+                                         tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, items,
+                                         misc, f);
     if (threadIdx.x == 0) tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
-    if (tr.inside && writer) {
+    if (tr.inside) {
         const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
         rgb[3 * pix + 0] = fmaf(f.T, cam.bg[0], f.cr);
         rgb[3 * pix + 1] = fmaf(f.T, cam.bg[1], f.cg);
@@ -857,9 +787,9 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
 
 cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_final, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
-    constexpr int R = GEER_FWD_ROWS, H = GEER_FWD_HALVES, B = GEER_FWD_BATCH;
-    launch_k(ws->params.alpha_model == GEER_ALPHA_EXACT ? k_render_fwd<R, H, B, false> : k_render_fwd<R, H, B, true>,
-        dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile * H), 0, s,
+    constexpr int R = GEER_FWD_ROWS, B = GEER_FWD_BATCH;
+    launch_k(ws->params.alpha_model == GEER_ALPHA_EXACT ? k_render_fwd<R, B, false> : k_render_fwd<R, B, true>,
+        dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile), 0, s,
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_tile_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         ws->params, rgb, T_final,
