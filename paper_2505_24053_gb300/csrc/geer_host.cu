@@ -310,14 +310,19 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_misc = L.take(sizeof(uint32_t) * kMiscCount);
     size_t o_tr = L.take((sizeof(uint2) + sizeof(uint32_t)) * c.tiles);
     size_t o_to = L.take(sizeof(uint32_t) * c.tiles);
-    size_t o_bo = L.take(sizeof(uint32_t) * c.tiles);
+    const bool bwd = c.hit_entries > 0;  // the forward-only layout has no backward state
+    size_t o_bo = L.take(sizeof(uint32_t) * c.tiles * (bwd ? kCkptMax + 1 : 1));
     size_t o_sr = L.take((sizeof(uint2) + sizeof(uint32_t)) * c.tiles);
     size_t o_last = L.take(sizeof(uint32_t) * c.pixels);
     size_t o_tfin = L.take(sizeof(float) * c.pixels);
     size_t o_ev = L.take(sizeof(uint2) * c.pixels);
     size_t o_gacc = L.take(sizeof(GradAcc) * cg);
     size_t o_hit = L.take(sizeof(uint2) * c.tiles * c.hit_entries);
-    size_t o_mask = L.take(c.hit_entries > 0 ? sizeof(uint8_t) * c.tiles : 0);  // not in the forward-only layout
+    size_t o_mask = L.take(bwd ? sizeof(uint8_t) * c.tiles : 0);  // not in the forward-only layout
+    size_t o_ck = L.take(bwd ? sizeof(float4) * c.tiles * kCkptMax * kTilePix : 0);
+    size_t o_cka = L.take(bwd ? sizeof(uint2) * c.tiles * kCkptMax : 0);
+    size_t o_ckn = L.take(bwd ? sizeof(uint32_t) * c.tiles : 0);
+    size_t o_cf = L.take(bwd ? sizeof(float4) * c.pixels : 0);
     if (base && ws) {
         ws->d_cams = reinterpret_cast<DevCam *>(base + o_cams);
         ws->d_tile_tab = reinterpret_cast<float4 *>(base + o_ttab);
@@ -353,7 +358,11 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_gacc = reinterpret_cast<GradAcc *>(base + o_gacc);
         ws->d_hit = c.hit_entries > 0 ? reinterpret_cast<uint2 *>(base + o_hit) : nullptr;
         ws->hit_entries = c.hit_entries;
-        ws->d_tile_mask = c.hit_entries > 0 ? reinterpret_cast<uint8_t *>(base + o_mask) : nullptr;
+        ws->d_tile_mask = bwd ? reinterpret_cast<uint8_t *>(base + o_mask) : nullptr;
+        ws->d_ckpt = bwd ? reinterpret_cast<float4 *>(base + o_ck) : nullptr;
+        ws->d_ckpt_at = bwd ? reinterpret_cast<uint2 *>(base + o_cka) : nullptr;
+        ws->d_ckpt_cnt = bwd ? reinterpret_cast<uint32_t *>(base + o_ckn) : nullptr;
+        ws->d_Cfin = bwd ? reinterpret_cast<float4 *>(base + o_cf) : nullptr;
     }
     return L.off;
 }
@@ -521,6 +530,7 @@ geer_status geer_workspace_init(void *dev_mem, size_t bytes, const geer_camera *
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) { free(ws); return GEER_ERR_CUDA; }
     ws->sort_grid = ws->num_sms * sort_blocks_per_sm();
+    ws->bwd_grid = ws->num_sms * render_bwd_blocks_per_sm(ws->params.alpha_model);
     ws->stage_bytes = sizeof(DevCam) * c.cams + sizeof(float4) * c.tile_tab + sizeof(float2) * c.pix_tab;
     if (cudaMallocHost(&ws->h_stage, ws->stage_bytes) != cudaSuccess) { free(ws); return GEER_ERR_CUDA; }
     // status words and radix group sums start from zero

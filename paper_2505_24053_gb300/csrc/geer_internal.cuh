@@ -13,6 +13,12 @@ constexpr int kTilePix = kTile * kTile;
 constexpr int kTileWarps = kTilePix / 32;    // warps of a tile's rays (one byte each in the hit record)
 constexpr uint8_t kRegionCentral = 0, kRegionPeripheral = 1, kRegionNone = 255;  // native evaluation regions
 constexpr int64_t kHitEntries = 2048;      // tile-list entries per tile whose hit bytes are recorded
+// Forward checkpoints: the rays' (T, C) at the end of the first forward batch
+// reaching tile-list index kCkptFirst, then every kCkptStride entries, at most
+// kCkptMax per tile. The backward splits a tile's walk there into units that
+// run in parallel.
+constexpr int kCkptMax = 8;
+constexpr uint32_t kCkptFirst = 448, kCkptStride = 512;
 constexpr int kPrepThreads = 256;           // preprocess / duplicate block size
 constexpr int kSortThreads = 256;           // onesweep block size (8 warps)
 constexpr int kSortItems = 12;              // keys per thread per sort tile
@@ -42,6 +48,8 @@ enum Misc : int {
     kMiscCheckSite = 10,  // GEER_CHECKED build: site of the first bounds violation (0: none)
     kMiscCheckLo = 11,    // its index mod 2^32
     kMiscCheckHi = 12,    // its index / 2^32
+    kMiscUnits = 13,      // backward units of the last geer_render_bwd_tiles (tile walks split at checkpoints)
+    kMiscUnitNext = 14,   // the next backward unit to take (persistent blocks)
     kMiscCount = 32
 };
 
@@ -243,7 +251,12 @@ struct geer_workspace {
     uint2 *d_tile_walk;     // [cap_tiles] per tile, where the forward's scan of its super-tile list ended:
                             // (position, tile-list entries found before it); followed by [cap_tiles] u32 scratch
     uint32_t *d_tile_order; // [cap_tiles] tiles by descending super-tile list length: the forward's schedule
-    uint32_t *d_bwd_order;  // [cap_tiles] tiles by descending walked list length: the backward's schedule
+    uint32_t *d_bwd_order;  // [cap_tiles * (kCkptMax + 1)] backward units (tile << 4 | piece) by descending length
+    float4 *d_ckpt;         // [cap_tiles][kCkptMax][kTilePix] rays' (T, C) at the forward's checkpoints (or null)
+    uint2 *d_ckpt_at;       // [cap_tiles][kCkptMax] checkpoint (tile-list index, super-list position)
+    uint32_t *d_ckpt_cnt;   // [cap_tiles] checkpoints recorded by the last forward
+    float4 *d_Cfin;         // [cap_pixels] composited colour before the background (tiles with checkpoints)
+    int bwd_grid;           // persistent backward blocks
     uint4 *d_sranges;       // [cap_pairs] association ranges of the sorted pairs' items (in list order)
     uint2 *d_srange;        // [cap_tiles] super-tile [start, end) in the sorted pairs, followed by [cap_tiles] u32 counts
     uint32_t *d_last;       // [cap_pixels] list entries walked per ray
@@ -317,6 +330,7 @@ cudaError_t launch_opacity_reset(int64_t n, float value, float *logit, float *m_
 cudaError_t launch_image_metrics(const float *pred, const float *gt, int width, int height, const uint8_t *regions,
                                  int n_regions, double *acc, cudaStream_t s);
 int sort_blocks_per_sm();
+int render_bwd_blocks_per_sm(int alpha_model);
 
 inline int64_t prep_blocks(int64_t n) { return (n + kPrepThreads - 1) / kPrepThreads; }
 

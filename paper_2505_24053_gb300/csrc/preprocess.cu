@@ -1042,30 +1042,61 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
     }
 }
 
-// One block: the backward's schedule, tiles by descending length of the list
-// prefix the forward walked (bucketed as for the forward's schedule).
-__global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ tile_walk, int ntiles,
-                                                    const uint32_t *__restrict__ misc,
-                                                    uint32_t *__restrict__ order) {
+// One block: the backward's units and their schedule. A tile whose forward walk
+// covered W > 0 list entries and passed the checkpoints B_1 < ... < B_m < W
+// (the first m of the tile's recorded ones) has the units k = 0..m, entries
+// [B_k, B_{k+1}) with B_0 = 0 and B_{m+1} = W; they are ordered by descending
+// length (bucketed as the forward's schedule), units[slot] = tile << 4 | k.
+// Also sets the unit count and resets the counter the persistent backward
+// blocks take units from.
+__global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ tile_walk,
+                                                    const uint32_t *__restrict__ ckpt_cnt,
+                                                    const uint2 *__restrict__ ckpt_at, int ntiles,
+                                                    uint32_t *__restrict__ misc, uint32_t *__restrict__ order) {
     grid_dep_sync();
     __shared__ uint32_t hist[kOrderBuckets];
+    __shared__ uint32_t s_total;
     if (misc[kMiscStatus] & kStatusCapacity) return;
     const int t = threadIdx.x;
     for (int i = t; i < kOrderBuckets; i += 1024) hist[i] = 0u;
+    if (t == 0) s_total = 0u;
     __syncthreads();
     const int chunk = (ntiles + 1023) / 1024;
     const int b = t * chunk, e = min(ntiles, b + chunk);
-    for (int k = 0; k < chunk; ++k) {
-        const int i = b + k;
-        bucket_add(hist, i < e, i < e ? order_bucket(tile_walk[i].y) : 0);
+    for (int pass = 0; pass < 2; ++pass) {
+        uint32_t mine = 0;
+        for (int c = 0; c < chunk; ++c) {  // the same trip count in every lane (warp-wide atomics)
+            const int i = b + c;
+            uint32_t W = 0, m = 0;
+            if (i < e) {
+                W = tile_walk[i].y;
+                const uint32_t n = ckpt_cnt ? min(ckpt_cnt[i], (uint32_t)kCkptMax) : 0u;
+                while (m < n && ckpt_at[(size_t)i * kCkptMax + m].x < W) ++m;
+            }
+            const uint32_t units = W > 0 ? m + 1 : 0u;
+            for (uint32_t k = 0; __any_sync(0xffffffffu, k < units); ++k) {
+                const bool ok = k < units;
+                uint32_t len = 0;
+                if (ok) {
+                    const uint32_t lo = k == 0 ? 0u : ckpt_at[(size_t)i * kCkptMax + k - 1].x;
+                    const uint32_t hi = k < m ? ckpt_at[(size_t)i * kCkptMax + k].x : W;
+                    len = hi - lo;
+                }
+                const uint32_t slot = bucket_add(hist, ok, order_bucket(len));
+                if (pass == 1 && ok) order[slot] = ((uint32_t)i << 4) | k;
+            }
+            mine += units;
+        }
+        if (pass == 0) {
+            atomicAdd(&s_total, mine);
+            __syncthreads();
+            bucket_scan(hist);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    bucket_scan(hist);
-    __syncthreads();
-    for (int k = 0; k < chunk; ++k) {
-        const int i = b + k;
-        const uint32_t slot = bucket_add(hist, i < e, i < e ? order_bucket(tile_walk[i].y) : 0);
-        if (i < e) order[slot] = (uint32_t)i;
+    if (t == 0) {
+        misc[kMiscUnits] = s_total;
+        misc[kMiscUnitNext] = 0u;
     }
 }
 
@@ -1142,7 +1173,8 @@ cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
 
 cudaError_t launch_bwd_order(const geer_workspace *ws, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
-    launch_k(k_bwd_order, dim3(1), dim3(1024), 0, s, ws->d_tile_walk, (int)ws->n_tiles, ws->d_misc, ws->d_bwd_order);
+    launch_k(k_bwd_order, dim3(1), dim3(1024), 0, s, ws->d_tile_walk, ws->d_ckpt_cnt, ws->d_ckpt_at,
+             (int)ws->n_tiles, ws->d_misc, ws->d_bwd_order);
     return cudaGetLastError();
 }
 

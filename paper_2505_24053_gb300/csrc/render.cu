@@ -12,6 +12,8 @@
 // skipping alpha < alpha_min and Gaussians whose closest approach lies behind
 // the camera (o_u . d_u >= 0), stopping before the contributor that would take
 // the transmittance below T_min (App. B.1 colour equation, 3DGS thresholds).
+#include <algorithm>
+
 #include "geer_internal.cuh"
 
 namespace geer {
@@ -202,6 +204,7 @@ struct WalkSmem {
     uint2 hit[BATCH];                // per entry: one byte per warp of the tile, nonzero if a ray hit it
     uint32_t wcnt[kThreads / 32];
     uint32_t maxlast, walkpos;       // the tile's last contributor and its super-list position + 1
+    uint32_t nck, next_ck;           // forward: checkpoints recorded, list index of the next one
     int cam;
 };
 
@@ -320,12 +323,15 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                                              const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
                                              const Params &p, const float4 &col, const float4 &row, int cx, int cy,
                                              uint2 sr, float dx, float dy, float dz, uint2 *__restrict__ hit_rec,
-                                             int64_t hit_entries, uint64_t items, uint32_t *misc, FwdRay &f) {
+                                             int64_t hit_entries, uint64_t items, uint32_t *misc,
+                                             float4 *__restrict__ ckpt, uint2 *__restrict__ ckpt_at, FwdRay &f) {
     const int tid = threadIdx.x;
     uint8_t *const hit_b = reinterpret_cast<uint8_t *>(sm.hit) + (tid >> 5);  // this warp's byte of entry 0
     if (tid == 0) {
         sm.maxlast = 0u;
         sm.walkpos = sr.x;
+        sm.nck = 0u;
+        sm.next_ck = ckpt ? kCkptFirst : 0xffffffffu;
     }
     const float log2_amin = log2f(p.alpha_min);
     uint32_t pos = sr.x, n_list = 0;
@@ -343,10 +349,22 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
         }
         __syncthreads();
         if (!f.done) walk_entries<SPLAT>(sm.rec, 0, cnt, n_list, hit_b, p, log2_amin, dx, dy, dz, f);
+        // a checkpoint for the backward: every ray's (T, C) in front of tile-list
+        // entry n_list + cnt and where that entry's search starts in the super-tile list
+        // (its state lives in shared memory, advanced by thread 0 after the next
+        // barrier: the walk's registers are at their limit)
+        const uint32_t nck = sm.nck;
+        const bool ck = n_list + (uint32_t)cnt >= sm.next_ck && nck < (uint32_t)kCkptMax;
+        if (ck) ckpt[(size_t)nck * kThreads + tid] = make_float4(f.T, f.cr, f.cg, f.cb);
         // the tile's last contributor so far and where it lies in the super-tile list
         const uint32_t wl = __reduce_max_sync(0xffffffffu, f.last);
         if ((tid & 31) == 0) atomicMax(&sm.maxlast, wl);
         __syncthreads();
+        if (ck && tid == 0) {
+            ckpt_at[nck] = make_uint2(n_list + (uint32_t)cnt, sm.pos[cnt - 1] + 1u);
+            sm.nck = nck + 1u;
+            sm.next_ck = n_list + (uint32_t)cnt + kCkptStride;
+        }
         if (tid == 0 && sm.maxlast > n_list) sm.walkpos = sm.pos[sm.maxlast - 1u - n_list] + 1u;
         // the batch's hit bytes, for the backward's skip of entries its warp never hit
         if (hit_rec)
@@ -412,7 +430,10 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                                             uint2 *__restrict__ evals, uint2 *__restrict__ hit,
                                                             int64_t hit_entries,
                                                             const uint8_t *__restrict__ tile_mask, int64_t ntiles,
-                                                            uint64_t items, int64_t cap_pairs) {
+                                                            uint64_t items, int64_t cap_pairs,
+                                                            float4 *__restrict__ ckpt, uint2 *__restrict__ ckpt_at,
+                                                            uint32_t *__restrict__ ckpt_cnt,
+                                                            float4 *__restrict__ Cfin) {
     grid_dep_sync();
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
     static_assert(kParts == 1, "one block per tile: the block records the tile's walk");
@@ -426,12 +447,18 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
     const DevCam &cam = cams[sm.cam];
     TileRay tr;
     if (!tile_ray(cam, t, 0, ptab, ttab, srange, S, tr, (int)threadIdx.x)) {
-        if (threadIdx.x == 0) tile_walk[t] = make_uint2(0u, 0u);
+        if (threadIdx.x == 0) {
+            tile_walk[t] = make_uint2(0u, 0u);
+            if (ckpt_cnt) ckpt_cnt[t] = 0u;
+        }
         return;
     }
     tr.sr = checked_range(tr.sr, cap_pairs, kSiteFwdList, misc);
     if (tile_mask && !tile_mask[t]) {  // another part's tile: zeros, nothing for the backward to walk
-        if (threadIdx.x == 0) tile_walk[t] = make_uint2(0u, 0u);
+        if (threadIdx.x == 0) {
+            tile_walk[t] = make_uint2(0u, 0u);
+            if (ckpt_cnt) ckpt_cnt[t] = 0u;
+        }
         if (tr.inside) {
             const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
             rgb[3 * pix + 0] = 0.0f;
@@ -452,8 +479,12 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
     }
     forward_walk<kThreads, BATCH, SPLAT>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy,
                                          tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, items,
-                                         misc, f);
-    if (threadIdx.x == 0) tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
+                                         misc, ckpt ? ckpt + (size_t)t * kCkptMax * kThreads : nullptr,
+                                         ckpt ? ckpt_at + (size_t)t * kCkptMax : nullptr, f);
+    if (threadIdx.x == 0) {
+        tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
+        if (ckpt_cnt) ckpt_cnt[t] = sm.nck;
+    }
     if (tr.inside) {
         const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
         rgb[3 * pix + 0] = fmaf(f.T, cam.bg[0], f.cr);
@@ -463,6 +494,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         Tfin[pix] = f.T;
         last_out[pix] = f.last;
         evals[pix] = make_uint2(f.n_eval, f.n_applied);
+        if (Cfin && sm.nck) Cfin[pix] = make_float4(f.cr, f.cg, f.cb, f.T);  // the backward's colour behind
     }
 }
 
@@ -586,15 +618,16 @@ __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const f
     }
 }
 
-// The tile's backward walk: its list read back to front from the walk record
-// (walk.x: super-list position just past the tile's last contributor, walk.y:
-// that contributor's list index + 1), filtered as in the forward.
+// A backward unit's walk: tile-list entries [lo, walk.y) read back to front,
+// filtered as in the forward from super-list positions [plo, walk.x) (walk.x:
+// just past entry walk.y - 1; plo: where entry lo's search starts).
 template <int kThreads, int BATCH, bool SPLAT>
 __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, float (*s_acc)[17],
                                               const uint32_t *__restrict__ svals,
                                               const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
                                               const Params &p, const float4 &col, const float4 &row, int cx, int cy,
-                                              uint2 sr, uint2 walk, uint32_t warp_last, uint32_t block_last,
+                                              uint32_t plo, uint32_t lo, uint2 walk, uint32_t warp_last,
+                                              uint32_t block_last,
                                               const uint2 *__restrict__ hit_rec, int64_t hit_entries, int fwarp,
                                               BwdRay &ray, GradAcc *__restrict__ gacc, uint64_t items,
                                               uint32_t *misc) {
@@ -603,8 +636,8 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
     // entry r of a batch has list index top - 1 - r
     uint32_t pos = walk.x, top = walk.y;
     int s_cnt = 0;
-    while (top > 0) {
-        fill_list_rev<kThreads, BATCH>(svals, sranges, col, row, cx, cy, pos, sr.x, sm.id, s_cnt, sm.wcnt);
+    while (top > lo) {
+        fill_list_rev<kThreads, BATCH>(svals, sranges, col, row, cx, cy, pos, plo, sm.id, s_cnt, sm.wcnt);
         const int cnt = min(s_cnt, BATCH);
         if (cnt == 0) break;
         // entries at or beyond the block's last contributor are not walked
@@ -717,12 +750,21 @@ __device__ __forceinline__ BwdRay bwd_ray(const TileRay &tr, const DevCam &cam, 
     return r;
 }
 
+// The backward in units: a tile's walk [0, W) is split at the forward's
+// checkpoints B_1 < B_2 < ... below W into the units [0, B_1), [B_1, B_2), ...,
+// [B_m, W), each walked back to front by one block. A unit below the top starts
+// every ray that walks past it from the checkpoint's state (T in front of
+// B_{k+1}, and the colour behind it, C_final - C_checkpoint + T_final bg);
+// the top unit starts from the final state. The units are independent, so a
+// tile's long walk runs on several SMs at once and its transmittance is
+// recovered by division over one unit at most. Persistent blocks take units
+// in the order of k_bwd_order (descending length) from a counter.
 template <int ROWS, int BATCH, bool SPLAT>
 __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(const DevCam *__restrict__ cams, int ncams,
                                                                            const float2 *__restrict__ ptab,
                                                                            const float4 *__restrict__ ttab, int S,
                                                                            const uint2 *__restrict__ tile_walk,
-                                                                           const uint32_t *__restrict__ tile_order,
+                                                                           const uint32_t *__restrict__ units,
                                                                            const uint2 *__restrict__ srange,
                                                                            const uint32_t *__restrict__ svals,
                                                                            const uint4 *__restrict__ sranges,
@@ -734,53 +776,96 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
                                                                            const uint2 *__restrict__ hit,
                                                                            int64_t hit_entries,
                                                                            GradAcc *__restrict__ gacc, int64_t ntiles,
-                                                                           uint64_t items, int64_t cap_pairs) {
+                                                                           uint64_t items, int64_t cap_pairs,
+                                                                           const float4 *__restrict__ ckpt,
+                                                                           const uint2 *__restrict__ ckpt_at,
+                                                                           const uint32_t *__restrict__ ckpt_cnt,
+                                                                           const float4 *__restrict__ Cfin) {
     grid_dep_sync();
-    constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
+    constexpr int kThreads = ROWS * kTile;
+    static_assert(ROWS == kTile, "one block per backward unit covers the tile's rays");
     __shared__ WalkSmem<kThreads, BATCH> sm;
     __shared__ float s_acc[BATCH][17];
+    __shared__ uint32_t s_unit;
     if (misc[kMiscStatus] & kStatusCapacity) return;
-    const uint32_t t_id = tile_order[blockIdx.x / kParts];
-    if (!in_bounds(t_id, (uint64_t)ntiles, kSiteBwdTile, misc)) return;  // block-uniform
-    const int t = (int)t_id, part = blockIdx.x % kParts;
-    if (threadIdx.x == 0) {
-        sm.cam = find_cam(cams, ncams, t);
-        sm.maxlast = 0u;
+    const uint32_t n_units = misc[kMiscUnits];
+    while (true) {
+        __syncthreads();  // the previous unit's shared state has been read
+        if (threadIdx.x == 0) {
+            s_unit = atomicAdd(&misc[kMiscUnitNext], 1u);
+            sm.maxlast = 0u;
+        }
+        __syncthreads();
+        const uint32_t u = s_unit;
+        if (u >= n_units) break;
+        const uint32_t code = units[u];
+        const uint32_t t_id = code >> 4, k = code & 15u;
+        if (!in_bounds(t_id, (uint64_t)ntiles, kSiteBwdTile, misc)) continue;  // block-uniform
+        const int t = (int)t_id;
+        if (threadIdx.x == 0) sm.cam = find_cam(cams, ncams, t);
+        __syncthreads();
+        const DevCam &cam = cams[sm.cam];
+        TileRay tr;
+        if (!tile_ray(cam, t, 0, ptab, ttab, srange, S, tr, (int)threadIdx.x)) continue;
+        tr.sr = checked_range(tr.sr, cap_pairs, kSiteBwdList, misc);
+        uint2 walk = tile_walk[t];
+        if (!in_bounds(walk.x, (uint64_t)tr.sr.y + 1u, kSiteBwdList, misc)) walk = make_uint2(0u, 0u);
+        // the unit: tile-list entries [lo, hi), super-list positions [plo, phi)
+        uint32_t lo = 0u, plo = tr.sr.x, hi = walk.y, phi = walk.x;
+        bool top = true;
+        const uint32_t nck = ckpt_cnt ? min(ckpt_cnt[t], (uint32_t)kCkptMax) : 0u;
+        if (k > 0 && k <= nck) {
+            const uint2 a = ckpt_at[(size_t)t * kCkptMax + k - 1];
+            lo = a.x;
+            plo = a.y;
+        }
+        if (k < nck) {
+            const uint2 b = ckpt_at[(size_t)t * kCkptMax + k];
+            if (b.x < walk.y) {
+                hi = b.x;
+                phi = b.y;
+                top = false;
+            }
+        }
+        if (!in_bounds(phi, (uint64_t)walk.x + 1u, kSiteBwdList, misc) ||
+            !in_bounds(plo, (uint64_t)phi + 1u, kSiteBwdList, misc) || lo >= hi)
+            continue;
+        float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, T = 1.0f;
+        uint32_t last = 0;
+        int64_t pix = 0;
+        if (tr.inside) {
+            pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
+            g0 = dL_drgb[3 * pix + 0];
+            g1 = dL_drgb[3 * pix + 1];
+            g2 = dL_drgb[3 * pix + 2];
+            T = Tfin[pix];
+            last = last_in[pix];
+        }
+        if (SPLAT) {  // the ray's screen angles
+            const float ts = atan2f(tr.dx, tr.dz), ps = atan2f(tr.dy, tr.dz);
+            tr.dx = ts;
+            tr.dy = ps;
+        }
+        BwdRay ray = bwd_ray(tr, cam, g0, g1, g2, T, last);
+        if (!top && last > hi) {
+            // the ray walks past this unit: its state in front of entry hi is the forward's checkpoint
+            const float4 c = ckpt[((size_t)t * kCkptMax + k) * kThreads + threadIdx.x];
+            const float4 cf = Cfin[pix];
+            ray.T = c.x;
+            ray.S0 = fmaf(T, cam.bg[0], cf.x - c.y);
+            ray.S1 = fmaf(T, cam.bg[1], cf.y - c.z);
+            ray.S2 = fmaf(T, cam.bg[2], cf.z - c.w);
+        }
+        const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
+        if ((threadIdx.x & 31) == 0) atomicMax(&sm.maxlast, warp_last);
+        __syncthreads();
+        const uint32_t block_last = sm.maxlast;
+        if (block_last <= lo) continue;
+        backward_walk<kThreads, BATCH, SPLAT>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, plo, lo,
+                                              make_uint2(phi, hi), warp_last, block_last,
+                                              hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries,
+                                              (int)threadIdx.x >> 5, ray, gacc, items, misc);
     }
-    __syncthreads();
-    const DevCam &cam = cams[sm.cam];
-    TileRay tr;
-    if (!tile_ray(cam, t, part * ROWS, ptab, ttab, srange, S, tr, (int)threadIdx.x)) return;
-    tr.sr = checked_range(tr.sr, cap_pairs, kSiteBwdList, misc);
-    float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, T = 1.0f;
-    uint32_t last = 0;
-    if (tr.inside) {
-        const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
-        g0 = dL_drgb[3 * pix + 0];
-        g1 = dL_drgb[3 * pix + 1];
-        g2 = dL_drgb[3 * pix + 2];
-        T = Tfin[pix];
-        last = last_in[pix];
-    }
-    if (SPLAT) {  // the ray's screen angles
-        const float ts = atan2f(tr.dx, tr.dz), ps = atan2f(tr.dy, tr.dz);
-        tr.dx = ts;
-        tr.dy = ps;
-    }
-    BwdRay ray = bwd_ray(tr, cam, g0, g1, g2, T, last);
-    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
-    if ((threadIdx.x & 31) == 0) atomicMax(&sm.maxlast, warp_last);
-    __syncthreads();
-    const uint32_t block_last = sm.maxlast;
-    if (block_last == 0) return;
-    // the forward's warp of these rays: its rows 2w, 2w + 1 of the tile
-    const int fwarp = (part * ROWS * kTile + (int)threadIdx.x) >> 5;
-    uint2 walk = tile_walk[t];
-    if (!in_bounds(walk.x, (uint64_t)tr.sr.y + 1u, kSiteBwdList, misc)) walk = make_uint2(0u, 0u);
-    backward_walk<kThreads, BATCH, SPLAT>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr,
-                                   walk, warp_last, block_last,
-                                   hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, fwarp, ray, gacc,
-                                   items, misc);
 }
 
 }  // namespace
@@ -795,7 +880,8 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
         ws->params, rgb, T_final,
         ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->hit_entries,
         ws->tile_mask_on ? static_cast<const uint8_t *>(ws->d_tile_mask) : nullptr, ws->n_tiles,
-        (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs);
+        (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs, ws->d_ckpt, ws->d_ckpt_at, ws->d_ckpt_cnt,
+        ws->d_Cfin);
     return cudaGetLastError();
 }
 
@@ -811,13 +897,24 @@ cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cu
     if (ws->n_tiles == 0) return cudaSuccess;
     constexpr int R = GEER_BWD_ROWS, B = GEER_BWD_BATCH;
     launch_k(ws->params.alpha_model == GEER_ALPHA_EXACT ? k_render_bwd<R, B, false> : k_render_bwd<R, B, true>,
-        dim3((unsigned)(ws->n_tiles * (kTile / R))), dim3(R * kTile), 0, s,
+        dim3((unsigned)std::max(1, ws->bwd_grid)), dim3(R * kTile), 0, s,
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_bwd_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         ws->params, dL_drgb,
         ws->d_Tfin, ws->d_last, ws->d_hit, ws->hit_entries, ws->d_gacc, ws->n_tiles,
-        (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs);
+        (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs, ws->d_ckpt, ws->d_ckpt_at, ws->d_ckpt_cnt,
+        ws->d_Cfin);
     return cudaGetLastError();
+}
+
+int render_bwd_blocks_per_sm(int alpha_model) {
+    constexpr int R = GEER_BWD_ROWS, B = GEER_BWD_BATCH;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, alpha_model == GEER_ALPHA_EXACT ? k_render_bwd<R, B, false> : k_render_bwd<R, B, true>, R * kTile,
+            0) != cudaSuccess)
+        b = 1;
+    return b < 1 ? 1 : b;
 }
 
 }  // namespace geer

@@ -111,10 +111,11 @@ def test_backward_beyond_the_hit_record(geer, orc):
     forward records: 3000 broad, faint Gaussians (alpha just above alpha_min)
     stacked on the axis of a 16x16 pinhole, so that the centre rays composite
     ~2270 of them before T falls below T_min. The backward evaluates every entry
-    beyond the record. Tolerance: the reverse recovery T_i = T_(i+1) / (1 - a_i)
-    over N ~ 2300 steps, each with an approximate reciprocal (<= 2 ulp) and a
-    rounding, leaves a relative error up to N * 3 * 2^-24 ~ 4e-4 in the front
-    entries' transmittance: 2e-3 here (1e-3 elsewhere)."""
+    beyond the record. The walk is split into units at the forward's
+    checkpoints (every ~512 entries from entry 448), each starting from the
+    forward's own transmittance, so the reverse recovery T_i = T_(i+1) / (1 - a_i)
+    runs over at most ~512 steps (relative error <= 512 * 3 * 2^-24 ~ 1e-4):
+    the common 1e-3 tolerance holds."""
     n = 3000
     rng = np.random.default_rng(11)
     mean = np.stack([rng.normal(0, 0.02, n), rng.normal(0, 0.02, n), rng.uniform(2.0, 5.0, n)], 1)
@@ -138,7 +139,7 @@ def test_backward_beyond_the_hit_record(geer, orc):
         a, b = gpu[k].ravel(), ref[k].ravel()
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         mx = np.abs(a - b).max() / np.abs(b).max()
-        assert rel <= 2e-3 and mx <= 2e-3, (k, rel, mx)
+        assert rel <= 1e-3 and mx <= 1e-3, (k, rel, mx)
 
 
 def test_backward_workload3_subset_l1(geer, orc):
