@@ -318,6 +318,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_ev = L.take(sizeof(uint2) * c.pixels);
     size_t o_gacc = L.take(sizeof(GradAcc) * cg);
     size_t o_hit = L.take(sizeof(uint2) * c.tiles * c.hit_entries);
+    size_t o_idr = L.take(sizeof(uint32_t) * c.tiles * c.hit_entries);
     size_t o_mask = L.take(bwd ? sizeof(uint8_t) * c.tiles : 0);  // not in the forward-only layout
     size_t o_ck = L.take(bwd ? sizeof(float4) * c.tiles * kCkptMax * kTilePix : 0);
     size_t o_cka = L.take(bwd ? sizeof(uint2) * c.tiles * kCkptMax : 0);
@@ -357,6 +358,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_evals = reinterpret_cast<uint2 *>(base + o_ev);
         ws->d_gacc = reinterpret_cast<GradAcc *>(base + o_gacc);
         ws->d_hit = c.hit_entries > 0 ? reinterpret_cast<uint2 *>(base + o_hit) : nullptr;
+        ws->d_idrec = c.hit_entries > 0 ? reinterpret_cast<uint32_t *>(base + o_idr) : nullptr;
         ws->hit_entries = c.hit_entries;
         ws->d_tile_mask = bwd ? reinterpret_cast<uint8_t *>(base + o_mask) : nullptr;
         ws->d_ckpt = bwd ? reinterpret_cast<float4 *>(base + o_ck) : nullptr;

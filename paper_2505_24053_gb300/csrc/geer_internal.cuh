@@ -265,6 +265,7 @@ struct geer_workspace {
     geer::GradAcc *d_gacc;  // [cap_cams * cap_gauss]
     uint2 *d_hit;           // [cap_tiles][hit_entries] per tile-list entry, one byte per warp of the tile:
                             // nonzero when one of the warp's rays hit the entry in the forward (or null)
+    uint32_t *d_idrec;      // [cap_tiles][hit_entries] the item id of each of those tile-list entries
     int64_t hit_entries;    // list entries recorded per tile (0: none)
     uint8_t *d_tile_mask;   // [cap_tiles] tiles the forward renders (geer_set_tile_mask; null: no mask room)
     int tile_mask_on;       // the mask is in effect for the current camera set

@@ -323,7 +323,8 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                                              const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
                                              const Params &p, const float4 &col, const float4 &row, int cx, int cy,
                                              uint2 sr, float dx, float dy, float dz, uint2 *__restrict__ hit_rec,
-                                             int64_t hit_entries, uint64_t items, uint32_t *misc,
+                                             uint32_t *__restrict__ id_rec, int64_t hit_entries, uint64_t items,
+                                             uint32_t *misc,
                                              float4 *__restrict__ ckpt, uint2 *__restrict__ ckpt_at, FwdRay &f) {
     const int tid = threadIdx.x;
     uint8_t *const hit_b = reinterpret_cast<uint8_t *>(sm.hit) + (tid >> 5);  // this warp's byte of entry 0
@@ -366,9 +367,13 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
             sm.next_ck = n_list + (uint32_t)cnt + kCkptStride;
         }
         if (tid == 0 && sm.maxlast > n_list) sm.walkpos = sm.pos[sm.maxlast - 1u - n_list] + 1u;
-        // the batch's hit bytes, for the backward's skip of entries its warp never hit
+        // the batch's hit bytes, for the backward's skip of entries its warp never hit,
+        // and its item ids: the backward reads the tile's list from here without filtering
         if (hit_rec)
-            for (int r = tid; r < cnt && (int64_t)n_list + r < hit_entries; r += kThreads) hit_rec[n_list + r] = sm.hit[r];
+            for (int r = tid; r < cnt && (int64_t)n_list + r < hit_entries; r += kThreads) {
+                hit_rec[n_list + r] = sm.hit[r];
+                id_rec[n_list + r] = sm.id[r];
+            }
         shift_list<kThreads>(sm.id, sm.pos, cnt, s_cnt);
         n_list += (uint32_t)cnt;
     }
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                                             float *__restrict__ Tout, float *__restrict__ Tfin,
                                                             uint32_t *__restrict__ last_out,
                                                             uint2 *__restrict__ evals, uint2 *__restrict__ hit,
-                                                            int64_t hit_entries,
+                                                            uint32_t *__restrict__ idrec, int64_t hit_entries,
                                                             const uint8_t *__restrict__ tile_mask, int64_t ntiles,
                                                             uint64_t items, int64_t cap_pairs,
                                                             float4 *__restrict__ ckpt, uint2 *__restrict__ ckpt_at,
@@ -478,7 +483,8 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         tr.dy = ps;
     }
     forward_walk<kThreads, BATCH, SPLAT>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy,
-                                         tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries, items,
+                                         tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr,
+                                         hit ? idrec + (int64_t)t * hit_entries : nullptr, hit_entries, items,
                                          misc, ckpt ? ckpt + (size_t)t * kCkptMax * kThreads : nullptr,
                                          ckpt ? ckpt_at + (size_t)t * kCkptMax : nullptr, f);
     if (threadIdx.x == 0) {
@@ -628,7 +634,8 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
                                               const Params &p, const float4 &col, const float4 &row, int cx, int cy,
                                               uint32_t plo, uint32_t lo, uint2 walk, uint32_t warp_last,
                                               uint32_t block_last,
-                                              const uint2 *__restrict__ hit_rec, int64_t hit_entries, int fwarp,
+                                              const uint2 *__restrict__ hit_rec,
+                                              const uint32_t *__restrict__ id_rec, int64_t hit_entries, int fwarp,
                                               BwdRay &ray, GradAcc *__restrict__ gacc, uint64_t items,
                                               uint32_t *misc) {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -637,17 +644,32 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
     uint32_t pos = walk.x, top = walk.y;
     int s_cnt = 0;
     while (top > lo) {
-        fill_list_rev<kThreads, BATCH>(svals, sranges, col, row, cx, cy, pos, plo, sm.id, s_cnt, sm.wcnt);
-        const int cnt = min(s_cnt, BATCH);
-        if (cnt == 0) break;
+        // within the forward's record the list is read directly, beyond it filtered again
+        const bool direct = id_rec && (int64_t)top <= hit_entries;
+        int cnt;
+        if (direct) {
+            cnt = (int)min((uint32_t)BATCH, top - lo);
+        } else {
+            fill_list_rev<kThreads, BATCH>(svals, sranges, col, row, cx, cy, pos, plo, sm.id, s_cnt, sm.wcnt);
+            cnt = min(s_cnt, BATCH);
+            if (cnt == 0) break;
+        }
         // entries at or beyond the block's last contributor are not walked
         const int skip = top > block_last ? (int)min((uint32_t)cnt, top - block_last) : 0;
         for (int r = skip + tid; r < cnt; r += kThreads) {
-            stage_record(sm.rec + r * 4, rec, sm.id[r], items, kSiteBwdItem, misc);
-            // beyond the recorded entries every warp evaluates
             const uint32_t j = top - 1u - (uint32_t)r;
-            // transposed to warp-major order: warp w's flags of the batch are contiguous
+            uint32_t id;
+            if (direct) {
+                id = id_rec[j];
+                sm.id[r] = id;
+            } else {
+                id = sm.id[r];
+            }
+            // beyond the recorded entries every warp evaluates
             const uint2 h = hit_rec && (int64_t)j < hit_entries ? hit_rec[j] : make_uint2(~0u, ~0u);
+            // an entry no warp hit is never read: its record is not staged
+            if (h.x | h.y) stage_record(sm.rec + r * 4, rec, id, items, kSiteBwdItem, misc);
+            // transposed to warp-major order: warp w's flags of the batch are contiguous
             uint8_t *hw = reinterpret_cast<uint8_t *>(sm.hit);
 #pragma unroll
             for (int w = 0; w < kTileWarps; ++w)
@@ -726,7 +748,7 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
                 atomicAdd(dst + 3, make_float4(v[12], v[13], v[14], v[15]));
             }
         }
-        shift_list<kThreads>(sm.id, nullptr, cnt, s_cnt);
+        if (!direct) shift_list<kThreads>(sm.id, nullptr, cnt, s_cnt);
         top -= (uint32_t)cnt;
     }
 }
@@ -774,6 +796,7 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
                                                                            const float *__restrict__ Tfin,
                                                                            const uint32_t *__restrict__ last_in,
                                                                            const uint2 *__restrict__ hit,
+                                                                           const uint32_t *__restrict__ idrec,
                                                                            int64_t hit_entries,
                                                                            GradAcc *__restrict__ gacc, int64_t ntiles,
                                                                            uint64_t items, int64_t cap_pairs,
@@ -863,7 +886,8 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
         if (block_last <= lo) continue;
         backward_walk<kThreads, BATCH, SPLAT>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, plo, lo,
                                               make_uint2(phi, hi), warp_last, block_last,
-                                              hit ? hit + (int64_t)t * hit_entries : nullptr, hit_entries,
+                                              hit ? hit + (int64_t)t * hit_entries : nullptr,
+                                              hit ? idrec + (int64_t)t * hit_entries : nullptr, hit_entries,
                                               (int)threadIdx.x >> 5, ray, gacc, items, misc);
     }
 }
@@ -878,7 +902,7 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_tile_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         ws->params, rgb, T_final,
-        ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->hit_entries,
+        ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->d_idrec, ws->hit_entries,
         ws->tile_mask_on ? static_cast<const uint8_t *>(ws->d_tile_mask) : nullptr, ws->n_tiles,
         (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs, ws->d_ckpt, ws->d_ckpt_at, ws->d_ckpt_cnt,
         ws->d_Cfin);
@@ -901,7 +925,7 @@ cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cu
         ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_bwd_order,
         ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc,
         ws->params, dL_drgb,
-        ws->d_Tfin, ws->d_last, ws->d_hit, ws->hit_entries, ws->d_gacc, ws->n_tiles,
+        ws->d_Tfin, ws->d_last, ws->d_hit, ws->d_idrec, ws->hit_entries, ws->d_gacc, ws->n_tiles,
         (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs, ws->d_ckpt, ws->d_ckpt_at, ws->d_ckpt_cnt,
         ws->d_Cfin);
     return cudaGetLastError();
