@@ -44,12 +44,13 @@ enum Misc : int {
     kMiscTileLo = 6,      // (tile, item) associations P mod 2^32
     kMiscTileHi = 7,      // P / 2^32
     kMiscSortDone = 8,    // radix histogram blocks finished in the current pass
-    kMiscSortSame = 9,    // the current pass's digit is the same for every key (an identity pass)
+    kMiscSortSame = 9,    // the current pass's digit is the same for every key (an identity pass, skipped)
     kMiscCheckSite = 10,  // GEER_CHECKED build: site of the first bounds violation (0: none)
     kMiscCheckLo = 11,    // its index mod 2^32
     kMiscCheckHi = 12,    // its index / 2^32
     kMiscUnits = 13,      // backward units of the last geer_render_bwd_tiles (tile walks split at checkpoints)
     kMiscUnitNext = 14,   // the next backward unit to take (persistent blocks)
+    kMiscSortCur = 15,    // depth sort: the buffer the current pass reads (set by its histogram kernel)
     kMiscCount = 32
 };
 
@@ -275,7 +276,6 @@ struct geer_workspace {
     int32_t sh_degree;
     int stage;               // 0 none, 1 preprocessed, 2 sorted, 3 rendered, 4 render-stage gradients
     int sorted_buf;          // which ping-pong buffer holds the sorted super-tile pairs
-    int depth_buf;           // which ping-pong buffer holds the depth-sorted items
     int sort_grid;           // grid of the radix kernels (grid-stride over sort tiles)
     int num_sms;
 
@@ -334,5 +334,12 @@ int sort_blocks_per_sm();
 int render_bwd_blocks_per_sm(int alpha_model);
 
 inline int64_t prep_blocks(int64_t n) { return (n + kPrepThreads - 1) / kPrepThreads; }
+
+// The buffer (0 or 1) holding the depth-sorted items after the depth sort: the
+// passes whose digit was the same for every key are skipped on the device, so
+// the ping-pong parity is known there only (misc as left by the last pass).
+__device__ __forceinline__ int depth_sorted_buf(const uint32_t *misc) {
+    return misc[kMiscSortSame] ? (int)misc[kMiscSortCur] : 1 - (int)misc[kMiscSortCur];
+}
 
 }  // namespace geer

@@ -728,6 +728,9 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *__restrict__ blo
         const unsigned long long total = excl;
         if (mode == 0) {
             misc[kMiscLive] = (uint32_t)total;
+            // the depth sort's first pass reads buffer 0 (see depth_sorted_buf)
+            misc[kMiscSortCur] = 1u;
+            misc[kMiscSortSame] = 0u;
         } else if (mode == 2) {
             misc[kMiscTileLo] = (uint32_t)total;
             misc[kMiscTileHi] = (uint32_t)(total >> 32);
@@ -783,7 +786,8 @@ __device__ __forceinline__ uint32_t super_count(const DevCam &cam, int S, const 
 // offsets) and their tile pairs (the total, for the capacity check).
 __global__ void __launch_bounds__(kPrepThreads) k_gather_counts(const DevCam *__restrict__ cams,
                                                                 const float4 *__restrict__ ttab, int64_t n, int S,
-                                                                const uint32_t *__restrict__ sorted_id,
+                                                                const uint32_t *__restrict__ sorted0,
+                                                                const uint32_t *__restrict__ sorted1,
                                                                 const uint32_t *__restrict__ count,
                                                                 const uint4 *__restrict__ ranges,
                                                                 const uint32_t *__restrict__ misc,
@@ -792,6 +796,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_gather_counts(const DevCam *__
     grid_dep_sync();
     __shared__ uint32_t red[kPrepThreads / 32];
     const uint32_t L = misc[kMiscLive];
+    const uint32_t *__restrict__ sorted_id = depth_sorted_buf(misc) ? sorted1 : sorted0;
     const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
     uint32_t c = 0, sc = 0;
     if (i < L) {
@@ -816,8 +821,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_gather_counts(const DevCam *__
 // warp together (lane j writes output j: coalesced); others loop per thread.
 __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
     const DevCam *__restrict__ cams, const float4 *__restrict__ ttab, int64_t n, int S,
-    const uint32_t *__restrict__ sorted_id, const uint4 *__restrict__ ranges, const uint32_t *__restrict__ count,
-    uint32_t *__restrict__ misc, const uint32_t *__restrict__ blocksum, uint32_t *__restrict__ okeys,
+    const uint32_t *__restrict__ sorted0, const uint32_t *__restrict__ sorted1, const uint4 *__restrict__ ranges,
+    const uint32_t *__restrict__ count, uint32_t *__restrict__ misc, const uint32_t *__restrict__ blocksum,
+    uint32_t *__restrict__ okeys,
     uint32_t *__restrict__ ovals, uint32_t *__restrict__ scount, int nst, int64_t cap) {
     grid_dep_sync();
     __shared__ uint32_t wsum[kPrepThreads / 32];
@@ -826,6 +832,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
     if (smem)
         for (int k = threadIdx.x; k < nst; k += kPrepThreads) sh[k] = 0u;
     const uint32_t L = misc[kMiscLive];
+    const uint32_t *__restrict__ sorted_id = depth_sorted_buf(misc) ? sorted1 : sorted0;
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
     uint32_t item = 0, cnt = 0;
@@ -1063,29 +1070,39 @@ __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ ti
     __syncthreads();
     const int chunk = (ntiles + 1023) / 1024;
     const int b = t * chunk, e = min(ntiles, b + chunk);
+    constexpr int G = 8;  // tiles whose walk records are loaded together
     for (int pass = 0; pass < 2; ++pass) {
         uint32_t mine = 0;
-        for (int c = 0; c < chunk; ++c) {  // the same trip count in every lane (warp-wide atomics)
-            const int i = b + c;
-            uint32_t W = 0, m = 0;
-            if (i < e) {
-                W = tile_walk[i].y;
-                const uint32_t n = ckpt_cnt ? min(ckpt_cnt[i], (uint32_t)kCkptMax) : 0u;
-                while (m < n && ckpt_at[(size_t)i * kCkptMax + m].x < W) ++m;
+        for (int c0 = 0; c0 < chunk; c0 += G) {  // the same trip counts in every lane (warp-wide atomics)
+            uint32_t W[G], n[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const int i = b + c0 + u;
+                const bool in = c0 + u < chunk && i < e;
+                W[u] = in ? tile_walk[i].y : 0u;
+                n[u] = in && ckpt_cnt ? ckpt_cnt[i] : 0u;
             }
-            const uint32_t units = W > 0 ? m + 1 : 0u;
-            for (uint32_t k = 0; __any_sync(0xffffffffu, k < units); ++k) {
-                const bool ok = k < units;
-                uint32_t len = 0;
-                if (ok) {
-                    const uint32_t lo = k == 0 ? 0u : ckpt_at[(size_t)i * kCkptMax + k - 1].x;
-                    const uint32_t hi = k < m ? ckpt_at[(size_t)i * kCkptMax + k].x : W;
-                    len = hi - lo;
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const int i = b + c0 + u;
+                // the checkpoints below the walk's end split it (rare: walks beyond kCkptFirst)
+                uint32_t m = 0;
+                const uint32_t nk = W[u] > kCkptFirst ? min(n[u], (uint32_t)kCkptMax) : 0u;
+                while (m < nk && ckpt_at[(size_t)i * kCkptMax + m].x < W[u]) ++m;
+                const uint32_t units = W[u] > 0 ? m + 1 : 0u;
+                for (uint32_t k = 0; __any_sync(0xffffffffu, k < units); ++k) {
+                    const bool ok = k < units;
+                    uint32_t len = 0;
+                    if (ok) {
+                        const uint32_t lo = k == 0 ? 0u : ckpt_at[(size_t)i * kCkptMax + k - 1].x;
+                        const uint32_t hi = k < m ? ckpt_at[(size_t)i * kCkptMax + k].x : W[u];
+                        len = hi - lo;
+                    }
+                    const uint32_t slot = bucket_add(hist, ok, order_bucket(len));
+                    if (pass == 1 && ok) order[slot] = ((uint32_t)i << 4) | k;
                 }
-                const uint32_t slot = bucket_add(hist, ok, order_bucket(len));
-                if (pass == 1 && ok) order[slot] = ((uint32_t)i << 4) | k;
+                mine += units;
             }
-            mine += units;
         }
         if (pass == 0) {
             atomicAdd(&s_total, mine);
@@ -1144,7 +1161,7 @@ cudaError_t launch_count_pairs(const geer_workspace *ws, cudaStream_t s) {
     const int64_t m = prep_blocks((int64_t)ws->n_cams * ws->n_gauss);
     if (m > 0) {
         launch_k(k_gather_counts, dim3((unsigned)m), dim3(kPrepThreads), 0, s, ws->d_cams, ws->d_tile_tab,
-                 ws->n_gauss, ws->super_size, ws->d_iid[ws->depth_buf], ws->d_count, ws->d_ranges, ws->d_misc,
+                 ws->n_gauss, ws->super_size, ws->d_iid[0], ws->d_iid[1], ws->d_count, ws->d_ranges, ws->d_misc,
                  ws->d_blocksum2, ws->d_blocksum3);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1161,7 +1178,7 @@ cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
     if (m > 0) {
         const size_t smem = ws->n_stiles <= kSmemTiles ? sizeof(uint32_t) * ws->n_stiles : 0;
         launch_k(k_duplicate, dim3((unsigned)m), dim3(kPrepThreads), smem, s, ws->d_cams, ws->d_tile_tab,
-                 ws->n_gauss, ws->super_size, ws->d_iid[ws->depth_buf], ws->d_ranges, ws->d_count, ws->d_misc,
+                 ws->n_gauss, ws->super_size, ws->d_iid[0], ws->d_iid[1], ws->d_ranges, ws->d_count, ws->d_misc,
                  ws->d_blocksum2, ws->d_keys[0], ws->d_vals[0], scount, (int)ws->n_stiles, ws->cap_pairs);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -33,8 +33,12 @@ __device__ __forceinline__ uint32_t key_count(const uint32_t *misc, int count_sl
     return misc[count_slot];
 }
 
+// dev_buf: the pass's input buffer is chosen on the device (kin0 or kin1): the
+// one the previous pass wrote, or read, if that pass was skipped (its digit the
+// same for every key). Otherwise kin0 is the input.
 template <int ITEMS>
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ kin0,
+                                                             const uint32_t *__restrict__ kin1, int dev_buf,
                                                              uint32_t *__restrict__ misc, int count_slot,
                                                              int check_capacity, int shift,
                                                              uint32_t *__restrict__ tile_hist,
@@ -51,6 +55,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
     const uint32_t tile = blockIdx.x;
     const uint32_t ntiles = (n + TILE - 1) / TILE;
     if (tile >= ntiles) return;
+    // read before the last block of this pass updates them (it finishes after every block started)
+    const int in = dev_buf ? depth_sorted_buf(misc) : 0;
+    const uint32_t *__restrict__ kin = in ? kin1 : kin0;
     for (int i = tid; i < W * kRadix; i += kSortThreads) (&s_h[0][0])[i] = 0u;
     const uint64_t base = (uint64_t)tile * TILE + (uint64_t)warp * 32 * ITEMS + lane;
     uint32_t key[ITEMS];
@@ -106,10 +113,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
 #pragma unroll
     for (int w = 0; w < W; ++w) pre += w < warp ? s_wsum[w] : 0u;
     digit_base[d] = pre + v - run;
-    // one digit holds every key: the pass keeps the order and the scatter only copies
+    // one digit holds every key: the pass keeps the order (its scatter copies, or
+    // with dev_buf is skipped, the data staying in its input buffer)
     const bool all = __syncthreads_or(run == n);
     if (tid == 0) {
         misc[kMiscSortSame] = all ? 1u : 0u;
+        if (dev_buf) misc[kMiscSortCur] = (uint32_t)in;
         misc[kMiscSortDone] = 0u;
     }
 }
@@ -118,11 +127,19 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
 // of the super-tile sort gathers the association ranges into list order).
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
-    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, const uint32_t *__restrict__ misc, int count_slot, int check_capacity, int shift,
-    const uint32_t *__restrict__ tile_hist, const uint32_t *__restrict__ group_excl,
+    const uint32_t *__restrict__ kin_, const uint32_t *__restrict__ vin_, uint32_t *__restrict__ kout_,
+    uint32_t *__restrict__ vout_, int dev_buf, const uint32_t *__restrict__ misc, int count_slot,
+    int check_capacity, int shift, const uint32_t *__restrict__ tile_hist, const uint32_t *__restrict__ group_excl,
     const uint32_t *__restrict__ digit_base, const uint4 *__restrict__ ranges, uint4 *__restrict__ rout) {
     grid_dep_sync();
+    // dev_buf: (kin_, vin_) is buffer 0 and (kout_, vout_) buffer 1; the input is
+    // the one the histogram kernel recorded, and an identity pass is skipped
+    if (dev_buf && misc[kMiscSortSame]) return;
+    const bool swap = dev_buf && misc[kMiscSortCur];
+    const uint32_t *__restrict__ kin = swap ? kout_ : kin_;
+    const uint32_t *__restrict__ vin = swap ? vout_ : vin_;
+    uint32_t *__restrict__ kout = swap ? const_cast<uint32_t *>(kin_) : kout_;
+    uint32_t *__restrict__ vout = swap ? const_cast<uint32_t *>(vin_) : vout_;
     constexpr int W = kSortThreads / 32, TILE = kSortThreads * ITEMS, GROUP = kGroupTiles;
     __shared__ uint32_t s_whist[W][kRadix];
     __shared__ uint32_t s_match[W][kRadix];  // lane masks per digit, zero between ranking steps
@@ -257,39 +274,43 @@ int sort_blocks_per_sm() {
 
 template <int ITEMS>
 static cudaError_t radix_pass_t(geer_workspace *ws, uint32_t *const kbuf[2], uint32_t *const vbuf[2], int cur,
-                                int slot, int check, int shift, int64_t cap_keys, uint4 *rout, cudaStream_t s) {
+                                int dev_buf, int slot, int check, int shift, int64_t cap_keys, uint4 *rout,
+                                cudaStream_t s) {
     constexpr int TILE = kSortThreads * ITEMS;
     const unsigned tiles = (unsigned)std::max<int64_t>(1, (cap_keys + TILE - 1) / TILE);
-    launch_k(k_radix_hist<ITEMS>, dim3(tiles), dim3(kSortThreads), 0, s, kbuf[cur], ws->d_misc, slot, check, shift,
-             ws->d_tile_hist, ws->d_group_sum, ws->d_group_excl, ws->d_digit_base);
+    launch_k(k_radix_hist<ITEMS>, dim3(tiles), dim3(kSortThreads), 0, s, kbuf[cur], kbuf[cur ^ 1], dev_buf,
+             ws->d_misc, slot, check, shift, ws->d_tile_hist, ws->d_group_sum, ws->d_group_excl, ws->d_digit_base);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     launch_k(k_radix_scatter<ITEMS>, dim3(tiles), dim3(kSortThreads), 0, s, kbuf[cur], vbuf[cur], kbuf[cur ^ 1],
-             vbuf[cur ^ 1], ws->d_misc, slot, check, shift, ws->d_tile_hist, ws->d_group_excl, ws->d_digit_base,
-             ws->d_ranges, rout);
+             vbuf[cur ^ 1], dev_buf, ws->d_misc, slot, check, shift, ws->d_tile_hist, ws->d_group_excl,
+             ws->d_digit_base, ws->d_ranges, rout);
     return cudaGetLastError();
 }
 
-// One stable pass over digit `pass` of the keys in buffer `cur` (count in misc[slot]).
+// One stable pass over digit `pass` of the keys in buffer `cur` (count in
+// misc[slot]); with dev_buf the buffers are chosen on the device and a pass
+// whose digit is the same for every key is skipped.
 // (Tiles of 1024 keys for small sorts were measured slower: 0.106 against 0.079 ms
 // for the four passes over 1M depth keys.)
 static cudaError_t radix_pass(geer_workspace *ws, uint32_t *const kbuf[2], uint32_t *const vbuf[2], int cur, int slot,
-                              int check, int pass, int64_t cap_keys, cudaStream_t s, uint4 *rout = nullptr) {
-    return radix_pass_t<kSortItems>(ws, kbuf, vbuf, cur, slot, check, kRadixBits * pass, cap_keys, rout, s);
+                              int check, int pass, int64_t cap_keys, cudaStream_t s, uint4 *rout = nullptr,
+                              int dev_buf = 0) {
+    return radix_pass_t<kSortItems>(ws, kbuf, vbuf, cur, dev_buf, slot, check, kRadixBits * pass, cap_keys, rout, s);
 }
 
-// Stable sort of the live items by depth key (4 digits of the FP32 bits).
+// Stable sort of the live items by depth key (4 digits of the FP32 bits). The
+// passes choose their buffers on the device (see depth_sorted_buf): a digit
+// that is the same for every key (the exponent's high bits when the depths span
+// less than a factor of two) costs its histogram only.
 cudaError_t launch_depth_sort(geer_workspace *ws, cudaStream_t s) {
-    int cur = 0;
     const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
     if (items > 0) {
         for (int p = 0; p < 4; ++p) {
-            cudaError_t e = radix_pass(ws, ws->d_ikey, ws->d_iid, cur, kMiscLive, 0, p, items, s);
+            cudaError_t e = radix_pass(ws, ws->d_ikey, ws->d_iid, 0, kMiscLive, 0, p, items, s, nullptr, 1);
             if (e != cudaSuccess) return e;
-            cur ^= 1;
         }
     }
-    ws->depth_buf = cur;
     return cudaSuccess;
 }
 
