@@ -32,9 +32,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpix/s fwd and fwd+bwd at 1M Gaussians, 180° fisheye; serving p50/p99 ms"
 WORKLOAD = "1M Gaussians (cube 4 m, 3-7 m ahead, SH3), Kannala-Brandt 1280x960 190deg, BEAP 16x16 tiles"
-FLOPS_TEST = 43    # per ray-Gaussian evaluation: W d, cross product, two norms, divide, exp arg, exp, t* dot
-FLOPS_BLEND = 10   # per applied contributor: clamp, transmittance update, weight, 3 colour FMAs
-FLOPS_BWD = 96  # per backward contributor: alpha, transmittance and colour terms, dL/dkappa, the d_u and o_u gradients, 16 accumulations
+# Algorithmic work of the render kernels, the scope table's counts: 66 flop per
+# ray-Gaussian evaluation in the forward (W d, the cross product, two norms, the
+# divide, the exponent and the blend, FMAs counted as two), and twice that per
+# list entry the backward walks back (re-evaluation, then the gradient terms).
+FLOPS_FWD_EVAL = 66
+FLOPS_BWD_EVAL = 2 * FLOPS_FWD_EVAL
                    # d_u / o_u / W (80) and its share of the warp reduction (16)
 
 
@@ -369,44 +372,53 @@ def run(args):
         else:
             ws.render_bwd(gk, dL, grads, accumulate=False)
 
-    def train_step(ev):
+    # ev[0] and ev[3] bracket a step; with detail, ev[1] and ev[2] also mark the
+    # end of the preprocess and of the binning (a breakdown run, not the timed one:
+    # an event between two kernels keeps the second from launching while the first
+    # runs, which the binning's short kernels would pay for)
+    def train_step(ev, detail=False):
         ev[0].record(stream)
         ws.preprocess(g)
-        ev[1].record(stream)
+        if detail:
+            ev[1].record(stream)
         ws.bin_sort(sync=False)
-        ev[2].record(stream)
+        if detail:
+            ev[2].record(stream)
         # training step: forward, L1 loss gradient, backward (the step's gradients written)
         ws.render_fwd(rgb)
         geer.l1_loss_grad(rgb, target_step, dL)
         backward(g)
         ev[3].record(stream)
 
-    def fwd_step(ev):
+    def fwd_step(ev, detail=False):
         ev[0].record(stream)
         ws.preprocess(g)
-        ev[1].record(stream)
+        if detail:
+            ev[1].record(stream)
         ws.bin_sort(sync=False)
-        ev[2].record(stream)
+        if detail:
+            ev[2].record(stream)
         ws.render_fwd(rgb)
         ev[3].record(stream)
 
-    def timed(step, clk_sample):
+    def timed(step, clk_sample, steps=None, detail=False):
+        steps = args.steps if steps is None else steps
         for _ in range(args.warmup):
             flush.zero_()
-            step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+            step([torch.cuda.Event(enable_timing=True) for _ in range(4)], detail)
         torch.cuda.synchronize()
         st, _ = ws.device_status()
         if st != geer.OK:
             raise RuntimeError(f"device status after warm-up: {geer.status_string(st)}")
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) if clk_sample else contextlib.nullcontext() as clk:
             t0 = time.perf_counter()
-            for k in range(args.steps):
+            for k in range(steps):
                 flush.zero_()  # between timed steps, outside the step's events
-                step(evs[k])
+                step(evs[k], detail)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
         if world > 1:
@@ -416,26 +428,36 @@ def run(args):
             raise RuntimeError(f"device status after timed steps: {geer.status_string(st)}")
         return evs, wall, clk
 
-    ws.enable_timing(True)
+    # the timed steps: the library's stage events around the dominant kernel's stage
+    # only (the backward render; the forward render without a backward)
+    dom_stage = "render_bwd" if have_bwd else "render_fwd"
+    ws.enable_timing(True, stages=(dom_stage,))
     train_evs = None
     if have_bwd:
         train_evs, t_wall, clk = timed(train_step, True)
+        dom_stage_ms = {dom_stage: ws.stage_times()[dom_stage][0]}  # the last 64 timed steps
     fwd_evs, fwd_wall, fclk = timed(fwd_step, not have_bwd)
     if not have_bwd:
         t_wall, clk = fwd_wall, fclk
+        dom_stage_ms = {dom_stage: ws.stage_times()[dom_stage][0]}
     pairs, super_pairs = ws.pair_counts()
     tile_stats = _tile_stats(ws, cams)
-    stage_ms = {k: v[0] for k, v in ws.stage_times().items()}  # mean of the last 64 recorded occurrences
+    # the breakdown: the same step with every stage's events, in a run of its own
+    ws.enable_timing(False)
+    ws.enable_timing(True)
+    bd_evs, _, _ = timed(train_step if have_bwd else fwd_step, False, steps=min(args.steps, 64), detail=True)
+    stage_ms = {k: v[0] for k, v in ws.stage_times().items()}
+    stage_ms.update(dom_stage_ms)
     ws.enable_timing(False)
     main_evs = train_evs if have_bwd else fwd_evs
     step_ms = [e[0].elapsed_time(e[3]) for e in main_evs]
-    prep_ms = [e[0].elapsed_time(e[1]) for e in main_evs]
-    sort_ms = [e[1].elapsed_time(e[2]) for e in main_evs]
-    rend_ms = [e[2].elapsed_time(e[3]) for e in main_evs]
+    prep_ms = [e[0].elapsed_time(e[1]) for e in bd_evs]
+    sort_ms = [e[1].elapsed_time(e[2]) for e in bd_evs]
+    rend_ms = [e[2].elapsed_time(e[3]) for e in bd_evs]
     value, total_ms = aggregate(float(sum(step_ms)), pixels, args.steps, world, dist, dev, shared=split)
     fwd_ms = [e[0].elapsed_time(e[3]) for e in fwd_evs]
     fwd_value = pixels / (statistics.mean(fwd_ms) / 1e3) / 1e6
-    fwd_render_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in fwd_evs)
+    fwd_render_ms = stage_ms["render_fwd"]
 
     # end to end through the C ABI with host buffers: every step copies its
     # Gaussians from pinned host memory and reads its image back into pinned host
@@ -565,8 +587,8 @@ def run(args):
         "duplicate": ("hbm", live * (4 + 4 + 16) + int(super_pairs) * 8),
         # passes x (read key 4 B + key/value 8 B, write 8 B), and 16 B of ranges gathered + written
         "tile_sort": ("hbm", sort_passes * 20 * int(super_pairs) + 32 * int(super_pairs)),
-        "render_fwd": ("alu", FLOPS_TEST * evals + FLOPS_BLEND * applied),
-        "render_bwd": ("alu", FLOPS_TEST * walked + FLOPS_BWD * applied),
+        "render_fwd": ("alu", FLOPS_FWD_EVAL * evals),
+        "render_bwd": ("alu", FLOPS_BWD_EVAL * walked),
         # the step writes its gradients: parameters and accumulators read, gradients written
         "preprocess_bwd": ("hbm", scene.n * g_bytes * 2 + n_items * 64),
     }

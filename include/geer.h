@@ -370,6 +370,11 @@ geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t
  * their number into counts (may be NULL). Do not enable it while capturing a
  * CUDA graph. */
 geer_status geer_enable_timing(geer_workspace *ws, int32_t enable);
+/* As geer_enable_timing, recording events for the stages in `mask` only (bit s
+ * = stage s, 0: timing off). An event between two kernels keeps the second
+ * from launching while the first runs (programmatic dependent launch), so a
+ * measurement of whole steps times the long stages only. */
+geer_status geer_enable_stage_timing(geer_workspace *ws, uint32_t mask);
 geer_status geer_stage_times(geer_workspace *ws, float *ms, int32_t n, int32_t *counts, void *stream);
 const char *geer_stage_name(int32_t stage);
 

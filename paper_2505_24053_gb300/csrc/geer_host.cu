@@ -377,7 +377,7 @@ struct StageTimer {
     int stage, slot;
     cudaStream_t s;
     StageTimer(geer_workspace *w, int st, cudaStream_t str) : ws(w), stage(st), slot(-1), s(str) {
-        if (ws->timing) {
+        if (ws->timing && ((ws->timing_mask >> stage) & 1u)) {
             slot = ws->ev_count[stage] % kTimingRing;
             cudaEventRecord(ws->ev[stage][slot][0], s);
         }
@@ -1120,8 +1120,17 @@ const char *geer_stage_name(int32_t stage) {
     return (stage >= 0 && stage < kStageCount) ? kStageNames[stage] : "unknown";
 }
 
+geer_status geer_enable_stage_timing(geer_workspace *ws, uint32_t mask) {
+    if (!ws) return GEER_ERR_ARG;
+    mask &= (1u << kStageCount) - 1u;
+    geer_status st = geer_enable_timing(ws, mask ? 1 : 0);
+    if (st == GEER_OK) ws->timing_mask = mask;
+    return st;
+}
+
 geer_status geer_enable_timing(geer_workspace *ws, int32_t enable) {
     if (!ws) return GEER_ERR_ARG;
+    ws->timing_mask = (1u << kStageCount) - 1u;
     if (enable && !ws->timing) {
         for (int a = 0; a < kStageCount; ++a) {
             ws->ev_count[a] = 0;

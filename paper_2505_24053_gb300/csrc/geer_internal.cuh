@@ -285,6 +285,7 @@ struct geer_workspace {
 
     // optional stage timing: a ring of (begin, end) events per stage
     int timing;
+    uint32_t timing_mask;    // the stages that record events (bit s = stage s)
     cudaEvent_t ev[geer::kStageCount][geer::kTimingRing][2];
     int ev_count[geer::kStageCount];
 };

@@ -50,7 +50,8 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_pair_counts", "geer_debug_render_state", "geer_densify_accumulate", "geer_densify_scratch_bytes",
            "geer_densify_plan", "geer_densify_apply", "geer_opacity_reset", "geer_render_bwd_tiles",
            "geer_grad_accumulators", "geer_preprocess_bwd", "geer_tile_owners", "geer_set_tile_mask",
-           "geer_tile_counts", "geer_checked_build", "geer_bounds_violation", "geer_debug_set_render_order"]
+           "geer_tile_counts", "geer_checked_build", "geer_bounds_violation", "geer_debug_set_render_order",
+           "geer_enable_stage_timing"]
 
 _lib = None
 
@@ -120,6 +121,7 @@ def lib(build_if_missing: bool = True, checked: bool = False):
         "geer_tile_counts": [P, P, P],
         "geer_bounds_violation": [P, P, P, P],
         "geer_debug_set_render_order": [P, P, I64, P],
+        "geer_enable_stage_timing": [P, C.c_uint32],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -421,8 +423,14 @@ class Workspace:
                "geer_debug_render_state")
         return ev, last, walk
 
-    def enable_timing(self, on: bool = True):
-        _check(self._L.geer_enable_timing(self._handle, 1 if on else 0), "geer_enable_timing")
+    def enable_timing(self, on: bool = True, stages=None):
+        """Stage timing on (every stage, or the named stages only) or off."""
+        if stages is None or not on:
+            _check(self._L.geer_enable_timing(self._handle, 1 if on else 0), "geer_enable_timing")
+            return
+        names = [self._L.geer_stage_name(i).decode() for i in range(9)]
+        mask = sum(1 << names.index(n) for n in stages)
+        _check(self._L.geer_enable_stage_timing(self._handle, mask), "geer_enable_stage_timing")
 
     def stage_times(self, stream=None) -> dict:
         """Mean ms of the recorded occurrences of each stage (timing must be enabled)."""
