@@ -356,7 +356,7 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
         // barrier: the walk's registers are at their limit)
         const uint32_t nck = sm.nck;
         const bool ck = n_list + (uint32_t)cnt >= sm.next_ck && nck < (uint32_t)kCkptMax;
-        if (ck) ckpt[(size_t)nck * kThreads + tid] = make_float4(f.T, f.cr, f.cg, f.cb);
+        if (ck) ckpt[(size_t)nck * kTilePix + tid] = make_float4(f.T, f.cr, f.cg, f.cb);
         // the tile's last contributor so far and where it lies in the super-tile list
         const uint32_t wl = __reduce_max_sync(0xffffffffu, f.last);
         if ((tid & 31) == 0) atomicMax(&sm.maxlast, wl);
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
     forward_walk<kThreads, BATCH, SPLAT>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy,
                                          tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr,
                                          hit ? idrec + (int64_t)t * hit_entries : nullptr, hit_entries, items,
-                                         misc, ckpt ? ckpt + (size_t)t * kCkptMax * kThreads : nullptr,
+                                         misc, ckpt ? ckpt + (size_t)t * kCkptMax * kTilePix : nullptr,
                                          ckpt ? ckpt_at + (size_t)t * kCkptMax : nullptr, f);
     if (threadIdx.x == 0) {
         tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
@@ -805,13 +805,13 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
                                                                            const uint32_t *__restrict__ ckpt_cnt,
                                                                            const float4 *__restrict__ Cfin) {
     grid_dep_sync();
-    constexpr int kThreads = ROWS * kTile;
-    static_assert(ROWS == kTile, "one block per backward unit covers the tile's rays");
+    constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
+    static_assert(kParts * ROWS == kTile, "a unit's rays are split into kParts blocks of ROWS rows");
     __shared__ WalkSmem<kThreads, BATCH> sm;
     __shared__ float s_acc[BATCH][17];
     __shared__ uint32_t s_unit;
     if (misc[kMiscStatus] & kStatusCapacity) return;
-    const uint32_t n_units = misc[kMiscUnits];
+    const uint32_t n_work = misc[kMiscUnits] * (uint32_t)kParts;  // (unit, row part) pairs
     while (true) {
         __syncthreads();  // the previous unit's shared state has been read
         if (threadIdx.x == 0) {
@@ -819,9 +819,11 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
             sm.maxlast = 0u;
         }
         __syncthreads();
-        const uint32_t u = s_unit;
-        if (u >= n_units) break;
-        const uint32_t code = units[u];
+        const uint32_t w = s_unit;
+        if (w >= n_work) break;
+        const uint32_t code = units[w / kParts];
+        const int part = (int)(w % kParts);
+        const int tray = part * kThreads + (int)threadIdx.x;  // the ray's index in the tile
         const uint32_t t_id = code >> 4, k = code & 15u;
         if (!in_bounds(t_id, (uint64_t)ntiles, kSiteBwdTile, misc)) continue;  // block-uniform
         const int t = (int)t_id;
@@ -829,7 +831,7 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
         __syncthreads();
         const DevCam &cam = cams[sm.cam];
         TileRay tr;
-        if (!tile_ray(cam, t, 0, ptab, ttab, srange, S, tr, (int)threadIdx.x)) continue;
+        if (!tile_ray(cam, t, part * ROWS, ptab, ttab, srange, S, tr, (int)threadIdx.x)) continue;
         tr.sr = checked_range(tr.sr, cap_pairs, kSiteBwdList, misc);
         uint2 walk = tile_walk[t];
         if (!in_bounds(walk.x, (uint64_t)tr.sr.y + 1u, kSiteBwdList, misc)) walk = make_uint2(0u, 0u);
@@ -872,7 +874,7 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
         BwdRay ray = bwd_ray(tr, cam, g0, g1, g2, T, last);
         if (!top && last > hi) {
             // the ray walks past this unit: its state in front of entry hi is the forward's checkpoint
-            const float4 c = ckpt[((size_t)t * kCkptMax + k) * kThreads + threadIdx.x];
+            const float4 c = ckpt[((size_t)t * kCkptMax + k) * kTilePix + tray];
             const float4 cf = Cfin[pix];
             ray.T = c.x;
             ray.S0 = fmaf(T, cam.bg[0], cf.x - c.y);
@@ -888,7 +890,7 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
                                               make_uint2(phi, hi), warp_last, block_last,
                                               hit ? hit + (int64_t)t * hit_entries : nullptr,
                                               hit ? idrec + (int64_t)t * hit_entries : nullptr, hit_entries,
-                                              (int)threadIdx.x >> 5, ray, gacc, items, misc);
+                                              tray >> 5, ray, gacc, items, misc);
     }
 }
 
