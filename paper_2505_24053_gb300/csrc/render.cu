@@ -560,8 +560,11 @@ __global__ void __launch_bounds__(kTilePix) k_expand_tiles(const DevCam *__restr
 // atomics per (block, Gaussian). A warp skips list entries beyond the last
 // contributor of its rays, and entries that none of its rays hit in the forward
 // (the forward's per-warp hit record; the same FP32 evaluation decides both).
+// gS: the colour behind the current entry (what lies after it in the list, the
+// background included) projected on dL/dC. dL/dalpha needs only this dot product,
+// so the ray carries one scalar instead of the three channels.
 struct BwdRay {
-    float dx, dy, dz, g0, g1, g2, T, S0, S1, S2;
+    float dx, dy, dz, g0, g1, g2, T, gS;
     uint32_t last;
 };
 
@@ -589,11 +592,10 @@ __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const f
     gv[1] = fmaf(r.g0, wgt, gv[1]);
     gv[2] = fmaf(r.g1, wgt, gv[2]);
     gv[3] = fmaf(r.g2, wgt, gv[3]);
-    const float dLda = r.g0 * (Ti * e.y - r.S0 * inv_om) + r.g1 * (Ti * e.z - r.S1 * inv_om) +
-                       r.g2 * (Ti * e.w - r.S2 * inv_om);
-    r.S0 = fmaf(wgt, e.y, r.S0);
-    r.S1 = fmaf(wgt, e.z, r.S1);
-    r.S2 = fmaf(wgt, e.w, r.S2);
+    // dL/dalpha = sum_ch g_ch (T_i c_ch - S_ch / (1 - alpha)) = T_i (g . c) - (g . S) / (1 - alpha)
+    const float gc = fmaf(r.g0, e.y, fmaf(r.g1, e.z, r.g2 * e.w));
+    const float dLda = fmaf(Ti, gc, -r.gS * inv_om);
+    r.gS = fmaf(wgt, gc, r.gS);
     r.T = Ti;
     if (ae < alpha_max) {
         gv[0] = fmaf(dLda, exp2f(v.kappa * kNegHalfLog2e), gv[0]);  // dL/dsigma = dL/da e^{-kappa/2}
@@ -766,9 +768,7 @@ __device__ __forceinline__ BwdRay bwd_ray(const TileRay &tr, const DevCam &cam, 
     r.g2 = g2;
     r.T = T;
     r.last = last;
-    r.S0 = T * cam.bg[0];
-    r.S1 = T * cam.bg[1];
-    r.S2 = T * cam.bg[2];
+    r.gS = T * fmaf(g0, cam.bg[0], fmaf(g1, cam.bg[1], g2 * cam.bg[2]));
     return r;
 }
 
@@ -877,9 +877,9 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
             const float4 c = ckpt[((size_t)t * kCkptMax + k) * kTilePix + tray];
             const float4 cf = Cfin[pix];
             ray.T = c.x;
-            ray.S0 = fmaf(T, cam.bg[0], cf.x - c.y);
-            ray.S1 = fmaf(T, cam.bg[1], cf.y - c.z);
-            ray.S2 = fmaf(T, cam.bg[2], cf.z - c.w);
+            const float S0 = fmaf(T, cam.bg[0], cf.x - c.y), S1 = fmaf(T, cam.bg[1], cf.y - c.z),
+                        S2 = fmaf(T, cam.bg[2], cf.z - c.w);
+            ray.gS = fmaf(g0, S0, fmaf(g1, S1, g2 * S2));
         }
         const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
         if ((threadIdx.x & 31) == 0) atomicMax(&sm.maxlast, warp_last);
