@@ -1085,21 +1085,24 @@ __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ ti
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 const int i = b + c0 + u;
-                // the checkpoints below the walk's end split it (rare: walks beyond kCkptFirst)
-                uint32_t m = 0;
+                // the checkpoints below the walk's end split it (walks beyond kCkptFirst);
+                // their list indices are loaded together, then used from registers
                 const uint32_t nk = W[u] > kCkptFirst ? min(n[u], (uint32_t)kCkptMax) : 0u;
-                while (m < nk && ckpt_at[(size_t)i * kCkptMax + m].x < W[u]) ++m;
+                uint32_t B[kCkptMax];
+#pragma unroll
+                for (int j = 0; j < kCkptMax; ++j) B[j] = (uint32_t)j < nk ? ckpt_at[(size_t)i * kCkptMax + j].x : 0u;
+                uint32_t m = 0;
+#pragma unroll
+                for (int j = 0; j < kCkptMax; ++j) m += ((uint32_t)j < nk && B[j] < W[u]) ? 1u : 0u;
                 const uint32_t units = W[u] > 0 ? m + 1 : 0u;
-                for (uint32_t k = 0; __any_sync(0xffffffffu, k < units); ++k) {
-                    const bool ok = k < units;
-                    uint32_t len = 0;
-                    if (ok) {
-                        const uint32_t lo = k == 0 ? 0u : ckpt_at[(size_t)i * kCkptMax + k - 1].x;
-                        const uint32_t hi = k < m ? ckpt_at[(size_t)i * kCkptMax + k].x : W[u];
-                        len = hi - lo;
-                    }
-                    const uint32_t slot = bucket_add(hist, ok, order_bucket(len));
-                    if (pass == 1 && ok) order[slot] = ((uint32_t)i << 4) | k;
+#pragma unroll
+                for (int k = 0; k <= kCkptMax; ++k) {
+                    if (!__any_sync(0xffffffffu, (uint32_t)k < units)) break;
+                    const bool ok = (uint32_t)k < units;
+                    const uint32_t lo = k == 0 ? 0u : B[k - 1];
+                    const uint32_t hi = (uint32_t)k < m ? B[k < kCkptMax ? k : kCkptMax - 1] : W[u];
+                    const uint32_t slot = bucket_add(hist, ok, order_bucket(ok ? hi - lo : 0u));
+                    if (pass == 1 && ok) order[slot] = ((uint32_t)i << 4) | (uint32_t)k;
                 }
                 mine += units;
             }
