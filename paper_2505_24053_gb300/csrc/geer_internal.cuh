@@ -33,6 +33,7 @@ constexpr int kSmemTiles = 12288;          // per-block tile histogram in shared
 constexpr uint32_t kStatusCapacity = 1u;
 constexpr uint32_t kStatusListOverflow = 2u;  // inspection: a tile list differs from its counted length
 constexpr uint32_t kStatusBounds = 4u;        // GEER_CHECKED build: a bounds guard skipped an access
+constexpr uint32_t kStatusTimeout = 8u;       // a bounded wait on a shared-memory barrier gave up
 
 // Indices into the misc u32 array of the workspace.
 enum Misc : int {
@@ -178,6 +179,47 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
 __device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+
+// Bulk (TMA engine) copies into shared memory that complete on an mbarrier.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Arrive once on the barrier, announcing `bytes` more to be written by bulk copies.
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to this
+// CTA's shared memory; completion is counted on bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Orders this thread's earlier generic accesses of shared memory before later
+// bulk copies into it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Waits for the barrier's phase `parity` to complete, at most `limit` polls;
+// false if it did not (the caller records a timeout and goes on).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 __device__ __forceinline__ void unpack_ranges(const uint4 r4, int rg[8]) {

@@ -28,6 +28,10 @@ namespace {
 #ifndef GEER_FWD_UNROLL
 #define GEER_FWD_UNROLL 4
 #endif
+#ifndef GEER_FWD_BULK
+#define GEER_FWD_BULK 0  // 1: the forward stages its records with bulk copies (TMA engine) on an mbarrier
+#endif
+constexpr uint32_t kBarPolls = 1u << 22;  // bound of a wait on a shared-memory barrier
 constexpr int kFwdUnroll = GEER_FWD_UNROLL;
 #ifndef GEER_BWD_ROWS
 #define GEER_BWD_ROWS 16
@@ -206,6 +210,7 @@ struct WalkSmem {
     uint32_t maxlast, walkpos;       // the tile's last contributor and its super-list position + 1
     uint32_t nck, next_ck;           // forward: checkpoints recorded, list index of the next one
     int cam;
+    uint64_t bar;                    // forward with bulk staging: the batch's records have landed
 };
 
 // Copies item `id`'s 64-byte record into shared memory (4 x 16 B). An id beyond
@@ -337,6 +342,11 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
     const float log2_amin = log2f(p.alpha_min);
     uint32_t pos = sr.x, n_list = 0;
     int s_cnt = 0, want = BATCH < 64 ? BATCH : 64;
+#if GEER_FWD_BULK
+    static_assert(BATCH <= kThreads, "one record per thread and batch");
+    uint32_t parity = 0;
+    if (tid == 0) mbar_init(&sm.bar, kThreads);
+#endif
     while (true) {
         if (__syncthreads_count(f.done) == kThreads) break;
         // batches grow 64, 128, ... BATCH: most rays of a dense scene stop early
@@ -344,11 +354,33 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
         want = min(2 * want, BATCH);
         const int cnt = min(s_cnt, BATCH);
         if (cnt == 0) break;
+#if GEER_FWD_BULK
+        // every thread arrives once; thread r < cnt copies record r (64 B) with the
+        // TMA engine and announces its bytes
+        fence_proxy_async();
+        if (tid < cnt) {
+            const uint32_t id = sm.id[tid];
+            if (in_bounds(id, items, kSiteFwdItem, misc)) {
+                mbar_arrive_expect(&sm.bar, (uint32_t)sizeof(Record));
+                bulk_g2s(sm.rec + tid * 4, rec + id, (uint32_t)sizeof(Record), &sm.bar);
+            } else {
+                stage_record(sm.rec + tid * 4, rec, id, items, kSiteFwdItem, misc);
+                mbar_arrive_expect(&sm.bar, 0u);
+            }
+            sm.hit[tid] = make_uint2(0u, 0u);
+        } else {
+            mbar_arrive_expect(&sm.bar, 0u);
+        }
+        __syncthreads();
+        if (!mbar_wait(&sm.bar, parity, kBarPolls)) atomicOr(misc + kMiscStatus, kStatusTimeout);
+        parity ^= 1u;
+#else
         for (int r = tid; r < cnt; r += kThreads) {
             stage_record(sm.rec + r * 4, rec, sm.id[r], items, kSiteFwdItem, misc);
             sm.hit[r] = make_uint2(0u, 0u);
         }
         __syncthreads();
+#endif
         if (!f.done) walk_entries<SPLAT>(sm.rec, 0, cnt, n_list, hit_b, p, log2_amin, dx, dy, dz, f);
         // a checkpoint for the backward: every ray's (T, C) in front of tile-list
         // entry n_list + cnt and where that entry's search starts in the super-tile list
