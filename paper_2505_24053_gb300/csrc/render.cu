@@ -33,6 +33,10 @@ namespace {
 #endif
 constexpr uint32_t kBarPolls = 1u << 22;  // bound of a wait on a shared-memory barrier
 constexpr int kFwdUnroll = GEER_FWD_UNROLL;
+#ifndef GEER_SCAN
+#define GEER_SCAN 4
+#endif
+constexpr int kScan = GEER_SCAN;  // super-list loads in flight per thread in a list fill
 #ifndef GEER_BWD_ROWS
 #define GEER_BWD_ROWS 16
 #endif
@@ -107,43 +111,71 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 // Tile (cx, cy)'s list is its super-tile's depth-ordered list filtered by the
 // association test (sranges: the association ranges of the sorted pairs, in
-// list order): appends the entries of [pos, end) that pass, kThreads per step,
-// until s_id holds at least `want` entries or the list ends. Block-uniform (pos,
-// end, s_cnt, want are the same in every thread); s_id is visible on return.
+// list order): appends the entries of [pos, end) that pass until s_id holds at
+// least `want` entries or the list ends. Each step loads kScan x kThreads
+// entries at once (independent loads: a sparse tile's scan is bound by their
+// latency) and appends them in sub-steps of kThreads while s_id holds fewer than
+// `want`, so that s_id never takes more than want - 1 + kThreads entries; the
+// entries of sub-steps it did not take are read again by the next call.
+// Block-uniform (pos, end, s_cnt, want are the same in every thread); s_id is
+// visible on return. s_wcnt holds kScan x kThreads / 32 counts.
 template <int kThreads>
 __device__ __forceinline__ void fill_list(const uint32_t *__restrict__ svals, const uint4 *__restrict__ sranges,
                                           const float4 &col, const float4 &row, int cx, int cy, uint32_t &pos,
                                           uint32_t end, int want, uint32_t *s_id, uint32_t *s_pos, int &s_cnt,
                                           uint32_t *s_wcnt) {
+    constexpr int kWarps = kThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     while (s_cnt < want && pos < end) {
-        const uint32_t i = pos + threadIdx.x;
-        bool ok = false;
-        uint32_t id = 0;
-        if (i < end) {
-            int rg[8];
-            unpack_ranges(sranges[i], rg);
-            ok = tile_assoc(col, row, cx, cy, rg);
-            if (ok) id = svals[i];
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
-        if (lane == 0) s_wcnt[warp] = __popc(bal);
-        __syncthreads();
-        uint32_t base = 0, tot = 0;
+        uint4 raw[kScan];
+        uint32_t id[kScan];
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) {
-            const uint32_t c = s_wcnt[w];
-            base += w < warp ? c : 0u;
-            tot += c;
+        for (int r = 0; r < kScan; ++r) {
+            const uint32_t i = pos + (uint32_t)(r * kThreads) + threadIdx.x;
+            raw[r] = make_uint4(0u, 0u, 0u, 0u);
+            id[r] = 0u;
+            if (i < end) {
+                raw[r] = sranges[i];
+                id[r] = svals[i];
+            }
         }
-        if (ok) {
-            const int k = s_cnt + (int)(base + __popc(bal & lanemask_lt()));
-            s_id[k] = id;
-            if (s_pos) s_pos[k] = i;
+        uint32_t bal[kScan];
+#pragma unroll
+        for (int r = 0; r < kScan; ++r) {
+            const uint32_t i = pos + (uint32_t)(r * kThreads) + threadIdx.x;
+            bool ok = false;
+            if (i < end) {
+                int rg[8];
+                unpack_ranges(raw[r], rg);
+                ok = tile_assoc(col, row, cx, cy, rg);
+            }
+            bal[r] = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) s_wcnt[r * kWarps + warp] = __popc(bal[r]);
         }
         __syncthreads();
-        s_cnt += (int)tot;
-        pos += kThreads;
+        int cnt = s_cnt;
+        uint32_t adv = 0;
+#pragma unroll
+        for (int r = 0; r < kScan; ++r) {
+            if (cnt >= want) break;  // block-uniform: every thread reads the same counts
+            uint32_t base = 0, tot = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = s_wcnt[r * kWarps + w];
+                base += w < warp ? c : 0u;
+                tot += c;
+            }
+            if (bal[r] >> lane & 1u) {
+                const int k = cnt + (int)(base + __popc(bal[r] & lanemask_lt()));
+                s_id[k] = id[r];
+                if (s_pos) s_pos[k] = pos + (uint32_t)(r * kThreads) + threadIdx.x;
+            }
+            cnt += (int)tot;
+            adv += kThreads;
+        }
+        __syncthreads();
+        s_cnt = cnt;
+        pos += adv;
     }
 }
 
@@ -206,7 +238,7 @@ struct WalkSmem {
     uint32_t id[BATCH + kThreads];   // tile-list entries found by the filter (item ids)
     uint32_t pos[BATCH + kThreads];  // their positions in the super-tile list (forward)
     uint2 hit[BATCH];                // per entry: one byte per warp of the tile, nonzero if a ray hit it
-    uint32_t wcnt[kThreads / 32];
+    uint32_t wcnt[kScan * kThreads / 32];
     uint32_t maxlast, walkpos;       // the tile's last contributor and its super-list position + 1
     uint32_t nck, next_ck;           // forward: checkpoints recorded, list index of the next one
     int cam;
@@ -549,7 +581,7 @@ __global__ void __launch_bounds__(kTilePix) k_expand_tiles(const DevCam *__restr
                                                           uint32_t *__restrict__ lists, int64_t cap) {
     grid_dep_sync();
     __shared__ uint32_t s_id[2 * kTilePix];
-    __shared__ uint32_t s_wcnt[kTilePix / 32];
+    __shared__ uint32_t s_wcnt[kScan * kTilePix / 32];
     __shared__ int s_cam;
     if (misc[kMiscStatus] & kStatusCapacity) return;
     const int t = blockIdx.x, tid = threadIdx.x;
