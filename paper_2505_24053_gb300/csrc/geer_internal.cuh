@@ -18,7 +18,7 @@ constexpr int64_t kHitEntries = 2048;      // tile-list entries per tile whose h
 // kCkptMax per tile. The backward splits a tile's walk there into units that
 // run in parallel.
 constexpr int kCkptMax = 8;
-constexpr uint32_t kCkptFirst = 448, kCkptStride = 512;
+constexpr uint32_t kCkptFirst = 192, kCkptStride = 256;
 constexpr int kPrepThreads = 256;           // preprocess / duplicate block size
 constexpr int kSortThreads = 256;           // onesweep block size (8 warps)
 constexpr int kSortItems = 12;              // keys per thread per sort tile

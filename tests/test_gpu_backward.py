@@ -112,7 +112,7 @@ def test_backward_beyond_the_hit_record(geer, orc):
     stacked on the axis of a 16x16 pinhole, so that the centre rays composite
     ~2270 of them before T falls below T_min. The backward evaluates every entry
     beyond the record. The walk is split into units at the forward's
-    checkpoints (every ~512 entries from entry 448), each starting from the
+    checkpoints (every ~256 entries from entry 192), each starting from the
     forward's own transmittance, so the reverse recovery T_i = T_(i+1) / (1 - a_i)
     runs over at most ~512 steps (relative error <= 512 * 3 * 2^-24 ~ 1e-4):
     the common 1e-3 tolerance holds."""
