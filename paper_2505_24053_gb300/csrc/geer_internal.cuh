@@ -298,6 +298,7 @@ struct geer_workspace {
     float4 *d_ckpt;         // [cap_tiles][kCkptMax][kTilePix] rays' (T, C) at the forward's checkpoints (or null)
     uint2 *d_ckpt_at;       // [cap_tiles][kCkptMax] checkpoint (tile-list index, super-list position)
     uint32_t *d_ckpt_cnt;   // [cap_tiles] checkpoints recorded by the last forward
+    uint32_t *d_ckpt_work;  // [cap_tiles][kCkptMax + 1] (entry, warp) hits counted up to each checkpoint, then to the walk's end
     float4 *d_Cfin;         // [cap_pixels] composited colour before the background (tiles with checkpoints)
     int bwd_grid;           // persistent backward blocks
     uint4 *d_sranges;       // [cap_pairs] association ranges of the sorted pairs' items (in list order)

@@ -1053,12 +1053,16 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
 // covered W > 0 list entries and passed the checkpoints B_1 < ... < B_m < W
 // (the first m of the tile's recorded ones) has the units k = 0..m, entries
 // [B_k, B_{k+1}) with B_0 = 0 and B_{m+1} = W; they are ordered by descending
-// length (bucketed as the forward's schedule), units[slot] = tile << 4 | k.
+// cost (bucketed as the forward's schedule), units[slot] = tile << 4 | k. The
+// cost is the unit's (entry, warp) pairs whose hit byte the forward set (its
+// counts at the checkpoints and at the walk's end): a backward warp walks those
+// steps, so a dense tile's unit costs more than a sparse one's of the same length.
 // Also sets the unit count and resets the counter the persistent backward
 // blocks take units from.
 __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ tile_walk,
                                                     const uint32_t *__restrict__ ckpt_cnt,
-                                                    const uint2 *__restrict__ ckpt_at, int ntiles,
+                                                    const uint2 *__restrict__ ckpt_at,
+                                                    const uint32_t *__restrict__ ckpt_work, int ntiles,
                                                     uint32_t *__restrict__ misc, uint32_t *__restrict__ order) {
     grid_dep_sync();
     __shared__ uint32_t hist[kOrderBuckets];
@@ -1088,9 +1092,13 @@ __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ ti
                 // the checkpoints below the walk's end split it (walks beyond kCkptFirst);
                 // their list indices are loaded together, then used from registers
                 const uint32_t nk = W[u] > kCkptFirst ? min(n[u], (uint32_t)kCkptMax) : 0u;
-                uint32_t B[kCkptMax];
+                uint32_t B[kCkptMax], A[kCkptMax];
 #pragma unroll
-                for (int j = 0; j < kCkptMax; ++j) B[j] = (uint32_t)j < nk ? ckpt_at[(size_t)i * kCkptMax + j].x : 0u;
+                for (int j = 0; j < kCkptMax; ++j) {
+                    B[j] = (uint32_t)j < nk ? ckpt_at[(size_t)i * kCkptMax + j].x : 0u;
+                    A[j] = (uint32_t)j < nk && ckpt_work ? ckpt_work[(size_t)i * (kCkptMax + 1) + j] : 0u;
+                }
+                const uint32_t Atot = W[u] > 0 && ckpt_work ? ckpt_work[(size_t)i * (kCkptMax + 1) + kCkptMax] : 0u;
                 uint32_t m = 0;
 #pragma unroll
                 for (int j = 0; j < kCkptMax; ++j) m += ((uint32_t)j < nk && B[j] < W[u]) ? 1u : 0u;
@@ -1101,7 +1109,11 @@ __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ ti
                     const bool ok = (uint32_t)k < units;
                     const uint32_t lo = k == 0 ? 0u : B[k - 1];
                     const uint32_t hi = (uint32_t)k < m ? B[k < kCkptMax ? k : kCkptMax - 1] : W[u];
-                    const uint32_t slot = bucket_add(hist, ok, order_bucket(ok ? hi - lo : 0u));
+                    // the unit's cost: the warp steps the forward counted in it, else its length
+                    const uint32_t wlo = k == 0 ? 0u : A[k - 1];
+                    const uint32_t whi = (uint32_t)k < m ? A[k < kCkptMax ? k : kCkptMax - 1] : Atot;
+                    const uint32_t cost = ckpt_work ? max(whi - wlo, 1u) : hi - lo;
+                    const uint32_t slot = bucket_add(hist, ok, order_bucket(ok ? cost : 0u));
                     if (pass == 1 && ok) order[slot] = ((uint32_t)i << 4) | (uint32_t)k;
                 }
                 mine += units;
@@ -1193,7 +1205,7 @@ cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
 
 cudaError_t launch_bwd_order(const geer_workspace *ws, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
-    launch_k(k_bwd_order, dim3(1), dim3(1024), 0, s, ws->d_tile_walk, ws->d_ckpt_cnt, ws->d_ckpt_at,
+    launch_k(k_bwd_order, dim3(1), dim3(1024), 0, s, ws->d_tile_walk, ws->d_ckpt_cnt, ws->d_ckpt_at, ws->d_ckpt_work,
              (int)ws->n_tiles, ws->d_misc, ws->d_bwd_order);
     return cudaGetLastError();
 }

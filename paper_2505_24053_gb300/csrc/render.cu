@@ -241,6 +241,9 @@ struct WalkSmem {
     uint32_t wcnt[kScan * kThreads / 32];
     uint32_t maxlast, walkpos;       // the tile's last contributor and its super-list position + 1
     uint32_t nck, next_ck;           // forward: checkpoints recorded, list index of the next one
+    uint32_t wacc[kThreads];         // forward: each thread's count of backward steps
+    uint32_t ckw[kCkptMax];          // forward: the counts at the checkpoints (work: then the walk's)
+    uint32_t work, pend;             // forward: a checkpoint's count of backward steps; its index + 1 while due
     int cam;
     uint64_t bar;                    // forward with bulk staging: the batch's records have landed
 };
@@ -362,7 +365,8 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
                                              uint2 sr, float dx, float dy, float dz, uint2 *__restrict__ hit_rec,
                                              uint32_t *__restrict__ id_rec, int64_t hit_entries, uint64_t items,
                                              uint32_t *misc,
-                                             float4 *__restrict__ ckpt, uint2 *__restrict__ ckpt_at, FwdRay &f) {
+                                             float4 *__restrict__ ckpt, uint2 *__restrict__ ckpt_at,
+                                             FwdRay &f) {
     const int tid = threadIdx.x;
     uint8_t *const hit_b = reinterpret_cast<uint8_t *>(sm.hit) + (tid >> 5);  // this warp's byte of entry 0
     if (tid == 0) {
@@ -370,7 +374,10 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
         sm.walkpos = sr.x;
         sm.nck = 0u;
         sm.next_ck = ckpt ? kCkptFirst : 0xffffffffu;
+        sm.work = 0u;
+        sm.pend = 0u;
     }
+    sm.wacc[tid] = 0u;
     const float log2_amin = log2f(p.alpha_min);
     uint32_t pos = sr.x, n_list = 0;
     int s_cnt = 0, want = BATCH < 64 ? BATCH : 64;
@@ -427,21 +434,46 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
         __syncthreads();
         if (ck && tid == 0) {
             ckpt_at[nck] = make_uint2(n_list + (uint32_t)cnt, sm.pos[cnt - 1] + 1u);
+            sm.pend = nck + 1u;
             sm.nck = nck + 1u;
             sm.next_ck = n_list + (uint32_t)cnt + kCkptStride;
         }
         if (tid == 0 && sm.maxlast > n_list) sm.walkpos = sm.pos[sm.maxlast - 1u - n_list] + 1u;
         // the batch's hit bytes, for the backward's skip of entries its warp never hit,
-        // and its item ids: the backward reads the tile's list from here without filtering
-        if (hit_rec)
-            for (int r = tid; r < cnt && (int64_t)n_list + r < hit_entries; r += kThreads) {
-                hit_rec[n_list + r] = sm.hit[r];
+        // and its item ids: the backward reads the tile's list from here without
+        // filtering; with checkpoints, the count of the backward's steps (one per
+        // entry and warp that hit it), summed over the block at each checkpoint
+        uint32_t we = 0;
+        for (int r = tid; r < cnt; r += kThreads) {
+            const uint2 h = sm.hit[r];
+            if (ckpt) we += (uint32_t)(__popc(__vcmpne4(h.x, 0u)) + __popc(__vcmpne4(h.y, 0u))) >> 3;
+            if (hit_rec && (int64_t)n_list + r < hit_entries) {
+                hit_rec[n_list + r] = h;
                 id_rec[n_list + r] = sm.id[r];
             }
+        }
+        if (ckpt) {  // the thread's count lives in shared memory: the walk's registers are at their limit
+            we += sm.wacc[tid];
+            sm.wacc[tid] = we;
+            if (ck) {
+                we = __reduce_add_sync(0xffffffffu, we);
+                if ((tid & 31) == 0) atomicAdd(&sm.work, we);
+            }
+        }
         shift_list<kThreads>(sm.id, sm.pos, cnt, s_cnt);
+        // after shift_list's barrier: the checkpoint's count has landed
+        if (tid == 0 && sm.pend) {
+            sm.ckw[sm.pend - 1u] = sm.work;
+            sm.work = 0u;
+            sm.pend = 0u;
+        }
         n_list += (uint32_t)cnt;
     }
     if (!f.done) f.n_eval = n_list;  // a ray that never terminated evaluated every entry walked
+    if (ckpt) {
+        const uint32_t we = __reduce_add_sync(0xffffffffu, sm.wacc[tid]);
+        if ((tid & 31) == 0) atomicAdd(&sm.work, we);
+    }
     __syncthreads();
 }
 
@@ -502,6 +534,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                                             uint64_t items, int64_t cap_pairs,
                                                             float4 *__restrict__ ckpt, uint2 *__restrict__ ckpt_at,
                                                             uint32_t *__restrict__ ckpt_cnt,
+                                                            uint32_t *__restrict__ ckpt_work,
                                                             float4 *__restrict__ Cfin) {
     grid_dep_sync();
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
@@ -550,11 +583,14 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                          tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr,
                                          hit ? idrec + (int64_t)t * hit_entries : nullptr, hit_entries, items,
                                          misc, ckpt ? ckpt + (size_t)t * kCkptMax * kTilePix : nullptr,
-                                         ckpt ? ckpt_at + (size_t)t * kCkptMax : nullptr, f);
+                                         ckpt ? ckpt_at + (size_t)t * kCkptMax : nullptr,
+                                         f);
     if (threadIdx.x == 0) {
         tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
         if (ckpt_cnt) ckpt_cnt[t] = sm.nck;
     }
+    if (ckpt_work && (int)threadIdx.x <= kCkptMax && (threadIdx.x < sm.nck || threadIdx.x == kCkptMax))
+        ckpt_work[(size_t)t * (kCkptMax + 1) + threadIdx.x] = threadIdx.x == kCkptMax ? sm.work : sm.ckw[threadIdx.x];
     if (tr.inside) {
         const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
         rgb[3 * pix + 0] = fmaf(f.T, cam.bg[0], f.cr);
@@ -971,7 +1007,7 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
         ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->d_idrec, ws->hit_entries,
         ws->tile_mask_on ? static_cast<const uint8_t *>(ws->d_tile_mask) : nullptr, ws->n_tiles,
         (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs, ws->d_ckpt, ws->d_ckpt_at, ws->d_ckpt_cnt,
-        ws->d_Cfin);
+        ws->d_ckpt_work, ws->d_Cfin);
     return cudaGetLastError();
 }
 
