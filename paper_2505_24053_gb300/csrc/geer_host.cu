@@ -323,7 +323,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
     size_t o_ck = L.take(bwd ? sizeof(float4) * c.tiles * kCkptMax * kTilePix : 0);
     size_t o_cka = L.take(bwd ? sizeof(uint2) * c.tiles * kCkptMax : 0);
     size_t o_ckn = L.take(bwd ? sizeof(uint32_t) * c.tiles : 0);
-    size_t o_ckw = L.take(bwd ? sizeof(uint32_t) * c.tiles * (kCkptMax + 1) : 0);
+    size_t o_ckw = L.take(bwd ? sizeof(uint4) * c.tiles : 0);
     size_t o_cf = L.take(bwd ? sizeof(float4) * c.pixels : 0);
     if (base && ws) {
         ws->d_cams = reinterpret_cast<DevCam *>(base + o_cams);
@@ -365,7 +365,7 @@ size_t layout(const Caps &c, char *base, geer_workspace *ws) {
         ws->d_ckpt = bwd ? reinterpret_cast<float4 *>(base + o_ck) : nullptr;
         ws->d_ckpt_at = bwd ? reinterpret_cast<uint2 *>(base + o_cka) : nullptr;
         ws->d_ckpt_cnt = bwd ? reinterpret_cast<uint32_t *>(base + o_ckn) : nullptr;
-        ws->d_ckpt_work = bwd ? reinterpret_cast<uint32_t *>(base + o_ckw) : nullptr;
+        ws->d_unit_rec = bwd ? reinterpret_cast<uint4 *>(base + o_ckw) : nullptr;
         ws->d_Cfin = bwd ? reinterpret_cast<float4 *>(base + o_cf) : nullptr;
     }
     return L.off;

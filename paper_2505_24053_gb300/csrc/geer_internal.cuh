@@ -237,6 +237,22 @@ __device__ __forceinline__ bool tile_assoc(const float4 &col, const float4 &row,
     return aok && bok;
 }
 
+// Schedule bucket of a cost c (a tile's pair count, a backward unit's steps):
+// larger costs first, four buckets per octave, zero cost last.
+constexpr int kOrderBuckets = 129;
+__device__ __forceinline__ int order_bucket(uint32_t c) {
+    if (c == 0) return kOrderBuckets - 1;
+    const int lg = 31 - __clz(c);
+    const int sub = (int)((c >> (lg >= 2 ? lg - 2 : 0)) & 3u);
+    return 127 - (lg * 4 + (lg >= 2 ? sub : 0));
+}
+
+// A tile's backward units as the forward leaves them (one uint4 per tile):
+// byte k (k <= kCkptMax) the schedule bucket of unit k, byte 15 the number of
+// units (0: nothing to walk back).
+constexpr int kUnitCountByte = 15;
+static_assert(kCkptMax + 1 <= kUnitCountByte, "the unit buckets and their count share one uint4");
+
 // Stages timed by geer_enable_timing (CUDA events around each stage's kernels).
 enum Stage : int {
     kStagePreprocess = 0,
@@ -298,7 +314,7 @@ struct geer_workspace {
     float4 *d_ckpt;         // [cap_tiles][kCkptMax][kTilePix] rays' (T, C) at the forward's checkpoints (or null)
     uint2 *d_ckpt_at;       // [cap_tiles][kCkptMax] checkpoint (tile-list index, super-list position)
     uint32_t *d_ckpt_cnt;   // [cap_tiles] checkpoints recorded by the last forward
-    uint32_t *d_ckpt_work;  // [cap_tiles][kCkptMax + 1] (entry, warp) hits counted up to each checkpoint, then to the walk's end
+    uint4 *d_unit_rec;      // [cap_tiles] the tile's backward units: their schedule buckets and count
     float4 *d_Cfin;         // [cap_pixels] composited colour before the background (tiles with checkpoints)
     int bwd_grid;           // persistent backward blocks
     uint4 *d_sranges;       // [cap_pairs] association ranges of the sorted pairs' items (in list order)

@@ -913,16 +913,6 @@ __global__ void __launch_bounds__(kPrepThreads) k_duplicate(
             if (sh[k]) atomicAdd(&scount[k], sh[k]);
 }
 
-// Render schedule bucket of a tile with c pairs: larger counts first, four
-// buckets per octave, empty tiles last.
-constexpr int kOrderBuckets = 129;
-__device__ __forceinline__ int order_bucket(uint32_t c) {
-    if (c == 0) return kOrderBuckets - 1;
-    const int lg = 31 - __clz(c);
-    const int sub = (int)((c >> (lg >= 2 ? lg - 2 : 0)) & 3u);
-    return 127 - (lg * 4 + (lg >= 2 ? sub : 0));
-}
-
 // Warp-aggregated bucket atomic: the lanes with ok hold bucket bk; one atomic
 // per distinct bucket of the warp adds the lanes' count to hist[bk]. Returns the
 // lane's slot (old value + its rank among the lanes of its bucket). All lanes of
@@ -1051,18 +1041,14 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
 
 // One block: the backward's units and their schedule. A tile whose forward walk
 // covered W > 0 list entries and passed the checkpoints B_1 < ... < B_m < W
-// (the first m of the tile's recorded ones) has the units k = 0..m, entries
-// [B_k, B_{k+1}) with B_0 = 0 and B_{m+1} = W; they are ordered by descending
-// cost (bucketed as the forward's schedule), units[slot] = tile << 4 | k. The
-// cost is the unit's (entry, warp) pairs whose hit byte the forward set (its
-// counts at the checkpoints and at the walk's end): a backward warp walks those
-// steps, so a dense tile's unit costs more than a sparse one's of the same length.
-// Also sets the unit count and resets the counter the persistent backward
-// blocks take units from.
-__global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ tile_walk,
-                                                    const uint32_t *__restrict__ ckpt_cnt,
-                                                    const uint2 *__restrict__ ckpt_at,
-                                                    const uint32_t *__restrict__ ckpt_work, int ntiles,
+// has the units k = 0..m, entries [B_k, B_{k+1}) with B_0 = 0 and B_{m+1} = W.
+// The forward leaves per tile their number and schedule buckets (unit_rec: the
+// bucket of each unit's cost, the (entry, warp) pairs whose hit byte it set in
+// the unit: a backward warp walks those steps, so a dense tile's unit costs
+// more than a sparse one's of the same length). The units are ordered by
+// descending cost, units[slot] = tile << 4 | k. Also sets the unit count and
+// resets the counter the persistent backward blocks take units from.
+__global__ void __launch_bounds__(1024) k_bwd_order(const uint4 *__restrict__ unit_rec, int ntiles,
                                                     uint32_t *__restrict__ misc, uint32_t *__restrict__ order) {
     grid_dep_sync();
     __shared__ uint32_t hist[kOrderBuckets];
@@ -1074,46 +1060,27 @@ __global__ void __launch_bounds__(1024) k_bwd_order(const uint2 *__restrict__ ti
     __syncthreads();
     const int chunk = (ntiles + 1023) / 1024;
     const int b = t * chunk, e = min(ntiles, b + chunk);
-    constexpr int G = 8;  // tiles whose walk records are loaded together
+    constexpr int G = 4;  // tiles whose records are loaded together
     for (int pass = 0; pass < 2; ++pass) {
         uint32_t mine = 0;
         for (int c0 = 0; c0 < chunk; c0 += G) {  // the same trip counts in every lane (warp-wide atomics)
-            uint32_t W[G], n[G];
+            uint4 r[G];
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 const int i = b + c0 + u;
-                const bool in = c0 + u < chunk && i < e;
-                W[u] = in ? tile_walk[i].y : 0u;
-                n[u] = in && ckpt_cnt ? ckpt_cnt[i] : 0u;
+                r[u] = c0 + u < chunk && i < e ? unit_rec[i] : make_uint4(0u, 0u, 0u, 0u);
             }
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 const int i = b + c0 + u;
-                // the checkpoints below the walk's end split it (walks beyond kCkptFirst);
-                // their list indices are loaded together, then used from registers
-                const uint32_t nk = W[u] > kCkptFirst ? min(n[u], (uint32_t)kCkptMax) : 0u;
-                uint32_t B[kCkptMax], A[kCkptMax];
-#pragma unroll
-                for (int j = 0; j < kCkptMax; ++j) {
-                    B[j] = (uint32_t)j < nk ? ckpt_at[(size_t)i * kCkptMax + j].x : 0u;
-                    A[j] = (uint32_t)j < nk && ckpt_work ? ckpt_work[(size_t)i * (kCkptMax + 1) + j] : 0u;
-                }
-                const uint32_t Atot = W[u] > 0 && ckpt_work ? ckpt_work[(size_t)i * (kCkptMax + 1) + kCkptMax] : 0u;
-                uint32_t m = 0;
-#pragma unroll
-                for (int j = 0; j < kCkptMax; ++j) m += ((uint32_t)j < nk && B[j] < W[u]) ? 1u : 0u;
-                const uint32_t units = W[u] > 0 ? m + 1 : 0u;
+                const uint32_t units = min((r[u].w >> (8 * (kUnitCountByte & 3))) & 0xffu, (uint32_t)kCkptMax + 1u);
 #pragma unroll
                 for (int k = 0; k <= kCkptMax; ++k) {
                     if (!__any_sync(0xffffffffu, (uint32_t)k < units)) break;
                     const bool ok = (uint32_t)k < units;
-                    const uint32_t lo = k == 0 ? 0u : B[k - 1];
-                    const uint32_t hi = (uint32_t)k < m ? B[k < kCkptMax ? k : kCkptMax - 1] : W[u];
-                    // the unit's cost: the warp steps the forward counted in it, else its length
-                    const uint32_t wlo = k == 0 ? 0u : A[k - 1];
-                    const uint32_t whi = (uint32_t)k < m ? A[k < kCkptMax ? k : kCkptMax - 1] : Atot;
-                    const uint32_t cost = ckpt_work ? max(whi - wlo, 1u) : hi - lo;
-                    const uint32_t slot = bucket_add(hist, ok, order_bucket(ok ? cost : 0u));
+                    const uint32_t word = k < 4 ? r[u].x : (k < 8 ? r[u].y : r[u].z);
+                    const int bk = min((int)((word >> (8 * (k & 3))) & 0xffu), kOrderBuckets - 1);
+                    const uint32_t slot = bucket_add(hist, ok, bk);
                     if (pass == 1 && ok) order[slot] = ((uint32_t)i << 4) | (uint32_t)k;
                 }
                 mine += units;
@@ -1205,8 +1172,8 @@ cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
 
 cudaError_t launch_bwd_order(const geer_workspace *ws, cudaStream_t s) {
     if (ws->n_tiles == 0) return cudaSuccess;
-    launch_k(k_bwd_order, dim3(1), dim3(1024), 0, s, ws->d_tile_walk, ws->d_ckpt_cnt, ws->d_ckpt_at, ws->d_ckpt_work,
-             (int)ws->n_tiles, ws->d_misc, ws->d_bwd_order);
+    launch_k(k_bwd_order, dim3(1), dim3(1024), 0, s, ws->d_unit_rec, (int)ws->n_tiles, ws->d_misc,
+             ws->d_bwd_order);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,9 @@ namespace {
 #ifndef GEER_FWD_UNROLL
 #define GEER_FWD_UNROLL 4
 #endif
+#ifndef GEER_FWD_MINB
+#define GEER_FWD_MINB 4  // resident forward blocks per SM the registers must allow
+#endif
 #ifndef GEER_FWD_BULK
 #define GEER_FWD_BULK 0  // 1: the forward stages its records with bulk copies (TMA engine) on an mbarrier
 #endif
@@ -243,6 +246,7 @@ struct WalkSmem {
     uint32_t nck, next_ck;           // forward: checkpoints recorded, list index of the next one
     uint32_t wacc[kThreads];         // forward: each thread's count of backward steps
     uint32_t ckw[kCkptMax];          // forward: the counts at the checkpoints (work: then the walk's)
+    uint32_t ckB[kCkptMax];          // forward: the checkpoints' tile-list indices
     uint32_t work, pend;             // forward: a checkpoint's count of backward steps; its index + 1 while due
     int cam;
     uint64_t bar;                    // forward with bulk staging: the batch's records have landed
@@ -434,6 +438,7 @@ __device__ __forceinline__ void forward_walk(WalkSmem<kThreads, BATCH> &sm, cons
         __syncthreads();
         if (ck && tid == 0) {
             ckpt_at[nck] = make_uint2(n_list + (uint32_t)cnt, sm.pos[cnt - 1] + 1u);
+            sm.ckB[nck] = n_list + (uint32_t)cnt;
             sm.pend = nck + 1u;
             sm.nck = nck + 1u;
             sm.next_ck = n_list + (uint32_t)cnt + kCkptStride;
@@ -515,7 +520,7 @@ __device__ __forceinline__ bool tile_ray(const DevCam &cam, int t, int row0, con
 }
 
 template <int ROWS, int BATCH, bool SPLAT>
-__global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
+__global__ void __launch_bounds__(ROWS * kTile, GEER_FWD_MINB) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
                                                             const float2 *__restrict__ ptab,
                                                             const float4 *__restrict__ ttab, int S,
                                                             uint2 *__restrict__ tile_walk,
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
                                                             uint64_t items, int64_t cap_pairs,
                                                             float4 *__restrict__ ckpt, uint2 *__restrict__ ckpt_at,
                                                             uint32_t *__restrict__ ckpt_cnt,
-                                                            uint32_t *__restrict__ ckpt_work,
+                                                            uint4 *__restrict__ unit_rec,
                                                             float4 *__restrict__ Cfin) {
     grid_dep_sync();
     constexpr int kThreads = ROWS * kTile, kParts = kTile / ROWS;
@@ -552,6 +557,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         if (threadIdx.x == 0) {
             tile_walk[t] = make_uint2(0u, 0u);
             if (ckpt_cnt) ckpt_cnt[t] = 0u;
+            if (unit_rec) unit_rec[t] = make_uint4(0u, 0u, 0u, 0u);
         }
         return;
     }
@@ -560,6 +566,7 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         if (threadIdx.x == 0) {
             tile_walk[t] = make_uint2(0u, 0u);
             if (ckpt_cnt) ckpt_cnt[t] = 0u;
+            if (unit_rec) unit_rec[t] = make_uint4(0u, 0u, 0u, 0u);
         }
         if (tr.inside) {
             const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
@@ -589,8 +596,6 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
         if (ckpt_cnt) ckpt_cnt[t] = sm.nck;
     }
-    if (ckpt_work && (int)threadIdx.x <= kCkptMax && (threadIdx.x < sm.nck || threadIdx.x == kCkptMax))
-        ckpt_work[(size_t)t * (kCkptMax + 1) + threadIdx.x] = threadIdx.x == kCkptMax ? sm.work : sm.ckw[threadIdx.x];
     if (tr.inside) {
         const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
         rgb[3 * pix + 0] = fmaf(f.T, cam.bg[0], f.cr);
@@ -601,6 +606,22 @@ __global__ void __launch_bounds__(ROWS * kTile) k_render_fwd(const DevCam *__res
         last_out[pix] = f.last;
         evals[pix] = make_uint2(f.n_eval, f.n_applied);
         if (Cfin && sm.nck) Cfin[pix] = make_float4(f.cr, f.cg, f.cb, f.T);  // the backward's colour behind
+    }
+    // the backward's units: the checkpoints inside the walk [0, W) split it; thread k
+    // writes unit k's schedule bucket (from the steps counted in it), thread
+    // kUnitCountByte the number of units
+    if (unit_rec && ((int)threadIdx.x <= kCkptMax || threadIdx.x == kUnitCountByte)) {
+        const uint32_t W = sm.maxlast, nk = W > kCkptFirst ? min(sm.nck, (uint32_t)kCkptMax) : 0u;
+        uint32_t m = 0;
+        for (uint32_t j = 0; j < nk; ++j) m += sm.ckB[j] < W ? 1u : 0u;
+        const uint32_t units = W > 0 ? m + 1u : 0u, k = threadIdx.x;
+        uint8_t *rb = reinterpret_cast<uint8_t *>(unit_rec + t);
+        if (k == (uint32_t)kUnitCountByte) {
+            rb[k] = (uint8_t)units;
+        } else if (k < units) {
+            const uint32_t wlo = k == 0 ? 0u : sm.ckw[k - 1], whi = k < m ? sm.ckw[k] : sm.work;
+            rb[k] = (uint8_t)order_bucket(max(whi - wlo, 1u));
+        }
     }
 }
 
@@ -1007,7 +1028,7 @@ cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_fin
         ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->d_idrec, ws->hit_entries,
         ws->tile_mask_on ? static_cast<const uint8_t *>(ws->d_tile_mask) : nullptr, ws->n_tiles,
         (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs, ws->d_ckpt, ws->d_ckpt_at, ws->d_ckpt_cnt,
-        ws->d_ckpt_work, ws->d_Cfin);
+        ws->d_unit_rec, ws->d_Cfin);
     return cudaGetLastError();
 }
 
