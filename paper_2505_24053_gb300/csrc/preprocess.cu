@@ -991,10 +991,13 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
                                                        const uint32_t *__restrict__ misc,
                                                        uint32_t *__restrict__ tile_order) {
     grid_dep_sync();
+    constexpr int kOrderSmem = 16384;  // super-tiles / tiles whose buckets the block keeps in shared memory
     __shared__ uint32_t warp_tot[32];
     __shared__ uint32_t hist[kOrderBuckets];
+    __shared__ uint8_t s_sbk[kOrderSmem], s_tbk[kOrderSmem];
     if (misc[kMiscStatus] & kStatusCapacity) return;
     const int t = threadIdx.x;
+    const bool keep_s = nst <= kOrderSmem, keep_t = ntiles <= kOrderSmem;
     for (int i = t; i < kOrderBuckets; i += 1024) hist[i] = 0u;
     // super-tile ranges
     const uint32_t *scount = reinterpret_cast<const uint32_t *>(srange + nst);
@@ -1006,10 +1009,12 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
     for (int i = sb; i < se; ++i) {
         const uint32_t cnt = scount[i];
         srange[i] = make_uint2(srun, srun + cnt);
+        if (keep_s) s_sbk[i] = (uint8_t)order_bucket(cnt);
         srun += cnt;
     }
     __syncthreads();
-    // each tile's cost estimate: its super-tile's list length (0 for padding tiles)
+    // each tile's cost estimate: its super-tile's list length (0 for padding tiles),
+    // bucketed in the first pass and kept for the second
     const int chunk = (ntiles + 1023) / 1024;
     const int b = t * chunk, e = min(ntiles, b + chunk);
     int c = 0;
@@ -1019,18 +1024,26 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict_
         int cc = c;
         for (int k = 0; k < chunk; ++k) {  // the same trip count in every lane (warp-wide atomics)
             const int i = b + k;
-            uint32_t len = 0;
-            if (i < e) {
+            int bk = kOrderBuckets - 1;
+            if (i < e && pass == 1 && keep_t) {
+                bk = s_tbk[i];
+            } else if (i < e) {
                 while (cc + 1 < ncams && cams[cc + 1].tile_base <= i) ++cc;
                 const DevCam &cm = cams[cc];
                 const int lt = i - cm.tile_base;
                 if (lt >= 0 && lt < cm.tiles_x * cm.tiles_y) {
                     const int cy = lt / cm.tiles_x, cx = lt - cy * cm.tiles_x;
-                    const uint2 r = srange[cm.stile_base + (cy / S) * cm.stiles_x + cx / S];
-                    len = r.y - r.x;
+                    const int si = cm.stile_base + (cy / S) * cm.stiles_x + cx / S;
+                    if (keep_s) {
+                        bk = s_sbk[si];
+                    } else {
+                        const uint2 r = srange[si];
+                        bk = order_bucket(r.y - r.x);
+                    }
                 }
+                if (keep_t) s_tbk[i] = (uint8_t)bk;
             }
-            const uint32_t slot = bucket_add(hist, i < e, order_bucket(len));
+            const uint32_t slot = bucket_add(hist, i < e, bk);
             if (pass == 1 && i < e) tile_order[slot] = (uint32_t)i;
         }
         __syncthreads();
