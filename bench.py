@@ -364,6 +364,8 @@ def run(args):
         ts = tilesplit.TileSplit(ws, rank, world)
         target_step = ts.masked_target(target)
 
+    fused = not args.separate_render
+
     def backward(gk):
         if split:
             ws.render_bwd_tiles(dL)
@@ -371,6 +373,20 @@ def run(args):
             ws.preprocess_bwd(gk, grads, accumulate=False)
         else:
             ws.render_bwd(gk, dL, grads, accumulate=False)
+
+    def render_step(gk, rgb_out):
+        """The step's render: forward, L1 gradient and backward (the gradients written).
+        Fused: one launch for the forward, the L1 gradient and the backward's render
+        stage (geer_render_train_l1), then its preprocess stage."""
+        if fused:
+            ws.render_train_l1(target_step, rgb_out, dL)
+            if split:
+                tilesplit.reduce_sum(ws.grad_accumulators(), None, world)
+            ws.preprocess_bwd(gk, grads, accumulate=False)
+        else:
+            ws.render_fwd(rgb_out)
+            geer.l1_loss_grad(rgb_out, target_step, dL)
+            backward(gk)
 
     # ev[0] and ev[3] bracket a step; with detail, ev[1] and ev[2] also mark the
     # end of the preprocess and of the binning (a breakdown run, not the timed one:
@@ -385,9 +401,7 @@ def run(args):
         if detail:
             ev[2].record(stream)
         # training step: forward, L1 loss gradient, backward (the step's gradients written)
-        ws.render_fwd(rgb)
-        geer.l1_loss_grad(rgb, target_step, dL)
-        backward(g)
+        render_step(g, rgb)
         ev[3].record(stream)
 
     def fwd_step(ev, detail=False):
@@ -430,13 +444,14 @@ def run(args):
 
     # the timed steps: the library's stage events around the dominant kernel's stage
     # only (the backward render; the forward render without a backward)
-    dom_stage = "render_bwd" if have_bwd else "render_fwd"
-    ws.enable_timing(True, stages=(dom_stage,))
+    dom_stage = ("render_train" if fused else "render_bwd") if have_bwd else "render_fwd"
+    ws.enable_timing(True, stages=(dom_stage, "render_fwd") if have_bwd and fused else (dom_stage,))
     train_evs = None
     if have_bwd:
         train_evs, t_wall, clk = timed(train_step, True)
         dom_stage_ms = {dom_stage: ws.stage_times()[dom_stage][0]}  # the last 64 timed steps
     fwd_evs, fwd_wall, fclk = timed(fwd_step, not have_bwd)
+    fwd_stage_ms = ws.stage_times()["render_fwd"][0]  # the forward render in the forward-only steps
     if not have_bwd:
         t_wall, clk = fwd_wall, fclk
         dom_stage_ms = {dom_stage: ws.stage_times()[dom_stage][0]}
@@ -457,7 +472,9 @@ def run(args):
     value, total_ms = aggregate(float(sum(step_ms)), pixels, args.steps, world, dist, dev, shared=split)
     fwd_ms = [e[0].elapsed_time(e[3]) for e in fwd_evs]
     fwd_value = pixels / (statistics.mean(fwd_ms) / 1e3) / 1e6
-    fwd_render_ms = stage_ms["render_fwd"]
+    fwd_render_ms = stage_ms.get("render_fwd") or fwd_stage_ms
+    if fused and have_bwd:
+        stage_ms["render_fwd"] = fwd_stage_ms
 
     # end to end through the C ABI with host buffers: every step copies its
     # Gaussians from pinned host memory and reads its image back into pinned host
@@ -499,10 +516,10 @@ def run(args):
             gk = gbuf[b]
             ws.preprocess(gk)
             ws.bin_sort(sync=False)
-            ws.render_fwd(rgb_buf[b])
             if have_bwd:
-                geer.l1_loss_grad(rgb_buf[b], target_step, dL)
-                backward(gk)
+                render_step(gk, rgb_buf[b])
+            else:
+                ws.render_fwd(rgb_buf[b])
             comp_done[b].record(stream)
             down_s.wait_event(comp_done[b])
             with torch.cuda.stream(down_s):
@@ -589,6 +606,8 @@ def run(args):
         "tile_sort": ("hbm", sort_passes * 20 * int(super_pairs) + 32 * int(super_pairs)),
         "render_fwd": ("alu", FLOPS_FWD_EVAL * evals),
         "render_bwd": ("alu", FLOPS_BWD_EVAL * walked),
+        # the fused render: the forward's evaluations and the backward's walked entries
+        "render_train": ("alu", FLOPS_FWD_EVAL * evals + FLOPS_BWD_EVAL * walked),
         # the step writes its gradients: parameters and accumulators read, gradients written
         "preprocess_bwd": ("hbm", scene.n * g_bytes * 2 + n_items * 64),
     }
@@ -605,7 +624,8 @@ def run(args):
             ach = amount / (t / 1e3) / 1e12
             stages[name] = {"ms": t, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                             "frac": ach / fp32_peak, "algorithmic_flops": amount}
-    kernel_of = {"render_fwd": "k_render_fwd", "render_bwd": "k_render_bwd", "preprocess": "k_preprocess",
+    kernel_of = {"render_fwd": "k_render_fwd", "render_bwd": "k_render_bwd", "render_train": "k_render_train",
+                 "preprocess": "k_preprocess",
                  "preprocess_bwd": "k_preprocess_bwd", "duplicate": "k_duplicate"}
     single = {k: v for k, v in stages.items() if k in kernel_of}
     dom = max(single, key=lambda k: single[k]["ms"])
@@ -634,9 +654,13 @@ def run(args):
         ga = adam.gaussians
         ws.preprocess(ga)
         ws.bin_sort(sync=False)
-        ws.render_fwd(rgb)
-        geer.l1_loss_grad(rgb, target, dL)
-        ws.render_bwd(ga, dL, tgrads, accumulate=False)
+        if fused:
+            ws.render_train_l1(target, rgb, dL)
+            ws.preprocess_bwd(ga, tgrads, accumulate=False)
+        else:
+            ws.render_fwd(rgb)
+            geer.l1_loss_grad(rgb, target, dL)
+            ws.render_bwd(ga, dL, tgrads, accumulate=False)
         ev[1].record(stream)
         adam.step(tgrads)
         ev[2].record(stream)
@@ -702,7 +726,7 @@ def run(args):
     # preprocess, live scan, compact, 4 depth passes x 2, gather, pair scan, emit, offsets,
     # super-tile sort passes x 2, render forward (+ L1 gradient, backward order, render backward,
     # preprocess backward): 22 per training step with one super-tile pass, as the ncu launch list shows
-    launches_per_step = 16 + 2 * sort_passes + (4 if have_bwd else 0)
+    launches_per_step = 16 + 2 * sort_passes + ((1 if fused else 4) if have_bwd else 0)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
@@ -766,6 +790,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fwd-only", action="store_true", help="time the forward render only")
+    ap.add_argument("--separate-render", action="store_true",
+                    help="the training step's render as three calls (forward, L1 gradient, backward) "
+                         "instead of the fused launch")
     ap.add_argument("--no-ablation", action="store_true", help="skip the association ablation")
     ap.add_argument("--serving-seconds", type=float, default=8.0, help="serving trace length (0: skip)")
     ap.add_argument("--serving-warmup", type=float, default=1.0)

@@ -40,7 +40,7 @@ typedef enum {
     GEER_ERR_ARG = 1,         /* invalid argument (null, negative size, bad camera, ...) */
     GEER_ERR_CAPACITY = 2,    /* more (tile, Gaussian) pairs than the workspace holds */
     GEER_ERR_CUDA = 3,        /* a CUDA runtime call failed */
-    GEER_ERR_TIMEOUT = 4,     /* reserved: the library has no device-side waits */
+    GEER_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (geer_render_train_l1's unit queue) */
     GEER_ERR_UNSUPPORTED = 5, /* a valid request the library does not implement */
     GEER_ERR_STATE = 6,       /* call out of order (e.g. render before bin_sort) */
     GEER_ERR_BOUNDS = 7       /* checked build: a device bounds guard skipped an access */
@@ -232,6 +232,30 @@ geer_status geer_render_bwd(geer_workspace *ws, const geer_gaussians *g, const f
  * GEER_ERR_STATE before a geer_render_fwd. Asynchronous on `stream`. */
 geer_status geer_render_bwd_tiles(geer_workspace *ws, const float *dL_drgb, void *stream);
 
+/* A training step's render with the L1 loss in one launch: geer_render_fwd,
+ * geer_l1_loss_grad(rgb, target) and geer_render_bwd_tiles fused (App. C's
+ * RenderCUDA backward needs, per ray, only its own pixel's dL/drgb, and the L1
+ * gradient sign(rgb - target) / n of a pixel only that pixel). Persistent
+ * blocks render the tiles in the render order; a finished tile publishes its
+ * backward units in a device queue, and once every tile is taken the blocks
+ * walk the published units back, waiting (a bounded poll) for the tiles still
+ * rendering, so the backward of the finished tiles fills the SMs that the
+ * heaviest tiles' walks leave idle.
+ * Outputs as the three calls: rgb and T_final (NULL to skip) as
+ * geer_render_fwd, dL_drgb [sum h*w][3] f32 the L1 gradient (n = 3 x pixels
+ * values), *loss (device f32, NULL to skip) the mean absolute difference
+ * (summed in another order than geer_l1_loss_grad: equal to rounding), and the
+ * render-stage accumulators of geer_render_bwd_tiles (equal up to the order of
+ * FP32 atomic additions); then geer_preprocess_bwd. target: device, rgb's
+ * layout. A tile mask (geer_set_tile_mask) applies as in geer_render_fwd: a
+ * caller that splits tiles passes a target that is zero on the other parts'
+ * pixels. GEER_ERR_STATE before geer_bin_sort; GEER_ERR_UNSUPPORTED on a
+ * forward-only workspace. A queue wait that gave up (it cannot happen while
+ * the device makes progress) is reported by geer_last_device_status as
+ * GEER_ERR_TIMEOUT. Asynchronous on `stream`. */
+geer_status geer_render_train_l1(geer_workspace *ws, const float *target, float *rgb, float *T_final,
+                                 float *dL_drgb, float *loss, void *stream);
+
 /* Device address and size (in f32) of the accumulators geer_render_bwd_tiles
  * writes: [n_cams * n][16] f32 inside the workspace memory, n the Gaussian
  * count of the last geer_preprocess. The caller may read and overwrite them
@@ -366,7 +390,7 @@ geer_status geer_render_counts(geer_workspace *ws, uint64_t *evaluated, uint64_t
  * preprocess, bin_front, depth_sort, count_pairs, duplicate, tile_sort,
  * render_fwd, render_bwd, preprocess_bwd), keeping the most recent 64 per
  * stage. geer_stage_times synchronises `stream` and writes the mean duration in
- * ms of the recorded occurrences of each stage into ms[0..8] (n >= 9) and
+ * ms of the recorded occurrences of each stage into ms[0..9] (n >= 10) and
  * their number into counts (may be NULL). Do not enable it while capturing a
  * CUDA graph. */
 geer_status geer_enable_timing(geer_workspace *ws, int32_t enable);

@@ -535,6 +535,7 @@ geer_status geer_workspace_init(void *dev_mem, size_t bytes, const geer_camera *
     if (e != cudaSuccess) { free(ws); return GEER_ERR_CUDA; }
     ws->sort_grid = ws->num_sms * sort_blocks_per_sm();
     ws->bwd_grid = ws->num_sms * render_bwd_blocks_per_sm(ws->params.alpha_model);
+    ws->train_grid = ws->num_sms * render_train_blocks_per_sm(ws->params.alpha_model);
     ws->stage_bytes = sizeof(DevCam) * c.cams + sizeof(float4) * c.tile_tab + sizeof(float2) * c.pix_tab;
     if (cudaMallocHost(&ws->h_stage, ws->stage_bytes) != cudaSuccess) { free(ws); return GEER_ERR_CUDA; }
     // status words and radix group sums start from zero
@@ -692,6 +693,27 @@ geer_status geer_render_bwd_tiles(geer_workspace *ws, const float *dL_drgb, void
     return GEER_OK;
 }
 
+geer_status geer_render_train_l1(geer_workspace *ws, const float *target, float *rgb, float *T_final,
+                                 float *dL_drgb, float *loss, void *stream) {
+    if (!ws || !target || !rgb || !dL_drgb) return GEER_ERR_ARG;
+    if (ws->stage < 2) return GEER_ERR_STATE;
+    if (ws->hit_entries == 0) return GEER_ERR_UNSUPPORTED;  // a forward-only workspace has no backward state
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
+    if ((items > 0 && cudaMemsetAsync(ws->d_gacc, 0, sizeof(GradAcc) * items, s) != cudaSuccess) ||
+        (loss && cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) ||
+        cudaMemsetAsync(ws->d_bwd_order, 0xff, sizeof(uint32_t) * ws->n_tiles * (kCkptMax + 1), s) != cudaSuccess ||
+        cudaMemsetAsync(ws->d_misc + kMiscFwdNext, 0, sizeof(uint32_t) * (kMiscTrainNext - kMiscFwdNext + 1), s) !=
+            cudaSuccess)
+        return GEER_ERR_CUDA;
+    {
+        StageTimer tm(ws, kStageRenderTrain, s);
+        if (launch_render_train(ws, target, rgb, T_final, dL_drgb, loss, s) != cudaSuccess) return GEER_ERR_CUDA;
+    }
+    ws->stage = 4;
+    return GEER_OK;
+}
+
 geer_status geer_grad_accumulators(geer_workspace *ws, float **acc, int64_t *n_floats) {
     if (!ws || !acc || !n_floats) return GEER_ERR_ARG;
     *acc = reinterpret_cast<float *>(ws->d_gacc);
@@ -757,6 +779,7 @@ geer_status geer_last_device_status(geer_workspace *ws, int64_t *pairs, void *st
     }
     if (m[kMiscStatus] & kStatusCapacity) return GEER_ERR_CAPACITY;
     if (m[kMiscStatus] & kStatusBounds) return GEER_ERR_BOUNDS;
+    if (m[kMiscStatus] & kStatusTimeout) return GEER_ERR_TIMEOUT;
     return GEER_OK;
 }
 
@@ -1116,7 +1139,8 @@ geer_status geer_image_metrics(const float *pred, const float *gt, int32_t width
 }
 
 static const char *kStageNames[kStageCount] = {"preprocess", "bin_front", "depth_sort", "count_pairs", "duplicate",
-                                               "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd"};
+                                               "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd",
+                                               "render_train"};
 
 const char *geer_stage_name(int32_t stage) {
     return (stage >= 0 && stage < kStageCount) ? kStageNames[stage] : "unknown";

@@ -33,7 +33,7 @@ constexpr int kSmemTiles = 12288;          // per-block tile histogram in shared
 constexpr uint32_t kStatusCapacity = 1u;
 constexpr uint32_t kStatusListOverflow = 2u;  // inspection: a tile list differs from its counted length
 constexpr uint32_t kStatusBounds = 4u;        // GEER_CHECKED build: a bounds guard skipped an access
-constexpr uint32_t kStatusTimeout = 8u;       // a bounded wait on a shared-memory barrier gave up
+constexpr uint32_t kStatusTimeout = 8u;       // a bounded wait (a shared-memory barrier, the fused render's unit queue) gave up
 
 // Indices into the misc u32 array of the workspace.
 enum Misc : int {
@@ -52,6 +52,10 @@ enum Misc : int {
     kMiscUnits = 13,      // backward units of the last geer_render_bwd_tiles (tile walks split at checkpoints)
     kMiscUnitNext = 14,   // the next backward unit to take (persistent blocks)
     kMiscSortCur = 15,    // depth sort: the buffer the current pass reads (set by its histogram kernel)
+    kMiscFwdNext = 16,    // fused render: the next forward tile (of the render order) to take
+    kMiscFwdDone = 17,    // fused render: forward tiles finished, their units published
+    kMiscUnitsPub = 18,   // fused render: backward units published (slots reserved in the unit queue)
+    kMiscTrainNext = 19,  // fused render: the next queue slot a block takes
     kMiscCount = 32
 };
 
@@ -264,6 +268,7 @@ enum Stage : int {
     kStageRenderFwd,
     kStageRenderBwd,
     kStagePreprocessBwd,
+    kStageRenderTrain,   // the fused forward + L1 + render-stage backward
     kStageCount
 };
 constexpr int kTimingRing = 64;
@@ -317,6 +322,7 @@ struct geer_workspace {
     uint4 *d_unit_rec;      // [cap_tiles] the tile's backward units: their schedule buckets and count
     float4 *d_Cfin;         // [cap_pixels] composited colour before the background (tiles with checkpoints)
     int bwd_grid;           // persistent backward blocks
+    int train_grid;         // persistent blocks of the fused forward + L1 + backward render
     uint4 *d_sranges;       // [cap_pairs] association ranges of the sorted pairs' items (in list order)
     uint2 *d_srange;        // [cap_tiles] super-tile [start, end) in the sorted pairs, followed by [cap_tiles] u32 counts
     uint32_t *d_last;       // [cap_pixels] list entries walked per ray
@@ -362,6 +368,8 @@ cudaError_t launch_expand_tiles(const geer_workspace *ws, uint32_t *counts_or_of
 cudaError_t launch_tile_sort(geer_workspace *ws, cudaStream_t s);
 cudaError_t launch_render_fwd(const geer_workspace *ws, float *rgb, float *T_final, cudaStream_t s);
 cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cudaStream_t s);
+cudaError_t launch_render_train(const geer_workspace *ws, const float *target, float *rgb, float *T_final,
+                                float *dL_drgb, float *loss, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const geer_workspace *ws, const geer_gaussians *g, float *d_mean, float *d_scale,
                                   float *d_quat, float *d_opacity, float *d_sh, int accumulate, cudaStream_t s);
 cudaError_t launch_l1_grad(const float *pred, const float *target, int64_t m, float *grad, float *loss, int num_sms,
@@ -392,6 +400,7 @@ cudaError_t launch_image_metrics(const float *pred, const float *gt, int width, 
                                  int n_regions, double *acc, cudaStream_t s);
 int sort_blocks_per_sm();
 int render_bwd_blocks_per_sm(int alpha_model);
+int render_train_blocks_per_sm(int alpha_model);
 
 inline int64_t prep_blocks(int64_t n) { return (n + kPrepThreads - 1) / kPrepThreads; }
 

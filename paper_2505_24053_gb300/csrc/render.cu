@@ -51,6 +51,14 @@ constexpr int kScan = GEER_SCAN;  // super-list loads in flight per thread in a 
 #endif
 constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -log2(e) / 2
 
+// A load of data written earlier in the same launch (CG: through L2, never a
+// stale L1 line) or an ordinary one.
+template <bool CG, typename T>
+__device__ __forceinline__ T ld_cg(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 __device__ __forceinline__ int find_cam(const DevCam *cams, int ncams, int t) {
     int c = 0;
     for (int i = 1; i < ncams; ++i)
@@ -519,6 +527,144 @@ __device__ __forceinline__ bool tile_ray(const DevCam &cam, int t, int row0, con
     return true;
 }
 
+// The L1 loss at one pixel, as geer_l1_loss_grad computes it over the n = 3 x
+// pixels values (the mean absolute difference): dL/dC = sign(C - target) / n
+// into dL, |C - target| added to acc.
+__device__ __forceinline__ void l1_pixel(float c0, float c1, float c2, const float *__restrict__ target,
+                                         float *__restrict__ dL, int64_t pix, float inv_m, float &acc) {
+    const float c[3] = {c0, c1, c2};
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float d = c[ch] - target[3 * pix + ch];
+        dL[3 * pix + ch] = d > 0.0f ? inv_m : (d < 0.0f ? -inv_m : 0.0f);
+        acc += fabsf(d);
+    }
+}
+
+// One tile of the forward (the body of k_render_fwd): the tile's rays walk its
+// list and write their colour, transmittance, last contributor and counts, the
+// hit and list records, the checkpoints and the backward's unit record. With
+// L1, each pixel's L1 gradient against target too (dL; |differences| summed
+// into l1acc). Returns the tile's backward unit count in thread 0.
+template <int ROWS, int BATCH, bool SPLAT, bool L1>
+__device__ __forceinline__ uint32_t fwd_tile(WalkSmem<ROWS * kTile, BATCH> &sm, uint32_t t_id,
+                                         const DevCam *__restrict__ cams,
+                                         int ncams,
+                                         const float2 *__restrict__ ptab,
+                                         const float4 *__restrict__ ttab,
+                                         int S,
+                                         uint2 *__restrict__ tile_walk,
+                                         const uint2 *__restrict__ srange,
+                                         const uint32_t *__restrict__ svals,
+                                         const uint4 *__restrict__ sranges,
+                                         const Record *__restrict__ rec,
+                                         uint32_t *__restrict__ misc,
+                                         Params p,
+                                         float *__restrict__ rgb,
+                                         float *__restrict__ Tout,
+                                         float *__restrict__ Tfin,
+                                         uint32_t *__restrict__ last_out,
+                                         uint2 *__restrict__ evals,
+                                         uint2 *__restrict__ hit,
+                                         uint32_t *__restrict__ idrec,
+                                         int64_t hit_entries,
+                                         const uint8_t *__restrict__ tile_mask,
+                                         int64_t ntiles,
+                                         uint64_t items,
+                                         int64_t cap_pairs,
+                                         float4 *__restrict__ ckpt,
+                                         uint2 *__restrict__ ckpt_at,
+                                         uint32_t *__restrict__ ckpt_cnt,
+                                         uint4 *__restrict__ unit_rec,
+                                         float4 *__restrict__ Cfin,
+                                         const float *__restrict__ target, float *__restrict__ dL, float inv_m,
+                                         float &l1acc) {
+    constexpr int kThreads = ROWS * kTile;
+    if (!in_bounds(t_id, (uint64_t)ntiles, kSiteFwdTile, misc)) return 0u;  // block-uniform
+    const int t = (int)t_id;
+    if (threadIdx.x == 0) sm.cam = find_cam(cams, ncams, t);
+    __syncthreads();
+    const DevCam &cam = cams[sm.cam];
+    TileRay tr;
+    if (!tile_ray(cam, t, 0, ptab, ttab, srange, S, tr, (int)threadIdx.x)) {
+        if (threadIdx.x == 0) {
+            tile_walk[t] = make_uint2(0u, 0u);
+            if (ckpt_cnt) ckpt_cnt[t] = 0u;
+            if (unit_rec) unit_rec[t] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        return 0u;
+    }
+    tr.sr = checked_range(tr.sr, cap_pairs, kSiteFwdList, misc);
+    if (tile_mask && !tile_mask[t]) {  // another part's tile: zeros, nothing for the backward to walk
+        if (threadIdx.x == 0) {
+            tile_walk[t] = make_uint2(0u, 0u);
+            if (ckpt_cnt) ckpt_cnt[t] = 0u;
+            if (unit_rec) unit_rec[t] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (tr.inside) {
+            const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
+            rgb[3 * pix + 0] = 0.0f;
+            rgb[3 * pix + 1] = 0.0f;
+            rgb[3 * pix + 2] = 0.0f;
+            if (Tout) Tout[pix] = 0.0f;
+            Tfin[pix] = 0.0f;
+            last_out[pix] = 0u;
+            evals[pix] = make_uint2(0u, 0u);
+            if (L1) l1_pixel(0.0f, 0.0f, 0.0f, target, dL, pix, inv_m, l1acc);
+        }
+        return 0u;
+    }
+    FwdRay f{1.0f, 0.0f, 0.0f, 0.0f, 0u, 0u, 0u, !tr.inside};
+    if (SPLAT) {  // the ray's screen angles
+        const float ts = atan2f(tr.dx, tr.dz), ps = atan2f(tr.dy, tr.dz);
+        tr.dx = ts;
+        tr.dy = ps;
+    }
+    forward_walk<kThreads, BATCH, SPLAT>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy,
+                                         tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr,
+                                         hit ? idrec + (int64_t)t * hit_entries : nullptr, hit_entries, items,
+                                         misc, ckpt ? ckpt + (size_t)t * kCkptMax * kTilePix : nullptr,
+                                         ckpt ? ckpt_at + (size_t)t * kCkptMax : nullptr,
+                                         f);
+    if (threadIdx.x == 0) {
+        tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
+        if (ckpt_cnt) ckpt_cnt[t] = sm.nck;
+    }
+    if (tr.inside) {
+        const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
+        const float c0 = fmaf(f.T, cam.bg[0], f.cr), c1 = fmaf(f.T, cam.bg[1], f.cg), c2 = fmaf(f.T, cam.bg[2], f.cb);
+        rgb[3 * pix + 0] = c0;
+        rgb[3 * pix + 1] = c1;
+        rgb[3 * pix + 2] = c2;
+        if (Tout) Tout[pix] = f.T;
+        Tfin[pix] = f.T;
+        last_out[pix] = f.last;
+        evals[pix] = make_uint2(f.n_eval, f.n_applied);
+        if (Cfin && sm.nck) Cfin[pix] = make_float4(f.cr, f.cg, f.cb, f.T);  // the backward's colour behind
+        if (L1) l1_pixel(c0, c1, c2, target, dL, pix, inv_m, l1acc);
+    }
+    // the backward's units: the checkpoints inside the walk [0, W) split it; thread k
+    // writes unit k's schedule bucket (from the steps counted in it), thread
+    // kUnitCountByte the number of units
+    // (returns the number of units in thread 0)
+    uint32_t units = 0;
+    if (unit_rec && ((int)threadIdx.x <= kCkptMax || threadIdx.x == kUnitCountByte)) {
+        const uint32_t W = sm.maxlast, nk = W > kCkptFirst ? min(sm.nck, (uint32_t)kCkptMax) : 0u;
+        uint32_t m = 0;
+        for (uint32_t j = 0; j < nk; ++j) m += sm.ckB[j] < W ? 1u : 0u;
+        units = W > 0 ? m + 1u : 0u;
+        const uint32_t k = threadIdx.x;
+        uint8_t *rb = reinterpret_cast<uint8_t *>(unit_rec + t);
+        if (k == (uint32_t)kUnitCountByte) {
+            rb[k] = (uint8_t)units;
+        } else if (k < units) {
+            const uint32_t wlo = k == 0 ? 0u : sm.ckw[k - 1], whi = k < m ? sm.ckw[k] : sm.work;
+            rb[k] = (uint8_t)order_bucket(max(whi - wlo, 1u));
+        }
+    }
+    return units;
+}
+
 template <int ROWS, int BATCH, bool SPLAT>
 __global__ void __launch_bounds__(ROWS * kTile, GEER_FWD_MINB) k_render_fwd(const DevCam *__restrict__ cams, int ncams,
                                                             const float2 *__restrict__ ptab,
@@ -546,83 +692,9 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_FWD_MINB) k_render_fwd(cons
     static_assert(kParts == 1, "one block per tile: the block records the tile's walk");
     __shared__ WalkSmem<kThreads, BATCH> sm;
     if (misc[kMiscStatus] & kStatusCapacity) return;
-    const uint32_t t_id = tile_order[blockIdx.x];
-    if (!in_bounds(t_id, (uint64_t)ntiles, kSiteFwdTile, misc)) return;  // block-uniform
-    const int t = (int)t_id;
-    if (threadIdx.x == 0) sm.cam = find_cam(cams, ncams, t);
-    __syncthreads();
-    const DevCam &cam = cams[sm.cam];
-    TileRay tr;
-    if (!tile_ray(cam, t, 0, ptab, ttab, srange, S, tr, (int)threadIdx.x)) {
-        if (threadIdx.x == 0) {
-            tile_walk[t] = make_uint2(0u, 0u);
-            if (ckpt_cnt) ckpt_cnt[t] = 0u;
-            if (unit_rec) unit_rec[t] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        return;
-    }
-    tr.sr = checked_range(tr.sr, cap_pairs, kSiteFwdList, misc);
-    if (tile_mask && !tile_mask[t]) {  // another part's tile: zeros, nothing for the backward to walk
-        if (threadIdx.x == 0) {
-            tile_walk[t] = make_uint2(0u, 0u);
-            if (ckpt_cnt) ckpt_cnt[t] = 0u;
-            if (unit_rec) unit_rec[t] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        if (tr.inside) {
-            const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
-            rgb[3 * pix + 0] = 0.0f;
-            rgb[3 * pix + 1] = 0.0f;
-            rgb[3 * pix + 2] = 0.0f;
-            if (Tout) Tout[pix] = 0.0f;
-            Tfin[pix] = 0.0f;
-            last_out[pix] = 0u;
-            evals[pix] = make_uint2(0u, 0u);
-        }
-        return;
-    }
-    FwdRay f{1.0f, 0.0f, 0.0f, 0.0f, 0u, 0u, 0u, !tr.inside};
-    if (SPLAT) {  // the ray's screen angles
-        const float ts = atan2f(tr.dx, tr.dz), ps = atan2f(tr.dy, tr.dz);
-        tr.dx = ts;
-        tr.dy = ps;
-    }
-    forward_walk<kThreads, BATCH, SPLAT>(sm, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, tr.sr, tr.dx, tr.dy,
-                                         tr.dz, hit ? hit + (int64_t)t * hit_entries : nullptr,
-                                         hit ? idrec + (int64_t)t * hit_entries : nullptr, hit_entries, items,
-                                         misc, ckpt ? ckpt + (size_t)t * kCkptMax * kTilePix : nullptr,
-                                         ckpt ? ckpt_at + (size_t)t * kCkptMax : nullptr,
-                                         f);
-    if (threadIdx.x == 0) {
-        tile_walk[t] = make_uint2(sm.walkpos, sm.maxlast);
-        if (ckpt_cnt) ckpt_cnt[t] = sm.nck;
-    }
-    if (tr.inside) {
-        const int64_t pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
-        rgb[3 * pix + 0] = fmaf(f.T, cam.bg[0], f.cr);
-        rgb[3 * pix + 1] = fmaf(f.T, cam.bg[1], f.cg);
-        rgb[3 * pix + 2] = fmaf(f.T, cam.bg[2], f.cb);
-        if (Tout) Tout[pix] = f.T;
-        Tfin[pix] = f.T;
-        last_out[pix] = f.last;
-        evals[pix] = make_uint2(f.n_eval, f.n_applied);
-        if (Cfin && sm.nck) Cfin[pix] = make_float4(f.cr, f.cg, f.cb, f.T);  // the backward's colour behind
-    }
-    // the backward's units: the checkpoints inside the walk [0, W) split it; thread k
-    // writes unit k's schedule bucket (from the steps counted in it), thread
-    // kUnitCountByte the number of units
-    if (unit_rec && ((int)threadIdx.x <= kCkptMax || threadIdx.x == kUnitCountByte)) {
-        const uint32_t W = sm.maxlast, nk = W > kCkptFirst ? min(sm.nck, (uint32_t)kCkptMax) : 0u;
-        uint32_t m = 0;
-        for (uint32_t j = 0; j < nk; ++j) m += sm.ckB[j] < W ? 1u : 0u;
-        const uint32_t units = W > 0 ? m + 1u : 0u, k = threadIdx.x;
-        uint8_t *rb = reinterpret_cast<uint8_t *>(unit_rec + t);
-        if (k == (uint32_t)kUnitCountByte) {
-            rb[k] = (uint8_t)units;
-        } else if (k < units) {
-            const uint32_t wlo = k == 0 ? 0u : sm.ckw[k - 1], whi = k < m ? sm.ckw[k] : sm.work;
-            rb[k] = (uint8_t)order_bucket(max(whi - wlo, 1u));
-        }
-    }
+    float l1acc = 0.0f;
+    fwd_tile<ROWS, BATCH, SPLAT, false>(sm, tile_order[blockIdx.x], cams, ncams, ptab, ttab, S, tile_walk, srange, svals, sranges, rec, misc, p, rgb, Tout, Tfin, last_out, evals, hit, idrec, hit_entries, tile_mask, ntiles, items, cap_pairs, ckpt, ckpt_at, ckpt_cnt, unit_rec, Cfin, nullptr, nullptr, 0.0f,
+                                        l1acc);
 }
 
 // Every tile's full list (no early termination), filtered from its super-tile's
@@ -750,7 +822,7 @@ __device__ __forceinline__ void ray_gradient(BwdRay &r, const float4 &a, const f
 // A backward unit's walk: tile-list entries [lo, walk.y) read back to front,
 // filtered as in the forward from super-list positions [plo, walk.x) (walk.x:
 // just past entry walk.y - 1; plo: where entry lo's search starts).
-template <int kThreads, int BATCH, bool SPLAT>
+template <int kThreads, int BATCH, bool SPLAT, bool CG>
 __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, float (*s_acc)[17],
                                               const uint32_t *__restrict__ svals,
                                               const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
@@ -783,13 +855,13 @@ __device__ __forceinline__ void backward_walk(WalkSmem<kThreads, BATCH> &sm, flo
             const uint32_t j = top - 1u - (uint32_t)r;
             uint32_t id;
             if (direct) {
-                id = id_rec[j];
+                id = ld_cg<CG>(id_rec + j);
                 sm.id[r] = id;
             } else {
                 id = sm.id[r];
             }
             // beyond the recorded entries every warp evaluates
-            const uint2 h = hit_rec && (int64_t)j < hit_entries ? hit_rec[j] : make_uint2(~0u, ~0u);
+            const uint2 h = hit_rec && (int64_t)j < hit_entries ? ld_cg<CG>(hit_rec + j) : make_uint2(~0u, ~0u);
             // an entry no warp hit is never read: its record is not staged
             if (h.x | h.y) stage_record(sm.rec + r * 4, rec, id, items, kSiteBwdItem, misc);
             // transposed to warp-major order: warp w's flags of the batch are contiguous
@@ -902,6 +974,109 @@ __device__ __forceinline__ BwdRay bwd_ray(const TileRay &tr, const DevCam &cam, 
 // tile's long walk runs on several SMs at once and its transmittance is
 // recovered by division over one unit at most. Persistent blocks take units
 // in the order of k_bwd_order (descending length) from a counter.
+// One backward unit (the body of k_render_bwd's loop): unit code = tile << 4 | k,
+// row part `part` of the tile's rays. CG: read what the forward wrote through
+// L2 (the fused kernel reads it in the launch that wrote it).
+template <int ROWS, int BATCH, bool SPLAT, bool CG>
+__device__ __forceinline__ void bwd_unit(WalkSmem<ROWS * kTile, BATCH> &sm, float (*s_acc)[17], uint32_t code,
+                                         int part,
+                                         const DevCam *__restrict__ cams,
+                                         int ncams,
+                                         const float2 *__restrict__ ptab,
+                                         const float4 *__restrict__ ttab,
+                                         int S,
+                                         const uint2 *__restrict__ tile_walk,
+                                         const uint2 *__restrict__ srange,
+                                         const uint32_t *__restrict__ svals,
+                                         const uint4 *__restrict__ sranges,
+                                         const Record *__restrict__ rec,
+                                         uint32_t *__restrict__ misc,
+                                         Params p,
+                                         const float *__restrict__ dL_drgb,
+                                         const float *__restrict__ Tfin,
+                                         const uint32_t *__restrict__ last_in,
+                                         const uint2 *__restrict__ hit,
+                                         const uint32_t *__restrict__ idrec,
+                                         int64_t hit_entries,
+                                         GradAcc *__restrict__ gacc,
+                                         int64_t ntiles,
+                                         uint64_t items,
+                                         int64_t cap_pairs,
+                                         const float4 *__restrict__ ckpt,
+                                         const uint2 *__restrict__ ckpt_at,
+                                         const uint32_t *__restrict__ ckpt_cnt,
+                                         const float4 *__restrict__ Cfin) {
+    constexpr int kThreads = ROWS * kTile;
+    const int tray = part * kThreads + (int)threadIdx.x;  // the ray's index in the tile
+    const uint32_t t_id = code >> 4, k = code & 15u;
+    if (!in_bounds(t_id, (uint64_t)ntiles, kSiteBwdTile, misc)) return;  // block-uniform
+    const int t = (int)t_id;
+    if (threadIdx.x == 0) sm.cam = find_cam(cams, ncams, t);
+    __syncthreads();
+    const DevCam &cam = cams[sm.cam];
+    TileRay tr;
+    if (!tile_ray(cam, t, part * ROWS, ptab, ttab, srange, S, tr, (int)threadIdx.x)) return;
+    tr.sr = checked_range(tr.sr, cap_pairs, kSiteBwdList, misc);
+    uint2 walk = ld_cg<CG>(tile_walk + t);
+    if (!in_bounds(walk.x, (uint64_t)tr.sr.y + 1u, kSiteBwdList, misc)) walk = make_uint2(0u, 0u);
+    // the unit: tile-list entries [lo, hi), super-list positions [plo, phi)
+    uint32_t lo = 0u, plo = tr.sr.x, hi = walk.y, phi = walk.x;
+    bool top = true;
+    const uint32_t nck = ckpt_cnt ? min(ld_cg<CG>(ckpt_cnt + t), (uint32_t)kCkptMax) : 0u;
+    if (k > 0 && k <= nck) {
+        const uint2 a = ld_cg<CG>(ckpt_at + (size_t)t * kCkptMax + k - 1);
+        lo = a.x;
+        plo = a.y;
+    }
+    if (k < nck) {
+        const uint2 b = ld_cg<CG>(ckpt_at + (size_t)t * kCkptMax + k);
+        if (b.x < walk.y) {
+            hi = b.x;
+            phi = b.y;
+            top = false;
+        }
+    }
+    if (!in_bounds(phi, (uint64_t)walk.x + 1u, kSiteBwdList, misc) ||
+        !in_bounds(plo, (uint64_t)phi + 1u, kSiteBwdList, misc) || lo >= hi)
+        return;
+    float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, T = 1.0f;
+    uint32_t last = 0;
+    int64_t pix = 0;
+    if (tr.inside) {
+        pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
+        g0 = ld_cg<CG>(dL_drgb + 3 * pix + 0);
+        g1 = ld_cg<CG>(dL_drgb + 3 * pix + 1);
+        g2 = ld_cg<CG>(dL_drgb + 3 * pix + 2);
+        T = ld_cg<CG>(Tfin + pix);
+        last = ld_cg<CG>(last_in + pix);
+    }
+    if (SPLAT) {  // the ray's screen angles
+        const float ts = atan2f(tr.dx, tr.dz), ps = atan2f(tr.dy, tr.dz);
+        tr.dx = ts;
+        tr.dy = ps;
+    }
+    BwdRay ray = bwd_ray(tr, cam, g0, g1, g2, T, last);
+    if (!top && last > hi) {
+        // the ray walks past this unit: its state in front of entry hi is the forward's checkpoint
+        const float4 c = ld_cg<CG>(ckpt + ((size_t)t * kCkptMax + k) * kTilePix + tray);
+        const float4 cf = ld_cg<CG>(Cfin + pix);
+        ray.T = c.x;
+        const float S0 = fmaf(T, cam.bg[0], cf.x - c.y), S1 = fmaf(T, cam.bg[1], cf.y - c.z),
+                    S2 = fmaf(T, cam.bg[2], cf.z - c.w);
+        ray.gS = fmaf(g0, S0, fmaf(g1, S1, g2 * S2));
+    }
+    const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
+    if ((threadIdx.x & 31) == 0) atomicMax(&sm.maxlast, warp_last);
+    __syncthreads();
+    const uint32_t block_last = sm.maxlast;
+    if (block_last <= lo) return;
+    backward_walk<kThreads, BATCH, SPLAT, CG>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, plo, lo,
+                                          make_uint2(phi, hi), warp_last, block_last,
+                                          hit ? hit + (int64_t)t * hit_entries : nullptr,
+                                          hit ? idrec + (int64_t)t * hit_entries : nullptr, hit_entries,
+                                          tray >> 5, ray, gacc, items, misc);
+}
+
 template <int ROWS, int BATCH, bool SPLAT>
 __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(const DevCam *__restrict__ cams, int ncams,
                                                                            const float2 *__restrict__ ptab,
@@ -942,76 +1117,107 @@ __global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_bwd(cons
         __syncthreads();
         const uint32_t w = s_unit;
         if (w >= n_work) break;
-        const uint32_t code = units[w / kParts];
-        const int part = (int)(w % kParts);
-        const int tray = part * kThreads + (int)threadIdx.x;  // the ray's index in the tile
-        const uint32_t t_id = code >> 4, k = code & 15u;
-        if (!in_bounds(t_id, (uint64_t)ntiles, kSiteBwdTile, misc)) continue;  // block-uniform
-        const int t = (int)t_id;
-        if (threadIdx.x == 0) sm.cam = find_cam(cams, ncams, t);
+        bwd_unit<ROWS, BATCH, SPLAT, false>(sm, s_acc, units[w / kParts], (int)(w % kParts), cams, ncams, ptab, ttab, S, tile_walk, srange, svals, sranges, rec, misc, p, dL_drgb, Tfin, last_in, hit, idrec, hit_entries, gacc, ntiles, items, cap_pairs, ckpt, ckpt_at, ckpt_cnt, Cfin);
+    }
+}
+
+// Forward, L1 gradient and the render stage of the backward in one persistent
+// launch (a training step's render with the per-pixel L1 loss: a tile's
+// gradient needs only its own pixels, so its backward can start when its
+// forward ends). Blocks take forward tiles in the render order; a finished tile
+// publishes its backward units (tile << 4 | k) in a queue. Once every tile is
+// taken, blocks take queue slots in order and wait, bounded, for the units of
+// tiles still rendering: the backward of the finished tiles fills the SMs the
+// heaviest tiles' walks leave idle. A block waits only for work that a running
+// block holds. A unit's tile data, written in this launch, is read through L2
+// after the slot's acquire.
+constexpr uint32_t kQueueEmpty = 0xffffffffu;  // an unpublished queue slot (the host fills the queue with it)
+constexpr uint32_t kQueuePolls = 1u << 22;     // bound of a wait for a queue slot (<= ~1 us sleep between polls)
+
+template <int ROWS, int BATCH, bool SPLAT>
+__global__ void __launch_bounds__(ROWS * kTile, GEER_BWD_MINB) k_render_train(
+    const DevCam *__restrict__ cams, int ncams, const float2 *__restrict__ ptab, const float4 *__restrict__ ttab,
+    int S, uint2 *__restrict__ tile_walk, const uint32_t *__restrict__ tile_order, const uint2 *__restrict__ srange,
+    const uint32_t *__restrict__ svals, const uint4 *__restrict__ sranges, const Record *__restrict__ rec,
+    uint32_t *__restrict__ misc, Params p, float *__restrict__ rgb, float *__restrict__ Tout,
+    float *__restrict__ Tfin, uint32_t *__restrict__ last, uint2 *__restrict__ evals, uint2 *__restrict__ hit,
+    uint32_t *__restrict__ idrec, int64_t hit_entries, const uint8_t *__restrict__ tile_mask, int64_t ntiles,
+    uint64_t items, int64_t cap_pairs, float4 *__restrict__ ckpt, uint2 *__restrict__ ckpt_at,
+    uint32_t *__restrict__ ckpt_cnt, uint4 *__restrict__ unit_rec, float4 *__restrict__ Cfin,
+    const float *__restrict__ target, float *__restrict__ dL, float inv_m, float *__restrict__ loss,
+    GradAcc *__restrict__ gacc, uint32_t *__restrict__ queue, uint32_t queue_cap) {
+    grid_dep_sync();
+    constexpr int kThreads = ROWS * kTile;
+    static_assert(ROWS == kTile, "one block per tile and per unit");
+    __shared__ WalkSmem<kThreads, BATCH> sm;
+    __shared__ float s_acc[BATCH][17];
+    __shared__ uint32_t s_work;
+    __shared__ float s_loss;
+    if (misc[kMiscStatus] & kStatusCapacity) return;
+    float l1acc = 0.0f;
+    if (threadIdx.x == 0) s_loss = 0.0f;
+    while (true) {  // forward tiles
+        __syncthreads();  // the previous tile's shared state has been read
+        if (threadIdx.x == 0) s_work = atomicAdd(&misc[kMiscFwdNext], 1u);
         __syncthreads();
-        const DevCam &cam = cams[sm.cam];
-        TileRay tr;
-        if (!tile_ray(cam, t, part * ROWS, ptab, ttab, srange, S, tr, (int)threadIdx.x)) continue;
-        tr.sr = checked_range(tr.sr, cap_pairs, kSiteBwdList, misc);
-        uint2 walk = tile_walk[t];
-        if (!in_bounds(walk.x, (uint64_t)tr.sr.y + 1u, kSiteBwdList, misc)) walk = make_uint2(0u, 0u);
-        // the unit: tile-list entries [lo, hi), super-list positions [plo, phi)
-        uint32_t lo = 0u, plo = tr.sr.x, hi = walk.y, phi = walk.x;
-        bool top = true;
-        const uint32_t nck = ckpt_cnt ? min(ckpt_cnt[t], (uint32_t)kCkptMax) : 0u;
-        if (k > 0 && k <= nck) {
-            const uint2 a = ckpt_at[(size_t)t * kCkptMax + k - 1];
-            lo = a.x;
-            plo = a.y;
-        }
-        if (k < nck) {
-            const uint2 b = ckpt_at[(size_t)t * kCkptMax + k];
-            if (b.x < walk.y) {
-                hi = b.x;
-                phi = b.y;
-                top = false;
+        const uint32_t f = s_work;
+        if (f >= (uint32_t)ntiles) break;
+        const uint32_t t = tile_order[f];
+        const uint32_t nu = fwd_tile<ROWS, BATCH, SPLAT, true>(
+            sm, t, cams, ncams, ptab, ttab, S, tile_walk, srange, svals, sranges, rec, misc, p, rgb, Tout, Tfin, last,
+            evals, hit, idrec, hit_entries, tile_mask, ntiles, items, cap_pairs, ckpt, ckpt_at, ckpt_cnt, unit_rec,
+            Cfin, target, dL, inv_m, l1acc);
+        __syncthreads();  // every thread's outputs of the tile are written
+        if (threadIdx.x == 0) {
+            __threadfence();  // release: the tile's outputs before its units
+            if (nu) {
+                const uint32_t slot = atomicAdd(&misc[kMiscUnitsPub], nu);
+                for (uint32_t k = 0; k < nu; ++k)
+                    if (slot + k < queue_cap) atomicExch(&queue[slot + k], (t << 4) | k);
             }
+            __threadfence();
+            atomicAdd(&misc[kMiscFwdDone], 1u);
         }
-        if (!in_bounds(phi, (uint64_t)walk.x + 1u, kSiteBwdList, misc) ||
-            !in_bounds(plo, (uint64_t)phi + 1u, kSiteBwdList, misc) || lo >= hi)
-            continue;
-        float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, T = 1.0f;
-        uint32_t last = 0;
-        int64_t pix = 0;
-        if (tr.inside) {
-            pix = cam.pix_base + (int64_t)tr.y * cam.width + tr.x;
-            g0 = dL_drgb[3 * pix + 0];
-            g1 = dL_drgb[3 * pix + 1];
-            g2 = dL_drgb[3 * pix + 2];
-            T = Tfin[pix];
-            last = last_in[pix];
+    }
+    // the L1 loss: one atomic per block
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l1acc += __shfl_xor_sync(0xffffffffu, l1acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_loss, l1acc);
+    __syncthreads();
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, s_loss * inv_m);
+    while (true) {  // backward units, in the order they were published
+        __syncthreads();  // the previous unit's shared state has been read
+        if (threadIdx.x == 0) {
+            const uint32_t w = atomicAdd(&misc[kMiscTrainNext], 1u);
+            uint32_t code = kQueueEmpty, sleep = 32;
+            for (uint32_t it = 0; w < queue_cap; ++it) {
+                const uint32_t c = atomicAdd(&queue[w], 0u);
+                if (c != kQueueEmpty) {
+                    code = c;
+                    break;
+                }
+                // every tile finished and published: slot w beyond the published units stays empty
+                if (atomicAdd(&misc[kMiscFwdDone], 0u) >= (uint32_t)ntiles) {
+                    __threadfence();  // the final unit count after the last tile's count
+                    if (w >= atomicAdd(&misc[kMiscUnitsPub], 0u)) break;
+                }
+                if (it + 1 == kQueuePolls) {
+                    atomicOr(&misc[kMiscStatus], kStatusTimeout);
+                    break;
+                }
+                __nanosleep(sleep);
+                sleep = min(sleep * 2u, 1024u);
+            }
+            __threadfence();  // acquire: the unit's tile data after its slot
+            sm.maxlast = 0u;
+            s_work = code;
         }
-        if (SPLAT) {  // the ray's screen angles
-            const float ts = atan2f(tr.dx, tr.dz), ps = atan2f(tr.dy, tr.dz);
-            tr.dx = ts;
-            tr.dy = ps;
-        }
-        BwdRay ray = bwd_ray(tr, cam, g0, g1, g2, T, last);
-        if (!top && last > hi) {
-            // the ray walks past this unit: its state in front of entry hi is the forward's checkpoint
-            const float4 c = ckpt[((size_t)t * kCkptMax + k) * kTilePix + tray];
-            const float4 cf = Cfin[pix];
-            ray.T = c.x;
-            const float S0 = fmaf(T, cam.bg[0], cf.x - c.y), S1 = fmaf(T, cam.bg[1], cf.y - c.z),
-                        S2 = fmaf(T, cam.bg[2], cf.z - c.w);
-            ray.gS = fmaf(g0, S0, fmaf(g1, S1, g2 * S2));
-        }
-        const uint32_t warp_last = __reduce_max_sync(0xffffffffu, last);
-        if ((threadIdx.x & 31) == 0) atomicMax(&sm.maxlast, warp_last);
         __syncthreads();
-        const uint32_t block_last = sm.maxlast;
-        if (block_last <= lo) continue;
-        backward_walk<kThreads, BATCH, SPLAT>(sm, s_acc, svals, sranges, rec, p, tr.col, tr.row, tr.cx, tr.cy, plo, lo,
-                                              make_uint2(phi, hi), warp_last, block_last,
-                                              hit ? hit + (int64_t)t * hit_entries : nullptr,
-                                              hit ? idrec + (int64_t)t * hit_entries : nullptr, hit_entries,
-                                              tray >> 5, ray, gacc, items, misc);
+        const uint32_t code = s_work;
+        if (code == kQueueEmpty) break;
+        bwd_unit<ROWS, BATCH, SPLAT, true>(sm, s_acc, code, 0, cams, ncams, ptab, ttab, S, tile_walk, srange, svals,
+                                           sranges, rec, misc, p, dL, Tfin, last, hit, idrec, hit_entries, gacc,
+                                           ntiles, items, cap_pairs, ckpt, ckpt_at, ckpt_cnt, Cfin);
     }
 }
 
@@ -1052,6 +1258,33 @@ cudaError_t launch_render_bwd(const geer_workspace *ws, const float *dL_drgb, cu
         (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs, ws->d_ckpt, ws->d_ckpt_at, ws->d_ckpt_cnt,
         ws->d_Cfin);
     return cudaGetLastError();
+}
+
+cudaError_t launch_render_train(const geer_workspace *ws, const float *target, float *rgb, float *T_final,
+                                float *dL_drgb, float *loss, cudaStream_t s) {
+    if (ws->n_tiles == 0) return cudaSuccess;
+    constexpr int R = GEER_BWD_ROWS, B = GEER_BWD_BATCH;
+    const int64_t m = 3 * ws->n_pixels;  // the L1 mean's value count
+    launch_k(ws->params.alpha_model == GEER_ALPHA_EXACT ? k_render_train<R, B, false> : k_render_train<R, B, true>,
+        dim3((unsigned)std::max(1, ws->train_grid)), dim3(R * kTile), 0, s,
+        ws->d_cams, ws->n_cams, ws->d_pix_tab, ws->d_tile_tab, ws->super_size, ws->d_tile_walk, ws->d_tile_order,
+        ws->d_srange, ws->d_vals[ws->sorted_buf], ws->d_sranges, ws->d_rec, ws->d_misc, ws->params, rgb, T_final,
+        ws->d_Tfin, ws->d_last, ws->d_evals, ws->d_hit, ws->d_idrec, ws->hit_entries,
+        ws->tile_mask_on ? static_cast<const uint8_t *>(ws->d_tile_mask) : nullptr, ws->n_tiles,
+        (uint64_t)ws->n_cams * (uint64_t)ws->n_gauss, ws->cap_pairs, ws->d_ckpt, ws->d_ckpt_at, ws->d_ckpt_cnt,
+        ws->d_unit_rec, ws->d_Cfin, target, dL_drgb, m > 0 ? 1.0f / (float)m : 0.0f, loss, ws->d_gacc,
+        ws->d_bwd_order, (uint32_t)(ws->n_tiles * (kCkptMax + 1)));
+    return cudaGetLastError();
+}
+
+int render_train_blocks_per_sm(int alpha_model) {
+    constexpr int R = GEER_BWD_ROWS, B = GEER_BWD_BATCH;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, alpha_model == GEER_ALPHA_EXACT ? k_render_train<R, B, false> : k_render_train<R, B, true>,
+            R * kTile, 0) != cudaSuccess)
+        b = 1;
+    return b < 1 ? 1 : b;
 }
 
 int render_bwd_blocks_per_sm(int alpha_model) {

@@ -51,9 +51,10 @@ EXPORTS = ["geer_status_string", "geer_default_params", "geer_workspace_size", "
            "geer_densify_plan", "geer_densify_apply", "geer_opacity_reset", "geer_render_bwd_tiles",
            "geer_grad_accumulators", "geer_preprocess_bwd", "geer_tile_owners", "geer_set_tile_mask",
            "geer_tile_counts", "geer_checked_build", "geer_bounds_violation", "geer_debug_set_render_order",
-           "geer_enable_stage_timing"]
+           "geer_enable_stage_timing", "geer_render_train_l1"]
 
 _lib = None
+N_STAGES = 10  # the stages geer_stage_name names (geer_stage_times fills that many)
 
 
 _lib_checked = None
@@ -114,6 +115,7 @@ def lib(build_if_missing: bool = True, checked: bool = False):
         "geer_densify_apply": [I64, I32, P, P, P, P, P, P, P, P, P, C.c_size_t, I64, P, P, P, P, P, P, P, P, P, P],
         "geer_opacity_reset": [I64, I32, C.c_float, P, P, P, P, P],
         "geer_render_bwd_tiles": [P, P, P],
+        "geer_render_train_l1": [P, P, P, P, P, P, P],
         "geer_grad_accumulators": [P, P, P],
         "geer_preprocess_bwd": [P, P, P, P, P, P, P, I32, P],
         "geer_tile_owners": [P, I32, I32, P],
@@ -303,6 +305,19 @@ class Workspace:
                                      _stream(stream)),
                "geer_render_bwd")
 
+    def render_train_l1(self, target: torch.Tensor, rgb: torch.Tensor, dL_drgb: torch.Tensor,
+                        loss: torch.Tensor | None = None, T_final: torch.Tensor | None = None, stream=None):
+        """Forward, L1 gradient against target and the backward's render stage in
+        one launch (geer_render_train_l1): rgb, dL_drgb, loss (a device f32 [1],
+        or None) and the accumulators, as render_fwd + l1_loss_grad +
+        render_bwd_tiles; then preprocess_bwd."""
+        _check(self._L.geer_render_train_l1(self._handle, C.c_void_p(target.data_ptr()), C.c_void_p(rgb.data_ptr()),
+                                          C.c_void_p(T_final.data_ptr()) if T_final is not None else None,
+                                          C.c_void_p(dL_drgb.data_ptr()),
+                                          C.c_void_p(loss.data_ptr()) if loss is not None else None,
+                                          _stream(stream)),
+               "geer_render_train_l1")
+
     def render_bwd_tiles(self, dL_drgb: torch.Tensor, stream=None):
         """The render stage of the backward (geer_render_bwd_tiles): the
         per-(camera, Gaussian) accumulators over the rendered tiles' rays."""
@@ -428,7 +443,7 @@ class Workspace:
         if stages is None or not on:
             _check(self._L.geer_enable_timing(self._handle, 1 if on else 0), "geer_enable_timing")
             return
-        names = [self._L.geer_stage_name(i).decode() for i in range(9)]
+        names = [self._L.geer_stage_name(i).decode() for i in range(N_STAGES)]
         mask = sum(1 << names.index(n) for n in stages)
         _check(self._L.geer_enable_stage_timing(self._handle, mask), "geer_enable_stage_timing")
 
@@ -437,7 +452,7 @@ class Workspace:
         ms = (C.c_float * 16)()
         cnt = (C.c_int32 * 16)()
         _check(self._L.geer_stage_times(self._handle, ms, 16, cnt, _stream(stream)), "geer_stage_times")
-        return {self._L.geer_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(9)}
+        return {self._L.geer_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(N_STAGES)}
 
     def debug_pairs(self, cap: int | None = None, stream=None):
         cap = self.pair_capacity if cap is None else cap
