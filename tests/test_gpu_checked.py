@@ -9,6 +9,10 @@ record the first one (site and index) next to the device status word.
   libgeer.so refuses the same schedule on the host. The planted index stays
   within the workspace's tile capacity, so no access could leave the
   workspace's arrays even without the guard.
+- The fused training render with the checked build: no violation on a
+  normal step, and the planted schedule entry recorded and skipped there
+  too, with the launch ending (its unit queue does not wait for the skipped
+  tile).
 """
 import math
 
@@ -104,3 +108,48 @@ def test_planted_tile_index_is_recorded_and_skipped(libs):
     skipped[16:32, 16:32] = True  # tile 5 = (1, 1) of a 4-wide grid was taken out of the schedule
     assert torch.all(img[skipped] == -1.0)
     assert torch.equal(img[~skipped], ref[~skipped])
+
+
+def test_checked_build_fused_render(libs):
+    """The fused training render (forward, L1 gradient and the backward's render
+    stage in one launch) records no violation and matches the plain build."""
+    geer, plain, checked = libs
+    target = torch.as_tensor(np.random.default_rng(4).uniform(0, 1, (SMALL.pixels, 3)).astype(np.float32),
+                             device="cuda")
+    out = {}
+    for name, L in (("plain", plain), ("checked", checked)):
+        ws, g = _workspace(geer, L)
+        rgb, dL = torch.empty((SMALL.pixels, 3), device="cuda"), torch.empty((SMALL.pixels, 3), device="cuda")
+        ws.render_train_l1(target, rgb, dL)
+        grads = {k: torch.empty_like(v) for k, v in (("mean", g.mean), ("scale", g.scale), ("quat", g.quat),
+                                                     ("opacity", g.opacity), ("sh", g.sh))}
+        ws.preprocess_bwd(g, grads, accumulate=False)
+        assert ws.device_status()[0] == geer.OK
+        assert ws.bounds_violation() == (0, 0)
+        out[name] = (rgb.cpu(), dL.cpu(), {k: v.cpu() for k, v in grads.items()})
+    assert torch.equal(out["plain"][0], out["checked"][0]) and torch.equal(out["plain"][1], out["checked"][1])
+    for k, a in out["plain"][2].items():
+        b = out["checked"][2][k]
+        assert float((a - b).abs().max()) <= 1e-4 * float(a.abs().max()) + 1e-12, k
+
+
+def test_planted_tile_index_in_the_fused_render(libs):
+    """The same planted schedule entry in the fused render: the guard records it,
+    the block counts the tile as finished with no units, and the launch ends
+    (the backward's queue never waits for the skipped tile)."""
+    geer, _, checked = libs
+    order = np.arange(12, dtype=np.uint32)
+    order[5] = 12 + 3
+    ws, g = _workspace(geer, checked)
+    target = torch.zeros((SMALL.pixels, 3), device="cuda")
+    rgb, dL = torch.full((SMALL.pixels, 3), -1.0, device="cuda"), torch.empty((SMALL.pixels, 3), device="cuda")
+    ws.set_render_order(order)
+    ws.render_train_l1(target, rgb, dL)
+    torch.cuda.synchronize()
+    st, _ = ws.device_status()
+    assert st == geer.ERR_BOUNDS  # not ERR_TIMEOUT: the queue drained
+    assert ws.bounds_violation() == (SITE_FWD_TILE, 15)
+    img = rgb.view(SMALL.height, SMALL.width, 3)
+    skipped = torch.zeros((SMALL.height, SMALL.width), dtype=torch.bool, device="cuda")
+    skipped[16:32, 16:32] = True
+    assert torch.all(img[skipped] == -1.0) and torch.all(img[~skipped] >= 0.0)
