@@ -598,7 +598,9 @@ def run(args):
     sh_bytes = 4 * 3 * (scene.sh_degree + 1) ** 2
     g_bytes = 4 * (3 + 3 + 4 + 1) + sh_bytes
     work = {
-        "preprocess": ("hbm", scene.n * g_bytes + n_items * (64 + 16 + 4 + 4)),
+        # record, ranges, count, key per item; in the training step also the item's
+        # backward accumulators zeroed (64 B)
+        "preprocess": ("hbm", scene.n * g_bytes + n_items * (64 + 16 + 4 + 4 + (64 if have_bwd else 0))),
         "depth_sort": ("hbm", 4 * 20 * live),
         # per live item: id, tile count and ranges read; 8 B per (super-tile, item) pair written
         "duplicate": ("hbm", live * (4 + 4 + 16) + int(super_pairs) * 8),

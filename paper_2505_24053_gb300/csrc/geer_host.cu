@@ -604,13 +604,16 @@ geer_status geer_preprocess(geer_workspace *ws, const geer_gaussians *g, void *s
     ws->sh_degree = g->sh_degree;
     ws->stage = 1;
     StageTimer tm(ws, kStagePreprocess, static_cast<cudaStream_t>(stream));
-    return cuda_status(launch_preprocess(ws, g, static_cast<cudaStream_t>(stream)));
+    st = cuda_status(launch_preprocess(ws, g, static_cast<cudaStream_t>(stream)));
+    ws->acc_zero = st == GEER_OK && ws->trains;  // the kernel zeroed the items' accumulators
+    return st;
 }
 
 geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *stream) {
     if (!ws) return GEER_ERR_ARG;
     if (ws->stage < 1) return GEER_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ws->queue_ready = false;
     // live items in index order -> stable depth sort -> pair counts in depth order
     {
         StageTimer tm(ws, kStageBinFront, s);
@@ -649,6 +652,7 @@ geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *strea
         StageTimer tm(ws, kStageTileSort, s);
         if (launch_tile_sort(ws, s) != cudaSuccess) return GEER_ERR_CUDA;
     }
+    ws->queue_ready = ws->trains;  // the render order's kernel reset the unit queue
     ws->stage = 2;
     return GEER_OK;
 }
@@ -683,7 +687,11 @@ geer_status geer_render_bwd_tiles(geer_workspace *ws, const float *dL_drgb, void
     if (ws->stage < 3) return GEER_ERR_STATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
-    if (items > 0 && cudaMemsetAsync(ws->d_gacc, 0, sizeof(GradAcc) * items, s) != cudaSuccess) return GEER_ERR_CUDA;
+    if (!ws->acc_zero && items > 0 && cudaMemsetAsync(ws->d_gacc, 0, sizeof(GradAcc) * items, s) != cudaSuccess)
+        return GEER_ERR_CUDA;
+    ws->acc_zero = false;
+    ws->queue_ready = false;  // the unit order overwrites the queue
+    ws->trains = true;        // from now on the preprocess zeroes the accumulators
     {
         StageTimer tm(ws, kStageRenderBwd, s);
         if (launch_bwd_order(ws, s) != cudaSuccess || launch_render_bwd(ws, dL_drgb, s) != cudaSuccess)
@@ -700,12 +708,18 @@ geer_status geer_render_train_l1(geer_workspace *ws, const float *target, float 
     if (ws->hit_entries == 0) return GEER_ERR_UNSUPPORTED;  // a forward-only workspace has no backward state
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t items = (int64_t)ws->n_cams * ws->n_gauss;
-    if ((items > 0 && cudaMemsetAsync(ws->d_gacc, 0, sizeof(GradAcc) * items, s) != cudaSuccess) ||
+    // the accumulators and the unit queue: zeroed / reset by the preprocess and the
+    // binning of this step unless a backward has used them since
+    if ((!ws->acc_zero && items > 0 && cudaMemsetAsync(ws->d_gacc, 0, sizeof(GradAcc) * items, s) != cudaSuccess) ||
         (loss && cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) ||
-        cudaMemsetAsync(ws->d_bwd_order, 0xff, sizeof(uint32_t) * ws->n_tiles * (kCkptMax + 1), s) != cudaSuccess ||
-        cudaMemsetAsync(ws->d_misc + kMiscFwdNext, 0, sizeof(uint32_t) * (kMiscTrainNext - kMiscFwdNext + 1), s) !=
-            cudaSuccess)
+        (!ws->queue_ready &&
+         (cudaMemsetAsync(ws->d_bwd_order, 0xff, sizeof(uint32_t) * ws->n_tiles * (kCkptMax + 1), s) != cudaSuccess ||
+          cudaMemsetAsync(ws->d_misc + kMiscFwdNext, 0, sizeof(uint32_t) * (kMiscTrainNext - kMiscFwdNext + 1), s) !=
+              cudaSuccess)))
         return GEER_ERR_CUDA;
+    ws->acc_zero = false;
+    ws->queue_ready = false;
+    ws->trains = true;  // from now on the preprocess and the binning prepare the accumulators and the queue
     {
         StageTimer tm(ws, kStageRenderTrain, s);
         if (launch_render_train(ws, target, rgb, T_final, dL_drgb, loss, s) != cudaSuccess) return GEER_ERR_CUDA;

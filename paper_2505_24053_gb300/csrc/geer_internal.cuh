@@ -255,6 +255,7 @@ __device__ __forceinline__ int order_bucket(uint32_t c) {
 // byte k (k <= kCkptMax) the schedule bucket of unit k, byte 15 the number of
 // units (0: nothing to walk back).
 constexpr int kUnitCountByte = 15;
+static_assert(kMiscTrainNext == kMiscFwdNext + 3, "the fused render's four counters are contiguous");
 static_assert(kCkptMax + 1 <= kUnitCountByte, "the unit buckets and their count share one uint4");
 
 // Stages timed by geer_enable_timing (CUDA events around each stage's kernels).
@@ -340,6 +341,9 @@ struct geer_workspace {
     int64_t n_gauss;
     int32_t sh_degree;
     int stage;               // 0 none, 1 preprocessed, 2 sorted, 3 rendered, 4 render-stage gradients
+    bool trains;             // a backward has run on this workspace: the preprocess and the binning prepare the next
+    bool acc_zero;           // the last preprocess zeroed the items' accumulators; no backward since
+    bool queue_ready;        // the last bin_sort reset the fused render's unit queue; not used since
     int sorted_buf;          // which ping-pong buffer holds the sorted super-tile pairs
     int sort_grid;           // grid of the radix kernels (grid-stride over sort tiles)
     int num_sms;

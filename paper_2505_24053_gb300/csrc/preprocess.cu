@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
     const DevCam *__restrict__ cams, int ncams, const float4 *__restrict__ ttab, Params p,
     const float *__restrict__ mean, const float *__restrict__ scale, const float *__restrict__ quat,
     const float *__restrict__ opacity, const float *__restrict__ sh, int64_t n, Record *__restrict__ rec,
-    uint4 *__restrict__ ranges, uint32_t *__restrict__ count, uint32_t *__restrict__ key,
+    uint4 *__restrict__ ranges, GradAcc *__restrict__ gacc, uint32_t *__restrict__ count, uint32_t *__restrict__ key,
     uint32_t *__restrict__ blocksum, int64_t nblk) {
     grid_dep_sync();
     constexpr int NC = 3 * (DEG + 1) * (DEG + 1), ST = PrepSh<DEG>::kStride;
@@ -673,6 +673,11 @@ __global__ void __launch_bounds__(kPrepThreads, GEER_PREP_MINB) k_preprocess(
             for (int i = 0; i < 4; ++i) dst[i] = src[i];
         }
         if (g < n) count[idx] = cnt;
+        if (g < n && gacc) {  // every item's backward accumulators start from zero
+            float4 *acc = reinterpret_cast<float4 *>(gacc + idx);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
         uint32_t tot = block_sum_u32(cnt > 0 ? 1u : 0u, red);
         if (threadIdx.x == 0) blocksum[(int64_t)ci * nblk + blockIdx.x] = tot;
     }
@@ -988,9 +993,15 @@ __device__ __forceinline__ uint32_t block_chunk_prefix(uint32_t s, uint32_t *war
 // with the length capped at 16K - 1K entries and 0.424 ms in tile order.)
 __global__ void __launch_bounds__(1024) k_tile_offsets(const DevCam *__restrict__ cams, int ncams, int S,
                                                        int ntiles, uint2 *__restrict__ srange, int nst,
-                                                       const uint32_t *__restrict__ misc,
-                                                       uint32_t *__restrict__ tile_order) {
+                                                       uint32_t *__restrict__ misc,
+                                                       uint32_t *__restrict__ tile_order,
+                                                       uint32_t *__restrict__ queue, uint32_t queue_n) {
     grid_dep_sync();
+    // the fused render's unit queue and its counters start afresh with every binning
+    if (queue) {
+        for (uint32_t i = threadIdx.x; i < queue_n; i += 1024) queue[i] = 0xffffffffu;
+        if (threadIdx.x < 4) misc[kMiscFwdNext + threadIdx.x] = 0u;
+    }
     constexpr int kOrderSmem = 16384;  // super-tiles / tiles whose buckets the block keeps in shared memory
     __shared__ uint32_t warp_tot[32];
     __shared__ uint32_t hist[kOrderBuckets];
@@ -1129,7 +1140,8 @@ cudaError_t launch_preprocess(const geer_workspace *ws, const geer_gaussians *g,
         }                                                                                                        \
         launch_k(kern, dim3((unsigned)nblk), dim3(kPrepThreads), smem, s, ws->d_cams, ws->n_cams,                 \
                  ws->d_tile_tab, prm, g->mean, g->scale, g->quat, g->opacity, g->sh, g->n, ws->d_rec,            \
-                 ws->d_ranges, ws->d_count, ws->d_key, ws->d_blocksum, nblk);                             \
+                 ws->d_ranges, ws->trains ? ws->d_gacc : nullptr, ws->d_count, ws->d_key,                    \
+                 ws->d_blocksum, nblk);                                                                   \
     }
     switch (g->sh_degree) {
         case 0: GEER_PREP_LAUNCH(0); break;
@@ -1179,7 +1191,8 @@ cudaError_t launch_duplicate(const geer_workspace *ws, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     launch_k(k_tile_offsets, dim3(1), dim3(1024), 0, s, ws->d_cams, ws->n_cams, ws->super_size, (int)ws->n_tiles,
-             ws->d_srange, (int)ws->n_stiles, ws->d_misc, ws->d_tile_order);
+             ws->d_srange, (int)ws->n_stiles, ws->d_misc, ws->d_tile_order,
+             ws->trains ? ws->d_bwd_order : nullptr, (uint32_t)(ws->n_tiles * (kCkptMax + 1)));
     return cudaGetLastError();
 }
 

@@ -190,3 +190,34 @@ def test_fused_errors(geer):
     with pytest.raises(geer.GeerError) as e:
         ws.render_train_l1(x, x.clone(), x.clone())  # before bin_sort
     assert e.value.status == geer.ERR_STATE
+
+
+def test_fused_repeated_without_a_new_binning(geer):
+    """The step's preprocess zeroes the accumulators and its binning resets the
+    unit queue; a fused render that follows another render stage without a new
+    preprocess or binning must reset them itself: the same results every time."""
+    scene = wl.cube_scene(20000, 7, 3)
+    cams = [wl.Camera(wl.KANNALA_BRANDT, 160, 128, math.radians(190), k=wl.kb_coeffs(3))]
+    g = geer.Gaussians.from_scene(scene)
+    npix = cams[0].pixels
+    target = _target(npix, 8)
+    ws = geer.Workspace(cams, scene.n, scene.sh_degree, 4_000_000)
+    sep = _separate(geer, ws, g, target, npix)  # leaves the queue holding the separate backward's unit order
+    runs = []
+    for _ in range(2):  # twice after the same binning
+        rgb, dL = torch.empty((npix, 3), device="cuda"), torch.empty((npix, 3), device="cuda")
+        loss = torch.empty(1, device="cuda")
+        ws.render_train_l1(target, rgb, dL, loss)
+        acc = ws.grad_accumulators().clone()
+        grads = _grads_like(g)
+        ws.preprocess_bwd(g, grads, accumulate=False)
+        torch.cuda.synchronize()
+        assert ws.device_status()[0] == geer.OK
+        runs.append((rgb, sep[1], dL, float(loss.item()), acc, grads))
+    for run in runs:
+        rgb, T, dL, loss, acc, grads = run
+        assert torch.equal(rgb, sep[0]) and torch.equal(dL, sep[2])
+        assert loss == pytest.approx(sep[3], rel=1e-5)
+        assert _rel(acc, sep[4]) <= 1e-5
+        for k in BLOCKS:
+            assert _rel(grads[k], sep[5][k]) <= 1e-4, k
