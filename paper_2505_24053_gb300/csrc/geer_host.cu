@@ -660,6 +660,7 @@ geer_status geer_bin_sort(geer_workspace *ws, int64_t *pairs_needed, void *strea
 geer_status geer_render_fwd(geer_workspace *ws, float *rgb, float *T_final, void *stream) {
     if (!ws || !rgb) return GEER_ERR_ARG;
     if (ws->stage < 2) return GEER_ERR_STATE;
+    ws->trains = false;  // forward-only steps: the next preprocess leaves the accumulators (a backward turns it back on)
     geer_status st;
     {
         StageTimer tm(ws, kStageRenderFwd, static_cast<cudaStream_t>(stream));

@@ -341,7 +341,7 @@ struct geer_workspace {
     int64_t n_gauss;
     int32_t sh_degree;
     int stage;               // 0 none, 1 preprocessed, 2 sorted, 3 rendered, 4 render-stage gradients
-    bool trains;             // a backward has run on this workspace: the preprocess and the binning prepare the next
+    bool trains;             // the last render stage was a backward: the preprocess and the binning prepare the next
     bool acc_zero;           // the last preprocess zeroed the items' accumulators; no backward since
     bool queue_ready;        // the last bin_sort reset the fused render's unit queue; not used since
     int sorted_buf;          // which ping-pong buffer holds the sorted super-tile pairs
